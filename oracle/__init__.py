@@ -1,0 +1,24 @@
+"""CPU oracle for the LRDMC hot path — TEST INFRASTRUCTURE ONLY.
+
+A plain, slow, FP64 restatement of what the walker propagation and branching
+step compute, written from the paper (Nakano, Sorella, Casula, "Load-Balanced
+Diffusion Monte Carlo Method with Lattice Regularization", arXiv 2508.12033)
+and from the plain definitions of the trial-wavefunction quantities:
+
+* ``philox``       counter-based random numbers (Philox4x32-10, Salmon et al. 2011)
+* ``wavefunction`` Slater-Jastrow values, ratios by freshly computed determinants
+* ``hamiltonian``  lattice-regularised fixed-node Hamiltonian: hops, V_sf, W, e_L
+* ``lrdmc``        load-balanced and conventional steps, reconfiguration, run loop
+* ``estimator``    global population factor, weighted energy, blocked error bar
+
+It shares no code with the CUDA library and never imports it.  Only the test
+suite, the smoke check and the benchmark's CPU-baseline leg may import it; the
+product path must never route through it.
+
+Parity status: every function is pinned by a test against something other than
+itself (closed forms, brute force, invariants, exact diagonalisation, an
+independent Philox implementation), except the two readings listed as
+"parity unpinned" in the design notes: the E_0 update rule / estimator
+parameters and the per-electron nodal-regularisation rule for node-crossing
+electrons.
+"""

@@ -1,0 +1,256 @@
+"""Pins for the oracle's schedules, heat-bath choice, reconfiguration and
+estimator: closed forms, invariants, distribution laws and an exact
+diagonalisation of a one-electron lattice Hamiltonian."""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+from scipy import stats
+
+import workloads as W
+from oracle import estimator as est
+from oracle import lrdmc as L
+from oracle import philox
+
+
+# ---------------------------------------------------------------- reconfiguration
+@pytest.mark.parametrize("n", [1, 2, 7, 100, 4096])
+def test_reconfiguration_invariants(n):
+    rng = np.random.default_rng(n)
+    w = rng.lognormal(0.0, 0.7, n)
+    xi = int(rng.integers(0, 2**32))
+    src = L.reconfigure_indices(w, xi)
+    assert len(src) == n
+    assert np.all(np.diff(src) >= 0)                    # comb order is monotone
+    counts = np.bincount(src, minlength=n)
+    expect = n * w / w.sum()
+    # each walker is copied floor or ceil of N w / sum w times (up to 2^-S quantisation)
+    assert np.all(counts >= np.floor(expect - 1e-9)) and np.all(counts <= np.ceil(expect + 1e-9))
+
+
+def test_reconfiguration_equal_weights_is_identity():
+    for n in (1, 5, 1000):
+        for xi in (0, 1, 2**31, 2**32 - 1):
+            np.testing.assert_array_equal(L.reconfigure_indices(np.full(n, 3.7), xi), np.arange(n))
+
+
+def test_reconfiguration_matches_float_comb():
+    """Against the comb of Eq. (correlated random numbers) in exact rational
+    arithmetic on the same quantised weights, for random inputs."""
+    from fractions import Fraction
+    rng = np.random.default_rng(1)
+    for n in (3, 17, 64):
+        w = rng.random(n) ** 3
+        xi = int(rng.integers(0, 2**32))
+        S = L.quant_shift(n)
+        wmax = w.max()
+        q = [int(math.floor((v / wmax) * 2.0**S)) for v in w]
+        tot = sum(q)
+        cum = np.cumsum(q)
+        ref = []
+        for alpha in range(n):
+            z = (Fraction(xi, 2**32) + alpha) / n
+            ref.append(next(b for b in range(n) if z < Fraction(int(cum[b]), tot)))
+        np.testing.assert_array_equal(L.reconfigure_indices(w, xi), ref)
+
+
+def test_reconfiguration_unbiased_copy_counts():
+    """E[copies of b] = N w_b / sum w over the comb offset xi."""
+    w = np.array([0.1, 2.0, 0.5, 0.5, 1.4, 0.0])
+    n = len(w)
+    acc = np.zeros(n)
+    m = 4000
+    for xi in np.linspace(0, 2**32 - 1, m).astype(np.int64):
+        acc += np.bincount(L.reconfigure_indices(w, int(xi)), minlength=n)
+    np.testing.assert_allclose(acc / m, n * w / w.sum(), atol=2e-3)
+
+
+# ------------------------------------------------------------------- heat bath
+def test_heat_bath_choice_distribution():
+    rng = np.random.default_rng(2)
+    r = rng.normal(0.5, 0.6, (1, 12))
+    n = 200000
+    u = rng.random(n)
+    hop = L.choose_hop(np.repeat(r, n, axis=0), u)
+    kept = np.where(r[0] > 0, r[0], 0.0)
+    counts = np.bincount(hop, minlength=12)
+    assert np.all(counts[kept == 0] == 0)
+    expect = n * kept / kept.sum()
+    m = kept > 0
+    chi2 = np.sum((counts[m] - expect[m]) ** 2 / expect[m])
+    assert stats.chi2.sf(chi2, m.sum() - 1) > 1e-4
+    assert np.all(L.choose_hop(-np.abs(r), np.array([0.3])) == -1)
+
+
+def test_heat_bath_edge_uniforms():
+    r = np.array([[0.0, 1.0, -2.0, 3.0, 0.0, 0.0]])
+    assert L.choose_hop(r, np.array([0.0]))[0] == 1
+    assert L.choose_hop(r, np.array([1.0 - 2.0**-53]))[0] == 3
+    assert L.choose_hop(r, np.array([0.2499999]))[0] == 1
+    assert L.choose_hop(r, np.array([0.25]))[0] == 3          # strict '>' on the running sum
+
+
+# --------------------------------------------------------- exact H atom end to end
+@pytest.mark.parametrize("schedule", [L.LOAD_BALANCED, L.CONVENTIONAL])
+def test_exact_wavefunction_zero_variance_run(schedule):
+    s = W.hydrogen_atom_sto(1.0)
+    x0 = W.initial_walkers(s, 32, seed=3)
+    h, Wk = L.run(s, x0, 0.2, schedule, 8, seed=1, n_proj=10, tau=0.07)
+    assert abs(h.energy + 0.5) < 1e-12
+    np.testing.assert_allclose(h.ebar, -0.5, atol=1e-12)
+    if schedule == L.CONVENTIONAL:
+        # w = exp(-tau e_L) exactly for a constant local energy
+        np.testing.assert_allclose(h.wbar, math.exp(0.07 * 0.5), rtol=1e-13)
+    assert h.status_or == 0
+
+
+# ------------------------------------------------ conventional persistence times
+class _ConstEval:
+    """Stand-in Hamiltonian with every hop ratio equal (b_bar constant), local
+    energy e: the number of hops in tau is a Poisson(tau b_bar) count."""
+
+    def __init__(self, ratio, a, e=0.0):
+        self.ratio, self.a, self.e = ratio, a, e
+
+    def __call__(self, sys, x, a, node_rule=0):
+        n = x.shape[0]
+        ne = x.shape[1]
+        bbar = 6 * ne * self.ratio / (2 * a * a)
+        return dict(ratios=np.full((n, ne, 6), self.ratio), bbar=np.full(n, bbar),
+                    vsf=np.zeros(n), W=np.full(n, bbar + self.e), eL=np.full(n, self.e),
+                    n_node=np.zeros(n, np.int64), lap=np.zeros((n, ne)),
+                    nu_opt=np.zeros((n, ne)))
+
+
+def test_conventional_hop_count_is_poisson(monkeypatch):
+    a = 0.5
+    fake = _ConstEval(1.0 / 3.0, a, e=0.3)
+    monkeypatch.setattr(L.ham, "evaluate", fake)
+    s = W.hydrogen_atom_sto()
+    n = 20000
+    Wk = L.init_walkers(s, np.zeros((n, 1, 3)), a)
+    bbar = 2.0 * 1.0 / (a * a) * 1.0 / 1.0   # 6 * (1/3) / (2 a^2) = 1/a^2 = 4
+    tau = 2.5
+    L.propagate_conventional(s, Wk, a, tau, seed=9, interval=4)
+    lam = tau * 4.0
+    assert abs(Wk.moves.mean() - lam) < 4 * math.sqrt(lam / n)
+    assert abs(Wk.moves.var() / lam - 1.0) < 0.05
+    ks = np.arange(0, 30)
+    obs = np.bincount(Wk.moves, minlength=30)[:30]
+    exp_ = n * stats.poisson.pmf(ks, lam)
+    m = exp_ > 5
+    chi2 = np.sum((obs[m] - exp_[m]) ** 2 / exp_[m])
+    assert stats.chi2.sf(chi2, m.sum() - 1) > 1e-4
+    np.testing.assert_allclose(Wk.w, math.exp(-tau * 0.3), rtol=1e-12)
+    del bbar
+
+
+def test_conventional_slowest_walker_grows_with_population(monkeypatch):
+    """Appendix C's emulation: the mean number of hops to exhaust tau is flat in
+    N_w while the maximum (what a synchronised interval waits for) grows."""
+    a = 1.0
+    monkeypatch.setattr(L.ham, "evaluate", _ConstEval(1.0 / 3.0, a))
+    s = W.hydrogen_atom_sto()
+    means, maxs = [], []
+    for n in (10, 100, 1000, 10000):
+        Wk = L.init_walkers(s, np.zeros((n, 1, 3)), a)
+        L.propagate_conventional(s, Wk, a, 5.0, seed=3, interval=0)
+        means.append(Wk.moves.mean())
+        maxs.append(Wk.moves.max())
+    assert np.all(np.abs(np.array(means) - 5.0) < 1.5)
+    assert maxs[0] < maxs[1] < maxs[3] and maxs[2] <= maxs[3]
+
+
+def test_load_balanced_every_walker_makes_n_proj_hops():
+    s = W.h2_sto3g()
+    Wk = L.init_walkers(s, W.initial_walkers(s, 16, seed=2), 0.2)
+    L.propagate_lb(s, Wk, 0.2, -1.1, 7, seed=1, interval=0)
+    assert np.all(Wk.moves == 7)
+
+
+# ------------------------------------------------------------- estimator
+def test_estimator_worked_example():
+    # Gbar_0 = 1, Gbar_1 = 2, Gbar_2 = 2*3 (p = 2): E = (1 + 4 + 24) / 9
+    assert abs(est.energy([2.0, 3.0, 5.0], [1.0, 2.0, 4.0], p=2) - 29.0 / 9.0) < 1e-15
+    # p = 1: Gbar = 1, 2, 3
+    assert abs(est.energy([2.0, 3.0, 5.0], [1.0, 2.0, 4.0], p=1) - (1 + 4 + 12) / 6.0) < 1e-15
+    # equilibration cut
+    assert abs(est.energy([2.0, 3.0, 5.0], [1.0, 2.0, 4.0], p=2, n_equil=1) - (4 + 24) / 8.0) < 1e-15
+    # huge weights do not overflow: Gbar = 1, 1e200, 1e400, 1e600, 1e600
+    assert abs(est.energy([1e200] * 5, [1.0, 2.0, 3.0, 4.0, 5.0], p=3) - 4.5) < 1e-12
+
+
+def test_estimator_error_on_iid_series():
+    rng = np.random.default_rng(0)
+    n = 4096
+    e = rng.normal(-1.0, 0.2, n)
+    err = est.energy_error(np.ones(n), e, p=5)
+    assert 0.8 * 0.2 / math.sqrt(n) < err < 1.5 * 0.2 / math.sqrt(n)
+
+
+# ------------------------------------- exact diagonalisation of the lattice problem
+def _lattice_ground_energy(psi, lap_over_psi, a, L_side):
+    """Lowest eigenvalue of H^a (Appendix D) for one electron and a bare proton
+    at the origin, on the sites a (n + 1/2) of an L^3 box (hops that leave the
+    box dropped), for a nodeless guiding function psi(r) with continuum
+    lap psi / psi given in closed form.  Built directly from the paper's
+    definitions: off-diagonal -1/(2a^2) between neighbours; diagonal
+    3/a^2 + nu_zv with nu_zv = -1/r + [Delta_a Psi/Psi - Delta Psi/Psi]/2."""
+    n1 = np.arange(L_side) - L_side // 2
+    c = a * (n1 + 0.5)
+    X, Y, Z = np.meshgrid(c, c, c, indexing="ij")
+    r = np.sqrt(X * X + Y * Y + Z * Z)
+    disc = np.zeros_like(r)
+    for Q in (X, Y, Z):
+        for sgn in (1.0, -1.0):
+            rq = np.sqrt(r * r + 2 * sgn * a * Q + a * a)
+            disc += psi(rq) / psi(r)
+    disc = (disc - 6.0) / (a * a)
+    diag = 3.0 / (a * a) - 1.0 / r + 0.5 * (disc - lap_over_psi(r))
+    N = L_side ** 3
+    idx = np.arange(N).reshape(L_side, L_side, L_side)
+    rows, cols = [], []
+    for ax in range(3):
+        a0 = [slice(None)] * 3
+        a1 = [slice(None)] * 3
+        a0[ax] = slice(0, L_side - 1)
+        a1[ax] = slice(1, L_side)
+        rows.append(idx[tuple(a0)].ravel())
+        cols.append(idx[tuple(a1)].ravel())
+    rr = np.concatenate(rows)
+    cc = np.concatenate(cols)
+    off = -1.0 / (2 * a * a)
+    Hm = sp.coo_matrix((np.full(2 * len(rr), off), (np.concatenate([rr, cc]), np.concatenate([cc, rr]))),
+                       shape=(N, N)).tocsr() + sp.diags(diag.ravel())
+    vals = spla.eigsh(Hm, k=1, which="SA", tol=1e-10)[0]
+    return float(vals[0])
+
+
+ZETA_ED = 0.8
+
+
+def lattice_ground_energy_sto(zeta, a, L_side=56):
+    return _lattice_ground_energy(lambda r: np.exp(-zeta * r),
+                                  lambda r: zeta * zeta - 2.0 * zeta / r, a, L_side)
+
+
+@pytest.mark.parametrize("schedule", [L.LOAD_BALANCED, L.CONVENTIONAL])
+def test_both_schedules_reach_the_lattice_ground_energy(schedule):
+    a = 0.4
+    e_exact = lattice_ground_energy_sto(ZETA_ED, a)
+    s = W.hydrogen_atom_sto(ZETA_ED)
+    x0 = W.lattice_walkers(300, a, seed=4, spread=3)
+    # conventional: tau chosen for ~15 hops per interval (b_bar ~ 6/(2a^2))
+    h, _ = L.run(s, x0, a, schedule, 160, seed=5, n_proj=15, tau=15 / (6 / (2 * a * a)),
+                 p_gbar=20, n_equil=30)
+    assert h.status_or == 0
+    assert h.error < 2e-3
+    assert abs(h.energy - e_exact) < 4 * h.error + 1e-4, (h.energy, h.error, e_exact)
+    if schedule == L.LOAD_BALANCED:
+        # Appendix B: with E_0 at the ground energy, (W - E_0) Psi_G Psi_0 is
+        # stationary under the modified Green's function with eigenvalue 1, so
+        # the mean weight gained per interval is 1 once equilibrated.
+        wb = np.array(h.wbar[30:])
+        assert abs(wb.mean() - 1.0) < 5 * wb.std() / math.sqrt(len(wb)) + 2e-3
