@@ -1,0 +1,233 @@
+/*
+ * lrdmc.h — C ABI of the B300 (sm_103a) LRDMC walker-propagation library.
+ *
+ * Implements the data-parallel hot path of lattice-regularised diffusion Monte
+ * Carlo as described in Nakano, Sorella, Casula, "Load-Balanced Diffusion Monte
+ * Carlo Method with Lattice Regularization" (arXiv 2508.12033):
+ *   - the projection steps of all N_w walkers between two branchings, under the
+ *     conventional fixed-projection-time schedule (Algorithm 1; Sec. II.B, the
+ *     persistence time and continuous-time weight update) and the load-balanced
+ *     fixed-N_proj schedule (Algorithm 2; Sec. II.C, the modified Green's function
+ *     and its partition b_x, b_bar_x, p_{x',x});
+ *   - the lattice-regularised fixed-node Hamiltonian those steps sample
+ *     (Appendix D: 6 N_e single-electron hops of length a, spin-flip term,
+ *     regularised local potential, per-electron nodal/nuclear cap);
+ *   - the reconfiguration (branching) step with the correlated comb of Sec. II.A
+ *     and the global-population-factor energy estimator of Sec. II.A.
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns an lrdmc_status; none aborts, none traps on the
+ *     device.  After a failure lrdmc_last_error() describes it.
+ *   - Inputs passed by host pointer are copied before the call returns; the
+ *     caller keeps ownership.  A handle owns its device state unless the caller
+ *     supplied the workspace (then the caller owns that memory and must keep it
+ *     alive until lrdmc_destroy).
+ *   - Device pointers (marked "device") must be CUDA device (or managed)
+ *     allocations visible from the handle's device, 8-byte aligned.
+ *   - All work is enqueued on the CUDA stream given at creation (NULL = the
+ *     legacy default stream).  Calls marked "synchronises" wait for that stream.
+ *   - Electrons 0..n_up-1 are spin up, n_up..n_up+n_dn-1 spin down; positions are
+ *     row-major [walker][electron][xyz] in bohr, energies in hartree.
+ *   - Hop order of the 6 N_e lattice neighbours: p = 6 i + d with
+ *     d = 0..5 -> (+x, -x, +y, -y, +z, -z) displacements of electron i by a.
+ */
+#ifndef LRDMC_H
+#define LRDMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lrdmc_s* lrdmc_handle;
+
+typedef enum {
+    LRDMC_OK = 0,
+    LRDMC_ERR_ARG = 1,          /* invalid argument (sizes, NULL, out of range)     */
+    LRDMC_ERR_CUDA = 2,         /* a CUDA runtime call failed                        */
+    LRDMC_ERR_NONFINITE = 3,    /* a walker weight or local energy became non-finite */
+    LRDMC_ERR_NEG_DIAG = 4,     /* W(x) - E_0 <= 0 met in a load-balanced step       */
+    LRDMC_ERR_STEP_CAP = 5,     /* a conventional walker reached max_moves           */
+    LRDMC_ERR_SINGULAR = 6,     /* a Slater matrix had a zero pivot                  */
+    LRDMC_ERR_UNSUPPORTED = 7   /* system too large for the kernels' on-chip layout  */
+} lrdmc_status;
+
+/* Per-walker status bits (sticky until lrdmc_clear_status). */
+#define LRDMC_WALKER_NEG_DIAG  1u   /* W - E_0 <= 0: the step weight was set to 0    */
+#define LRDMC_WALKER_NONFINITE 2u
+#define LRDMC_WALKER_STEP_CAP  4u
+#define LRDMC_WALKER_STUCK     8u   /* no hop kept by the fixed-node rule (b_bar = 0) */
+#define LRDMC_WALKER_SINGULAR  16u
+
+/* Nuclei and electron counts (Appendix D: V_loc = sum nu_ei + sum nu_ee + V_ii). */
+typedef struct {
+    int n_nuc;
+    const double* R;         /* host, n_nuc x 3                                      */
+    const double* Z;         /* host, n_nuc: charge (valence charge for pseudo)      */
+    const int* pot_kind;     /* host, n_nuc: 0 bare -Z/r, 1 screened -Z erf(r/r_c)/r */
+    const double* r_c;       /* host, n_nuc: screening radius (kind 1 only)          */
+    int n_up, n_dn;
+} lrdmc_system;
+
+/* Slater-Jastrow guiding function Psi_G = det A_up det A_dn exp(J).
+ * Shell s: type shell_l[s] (0 = s, 1 = p with functions x,y,z, -1 = Slater 1s
+ * exp(-zeta r)), centred on nucleus shell_atom[s], primitives
+ * exps/coefs[off_s .. off_s + shell_nprim[s]) with off_s the running sum of
+ * shell_nprim.  A contracted function is angular(d) * sum_g coefs_g exp(-exps_g |d|^2)
+ * (Slater type: sum_g coefs_g exp(-exps_g |d|)); coefficients are used as given.
+ * Orbitals phi_k = sum_mu C[k][mu] chi_mu; both spins use orbitals 0..n_sigma-1.
+ * J = sum_{i<j} c r_ij/(1 + j2_b r_ij) - sum_{i,I} j1_A[I] r_iI/(1 + j1_B[I] r_iI),
+ * c = j2_anti for opposite spins, j2_par for equal spins. */
+typedef struct {
+    int n_shell;
+    const int* shell_atom;
+    const int* shell_l;
+    const int* shell_nprim;
+    const double* exps;
+    const double* coefs;
+    int n_orb;
+    const double* C;         /* host, n_orb x n_bf, row-major                         */
+    double j2_anti, j2_par, j2_b;
+    const double* j1_A;      /* host, n_nuc                                           */
+    const double* j1_B;      /* host, n_nuc                                           */
+} lrdmc_trial_wf;
+
+typedef enum { LRDMC_CONVENTIONAL = 0, LRDMC_LOAD_BALANCED = 1 } lrdmc_kind;
+
+/* One branching interval.  LOAD_BALANCED: every walker makes n_proj hops
+ * (Algorithm 2).  CONVENTIONAL: every walker runs until its projection time tau
+ * is used up (Algorithm 1), at most max_moves hops. */
+typedef struct {
+    int kind;
+    int n_proj;
+    double tau;
+    int max_moves;
+} lrdmc_schedule;
+
+/* Run parameters.
+ *   a            lattice spacing (Appendix D)
+ *   n_w          number of walkers (fixed by reconfiguration)
+ *   seed         Philox4x32-10 key; streams are keyed by (walker slot, step,
+ *                interval) so every call is reproducible
+ *   node_rule    0: cap nu_zv,i by nu^a_ei only for electrons with a node-crossing
+ *                hop (the paper's rule, per electron); 1: for all electrons when any
+ *                hop crosses; 2: always; -1: never
+ *   reinv_period Slater matrices are re-inverted from scratch every this many
+ *                accepted hops of a walker (Sherman-Morrison in between)
+ *   p_gbar       length p of the global population factor (Sec. II.A)
+ *   n_equil      branchings discarded by lrdmc_energy
+ *   precision    0 = FP64 throughout (the only value accepted so far)          */
+typedef struct {
+    double a;
+    int n_w;
+    uint64_t seed;
+    int node_rule;
+    int reinv_period;
+    int p_gbar;
+    int n_equil;
+    int precision;
+} lrdmc_params;
+
+/* Device bytes a handle needs for this system and parameters (no allocation). */
+lrdmc_status lrdmc_workspace_bytes(const lrdmc_system* sys, const lrdmc_trial_wf* wf,
+                                   const lrdmc_params* prm, size_t* bytes);
+
+/* Create a handle: copies the system and trial function to the device, places
+ * the walkers at x0 (host, n_w x n_e x 3), inverts every Slater matrix from
+ * scratch, evaluates the Hamiltonian at every walker and sets E_0 to the mean
+ * local energy (the initial configurations of Algorithms 1 and 2).
+ * workspace: device memory of at least lrdmc_workspace_bytes, 256-byte aligned,
+ * or NULL to let the library allocate (and free) it.  stream: cudaStream_t or
+ * NULL.  Synchronises. */
+lrdmc_status lrdmc_create(const lrdmc_system* sys, const lrdmc_trial_wf* wf,
+                          const lrdmc_params* prm, const double* x0,
+                          void* workspace, size_t workspace_bytes, void* stream,
+                          lrdmc_handle* out);
+
+lrdmc_status lrdmc_destroy(lrdmc_handle h);
+
+/* One interval: propagate all walkers between two branchings with the given
+ * schedule (weights restart at 1).  Asynchronous. */
+lrdmc_status lrdmc_propagate(lrdmc_handle h, const lrdmc_schedule* sch);
+
+/* Branching step: records wbar_n = sum w / N_w and the walker-averaged local
+ * energy ebar_n (Sec. II.A Eq. for ebar with weights w for the conventional
+ * schedule, Sec. II.C form with weights w/(W - E_0) for the load-balanced one,
+ * selected by the kind of the last lrdmc_propagate), reconfigures the
+ * population with the integer comb (bit-exact, see lrdmc_reconfigure_indices),
+ * resets every weight to 1 and, for the load-balanced schedule, sets E_0 to the
+ * estimator over the history so far.  Synchronises (reads back a few scalars).
+ * Returns the first non-OK status implied by the walkers' status bits. */
+lrdmc_status lrdmc_branch(lrdmc_handle h);
+
+/* Energy estimator E = sum_n Gbar_n^p ebar_n / sum_n Gbar_n^p over branchings
+ * n >= n_equil, Gbar_n^p = prod_{j=1..p} wbar_{n-j}, with a block-jackknife error
+ * (largest over block lengths 1, 2, 4, ... with >= 8 blocks; NaN if too few). */
+lrdmc_status lrdmc_energy(lrdmc_handle h, double* E, double* err);
+
+/* Branching history: up to cap entries of wbar_n, ebar_n, the E_0 used in
+ * interval n, the mean and max hops per walker and the number of distinct
+ * walkers that survived reconfiguration.  Any pointer may be NULL. */
+lrdmc_status lrdmc_history(lrdmc_handle h, int cap, int* n, double* wbar, double* ebar,
+                           double* e0, double* moves_mean, int* moves_max, int* survivors);
+
+lrdmc_status lrdmc_get_e0(lrdmc_handle h, double* e0);
+lrdmc_status lrdmc_set_e0(lrdmc_handle h, double e0);
+
+/* Copy walker state to the host (synchronises).  Any pointer may be NULL.
+ *   x (n_w x n_e x 3), w (n_w), ev (n_w x 4: b_bar, V_sf, W, e_L at the current
+ *   configuration), ratios (n_w x 6 n_e: Psi_G(x_p)/Psi_G(x)), status (n_w),
+ *   moves (n_w: hops in the last interval). */
+lrdmc_status lrdmc_get_walkers(lrdmc_handle h, double* x, double* w, double* ev,
+                               double* ratios, uint32_t* status, int32_t* moves);
+
+/* Replace all walkers (host arrays; w may be NULL for all ones), re-invert and
+ * re-evaluate from scratch.  Synchronises. */
+lrdmc_status lrdmc_set_walkers(lrdmc_handle h, const double* x, const double* w);
+
+lrdmc_status lrdmc_clear_status(lrdmc_handle h);
+
+/* Evaluate the lattice-regularised FN Hamiltonian at n <= n_w arbitrary
+ * configurations (Appendix D), each from a freshly inverted Slater matrix.
+ *   x       device, n x n_e x 3
+ *   ratios  device, n x 6 n_e: Psi_G(x_p)/Psi_G(x) for every hop p
+ *   ev      device, n x 4: b_bar, V_sf, W, e_L
+ *   n_node  device, n: electrons with at least one node-crossing hop
+ * Does not touch the walkers.  Asynchronous. */
+lrdmc_status lrdmc_eval_configs(lrdmc_handle h, int n, const double* x, double* ratios,
+                                double* ev, int32_t* n_node);
+
+/* Reconfiguration indices alone (Sec. II.A, Eqs. for p_alpha and the comb
+ * Z_alpha = (xi + alpha - 1)/N_w), handle-free:
+ *   q_b = floor(w_b / max w * 2^S), S = 62 - bitlength(n), Q = inclusive prefix
+ *   sum, and slot alpha (0-based) copies the first b with
+ *   (xi32 + alpha 2^32) Q_total < n 2^32 Q_b   (exact 128-bit integer test).
+ *   w          device, n doubles, finite, >= 0, not all 0
+ *   src        device, n int32 outputs
+ *   scratch    device, >= lrdmc_reconfigure_scratch_bytes(n) bytes, 256-byte aligned
+ *   status_out device int32 (may be NULL): 0 ok, 1 invalid weights (src untouched)
+ * 1 <= n <= 2^24.  Asynchronous on stream. */
+size_t lrdmc_reconfigure_scratch_bytes(int n);
+lrdmc_status lrdmc_reconfigure_indices(int n, const double* w, uint32_t xi32, int32_t* src,
+                                       void* scratch, size_t scratch_bytes,
+                                       int32_t* status_out, void* stream);
+
+/* Philox4x32-10 block for counter (c0, c1, c2, c3) under key = seed, computed on
+ * the host with the library's own implementation (testing aid). */
+void lrdmc_philox4x32(uint64_t seed, const uint32_t ctr[4], uint32_t out[4]);
+
+/* Number of kernels this handle has launched so far (all entry points). */
+lrdmc_status lrdmc_launch_count(lrdmc_handle h, int64_t* n);
+
+/* The cudaStream_t given at creation (for event timing on that stream). */
+lrdmc_status lrdmc_stream(lrdmc_handle h, void** stream);
+
+const char* lrdmc_last_error(lrdmc_handle h);
+const char* lrdmc_status_string(lrdmc_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LRDMC_H */
