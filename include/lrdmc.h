@@ -159,7 +159,10 @@ lrdmc_status lrdmc_propagate(lrdmc_handle h, const lrdmc_schedule* sch);
  * population with the integer comb (bit-exact, see lrdmc_reconfigure_indices),
  * resets every weight to 1 and, for the load-balanced schedule, sets E_0 to the
  * estimator over the history so far.  Synchronises (reads back a few scalars).
- * Returns the first non-OK status implied by the walkers' status bits. */
+ * Returns LRDMC_ERR_NONFINITE, leaving the population and history unchanged,
+ * when a weight is negative or non-finite or all weights are zero; the other
+ * per-walker conditions (NEG_DIAG, STEP_CAP, STUCK, SINGULAR) do not stop the
+ * run and are reported through the status bits and lrdmc_history. */
 lrdmc_status lrdmc_branch(lrdmc_handle h);
 
 /* Energy estimator E = sum_n Gbar_n^p ebar_n / sum_n Gbar_n^p over branchings
@@ -168,10 +171,12 @@ lrdmc_status lrdmc_branch(lrdmc_handle h);
 lrdmc_status lrdmc_energy(lrdmc_handle h, double* E, double* err);
 
 /* Branching history: up to cap entries of wbar_n, ebar_n, the E_0 used in
- * interval n, the mean and max hops per walker and the number of distinct
- * walkers that survived reconfiguration.  Any pointer may be NULL. */
+ * interval n, the mean and max hops per walker, the number of distinct walkers
+ * that survived reconfiguration and the OR of all walkers' status bits before
+ * it.  *n receives the number of branchings so far.  Any pointer may be NULL. */
 lrdmc_status lrdmc_history(lrdmc_handle h, int cap, int* n, double* wbar, double* ebar,
-                           double* e0, double* moves_mean, int* moves_max, int* survivors);
+                           double* e0, double* moves_mean, int* moves_max, int* survivors,
+                           uint32_t* status_or);
 
 lrdmc_status lrdmc_get_e0(lrdmc_handle h, double* e0);
 lrdmc_status lrdmc_set_e0(lrdmc_handle h, double e0);
@@ -207,7 +212,8 @@ lrdmc_status lrdmc_eval_configs(lrdmc_handle h, int n, const double* x, double* 
  *   w          device, n doubles, finite, >= 0, not all 0
  *   src        device, n int32 outputs
  *   scratch    device, >= lrdmc_reconfigure_scratch_bytes(n) bytes, 256-byte aligned
- *   status_out device int32 (may be NULL): 0 ok, 1 invalid weights (src untouched)
+ *   status_out device, 2 int32 (may be NULL): [0] = 0 ok / 1 invalid weights
+ *              (src untouched), [1] = number of distinct source walkers
  * 1 <= n <= 2^24.  Asynchronous on stream. */
 size_t lrdmc_reconfigure_scratch_bytes(int n);
 lrdmc_status lrdmc_reconfigure_indices(int n, const double* w, uint32_t xi32, int32_t* src,

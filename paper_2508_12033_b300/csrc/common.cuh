@@ -1,0 +1,145 @@
+// Shared definitions of the LRDMC CUDA library: device-side system tables,
+// per-walker memory layout, status bits and the Philox4x32-10 generator.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lrdmc {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int WARP = 32;
+
+// per-walker status bits (mirror LRDMC_WALKER_* in lrdmc.h)
+constexpr uint32_t ST_NEG_DIAG = 1u;
+constexpr uint32_t ST_NONFINITE = 2u;
+constexpr uint32_t ST_STEP_CAP = 4u;
+constexpr uint32_t ST_STUCK = 8u;
+constexpr uint32_t ST_SINGULAR = 16u;
+
+// Scalars kept at the end of every walker block (doubles; integer-valued
+// fields are exact in double up to 2^53).
+enum Scalar : int {
+  SC_W = 0,       // weight accumulated in the current interval
+  SC_BBAR = 1,    // b_bar(x): sum of kept hop ratios / (2 a^2)
+  SC_VSF = 2,     // spin-flip term V_sf(x)
+  SC_WDIAG = 3,   // W(x): diagonal of the FN lattice Hamiltonian
+  SC_EL = 4,      // e_L(x) = W(x) - b_bar(x)
+  SC_NNODE = 5,   // electrons with at least one node-crossing hop
+  SC_STATUS = 6,  // sticky status bits
+  SC_MOVES = 7,   // hops made in the last interval
+  SC_SINCE = 8,   // hops since the last from-scratch inversion
+  SC_COUNT = 16
+};
+
+// System and trial-wavefunction tables in device memory (read-only).
+struct DevSys {
+  int n_nuc, n_shell, n_prim, n_bf, n_orb, n_up, n_dn, n_e, n_max;
+  const double* R;       // n_nuc x 3
+  const double* Z;       // n_nuc
+  const double* rc;      // n_nuc
+  const int* kind;       // n_nuc: 0 bare Coulomb, 1 erf-screened
+  const double* j1A;     // n_nuc
+  const double* j1B;     // n_nuc
+  const int* sh_atom;    // n_shell
+  const int* sh_l;       // n_shell: 0 s, 1 p, -1 Slater 1s
+  const int* sh_nprim;   // n_shell
+  const int* sh_off;     // n_shell: first primitive
+  const int* sh_bf;      // n_shell: first basis function
+  const double* exps;    // n_prim
+  const double* coefs;   // n_prim
+  const double* C;       // n_orb x n_bf
+  double j2_anti, j2_par, j2_b;
+  double v_ii;           // nucleus-nucleus repulsion
+};
+
+// Offsets (in doubles) of the walker block in global memory and of the
+// per-warp working set in shared memory.
+struct Layout {
+  int n_e, n_up, n_dn, n_max, n_bf, n_hop;
+  // global walker block
+  int g_x, g_bt, g_cache, g_rat, g_sc, g_stride;
+  // shared memory per warp
+  int s_x, s_bt, s_g, s_rat, s_cache, s_ej, s_ep, s_chi5, s_phi5, s_u, s_row, s_sc, s_stride;
+};
+
+__host__ __device__ inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+// Slater block of electron i: offset of its B^T block, index inside the spin
+// block and the block order.
+struct SpinRef {
+  int bt_off, ii, n;
+};
+__host__ __device__ inline SpinRef spin_ref(const Layout& L, int i) {
+  SpinRef s;
+  if (i < L.n_up) {
+    s.bt_off = 0; s.ii = i; s.n = L.n_up;
+  } else {
+    s.bt_off = L.n_up * L.n_up; s.ii = i - L.n_up; s.n = L.n_dn;
+  }
+  return s;
+}
+
+// ---------------------------------------------------------------- Philox
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of
+//   (X0,X1,X2,X3) -> (hi(M1 X2) ^ X1 ^ K0, lo(M1 X2), hi(M0 X0) ^ X3 ^ K1, lo(M0 X0))
+// with the key bumped by the Weyl increments between rounds.
+constexpr uint32_t PHILOX_M0 = 0xD2511F53u;
+constexpr uint32_t PHILOX_M1 = 0xCD9E8D57u;
+constexpr uint32_t PHILOX_W0 = 0x9E3779B9u;
+constexpr uint32_t PHILOX_W1 = 0xBB67AE85u;
+
+__host__ __device__ inline void mulhilo32(uint32_t a, uint32_t b, uint32_t& hi, uint32_t& lo) {
+#ifdef __CUDA_ARCH__
+  hi = __umulhi(a, b);
+  lo = a * b;
+#else
+  uint64_t p = (uint64_t)a * (uint64_t)b;
+  hi = (uint32_t)(p >> 32);
+  lo = (uint32_t)p;
+#endif
+}
+
+__host__ __device__ inline void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += PHILOX_W0;
+      k1 += PHILOX_W1;
+    }
+    uint32_t hi0, lo0, hi1, lo1;
+    mulhilo32(PHILOX_M0, c[0], hi0, lo0);
+    mulhilo32(PHILOX_M1, c[2], hi1, lo1);
+    uint32_t n0 = hi1 ^ c[1] ^ k0;
+    uint32_t n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+  }
+}
+
+// Uniform in [0,1): top 32 bits from hi, next 21 from the top of lo, times 2^-53.
+__host__ __device__ inline double uniform53(uint32_t hi, uint32_t lo) {
+  uint64_t v = ((uint64_t)hi << 21) | (uint64_t)(lo >> 11);
+  return (double)v * 0x1p-53;
+}
+
+// Stream layout: counter (walker slot, step, interval, 0) gives the persistence
+// time uniform from words 0-1 and the heat-bath uniform from words 2-3;
+// counter (0, 0, interval, 1) word 0 is the reconfiguration comb offset.
+__host__ __device__ inline void step_uniforms(uint64_t seed, uint32_t walker, uint32_t step,
+                                              uint32_t interval, double& u_tau, double& u_move) {
+  uint32_t c[4] = {walker, step, interval, 0u};
+  philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+  u_tau = uniform53(c[0], c[1]);
+  u_move = uniform53(c[2], c[3]);
+}
+
+__host__ __device__ inline uint32_t branch_offset32(uint64_t seed, uint32_t interval) {
+  uint32_t c[4] = {0u, 0u, interval, 1u};
+  philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+  return c[0];
+}
+
+}  // namespace lrdmc

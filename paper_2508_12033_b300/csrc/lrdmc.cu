@@ -1,0 +1,625 @@
+// Host side of the LRDMC library: handle, workspace layout, launches and the
+// branching-history energy estimator.  See include/lrdmc.h for the ABI.
+#include "lrdmc.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "branch.cuh"
+#include "common.cuh"
+#include "walker.cuh"
+
+using namespace lrdmc;
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+constexpr int MAX_WALKERS = 1 << 24;
+
+size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
+
+// Everything derived from the inputs before any device work.
+struct Plan {
+  int n_nuc = 0, n_shell = 0, n_prim = 0, n_bf = 0, n_orb = 0, n_up = 0, n_dn = 0, n_e = 0, n_max = 0;
+  int n_w = 0;
+  Layout L{};
+  size_t smem_per_warp = 0;
+  // workspace offsets (bytes)
+  size_t o_sys = 0, sys_bytes = 0, o_state = 0, o_alt = 0, state_bytes = 0, o_stats = 0, o_q = 0,
+         o_src = 0, o_dstat = 0, total = 0;
+  // system image offsets (bytes, inside the sys block)
+  size_t i_R, i_Z, i_rc, i_j1A, i_j1B, i_exps, i_coefs, i_C, i_kind, i_atom, i_l, i_nprim, i_off, i_bf;
+  std::string err;
+};
+
+bool make_plan(const lrdmc_system* sys, const lrdmc_trial_wf* wf, const lrdmc_params* prm, Plan& P) {
+  if (!sys || !wf || !prm) { P.err = "NULL argument"; return false; }
+  if (sys->n_nuc < 1 || !sys->R || !sys->Z || !sys->pot_kind || !sys->r_c) { P.err = "bad nuclei"; return false; }
+  if (sys->n_up < 0 || sys->n_dn < 0 || sys->n_up + sys->n_dn < 1) { P.err = "bad electron counts"; return false; }
+  if (wf->n_shell < 1 || !wf->shell_atom || !wf->shell_l || !wf->shell_nprim || !wf->exps || !wf->coefs || !wf->C ||
+      !wf->j1_A || !wf->j1_B) { P.err = "bad trial wavefunction arrays"; return false; }
+  if (!(prm->a > 0.0) || prm->n_w < 1 || prm->n_w > MAX_WALKERS || prm->reinv_period < 1 ||
+      prm->node_rule < -1 || prm->node_rule > 2 || prm->p_gbar < 0 || prm->n_equil < 0) {
+    P.err = "bad run parameters"; return false;
+  }
+  if (prm->precision != 0) { P.err = "only precision 0 (FP64) is available"; return false; }
+  P.n_nuc = sys->n_nuc;
+  P.n_up = sys->n_up;
+  P.n_dn = sys->n_dn;
+  P.n_e = P.n_up + P.n_dn;
+  P.n_max = std::max(P.n_up, P.n_dn);
+  P.n_shell = wf->n_shell;
+  P.n_w = prm->n_w;
+  for (int I = 0; I < P.n_nuc; ++I) {
+    if (sys->pot_kind[I] != 0 && sys->pot_kind[I] != 1) { P.err = "pot_kind must be 0 or 1"; return false; }
+    if (sys->pot_kind[I] == 1 && !(sys->r_c[I] > 0.0)) { P.err = "r_c must be > 0"; return false; }
+  }
+  for (int s = 0; s < P.n_shell; ++s) {
+    const int l = wf->shell_l[s];
+    if (l < -1 || l > 1) { P.err = "shell_l must be -1, 0 or 1"; return false; }
+    if (wf->shell_atom[s] < 0 || wf->shell_atom[s] >= P.n_nuc) { P.err = "shell_atom out of range"; return false; }
+    if (wf->shell_nprim[s] < 1) { P.err = "shell_nprim must be >= 1"; return false; }
+    P.n_prim += wf->shell_nprim[s];
+    P.n_bf += (l == 1) ? 3 : 1;
+  }
+  P.n_orb = wf->n_orb;
+  if (P.n_orb < P.n_max) { P.err = "n_orb < max(n_up, n_dn)"; return false; }
+  // walker block in global memory
+  Layout& L = P.L;
+  L.n_e = P.n_e; L.n_up = P.n_up; L.n_dn = P.n_dn; L.n_max = P.n_max; L.n_bf = P.n_bf; L.n_hop = 6 * P.n_e;
+  const int nbt = P.n_up * P.n_up + P.n_dn * P.n_dn;
+  L.g_x = 0;
+  L.g_bt = 3 * P.n_e;
+  L.g_cache = L.g_bt + nbt;
+  L.g_rat = L.g_cache + 5 * P.n_max * P.n_e;
+  L.g_sc = round_up(L.g_rat + L.n_hop, 16);
+  L.g_stride = round_up(L.g_sc + SC_COUNT, 16);
+  // per-warp shared memory
+  L.s_x = 0;
+  L.s_bt = 3 * P.n_e;
+  L.s_g = L.s_bt + nbt;
+  const int gsz = std::max(P.n_e * P.n_bf, 2 * P.n_max * P.n_max);
+  L.s_rat = L.s_g + gsz;
+  L.s_cache = L.s_rat + L.n_hop;
+  L.s_ej = L.s_cache + 5 * P.n_max * P.n_e;
+  L.s_ep = L.s_ej + 2 * P.n_e;
+  L.s_chi5 = L.s_ep + 3 * P.n_e;
+  L.s_phi5 = L.s_chi5 + 5 * P.n_bf;
+  L.s_u = L.s_phi5 + 5 * P.n_max;
+  L.s_row = L.s_u + P.n_max;
+  L.s_sc = L.s_row + P.n_max;
+  L.s_stride = round_up(L.s_sc + SC_COUNT, 4);
+  P.smem_per_warp = (size_t)L.s_stride * sizeof(double);
+  if (P.smem_per_warp > 200 * 1024) { P.err = "system too large for the per-warp shared-memory layout"; return false; }
+  // system image
+  size_t o = 0;
+  auto take = [&](size_t bytes) { size_t r = o; o += (bytes + 15) / 16 * 16; return r; };
+  P.i_R = take(sizeof(double) * 3 * P.n_nuc);
+  P.i_Z = take(sizeof(double) * P.n_nuc);
+  P.i_rc = take(sizeof(double) * P.n_nuc);
+  P.i_j1A = take(sizeof(double) * P.n_nuc);
+  P.i_j1B = take(sizeof(double) * P.n_nuc);
+  P.i_exps = take(sizeof(double) * P.n_prim);
+  P.i_coefs = take(sizeof(double) * P.n_prim);
+  P.i_C = take(sizeof(double) * (size_t)P.n_orb * P.n_bf);
+  P.i_kind = take(sizeof(int) * P.n_nuc);
+  P.i_atom = take(sizeof(int) * P.n_shell);
+  P.i_l = take(sizeof(int) * P.n_shell);
+  P.i_nprim = take(sizeof(int) * P.n_shell);
+  P.i_off = take(sizeof(int) * P.n_shell);
+  P.i_bf = take(sizeof(int) * P.n_shell);
+  P.sys_bytes = o;
+  // workspace
+  size_t w = 0;
+  P.o_sys = w; w += align_up(P.sys_bytes);
+  P.state_bytes = (size_t)P.n_w * L.g_stride * sizeof(double);
+  P.o_state = w; w += align_up(P.state_bytes);
+  P.o_alt = w; w += align_up(P.state_bytes);
+  P.o_stats = w; w += align_up(sizeof(double) * BS_COUNT);
+  P.o_q = w; w += align_up(sizeof(unsigned long long) * P.n_w);
+  P.o_src = w; w += align_up(sizeof(int32_t) * P.n_w);
+  P.o_dstat = w; w += align_up(sizeof(int32_t) * 16);
+  P.total = w;
+  return true;
+}
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+double estimate(const std::vector<double>& wbar, const std::vector<double>& ebar, int p, int n0, double* err) {
+  const int n = (int)wbar.size();
+  std::vector<double> lg(n, 0.0);
+  for (int k = 0; k < n; ++k) {
+    double s = 0.0;
+    for (int j = std::max(0, k - p); j < k; ++j) s += std::log(wbar[j]);
+    lg[k] = s;
+  }
+  const int m = n - n0;
+  if (err) *err = NAN;
+  if (m <= 0) return NAN;
+  double lmax = -INFINITY;
+  for (int k = n0; k < n; ++k) lmax = std::max(lmax, lg[k]);
+  std::vector<double> g(m), e(m);
+  double num = 0.0, den = 0.0;
+  for (int k = 0; k < m; ++k) {
+    g[k] = std::exp(lg[n0 + k] - lmax);
+    e[k] = ebar[n0 + k];
+    num += g[k] * e[k];
+    den += g[k];
+  }
+  if (err && m >= 16) {
+    double best = 0.0;
+    for (int B = 1; m / B >= 8; B *= 2) {
+      const int nb = m / B;
+      std::vector<double> bn(nb, 0.0), bd(nb, 0.0);
+      for (int b = 0; b < nb; ++b)
+        for (int k = b * B; k < (b + 1) * B; ++k) { bn[b] += g[k] * e[k]; bd[b] += g[k]; }
+      double tn = 0.0, td = 0.0;
+      for (int b = 0; b < nb; ++b) { tn += bn[b]; td += bd[b]; }
+      std::vector<double> jk(nb);
+      double mean = 0.0;
+      for (int b = 0; b < nb; ++b) { jk[b] = (tn - bn[b]) / (td - bd[b]); mean += jk[b]; }
+      mean /= nb;
+      double var = 0.0;
+      for (int b = 0; b < nb; ++b) var += (jk[b] - mean) * (jk[b] - mean);
+      var *= (double)(nb - 1) / nb;
+      best = std::max(best, std::sqrt(var));
+    }
+    *err = best;
+  }
+  return num / den;
+}
+
+}  // namespace
+
+struct lrdmc_s {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  bool owns = false;
+  Plan P;
+  DevSys S{};
+  lrdmc_params prm{};
+  double* state = nullptr;
+  double* alt = nullptr;
+  double* stats = nullptr;
+  unsigned long long* Q = nullptr;
+  int32_t* src = nullptr;
+  int32_t* dstat = nullptr;
+  int wpb = 4, grid = 1, num_sms = 1;
+  double E0 = 0.0;
+  uint32_t interval = 0;
+  int last_kind = 1;
+  std::vector<double> wbar, ebar, e0h, mmean;
+  std::vector<int> mmax, surv;
+  std::vector<uint32_t> stor;
+  int64_t launches = 0;
+  std::string err;
+};
+
+static lrdmc_status fail(lrdmc_handle h, lrdmc_status s, const std::string& msg) {
+  if (h) h->err = msg;
+  return s;
+}
+
+static lrdmc_status cuda_fail(lrdmc_handle h, const char* what, cudaError_t e) {
+  char buf[512];
+  snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+  return fail(h, LRDMC_ERR_CUDA, buf);
+}
+
+#define CK(h, call)                                   \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return cuda_fail(h, #call, e_); \
+  } while (0)
+
+#define LAUNCHED(h)                                          \
+  do {                                                       \
+    ++(h)->launches;                                         \
+    cudaError_t e_ = cudaGetLastError();                     \
+    if (e_ != cudaSuccess) return cuda_fail(h, "kernel launch", e_); \
+  } while (0)
+
+static lrdmc_status set_kernel_smem(lrdmc_handle h) {
+  const int bytes = (int)(h->wpb * h->P.smem_per_warp);
+  CK(h, cudaFuncSetAttribute(k_propagate, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  CK(h, cudaFuncSetAttribute(k_init_walkers, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  CK(h, cudaFuncSetAttribute(k_eval_configs, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  return LRDMC_OK;
+}
+
+static int walker_grid(lrdmc_handle h, int n) {
+  const int need = (n + h->wpb - 1) / h->wpb;
+  return std::max(1, std::min(need, h->grid));
+}
+
+// Place walkers from host arrays and evaluate (x staged through the alternate buffer).
+static lrdmc_status place_walkers(lrdmc_handle h, const double* x, const double* w) {
+  const Plan& P = h->P;
+  const size_t xbytes = sizeof(double) * (size_t)P.n_w * 3 * P.n_e;
+  double* dx = h->alt;
+  double* dw = nullptr;
+  CK(h, cudaMemcpyAsync(dx, x, xbytes, cudaMemcpyHostToDevice, h->stream));
+  if (w) {
+    dw = h->alt + (size_t)P.n_w * 3 * P.n_e;
+    CK(h, cudaMemcpyAsync(dw, w, sizeof(double) * P.n_w, cudaMemcpyHostToDevice, h->stream));
+  }
+  const int smem = (int)(h->wpb * P.smem_per_warp);
+  k_init_walkers<<<walker_grid(h, P.n_w), h->wpb * 32, smem, h->stream>>>(h->S, P.L, h->state, dx, dw, P.n_w,
+                                                                          h->prm.a, h->prm.node_rule);
+  LAUNCHED(h);
+  CK(h, cudaStreamSynchronize(h->stream));
+  return LRDMC_OK;
+}
+
+// Copy compact walker fields to host vectors (uses the alternate buffer).
+static lrdmc_status extract(lrdmc_handle h, std::vector<double>& buf) {
+  const Plan& P = h->P;
+  const size_t nx = (size_t)P.n_w * 3 * P.n_e, nr = (size_t)P.n_w * P.L.n_hop, nw = P.n_w;
+  const size_t tot = nx + nr + 7 * nw;
+  buf.resize(tot);
+  double* b = h->alt;
+  k_extract<<<std::min(1024, (int)((tot + 255) / 256)), 256, 0, h->stream>>>(
+      P.L, h->state, P.n_w, b, b + nx, b + nx + nw, b + nx + 5 * nw, b + nx + 5 * nw + nr,
+      b + nx + 6 * nw + nr);
+  LAUNCHED(h);
+  CK(h, cudaMemcpyAsync(buf.data(), b, sizeof(double) * tot, cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  return LRDMC_OK;
+}
+
+extern "C" {
+
+const char* lrdmc_status_string(lrdmc_status s) {
+  switch (s) {
+    case LRDMC_OK: return "ok";
+    case LRDMC_ERR_ARG: return "invalid argument";
+    case LRDMC_ERR_CUDA: return "CUDA error";
+    case LRDMC_ERR_NONFINITE: return "non-finite or invalid weights";
+    case LRDMC_ERR_NEG_DIAG: return "W - E0 <= 0";
+    case LRDMC_ERR_STEP_CAP: return "step cap reached";
+    case LRDMC_ERR_SINGULAR: return "singular Slater matrix";
+    case LRDMC_ERR_UNSUPPORTED: return "unsupported size";
+  }
+  return "unknown status";
+}
+
+const char* lrdmc_last_error(lrdmc_handle h) { return h ? h->err.c_str() : "NULL handle"; }
+
+void lrdmc_philox4x32(uint64_t seed, const uint32_t ctr[4], uint32_t out[4]) {
+  uint32_t c[4] = {ctr[0], ctr[1], ctr[2], ctr[3]};
+  philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+  for (int k = 0; k < 4; ++k) out[k] = c[k];
+}
+
+lrdmc_status lrdmc_workspace_bytes(const lrdmc_system* sys, const lrdmc_trial_wf* wf, const lrdmc_params* prm,
+                                   size_t* bytes) {
+  Plan P;
+  if (!bytes) return LRDMC_ERR_ARG;
+  if (!make_plan(sys, wf, prm, P))
+    return P.err.find("too large") != std::string::npos ? LRDMC_ERR_UNSUPPORTED : LRDMC_ERR_ARG;
+  *bytes = P.total;
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_create(const lrdmc_system* sys, const lrdmc_trial_wf* wf, const lrdmc_params* prm,
+                          const double* x0, void* workspace, size_t workspace_bytes, void* stream,
+                          lrdmc_handle* out) {
+  if (!out) return LRDMC_ERR_ARG;
+  *out = nullptr;
+  lrdmc_handle h = new lrdmc_s();
+  if (!make_plan(sys, wf, prm, h->P) || !x0) {
+    lrdmc_status s = (h->P.err.find("too large") != std::string::npos) ? LRDMC_ERR_UNSUPPORTED : LRDMC_ERR_ARG;
+    *out = h;   // keep the handle so the caller can read the message; destroy frees it
+    if (!x0) h->err = "x0 is NULL"; else h->err = h->P.err;
+    return s;
+  }
+  const Plan& P = h->P;
+  h->prm = *prm;
+  h->stream = (cudaStream_t)stream;
+  *out = h;
+  CK(h, cudaGetDevice(&h->device));
+  CK(h, cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
+  if (workspace) {
+    if (workspace_bytes < P.total) return fail(h, LRDMC_ERR_ARG, "workspace too small");
+    if ((uintptr_t)workspace % ALIGN) return fail(h, LRDMC_ERR_ARG, "workspace not 256-byte aligned");
+    h->ws = workspace;
+    h->ws_bytes = workspace_bytes;
+  } else {
+    CK(h, cudaMalloc(&h->ws, P.total));
+    h->owns = true;
+    h->ws_bytes = P.total;
+  }
+  char* base = (char*)h->ws;
+  // system image
+  std::vector<char> img(P.sys_bytes, 0);
+  auto putd = [&](size_t off, const double* src, size_t n) { if (n) memcpy(img.data() + off, src, n * sizeof(double)); };
+  auto puti = [&](size_t off, const int* src, size_t n) { if (n) memcpy(img.data() + off, src, n * sizeof(int)); };
+  putd(P.i_R, sys->R, 3 * (size_t)P.n_nuc);
+  putd(P.i_Z, sys->Z, P.n_nuc);
+  putd(P.i_rc, sys->r_c, P.n_nuc);
+  putd(P.i_j1A, wf->j1_A, P.n_nuc);
+  putd(P.i_j1B, wf->j1_B, P.n_nuc);
+  putd(P.i_exps, wf->exps, P.n_prim);
+  putd(P.i_coefs, wf->coefs, P.n_prim);
+  putd(P.i_C, wf->C, (size_t)P.n_orb * P.n_bf);
+  puti(P.i_kind, sys->pot_kind, P.n_nuc);
+  puti(P.i_atom, wf->shell_atom, P.n_shell);
+  puti(P.i_l, wf->shell_l, P.n_shell);
+  puti(P.i_nprim, wf->shell_nprim, P.n_shell);
+  std::vector<int> off(P.n_shell), bf(P.n_shell);
+  for (int s = 0, po = 0, bo = 0; s < P.n_shell; ++s) {
+    off[s] = po; bf[s] = bo;
+    po += wf->shell_nprim[s];
+    bo += wf->shell_l[s] == 1 ? 3 : 1;
+  }
+  puti(P.i_off, off.data(), P.n_shell);
+  puti(P.i_bf, bf.data(), P.n_shell);
+  char* dsys = base + P.o_sys;
+  CK(h, cudaMemcpyAsync(dsys, img.data(), P.sys_bytes, cudaMemcpyHostToDevice, h->stream));
+  DevSys& S = h->S;
+  S.n_nuc = P.n_nuc; S.n_shell = P.n_shell; S.n_prim = P.n_prim; S.n_bf = P.n_bf; S.n_orb = P.n_orb;
+  S.n_up = P.n_up; S.n_dn = P.n_dn; S.n_e = P.n_e; S.n_max = P.n_max;
+  S.R = (const double*)(dsys + P.i_R);
+  S.Z = (const double*)(dsys + P.i_Z);
+  S.rc = (const double*)(dsys + P.i_rc);
+  S.j1A = (const double*)(dsys + P.i_j1A);
+  S.j1B = (const double*)(dsys + P.i_j1B);
+  S.exps = (const double*)(dsys + P.i_exps);
+  S.coefs = (const double*)(dsys + P.i_coefs);
+  S.C = (const double*)(dsys + P.i_C);
+  S.kind = (const int*)(dsys + P.i_kind);
+  S.sh_atom = (const int*)(dsys + P.i_atom);
+  S.sh_l = (const int*)(dsys + P.i_l);
+  S.sh_nprim = (const int*)(dsys + P.i_nprim);
+  S.sh_off = (const int*)(dsys + P.i_off);
+  S.sh_bf = (const int*)(dsys + P.i_bf);
+  S.j2_anti = wf->j2_anti;
+  S.j2_par = wf->j2_par;
+  S.j2_b = wf->j2_b;
+  double vii = 0.0;
+  for (int I = 0; I < P.n_nuc; ++I)
+    for (int J = I + 1; J < P.n_nuc; ++J) {
+      const double dx = sys->R[3 * I] - sys->R[3 * J], dy = sys->R[3 * I + 1] - sys->R[3 * J + 1],
+                   dz = sys->R[3 * I + 2] - sys->R[3 * J + 2];
+      vii += sys->Z[I] * sys->Z[J] / std::sqrt(dx * dx + dy * dy + dz * dz);
+    }
+  S.v_ii = vii;
+  h->state = (double*)(base + P.o_state);
+  h->alt = (double*)(base + P.o_alt);
+  h->stats = (double*)(base + P.o_stats);
+  h->Q = (unsigned long long*)(base + P.o_q);
+  h->src = (int32_t*)(base + P.o_src);
+  h->dstat = (int32_t*)(base + P.o_dstat);
+  CK(h, cudaMemsetAsync(h->dstat, 0, sizeof(int32_t) * 16, h->stream));
+  // launch geometry: up to 4 walkers (warps) per CTA within the shared-memory budget
+  int smem_optin = 0;
+  CK(h, cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+  h->wpb = 4;
+  while (h->wpb > 1 && (size_t)h->wpb * P.smem_per_warp > (size_t)smem_optin) h->wpb >>= 1;
+  if ((size_t)h->wpb * P.smem_per_warp > (size_t)smem_optin)
+    return fail(h, LRDMC_ERR_UNSUPPORTED, "walker working set exceeds shared memory");
+  lrdmc_status st = set_kernel_smem(h);
+  if (st != LRDMC_OK) return st;
+  int bps = 0;
+  CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_propagate, h->wpb * 32,
+                                                      (int)(h->wpb * P.smem_per_warp)));
+  if (bps < 1) return fail(h, LRDMC_ERR_UNSUPPORTED, "propagate kernel does not fit on an SM");
+  h->grid = bps * h->num_sms;
+  st = place_walkers(h, x0, nullptr);
+  if (st != LRDMC_OK) return st;
+  std::vector<double> buf;
+  st = extract(h, buf);
+  if (st != LRDMC_OK) return st;
+  const size_t nx = (size_t)P.n_w * 3 * P.n_e, nw = P.n_w;
+  double s = 0.0;
+  for (size_t a = 0; a < nw; ++a) s += buf[nx + nw + 4 * a + 3];
+  h->E0 = s / (double)nw;
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_destroy(lrdmc_handle h) {
+  if (!h) return LRDMC_ERR_ARG;
+  if (h->owns && h->ws) {
+    DeviceGuard g(h->device);
+    cudaStreamSynchronize(h->stream);
+    cudaFree(h->ws);
+  }
+  delete h;
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_propagate(lrdmc_handle h, const lrdmc_schedule* sch) {
+  if (!h || !h->state) return LRDMC_ERR_ARG;
+  if (!sch) return fail(h, LRDMC_ERR_ARG, "NULL schedule");
+  if (sch->kind != LRDMC_CONVENTIONAL && sch->kind != LRDMC_LOAD_BALANCED)
+    return fail(h, LRDMC_ERR_ARG, "schedule kind must be 0 or 1");
+  if (sch->kind == LRDMC_LOAD_BALANCED && sch->n_proj < 0) return fail(h, LRDMC_ERR_ARG, "n_proj < 0");
+  if (sch->kind == LRDMC_CONVENTIONAL && (!(sch->tau > 0.0) || sch->max_moves < 1))
+    return fail(h, LRDMC_ERR_ARG, "conventional schedule needs tau > 0 and max_moves >= 1");
+  DeviceGuard g(h->device);
+  StepParams sp;
+  sp.kind = sch->kind;
+  sp.n_proj = sch->n_proj;
+  sp.tau = sch->tau;
+  sp.max_moves = sch->max_moves;
+  sp.E0 = h->E0;
+  sp.seed = h->prm.seed;
+  sp.interval = h->interval;
+  sp.a = h->prm.a;
+  sp.node_rule = h->prm.node_rule;
+  sp.reinv_period = h->prm.reinv_period;
+  const int smem = (int)(h->wpb * h->P.smem_per_warp);
+  k_propagate<<<walker_grid(h, h->P.n_w), h->wpb * 32, smem, h->stream>>>(h->S, h->P.L, h->state, h->P.n_w, sp);
+  LAUNCHED(h);
+  h->last_kind = sch->kind;
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_branch(lrdmc_handle h) {
+  if (!h || !h->state) return LRDMC_ERR_ARG;
+  DeviceGuard g(h->device);
+  const Plan& P = h->P;
+  const int lb = h->last_kind == LRDMC_LOAD_BALANCED;
+  k_branch_reduce<<<1, BR_THREADS, 0, h->stream>>>(P.L, h->state, P.n_w, h->E0, lb, h->stats);
+  LAUNCHED(h);
+  const uint32_t xi = branch_offset32(h->prm.seed, h->interval);
+  k_reconfigure<<<1, BR_THREADS, 0, h->stream>>>(h->state + P.L.g_sc + SC_W, P.L.g_stride, P.n_w, xi, h->Q,
+                                                 h->src, h->dstat, h->stats);
+  LAUNCHED(h);
+  const size_t per = (size_t)P.n_w * P.L.g_stride / 2;
+  const int gb = (int)std::min<size_t>((per + 255) / 256, (size_t)h->num_sms * 8);
+  k_gather<<<std::max(1, gb), 256, 0, h->stream>>>(P.L, h->state, h->alt, h->src, P.n_w, h->dstat);
+  LAUNCHED(h);
+  double hs[BS_COUNT];
+  CK(h, cudaMemcpyAsync(hs, h->stats, sizeof hs, cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  if (hs[BS_BAD] != 0.0)
+    return fail(h, LRDMC_ERR_NONFINITE, "weights negative, non-finite or all zero: population unchanged");
+  std::swap(h->state, h->alt);
+  h->wbar.push_back(hs[BS_SUMW] / (double)P.n_w);
+  h->ebar.push_back(hs[BS_SUMFE] / hs[BS_SUMF]);
+  h->e0h.push_back(h->E0);
+  h->mmean.push_back(hs[BS_MOVES] / (double)P.n_w);
+  h->mmax.push_back((int)hs[BS_MOVESMAX]);
+  h->surv.push_back((int)hs[BS_SURV]);
+  h->stor.push_back((uint32_t)hs[BS_STATUS]);
+  ++h->interval;
+  if (lb) h->E0 = estimate(h->wbar, h->ebar, h->prm.p_gbar, 0, nullptr);
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_energy(lrdmc_handle h, double* E, double* err) {
+  if (!h || !E) return LRDMC_ERR_ARG;
+  *E = estimate(h->wbar, h->ebar, h->prm.p_gbar, h->prm.n_equil, err);
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_history(lrdmc_handle h, int cap, int* n, double* wbar, double* ebar, double* e0,
+                           double* moves_mean, int* moves_max, int* survivors, uint32_t* status_or) {
+  if (!h) return LRDMC_ERR_ARG;
+  const int m = (int)h->wbar.size();
+  if (n) *n = m;
+  const int k = std::min(std::max(cap, 0), m);
+  for (int i = 0; i < k; ++i) {
+    if (wbar) wbar[i] = h->wbar[i];
+    if (ebar) ebar[i] = h->ebar[i];
+    if (e0) e0[i] = h->e0h[i];
+    if (moves_mean) moves_mean[i] = h->mmean[i];
+    if (moves_max) moves_max[i] = h->mmax[i];
+    if (survivors) survivors[i] = h->surv[i];
+    if (status_or) status_or[i] = h->stor[i];
+  }
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_get_e0(lrdmc_handle h, double* e0) {
+  if (!h || !e0) return LRDMC_ERR_ARG;
+  *e0 = h->E0;
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_set_e0(lrdmc_handle h, double e0) {
+  if (!h || !std::isfinite(e0)) return LRDMC_ERR_ARG;
+  h->E0 = e0;
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_get_walkers(lrdmc_handle h, double* x, double* w, double* ev, double* ratios, uint32_t* status,
+                               int32_t* moves) {
+  if (!h || !h->state) return LRDMC_ERR_ARG;
+  DeviceGuard g(h->device);
+  std::vector<double> buf;
+  lrdmc_status st = extract(h, buf);
+  if (st != LRDMC_OK) return st;
+  const Plan& P = h->P;
+  const size_t nx = (size_t)P.n_w * 3 * P.n_e, nr = (size_t)P.n_w * P.L.n_hop, nw = P.n_w;
+  if (x) memcpy(x, buf.data(), nx * sizeof(double));
+  if (w) memcpy(w, buf.data() + nx, nw * sizeof(double));
+  if (ev) memcpy(ev, buf.data() + nx + nw, 4 * nw * sizeof(double));
+  if (ratios) memcpy(ratios, buf.data() + nx + 5 * nw, nr * sizeof(double));
+  for (size_t a = 0; a < nw; ++a) {
+    if (status) status[a] = (uint32_t)buf[nx + 5 * nw + nr + a];
+    if (moves) moves[a] = (int32_t)buf[nx + 6 * nw + nr + a];
+  }
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_set_walkers(lrdmc_handle h, const double* x, const double* w) {
+  if (!h || !h->state) return LRDMC_ERR_ARG;
+  if (!x) return fail(h, LRDMC_ERR_ARG, "x is NULL");
+  DeviceGuard g(h->device);
+  return place_walkers(h, x, w);
+}
+
+lrdmc_status lrdmc_clear_status(lrdmc_handle h) {
+  if (!h || !h->state) return LRDMC_ERR_ARG;
+  DeviceGuard g(h->device);
+  k_clear_status<<<std::max(1, std::min(1024, (h->P.n_w + 255) / 256)), 256, 0, h->stream>>>(h->P.L, h->state,
+                                                                                             h->P.n_w);
+  LAUNCHED(h);
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_eval_configs(lrdmc_handle h, int n, const double* x, double* ratios, double* ev, int32_t* n_node) {
+  if (!h || !h->state) return LRDMC_ERR_ARG;
+  if (n < 0 || n > h->P.n_w) return fail(h, LRDMC_ERR_ARG, "n must be in [0, n_w]");
+  if (n == 0) return LRDMC_OK;
+  if (!x || !ratios || !ev) return fail(h, LRDMC_ERR_ARG, "NULL device pointer");
+  DeviceGuard g(h->device);
+  const int smem = (int)(h->wpb * h->P.smem_per_warp);
+  k_eval_configs<<<walker_grid(h, n), h->wpb * 32, smem, h->stream>>>(h->S, h->P.L, x, n, h->prm.a,
+                                                                      h->prm.node_rule, ratios, ev, n_node);
+  LAUNCHED(h);
+  return LRDMC_OK;
+}
+
+size_t lrdmc_reconfigure_scratch_bytes(int n) {
+  if (n < 1) return 0;
+  return align_up(sizeof(unsigned long long) * (size_t)n) + ALIGN;
+}
+
+lrdmc_status lrdmc_reconfigure_indices(int n, const double* w, uint32_t xi32, int32_t* src, void* scratch,
+                                       size_t scratch_bytes, int32_t* status_out, void* stream) {
+  if (n < 1 || n > MAX_WALKERS || !w || !src || !scratch) return LRDMC_ERR_ARG;
+  if (scratch_bytes < lrdmc_reconfigure_scratch_bytes(n) || (uintptr_t)scratch % ALIGN) return LRDMC_ERR_ARG;
+  unsigned long long* Q = (unsigned long long*)scratch;
+  int32_t* st = (int32_t*)((char*)scratch + align_up(sizeof(unsigned long long) * (size_t)n));
+  k_reconfigure<<<1, BR_THREADS, 0, (cudaStream_t)stream>>>(w, 1, n, xi32, Q, src, st, nullptr);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return LRDMC_ERR_CUDA;
+  if (status_out) {
+    e = cudaMemcpyAsync(status_out, st, 2 * sizeof(int32_t), cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+    if (e != cudaSuccess) return LRDMC_ERR_CUDA;
+  }
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_launch_count(lrdmc_handle h, int64_t* n) {
+  if (!h || !n) return LRDMC_ERR_ARG;
+  *n = h->launches;
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_stream(lrdmc_handle h, void** stream) {
+  if (!h || !stream) return LRDMC_ERR_ARG;
+  *stream = (void*)h->stream;
+  return LRDMC_OK;
+}
+
+}  // extern "C"
