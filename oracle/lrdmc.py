@@ -103,10 +103,11 @@ def _reevaluate(sys, W: Walkers, sel, a, node_rule):
         W.ev[k][sel] = v
 
 
-def propagate_lb(sys, W: Walkers, a, E0, n_proj, seed, interval, node_rule=0):
-    """One load-balanced interval (Algorithm 2, inner loop) for all walkers."""
+def propagate_lb(sys, W: Walkers, a, E0, n_proj, seed, interval, node_rule=0, walker_ids=None):
+    """One load-balanced interval (Algorithm 2, inner loop) for all walkers.
+    ``walker_ids``: Philox walker slots of the rows of W (default 0..n-1)."""
     n = W.x.shape[0]
-    ids = np.arange(n)
+    ids = np.arange(n) if walker_ids is None else np.asarray(walker_ids)
     W.w = np.ones(n)
     W.moves = np.zeros(n, np.int64)
     for k in range(n_proj):
@@ -126,10 +127,11 @@ def propagate_lb(sys, W: Walkers, a, E0, n_proj, seed, interval, node_rule=0):
 
 
 def propagate_conventional(sys, W: Walkers, a, tau, seed, interval, node_rule=0,
-                           max_moves=100000):
-    """One conventional interval (Algorithm 1, inner loop) for all walkers."""
+                           max_moves=100000, walker_ids=None):
+    """One conventional interval (Algorithm 1, inner loop) for all walkers.
+    ``walker_ids``: Philox walker slots of the rows of W (default 0..n-1)."""
     n = W.x.shape[0]
-    ids = np.arange(n)
+    ids = np.arange(n) if walker_ids is None else np.asarray(walker_ids)
     W.w = np.ones(n)
     W.moves = np.zeros(n, np.int64)
     tau_left = np.full(n, float(tau))
@@ -137,7 +139,7 @@ def propagate_conventional(sys, W: Walkers, a, tau, seed, interval, node_rule=0,
     k = 0
     while np.any(active):
         act = np.nonzero(active)[0]
-        u_tau, u_move = philox.step_uniforms(seed, act, k, interval)
+        u_tau, u_move = philox.step_uniforms(seed, ids[act], k, interval)
         bbar = W.ev["bbar"][act]
         with np.errstate(divide="ignore"):
             t = -np.log(1.0 - u_tau) / bbar

@@ -1,0 +1,286 @@
+"""ctypes binding of liblrdmc.so (argument marshalling only).
+
+Device memory comes from PyTorch's caching allocator (the handle's workspace
+and every device buffer passed to the library are torch tensors) and work is
+enqueued on a torch CUDA stream; all computation happens in the library's
+kernels.  Names follow the C ABI in include/lrdmc.h.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+LOAD_BALANCED = 1
+CONVENTIONAL = 0
+
+_LIB = None
+_LIBPATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "liblrdmc.so")
+
+c_double_p = C.POINTER(C.c_double)
+c_int_p = C.POINTER(C.c_int)
+
+
+class _System(C.Structure):
+    _fields_ = [("n_nuc", C.c_int), ("R", c_double_p), ("Z", c_double_p), ("pot_kind", c_int_p),
+                ("r_c", c_double_p), ("n_up", C.c_int), ("n_dn", C.c_int)]
+
+
+class _TrialWF(C.Structure):
+    _fields_ = [("n_shell", C.c_int), ("shell_atom", c_int_p), ("shell_l", c_int_p),
+                ("shell_nprim", c_int_p), ("exps", c_double_p), ("coefs", c_double_p),
+                ("n_orb", C.c_int), ("C", c_double_p), ("j2_anti", C.c_double),
+                ("j2_par", C.c_double), ("j2_b", C.c_double), ("j1_A", c_double_p),
+                ("j1_B", c_double_p)]
+
+
+class _Schedule(C.Structure):
+    _fields_ = [("kind", C.c_int), ("n_proj", C.c_int), ("tau", C.c_double), ("max_moves", C.c_int)]
+
+
+class _Params(C.Structure):
+    _fields_ = [("a", C.c_double), ("n_w", C.c_int), ("seed", C.c_uint64), ("node_rule", C.c_int),
+                ("reinv_period", C.c_int), ("p_gbar", C.c_int), ("n_equil", C.c_int),
+                ("precision", C.c_int)]
+
+
+class LrdmcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"lrdmc status {status}: {msg}")
+        self.status = status
+
+
+def load_library():
+    """Load liblrdmc.so from the package directory (raises if it is not built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(_LIBPATH):
+        raise RuntimeError(f"{_LIBPATH} is missing: build it with paper_2508_12033_b300.build.build()")
+    lib = C.CDLL(_LIBPATH)
+    P = C.c_void_p
+    sigs = {
+        "lrdmc_workspace_bytes": [C.POINTER(_System), C.POINTER(_TrialWF), C.POINTER(_Params), C.POINTER(C.c_size_t)],
+        "lrdmc_create": [C.POINTER(_System), C.POINTER(_TrialWF), C.POINTER(_Params), c_double_p, P, C.c_size_t,
+                         P, C.POINTER(P)],
+        "lrdmc_destroy": [P],
+        "lrdmc_propagate": [P, C.POINTER(_Schedule)],
+        "lrdmc_branch": [P],
+        "lrdmc_energy": [P, c_double_p, c_double_p],
+        "lrdmc_history": [P, C.c_int, c_int_p, c_double_p, c_double_p, c_double_p, c_double_p, c_int_p, c_int_p,
+                          C.POINTER(C.c_uint32)],
+        "lrdmc_get_e0": [P, c_double_p],
+        "lrdmc_set_e0": [P, C.c_double],
+        "lrdmc_get_walkers": [P, c_double_p, c_double_p, c_double_p, c_double_p, C.POINTER(C.c_uint32),
+                              C.POINTER(C.c_int32)],
+        "lrdmc_set_walkers": [P, c_double_p, c_double_p],
+        "lrdmc_clear_status": [P],
+        "lrdmc_eval_configs": [P, C.c_int, P, P, P, P],
+        "lrdmc_reconfigure_indices": [C.c_int, P, C.c_uint32, P, P, C.c_size_t, P, P],
+        "lrdmc_launch_count": [P, C.POINTER(C.c_int64)],
+        "lrdmc_stream": [P, C.POINTER(P)],
+    }
+    for name, args in sigs.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    lib.lrdmc_reconfigure_scratch_bytes.argtypes = [C.c_int]
+    lib.lrdmc_reconfigure_scratch_bytes.restype = C.c_size_t
+    lib.lrdmc_philox4x32.argtypes = [C.c_uint64, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
+    lib.lrdmc_philox4x32.restype = None
+    lib.lrdmc_last_error.argtypes = [P]
+    lib.lrdmc_last_error.restype = C.c_char_p
+    _LIB = lib
+    return lib
+
+
+def _dptr(a):
+    return a.ctypes.data_as(c_double_p)
+
+
+def _iptr(a):
+    return a.ctypes.data_as(c_int_p)
+
+
+def _tptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+class Lrdmc:
+    """One LRDMC population on one GPU.
+
+    ``system`` is any object with the attributes of ``lrdmc_system`` and
+    ``lrdmc_trial_wf`` (R, Z, pot_kind, r_c, n_up, n_dn, shell_atom, shell_l,
+    shell_nprim, exps, coefs, C, j2_anti, j2_par, j2_b, j1_A, j1_B)."""
+
+    def __init__(self, system, x0, a, seed=1, node_rule=0, reinv_period=100, p_gbar=10,
+                 n_equil=0, device=None, stream=None):
+        import torch
+        self._torch = torch
+        lib = load_library()
+        self.lib = lib
+        self.device = torch.device(device if device is not None else "cuda")
+        x0 = np.ascontiguousarray(x0, dtype=np.float64)
+        self.n_w, self.n_e = int(x0.shape[0]), int(x0.shape[1])
+        keep = {}
+
+        def d(v):
+            arr = np.ascontiguousarray(v, dtype=np.float64).reshape(-1)
+            keep[id(arr)] = arr
+            return _dptr(arr)
+
+        def i(v):
+            arr = np.ascontiguousarray(v, dtype=np.int32).reshape(-1)
+            keep[id(arr)] = arr
+            return _iptr(arr)
+
+        self._sys = _System(len(system.Z), d(system.R), d(system.Z), i(system.pot_kind), d(system.r_c),
+                            int(system.n_up), int(system.n_dn))
+        self._wf = _TrialWF(len(system.shell_l), i(system.shell_atom), i(system.shell_l), i(system.shell_nprim),
+                            d(system.exps), d(system.coefs), int(system.C.shape[0]), d(system.C),
+                            float(system.j2_anti), float(system.j2_par), float(system.j2_b), d(system.j1_A),
+                            d(system.j1_B))
+        self._prm = _Params(float(a), self.n_w, int(seed) & (2**64 - 1), int(node_rule), int(reinv_period),
+                            int(p_gbar), int(n_equil), 0)
+        nbytes = C.c_size_t(0)
+        self._check(lib.lrdmc_workspace_bytes(C.byref(self._sys), C.byref(self._wf), C.byref(self._prm),
+                                              C.byref(nbytes)), None)
+        with torch.cuda.device(self.device):
+            self._ws = torch.empty(nbytes.value + 256, dtype=torch.uint8, device=self.device)
+            base = self._ws.data_ptr()
+            aligned = (base + 255) // 256 * 256
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            h = C.c_void_p()
+            st = lib.lrdmc_create(C.byref(self._sys), C.byref(self._wf), C.byref(self._prm), _dptr(x0),
+                                  C.c_void_p(aligned), C.c_size_t(nbytes.value), C.c_void_p(self.stream.cuda_stream),
+                                  C.byref(h))
+        self._h = h
+        self._keep = keep
+        self._check(st)
+
+    # ---------------------------------------------------------------- plumbing
+    def _check(self, status, h=0):
+        if status != 0:
+            hh = self._h if h == 0 else h
+            msg = self.lib.lrdmc_last_error(hh).decode() if hh else ""
+            raise LrdmcError(status, msg)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.lrdmc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- hot path
+    def propagate(self, kind=LOAD_BALANCED, n_proj=20, tau=0.0, max_moves=100000):
+        s = _Schedule(int(kind), int(n_proj), float(tau), int(max_moves))
+        self._check(self.lib.lrdmc_propagate(self._h, C.byref(s)))
+
+    def branch(self):
+        self._check(self.lib.lrdmc_branch(self._h))
+
+    def energy(self):
+        E, err = C.c_double(), C.c_double()
+        self._check(self.lib.lrdmc_energy(self._h, C.byref(E), C.byref(err)))
+        return E.value, err.value
+
+    @property
+    def e0(self):
+        v = C.c_double()
+        self._check(self.lib.lrdmc_get_e0(self._h, C.byref(v)))
+        return v.value
+
+    @e0.setter
+    def e0(self, v):
+        self._check(self.lib.lrdmc_set_e0(self._h, float(v)))
+
+    def history(self):
+        n = C.c_int()
+        self._check(self.lib.lrdmc_history(self._h, 0, C.byref(n), None, None, None, None, None, None, None))
+        m = n.value
+        out = dict(wbar=np.zeros(m), ebar=np.zeros(m), e0=np.zeros(m), moves_mean=np.zeros(m),
+                   moves_max=np.zeros(m, np.int32), survivors=np.zeros(m, np.int32),
+                   status_or=np.zeros(m, np.uint32))
+        self._check(self.lib.lrdmc_history(self._h, m, C.byref(n), _dptr(out["wbar"]), _dptr(out["ebar"]),
+                                           _dptr(out["e0"]), _dptr(out["moves_mean"]), _iptr(out["moves_max"]),
+                                           _iptr(out["survivors"]),
+                                           out["status_or"].ctypes.data_as(C.POINTER(C.c_uint32))))
+        return out
+
+    def get_walkers(self):
+        n, ne = self.n_w, self.n_e
+        out = dict(x=np.zeros((n, ne, 3)), w=np.zeros(n), ev=np.zeros((n, 4)), ratios=np.zeros((n, ne, 6)),
+                   status=np.zeros(n, np.uint32), moves=np.zeros(n, np.int32))
+        self._check(self.lib.lrdmc_get_walkers(self._h, _dptr(out["x"]), _dptr(out["w"]), _dptr(out["ev"]),
+                                               _dptr(out["ratios"]),
+                                               out["status"].ctypes.data_as(C.POINTER(C.c_uint32)),
+                                               out["moves"].ctypes.data_as(C.POINTER(C.c_int32))))
+        return out
+
+    def set_walkers(self, x, w=None):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        assert x.shape == (self.n_w, self.n_e, 3)
+        wp = None
+        if w is not None:
+            w = np.ascontiguousarray(w, dtype=np.float64)
+            wp = _dptr(w)
+        self._check(self.lib.lrdmc_set_walkers(self._h, _dptr(x), wp))
+
+    def clear_status(self):
+        self._check(self.lib.lrdmc_clear_status(self._h))
+
+    def eval_configs(self, x):
+        """x: CUDA float64 tensor (n, n_e, 3) -> (ratios (n, n_e, 6), ev (n, 4), n_node (n,))."""
+        torch = self._torch
+        assert x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()
+        n = int(x.shape[0])
+        ratios = torch.empty((n, self.n_e, 6), dtype=torch.float64, device=x.device)
+        ev = torch.empty((n, 4), dtype=torch.float64, device=x.device)
+        nn = torch.empty((n,), dtype=torch.int32, device=x.device)
+        self._check(self.lib.lrdmc_eval_configs(self._h, n, _tptr(x), _tptr(ratios), _tptr(ev), _tptr(nn)))
+        return ratios, ev, nn
+
+    def launch_count(self):
+        v = C.c_int64()
+        self._check(self.lib.lrdmc_launch_count(self._h, C.byref(v)))
+        return v.value
+
+    def synchronize(self):
+        self.stream.synchronize()
+
+
+def reconfigure_indices(w, xi32, stream=None):
+    """Integer-comb source indices for device weights ``w`` (float64 CUDA tensor).
+
+    Returns (src int32 tensor, status int32 tensor of 2: [ok/invalid, survivors])."""
+    import torch
+    lib = load_library()
+    assert w.is_cuda and w.dtype == torch.float64 and w.is_contiguous() and w.dim() == 1
+    n = int(w.shape[0])
+    src = torch.empty(n, dtype=torch.int32, device=w.device)
+    st = torch.empty(2, dtype=torch.int32, device=w.device)
+    nb = lib.lrdmc_reconfigure_scratch_bytes(n)
+    scratch = torch.empty(nb + 256, dtype=torch.uint8, device=w.device)
+    sp = (scratch.data_ptr() + 255) // 256 * 256
+    s = stream if stream is not None else torch.cuda.current_stream(w.device)
+    r = lib.lrdmc_reconfigure_indices(n, _tptr(w), int(xi32) & 0xFFFFFFFF, _tptr(src), C.c_void_p(sp),
+                                      C.c_size_t(nb), _tptr(st), C.c_void_p(s.cuda_stream))
+    if r != 0:
+        raise LrdmcError(r, "lrdmc_reconfigure_indices failed")
+    s.synchronize()
+    del scratch
+    return src, st
+
+
+def philox4x32(seed, ctr):
+    lib = load_library()
+    c = (C.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    o = (C.c_uint32 * 4)()
+    lib.lrdmc_philox4x32(int(seed) & (2**64 - 1), c, o)
+    return tuple(int(v) for v in o)

@@ -1,0 +1,99 @@
+"""CPU-side checks of the C ABI library: it loads, exports every function the
+header declares, and its host-side pieces (Philox, argument validation,
+workspace sizing) behave -- no GPU compute is called here."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import philox as OP
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lrdmc.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2508_12033_b300 import build
+    build.build()
+    from paper_2508_12033_b300 import load_library
+    return load_library()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s+(lrdmc_[a-z0-9_]+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("lrdmc_create", "lrdmc_propagate", "lrdmc_branch", "lrdmc_energy", "lrdmc_destroy",
+              "lrdmc_eval_configs", "lrdmc_reconfigure_indices"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for n in declared_functions():
+        assert hasattr(lib, n), n
+
+
+def test_host_philox_matches_oracle(lib):
+    from paper_2508_12033_b300 import philox4x32
+    rng = np.random.default_rng(0)
+    for _ in range(50):
+        seed = int(rng.integers(0, 2**63))
+        ctr = [int(v) for v in rng.integers(0, 2**32, size=4)]
+        ref = OP.philox_generic(ctr, OP.seed_key(seed), 32, OP.M4x32, OP.W4x32)
+        assert philox4x32(seed, ctr) == tuple(ref)
+
+
+def _structs(sys_, n_w=64, **kw):
+    from paper_2508_12033_b300 import binding as B
+    keep = []
+
+    def d(v):
+        a = np.ascontiguousarray(v, dtype=np.float64).reshape(-1)
+        keep.append(a)
+        return a.ctypes.data_as(B.c_double_p)
+
+    def i(v):
+        a = np.ascontiguousarray(v, dtype=np.int32).reshape(-1)
+        keep.append(a)
+        return a.ctypes.data_as(B.c_int_p)
+
+    s = B._System(len(sys_.Z), d(sys_.R), d(sys_.Z), i(sys_.pot_kind), d(sys_.r_c), sys_.n_up, sys_.n_dn)
+    w = B._TrialWF(sys_.n_shell, i(sys_.shell_atom), i(sys_.shell_l), i(sys_.shell_nprim), d(sys_.exps),
+                   d(sys_.coefs), sys_.n_orb, d(sys_.C), sys_.j2_anti, sys_.j2_par, sys_.j2_b, d(sys_.j1_A),
+                   d(sys_.j1_B))
+    p = B._Params(kw.get("a", 0.2), n_w, 1, kw.get("node_rule", 0), kw.get("reinv_period", 100), 10, 0,
+                  kw.get("precision", 0))
+    return s, w, p, keep
+
+
+def test_workspace_sizing_and_validation(lib):
+    s, w, p, keep = _structs(W.water_methane(), n_w=4096)
+    nb = ctypes.c_size_t()
+    assert lib.lrdmc_workspace_bytes(ctypes.byref(s), ctypes.byref(w), ctypes.byref(p), ctypes.byref(nb)) == 0
+    # two walker buffers dominate: ~2 * 4096 * (walker block) bytes
+    assert 2 * 4096 * 8 * (48 + 128 + 640 + 96) < nb.value < 2 * 4096 * 8 * 2000
+    for bad in (dict(a=-1.0), dict(node_rule=5), dict(reinv_period=0), dict(precision=1)):
+        s, w, p, keep = _structs(W.h2_sto3g(), **bad)
+        assert lib.lrdmc_workspace_bytes(ctypes.byref(s), ctypes.byref(w), ctypes.byref(p),
+                                         ctypes.byref(nb)) == 1
+    s, w, p, keep = _structs(W.h2_sto3g(), n_w=0)
+    assert lib.lrdmc_workspace_bytes(ctypes.byref(s), ctypes.byref(w), ctypes.byref(p), ctypes.byref(nb)) == 1
+    # a system whose per-walker working set cannot fit in shared memory is refused
+    s, w, p, keep = _structs(W.hydrogen_chain(128), n_w=16)
+    assert lib.lrdmc_workspace_bytes(ctypes.byref(s), ctypes.byref(w), ctypes.byref(p),
+                                     ctypes.byref(nb)) == 7
+
+
+def test_reconfigure_rejects_bad_arguments(lib):
+    assert lib.lrdmc_reconfigure_indices(0, None, 0, None, None, 0, None, None) == 1
+    assert lib.lrdmc_reconfigure_scratch_bytes(0) == 0
+    assert lib.lrdmc_reconfigure_scratch_bytes(1000) >= 8000
