@@ -1,0 +1,316 @@
+"""Benchmark of the LRDMC hot path on one B300 (or N independent replicas).
+
+One *step* is one branching interval of the load-balanced schedule over the
+whole population: N_proj = 20 lattice hops for every walker (evaluation of all
+6 N_e hop ratios, diagonal W and local energy, weight update, heat-bath hop,
+Sherman-Morrison update) followed by the branching step (statistics,
+integer-comb reconfiguration, gather).  Workload: the synthetic water-methane
+complex (16 valence electrons, 56 Gaussian basis functions, 8 nuclei), 4096
+walkers, a = 0.2 bohr, FP64.
+
+Prints one JSON line.  ``--impl reference`` times the CPU oracle instead (the
+reference arm of this benchmark) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_W = 4096
+N_PROJ = 20
+A = 0.2
+SEED = 1
+FP64_PEAK_GFLOPS = 1250.0      # nominal B300 FP64 rate (profiling recipe table)
+# Pipe cost of FP64 functions in FMA slots, measured on B300 by the pipe
+# microbenchmark shipped with the library (see the profiles directory).
+SLOT_EXP, SLOT_SQRT, SLOT_RCP, SLOT_ERF = 20.0, 11.7, 6.6, 46.4
+
+
+def algorithmic_slots_per_walker_step(n_e, n_nuc, n_bf, n_prim, n_sig, n_shell):
+    """FP64 work the method needs per walker-step, in FMA-slot units (one slot =
+    one FP64 add/mul/FMA; a function counts its measured pipe cost).
+
+    hops P = 6 n_e; per hop: n_prim basis exponentials, the chi . g_i dot
+    (n_bf FMAs) plus distances (6 per shell), (n_e - 1 + n_nuc) Jastrow pair
+    terms (sqrt + reciprocal + 8 arithmetic), one Jastrow exponential;
+    per electron: g_i = C^T B[:, i] (n_bf n_sig FMAs), (n_e - 1 + n_nuc) pair
+    terms with derivatives (sqrt + 2 reciprocals + 20), the screened potential
+    (erf + reciprocal per nucleus), 4 n_sig FMAs of the determinant derivatives;
+    per hop applied: basis value/gradient/Laplacian at one point (n_prim
+    exponentials + 10 per primitive), 5 n_bf n_sig contraction FMAs,
+    2 n_sig^2 Sherman-Morrison FMAs."""
+    P = 6 * n_e
+    per_hop = n_prim * (SLOT_EXP + 2) + n_bf + 6 * n_shell + (n_e - 1 + n_nuc) * (SLOT_SQRT + SLOT_RCP + 8) + SLOT_EXP
+    per_elec = n_bf * n_sig + (n_e - 1 + n_nuc) * (SLOT_SQRT + 2 * SLOT_RCP + 20) + n_nuc * (SLOT_ERF + SLOT_RCP) + 4 * n_sig
+    move = n_prim * (SLOT_EXP + 10) + 5 * n_bf * n_sig + 2 * n_sig * n_sig
+    return P * per_hop + n_e * per_elec + move
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.rows = []
+        self.proc = None
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([v.strip() for v in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) >= 9:
+                for k, nm in enumerate(names):
+                    if r[5 + k].lower().startswith("active"):
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- oracle baseline
+def _oracle_chunk(args):
+    ids, n_proj, interval = args
+    import workloads as W
+    from oracle import lrdmc as L
+    s = W.water_methane()
+    x = W.initial_walkers(s, N_W, seed=SEED + 10)[ids]
+    Wk = L.init_walkers(s, x, A)
+    E0 = float(np.mean(Wk.ev["eL"]))
+    t = time.perf_counter()
+    L.propagate_lb(s, Wk, A, E0, n_proj, SEED, interval, walker_ids=ids)
+    return time.perf_counter() - t, len(ids) * n_proj
+
+
+def oracle_rate(n_walkers_per_proc=48, n_proj=N_PROJ, procs=None):
+    """Walker-steps/s of the CPU oracle on a bounded sample, all host cores
+    (one spawned process per core, each on its own walker slots)."""
+    import multiprocessing as mp
+    procs = procs or os.cpu_count() or 1
+    jobs = [(np.arange(k * n_walkers_per_proc, (k + 1) * n_walkers_per_proc) % N_W, n_proj, 0)
+            for k in range(procs)]
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(procs) as pool:
+        res = pool.map(_oracle_chunk, jobs)
+    wall = time.perf_counter() - t0
+    steps = sum(r[1] for r in res)
+    slowest = max(r[0] for r in res)
+    return steps / slowest, procs, steps, wall
+
+
+# ----------------------------------------------------------------- GPU arm
+def run_gpu(args, rank, world):
+    import torch
+    import workloads as W
+    from paper_2508_12033_b300 import build
+    build.build()
+    import paper_2508_12033_b300 as P
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    s = W.water_methane()
+    x0 = W.initial_walkers(s, N_W, seed=SEED + 10 + rank)
+    lr = P.Lrdmc(s, x0, A, seed=SEED + rank, reinv_period=100, p_gbar=10)
+    stream = lr.stream
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > 126 MB L2
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        lr.propagate(P.LOAD_BALANCED, n_proj=N_PROJ)
+        lr.branch()
+    torch.cuda.synchronize()
+    barrier()
+    n0 = lr.launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(dev.index) as clk:
+        torch.cuda.synchronize()
+        barrier()
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(k & 0xFF)               # L2 flush between timed steps (not timed)
+                ev[k][0].record(stream)
+                lr.propagate(P.LOAD_BALANCED, n_proj=N_PROJ)
+                ev[k][1].record(stream)
+                lr.branch()                          # synchronises on its statistics readback
+                ev[k][2].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    launches = lr.launch_count() - n0
+    step_ms = [e0.elapsed_time(e2) for e0, _, e2 in ev]
+    prop_ms = [e0.elapsed_time(e1) for e0, e1, _ in ev]
+    t_total = sum(step_ms) / 1e3
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_total = float(tt.item())
+    ws_per_step = N_W * N_PROJ
+    value = world * ws_per_step * args.steps / t_total
+    # roofline of the dominant kernel (the propagate kernel: one launch per step)
+    slots = algorithmic_slots_per_walker_step(s.n_elec, s.n_nuc, s.n_bf, s.n_prim_eval, max(s.n_up, s.n_dn),
+                                              s.n_shell)
+    prop_s = statistics.mean(prop_ms) / 1e3
+    achieved = 2.0 * slots * ws_per_step / prop_s / 1e9      # GFLOP/s, FP64-equivalent
+    # conventional schedule at the same mean hops per interval (tau = N_proj / <b_bar>)
+    g = lr.get_walkers()
+    tau = N_PROJ / float(np.mean(g["ev"][:, 0]))
+    conv_ms, conv_moves = [], []
+    for k in range(max(2, args.steps // 2)):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0xFF)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lr.propagate(P.CONVENTIONAL, tau=tau, max_moves=100 * N_PROJ)
+            lr.branch()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        conv_ms.append(e0.elapsed_time(e1))
+        h = lr.history()
+        conv_moves.append((float(h["moves_mean"][-1]), int(h["moves_max"][-1])))
+    conv_rate = N_W * statistics.mean(m for m, _ in conv_moves) / (statistics.mean(conv_ms) / 1e3)
+    # end to end through the public API with host buffers: upload the walkers
+    # from pinned host memory, one interval + branching, read them back
+    xh = torch.from_numpy(lr.get_walkers()["x"]).pin_memory()
+    e2e_ms = []
+    for k in range(max(2, args.steps // 2)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lr.set_walkers(xh.numpy())
+        lr.propagate(P.LOAD_BALANCED, n_proj=N_PROJ)
+        lr.branch()
+        out = lr.get_walkers()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        xh.copy_(torch.from_numpy(out["x"]))
+    h2d = N_W * s.n_elec * 3 * 8
+    d2h = 8 * (N_W * (3 * s.n_elec + 6 * s.n_elec + 7))
+    e2e_value = world * ws_per_step / (statistics.mean(e2e_ms) / 1e3)
+    return dict(value=value, t_total=t_total, step_ms=statistics.mean(step_ms), prop_ms=statistics.mean(prop_ms),
+                launches=launches, achieved=achieved, clocks=clk.summary(), conv_rate=conv_rate,
+                conv_moves=conv_moves, tau=tau, e2e=e2e_value, h2d=h2d, d2h=d2h, slots=slots,
+                energy=lr.energy())
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="lrdmc", choices=["lrdmc", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    workload = {"workload": "water-methane complex: 8 nuclei (C, 4 H, O, 2 H), 16 valence electrons "
+                            "(8 up, 8 down), erf-screened local pseudopotentials, 56 single-primitive GTOs, "
+                            "seeded orthonormal MOs, Pade 1- and 2-body Jastrow; a = 0.2 bohr",
+                "n_w": N_W, "n_e": 16, "n_proj": N_PROJ, "schedule": "load-balanced",
+                "step": "one branching interval (20 hops per walker) + reconfiguration",
+                "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{args.gpus}"}
+    metric = "walker-steps/s (LRDMC load-balanced, FP64)"
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        rates = []
+        t0 = time.perf_counter()
+        for k in range(args.warmup + args.steps):
+            r, procs, steps, _ = oracle_rate(n_walkers_per_proc=8, n_proj=4)
+            if k >= args.warmup:
+                rates.append(r)
+        v = statistics.mean(rates)
+        line = {"impl": "reference", "metric": metric, "value": v, "unit": "walker-steps/s", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * N_W * N_PROJ / v,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": workload,
+                "cpu_baseline": {"value": v, "unit": "walker-steps/s", "cores": procs, "kind": "oracle",
+                                 "sample": f"{procs} processes x 8 walkers x 4 hops per step"},
+                "e2e": {"value": v, "unit": "walker-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                "wall_s": time.perf_counter() - t0}
+        print(json.dumps(line))
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        r, procs, steps, wall = oracle_rate()
+        cpu = {"value": r, "unit": "walker-steps/s", "cores": procs, "kind": "oracle",
+               "sample": f"{procs} processes x 48 walkers x {N_PROJ} hops (one interval, load-balanced), "
+                         f"{steps} walker-steps, {wall:.1f} s wall"}
+    res = run_gpu(args, rank, world)
+    if rank == 0:
+        peak = FP64_PEAK_GFLOPS
+        line = {
+            "metric": metric, "value": res["value"], "unit": "walker-steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["step_ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload,
+            "electron_move_attempts_per_s": res["value"] * 6 * 16,
+            "roofline": {"bound": "alu", "kernel": "k_propagate", "achieved": res["achieved"], "peak": peak,
+                         "unit": "GFLOP/s (FP64, functions at measured pipe cost)",
+                         "frac": res["achieved"] / peak, "traffic": None,
+                         "peak_source": "nominal FP64 rate of the recipe table (no FP64 entry measured)",
+                         "kernel_ms": res["prop_ms"], "slots_per_walker_step": res["slots"]},
+            "conventional": {"value": res["conv_rate"], "unit": "walker-steps/s", "tau": res["tau"],
+                             "moves_mean_max": res["conv_moves"],
+                             "lb_speedup": res["value"] / res["conv_rate"]},
+            "cpu_baseline": cpu,
+            "e2e": {"value": res["e2e"], "unit": "walker-steps/s", "h2d_bytes_per_step": res["h2d"],
+                    "d2h_bytes_per_step": res["d2h"]},
+            "gpu_launches": res["launches"],
+            "clocks": res["clocks"],
+            "energy": {"E": res["energy"][0], "err": res["energy"][1]},
+        }
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
