@@ -1,0 +1,170 @@
+// Pipe-throughput microbenchmark: FP64/FP32 FMA and the FP64 functions the
+// propagate kernel calls.  Prints one line per operation: best-of-5 rate and,
+// for FP64 operations, the cost in FP64 FMA slots (FMA rate / op rate).  Used to
+// weight functions in the FP64 roofline model of the propagate kernel.
+#include <cstdio>
+#include <cuda_runtime.h>
+
+template <int ILP>
+__global__ void k_dfma(double* out, int iters, double s) {
+  double a[ILP];
+  for (int j = 0; j < ILP; j++) a[j] = threadIdx.x * 1e-3 + j;
+  for (int i = 0; i < iters; i++)
+#pragma unroll
+    for (int j = 0; j < ILP; j++) a[j] = fma(a[j], s, 0.999);
+  double r = 0;
+  for (int j = 0; j < ILP; j++) r += a[j];
+  if (r == 12345.678) out[0] = r;
+}
+
+template <int ILP>
+__global__ void k_ffma(float* out, int iters, float s) {
+  float a[ILP];
+  for (int j = 0; j < ILP; j++) a[j] = threadIdx.x * 1e-3f + j;
+  for (int i = 0; i < iters; i++)
+#pragma unroll
+    for (int j = 0; j < ILP; j++) a[j] = fmaf(a[j], s, 0.999f);
+  float r = 0;
+  for (int j = 0; j < ILP; j++) r += a[j];
+  if (r == 12345.678f) out[0] = r;
+}
+
+template <int OP>
+__global__ void k_dfun(double* out, int iters) {
+  double a[4];
+  for (int j = 0; j < 4; j++) a[j] = -(threadIdx.x % 7) * 0.1 - 0.5 - 0.01 * j;
+  double acc = 0;
+  for (int i = 0; i < iters; i++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      double v;
+      if (OP == 0) v = exp(a[j]);
+      else if (OP == 1) v = sqrt(-a[j]);
+      else if (OP == 2) v = 1.0 / a[j];
+      else if (OP == 3) v = erf(a[j]);
+      else v = rsqrt(-a[j]);
+      acc += v;
+      a[j] -= 1e-9;
+    }
+  if (acc == 12345.678) out[0] = acc;
+}
+
+// Conversions and the approximate FP64 reciprocal / reciprocal square root.
+__device__ __forceinline__ double rcp_approx_f64(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  return r;
+}
+__device__ __forceinline__ double rsqrt_approx_f64(double x) {
+  double r;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  return r;
+}
+
+template <int OP>
+__global__ void k_dmisc(double* out, int iters) {
+  double a[4];
+  for (int j = 0; j < 4; j++) a[j] = (threadIdx.x % 7) * 0.1 + 0.5 + 0.01 * j;
+  double acc = 0;
+  for (int i = 0; i < iters; i++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      double v;
+      if (OP == 0) v = (double)((float)a[j] * 1.0001f);          // f64 -> f32 -> f64
+      else if (OP == 1) v = rcp_approx_f64(a[j]);
+      else if (OP == 2) v = rsqrt_approx_f64(a[j]);
+      else v = (double)__double2int_rn(a[j] * 3.0);
+      acc += v;
+      a[j] += 1e-9;
+    }
+  if (acc == 12345.678) out[0] = acc;
+}
+
+template <int OP>
+__global__ void k_ffun(float* out, int iters) {
+  float a[4];
+  for (int j = 0; j < 4; j++) a[j] = -(threadIdx.x % 7) * 0.1f - 0.5f - 0.01f * j;
+  float acc = 0;
+  for (int i = 0; i < iters; i++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      float v;
+      if (OP == 0) v = __expf(a[j]);
+      else if (OP == 1) v = expf(a[j]);
+      else if (OP == 2) v = sqrtf(-a[j]);
+      else v = __fdividef(1.f, a[j]);
+      acc += v;
+      a[j] -= 1e-7f;
+    }
+  if (acc == 12345.678f) out[0] = acc;
+}
+
+template <typename F>
+static float best_ms(F launch) {
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  launch();
+  cudaDeviceSynchronize();
+  float best = 1e30f;
+  for (int r = 0; r < 5; r++) {
+    cudaEventRecord(e0);
+    launch();
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) best = ms;
+  }
+  return best;
+}
+
+int main() {
+  cudaDeviceProp p;
+  if (cudaGetDeviceProperties(&p, 0) != cudaSuccess) { printf("no device\n"); return 1; }
+  int clk = 0;
+  cudaDeviceGetAttribute(&clk, cudaDevAttrClockRate, 0);
+  printf("device %s, %d SMs, max clock %d kHz\n", p.name, p.multiProcessorCount, clk);
+  double* dout;
+  float* fout;
+  if (cudaMalloc(&dout, 8) != cudaSuccess || cudaMalloc(&fout, 8) != cudaSuccess) return 1;
+  const int sms = p.multiProcessorCount;
+  const int blocks = sms * 4, threads = 256;
+  const double n8 = (double)blocks * threads * 8, n4 = (double)blocks * threads * 4;
+  const int it = 20000, itf = 2000;
+  float ms = best_ms([&] { k_dfma<8><<<blocks, threads>>>(dout, it, 1.0000001); });
+  const double dfma = n8 * it / (ms * 1e-3);
+  printf("DFMA      %12.4g op/s  %8.3f TFLOP/s\n", dfma, 2 * dfma / 1e12);
+  ms = best_ms([&] { k_ffma<8><<<blocks, threads>>>(fout, it, 1.0000001f); });
+  printf("FFMA      %12.4g op/s  %8.3f TFLOP/s  (%.1fx DFMA)\n", n8 * it / (ms * 1e-3), 2 * n8 * it / (ms * 1e-3) / 1e12,
+         n8 * it / (ms * 1e-3) / dfma);
+  const char* dn[5] = {"exp", "sqrt", "rcp", "erf", "rsqrt"};
+  float t[5];
+  t[0] = best_ms([&] { k_dfun<0><<<blocks, threads>>>(dout, itf); });
+  t[1] = best_ms([&] { k_dfun<1><<<blocks, threads>>>(dout, itf); });
+  t[2] = best_ms([&] { k_dfun<2><<<blocks, threads>>>(dout, itf); });
+  t[3] = best_ms([&] { k_dfun<3><<<blocks, threads>>>(dout, itf); });
+  t[4] = best_ms([&] { k_dfun<4><<<blocks, threads>>>(dout, itf); });
+  for (int k = 0; k < 5; k++) {
+    const double r = n4 * itf / (t[k] * 1e-3);
+    printf("%-9s %12.4g op/s  %8.1f FP64 FMA slots\n", dn[k], r, dfma / r);
+  }
+  const char* mn[4] = {"cvt64-32-64", "rcp.approx.f64", "rsqrt.approx.f64", "d2i_rn+i2d"};
+  float tm[4];
+  tm[0] = best_ms([&] { k_dmisc<0><<<blocks, threads>>>(dout, itf); });
+  tm[1] = best_ms([&] { k_dmisc<1><<<blocks, threads>>>(dout, itf); });
+  tm[2] = best_ms([&] { k_dmisc<2><<<blocks, threads>>>(dout, itf); });
+  tm[3] = best_ms([&] { k_dmisc<3><<<blocks, threads>>>(dout, itf); });
+  for (int k = 0; k < 4; k++) {
+    const double r = n4 * itf / (tm[k] * 1e-3);
+    printf("%-17s %12.4g op/s  %8.1f FP64 FMA slots (incl. one DADD)\n", mn[k], r, dfma / r);
+  }
+  const char* fn[4] = {"__expf", "expf", "sqrtf", "fdividef"};
+  float tf[4];
+  tf[0] = best_ms([&] { k_ffun<0><<<blocks, threads>>>(fout, it); });
+  tf[1] = best_ms([&] { k_ffun<1><<<blocks, threads>>>(fout, it); });
+  tf[2] = best_ms([&] { k_ffun<2><<<blocks, threads>>>(fout, it); });
+  tf[3] = best_ms([&] { k_ffun<3><<<blocks, threads>>>(fout, it); });
+  for (int k = 0; k < 4; k++) printf("%-9s %12.4g op/s\n", fn[k], n4 * it / (tf[k] * 1e-3));
+  return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
