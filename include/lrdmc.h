@@ -220,6 +220,30 @@ lrdmc_status lrdmc_reconfigure_indices(int n, const double* w, uint32_t xi32, in
                                        void* scratch, size_t scratch_bytes,
                                        int32_t* status_out, void* stream);
 
+/* Allocation-free variant of lrdmc_reconfigure_indices (the paper has no
+ * counterpart; this is a library convenience).  It is meant for callers that
+ * cannot call cudaMalloc -- for example code running inside a CUDA graph that
+ * is being captured, a host with a custom or exhausted device allocator, or an
+ * embedding runtime that forbids allocation on its hot path.  Instead of a
+ * caller-provided scratch buffer it uses one fixed array in the library's
+ * device memory, sized for LRDMC_NOALLOC_MAX_WALKERS walkers (about 2 MiB,
+ * held on every GPU that loads the library until the process exits).
+ *   - Same inputs, outputs and results as lrdmc_reconfigure_indices (w, xi32,
+ *     src and status_out with the same meaning); nothing is allocated.
+ *   - n must be in [1, LRDMC_NOALLOC_MAX_WALKERS]; a larger n returns
+ *     LRDMC_ERR_UNSUPPORTED without launching anything, other bad arguments
+ *     LRDMC_ERR_ARG.
+ *   - The first call on a device looks up that device's copy of the array
+ *     (a one-time set-up with that device current); make that first call
+ *     before any stream capture.
+ *   - All calls share the one array and it keeps the last call's contents;
+ *     the kernel overwrites every scratch word before reading it.  Calls that
+ *     overlap on the GPU (e.g. on two streams at once) race on the array and
+ *     must be serialised by the caller. */
+#define LRDMC_NOALLOC_MAX_WALKERS (1 << 18)
+lrdmc_status lrdmc_reconfigure_indices_noalloc(int n, const double* w, uint32_t xi32, int32_t* src,
+                                               int32_t* status_out, void* stream);
+
 /* Philox4x32-10 block for counter (c0, c1, c2, c3) under key = seed, computed on
  * the host with the library's own implementation (testing aid). */
 void lrdmc_philox4x32(uint64_t seed, const uint32_t ctr[4], uint32_t out[4]);

@@ -284,3 +284,27 @@ def philox4x32(seed, ctr):
     o = (C.c_uint32 * 4)()
     lib.lrdmc_philox4x32(int(seed) & (2**64 - 1), c, o)
     return tuple(int(v) for v in o)
+
+
+def reconfigure_indices_noalloc(w, xi32, stream=None):
+    """Same as ``reconfigure_indices`` through the allocation-free entry point
+    (the library's fixed device scratch array; n <= LRDMC_NOALLOC_MAX_WALKERS).
+
+    For callers that cannot allocate device memory at call time.  The output
+    tensors here are allocated by PyTorch only because this helper returns new
+    tensors; the library call itself allocates nothing."""
+    import torch
+    lib = load_library()
+    f = lib.lrdmc_reconfigure_indices_noalloc
+    f.argtypes = [C.c_int, C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p]
+    f.restype = C.c_int
+    assert w.is_cuda and w.dtype == torch.float64 and w.is_contiguous() and w.dim() == 1
+    n = int(w.shape[0])
+    src = torch.empty(n, dtype=torch.int32, device=w.device)
+    st = torch.empty(2, dtype=torch.int32, device=w.device)
+    s = stream if stream is not None else torch.cuda.current_stream(w.device)
+    r = f(n, _tptr(w), int(xi32) & 0xFFFFFFFF, _tptr(src), _tptr(st), C.c_void_p(s.cuda_stream))
+    if r != 0:
+        raise LrdmcError(r, "lrdmc_reconfigure_indices_noalloc failed")
+    s.synchronize()
+    return src, st

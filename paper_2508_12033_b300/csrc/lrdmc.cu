@@ -3,6 +3,8 @@
 #include "lrdmc.h"
 
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -607,6 +609,61 @@ lrdmc_status lrdmc_reconfigure_indices(int n, const double* w, uint32_t xi32, in
     e = cudaMemcpyAsync(status_out, st, 2 * sizeof(int32_t), cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
     if (e != cudaSuccess) return LRDMC_ERR_CUDA;
   }
+  return LRDMC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free reconfiguration indices.  Scratch lives in one file-scope
+// device array (Q words followed by two status words); its device address is
+// looked up once per device with cudaGetSymbolAddress.  The host-side symbol
+// name is not a device address and is never passed to a kernel.
+}  // extern "C"
+
+namespace {
+constexpr int NOALLOC_Q_WORDS = LRDMC_NOALLOC_MAX_WALKERS;
+static __device__ __align__(256) unsigned long long g_noalloc_scratch[NOALLOC_Q_WORDS + 32];
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::atomic<unsigned long long*> g_noalloc_ptr[NOALLOC_MAX_DEVICES];
+std::mutex g_noalloc_mutex;
+
+// Device address of this device's scratch array (set up on first use).
+cudaError_t noalloc_scratch(unsigned long long** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+  unsigned long long* p = g_noalloc_ptr[dev].load();
+  if (!p) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    p = g_noalloc_ptr[dev].load();
+    if (!p) {
+      void* addr = nullptr;
+      e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
+      if (e != cudaSuccess) return e;
+      p = (unsigned long long*)addr;
+      g_noalloc_ptr[dev].store(p);
+    }
+  }
+  *out = p;
+  return cudaSuccess;
+}
+}  // namespace
+
+extern "C" {
+
+lrdmc_status lrdmc_reconfigure_indices_noalloc(int n, const double* w, uint32_t xi32, int32_t* src,
+                                               int32_t* status_out, void* stream) {
+  if (n > LRDMC_NOALLOC_MAX_WALKERS) return LRDMC_ERR_UNSUPPORTED;
+  if (n < 1 || !w || !src) return LRDMC_ERR_ARG;
+  unsigned long long* q = nullptr;
+  if (noalloc_scratch(&q) != cudaSuccess) return LRDMC_ERR_CUDA;
+  int32_t* st = (int32_t*)(q + NOALLOC_Q_WORDS);
+  k_reconfigure<<<1, BR_THREADS, 0, (cudaStream_t)stream>>>(w, 1, n, xi32, q, src, st, nullptr);
+  if (cudaGetLastError() != cudaSuccess) return LRDMC_ERR_CUDA;
+  if (status_out &&
+      cudaMemcpyAsync(status_out, st, 2 * sizeof(int32_t), cudaMemcpyDeviceToDevice, (cudaStream_t)stream) !=
+          cudaSuccess)
+    return LRDMC_ERR_CUDA;
   return LRDMC_OK;
 }
 
