@@ -34,29 +34,36 @@ N_PROJ = 20
 A = 0.2
 SEED = 1
 FP64_PEAK_GFLOPS = 1250.0      # nominal B300 FP64 rate (profiling recipe table)
-# Pipe cost of FP64 functions in FMA slots, measured on B300 by the pipe
-# microbenchmark shipped with the library (see the profiles directory).
-SLOT_EXP, SLOT_SQRT, SLOT_RCP, SLOT_ERF = 20.0, 11.7, 6.6, 46.4
+# Pipe cost, in FP64 FMA slots, of the FP64 functions as the propagate kernel
+# implements them (measured on B300 by the pipe microbenchmark shipped with the
+# library; see profiles/): table-driven exp, approximate reciprocal / rsqrt plus
+# two Newton steps, and CUDA's sqrt and erf for the moved electron's potential.
+SLOT_EXP, SLOT_RSQ, SLOT_RCP, SLOT_SQRT, SLOT_ERF = 10.0, 8.9, 4.9, 11.7, 46.4
 
 
-def algorithmic_slots_per_walker_step(n_e, n_nuc, n_bf, n_prim, n_sig, n_shell):
-    """FP64 work the method needs per walker-step, in FMA-slot units (one slot =
-    one FP64 add/mul/FMA; a function counts its measured pipe cost).
+def algorithmic_slots_per_walker_step(n_e, n_nuc, n_bf, n_prim, n_sig, n_s_shell, n_p_shell, one_body=True):
+    """FP64 work per walker-step of the load-balanced step as formulated in the
+    propagate kernel, in FMA slots (one FP64 add/mul/FMA = 1; a function counts
+    its pipe cost above).
 
-    hops P = 6 n_e; per hop: n_prim basis exponentials, the chi . g_i dot
-    (n_bf FMAs) plus distances (6 per shell), (n_e - 1 + n_nuc) Jastrow pair
-    terms (sqrt + reciprocal + 8 arithmetic), one Jastrow exponential;
-    per electron: g_i = C^T B[:, i] (n_bf n_sig FMAs), (n_e - 1 + n_nuc) pair
-    terms with derivatives (sqrt + 2 reciprocals + 20), the screened potential
-    (erf + reciprocal per nucleus), 4 n_sig FMAs of the determinant derivatives;
-    per hop applied: basis value/gradient/Laplacian at one point (n_prim
-    exponentials + 10 per primitive), 5 n_bf n_sig contraction FMAs,
-    2 n_sig^2 Sherman-Morrison FMAs."""
-    P = 6 * n_e
-    per_hop = n_prim * (SLOT_EXP + 2) + n_bf + 6 * n_shell + (n_e - 1 + n_nuc) * (SLOT_SQRT + SLOT_RCP + 8) + SLOT_EXP
-    per_elec = n_bf * n_sig + (n_e - 1 + n_nuc) * (SLOT_SQRT + 2 * SLOT_RCP + 20) + n_nuc * (SLOT_ERF + SLOT_RCP) + 4 * n_sig
-    move = n_prim * (SLOT_EXP + 10) + 5 * n_bf * n_sig + 2 * n_sig * n_sig
-    return P * per_hop + n_e * per_elec + move
+    Per hop (6 n_e of them): per nucleus the displaced squared distance and
+    offset (2) and, with a one-body Jastrow, its Pade term (rsqrt + reciprocal +
+    5); per primitive one exponential + 2; per s / p shell 1 / 4 for the dot
+    with g_i; per other electron the displaced distance (2) + Pade term; the
+    Jastrow exponential + 2.  Per electron (current configuration): per
+    partner (electrons and nuclei) distance (6), Pade value and derivatives
+    (rsqrt + reciprocal + 12), accumulation (7); determinant derivatives
+    4 n_sig; assembly 25.  Per applied hop: basis value/gradient/Laplacian
+    (exp + 10 per primitive), 5 n_bf n_sig contraction, 2 n_sig^2
+    Sherman-Morrison, n_sig n_bf update of g, potentials (sqrt + erf +
+    2 reciprocals + 6 per nucleus)."""
+    pade = SLOT_RSQ + SLOT_RCP + 5
+    per_hop = (n_nuc * (2 + (pade if one_body else 0)) + n_prim * (SLOT_EXP + 2) + n_s_shell + 4 * n_p_shell
+               + (n_e - 1) * (2 + pade) + SLOT_EXP + 2)
+    per_elec = (n_e - 1 + n_nuc) * (6 + SLOT_RSQ + SLOT_RCP + 12 + 7) + 4 * n_sig + 25
+    move = (n_prim * (SLOT_EXP + 10) + 5 * n_bf * n_sig + 2 * n_sig * n_sig + n_sig * n_bf
+            + n_nuc * (SLOT_SQRT + SLOT_ERF + 2 * SLOT_RCP + 6))
+    return 6 * n_e * per_hop + n_e * per_elec + move
 
 
 # ----------------------------------------------------------------- clocks
@@ -193,7 +200,8 @@ def run_gpu(args, rank, world):
     value = world * ws_per_step * args.steps / t_total
     # roofline of the dominant kernel (the propagate kernel: one launch per step)
     slots = algorithmic_slots_per_walker_step(s.n_elec, s.n_nuc, s.n_bf, s.n_prim_eval, max(s.n_up, s.n_dn),
-                                              s.n_shell)
+                                              int(np.sum(s.shell_l == 0)), int(np.sum(s.shell_l == 1)),
+                                              bool(np.any(s.j1_A != 0)))
     prop_s = statistics.mean(prop_ms) / 1e3
     achieved = 2.0 * slots * ws_per_step / prop_s / 1e9      # GFLOP/s, FP64-equivalent
     # conventional schedule at the same mean hops per interval (tau = N_proj / <b_bar>)

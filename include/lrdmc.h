@@ -248,6 +248,13 @@ lrdmc_status lrdmc_reconfigure_indices_noalloc(int n, const double* w, uint32_t 
  * the host with the library's own implementation (testing aid). */
 void lrdmc_philox4x32(uint64_t seed, const uint32_t ctr[4], uint32_t out[4]);
 
+/* Testing aid: the library's reduced-slot FP64 exp, reciprocal and reciprocal
+ * square root (table-driven exponential after Tang 1989; hardware approximations
+ * refined by two Newton steps) applied elementwise to n device doubles.  Any
+ * output may be NULL.  Asynchronous on stream. */
+lrdmc_status lrdmc_fp64math(int n, const double* x, double* exp_out, double* rcp_out, double* rsqrt_out,
+                            void* stream);
+
 /* Number of kernels this handle has launched so far (all entry points). */
 lrdmc_status lrdmc_launch_count(lrdmc_handle h, int64_t* n);
 

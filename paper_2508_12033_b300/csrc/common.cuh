@@ -46,6 +46,8 @@ struct DevSys {
   const int* sh_nprim;   // n_shell
   const int* sh_off;     // n_shell: first primitive
   const int* sh_bf;      // n_shell: first basis function
+  const int* atom_sh;    // n_nuc + 1: shells are grouped by nucleus, atom I owns [atom_sh[I], atom_sh[I+1])
+  const double* exptab;  // 64: 2^(j/64) for the table-driven exponential
   const double* exps;    // n_prim
   const double* coefs;   // n_prim
   const double* C;       // n_orb x n_bf
@@ -57,10 +59,14 @@ struct DevSys {
 // per-warp working set in shared memory.
 struct Layout {
   int n_e, n_up, n_dn, n_max, n_bf, n_hop;
-  // global walker block
-  int g_x, g_bt, g_cache, g_rat, g_sc, g_stride;
-  // shared memory per warp
-  int s_x, s_bt, s_g, s_rat, s_cache, s_ej, s_ep, s_chi5, s_phi5, s_u, s_row, s_sc, s_stride;
+  // global walker block: positions, B^T, orbital cache [n_e][5][n_max], hop
+  // ratios, per-electron potentials (nu_ei, nu^a_ei), scalars
+  int g_x, g_bt, g_cache, g_rat, g_pot, g_sc, g_stride;
+  // shared memory per warp: positions, B^T, g (also Gauss-Jordan scratch),
+  // ratios, per-electron Jastrow terms [6], potentials [2], determinant
+  // derivatives [4], electron-nucleus geometry [4] (also the moved electron's
+  // basis scratch), pair distances, orbital scratch, rank-1 factors, scalars
+  int s_x, s_bt, s_g, s_rat, s_ej, s_ep, s_dd, s_geo, s_pr2, s_phi5, s_u, s_row, s_sc, s_stride;
 };
 
 __host__ __device__ inline int round_up(int v, int m) { return (v + m - 1) / m * m; }

@@ -34,7 +34,8 @@ struct Plan {
   size_t o_sys = 0, sys_bytes = 0, o_state = 0, o_alt = 0, state_bytes = 0, o_stats = 0, o_q = 0,
          o_src = 0, o_dstat = 0, total = 0;
   // system image offsets (bytes, inside the sys block)
-  size_t i_R, i_Z, i_rc, i_j1A, i_j1B, i_exps, i_coefs, i_C, i_kind, i_atom, i_l, i_nprim, i_off, i_bf;
+  size_t i_R, i_Z, i_rc, i_j1A, i_j1B, i_exps, i_coefs, i_C, i_kind, i_atom, i_l, i_nprim, i_off, i_bf, i_ash,
+      i_tab;
   std::string err;
 };
 
@@ -78,7 +79,8 @@ bool make_plan(const lrdmc_system* sys, const lrdmc_trial_wf* wf, const lrdmc_pa
   L.g_bt = 3 * P.n_e;
   L.g_cache = L.g_bt + nbt;
   L.g_rat = L.g_cache + 5 * P.n_max * P.n_e;
-  L.g_sc = round_up(L.g_rat + L.n_hop, 16);
+  L.g_pot = L.g_rat + L.n_hop;
+  L.g_sc = round_up(L.g_pot + 2 * P.n_e, 16);
   L.g_stride = round_up(L.g_sc + SC_COUNT, 16);
   // per-warp shared memory
   L.s_x = 0;
@@ -86,17 +88,18 @@ bool make_plan(const lrdmc_system* sys, const lrdmc_trial_wf* wf, const lrdmc_pa
   L.s_g = L.s_bt + nbt;
   const int gsz = std::max(P.n_e * P.n_bf, 2 * P.n_max * P.n_max);
   L.s_rat = L.s_g + gsz;
-  L.s_cache = L.s_rat + L.n_hop;
-  L.s_ej = L.s_cache + 5 * P.n_max * P.n_e;
-  L.s_ep = L.s_ej + 2 * P.n_e;
-  L.s_chi5 = L.s_ep + 3 * P.n_e;
-  L.s_phi5 = L.s_chi5 + 5 * P.n_bf;
+  L.s_ej = L.s_rat + L.n_hop;
+  L.s_ep = L.s_ej + 6 * P.n_e;
+  L.s_dd = L.s_ep + 2 * P.n_e;
+  L.s_geo = L.s_dd + 4 * P.n_e;
+  L.s_pr2 = L.s_geo + std::max(4 * P.n_e * P.n_nuc, 6 * P.n_bf);
+  L.s_phi5 = L.s_pr2 + P.n_e * P.n_e;
   L.s_u = L.s_phi5 + 5 * P.n_max;
   L.s_row = L.s_u + P.n_max;
   L.s_sc = L.s_row + P.n_max;
   L.s_stride = round_up(L.s_sc + SC_COUNT, 4);
   P.smem_per_warp = (size_t)L.s_stride * sizeof(double);
-  if (P.smem_per_warp > 200 * 1024) { P.err = "system too large for the per-warp shared-memory layout"; return false; }
+  if (P.smem_per_warp + EXP_TAB * sizeof(double) > 200 * 1024) { P.err = "system too large for the per-warp shared-memory layout"; return false; }
   // system image
   size_t o = 0;
   auto take = [&](size_t bytes) { size_t r = o; o += (bytes + 15) / 16 * 16; return r; };
@@ -114,6 +117,8 @@ bool make_plan(const lrdmc_system* sys, const lrdmc_trial_wf* wf, const lrdmc_pa
   P.i_nprim = take(sizeof(int) * P.n_shell);
   P.i_off = take(sizeof(int) * P.n_shell);
   P.i_bf = take(sizeof(int) * P.n_shell);
+  P.i_ash = take(sizeof(int) * (P.n_nuc + 1));
+  P.i_tab = take(sizeof(double) * EXP_TAB);
   P.sys_bytes = o;
   // workspace
   size_t w = 0;
@@ -237,8 +242,12 @@ static lrdmc_status cuda_fail(lrdmc_handle h, const char* what, cudaError_t e) {
     if (e_ != cudaSuccess) return cuda_fail(h, "kernel launch", e_); \
   } while (0)
 
+static int smem_bytes(lrdmc_handle h) {
+  return (int)(EXP_TAB * sizeof(double) + h->wpb * h->P.smem_per_warp);
+}
+
 static lrdmc_status set_kernel_smem(lrdmc_handle h) {
-  const int bytes = (int)(h->wpb * h->P.smem_per_warp);
+  const int bytes = smem_bytes(h);
   CK(h, cudaFuncSetAttribute(k_propagate, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
   CK(h, cudaFuncSetAttribute(k_init_walkers, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
   CK(h, cudaFuncSetAttribute(k_eval_configs, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
@@ -261,7 +270,7 @@ static lrdmc_status place_walkers(lrdmc_handle h, const double* x, const double*
     dw = h->alt + (size_t)P.n_w * 3 * P.n_e;
     CK(h, cudaMemcpyAsync(dw, w, sizeof(double) * P.n_w, cudaMemcpyHostToDevice, h->stream));
   }
-  const int smem = (int)(h->wpb * P.smem_per_warp);
+  const int smem = smem_bytes(h);
   k_init_walkers<<<walker_grid(h, P.n_w), h->wpb * 32, smem, h->stream>>>(h->S, P.L, h->state, dx, dw, P.n_w,
                                                                           h->prm.a, h->prm.node_rule);
   LAUNCHED(h);
@@ -361,17 +370,34 @@ lrdmc_status lrdmc_create(const lrdmc_system* sys, const lrdmc_trial_wf* wf, con
   putd(P.i_coefs, wf->coefs, P.n_prim);
   putd(P.i_C, wf->C, (size_t)P.n_orb * P.n_bf);
   puti(P.i_kind, sys->pot_kind, P.n_nuc);
-  puti(P.i_atom, wf->shell_atom, P.n_shell);
-  puti(P.i_l, wf->shell_l, P.n_shell);
-  puti(P.i_nprim, wf->shell_nprim, P.n_shell);
+  // shells grouped by nucleus (stable); each keeps its primitive and basis offsets
   std::vector<int> off(P.n_shell), bf(P.n_shell);
   for (int s = 0, po = 0, bo = 0; s < P.n_shell; ++s) {
     off[s] = po; bf[s] = bo;
     po += wf->shell_nprim[s];
     bo += wf->shell_l[s] == 1 ? 3 : 1;
   }
-  puti(P.i_off, off.data(), P.n_shell);
-  puti(P.i_bf, bf.data(), P.n_shell);
+  std::vector<int> order(P.n_shell);
+  for (int s = 0; s < P.n_shell; ++s) order[s] = s;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return wf->shell_atom[x] < wf->shell_atom[y]; });
+  std::vector<int> r_atom(P.n_shell), r_l(P.n_shell), r_np(P.n_shell), r_off(P.n_shell), r_bf(P.n_shell);
+  std::vector<int> ash(P.n_nuc + 1, 0);
+  for (int k = 0; k < P.n_shell; ++k) {
+    const int s = order[k];
+    r_atom[k] = wf->shell_atom[s]; r_l[k] = wf->shell_l[s]; r_np[k] = wf->shell_nprim[s];
+    r_off[k] = off[s]; r_bf[k] = bf[s];
+    ash[r_atom[k] + 1]++;
+  }
+  for (int I = 0; I < P.n_nuc; ++I) ash[I + 1] += ash[I];
+  puti(P.i_atom, r_atom.data(), P.n_shell);
+  puti(P.i_l, r_l.data(), P.n_shell);
+  puti(P.i_nprim, r_np.data(), P.n_shell);
+  puti(P.i_off, r_off.data(), P.n_shell);
+  puti(P.i_bf, r_bf.data(), P.n_shell);
+  puti(P.i_ash, ash.data(), P.n_nuc + 1);
+  double tab[EXP_TAB];
+  for (int j = 0; j < EXP_TAB; ++j) tab[j] = (double)exp2l((long double)j / EXP_TAB);
+  putd(P.i_tab, tab, EXP_TAB);
   char* dsys = base + P.o_sys;
   CK(h, cudaMemcpyAsync(dsys, img.data(), P.sys_bytes, cudaMemcpyHostToDevice, h->stream));
   DevSys& S = h->S;
@@ -391,6 +417,8 @@ lrdmc_status lrdmc_create(const lrdmc_system* sys, const lrdmc_trial_wf* wf, con
   S.sh_nprim = (const int*)(dsys + P.i_nprim);
   S.sh_off = (const int*)(dsys + P.i_off);
   S.sh_bf = (const int*)(dsys + P.i_bf);
+  S.atom_sh = (const int*)(dsys + P.i_ash);
+  S.exptab = (const double*)(dsys + P.i_tab);
   S.j2_anti = wf->j2_anti;
   S.j2_par = wf->j2_par;
   S.j2_b = wf->j2_b;
@@ -413,14 +441,13 @@ lrdmc_status lrdmc_create(const lrdmc_system* sys, const lrdmc_trial_wf* wf, con
   int smem_optin = 0;
   CK(h, cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
   h->wpb = 4;
-  while (h->wpb > 1 && (size_t)h->wpb * P.smem_per_warp > (size_t)smem_optin) h->wpb >>= 1;
-  if ((size_t)h->wpb * P.smem_per_warp > (size_t)smem_optin)
+  while (h->wpb > 1 && (size_t)smem_bytes(h) > (size_t)smem_optin) h->wpb >>= 1;
+  if ((size_t)smem_bytes(h) > (size_t)smem_optin)
     return fail(h, LRDMC_ERR_UNSUPPORTED, "walker working set exceeds shared memory");
   lrdmc_status st = set_kernel_smem(h);
   if (st != LRDMC_OK) return st;
   int bps = 0;
-  CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_propagate, h->wpb * 32,
-                                                      (int)(h->wpb * P.smem_per_warp)));
+  CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_propagate, h->wpb * 32, smem_bytes(h)));
   if (bps < 1) return fail(h, LRDMC_ERR_UNSUPPORTED, "propagate kernel does not fit on an SM");
   h->grid = bps * h->num_sms;
   st = place_walkers(h, x0, nullptr);
@@ -466,7 +493,7 @@ lrdmc_status lrdmc_propagate(lrdmc_handle h, const lrdmc_schedule* sch) {
   sp.a = h->prm.a;
   sp.node_rule = h->prm.node_rule;
   sp.reinv_period = h->prm.reinv_period;
-  const int smem = (int)(h->wpb * h->P.smem_per_warp);
+  const int smem = smem_bytes(h);
   k_propagate<<<walker_grid(h, h->P.n_w), h->wpb * 32, smem, h->stream>>>(h->S, h->P.L, h->state, h->P.n_w, sp);
   LAUNCHED(h);
   h->last_kind = sch->kind;
@@ -584,8 +611,8 @@ lrdmc_status lrdmc_eval_configs(lrdmc_handle h, int n, const double* x, double* 
   if (n == 0) return LRDMC_OK;
   if (!x || !ratios || !ev) return fail(h, LRDMC_ERR_ARG, "NULL device pointer");
   DeviceGuard g(h->device);
-  const int smem = (int)(h->wpb * h->P.smem_per_warp);
-  k_eval_configs<<<walker_grid(h, n), h->wpb * 32, smem, h->stream>>>(h->S, h->P.L, x, n, h->prm.a,
+  const int smem = smem_bytes(h);
+  k_eval_configs<<<walker_grid(h, n), h->wpb * 32, smem, h->stream>>>(h->S, h->P.L, h->alt, x, n, h->prm.a,
                                                                       h->prm.node_rule, ratios, ev, n_node);
   LAUNCHED(h);
   return LRDMC_OK;
@@ -665,6 +692,24 @@ lrdmc_status lrdmc_reconfigure_indices_noalloc(int n, const double* w, uint32_t 
           cudaSuccess)
     return LRDMC_ERR_CUDA;
   return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_fp64math(int n, const double* x, double* exp_out, double* rcp_out, double* rsqrt_out,
+                            void* stream) {
+  if (n < 0 || (n > 0 && !x)) return LRDMC_ERR_ARG;
+  if (n == 0) return LRDMC_OK;
+  static double* d_tab[64] = {nullptr};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return LRDMC_ERR_CUDA;
+  if (!d_tab[dev]) {
+    double tab[EXP_TAB];
+    for (int j = 0; j < EXP_TAB; ++j) tab[j] = (double)exp2l((long double)j / EXP_TAB);
+    if (cudaMalloc(&d_tab[dev], sizeof tab) != cudaSuccess) return LRDMC_ERR_CUDA;
+    if (cudaMemcpy(d_tab[dev], tab, sizeof tab, cudaMemcpyHostToDevice) != cudaSuccess) return LRDMC_ERR_CUDA;
+  }
+  k_fp64math<<<std::min(1024, (n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(n, x, exp_out, rcp_out, rsqrt_out,
+                                                                                d_tab[dev]);
+  return cudaGetLastError() == cudaSuccess ? LRDMC_OK : LRDMC_ERR_CUDA;
 }
 
 lrdmc_status lrdmc_launch_count(lrdmc_handle h, int64_t* n) {

@@ -1,0 +1,42 @@
+"""The library's reduced-slot FP64 functions against CUDA's own exp, 1/x and
+rsqrt (computed by PyTorch on the same GPU): a few ulp over wide ranges."""
+import ctypes
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def test_fp64math_against_cuda():
+    import torch
+    from gpu_helpers import lib_or_skip
+    P = lib_or_skip()
+    lib = P.load_library()
+    f = lib.lrdmc_fp64math
+    f.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    rng = np.random.default_rng(0)
+    n = 1 << 20
+    xe = np.concatenate([rng.uniform(-700, 700, n // 2), rng.uniform(-5, 5, n // 2)])
+    xp = np.exp(rng.uniform(np.log(1e-30), np.log(1e30), n))
+    for x, which in ((xe, "exp"), (xp, "pos")):
+        xt = torch.tensor(x, device="cuda")
+        e = torch.empty_like(xt)
+        r = torch.empty_like(xt)
+        q = torch.empty_like(xt)
+        s = torch.cuda.current_stream().cuda_stream
+        assert f(n, xt.data_ptr(), e.data_ptr(), r.data_ptr(), q.data_ptr(), s) == 0
+        torch.cuda.synchronize()
+        if which == "exp":
+            ref = torch.exp(xt)
+            rel = ((e - ref).abs() / ref).max().item()
+            assert rel < 8e-16, rel
+            edge = torch.tensor([-701.0, -1e4, 0.0], dtype=torch.float64, device="cuda")
+            assert f(3, edge.data_ptr(), e.data_ptr(), None, None, s) == 0
+            torch.cuda.synchronize()
+            assert e[0].item() == 0.0 and e[1].item() == 0.0 and e[2].item() == 1.0
+        else:
+            rel_r = ((r - 1.0 / xt).abs() * xt).max().item()
+            rel_q = ((q - torch.rsqrt(xt)).abs() / torch.rsqrt(xt)).max().item()
+            assert rel_r < 4e-16 and rel_q < 6e-16, (rel_r, rel_q)
