@@ -118,7 +118,10 @@ typedef struct {
  *                accepted hops of a walker (Sherman-Morrison in between)
  *   p_gbar       length p of the global population factor (Sec. II.A)
  *   n_equil      branchings discarded by lrdmc_energy
- *   precision    0 = FP64 throughout (the only value accepted so far)          */
+ *   precision    0 = FP64 throughout; 1 = mixed: FP32 evaluation of every hop
+ *                ratio (as r - 1), Jastrow, basis, Sherman-Morrison and caches,
+ *                FP64 positions, weights, b_bar / W / e_L accumulators and
+ *                Gauss-Jordan re-inversion every reinv_period hops            */
 typedef struct {
     double a;
     int n_w;
@@ -193,6 +196,16 @@ lrdmc_status lrdmc_get_walkers(lrdmc_handle h, double* x, double* w, double* ev,
 lrdmc_status lrdmc_set_walkers(lrdmc_handle h, const double* x, const double* w);
 
 lrdmc_status lrdmc_clear_status(lrdmc_handle h);
+
+/* Checkpoint / resume (the paper is silent; library facility).  lrdmc_save
+ * writes the complete walker state, E_0, the interval counter and the branching
+ * history to a file (synchronises); lrdmc_load restores them into a handle
+ * created for the same system, trial function and parameters.  Because every
+ * random number is keyed by (seed, walker slot, step, interval), a run resumed
+ * from a checkpoint continues bit for bit like the uninterrupted run.
+ * Returns LRDMC_ERR_ARG if the file does not match the handle's layout. */
+lrdmc_status lrdmc_save(lrdmc_handle h, const char* path);
+lrdmc_status lrdmc_load(lrdmc_handle h, const char* path);
 
 /* Evaluate the lattice-regularised FN Hamiltonian at n <= n_w arbitrary
  * configurations (Appendix D), each from a freshly inverted Slater matrix.

@@ -79,6 +79,8 @@ def load_library():
         "lrdmc_eval_configs": [P, C.c_int, P, P, P, P],
         "lrdmc_reconfigure_indices": [C.c_int, P, C.c_uint32, P, P, C.c_size_t, P, P],
         "lrdmc_launch_count": [P, C.POINTER(C.c_int64)],
+        "lrdmc_save": [P, C.c_char_p],
+        "lrdmc_load": [P, C.c_char_p],
         "lrdmc_stream": [P, C.POINTER(P)],
     }
     for name, args in sigs.items():
@@ -115,7 +117,7 @@ class Lrdmc:
     shell_nprim, exps, coefs, C, j2_anti, j2_par, j2_b, j1_A, j1_B)."""
 
     def __init__(self, system, x0, a, seed=1, node_rule=0, reinv_period=100, p_gbar=10,
-                 n_equil=0, device=None, stream=None):
+                 n_equil=0, device=None, stream=None, precision=0):
         import torch
         self._torch = torch
         lib = load_library()
@@ -142,7 +144,7 @@ class Lrdmc:
                             float(system.j2_anti), float(system.j2_par), float(system.j2_b), d(system.j1_A),
                             d(system.j1_B))
         self._prm = _Params(float(a), self.n_w, int(seed) & (2**64 - 1), int(node_rule), int(reinv_period),
-                            int(p_gbar), int(n_equil), 0)
+                            int(p_gbar), int(n_equil), int(precision))
         nbytes = C.c_size_t(0)
         self._check(lib.lrdmc_workspace_bytes(C.byref(self._sys), C.byref(self._wf), C.byref(self._prm),
                                               C.byref(nbytes)), None)
@@ -245,6 +247,12 @@ class Lrdmc:
         nn = torch.empty((n,), dtype=torch.int32, device=x.device)
         self._check(self.lib.lrdmc_eval_configs(self._h, n, _tptr(x), _tptr(ratios), _tptr(ev), _tptr(nn)))
         return ratios, ev, nn
+
+    def save(self, path):
+        self._check(self.lib.lrdmc_save(self._h, os.fsencode(path)))
+
+    def load(self, path):
+        self._check(self.lib.lrdmc_load(self._h, os.fsencode(path)))
 
     def launch_count(self):
         v = C.c_int64()

@@ -14,6 +14,7 @@
 #include "branch.cuh"
 #include "common.cuh"
 #include "walker.cuh"
+#include "walker_mixed.cuh"
 
 using namespace lrdmc;
 
@@ -29,6 +30,8 @@ struct Plan {
   int n_nuc = 0, n_shell = 0, n_prim = 0, n_bf = 0, n_orb = 0, n_up = 0, n_dn = 0, n_e = 0, n_max = 0;
   int n_w = 0;
   Layout L{};
+  LayoutM M{};
+  int precision = 0;
   size_t smem_per_warp = 0;
   // workspace offsets (bytes)
   size_t o_sys = 0, sys_bytes = 0, o_state = 0, o_alt = 0, state_bytes = 0, o_stats = 0, o_q = 0,
@@ -49,7 +52,8 @@ bool make_plan(const lrdmc_system* sys, const lrdmc_trial_wf* wf, const lrdmc_pa
       prm->node_rule < -1 || prm->node_rule > 2 || prm->p_gbar < 0 || prm->n_equil < 0) {
     P.err = "bad run parameters"; return false;
   }
-  if (prm->precision != 0) { P.err = "only precision 0 (FP64) is available"; return false; }
+  if (prm->precision != 0 && prm->precision != 1) { P.err = "precision must be 0 (FP64) or 1 (mixed)"; return false; }
+  P.precision = prm->precision;
   P.n_nuc = sys->n_nuc;
   P.n_up = sys->n_up;
   P.n_dn = sys->n_dn;
@@ -98,7 +102,8 @@ bool make_plan(const lrdmc_system* sys, const lrdmc_trial_wf* wf, const lrdmc_pa
   L.s_row = L.s_u + P.n_max;
   L.s_sc = L.s_row + P.n_max;
   L.s_stride = round_up(L.s_sc + SC_COUNT, 4);
-  P.smem_per_warp = (size_t)L.s_stride * sizeof(double);
+  P.M = layout_mixed(L, P.n_nuc, P.n_prim);
+  P.smem_per_warp = P.precision == 0 ? (size_t)L.s_stride * sizeof(double) : (size_t)P.M.stride * sizeof(float);
   if (P.smem_per_warp + EXP_TAB * sizeof(double) > 200 * 1024) { P.err = "system too large for the per-warp shared-memory layout"; return false; }
   // system image
   size_t o = 0;
@@ -243,7 +248,7 @@ static lrdmc_status cuda_fail(lrdmc_handle h, const char* what, cudaError_t e) {
   } while (0)
 
 static int smem_bytes(lrdmc_handle h) {
-  return (int)(EXP_TAB * sizeof(double) + h->wpb * h->P.smem_per_warp);
+  return (int)((h->P.precision == 0 ? EXP_TAB * sizeof(double) : 0) + h->wpb * h->P.smem_per_warp);
 }
 
 static lrdmc_status set_kernel_smem(lrdmc_handle h) {
@@ -251,6 +256,9 @@ static lrdmc_status set_kernel_smem(lrdmc_handle h) {
   CK(h, cudaFuncSetAttribute(k_propagate, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
   CK(h, cudaFuncSetAttribute(k_init_walkers, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
   CK(h, cudaFuncSetAttribute(k_eval_configs, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  CK(h, cudaFuncSetAttribute(k_propagate_m, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  CK(h, cudaFuncSetAttribute(k_init_walkers_m, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  CK(h, cudaFuncSetAttribute(k_eval_configs_m, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
   return LRDMC_OK;
 }
 
@@ -271,8 +279,12 @@ static lrdmc_status place_walkers(lrdmc_handle h, const double* x, const double*
     CK(h, cudaMemcpyAsync(dw, w, sizeof(double) * P.n_w, cudaMemcpyHostToDevice, h->stream));
   }
   const int smem = smem_bytes(h);
-  k_init_walkers<<<walker_grid(h, P.n_w), h->wpb * 32, smem, h->stream>>>(h->S, P.L, h->state, dx, dw, P.n_w,
-                                                                          h->prm.a, h->prm.node_rule);
+  if (P.precision == 0)
+    k_init_walkers<<<walker_grid(h, P.n_w), h->wpb * 32, smem, h->stream>>>(h->S, P.L, h->state, dx, dw, P.n_w,
+                                                                            h->prm.a, h->prm.node_rule);
+  else
+    k_init_walkers_m<<<walker_grid(h, P.n_w), h->wpb * 32, smem, h->stream>>>(h->S, P.L, P.M, h->state, dx, dw,
+                                                                              P.n_w, h->prm.a, h->prm.node_rule);
   LAUNCHED(h);
   CK(h, cudaStreamSynchronize(h->stream));
   return LRDMC_OK;
@@ -447,7 +459,10 @@ lrdmc_status lrdmc_create(const lrdmc_system* sys, const lrdmc_trial_wf* wf, con
   lrdmc_status st = set_kernel_smem(h);
   if (st != LRDMC_OK) return st;
   int bps = 0;
-  CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_propagate, h->wpb * 32, smem_bytes(h)));
+  if (P.precision == 0)
+    CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_propagate, h->wpb * 32, smem_bytes(h)));
+  else
+    CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_propagate_m, h->wpb * 32, smem_bytes(h)));
   if (bps < 1) return fail(h, LRDMC_ERR_UNSUPPORTED, "propagate kernel does not fit on an SM");
   h->grid = bps * h->num_sms;
   st = place_walkers(h, x0, nullptr);
@@ -494,7 +509,11 @@ lrdmc_status lrdmc_propagate(lrdmc_handle h, const lrdmc_schedule* sch) {
   sp.node_rule = h->prm.node_rule;
   sp.reinv_period = h->prm.reinv_period;
   const int smem = smem_bytes(h);
-  k_propagate<<<walker_grid(h, h->P.n_w), h->wpb * 32, smem, h->stream>>>(h->S, h->P.L, h->state, h->P.n_w, sp);
+  if (h->P.precision == 0)
+    k_propagate<<<walker_grid(h, h->P.n_w), h->wpb * 32, smem, h->stream>>>(h->S, h->P.L, h->state, h->P.n_w, sp);
+  else
+    k_propagate_m<<<walker_grid(h, h->P.n_w), h->wpb * 32, smem, h->stream>>>(h->S, h->P.L, h->P.M, h->state,
+                                                                              h->P.n_w, sp);
   LAUNCHED(h);
   h->last_kind = sch->kind;
   return LRDMC_OK;
@@ -605,6 +624,81 @@ lrdmc_status lrdmc_clear_status(lrdmc_handle h) {
   return LRDMC_OK;
 }
 
+namespace {
+constexpr uint64_t CKPT_MAGIC = 0x4c52444d43434b31ull;   // "LRDMCCK1"
+
+struct CkptHeader {
+  uint64_t magic;
+  int32_t n_w, n_e, g_stride, precision, n_hist, pad;
+  uint64_t seed;
+  double a, E0;
+  uint32_t interval, last_kind;
+};
+}  // namespace
+
+lrdmc_status lrdmc_save(lrdmc_handle h, const char* path) {
+  if (!h || !h->state || !path) return LRDMC_ERR_ARG;
+  DeviceGuard g(h->device);
+  const Plan& P = h->P;
+  std::vector<double> st((size_t)P.n_w * P.L.g_stride);
+  CK(h, cudaMemcpyAsync(st.data(), h->state, sizeof(double) * st.size(), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  CkptHeader hd{};
+  hd.magic = CKPT_MAGIC;
+  hd.n_w = P.n_w; hd.n_e = P.n_e; hd.g_stride = P.L.g_stride; hd.precision = P.precision;
+  hd.n_hist = (int32_t)h->wbar.size();
+  hd.seed = h->prm.seed; hd.a = h->prm.a; hd.E0 = h->E0; hd.interval = h->interval; hd.last_kind = h->last_kind;
+  FILE* f = fopen(path, "wb");
+  if (!f) return fail(h, LRDMC_ERR_ARG, std::string("cannot open ") + path);
+  bool ok = fwrite(&hd, sizeof hd, 1, f) == 1 && fwrite(st.data(), sizeof(double), st.size(), f) == st.size();
+  const size_t m = h->wbar.size();
+  if (m) {
+    ok = ok && fwrite(h->wbar.data(), sizeof(double), m, f) == m && fwrite(h->ebar.data(), sizeof(double), m, f) == m &&
+         fwrite(h->e0h.data(), sizeof(double), m, f) == m && fwrite(h->mmean.data(), sizeof(double), m, f) == m &&
+         fwrite(h->mmax.data(), sizeof(int), m, f) == m && fwrite(h->surv.data(), sizeof(int), m, f) == m &&
+         fwrite(h->stor.data(), sizeof(uint32_t), m, f) == m;
+  }
+  ok = (fclose(f) == 0) && ok;
+  return ok ? LRDMC_OK : fail(h, LRDMC_ERR_ARG, "checkpoint write failed");
+}
+
+lrdmc_status lrdmc_load(lrdmc_handle h, const char* path) {
+  if (!h || !h->state || !path) return LRDMC_ERR_ARG;
+  DeviceGuard g(h->device);
+  const Plan& P = h->P;
+  FILE* f = fopen(path, "rb");
+  if (!f) return fail(h, LRDMC_ERR_ARG, std::string("cannot open ") + path);
+  CkptHeader hd{};
+  bool ok = fread(&hd, sizeof hd, 1, f) == 1;
+  if (!ok || hd.magic != CKPT_MAGIC || hd.n_w != P.n_w || hd.n_e != P.n_e || hd.g_stride != P.L.g_stride ||
+      hd.precision != P.precision || hd.n_hist < 0) {
+    fclose(f);
+    return fail(h, LRDMC_ERR_ARG, "checkpoint does not match this handle");
+  }
+  std::vector<double> st((size_t)P.n_w * P.L.g_stride);
+  ok = fread(st.data(), sizeof(double), st.size(), f) == st.size();
+  const size_t m = (size_t)hd.n_hist;
+  std::vector<double> wb(m), eb(m), e0(m), mm(m);
+  std::vector<int> mx(m), sv(m);
+  std::vector<uint32_t> so(m);
+  if (m) {
+    ok = ok && fread(wb.data(), sizeof(double), m, f) == m && fread(eb.data(), sizeof(double), m, f) == m &&
+         fread(e0.data(), sizeof(double), m, f) == m && fread(mm.data(), sizeof(double), m, f) == m &&
+         fread(mx.data(), sizeof(int), m, f) == m && fread(sv.data(), sizeof(int), m, f) == m &&
+         fread(so.data(), sizeof(uint32_t), m, f) == m;
+  }
+  fclose(f);
+  if (!ok) return fail(h, LRDMC_ERR_ARG, "checkpoint truncated");
+  CK(h, cudaMemcpyAsync(h->state, st.data(), sizeof(double) * st.size(), cudaMemcpyHostToDevice, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  h->prm.seed = hd.seed;
+  h->E0 = hd.E0;
+  h->interval = hd.interval;
+  h->last_kind = (int)hd.last_kind;
+  h->wbar = wb; h->ebar = eb; h->e0h = e0; h->mmean = mm; h->mmax = mx; h->surv = sv; h->stor = so;
+  return LRDMC_OK;
+}
+
 lrdmc_status lrdmc_eval_configs(lrdmc_handle h, int n, const double* x, double* ratios, double* ev, int32_t* n_node) {
   if (!h || !h->state) return LRDMC_ERR_ARG;
   if (n < 0 || n > h->P.n_w) return fail(h, LRDMC_ERR_ARG, "n must be in [0, n_w]");
@@ -612,8 +706,13 @@ lrdmc_status lrdmc_eval_configs(lrdmc_handle h, int n, const double* x, double* 
   if (!x || !ratios || !ev) return fail(h, LRDMC_ERR_ARG, "NULL device pointer");
   DeviceGuard g(h->device);
   const int smem = smem_bytes(h);
-  k_eval_configs<<<walker_grid(h, n), h->wpb * 32, smem, h->stream>>>(h->S, h->P.L, h->alt, x, n, h->prm.a,
-                                                                      h->prm.node_rule, ratios, ev, n_node);
+  if (h->P.precision == 0)
+    k_eval_configs<<<walker_grid(h, n), h->wpb * 32, smem, h->stream>>>(h->S, h->P.L, h->alt, x, n, h->prm.a,
+                                                                        h->prm.node_rule, ratios, ev, n_node);
+  else
+    k_eval_configs_m<<<walker_grid(h, n), h->wpb * 32, smem, h->stream>>>(h->S, h->P.L, h->P.M, h->alt, x, n,
+                                                                          h->prm.a, h->prm.node_rule, ratios, ev,
+                                                                          n_node);
   LAUNCHED(h);
   return LRDMC_OK;
 }

@@ -258,3 +258,34 @@ def test_full_size_sampled_walkers():
     assert np.all(g["moves"] == 20)
     hop = np.abs(g["x"] - x0) / 0.2
     assert np.all(np.abs(hop - np.round(hop)) < 1e-9)       # walkers stay on their lattices
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_checkpoint_resume_is_bit_identical(tmp_path, precision):
+    P = lib_or_skip()
+    s = W.h2_sto3g()
+    x0 = W.initial_walkers(s, 64, seed=5)
+    a = P.Lrdmc(s, x0, 0.2, seed=3, precision=precision)
+    for _ in range(3):
+        a.propagate(P.LOAD_BALANCED, n_proj=6)
+        a.branch()
+    path = str(tmp_path / "ck.bin")
+    a.save(path)
+    for _ in range(3):
+        a.propagate(P.CONVENTIONAL, tau=0.05, max_moves=500)
+        a.branch()
+    b = P.Lrdmc(s, W.initial_walkers(s, 64, seed=99), 0.2, seed=3, precision=precision)
+    b.load(path)
+    for _ in range(3):
+        b.propagate(P.CONVENTIONAL, tau=0.05, max_moves=500)
+        b.branch()
+    ga, gb = a.get_walkers(), b.get_walkers()
+    for k in ("x", "w", "ev", "ratios", "status", "moves"):
+        np.testing.assert_array_equal(ga[k], gb[k])
+    ha, hb = a.history(), b.history()
+    for k in ha:
+        np.testing.assert_array_equal(ha[k], hb[k])
+    assert a.energy() == b.energy() or (np.isnan(a.energy()[1]) and a.energy()[0] == b.energy()[0])
+    with pytest.raises(P.LrdmcError):
+        c = P.Lrdmc(W.water_methane(), W.initial_walkers(W.water_methane(), 64), 0.2)
+        c.load(path)

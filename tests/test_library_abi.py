@@ -81,7 +81,7 @@ def test_workspace_sizing_and_validation(lib):
     assert lib.lrdmc_workspace_bytes(ctypes.byref(s), ctypes.byref(w), ctypes.byref(p), ctypes.byref(nb)) == 0
     # two walker buffers dominate: ~2 * 4096 * (walker block) bytes
     assert 2 * 4096 * 8 * (48 + 128 + 640 + 96) < nb.value < 2 * 4096 * 8 * 2000
-    for bad in (dict(a=-1.0), dict(node_rule=5), dict(reinv_period=0), dict(precision=1)):
+    for bad in (dict(a=-1.0), dict(node_rule=5), dict(reinv_period=0), dict(precision=2)):
         s, w, p, keep = _structs(W.h2_sto3g(), **bad)
         assert lib.lrdmc_workspace_bytes(ctypes.byref(s), ctypes.byref(w), ctypes.byref(p),
                                          ctypes.byref(nb)) == 1
