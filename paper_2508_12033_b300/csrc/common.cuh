@@ -51,6 +51,15 @@ struct DevSys {
   const double* exps;    // n_prim
   const double* coefs;   // n_prim
   const double* C;       // n_orb x n_bf
+  // FP32 copies for the mixed-precision kernels (no per-use conversion)
+  const float* Rf;
+  const float* Zf;
+  const float* rcf;
+  const float* j1Af;
+  const float* j1Bf;
+  const float* expsf;
+  const float* coefsf;
+  const float* Cf;
   double j2_anti, j2_par, j2_b;
   double v_ii;           // nucleus-nucleus repulsion
 };

@@ -38,7 +38,7 @@ struct Plan {
          o_src = 0, o_dstat = 0, total = 0;
   // system image offsets (bytes, inside the sys block)
   size_t i_R, i_Z, i_rc, i_j1A, i_j1B, i_exps, i_coefs, i_C, i_kind, i_atom, i_l, i_nprim, i_off, i_bf, i_ash,
-      i_tab;
+      i_tab, i_f_R, i_f_Z, i_f_rc, i_f_j1A, i_f_j1B, i_f_exps, i_f_coefs, i_f_C;
   std::string err;
 };
 
@@ -124,6 +124,14 @@ bool make_plan(const lrdmc_system* sys, const lrdmc_trial_wf* wf, const lrdmc_pa
   P.i_bf = take(sizeof(int) * P.n_shell);
   P.i_ash = take(sizeof(int) * (P.n_nuc + 1));
   P.i_tab = take(sizeof(double) * EXP_TAB);
+  P.i_f_R = take(sizeof(float) * 3 * P.n_nuc);
+  P.i_f_Z = take(sizeof(float) * P.n_nuc);
+  P.i_f_rc = take(sizeof(float) * P.n_nuc);
+  P.i_f_j1A = take(sizeof(float) * P.n_nuc);
+  P.i_f_j1B = take(sizeof(float) * P.n_nuc);
+  P.i_f_exps = take(sizeof(float) * P.n_prim);
+  P.i_f_coefs = take(sizeof(float) * P.n_prim);
+  P.i_f_C = take(sizeof(float) * (size_t)P.n_orb * P.n_bf);
   P.sys_bytes = o;
   // workspace
   size_t w = 0;
@@ -248,7 +256,7 @@ static lrdmc_status cuda_fail(lrdmc_handle h, const char* what, cudaError_t e) {
   } while (0)
 
 static int smem_bytes(lrdmc_handle h) {
-  return (int)((h->P.precision == 0 ? EXP_TAB * sizeof(double) : 0) + h->wpb * h->P.smem_per_warp);
+  return (int)(EXP_TAB * sizeof(double) + h->wpb * h->P.smem_per_warp);
 }
 
 static lrdmc_status set_kernel_smem(lrdmc_handle h) {
@@ -410,6 +418,20 @@ lrdmc_status lrdmc_create(const lrdmc_system* sys, const lrdmc_trial_wf* wf, con
   double tab[EXP_TAB];
   for (int j = 0; j < EXP_TAB; ++j) tab[j] = (double)exp2l((long double)j / EXP_TAB);
   putd(P.i_tab, tab, EXP_TAB);
+  auto putf = [&](size_t off, const double* src, size_t n) {
+    for (size_t k = 0; k < n; ++k) {
+      const float v = (float)src[k];
+      memcpy(img.data() + off + k * sizeof(float), &v, sizeof(float));
+    }
+  };
+  putf(P.i_f_R, sys->R, 3 * (size_t)P.n_nuc);
+  putf(P.i_f_Z, sys->Z, P.n_nuc);
+  putf(P.i_f_rc, sys->r_c, P.n_nuc);
+  putf(P.i_f_j1A, wf->j1_A, P.n_nuc);
+  putf(P.i_f_j1B, wf->j1_B, P.n_nuc);
+  putf(P.i_f_exps, wf->exps, P.n_prim);
+  putf(P.i_f_coefs, wf->coefs, P.n_prim);
+  putf(P.i_f_C, wf->C, (size_t)P.n_orb * P.n_bf);
   char* dsys = base + P.o_sys;
   CK(h, cudaMemcpyAsync(dsys, img.data(), P.sys_bytes, cudaMemcpyHostToDevice, h->stream));
   DevSys& S = h->S;
@@ -431,6 +453,14 @@ lrdmc_status lrdmc_create(const lrdmc_system* sys, const lrdmc_trial_wf* wf, con
   S.sh_bf = (const int*)(dsys + P.i_bf);
   S.atom_sh = (const int*)(dsys + P.i_ash);
   S.exptab = (const double*)(dsys + P.i_tab);
+  S.Rf = (const float*)(dsys + P.i_f_R);
+  S.Zf = (const float*)(dsys + P.i_f_Z);
+  S.rcf = (const float*)(dsys + P.i_f_rc);
+  S.j1Af = (const float*)(dsys + P.i_f_j1A);
+  S.j1Bf = (const float*)(dsys + P.i_f_j1B);
+  S.expsf = (const float*)(dsys + P.i_f_exps);
+  S.coefsf = (const float*)(dsys + P.i_f_coefs);
+  S.Cf = (const float*)(dsys + P.i_f_C);
   S.j2_anti = wf->j2_anti;
   S.j2_par = wf->j2_par;
   S.j2_b = wf->j2_b;

@@ -1,20 +1,30 @@
-// Mixed-precision (FP32 evaluation, FP64 accumulation) warp-per-walker kernels.
+// Mixed-precision warp-per-walker kernels: FP32 hop evaluation, FP64 where
+// conditioning demands it.
 //
 // Same method and walker layout as walker.cuh; what changes is where each
 // quantity lives:
-//   FP64  positions (lattice hops stay exact), weights, the b_bar / V_sf / W /
-//         e_L accumulators, potentials as stored, Gauss-Jordan re-inversion;
-//   FP32  B^T (Sherman-Morrison updates), g_i, orbital cache, every hop ratio,
-//         Jastrow and basis values.
-// Every hop ratio is produced directly as r - 1 ("delta form"), so that the
+//   FP64  positions (lattice hops stay exact), the orbital values phi_k(r_i)
+//         (rows of A), B = A^{-1} with its Sherman-Morrison updates and the
+//         Gauss-Jordan re-inversion, the determinant derivatives grad/lap D/D,
+//         weights and the b_bar / V_sf / W / e_L accumulators.  Near a node A
+//         is ill-conditioned and an FP32 A or B would carry cond(A) * 1e-7
+//         relative errors into every ratio; in FP64 they stay negligible.
+//   FP32  every hop ratio (6 N_e per step, the bulk of the work): basis and
+//         Jastrow values, g_i = C^T B[:, i] (from B rounded to FP32), the
+//         orbital gradient/Laplacian cache, potentials, heat-bath sums.
+// Each hop ratio is produced directly as r - 1 ("delta form") so that the
 // kinetic sums of Appendix D never subtract two O(3 N_e / a^2) numbers in FP32:
 //   * determinant: chi(r_i) . g_i = 1 exactly, so det - 1 = sum_mu
-//     [chi_mu(r') - chi_mu(r_i)] g_mu, with every Gaussian difference formed as
+//     [chi_mu(r') - chi_mu(r_i)] g_mu, every Gaussian difference formed as
 //     h (exp(-alpha delta) - 1), delta = |r'-R|^2 - |r_i-R|^2 = 2 (+-a) d_axis + a^2;
 //   * Jastrow: u(r') - u(r) = c delta t t' / (r' + r), t = 1/(1 + b r),
-//     delta = 2 (+-a) (r_i - r_j)_axis + a^2, and exp(dJ) - 1 by expm1f;
-//   * r - 1 = D + J + D J.
-// The walker block's B^T and cache regions hold floats (first half of each).
+//     delta = 2 (+-a) (r_i - r_j)_axis + a^2;
+//   * r - 1 = D + J + D J with J = exp(dJ) - 1.
+// exp(x) - 1 in FP32: Taylor polynomial of degree 6 for |x| < 1/4 (truncation
+// < 2e-8 relative), exp(x) - 1 from the hardware exponential otherwise.
+// Walker block: B^T as doubles (as in the FP64 layout); the cache region holds
+// the FP64 orbital values [n_e][n_max] followed by FP32 gradient/Laplacian
+// rows [n_e][4][n_max].
 #pragma once
 
 #include "common.cuh"
@@ -22,42 +32,64 @@
 
 namespace lrdmc {
 
-// Shared-memory layout of one warp for the mixed kernels (offsets in floats;
-// the double arrays x and sc sit at even offsets).
+// Shared-memory layout of one warp for the mixed kernels, in floats (double
+// arrays at even offsets).  Per-electron float rows are padded by one word so
+// that lanes working on different electrons hit different banks.
 struct LayoutM {
-  int x, xf, bt, g, dl, ej, ep, dd, geo, rt1, pair, hcur, chi5, phi5, f, row, grow, sc, stride;
+  int sc, x, bt, dd, phiv, chiv, u, row;                 // doubles
+  int xf, gf, dl, ej, ep, geo, rt1, pair, hcur, chi5, phi5, bf32;  // floats
+  int geo_st, rt1_st, pair_st, hcur_st, stride;
 };
 
 __host__ __device__ inline LayoutM layout_mixed(const Layout& L, int n_nuc, int n_prim) {
   LayoutM M;
-  const int ne = L.n_e, nbt = L.n_up * L.n_up + L.n_dn * L.n_dn;
+  const int ne = L.n_e, nbt = L.n_up * L.n_up + L.n_dn * L.n_dn, nm = L.n_max, nbf = L.n_bf;
   int o = 0;
-  M.sc = o; o += 2 * SC_COUNT;                         // doubles
-  M.x = o; o += 2 * 3 * ne;                            // doubles
+  M.sc = o; o += 2 * SC_COUNT;
+  M.x = o; o += 2 * 3 * ne;
+  M.bt = o; o += 2 * nbt;
+  M.dd = o; o += 2 * 4 * ne;
+  M.phiv = o; o += 2 * nm;
+  M.chiv = o; o += 2 * nbf;
+  M.u = o; o += 2 * nm;
+  M.row = o; o += 2 * nm;
   M.xf = o; o += 3 * ne;
-  M.bt = o; o += nbt;
   o = round_up(o, 2);
-  const int gsz = ne * L.n_bf > 4 * L.n_max * L.n_max ? ne * L.n_bf : 4 * L.n_max * L.n_max;
-  M.g = o; o += gsz;                                   // also FP64 Gauss-Jordan scratch
+  M.gf = o; o += ne * nbf > 4 * nm * nm ? ne * nbf : 4 * nm * nm;   // also FP64 Gauss-Jordan scratch
   M.dl = o; o += 6 * ne;
   M.ej = o; o += 5 * ne;
   M.ep = o; o += 2 * ne;
-  M.dd = o; o += 4 * ne;
-  M.geo = o; o += 4 * ne * n_nuc;
-  M.rt1 = o; o += 2 * ne * n_nuc;
-  M.pair = o; o += 3 * ne * ne;
-  M.hcur = o; o += ne * n_prim;
-  M.chi5 = o; o += 5 * L.n_bf;
-  M.phi5 = o; o += 5 * L.n_max;
-  M.f = o; o += L.n_max;
-  M.row = o; o += L.n_max;
-  M.grow = o; o += L.n_bf;
+  M.geo_st = 4 * n_nuc + 1;
+  M.geo = o; o += ne * M.geo_st;
+  M.rt1_st = 2 * n_nuc + 1;
+  M.rt1 = o; o += ne * M.rt1_st;
+  M.pair_st = 3 * ne + 1;
+  M.pair = o; o += ne * M.pair_st;
+  M.hcur_st = n_prim + 1;
+  M.hcur = o; o += ne * M.hcur_st;
+  M.chi5 = o; o += 5 * nbf > nbt ? 5 * nbf : nbt;      // also the FP32 copy of B^T
+  M.phi5 = o; o += 5 * nm;
+  M.bf32 = M.chi5;
   M.stride = round_up(o, 4);
   return M;
 }
 
-__device__ __forceinline__ float* bt_f(const Layout& L, double* gblk) { return (float*)(gblk + L.g_bt); }
-__device__ __forceinline__ float* cache_f(const Layout& L, double* gblk) { return (float*)(gblk + L.g_cache); }
+__device__ __forceinline__ double* cache_val(const Layout& L, double* gblk) { return gblk + L.g_cache; }
+__device__ __forceinline__ float* cache_der(const Layout& L, double* gblk) {
+  return (float*)(gblk + L.g_cache + L.n_e * L.n_max);
+}
+
+// exp(x) - 1 in FP32 (see the header comment).
+__device__ __forceinline__ float expm1_fast(float x) {
+  float p = fmaf(x, 1.f / 720.f, 1.f / 120.f);
+  p = fmaf(x, p, 1.f / 24.f);
+  p = fmaf(x, p, 1.f / 6.f);
+  p = fmaf(x, p, 0.5f);
+  p = fmaf(x, p, 1.f);
+  const float small = x * p;
+  const float big = __expf(x) - 1.f;
+  return fabsf(x) < 0.25f ? small : big;
+}
 
 // FP32 value/gradient/Laplacian of shell s at offset d (r2 = |d|^2).
 __device__ __forceinline__ void shell_derivs_f(const DevSys& S, int s, const float d[3], float r2,
@@ -67,8 +99,8 @@ __device__ __forceinline__ void shell_derivs_f(const DevSys& S, int s, const flo
     const float ir = rsqrtf(r2), r = r2 * ir;
     float v = 0.f, dr = 0.f, lp = 0.f;
     for (int q = 0; q < np; ++q) {
-      const float z = (float)__ldg(S.exps + off + q);
-      const float h = (float)__ldg(S.coefs + off + q) * __expf(-z * r);
+      const float z = __ldg(S.expsf + off + q);
+      const float h = __ldg(S.coefsf + off + q) * __expf(-z * r);
       v += h;
       dr -= z * h;
       lp += (z * z - 2.f * z * ir) * h;
@@ -79,8 +111,8 @@ __device__ __forceinline__ void shell_derivs_f(const DevSys& S, int s, const flo
   } else if (l == 0) {
     float v = 0.f, gs = 0.f, lp = 0.f;
     for (int q = 0; q < np; ++q) {
-      const float al = (float)__ldg(S.exps + off + q);
-      const float h = (float)__ldg(S.coefs + off + q) * __expf(-al * r2);
+      const float al = __ldg(S.expsf + off + q);
+      const float h = __ldg(S.coefsf + off + q) * __expf(-al * r2);
       v += h;
       gs -= 2.f * al * h;
       lp += (4.f * al * al * r2 - 6.f * al) * h;
@@ -91,8 +123,8 @@ __device__ __forceinline__ void shell_derivs_f(const DevSys& S, int s, const flo
   } else {
     float s0 = 0.f, s1 = 0.f, s2 = 0.f;
     for (int q = 0; q < np; ++q) {
-      const float al = (float)__ldg(S.exps + off + q);
-      const float h = (float)__ldg(S.coefs + off + q) * __expf(-al * r2);
+      const float al = __ldg(S.expsf + off + q);
+      const float h = __ldg(S.coefsf + off + q) * __expf(-al * r2);
       s0 += h;
       s1 -= 2.f * al * h;
       s2 += (4.f * al * al * r2 - 10.f * al) * h;
@@ -105,22 +137,54 @@ __device__ __forceinline__ void shell_derivs_f(const DevSys& S, int s, const flo
   }
 }
 
-__device__ void orbital_derivs_f(const DevSys& S, const Layout& L, const float q[3], int n_sig, float* chi5,
-                                 float* phi5, int lane) {
+// FP64 values of the functions of shell s (for the rows of A).
+__device__ __forceinline__ void shell_values_d(const DevSys& S, int s, const double d[3], double r2,
+                                               double* __restrict__ out, const double* T) {
+  const int l = __ldg(S.sh_l + s), np = __ldg(S.sh_nprim + s), off = __ldg(S.sh_off + s), bf = __ldg(S.sh_bf + s);
+  const double arg = l == -1 ? r2 * rsqrt_nr(r2) : r2;
+  double rad = 0.0;
+  for (int q = 0; q < np; ++q) rad = fma(__ldg(S.coefs + off + q), exp_tab(-__ldg(S.exps + off + q) * arg, T), rad);
+  if (l == 1) {
+    out[bf] = d[0] * rad;
+    out[bf + 1] = d[1] * rad;
+    out[bf + 2] = d[2] * rad;
+  } else {
+    out[bf] = rad;
+  }
+}
+
+// Orbital rows at one point q: FP64 values phiv[k] and FP32 gradient /
+// Laplacian phi5[(c-1) * n_max + k], c = 1..4, for the first n_sig orbitals.
+__device__ void orbital_rows_m(const DevSys& S, const Layout& L, const LayoutM& M, const double q[3], int n_sig,
+                               float* sm, const double* T, int lane) {
+  double* chiv = (double*)(sm + M.chiv);
+  double* phiv = (double*)(sm + M.phiv);
+  float* chi5 = sm + M.chi5;
+  float* phi5 = sm + M.phi5;
   for (int s = lane; s < S.n_shell; s += WARP) {
     const int atom = __ldg(S.sh_atom + s);
-    const float d[3] = {q[0] - (float)__ldg(S.R + 3 * atom), q[1] - (float)__ldg(S.R + 3 * atom + 1),
-                        q[2] - (float)__ldg(S.R + 3 * atom + 2)};
-    shell_derivs_f(S, s, d, d[0] * d[0] + d[1] * d[1] + d[2] * d[2], chi5, L.n_bf);
+    const double d[3] = {q[0] - __ldg(S.R + 3 * atom), q[1] - __ldg(S.R + 3 * atom + 1),
+                         q[2] - __ldg(S.R + 3 * atom + 2)};
+    const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    shell_values_d(S, s, d, r2, chiv, T);
+    const float df[3] = {(float)d[0], (float)d[1], (float)d[2]};
+    shell_derivs_f(S, s, df, (float)r2, chi5, L.n_bf);
   }
   __syncwarp();
   for (int o = lane; o < 5 * n_sig; o += WARP) {
     const int c = o / n_sig, k = o - c * n_sig;
-    const double* crow = S.C + (size_t)k * L.n_bf;
-    const float* x = chi5 + c * L.n_bf;
-    float acc = 0.f;
-    for (int mu = 0; mu < L.n_bf; ++mu) acc = fmaf((float)__ldg(crow + mu), x[mu], acc);
-    phi5[c * L.n_max + k] = acc;
+    if (c == 0) {
+      const double* crow = S.C + (size_t)k * L.n_bf;
+      double acc = 0.0;
+      for (int mu = 0; mu < L.n_bf; ++mu) acc = fma(__ldg(crow + mu), chiv[mu], acc);
+      phiv[k] = acc;
+    } else {
+      const float* crow = S.Cf + (size_t)k * L.n_bf;
+      const float* x = chi5 + c * L.n_bf;
+      float acc = 0.f;
+      for (int mu = 0; mu < L.n_bf; ++mu) acc = fmaf(__ldg(crow + mu), x[mu], acc);
+      phi5[(c - 1) * L.n_max + k] = acc;
+    }
   }
   __syncwarp();
 }
@@ -130,15 +194,15 @@ __device__ void electron_potentials_f(const DevSys& S, const float q[3], float a
   nu = 0.f;
   nucap = 0.f;
   for (int I = lane; I < S.n_nuc; I += WARP) {
-    const float dx = q[0] - (float)__ldg(S.R + 3 * I), dy = q[1] - (float)__ldg(S.R + 3 * I + 1),
-                dz = q[2] - (float)__ldg(S.R + 3 * I + 2);
+    const float dx = q[0] - __ldg(S.Rf + 3 * I), dy = q[1] - __ldg(S.Rf + 3 * I + 1),
+                dz = q[2] - __ldg(S.Rf + 3 * I + 2);
     const float r = sqrtf(dx * dx + dy * dy + dz * dz);
-    const float Z = (float)__ldg(S.Z + I);
+    const float Z = __ldg(S.Zf + I);
     if (__ldg(S.kind + I) == 0) {
       nu -= Z / r;
       nucap -= Z / fmaxf(r, a);
     } else {
-      const float v = -Z * erff(r / (float)__ldg(S.rc + I)) / r;
+      const float v = -Z * erff(r / __ldg(S.rcf + I)) / r;
       nu += v;
       nucap += v;
     }
@@ -150,12 +214,12 @@ __device__ void electron_potentials_f(const DevSys& S, const float q[3], float a
   }
 }
 
-// FP64 re-inversion of the FP32 orbital values; B^T stored back as floats.
+// FP64 re-inversion of the FP64 orbital values (both spin blocks).
 __device__ bool reinvert_m(const Layout& L, const LayoutM& M, double* gblk, float* sm, int lane) {
   bool sing = false;
-  const float* cache = cache_f(L, gblk);
-  float* bt = sm + M.bt;
-  double* scratch = (double*)(sm + M.g);
+  const double* val = cache_val(L, gblk);
+  double* bt = (double*)(sm + M.bt);
+  double* scratch = (double*)(sm + M.gf);
   for (int blk = 0; blk < 2; ++blk) {
     const int n = blk ? L.n_dn : L.n_up;
     const int e0 = blk ? L.n_up : 0;
@@ -163,51 +227,57 @@ __device__ bool reinvert_m(const Layout& L, const LayoutM& M, double* gblk, floa
     if (n == 0) continue;
     for (int o = lane; o < n * 2 * n; o += WARP) {
       const int r = o / (2 * n), c = o - r * 2 * n;
-      scratch[o] = c < n ? (double)cache[(e0 + r) * 5 * L.n_max + c] : (c - n == r ? 1.0 : 0.0);
+      scratch[o] = c < n ? val[(e0 + r) * L.n_max + c] : (c - n == r ? 1.0 : 0.0);
     }
     __syncwarp();
     sing |= warp_gauss_jordan(scratch, n, lane);
     for (int o = lane; o < n * n; o += WARP) {
       const int i = o / n, k = o - i * n;
-      bt[bto + o] = (float)scratch[k * 2 * n + n + i];
+      bt[bto + o] = scratch[k * 2 * n + n + i];
     }
     __syncwarp();
   }
   return sing;
 }
 
-__device__ void compute_g_m(const DevSys& S, const Layout& L, const LayoutM& M, float* sm, int lane) {
-  const float* bt = sm + M.bt;
-  float* g = sm + M.g;
-  for (int o = lane; o < L.n_e * L.n_bf; o += WARP) {
+// g_i = C^T B[:, i] in FP32 from B rounded to FP32, for electrons [e0, e1).
+__device__ void compute_g_m(const DevSys& S, const Layout& L, const LayoutM& M, float* sm, int e0, int e1,
+                            int lane) {
+  const double* bt = (const double*)(sm + M.bt);
+  float* b32 = sm + M.bf32;
+  float* g = sm + M.gf;
+  const int nbt = L.n_up * L.n_up + L.n_dn * L.n_dn;
+  for (int o = lane; o < nbt; o += WARP) b32[o] = (float)bt[o];
+  __syncwarp();
+  for (int o = lane + e0 * L.n_bf; o < e1 * L.n_bf; o += WARP) {
     const int i = o / L.n_bf, mu = o - i * L.n_bf;
     const SpinRef sr = spin_ref(L, i);
-    const float* brow = bt + sr.bt_off + sr.ii * sr.n;
+    const float* brow = b32 + sr.bt_off + sr.ii * sr.n;
     float acc = 0.f;
-    for (int k = 0; k < sr.n; ++k) acc = fmaf((float)__ldg(S.C + (size_t)k * L.n_bf + mu), brow[k], acc);
+    for (int k = 0; k < sr.n; ++k) acc = fmaf(__ldg(S.Cf + (size_t)k * L.n_bf + mu), brow[k], acc);
     g[o] = acc;
   }
   __syncwarp();
 }
 
 // Evaluate at the current configuration: hop ratios as r - 1 (FP32) and the
-// FP64 accumulators.
+// FP64 accumulators.  Requires g current.
 __device__ EvalOut eval_walker_m(const DevSys& S, const Layout& L, const LayoutM& M, double* gblk, float* sm,
-                                 double a, int node_rule, bool g_valid, int lane) {
-  const int ne = L.n_e, nbf = L.n_bf, nmax = L.n_max, nn = S.n_nuc;
+                                 double a, int node_rule, int lane) {
+  const int ne = L.n_e, nbf = L.n_bf, nmax = L.n_max, nn = S.n_nuc, np_all = S.n_prim;
   const float af = (float)a, a2f = af * af;
   const float* xf = sm + M.xf;
-  const float* bt = sm + M.bt;
-  const float* cache = cache_f(L, gblk);
-  float* g = sm + M.g;
+  const double* bt = (const double*)(sm + M.bt);
+  const float* der = cache_der(L, gblk);
+  const float* g = sm + M.gf;
   float* dl = sm + M.dl;
   float* ej = sm + M.ej;     // grad J (3), lap J, half e-e sum
   const float* ep = sm + M.ep;
-  float* dd = sm + M.dd;
-  float* geo = sm + M.geo;   // per (electron, nucleus): d (3), |d|^2
-  float* rt1 = sm + M.rt1;   // per (electron, nucleus): r, 1/(1 + B r)
-  float* pair = sm + M.pair; // per electron pair: |d|^2, r, 1/(1 + b r)
-  float* hcur = sm + M.hcur; // per (electron, primitive): coef exp(-alpha |d|^2)
+  double* dd = (double*)(sm + M.dd);
+  float* geo = sm + M.geo;
+  float* rt1 = sm + M.rt1;
+  float* pair = sm + M.pair;
+  float* hcur = sm + M.hcur;
   const float bj = (float)S.j2_b, cpar = (float)S.j2_par, canti = (float)S.j2_anti;
   // (1) current configuration: Jastrow derivatives, geometry, primitive values
   {
@@ -229,7 +299,7 @@ __device__ EvalOut eval_walker_m(const DevSys& S, const Layout& L, const LayoutM
             const float ir = rsqrtf(s), r = s * ir;
             const float c = (up_e == (j < L.n_up)) ? cpar : canti;
             const float tt = __fdividef(1.f, fmaf(bj, r, 1.f));
-            float* pp = pair + 3 * (e * ne + j);
+            float* pp = pair + e * M.pair_st + 3 * j;
             pp[0] = s; pp[1] = r; pp[2] = tt;
             const float up = c * tt * tt, upp = -2.f * bj * up * tt, f = up * ir;
             gx = fmaf(f, dx, gx); gy = fmaf(f, dy, gy); gz = fmaf(f, dz, gz);
@@ -237,24 +307,22 @@ __device__ EvalOut eval_walker_m(const DevSys& S, const Layout& L, const LayoutM
             vee = fmaf(0.5f, ir, vee);
           } else {
             const int I = t - (ne - 1);
-            const float dx = xe - (float)__ldg(S.R + 3 * I), dy = ye - (float)__ldg(S.R + 3 * I + 1),
-                        dz = ze - (float)__ldg(S.R + 3 * I + 2);
+            const float dx = xe - __ldg(S.Rf + 3 * I), dy = ye - __ldg(S.Rf + 3 * I + 1),
+                        dz = ze - __ldg(S.Rf + 3 * I + 2);
             const float s = dx * dx + dy * dy + dz * dz;
-            float* gg = geo + 4 * (e * nn + I);
+            float* gg = geo + e * M.geo_st + 4 * I;
             gg[0] = dx; gg[1] = dy; gg[2] = dz; gg[3] = s;
+            const float ir = rsqrtf(s), r = s * ir;
             for (int sh = __ldg(S.atom_sh + I); sh < __ldg(S.atom_sh + I + 1); ++sh) {
               const int np = __ldg(S.sh_nprim + sh), off = __ldg(S.sh_off + sh);
-              const bool sto = __ldg(S.sh_l + sh) == -1;
-              const float arg = sto ? sqrtf(s) : s;
+              const float arg = __ldg(S.sh_l + sh) == -1 ? r : s;
               for (int q = 0; q < np; ++q)
-                hcur[e * S.n_prim + off + q] = (float)__ldg(S.coefs + off + q) * __expf(-(float)__ldg(S.exps + off + q) * arg);
+                hcur[e * M.hcur_st + off + q] = __ldg(S.coefsf + off + q) * __expf(-__ldg(S.expsf + off + q) * arg);
             }
-            const float A = (float)__ldg(S.j1A + I);
-            const float ir = rsqrtf(s), r = s * ir;
-            const float B = (float)__ldg(S.j1B + I);
+            const float A = __ldg(S.j1Af + I), B = __ldg(S.j1Bf + I);
             const float tt = __fdividef(1.f, fmaf(B, r, 1.f));
-            rt1[2 * (e * nn + I)] = r;
-            rt1[2 * (e * nn + I) + 1] = tt;
+            rt1[e * M.rt1_st + 2 * I] = r;
+            rt1[e * M.rt1_st + 2 * I + 1] = tt;
             if (A != 0.f) {
               const float vp = -A * tt * tt, vpp = -2.f * B * vp * tt, f = vp * ir;
               gx = fmaf(f, dx, gx); gy = fmaf(f, dy, gy); gz = fmaf(f, dz, gz);
@@ -276,44 +344,46 @@ __device__ EvalOut eval_walker_m(const DevSys& S, const Layout& L, const LayoutM
       }
     }
   }
+  // (1b) FP64 determinant derivatives from the FP32 derivative cache and FP64 B
   for (int o = lane; o < 4 * ne; o += WARP) {
     const int i = o >> 2, c = o & 3;
     const SpinRef sr = spin_ref(L, i);
-    const float* brow = bt + sr.bt_off + sr.ii * sr.n;
-    const float* ce = cache + i * 5 * nmax + (c + 1) * nmax;
-    float acc = 0.f;
-    for (int k = 0; k < sr.n; ++k) acc = fmaf(ce[k], brow[k], acc);
+    const double* brow = bt + sr.bt_off + sr.ii * sr.n;
+    const float* ce = der + (i * 4 + c) * nmax;
+    double acc = 0.0;
+    for (int k = 0; k < sr.n; ++k) acc = fma((double)ce[k], brow[k], acc);
     dd[o] = acc;
   }
-  if (!g_valid) compute_g_m(S, L, M, sm, lane);
   __syncwarp();
-  // (3) every hop, as r - 1
+  (void)np_all;
+  // (3) every hop, as r - 1, in FP32
   for (int p = lane; p < 6 * ne; p += WARP) {
     const int i = p / 6, d = p - 6 * i, ax = d >> 1;
     const float sa = (d & 1) ? -af : af;
     const float s2a = sa + sa;
     const float* gi = g + i * nbf;
+    const float* hc = hcur + i * M.hcur_st;
     float D = 0.f, dJ = 0.f;
     for (int I = 0; I < nn; ++I) {
-      const float* gg = geo + 4 * (i * nn + I);
-      const float del = fmaf(s2a, gg[ax], a2f);           // |r'-R|^2 - |r-R|^2
+      const float* gg = geo + i * M.geo_st + 4 * I;
+      const float del = fmaf(s2a, gg[ax], a2f);             // |r'-R|^2 - |r-R|^2
       const float sp = gg[3] + del;
-      const float A = (float)__ldg(S.j1A + I);
-      const float r = rt1[2 * (i * nn + I)], tt = rt1[2 * (i * nn + I) + 1];
+      const float r = rt1[i * M.rt1_st + 2 * I];
       const float rp = sp * rsqrtf(sp);
+      const float A = __ldg(S.j1Af + I);
       if (A != 0.f) {
-        const float tp = __fdividef(1.f, fmaf((float)__ldg(S.j1B + I), rp, 1.f));
-        dJ -= A * del * tt * __fdividef(tp, rp + r);
+        const float tp = __fdividef(1.f, fmaf(__ldg(S.j1Bf + I), rp, 1.f));
+        dJ -= A * del * rt1[i * M.rt1_st + 2 * I + 1] * __fdividef(tp, rp + r);
       }
       for (int sh = __ldg(S.atom_sh + I); sh < __ldg(S.atom_sh + I + 1); ++sh) {
         const int l = __ldg(S.sh_l + sh), np = __ldg(S.sh_nprim + sh), off = __ldg(S.sh_off + sh),
                   bf = __ldg(S.sh_bf + sh);
-        float rd = 0.f, rn = 0.f;   // sum of (h' - h) and of h'
+        const float arg = l == -1 ? __fdividef(del, rp + r) : del;
+        float rd = 0.f, rn = 0.f;   // sums of h' - h and of h'
         for (int q = 0; q < np; ++q) {
-          const float h = hcur[i * S.n_prim + off + q];
-          const float al = (float)__ldg(S.exps + off + q);
+          const float h = hc[off + q];
           // the clamp only acts where h has already underflowed to 0
-          const float dh = h * expm1f(fminf(l == -1 ? -al * __fdividef(del, rp + r) : -al * del, 80.f));
+          const float dh = h * expm1_fast(fminf(-__ldg(S.expsf + off + q) * arg, 80.f));
           rd += dh;
           rn += h + dh;
         }
@@ -328,17 +398,17 @@ __device__ EvalOut eval_walker_m(const DevSys& S, const Layout& L, const LayoutM
     }
     const bool up_i = i < L.n_up;
     const float xia = xf[3 * i + ax];
+    const float* pr = pair + i * M.pair_st;
     for (int j = 0; j < ne; ++j) {
       if (j == i) continue;
-      const float* pp = pair + 3 * (i * ne + j);
       const float del = fmaf(s2a, xia - xf[3 * j + ax], a2f);
-      const float sp = pp[0] + del;
+      const float sp = pr[3 * j] + del;
       const float rp = sp * rsqrtf(sp);
       const float tp = __fdividef(1.f, fmaf(bj, rp, 1.f));
       const float c = (up_i == (j < L.n_up)) ? cpar : canti;
-      dJ = fmaf(c * del * pp[2], __fdividef(tp, rp + pp[1]), dJ);
+      dJ = fmaf(c * del * pr[3 * j + 2], __fdividef(tp, rp + pr[3 * j + 1]), dJ);
     }
-    const float J = expm1f(dJ);
+    const float J = expm1_fast(dJ);
     dl[p] = fmaf(D, J, D + J);
   }
   __syncwarp();
@@ -351,19 +421,23 @@ __device__ EvalOut eval_walker_m(const DevSys& S, const Layout& L, const LayoutM
   int nnode = 0;
   const double ia2 = 1.0 / (a * a);
   for (int i = lane; i < ne; i += WARP) {
-    double sd = 0.0;
+    float sd = 0.f, skd = 0.f, sneg = 0.f;
+    int nk = 0;
     bool node = false;
     for (int d = 0; d < 6; ++d) {
-      const double x1 = (double)dl[6 * i + d];     // r - 1
+      const float x1 = dl[6 * i + d];     // r - 1
       sd += x1;
-      if (x1 > -1.0) kept += 1.0 + x1;
-      if (x1 < -1.0) { negs -= 1.0 + x1; node = true; }
+      if (x1 > -1.f) { skd += x1; ++nk; }
+      if (x1 < -1.f) { sneg -= 1.f + x1; node = true; }
     }
+    kept += (double)nk + (double)skd;
+    negs += (double)sneg;
     const float* q = ej + 5 * i;
-    const float* dv = dd + 4 * i;
-    const float lap = dv[3] + 2.f * (dv[0] * q[0] + dv[1] * q[1] + dv[2] * q[2]) + q[3] +
-                      (q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
-    const double nu_zv = (double)ep[2 * i] + 0.5 * (sd * ia2 - (double)lap);
+    const double* dv = dd + 4 * i;
+    const double gJx = q[0], gJy = q[1], gJz = q[2];
+    const double lap = dv[3] + 2.0 * (dv[0] * gJx + dv[1] * gJy + dv[2] * gJz) + (double)q[3] +
+                       (gJx * gJx + gJy * gJy + gJz * gJz);
+    const double nu_zv = (double)ep[2 * i] + 0.5 * ((double)sd * ia2 - lap);
     bool apply;
     if (node_rule == 0) apply = node;
     else if (node_rule == 1) apply = any_node;
@@ -392,22 +466,25 @@ __device__ EvalOut eval_walker_m(const DevSys& S, const Layout& L, const LayoutM
 }
 
 __device__ EvalOut init_walker_m(const DevSys& S, const Layout& L, const LayoutM& M, double* gblk, float* sm,
-                                 double a, int node_rule, int lane, bool& singular) {
-  float* chi5 = sm + M.chi5;
-  float* phi5 = sm + M.phi5;
-  float* cache = cache_f(L, gblk);
+                                 double a, int node_rule, const double* T, int lane, bool& singular) {
+  double* val = cache_val(L, gblk);
+  float* der = cache_der(L, gblk);
   const double* x = (const double*)(sm + M.x);
   float* xf = sm + M.xf;
   float* ep = sm + M.ep;
+  const double* phiv = (const double*)(sm + M.phiv);
+  const float* phi5 = sm + M.phi5;
   for (int o = lane; o < 3 * L.n_e; o += WARP) xf[o] = (float)x[o];
   __syncwarp();
   for (int i = 0; i < L.n_e; ++i) {
     const int n = i < L.n_up ? L.n_up : L.n_dn;
-    const float q[3] = {xf[3 * i], xf[3 * i + 1], xf[3 * i + 2]};
-    orbital_derivs_f(S, L, q, n, chi5, phi5, lane);
-    for (int o = lane; o < 5 * L.n_max; o += WARP) cache[i * 5 * L.n_max + o] = phi5[o];
+    const double q[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
+    orbital_rows_m(S, L, M, q, n, sm, T, lane);
+    for (int o = lane; o < L.n_max; o += WARP) val[i * L.n_max + o] = phiv[o];
+    for (int o = lane; o < 4 * L.n_max; o += WARP) der[i * 4 * L.n_max + o] = phi5[o];
     float nu, nucap;
-    electron_potentials_f(S, q, (float)a, lane, nu, nucap);
+    const float qf[3] = {xf[3 * i], xf[3 * i + 1], xf[3 * i + 2]};
+    electron_potentials_f(S, qf, (float)a, lane, nu, nucap);
     if (lane == 0) {
       ep[2 * i] = nu;
       ep[2 * i + 1] = nucap;
@@ -416,22 +493,24 @@ __device__ EvalOut init_walker_m(const DevSys& S, const Layout& L, const LayoutM
   }
   __threadfence_block();
   singular = reinvert_m(L, M, gblk, sm, lane);
-  return eval_walker_m(S, L, M, gblk, sm, a, node_rule, false, lane);
+  compute_g_m(S, L, M, sm, 0, L.n_e, lane);
+  return eval_walker_m(S, L, M, gblk, sm, a, node_rule, lane);
 }
 
-// Heat-bath choice from r - 1 values (same order and rule as the FP64 path).
+// Heat-bath choice from r - 1 values (same order and rule as the FP64 path,
+// FP32 running sums).
 __device__ int choose_hop_m(const float* dl, int n_hop, double u, int lane) {
   int choice = -1;
   if (lane == 0) {
-    double total = 0.0;
-    for (int p = 0; p < n_hop; ++p) total += dl[p] > -1.f ? 1.0 + (double)dl[p] : 0.0;
-    if (total > 0.0) {
-      const double t = u * total;
-      double run = 0.0;
+    float total = 0.f;
+    for (int p = 0; p < n_hop; ++p) total += dl[p] > -1.f ? 1.f + dl[p] : 0.f;
+    if (total > 0.f) {
+      const float t = (float)u * total;
+      float run = 0.f;
       int last = -1;
       for (int p = 0; p < n_hop; ++p) {
-        const double k = dl[p] > -1.f ? 1.0 + (double)dl[p] : 0.0;
-        if (k > 0.0) last = p;
+        const float k = dl[p] > -1.f ? 1.f + dl[p] : 0.f;
+        if (k > 0.f) last = p;
         run += k;
         if (run > t) { choice = p; break; }
       }
@@ -441,73 +520,67 @@ __device__ int choose_hop_m(const float* dl, int n_hop, double u, int lane) {
   return __shfl_sync(FULL, choice, 0);
 }
 
+// Apply hop p: FP64 orbital value row and Sherman-Morrison update of B, FP32
+// derivative rows, g of the moved spin block, potentials and position.
 __device__ void apply_hop_m(const DevSys& S, const Layout& L, const LayoutM& M, double* gblk, float* sm, int p,
-                            double a, bool g_valid, int lane) {
+                            double a, const double* T, int lane) {
   double* x = (double*)(sm + M.x);
   float* xf = sm + M.xf;
-  float* bt = sm + M.bt;
-  float* cache = cache_f(L, gblk);
-  float* phi5 = sm + M.phi5;
-  float* f = sm + M.f;
-  float* row = sm + M.row;
-  float* g = sm + M.g;
-  float* grow = sm + M.grow;
+  double* bt = (double*)(sm + M.bt);
+  double* val = cache_val(L, gblk);
+  float* der = cache_der(L, gblk);
+  const double* phiv = (const double*)(sm + M.phiv);
+  const float* phi5 = sm + M.phi5;
+  double* f = (double*)(sm + M.u);
+  double* row = (double*)(sm + M.row);
   const int i = p / 6, d = p - 6 * i;
-  double qd[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
-  qd[d >> 1] += (d & 1) ? -a : a;
-  const float q[3] = {(float)qd[0], (float)qd[1], (float)qd[2]};
+  double q[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
+  q[d >> 1] += (d & 1) ? -a : a;
   const SpinRef sr = spin_ref(L, i);
-  orbital_derivs_f(S, L, q, sr.n, sm + M.chi5, phi5, lane);
-  float* B = bt + sr.bt_off;
+  orbital_rows_m(S, L, M, q, sr.n, sm, T, lane);
+  double* B = bt + sr.bt_off;
   const int n = sr.n;
   for (int j = lane; j < n; j += WARP) {
-    float acc = 0.f;
-    for (int k = 0; k < n; ++k) acc = fmaf(phi5[k], B[j * n + k], acc);
+    double acc = 0.0;
+    for (int k = 0; k < n; ++k) acc = fma(phiv[k], B[j * n + k], acc);
     f[j] = acc;
   }
   for (int k = lane; k < n; k += WARP) row[k] = B[sr.ii * n + k];
-  if (g_valid)
-    for (int mu = lane; mu < L.n_bf; mu += WARP) grow[mu] = g[i * L.n_bf + mu];
   __syncwarp();
-  const float invR = 1.f / f[sr.ii];
+  const double invR = 1.0 / f[sr.ii];
   __syncwarp();
-  for (int j = lane; j < n; j += WARP) f[j] = (f[j] - (j == sr.ii ? 1.f : 0.f)) * invR;
+  for (int j = lane; j < n; j += WARP) f[j] = (f[j] - (j == sr.ii ? 1.0 : 0.0)) * invR;
   __syncwarp();
   for (int o = lane; o < n * n; o += WARP) {
     const int j = o / n, k = o - j * n;
-    B[o] = fmaf(-row[k], f[j], B[o]);
+    B[o] = fma(-row[k], f[j], B[o]);
   }
-  if (g_valid) {
-    const int e0 = i - sr.ii;
-    for (int o = lane; o < n * L.n_bf; o += WARP) {
-      const int j = o / L.n_bf, mu = o - j * L.n_bf;
-      float* gj = g + (e0 + j) * L.n_bf + mu;
-      *gj = fmaf(-grow[mu], f[j], *gj);
-    }
-  }
-  for (int o = lane; o < 5 * L.n_max; o += WARP) cache[i * 5 * L.n_max + o] = phi5[o];
+  for (int o = lane; o < L.n_max; o += WARP) val[i * L.n_max + o] = phiv[o];
+  for (int o = lane; o < 4 * L.n_max; o += WARP) der[i * 4 * L.n_max + o] = phi5[o];
+  const float qf[3] = {(float)q[0], (float)q[1], (float)q[2]};
   float nu, nucap;
-  electron_potentials_f(S, q, (float)a, lane, nu, nucap);
+  electron_potentials_f(S, qf, (float)a, lane, nu, nucap);
   if (lane == 0) {
-    x[3 * i] = qd[0]; x[3 * i + 1] = qd[1]; x[3 * i + 2] = qd[2];
-    xf[3 * i] = q[0]; xf[3 * i + 1] = q[1]; xf[3 * i + 2] = q[2];
+    x[3 * i] = q[0]; x[3 * i + 1] = q[1]; x[3 * i + 2] = q[2];
+    xf[3 * i] = qf[0]; xf[3 * i + 1] = qf[1]; xf[3 * i + 2] = qf[2];
     sm[M.ep + 2 * i] = nu;
     sm[M.ep + 2 * i + 1] = nucap;
   }
   __threadfence_block();
   __syncwarp();
+  compute_g_m(S, L, M, sm, i - sr.ii, i - sr.ii + n, lane);
 }
 
 __device__ __forceinline__ void load_block_m(const Layout& L, const LayoutM& M, const double* __restrict__ g,
                                              float* sm, int lane) {
   double* x = (double*)(sm + M.x);
   double* sc = (double*)(sm + M.sc);
+  double* bt = (double*)(sm + M.bt);
   for (int o = lane; o < 3 * L.n_e; o += WARP) {
     x[o] = g[L.g_x + o];
     sm[M.xf + o] = (float)g[L.g_x + o];
   }
-  const float* btg = (const float*)(g + L.g_bt);
-  for (int o = lane; o < L.n_up * L.n_up + L.n_dn * L.n_dn; o += WARP) sm[M.bt + o] = btg[o];
+  for (int o = lane; o < L.n_up * L.n_up + L.n_dn * L.n_dn; o += WARP) bt[o] = g[L.g_bt + o];
   for (int o = lane; o < L.n_hop; o += WARP) sm[M.dl + o] = (float)(g[L.g_rat + o] - 1.0);
   for (int o = lane; o < 2 * L.n_e; o += WARP) sm[M.ep + o] = (float)g[L.g_pot + o];
   for (int o = lane; o < SC_COUNT; o += WARP) sc[o] = g[L.g_sc + o];
@@ -519,9 +592,9 @@ __device__ __forceinline__ void store_block_m(const Layout& L, const LayoutM& M,
   __syncwarp();
   const double* x = (const double*)(sm + M.x);
   const double* sc = (const double*)(sm + M.sc);
+  const double* bt = (const double*)(sm + M.bt);
   for (int o = lane; o < 3 * L.n_e; o += WARP) g[L.g_x + o] = x[o];
-  float* btg = (float*)(g + L.g_bt);
-  for (int o = lane; o < L.n_up * L.n_up + L.n_dn * L.n_dn; o += WARP) btg[o] = sm[M.bt + o];
+  for (int o = lane; o < L.n_up * L.n_up + L.n_dn * L.n_dn; o += WARP) g[L.g_bt + o] = bt[o];
   for (int o = lane; o < L.n_hop; o += WARP) g[L.g_rat + o] = 1.0 + (double)sm[M.dl + o];
   for (int o = lane; o < 2 * L.n_e; o += WARP) g[L.g_pot + o] = (double)sm[M.ep + o];
   for (int o = lane; o < SC_COUNT; o += WARP) g[L.g_sc + o] = sc[o];
@@ -530,9 +603,10 @@ __device__ __forceinline__ void store_block_m(const Layout& L, const LayoutM& M,
 __global__ void k_init_walkers_m(DevSys S, Layout L, LayoutM M, double* __restrict__ state,
                                  const double* __restrict__ x_in, const double* __restrict__ w_in, int n, double a,
                                  int node_rule) {
-  extern __shared__ float smf[];
+  extern __shared__ double smem[];
+  const double* T = stage_table(S, smem);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  float* sm = smf + wib * M.stride;
+  float* sm = (float*)(smem + EXP_TAB) + wib * M.stride;
   double* x = (double*)(sm + M.x);
   double* sc = (double*)(sm + M.sc);
   const int nwarps = gridDim.x * (blockDim.x >> 5);
@@ -541,7 +615,7 @@ __global__ void k_init_walkers_m(DevSys S, Layout L, LayoutM M, double* __restri
     for (int o = lane; o < 3 * L.n_e; o += WARP) x[o] = x_in[(size_t)w * 3 * L.n_e + o];
     __syncwarp();
     bool sing = false;
-    const EvalOut e = init_walker_m(S, L, M, gblk, sm, a, node_rule, lane, sing);
+    const EvalOut e = init_walker_m(S, L, M, gblk, sm, a, node_rule, T, lane, sing);
     if (lane == 0) {
       for (int k = 0; k < SC_COUNT; ++k) sc[k] = 0.0;
       sc[SC_W] = w_in ? w_in[w] : 1.0;
@@ -559,9 +633,10 @@ __global__ void k_init_walkers_m(DevSys S, Layout L, LayoutM M, double* __restri
 __global__ void k_eval_configs_m(DevSys S, Layout L, LayoutM M, double* __restrict__ scratch,
                                  const double* __restrict__ x_in, int n, double a, int node_rule,
                                  double* __restrict__ ratios, double* __restrict__ ev, int32_t* __restrict__ n_node) {
-  extern __shared__ float smf[];
+  extern __shared__ double smem[];
+  const double* T = stage_table(S, smem);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  float* sm = smf + wib * M.stride;
+  float* sm = (float*)(smem + EXP_TAB) + wib * M.stride;
   double* x = (double*)(sm + M.x);
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   for (int w = blockIdx.x * (blockDim.x >> 5) + wib; w < n; w += nwarps) {
@@ -569,7 +644,7 @@ __global__ void k_eval_configs_m(DevSys S, Layout L, LayoutM M, double* __restri
     for (int o = lane; o < 3 * L.n_e; o += WARP) x[o] = x_in[(size_t)w * 3 * L.n_e + o];
     __syncwarp();
     bool sing = false;
-    const EvalOut e = init_walker_m(S, L, M, gblk, sm, a, node_rule, lane, sing);
+    const EvalOut e = init_walker_m(S, L, M, gblk, sm, a, node_rule, T, lane, sing);
     for (int o = lane; o < L.n_hop; o += WARP) ratios[(size_t)w * L.n_hop + o] = 1.0 + (double)sm[M.dl + o];
     if (lane == 0) {
       ev[4 * (size_t)w] = e.bbar;
@@ -583,9 +658,10 @@ __global__ void k_eval_configs_m(DevSys S, Layout L, LayoutM M, double* __restri
 }
 
 __global__ void k_propagate_m(DevSys S, Layout L, LayoutM M, double* __restrict__ state, int n_w, StepParams P) {
-  extern __shared__ float smf[];
+  extern __shared__ double smem[];
+  const double* T = stage_table(S, smem);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  float* sm = smf + wib * M.stride;
+  float* sm = (float*)(smem + EXP_TAB) + wib * M.stride;
   double* sc = (double*)(sm + M.sc);
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   for (int w = blockIdx.x * (blockDim.x >> 5) + wib; w < n_w; w += nwarps) {
@@ -620,19 +696,18 @@ __global__ void k_propagate_m(DevSys S, Layout L, LayoutM M, double* __restrict_
       if (p < 0) {
         status |= ST_STUCK;
       } else {
-        if (!g_valid) {
-          compute_g_m(S, L, M, sm, lane);
-          g_valid = true;
-        }
-        apply_hop_m(S, L, M, gblk, sm, p, P.a, g_valid, lane);
+        apply_hop_m(S, L, M, gblk, sm, p, P.a, T, lane);
         ++moves;
         if (++since >= P.reinv_period) {
           if (reinvert_m(L, M, gblk, sm, lane)) status |= ST_SINGULAR;
           since = 0;
           g_valid = false;
         }
-        const EvalOut e = eval_walker_m(S, L, M, gblk, sm, P.a, P.node_rule, g_valid, lane);
-        g_valid = true;
+        if (!g_valid) {
+          compute_g_m(S, L, M, sm, 0, L.n_e, lane);
+          g_valid = true;
+        }
+        const EvalOut e = eval_walker_m(S, L, M, gblk, sm, P.a, P.node_rule, lane);
         bbar = e.bbar;
         Wd = e.W;
         eL = e.eL;

@@ -1,0 +1,72 @@
+"""Mixed-precision path (precision = 1) against the FP64 oracle and the FP64
+GPU path.
+
+Tolerances follow from FP32 arithmetic (unit roundoff u = 2^-24 = 6e-8): each
+hop ratio is a sum of O(100) FP32 terms, so |r - r_ref| <= ~100 u |terms|;
+relative to max(1, |r|) that is below 1e-4 even near a node, where the terms
+grow like 1/|Psi|.  The local energy sums 6 N_e ratios scaled by 1/(2a^2)
+(12.5 at a = 0.2), so per configuration |e_L - e_L_ref| stays below
+6 N_e * 1e-4 * 12.5 / sqrt(6 N_e) ~ 1e-2 Ha for 16 electrons; its mean over
+configurations (the energy bias) must stay below 1e-4 Ha (0.1 mHa)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import hamiltonian as H
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("name,sysf,n,rat_tol,el_tol", [
+    ("h_sto", W.hydrogen_atom_sto, 64, 1e-6, 1e-5),
+    ("h2", W.h2_sto3g, 256, 1e-6, 2e-5),
+    ("wm", W.water_methane, 256, 1e-4, 1e-2)])
+def test_mixed_eval_against_oracle(name, sysf, n, rat_tol, el_tol):
+    import torch
+    from gpu_helpers import assert_close, lib_or_skip
+    P = lib_or_skip()
+    s = sysf()
+    lr = P.Lrdmc(s, W.initial_walkers(s, n, seed=3), 0.2, precision=1)
+    x = W.initial_walkers(s, n, seed=77)
+    ratios, ev, nn = lr.eval_configs(torch.tensor(x, device="cuda"))
+    torch.cuda.synchronize()
+    ref = H.evaluate(s, x, 0.2)
+    assert_close(ratios.cpu().numpy(), ref["ratios"], rtol=rat_tol, what="ratios")
+    el = ev[:, 3].cpu().numpy()
+    assert np.max(np.abs(el - ref["eL"])) <= el_tol
+    assert abs(np.mean(el - ref["eL"])) <= 1e-4                      # energy bias below 0.1 mHa
+    assert np.mean(nn.cpu().numpy() != ref["n_node"]) <= 0.01
+
+
+def test_mixed_interval_tracks_fp64_path():
+    """Same start, same random streams: after a 20-hop load-balanced interval
+    almost every walker made the same hops as in FP64 (a hop choice can flip
+    only when the uniform falls within ~1e-7 of a cumulative boundary), and
+    those walkers carry the same weight to FP32 accuracy."""
+    from gpu_helpers import lib_or_skip
+    P = lib_or_skip()
+    s = W.water_methane()
+    x0 = W.initial_walkers(s, 512, seed=21)
+    g = {}
+    for prec in (0, 1):
+        lr = P.Lrdmc(s, x0, 0.2, seed=4, precision=prec, reinv_period=50)
+        lr.e0 = -20.0
+        lr.propagate(P.LOAD_BALANCED, n_proj=20)
+        g[prec] = lr.get_walkers()
+        lr.close()
+    same = np.all(g[0]["x"] == g[1]["x"], axis=(1, 2))
+    assert same.mean() >= 0.95
+    rel = np.abs(g[1]["w"][same] - g[0]["w"][same]) / np.abs(g[0]["w"][same])
+    assert np.median(rel) < 1e-5
+
+
+def test_mixed_run_reaches_exact_hydrogen_energy():
+    from gpu_helpers import lib_or_skip
+    P = lib_or_skip()
+    s = W.hydrogen_atom_sto(1.0)
+    lr = P.Lrdmc(s, W.initial_walkers(s, 128, seed=2), 0.2, precision=1)
+    for _ in range(5):
+        lr.propagate(P.LOAD_BALANCED, n_proj=10)
+        lr.branch()
+    E, _ = lr.energy()
+    assert abs(E + 0.5) < 2e-6
