@@ -237,10 +237,64 @@ def run_gpu(args, rank, world):
     h2d = N_W * s.n_elec * 3 * 8
     d2h = 8 * (N_W * (3 * s.n_elec + 6 * s.n_elec + 7))
     e2e_value = world * ws_per_step / (statistics.mean(e2e_ms) / 1e3)
+    mixed = run_mixed(args, P, s, x0, lr, flush, rank) if not args.no_mixed else None
     return dict(value=value, t_total=t_total, step_ms=statistics.mean(step_ms), prop_ms=statistics.mean(prop_ms),
                 launches=launches, achieved=achieved, clocks=clk.summary(), conv_rate=conv_rate,
                 conv_moves=conv_moves, tau=tau, e2e=e2e_value, h2d=h2d, d2h=d2h, slots=slots,
-                energy=lr.energy())
+                energy=lr.energy(), mixed=mixed)
+
+
+def time_lb_intervals(lr, P, flush, steps, warmup):
+    """Mean ms per load-balanced interval (propagate + branch), L2 flushed between."""
+    import torch
+    for _ in range(warmup):
+        lr.propagate(P.LOAD_BALANCED, n_proj=N_PROJ)
+        lr.branch()
+    torch.cuda.synchronize()
+    ms = []
+    for k in range(steps):
+        with torch.cuda.stream(lr.stream):
+            flush.fill_(k & 0xFF)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(lr.stream)
+            lr.propagate(P.LOAD_BALANCED, n_proj=N_PROJ)
+            lr.branch()
+            e1.record(lr.stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return statistics.mean(ms)
+
+
+def run_mixed(args, P, s, x0, lr64, flush, rank):
+    """Mixed-precision form: throughput at the benchmark size and at 51200
+    walkers, and its energy bias against FP64 by correlated sampling on the
+    equilibrated FP64 population (same configurations evaluated both ways,
+    weighted as in the load-balanced estimator, w / (W - E_0) with w = 1)."""
+    import torch
+    import workloads as W
+    lm = P.Lrdmc(s, x0, A, seed=SEED + rank, reinv_period=50, p_gbar=10, precision=1)
+    ms = time_lb_intervals(lm, P, flush, args.steps, args.warmup)
+    x = torch.tensor(lr64.get_walkers()["x"], device=flush.device)
+    _, ev64, _ = lr64.eval_configs(x)
+    _, ev32, _ = lm.eval_configs(x)
+    torch.cuda.synchronize()
+    ev64, ev32 = ev64.cpu().numpy(), ev32.cpu().numpy()
+    f = 1.0 / (ev64[:, 2] - lr64.e0)
+    d = ev32[:, 3] - ev64[:, 3]
+    bias = float(np.sum(f * d) / np.sum(f))
+    err = float(np.std(d) * np.sqrt(np.sum(f * f)) / np.sum(f))
+    lm.close()
+    big = 51200
+    xb = W.initial_walkers(s, big, seed=SEED + 20 + rank)
+    lb = P.Lrdmc(s, xb, A, seed=SEED + rank, reinv_period=50, p_gbar=10, precision=1)
+    ms_big = time_lb_intervals(lb, P, flush, max(2, args.steps // 3), 2)
+    lb.close()
+    return {"value": N_W * N_PROJ / (ms / 1e3), "unit": "walker-steps/s", "ms_per_step": ms,
+            "n_w_51200": {"value": big * N_PROJ / (ms_big / 1e3), "ms_per_step": ms_big},
+            "energy_bias_mHa": 1e3 * bias, "energy_bias_err_mHa": 1e3 * err,
+            "bias_sample": f"{N_W} equilibrated FP64 configurations, weights 1/(W - E0)",
+            "max_abs_eL_diff_Ha": float(np.max(np.abs(d))),
+            "precision": "FP32 hop ratios / basis / Jastrow; FP64 A rows, B, Sherman-Morrison, accumulators"}
 
 
 def main():
@@ -250,6 +304,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lrdmc", choices=["lrdmc", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -310,6 +365,7 @@ def main():
             "cpu_baseline": cpu,
             "e2e": {"value": res["e2e"], "unit": "walker-steps/s", "h2d_bytes_per_step": res["h2d"],
                     "d2h_bytes_per_step": res["d2h"]},
+            "mixed": dict(res["mixed"], speedup_vs_fp64=res["mixed"]["value"] / res["value"]) if res["mixed"] else None,
             "gpu_launches": res["launches"],
             "clocks": res["clocks"],
             "energy": {"E": res["energy"][0], "err": res["energy"][1]},
