@@ -221,6 +221,14 @@ def run_gpu(args, rank, world):
         h = lr.history()
         conv_moves.append((float(h["moves_mean"][-1]), int(h["moves_max"][-1])))
     conv_rate = N_W * statistics.mean(m for m, _ in conv_moves) / (statistics.mean(conv_ms) / 1e3)
+    # load imbalance inside the GPU: per-walker start/stop stamps of one interval
+    lr.set_timing(True)
+    imbalance = {}
+    for name, kind in (("load_balanced", P.LOAD_BALANCED), ("conventional", P.CONVENTIONAL)):
+        lr.propagate(kind, n_proj=N_PROJ, tau=tau, max_moves=100 * N_PROJ)
+        imbalance[name] = lr.interval_timing()
+        lr.branch()
+    lr.set_timing(False)
     # end to end through the public API with host buffers: upload the walkers
     # from pinned host memory, one interval + branching, read them back
     xh = torch.from_numpy(lr.get_walkers()["x"]).pin_memory()
@@ -241,7 +249,7 @@ def run_gpu(args, rank, world):
     return dict(value=value, t_total=t_total, step_ms=statistics.mean(step_ms), prop_ms=statistics.mean(prop_ms),
                 launches=launches, achieved=achieved, clocks=clk.summary(), conv_rate=conv_rate,
                 conv_moves=conv_moves, tau=tau, e2e=e2e_value, h2d=h2d, d2h=d2h, slots=slots,
-                energy=lr.energy(), mixed=mixed)
+                energy=lr.energy(), mixed=mixed, imbalance=imbalance)
 
 
 def time_lb_intervals(lr, P, flush, steps, warmup):
@@ -362,6 +370,7 @@ def main():
             "conventional": {"value": res["conv_rate"], "unit": "walker-steps/s", "tau": res["tau"],
                              "moves_mean_max": res["conv_moves"],
                              "lb_speedup": res["value"] / res["conv_rate"]},
+            "load_imbalance": res["imbalance"],
             "cpu_baseline": cpu,
             "e2e": {"value": res["e2e"], "unit": "walker-steps/s", "h2d_bytes_per_step": res["h2d"],
                     "d2h_bytes_per_step": res["d2h"]},

@@ -268,6 +268,17 @@ void lrdmc_philox4x32(uint64_t seed, const uint32_t ctr[4], uint32_t out[4]);
 lrdmc_status lrdmc_fp64math(int n, const double* x, double* exp_out, double* rcp_out, double* rsqrt_out,
                             void* stream);
 
+/* Load-imbalance measurement (the in-GPU image of the paper's argument that
+ * a synchronised interval waits for its slowest walker).  With timing enabled
+ * every propagate records, per walker, its start and stop time and SM;
+ * lrdmc_interval_timing then reports for the last interval (synchronises):
+ *   out[0] span of the interval (first start to last stop), ms
+ *   out[1] mean and out[2] max walker time, ms
+ *   out[3] busy fraction: total walker time / (span x resident warps)
+ *   out[4] mean hops per walker, out[5] max hops per walker. */
+lrdmc_status lrdmc_set_timing(lrdmc_handle h, int enable);
+lrdmc_status lrdmc_interval_timing(lrdmc_handle h, double out[6]);
+
 /* Number of kernels this handle has launched so far (all entry points). */
 lrdmc_status lrdmc_launch_count(lrdmc_handle h, int64_t* n);
 

@@ -80,6 +80,8 @@ def load_library():
         "lrdmc_reconfigure_indices": [C.c_int, P, C.c_uint32, P, P, C.c_size_t, P, P],
         "lrdmc_launch_count": [P, C.POINTER(C.c_int64)],
         "lrdmc_save": [P, C.c_char_p],
+        "lrdmc_set_timing": [P, C.c_int],
+        "lrdmc_interval_timing": [P, c_double_p],
         "lrdmc_load": [P, C.c_char_p],
         "lrdmc_stream": [P, C.POINTER(P)],
     }
@@ -247,6 +249,16 @@ class Lrdmc:
         nn = torch.empty((n,), dtype=torch.int32, device=x.device)
         self._check(self.lib.lrdmc_eval_configs(self._h, n, _tptr(x), _tptr(ratios), _tptr(ev), _tptr(nn)))
         return ratios, ev, nn
+
+    def set_timing(self, enable=True):
+        self._check(self.lib.lrdmc_set_timing(self._h, 1 if enable else 0))
+
+    def interval_timing(self):
+        """Load-imbalance figures of the last interval (see lrdmc_interval_timing)."""
+        out = np.zeros(6)
+        self._check(self.lib.lrdmc_interval_timing(self._h, _dptr(out)))
+        return dict(span_ms=out[0], walker_ms_mean=out[1], walker_ms_max=out[2], busy_fraction=out[3],
+                    moves_mean=out[4], moves_max=out[5])
 
     def save(self, path):
         self._check(self.lib.lrdmc_save(self._h, os.fsencode(path)))

@@ -35,7 +35,7 @@ struct Plan {
   size_t smem_per_warp = 0;
   // workspace offsets (bytes)
   size_t o_sys = 0, sys_bytes = 0, o_state = 0, o_alt = 0, state_bytes = 0, o_stats = 0, o_q = 0,
-         o_src = 0, o_dstat = 0, total = 0;
+         o_src = 0, o_dstat = 0, o_stamps = 0, total = 0;
   // system image offsets (bytes, inside the sys block)
   size_t i_R, i_Z, i_rc, i_j1A, i_j1B, i_exps, i_coefs, i_C, i_kind, i_atom, i_l, i_nprim, i_off, i_bf, i_ash,
       i_tab, i_f_R, i_f_Z, i_f_rc, i_f_j1A, i_f_j1B, i_f_exps, i_f_coefs, i_f_C;
@@ -143,6 +143,7 @@ bool make_plan(const lrdmc_system* sys, const lrdmc_trial_wf* wf, const lrdmc_pa
   P.o_q = w; w += align_up(sizeof(unsigned long long) * P.n_w);
   P.o_src = w; w += align_up(sizeof(int32_t) * P.n_w);
   P.o_dstat = w; w += align_up(sizeof(int32_t) * 16);
+  P.o_stamps = w; w += align_up(sizeof(unsigned long long) * 3 * (size_t)P.n_w);
   P.total = w;
   return true;
 }
@@ -220,6 +221,8 @@ struct lrdmc_s {
   unsigned long long* Q = nullptr;
   int32_t* src = nullptr;
   int32_t* dstat = nullptr;
+  unsigned long long* stamps = nullptr;
+  bool timing = false;
   int wpb = 4, grid = 1, num_sms = 1;
   double E0 = 0.0;
   uint32_t interval = 0;
@@ -478,6 +481,7 @@ lrdmc_status lrdmc_create(const lrdmc_system* sys, const lrdmc_trial_wf* wf, con
   h->Q = (unsigned long long*)(base + P.o_q);
   h->src = (int32_t*)(base + P.o_src);
   h->dstat = (int32_t*)(base + P.o_dstat);
+  h->stamps = (unsigned long long*)(base + P.o_stamps);
   CK(h, cudaMemsetAsync(h->dstat, 0, sizeof(int32_t) * 16, h->stream));
   // launch geometry: up to 4 walkers (warps) per CTA within the shared-memory budget
   int smem_optin = 0;
@@ -538,6 +542,7 @@ lrdmc_status lrdmc_propagate(lrdmc_handle h, const lrdmc_schedule* sch) {
   sp.a = h->prm.a;
   sp.node_rule = h->prm.node_rule;
   sp.reinv_period = h->prm.reinv_period;
+  sp.stamps = h->timing ? h->stamps : nullptr;
   const int smem = smem_bytes(h);
   if (h->P.precision == 0)
     k_propagate<<<walker_grid(h, h->P.n_w), h->wpb * 32, smem, h->stream>>>(h->S, h->P.L, h->state, h->P.n_w, sp);
@@ -839,6 +844,50 @@ lrdmc_status lrdmc_fp64math(int n, const double* x, double* exp_out, double* rcp
   k_fp64math<<<std::min(1024, (n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(n, x, exp_out, rcp_out, rsqrt_out,
                                                                                 d_tab[dev]);
   return cudaGetLastError() == cudaSuccess ? LRDMC_OK : LRDMC_ERR_CUDA;
+}
+
+lrdmc_status lrdmc_set_timing(lrdmc_handle h, int enable) {
+  if (!h) return LRDMC_ERR_ARG;
+  h->timing = enable != 0;
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_interval_timing(lrdmc_handle h, double out[6]) {
+  if (!h || !out || !h->state) return LRDMC_ERR_ARG;
+  if (!h->timing) return fail(h, LRDMC_ERR_ARG, "timing is not enabled");
+  DeviceGuard g(h->device);
+  const int n = h->P.n_w;
+  std::vector<unsigned long long> st(3 * (size_t)n);
+  CK(h, cudaMemcpyAsync(st.data(), h->stamps, sizeof(unsigned long long) * st.size(), cudaMemcpyDeviceToHost,
+                        h->stream));
+  std::vector<double> buf;
+  lrdmc_status s = extract(h, buf);   // synchronises
+  if (s != LRDMC_OK) return s;
+  unsigned long long t0 = ~0ull, t1 = 0;
+  double sum = 0.0, mx = 0.0;
+  for (int a = 0; a < n; ++a) {
+    t0 = std::min(t0, st[3 * a]);
+    t1 = std::max(t1, st[3 * a + 1]);
+    const double d = (double)(st[3 * a + 1] - st[3 * a]) * 1e-6;
+    sum += d;
+    mx = std::max(mx, d);
+  }
+  const double span = (double)(t1 - t0) * 1e-6;
+  const int resident = std::min(n, h->grid * h->wpb);
+  const size_t nx = (size_t)n * 3 * h->P.n_e, nr = (size_t)n * h->P.L.n_hop;
+  double mv = 0.0, mvmax = 0.0;
+  for (int a = 0; a < n; ++a) {
+    const double m = buf[nx + 6 * (size_t)n + nr + a];
+    mv += m;
+    mvmax = std::max(mvmax, m);
+  }
+  out[0] = span;
+  out[1] = sum / n;
+  out[2] = mx;
+  out[3] = span > 0 ? sum / (span * resident) : 0.0;
+  out[4] = mv / n;
+  out[5] = mvmax;
+  return LRDMC_OK;
 }
 
 lrdmc_status lrdmc_launch_count(lrdmc_handle h, int64_t* n) {

@@ -547,7 +547,20 @@ struct StepParams {
   double a;
   int node_rule;
   int reinv_period;
+  unsigned long long* stamps;   // optional: per walker (start ns, end ns, SM id)
 };
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned sm_id() {
+  unsigned id;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(id));
+  return id;
+}
 
 // The exponential table sits at the start of dynamic shared memory, the
 // per-warp regions after it.
@@ -643,6 +656,7 @@ __global__ void k_propagate(DevSys S, Layout L, double* __restrict__ state, int 
   double* sc = sm + L.s_sc;
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   for (int w = blockIdx.x * (blockDim.x >> 5) + wib; w < n_w; w += nwarps) {
+    const unsigned long long t_start = global_ns();
     double* gblk = state + (size_t)w * L.g_stride;
     load_block(L, gblk, sm, lane);
     double weight = 1.0, tau_left = P.tau;
@@ -713,6 +727,11 @@ __global__ void k_propagate(DevSys S, Layout L, double* __restrict__ state, int 
       sc[SC_SINCE] = since;
     }
     store_block(L, gblk, sm, lane);
+    if (P.stamps && lane == 0) {
+      P.stamps[3 * (size_t)w] = t_start;
+      P.stamps[3 * (size_t)w + 1] = global_ns();
+      P.stamps[3 * (size_t)w + 2] = sm_id();
+    }
   }
 }
 

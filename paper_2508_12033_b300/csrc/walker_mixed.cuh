@@ -497,27 +497,39 @@ __device__ EvalOut init_walker_m(const DevSys& S, const Layout& L, const LayoutM
   return eval_walker_m(S, L, M, gblk, sm, a, node_rule, lane);
 }
 
-// Heat-bath choice from r - 1 values (same order and rule as the FP64 path,
-// FP32 running sums).
+// Heat-bath choice from r - 1 values: same order and rule as the FP64 path
+// (first hop whose running sum of kept ratios exceeds u * total, last kept hop
+// if rounding leaves none), with the running sums formed by warp scans over
+// chunks of 32 hops in FP32.
 __device__ int choose_hop_m(const float* dl, int n_hop, double u, int lane) {
-  int choice = -1;
-  if (lane == 0) {
-    float total = 0.f;
-    for (int p = 0; p < n_hop; ++p) total += dl[p] > -1.f ? 1.f + dl[p] : 0.f;
-    if (total > 0.f) {
-      const float t = (float)u * total;
-      float run = 0.f;
-      int last = -1;
-      for (int p = 0; p < n_hop; ++p) {
-        const float k = dl[p] > -1.f ? 1.f + dl[p] : 0.f;
-        if (k > 0.f) last = p;
-        run += k;
-        if (run > t) { choice = p; break; }
-      }
-      if (choice < 0) choice = last;
-    }
+  float total = 0.f;
+  for (int c = 0; c < n_hop; c += WARP) {
+    const int p = c + lane;
+    float k = (p < n_hop && dl[p] > -1.f) ? 1.f + dl[p] : 0.f;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) k += __shfl_xor_sync(FULL, k, o);
+    total += k;
   }
-  return __shfl_sync(FULL, choice, 0);
+  if (!(total > 0.f)) return -1;
+  const float t = (float)u * total;
+  float base = 0.f;
+  int last = -1;
+  for (int c = 0; c < n_hop; c += WARP) {
+    const int p = c + lane;
+    const float k = (p < n_hop && dl[p] > -1.f) ? 1.f + dl[p] : 0.f;
+    float incl = k;
+#pragma unroll
+    for (int o = 1; o < WARP; o <<= 1) {
+      const float v = __shfl_up_sync(FULL, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const unsigned hit = __ballot_sync(FULL, base + incl > t);
+    if (hit) return c + __ffs(hit) - 1;
+    const unsigned kept = __ballot_sync(FULL, k > 0.f);
+    if (kept) last = c + 31 - __clz(kept);
+    base += __shfl_sync(FULL, incl, WARP - 1);
+  }
+  return last;
 }
 
 // Apply hop p: FP64 orbital value row and Sherman-Morrison update of B, FP32
@@ -665,6 +677,7 @@ __global__ void k_propagate_m(DevSys S, Layout L, LayoutM M, double* __restrict_
   double* sc = (double*)(sm + M.sc);
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   for (int w = blockIdx.x * (blockDim.x >> 5) + wib; w < n_w; w += nwarps) {
+    const unsigned long long t_start = global_ns();
     double* gblk = state + (size_t)w * L.g_stride;
     load_block_m(L, M, gblk, sm, lane);
     double weight = 1.0, tau_left = P.tau;
@@ -732,6 +745,11 @@ __global__ void k_propagate_m(DevSys S, Layout L, LayoutM M, double* __restrict_
       sc[SC_SINCE] = since;
     }
     store_block_m(L, M, gblk, sm, lane);
+    if (P.stamps && lane == 0) {
+      P.stamps[3 * (size_t)w] = t_start;
+      P.stamps[3 * (size_t)w + 1] = global_ns();
+      P.stamps[3 * (size_t)w + 2] = sm_id();
+    }
   }
 }
 
