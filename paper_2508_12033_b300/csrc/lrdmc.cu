@@ -262,14 +262,16 @@ static int smem_bytes(lrdmc_handle h) {
   return (int)(EXP_TAB * sizeof(double) + h->wpb * h->P.smem_per_warp);
 }
 
-static lrdmc_status set_kernel_smem(lrdmc_handle h) {
-  const int bytes = smem_bytes(h);
-  CK(h, cudaFuncSetAttribute(k_propagate, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  CK(h, cudaFuncSetAttribute(k_init_walkers, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  CK(h, cudaFuncSetAttribute(k_eval_configs, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  CK(h, cudaFuncSetAttribute(k_propagate_m, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  CK(h, cudaFuncSetAttribute(k_init_walkers_m, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  CK(h, cudaFuncSetAttribute(k_eval_configs_m, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+// The dynamic shared-memory limit is a per-kernel attribute shared by every
+// handle in the process, so it is raised to the device's opt-in maximum (it
+// permits, it reserves nothing); each launch still requests only its own size.
+static lrdmc_status set_kernel_smem(lrdmc_handle h, int optin) {
+  CK(h, cudaFuncSetAttribute(k_propagate, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  CK(h, cudaFuncSetAttribute(k_init_walkers, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  CK(h, cudaFuncSetAttribute(k_eval_configs, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  CK(h, cudaFuncSetAttribute(k_propagate_m, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  CK(h, cudaFuncSetAttribute(k_init_walkers_m, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  CK(h, cudaFuncSetAttribute(k_eval_configs_m, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   return LRDMC_OK;
 }
 
@@ -490,7 +492,7 @@ lrdmc_status lrdmc_create(const lrdmc_system* sys, const lrdmc_trial_wf* wf, con
   while (h->wpb > 1 && (size_t)smem_bytes(h) > (size_t)smem_optin) h->wpb >>= 1;
   if ((size_t)smem_bytes(h) > (size_t)smem_optin)
     return fail(h, LRDMC_ERR_UNSUPPORTED, "walker working set exceeds shared memory");
-  lrdmc_status st = set_kernel_smem(h);
+  lrdmc_status st = set_kernel_smem(h, smem_optin);
   if (st != LRDMC_OK) return st;
   int bps = 0;
   if (P.precision == 0)

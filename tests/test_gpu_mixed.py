@@ -70,3 +70,24 @@ def test_mixed_run_reaches_exact_hydrogen_energy():
         lr.branch()
     E, _ = lr.energy()
     assert abs(E + 0.5) < 2e-6
+
+
+def test_handles_of_both_precisions_coexist():
+    """Kernel attributes are process-wide: a handle created later (with a
+    smaller shared-memory footprint) must not break an earlier one."""
+    import torch
+    from gpu_helpers import lib_or_skip
+    P = lib_or_skip()
+    s = W.water_methane()
+    x0 = W.initial_walkers(s, 64, seed=1)
+    h64 = P.Lrdmc(s, x0, 0.2, precision=0)
+    h32 = P.Lrdmc(s, x0, 0.2, precision=1)
+    x = torch.tensor(x0, device="cuda")
+    r64, e64, _ = h64.eval_configs(x)
+    r32, e32, _ = h32.eval_configs(x)
+    h64.propagate(P.LOAD_BALANCED, n_proj=2)
+    h32.propagate(P.LOAD_BALANCED, n_proj=2)
+    h64.branch()
+    h32.branch()
+    torch.cuda.synchronize()
+    assert torch.max(torch.abs(e64[:, 3] - e32[:, 3])).item() < 1e-2
