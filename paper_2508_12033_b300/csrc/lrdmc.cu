@@ -22,6 +22,9 @@ namespace {
 
 constexpr size_t ALIGN = 256;
 constexpr int MAX_WALKERS = 1 << 24;
+// Upper bound of resident warps that get per-warp scratch (148 SMs x 16 warps);
+// the launch grid is clamped to it.
+constexpr int SCRATCH_WARPS_CAP = 148 * 16;
 
 size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
@@ -35,7 +38,8 @@ struct Plan {
   size_t smem_per_warp = 0;
   // workspace offsets (bytes)
   size_t o_sys = 0, sys_bytes = 0, o_state = 0, o_alt = 0, state_bytes = 0, o_stats = 0, o_q = 0,
-         o_src = 0, o_dstat = 0, o_stamps = 0, total = 0;
+         o_src = 0, o_dstat = 0, o_stamps = 0, o_scr = 0, total = 0;
+  int scratch_warps = 0;
   // system image offsets (bytes, inside the sys block)
   size_t i_R, i_Z, i_rc, i_j1A, i_j1B, i_exps, i_coefs, i_C, i_kind, i_atom, i_l, i_nprim, i_off, i_bf, i_ash,
       i_tab, i_f_R, i_f_Z, i_f_rc, i_f_j1A, i_f_j1B, i_f_exps, i_f_coefs, i_f_C;
@@ -89,18 +93,21 @@ bool make_plan(const lrdmc_system* sys, const lrdmc_trial_wf* wf, const lrdmc_pa
   // per-warp shared memory
   L.s_x = 0;
   L.s_bt = 3 * P.n_e;
-  L.s_g = L.s_bt + nbt;
-  const int gsz = std::max(P.n_e * P.n_bf, 2 * P.n_max * P.n_max);
-  L.s_rat = L.s_g + gsz;
+  L.s_rat = L.s_bt + nbt;
   L.s_ej = L.s_rat + L.n_hop;
   L.s_ep = L.s_ej + 6 * P.n_e;
   L.s_dd = L.s_ep + 2 * P.n_e;
   L.s_geo = L.s_dd + 4 * P.n_e;
-  L.s_pr2 = L.s_geo + std::max(4 * P.n_e * P.n_nuc, 6 * P.n_bf);
-  L.s_phi5 = L.s_pr2 + P.n_e * P.n_e;
+  L.s_pr2 = L.s_geo + 4 * P.n_e * P.n_nuc;
+  L.s_hd = L.s_pr2 + P.n_e * P.n_e;
+  L.s_hj1 = L.s_hd + L.n_hop;
+  L.s_hj2 = L.s_hj1 + L.n_hop;
+  L.s_tmp = L.s_hj2 + L.n_hop;
+  L.s_phi5 = L.s_tmp + std::max(6 * (P.n_e - 1 + P.n_nuc), 6 * P.n_bf);
   L.s_u = L.s_phi5 + 5 * P.n_max;
   L.s_row = L.s_u + P.n_max;
-  L.s_sc = L.s_row + P.n_max;
+  L.s_xo = L.s_row + P.n_max;
+  L.s_sc = L.s_xo + 4;
   L.s_stride = round_up(L.s_sc + SC_COUNT, 4);
   P.M = layout_mixed(L, P.n_nuc, P.n_prim);
   P.smem_per_warp = P.precision == 0 ? (size_t)L.s_stride * sizeof(double) : (size_t)P.M.stride * sizeof(float);
@@ -144,6 +151,8 @@ bool make_plan(const lrdmc_system* sys, const lrdmc_trial_wf* wf, const lrdmc_pa
   P.o_src = w; w += align_up(sizeof(int32_t) * P.n_w);
   P.o_dstat = w; w += align_up(sizeof(int32_t) * 16);
   P.o_stamps = w; w += align_up(sizeof(unsigned long long) * 3 * (size_t)P.n_w);
+  P.scratch_warps = round_up(std::min(P.n_w, SCRATCH_WARPS_CAP), 4);
+  P.o_scr = w; w += align_up(sizeof(double) * scratch_doubles(L) * (size_t)P.scratch_warps);
   P.total = w;
   return true;
 }
@@ -222,6 +231,7 @@ struct lrdmc_s {
   int32_t* src = nullptr;
   int32_t* dstat = nullptr;
   unsigned long long* stamps = nullptr;
+  double* scr = nullptr;
   bool timing = false;
   int wpb = 4, grid = 1, num_sms = 1;
   double E0 = 0.0;
@@ -294,7 +304,7 @@ static lrdmc_status place_walkers(lrdmc_handle h, const double* x, const double*
   const int smem = smem_bytes(h);
   if (P.precision == 0)
     k_init_walkers<<<walker_grid(h, P.n_w), h->wpb * 32, smem, h->stream>>>(h->S, P.L, h->state, dx, dw, P.n_w,
-                                                                            h->prm.a, h->prm.node_rule);
+                                                                            h->prm.a, h->prm.node_rule, h->scr);
   else
     k_init_walkers_m<<<walker_grid(h, P.n_w), h->wpb * 32, smem, h->stream>>>(h->S, P.L, P.M, h->state, dx, dw,
                                                                               P.n_w, h->prm.a, h->prm.node_rule);
@@ -484,6 +494,7 @@ lrdmc_status lrdmc_create(const lrdmc_system* sys, const lrdmc_trial_wf* wf, con
   h->src = (int32_t*)(base + P.o_src);
   h->dstat = (int32_t*)(base + P.o_dstat);
   h->stamps = (unsigned long long*)(base + P.o_stamps);
+  h->scr = (double*)(base + P.o_scr);
   CK(h, cudaMemsetAsync(h->dstat, 0, sizeof(int32_t) * 16, h->stream));
   // launch geometry: up to 4 walkers (warps) per CTA within the shared-memory budget
   int smem_optin = 0;
@@ -500,7 +511,7 @@ lrdmc_status lrdmc_create(const lrdmc_system* sys, const lrdmc_trial_wf* wf, con
   else
     CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_propagate_m, h->wpb * 32, smem_bytes(h)));
   if (bps < 1) return fail(h, LRDMC_ERR_UNSUPPORTED, "propagate kernel does not fit on an SM");
-  h->grid = bps * h->num_sms;
+  h->grid = std::min(bps * h->num_sms, P.scratch_warps / h->wpb);
   st = place_walkers(h, x0, nullptr);
   if (st != LRDMC_OK) return st;
   std::vector<double> buf;
@@ -547,7 +558,8 @@ lrdmc_status lrdmc_propagate(lrdmc_handle h, const lrdmc_schedule* sch) {
   sp.stamps = h->timing ? h->stamps : nullptr;
   const int smem = smem_bytes(h);
   if (h->P.precision == 0)
-    k_propagate<<<walker_grid(h, h->P.n_w), h->wpb * 32, smem, h->stream>>>(h->S, h->P.L, h->state, h->P.n_w, sp);
+    k_propagate<<<walker_grid(h, h->P.n_w), h->wpb * 32, smem, h->stream>>>(h->S, h->P.L, h->state, h->P.n_w, sp,
+                                                                            h->scr);
   else
     k_propagate_m<<<walker_grid(h, h->P.n_w), h->wpb * 32, smem, h->stream>>>(h->S, h->P.L, h->P.M, h->state,
                                                                               h->P.n_w, sp);
@@ -745,7 +757,7 @@ lrdmc_status lrdmc_eval_configs(lrdmc_handle h, int n, const double* x, double* 
   const int smem = smem_bytes(h);
   if (h->P.precision == 0)
     k_eval_configs<<<walker_grid(h, n), h->wpb * 32, smem, h->stream>>>(h->S, h->P.L, h->alt, x, n, h->prm.a,
-                                                                        h->prm.node_rule, ratios, ev, n_node);
+                                                                        h->prm.node_rule, ratios, ev, n_node, h->scr);
   else
     k_eval_configs_m<<<walker_grid(h, n), h->wpb * 32, smem, h->stream>>>(h->S, h->P.L, h->P.M, h->alt, x, n,
                                                                           h->prm.a, h->prm.node_rule, ratios, ev,

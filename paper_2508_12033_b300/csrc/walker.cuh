@@ -174,9 +174,34 @@ __device__ bool warp_gauss_jordan(double* M, int N, int lane) {
   return false;
 }
 
+// Per-warp scratch in global memory (L2 resident): g_i = C^T B[:, i] for every
+// electron [n_e][n_bf], the basis values at every hop position [n_bf][6 n_e]
+// (mu-major so that lanes working on consecutive hops read consecutive words)
+// and the Gauss-Jordan work matrix [n_max][2 n_max].
+struct Scr {
+  double* g;
+  double* chi;
+  double* gj;
+};
+__host__ __device__ inline size_t scratch_doubles(const Layout& L) {
+  return (size_t)L.n_e * L.n_bf + (size_t)L.n_bf * L.n_hop + 2 * (size_t)L.n_max * L.n_max;
+}
+__device__ __forceinline__ Scr warp_scratch(const Layout& L, double* base, int slot) {
+  Scr s;
+  s.g = base + (size_t)slot * scratch_doubles(L);
+  s.chi = s.g + (size_t)L.n_e * L.n_bf;
+  s.gj = s.chi + (size_t)L.n_bf * L.n_hop;
+  return s;
+}
+
+// Squared distance written with explicit FMAs so that every call site rounds
+// identically (incremental updates subtract exactly what was added).
+__device__ __forceinline__ double sqdist(double dx, double dy, double dz) {
+  return fma(dz, dz, fma(dy, dy, dx * dx));
+}
+
 // B^T of both spin blocks from the cached orbital values A[i][k] = phi_k(r_i)
-// (walker block in global memory).  scratch: >= 2 n_max^2 doubles.  Returns
-// true if a block is singular.
+// (walker block in global memory).  Returns true if a block is singular.
 __device__ bool reinvert(const Layout& L, const double* __restrict__ gblk, double* sm, double* scratch, int lane) {
   bool sing = false;
   const double* cache = gblk + L.g_cache;
@@ -190,22 +215,23 @@ __device__ bool reinvert(const Layout& L, const double* __restrict__ gblk, doubl
       const int r = o / (2 * n), c = o - r * 2 * n;
       scratch[o] = c < n ? cache[(e0 + r) * 5 * L.n_max + c] : (c - n == r ? 1.0 : 0.0);
     }
+    __threadfence_block();
     __syncwarp();
     sing |= warp_gauss_jordan(scratch, n, lane);
     for (int o = lane; o < n * n; o += WARP) {
       const int i = o / n, k = o - i * n;
       bt[bto + o] = scratch[k * 2 * n + n + i];
     }
+    __threadfence_block();
     __syncwarp();
   }
   return sing;
 }
 
-// g_i = C^T B[:, i] for every electron.
-__device__ void compute_g(const DevSys& S, const Layout& L, double* sm, int lane) {
+// g_i = C^T B[:, i] for electrons [e0, e1).
+__device__ void compute_g(const DevSys& S, const Layout& L, const double* sm, double* g, int e0, int e1, int lane) {
   const double* bt = sm + L.s_bt;
-  double* g = sm + L.s_g;
-  for (int o = lane; o < L.n_e * L.n_bf; o += WARP) {
+  for (int o = lane + e0 * L.n_bf; o < e1 * L.n_bf; o += WARP) {
     const int i = o / L.n_bf, mu = o - i * L.n_bf;
     const SpinRef sr = spin_ref(L, i);
     const double* brow = bt + sr.bt_off + sr.ii * sr.n;
@@ -213,6 +239,7 @@ __device__ void compute_g(const DevSys& S, const Layout& L, double* sm, int lane
     for (int k = 0; k < sr.n; ++k) acc = fma(__ldg(S.C + (size_t)k * L.n_bf + mu), brow[k], acc);
     g[o] = acc;
   }
+  __threadfence_block();
   __syncwarp();
 }
 
@@ -241,146 +268,26 @@ __device__ __forceinline__ double pade_value(double s, double c, double b) {
   return c * r * rcp_nr(fma(b, r, 1.0));
 }
 
-// Evaluate the lattice-regularised FN Hamiltonian at the walker's current
-// configuration (Appendix D): all hop ratios, b_bar, V_sf, W and e_L.
-// Requires x, B^T, the per-electron potentials in shared memory, the orbital
-// cache in the global block, and g (recomputed here unless g_valid).
-__device__ EvalOut eval_walker(const DevSys& S, const Layout& L, const double* __restrict__ gblk, double* sm,
-                               double a, int node_rule, bool g_valid, const double* T, int lane) {
-  const int ne = L.n_e, nbf = L.n_bf, nmax = L.n_max, nn = S.n_nuc;
-  const double* x = sm + L.s_x;
-  const double* bt = sm + L.s_bt;
-  const double* cache = gblk + L.g_cache;
-  double* g = sm + L.s_g;
-  double* rat = sm + L.s_rat;
-  double* ej = sm + L.s_ej;     // per electron: U_i, grad J (3), lap J, half e-e sum
-  double* ep = sm + L.s_ep;     // per electron: nu_ei, nu^a_ei (kept across hops)
-  double* geo = sm + L.s_geo;   // per (electron, nucleus): d (3), |d|^2 + a^2
-  double* pr2 = sm + L.s_pr2;   // per electron pair: |r_i - r_j|^2 + a^2
-  double* dd = sm + L.s_dd;     // per electron: grad D / D (3), lap D / D
-  const double a2 = a * a;
+// Jastrow pair constant for electrons i, j.
+__device__ __forceinline__ double pair_c(const DevSys& S, const Layout& L, int i, int j) {
+  return ((i < L.n_up) == (j < L.n_up)) ? S.j2_par : S.j2_anti;
+}
 
-  // (1) current-configuration Jastrow sums/derivatives and geometry; G lanes
-  // share one electron, each taking every G-th partner (electrons, then nuclei)
-  {
-    int npad = 1;
-    while (npad < ne) npad <<= 1;
-    const int G = npad >= WARP ? 1 : WARP / npad;
-    const int per = ne - 1 + nn;
-    for (int base = 0; base < ne; base += WARP / G) {
-      const int e = base + lane / G, sub = lane % G;
-      double U = 0.0, gx = 0.0, gy = 0.0, gz = 0.0, LJ = 0.0, vee = 0.0;
-      if (e < ne) {
-        const double xe = x[3 * e], ye = x[3 * e + 1], ze = x[3 * e + 2];
-        const bool up_e = e < L.n_up;
-        for (int t = sub; t < per; t += G) {
-          if (t < ne - 1) {
-            const int j = t < e ? t : t + 1;
-            const double dx = xe - x[3 * j], dy = ye - x[3 * j + 1], dz = ze - x[3 * j + 2];
-            const double s = dx * dx + dy * dy + dz * dz;
-            pr2[e * ne + j] = s + a2;
-            const double c = (up_e == (j < L.n_up)) ? S.j2_par : S.j2_anti;
-            const Pair p = pade(s, c, S.j2_b);
-            const double f = p.up * p.ir;
-            U += p.u;
-            gx = fma(f, dx, gx); gy = fma(f, dy, gy); gz = fma(f, dz, gz);
-            LJ += p.upp + 2.0 * f;
-            vee = fma(0.5, p.ir, vee);
-          } else {
-            const int I = t - (ne - 1);
-            const double dx = xe - __ldg(S.R + 3 * I), dy = ye - __ldg(S.R + 3 * I + 1),
-                         dz = ze - __ldg(S.R + 3 * I + 2);
-            const double s = dx * dx + dy * dy + dz * dz;
-            double* gg = geo + (e * nn + I) * 4;
-            gg[0] = dx; gg[1] = dy; gg[2] = dz; gg[3] = s + a2;
-            const double A = __ldg(S.j1A + I);
-            if (A != 0.0) {
-              const Pair p = pade(s, -A, __ldg(S.j1B + I));
-              const double f = p.up * p.ir;
-              U += p.u;
-              gx = fma(f, dx, gx); gy = fma(f, dy, gy); gz = fma(f, dz, gz);
-              LJ += p.upp + 2.0 * f;
-            }
-          }
-        }
-      }
-      for (int o = G >> 1; o; o >>= 1) {
-        U += __shfl_xor_sync(FULL, U, o);
-        gx += __shfl_xor_sync(FULL, gx, o);
-        gy += __shfl_xor_sync(FULL, gy, o);
-        gz += __shfl_xor_sync(FULL, gz, o);
-        LJ += __shfl_xor_sync(FULL, LJ, o);
-        vee += __shfl_xor_sync(FULL, vee, o);
-      }
-      if (e < ne && sub == 0) {
-        double* q = ej + 6 * e;
-        q[0] = U; q[1] = gx; q[2] = gy; q[3] = gz; q[4] = LJ; q[5] = vee;
-      }
-    }
-  }
-  // (1b) determinant derivatives grad_i D/D, lap_i D/D from the orbital cache
-  for (int o = lane; o < 4 * ne; o += WARP) {
-    const int i = o >> 2, c = o & 3;
-    const SpinRef sr = spin_ref(L, i);
-    const double* brow = bt + sr.bt_off + sr.ii * sr.n;
-    const double* ce = cache + i * 5 * nmax + (c + 1) * nmax;
-    double acc = 0.0;
-    for (int k = 0; k < sr.n; ++k) acc = fma(ce[k], brow[k], acc);
-    dd[o] = acc;
-  }
-  // (2) g_i = C^T B[:, i] unless kept current by the rank-1 updates
-  if (!g_valid) compute_g(S, L, sm, lane);
-  __syncwarp();
-  // (3) every hop: determinant ratio chi(r') . g_i times the Jastrow ratio
-  for (int p = lane; p < 6 * ne; p += WARP) {
-    const int i = p / 6, d = p - 6 * i, ax = d >> 1;
-    const double sa = (d & 1) ? -a : a;
-    const double s2a = sa + sa;
-    const double* gi = g + i * nbf;
-    double det = 0.0, Up = 0.0;
-    for (int I = 0; I < nn; ++I) {
-      const double* gg = geo + (i * nn + I) * 4;
-      const double s = fma(s2a, gg[ax], gg[3]);            // |r' - R_I|^2
-      double dv[3] = {gg[0], gg[1], gg[2]};
-      dv[ax] += sa;
-      const double A = __ldg(S.j1A + I);
-      if (A != 0.0) Up += pade_value(s, -A, __ldg(S.j1B + I));
-      for (int sh = __ldg(S.atom_sh + I); sh < __ldg(S.atom_sh + I + 1); ++sh) {
-        const int l = __ldg(S.sh_l + sh), np = __ldg(S.sh_nprim + sh), off = __ldg(S.sh_off + sh),
-                  bf = __ldg(S.sh_bf + sh);
-        double rad = 0.0;
-        if (l == -1) {
-          const double r = s * rsqrt_nr(s);
-          for (int q = 0; q < np; ++q) rad = fma(__ldg(S.coefs + off + q), exp_tab(-__ldg(S.exps + off + q) * r, T), rad);
-          det = fma(rad, gi[bf], det);
-        } else {
-          for (int q = 0; q < np; ++q) rad = fma(__ldg(S.coefs + off + q), exp_tab(-__ldg(S.exps + off + q) * s, T), rad);
-          if (l == 0)
-            det = fma(rad, gi[bf], det);
-          else
-            det = fma(rad, fma(dv[0], gi[bf], fma(dv[1], gi[bf + 1], dv[2] * gi[bf + 2])), det);
-        }
-      }
-    }
-    const bool up_i = i < L.n_up;
-    const double xia = x[3 * i + ax];
-    for (int j = 0; j < ne; ++j) {
-      if (j == i) continue;
-      const double s = fma(s2a, xia - x[3 * j + ax], pr2[i * ne + j]);
-      const double c = (up_i == (j < L.n_up)) ? S.j2_par : S.j2_anti;
-      Up += pade_value(s, c, S.j2_b);
-    }
-    rat[p] = det * exp_tab(Up - ej[6 * i], T);
-  }
-  __syncwarp();
-  // (4) fixed-node split and regularised potential per electron
+// (4) fixed-node split and regularised potential per electron, from the hop
+// ratios, the Jastrow and determinant derivatives and the potentials.
+__device__ EvalOut assemble(const DevSys& S, const Layout& L, const double* sm, double a, int node_rule, int lane) {
+  const int ne = L.n_e;
+  const double* rat = sm + L.s_rat;
+  const double* ej = sm + L.s_ej;
+  const double* ep = sm + L.s_ep;
+  const double* dd = sm + L.s_dd;
   bool has_node = false;
   for (int i = lane; i < ne; i += WARP)
     for (int d = 0; d < 6; ++d) has_node |= rat[6 * i + d] < 0.0;
   const bool any_node = __any_sync(FULL, has_node);
   double kept = 0.0, negs = 0.0, nuopt = 0.0, vee = 0.0;
   int nnode = 0;
-  const double ia2 = 1.0 / a2;
+  const double ia2 = 1.0 / (a * a);
   for (int i = lane; i < ne; i += WARP) {
     double sr = 0.0;
     bool node = false;
@@ -422,11 +329,323 @@ __device__ EvalOut eval_walker(const DevSys& S, const Layout& L, const double* _
   return e;
 }
 
+// Determinant derivatives grad_i D/D, lap_i D/D for electrons [e0, e1).
+__device__ void det_derivs(const Layout& L, const double* __restrict__ gblk, double* sm, int e0, int e1, int lane) {
+  const double* bt = sm + L.s_bt;
+  const double* cache = gblk + L.g_cache;
+  double* dd = sm + L.s_dd;
+  for (int o = lane + 4 * e0; o < 4 * e1; o += WARP) {
+    const int i = o >> 2, c = o & 3;
+    const SpinRef sr = spin_ref(L, i);
+    const double* brow = bt + sr.bt_off + sr.ii * sr.n;
+    const double* ce = cache + i * 5 * L.n_max + (c + 1) * L.n_max;
+    double acc = 0.0;
+    for (int k = 0; k < sr.n; ++k) acc = fma(ce[k], brow[k], acc);
+    dd[o] = acc;
+  }
+}
+
+// Full evaluation at the walker's current configuration (Appendix D): every
+// hop ratio, b_bar, V_sf, W, e_L.  Requires x, B^T and potentials in shared
+// memory, the orbital cache in the walker block and g current in scr.g.
+// Fills the incremental caches: geometry, pair distances, per-electron
+// Jastrow sums and derivatives, per-hop determinant ratio and Jastrow sums,
+// and (when scr.chi is set) the basis values at every hop.
+__device__ EvalOut eval_full(const DevSys& S, const Layout& L, const double* __restrict__ gblk, double* sm, Scr scr,
+                             double a, int node_rule, const double* T, int lane) {
+  const int ne = L.n_e, nbf = L.n_bf, nn = S.n_nuc, P = L.n_hop;
+  const double* x = sm + L.s_x;
+  const double* g = scr.g;
+  double* rat = sm + L.s_rat;
+  double* ej = sm + L.s_ej;
+  double* geo = sm + L.s_geo;
+  double* pr2 = sm + L.s_pr2;
+  double* hD = sm + L.s_hd;
+  double* hJ1 = sm + L.s_hj1;
+  double* hJ2 = sm + L.s_hj2;
+  const double a2 = a * a;
+  // (1) current-configuration Jastrow sums/derivatives and geometry; G lanes
+  // share one electron, each taking every G-th partner (electrons, then nuclei)
+  {
+    int npad = 1;
+    while (npad < ne) npad <<= 1;
+    const int G = npad >= WARP ? 1 : WARP / npad;
+    const int per = ne - 1 + nn;
+    for (int base = 0; base < ne; base += WARP / G) {
+      const int e = base + lane / G, sub = lane % G;
+      double U = 0.0, gx = 0.0, gy = 0.0, gz = 0.0, LJ = 0.0, vee = 0.0;
+      if (e < ne) {
+        const double xe = x[3 * e], ye = x[3 * e + 1], ze = x[3 * e + 2];
+        for (int t = sub; t < per; t += G) {
+          if (t < ne - 1) {
+            const int j = t < e ? t : t + 1;
+            const double dx = xe - x[3 * j], dy = ye - x[3 * j + 1], dz = ze - x[3 * j + 2];
+            const double s = sqdist(dx, dy, dz);
+            pr2[e * ne + j] = s + a2;
+            const Pair p = pade(s, pair_c(S, L, e, j), S.j2_b);
+            const double f = p.up * p.ir;
+            U += p.u;
+            gx = fma(f, dx, gx); gy = fma(f, dy, gy); gz = fma(f, dz, gz);
+            LJ += p.upp + 2.0 * f;
+            vee = fma(0.5, p.ir, vee);
+          } else {
+            const int I = t - (ne - 1);
+            const double dx = xe - __ldg(S.R + 3 * I), dy = ye - __ldg(S.R + 3 * I + 1),
+                         dz = ze - __ldg(S.R + 3 * I + 2);
+            const double s = sqdist(dx, dy, dz);
+            double* gg = geo + (e * nn + I) * 4;
+            gg[0] = dx; gg[1] = dy; gg[2] = dz; gg[3] = s + a2;
+            const double A = __ldg(S.j1A + I);
+            if (A != 0.0) {
+              const Pair p = pade(s, -A, __ldg(S.j1B + I));
+              const double f = p.up * p.ir;
+              U += p.u;
+              gx = fma(f, dx, gx); gy = fma(f, dy, gy); gz = fma(f, dz, gz);
+              LJ += p.upp + 2.0 * f;
+            }
+          }
+        }
+      }
+      for (int o = G >> 1; o; o >>= 1) {
+        U += __shfl_xor_sync(FULL, U, o);
+        gx += __shfl_xor_sync(FULL, gx, o);
+        gy += __shfl_xor_sync(FULL, gy, o);
+        gz += __shfl_xor_sync(FULL, gz, o);
+        LJ += __shfl_xor_sync(FULL, LJ, o);
+        vee += __shfl_xor_sync(FULL, vee, o);
+      }
+      if (e < ne && sub == 0) {
+        double* q = ej + 6 * e;
+        q[0] = U; q[1] = gx; q[2] = gy; q[3] = gz; q[4] = LJ; q[5] = vee;
+      }
+    }
+  }
+  det_derivs(L, gblk, sm, 0, ne, lane);
+  __syncwarp();
+  // (3) every hop: basis values (kept in scr.chi), determinant ratio
+  // chi(r') . g_i, one-body and pair Jastrow sums
+  for (int p = lane; p < P; p += WARP) {
+    const int i = p / 6, d = p - 6 * i, ax = d >> 1;
+    const double sa = (d & 1) ? -a : a;
+    const double s2a = sa + sa;
+    const double* gi = g + i * nbf;
+    double det = 0.0, J1 = 0.0, J2 = 0.0;
+    for (int I = 0; I < nn; ++I) {
+      const double* gg = geo + (i * nn + I) * 4;
+      const double s = fma(s2a, gg[ax], gg[3]);            // |r' - R_I|^2
+      double dv[3] = {gg[0], gg[1], gg[2]};
+      dv[ax] += sa;
+      const double A = __ldg(S.j1A + I);
+      if (A != 0.0) J1 += pade_value(s, -A, __ldg(S.j1B + I));
+      for (int sh = __ldg(S.atom_sh + I); sh < __ldg(S.atom_sh + I + 1); ++sh) {
+        const int l = __ldg(S.sh_l + sh), np = __ldg(S.sh_nprim + sh), off = __ldg(S.sh_off + sh),
+                  bf = __ldg(S.sh_bf + sh);
+        const double arg = l == -1 ? s * rsqrt_nr(s) : s;
+        double rad = 0.0;
+        for (int q = 0; q < np; ++q) rad = fma(__ldg(S.coefs + off + q), exp_tab(-__ldg(S.exps + off + q) * arg, T), rad);
+        if (l != 1) {
+          det = fma(rad, gi[bf], det);
+          if (scr.chi) scr.chi[(size_t)bf * P + p] = rad;
+        } else {
+          const double c0 = dv[0] * rad, c1 = dv[1] * rad, c2 = dv[2] * rad;
+          det = fma(c0, gi[bf], fma(c1, gi[bf + 1], fma(c2, gi[bf + 2], det)));
+          if (scr.chi) {
+            scr.chi[(size_t)bf * P + p] = c0;
+            scr.chi[(size_t)(bf + 1) * P + p] = c1;
+            scr.chi[(size_t)(bf + 2) * P + p] = c2;
+          }
+        }
+      }
+    }
+    const double xia = x[3 * i + ax];
+    for (int j = 0; j < ne; ++j) {
+      if (j == i) continue;
+      J2 += pade_value(fma(s2a, xia - x[3 * j + ax], pr2[i * ne + j]), pair_c(S, L, i, j), S.j2_b);
+    }
+    hD[p] = det;
+    hJ1[p] = J1;
+    hJ2[p] = J2;
+    rat[p] = det * exp_tab(J1 + J2 - ej[6 * i], T);
+  }
+  __threadfence_block();
+  __syncwarp();
+  return assemble(S, L, sm, a, node_rule, lane);
+}
+
+// Incremental evaluation after electron m hopped from xo (kept at s_xo) to its
+// position in x.  Everything that does not depend on electron m keeps its
+// cached value: the basis values at the other electrons' hops, their one-body
+// Jastrow sums and, outside m's spin block, their determinant ratios.  With
+// all_blocks (after a from-scratch inversion changed B of both blocks) the
+// determinant ratios and derivatives of every electron are refreshed from the
+// cached basis values.
+__device__ EvalOut eval_incr(const DevSys& S, const Layout& L, const double* __restrict__ gblk, double* sm, Scr scr,
+                             int m, bool all_blocks, double a, int node_rule, const double* T, int lane) {
+  const int ne = L.n_e, nbf = L.n_bf, nn = S.n_nuc, P = L.n_hop;
+  const double* x = sm + L.s_x;
+  const double* xo = sm + L.s_xo;
+  const double* g = scr.g;
+  double* rat = sm + L.s_rat;
+  double* ej = sm + L.s_ej;
+  double* geo = sm + L.s_geo;
+  double* pr2 = sm + L.s_pr2;
+  double* hD = sm + L.s_hd;
+  double* hJ1 = sm + L.s_hj1;
+  double* hJ2 = sm + L.s_hj2;
+  double* tmp = sm + L.s_tmp;
+  const double a2 = a * a;
+  const int per = ne - 1 + nn;
+  const double xm = x[3 * m], ym = x[3 * m + 1], zm = x[3 * m + 2];
+  // (A) electron m: geometry and its Jastrow sums from scratch
+  {
+    double U = 0.0, gx = 0.0, gy = 0.0, gz = 0.0, LJ = 0.0, vee = 0.0;
+    for (int t = lane; t < per; t += WARP) {
+      if (t < ne - 1) {
+        const int j = t < m ? t : t + 1;
+        const double dx = xm - x[3 * j], dy = ym - x[3 * j + 1], dz = zm - x[3 * j + 2];
+        const double s = sqdist(dx, dy, dz);
+        pr2[m * ne + j] = s + a2;
+        pr2[j * ne + m] = s + a2;
+        const Pair p = pade(s, pair_c(S, L, m, j), S.j2_b);
+        const double f = p.up * p.ir;
+        U += p.u;
+        gx = fma(f, dx, gx); gy = fma(f, dy, gy); gz = fma(f, dz, gz);
+        LJ += p.upp + 2.0 * f;
+        vee = fma(0.5, p.ir, vee);
+      } else {
+        const int I = t - (ne - 1);
+        const double dx = xm - __ldg(S.R + 3 * I), dy = ym - __ldg(S.R + 3 * I + 1), dz = zm - __ldg(S.R + 3 * I + 2);
+        const double s = sqdist(dx, dy, dz);
+        double* gg = geo + (m * nn + I) * 4;
+        gg[0] = dx; gg[1] = dy; gg[2] = dz; gg[3] = s + a2;
+        const double A = __ldg(S.j1A + I);
+        if (A != 0.0) {
+          const Pair p = pade(s, -A, __ldg(S.j1B + I));
+          const double f = p.up * p.ir;
+          U += p.u;
+          gx = fma(f, dx, gx); gy = fma(f, dy, gy); gz = fma(f, dz, gz);
+          LJ += p.upp + 2.0 * f;
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      U += __shfl_xor_sync(FULL, U, o);
+      gx += __shfl_xor_sync(FULL, gx, o);
+      gy += __shfl_xor_sync(FULL, gy, o);
+      gz += __shfl_xor_sync(FULL, gz, o);
+      LJ += __shfl_xor_sync(FULL, LJ, o);
+      vee += __shfl_xor_sync(FULL, vee, o);
+    }
+    if (lane == 0) {
+      double* q = ej + 6 * m;
+      q[0] = U; q[1] = gx; q[2] = gy; q[3] = gz; q[4] = LJ; q[5] = vee;
+    }
+  }
+  // (B) every other electron: swap its pair term with m (old -> new position)
+  for (int i = lane; i < ne; i += WARP) {
+    if (i == m) continue;
+    const double c = pair_c(S, L, i, m);
+    const double xi = x[3 * i], yi = x[3 * i + 1], zi = x[3 * i + 2];
+    const double ox = xi - xo[0], oy = yi - xo[1], oz = zi - xo[2];
+    const double nx = xi - xm, ny = yi - ym, nz = zi - zm;
+    const Pair po = pade(sqdist(ox, oy, oz), c, S.j2_b);
+    const Pair pn = pade(sqdist(nx, ny, nz), c, S.j2_b);
+    const double fo = po.up * po.ir, fn = pn.up * pn.ir;
+    double* q = ej + 6 * i;
+    q[0] += pn.u - po.u;
+    q[1] += fn * nx - fo * ox;
+    q[2] += fn * ny - fo * oy;
+    q[3] += fn * nz - fo * oz;
+    q[4] += (pn.upp + 2.0 * fn) - (po.upp + 2.0 * fo);
+    q[5] += 0.5 * (pn.ir - po.ir);
+  }
+  // (C) determinant derivatives of the refreshed spin block(s)
+  const SpinRef srm = spin_ref(L, m);
+  const int b0 = all_blocks ? 0 : m - srm.ii, b1 = all_blocks ? ne : m - srm.ii + srm.n;
+  det_derivs(L, gblk, sm, b0, b1, lane);
+  __threadfence_block();
+  __syncwarp();
+  // (D) basis values at m's six hops, one (hop, shell) per lane, and m's
+  // Jastrow pair / one-body terms, one (hop, partner) per lane
+  for (int o = lane; o < 6 * S.n_shell; o += WARP) {
+    const int d = o / S.n_shell, sh = o - d * S.n_shell, ax = d >> 1;
+    const double sa = (d & 1) ? -a : a;
+    const int I = __ldg(S.sh_atom + sh);
+    const double* gg = geo + (m * nn + I) * 4;
+    const double s = fma(sa + sa, gg[ax], gg[3]);
+    const int l = __ldg(S.sh_l + sh), np = __ldg(S.sh_nprim + sh), off = __ldg(S.sh_off + sh), bf = __ldg(S.sh_bf + sh);
+    const double arg = l == -1 ? s * rsqrt_nr(s) : s;
+    double rad = 0.0;
+    for (int q = 0; q < np; ++q) rad = fma(__ldg(S.coefs + off + q), exp_tab(-__ldg(S.exps + off + q) * arg, T), rad);
+    const int p = 6 * m + d;
+    if (l != 1) {
+      scr.chi[(size_t)bf * P + p] = rad;
+    } else {
+      for (int k = 0; k < 3; ++k) scr.chi[(size_t)(bf + k) * P + p] = (gg[k] + (k == ax ? sa : 0.0)) * rad;
+    }
+  }
+  for (int o = lane; o < 6 * per; o += WARP) {
+    const int d = o / per, t = o - d * per, ax = d >> 1;
+    const double sa = (d & 1) ? -a : a;
+    double v = 0.0;
+    if (t < ne - 1) {
+      const int j = t < m ? t : t + 1;
+      v = pade_value(fma(sa + sa, x[3 * m + ax] - x[3 * j + ax], pr2[m * ne + j]), pair_c(S, L, m, j), S.j2_b);
+    } else {
+      const int I = t - (ne - 1);
+      const double A = __ldg(S.j1A + I);
+      const double* gg = geo + (m * nn + I) * 4;
+      if (A != 0.0) v = pade_value(fma(sa + sa, gg[ax], gg[3]), -A, __ldg(S.j1B + I));
+    }
+    tmp[o] = v;
+  }
+  __threadfence_block();
+  __syncwarp();
+  if (lane < 6) {
+    double J1 = 0.0, J2 = 0.0;
+    for (int t = 0; t < per; ++t) {
+      if (t < ne - 1) J2 += tmp[lane * per + t];
+      else J1 += tmp[lane * per + t];
+    }
+    hJ1[6 * m + lane] = J1;
+    hJ2[6 * m + lane] = J2;
+  }
+  // (E) determinant ratios of the refreshed block(s) from the cached basis values
+  for (int p = lane + 6 * b0; p < 6 * b1; p += WARP) {
+    const int i = p / 6;
+    const double* gi = g + i * nbf;
+    double det = 0.0;
+    for (int mu = 0; mu < nbf; ++mu) det = fma(scr.chi[(size_t)mu * P + p], gi[mu], det);
+    hD[p] = det;
+  }
+  // (F) pair Jastrow sums of the other electrons' hops: swap the term with m
+  for (int p = lane; p < P; p += WARP) {
+    const int i = p / 6;
+    if (i == m) continue;
+    const int d = p - 6 * i, ax = d >> 1;
+    const double s2a = (d & 1) ? -2.0 * a : 2.0 * a;
+    const double c = pair_c(S, L, i, m);
+    const double xia = x[3 * i + ax];
+    const double so = sqdist(x[3 * i] - xo[0], x[3 * i + 1] - xo[1], x[3 * i + 2] - xo[2]) + a2;
+    const double vo = pade_value(fma(s2a, xia - xo[ax], so), c, S.j2_b);
+    const double vn = pade_value(fma(s2a, xia - x[3 * m + ax], pr2[i * ne + m]), c, S.j2_b);
+    hJ2[p] += vn - vo;
+  }
+  __threadfence_block();
+  __syncwarp();
+  // (G) all hop ratios
+  for (int p = lane; p < P; p += WARP) rat[p] = hD[p] * exp_tab(hJ1[p] + hJ2[p] - ej[6 * (p / 6)], T);
+  __threadfence_block();
+  __syncwarp();
+  return assemble(S, L, sm, a, node_rule, lane);
+}
+
 // Build the orbital cache and potentials at every electron, invert both
 // Slater blocks and evaluate.  x must already be in shared memory.
-__device__ EvalOut init_walker(const DevSys& S, const Layout& L, double* __restrict__ gblk, double* sm, double a,
-                               int node_rule, const double* T, int lane, bool& singular) {
-  double* chi5 = sm + L.s_geo;     // scratch while no evaluation is in progress
+__device__ EvalOut init_walker(const DevSys& S, const Layout& L, double* __restrict__ gblk, double* sm, Scr scr,
+                               double a, int node_rule, const double* T, int lane, bool& singular) {
+  double* chi5 = sm + L.s_tmp;     // scratch while no evaluation is in progress
   double* phi5 = sm + L.s_phi5;
   double* cache = gblk + L.g_cache;
   const double* x = sm + L.s_x;
@@ -445,47 +664,59 @@ __device__ EvalOut init_walker(const DevSys& S, const Layout& L, double* __restr
     __syncwarp();
   }
   __threadfence_block();
-  singular = reinvert(L, gblk, sm, sm + L.s_g, lane);
-  return eval_walker(S, L, gblk, sm, a, node_rule, false, T, lane);
+  singular = reinvert(L, gblk, sm, scr.gj, lane);
+  compute_g(S, L, sm, scr.g, 0, L.n_e, lane);
+  return eval_full(S, L, gblk, sm, scr, a, node_rule, T, lane);
 }
 
 // Heat-bath choice over the kept hops (r > 0) in the order p = 6 i + d: the
 // first p whose running sum exceeds u * total; the last kept hop if rounding
-// leaves none; -1 without kept hops.  Sequential sum, as the method states it.
+// leaves none; -1 without kept hops.  Running sums by warp scans over chunks
+// of 32 hops.
 __device__ int choose_hop(const double* rat, int n_hop, double u, int lane) {
-  int choice = -1;
-  if (lane == 0) {
-    double total = 0.0;
-    for (int p = 0; p < n_hop; ++p) total += rat[p] > 0.0 ? rat[p] : 0.0;
-    if (total > 0.0) {
-      const double t = u * total;
-      double run = 0.0;
-      int last = -1;
-      for (int p = 0; p < n_hop; ++p) {
-        const double k = rat[p] > 0.0 ? rat[p] : 0.0;
-        if (k > 0.0) last = p;
-        run += k;
-        if (run > t) { choice = p; break; }
-      }
-      if (choice < 0) choice = last;
-    }
+  double total = 0.0;
+  for (int c = 0; c < n_hop; c += WARP) {
+    const int p = c + lane;
+    double k = (p < n_hop && rat[p] > 0.0) ? rat[p] : 0.0;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) k += __shfl_xor_sync(FULL, k, o);
+    total += k;
   }
-  return __shfl_sync(FULL, choice, 0);
+  if (!(total > 0.0)) return -1;
+  const double t = u * total;
+  double base = 0.0;
+  int last = -1;
+  for (int c = 0; c < n_hop; c += WARP) {
+    const int p = c + lane;
+    const double k = (p < n_hop && rat[p] > 0.0) ? rat[p] : 0.0;
+    double incl = k;
+#pragma unroll
+    for (int o = 1; o < WARP; o <<= 1) {
+      const double v = __shfl_up_sync(FULL, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const unsigned hit = __ballot_sync(FULL, base + incl > t);
+    if (hit) return c + __ffs(hit) - 1;
+    const unsigned kept = __ballot_sync(FULL, k > 0.0);
+    if (kept) last = c + 31 - __clz(kept);
+    base += __shfl_sync(FULL, incl, WARP - 1);
+  }
+  return last;
 }
 
 // Apply hop p: orbital derivatives at the moved electron, Sherman-Morrison
-// update of its spin block (and of g by the same factors when g_valid),
-// cache, potential and position update.
-__device__ void apply_hop(const DevSys& S, const Layout& L, double* __restrict__ gblk, double* sm, int p, double a,
-                          bool g_valid, const double* T, int lane) {
+// update of its spin block and of g by the same factors, cache, potential and
+// position update; the old position goes to s_xo.
+__device__ void apply_hop(const DevSys& S, const Layout& L, double* __restrict__ gblk, double* sm, Scr scr, int p,
+                          double a, const double* T, int lane) {
   double* x = sm + L.s_x;
   double* bt = sm + L.s_bt;
   double* cache = gblk + L.g_cache;
   double* phi5 = sm + L.s_phi5;
   double* f = sm + L.s_u;
   double* row = sm + L.s_row;
-  double* chi5 = sm + L.s_geo;     // geometry is rebuilt by the next evaluation
-  double* g = sm + L.s_g;
+  double* chi5 = sm + L.s_tmp;     // per-hop scratch, refilled by the next evaluation
+  double* g = scr.g;
   double* grow = chi5 + 5 * L.n_bf;
   const int i = p / 6, d = p - 6 * i;
   double q[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
@@ -501,8 +732,8 @@ __device__ void apply_hop(const DevSys& S, const Layout& L, double* __restrict__
     f[j] = acc;
   }
   for (int k = lane; k < n; k += WARP) row[k] = B[sr.ii * n + k];
-  if (g_valid)
-    for (int mu = lane; mu < L.n_bf; mu += WARP) grow[mu] = g[i * L.n_bf + mu];
+  for (int mu = lane; mu < L.n_bf; mu += WARP) grow[mu] = g[i * L.n_bf + mu];
+  __threadfence_block();
   __syncwarp();
   const double invR = 1.0 / f[sr.ii];
   __syncwarp();
@@ -513,18 +744,18 @@ __device__ void apply_hop(const DevSys& S, const Layout& L, double* __restrict__
     const int j = o / n, k = o - j * n;
     B[o] = fma(-row[k], f[j], B[o]);
   }
-  if (g_valid) {
-    const int e0 = i - sr.ii;
-    for (int o = lane; o < n * L.n_bf; o += WARP) {
-      const int j = o / L.n_bf, mu = o - j * L.n_bf;
-      double* gj = g + (e0 + j) * L.n_bf + mu;
-      *gj = fma(-grow[mu], f[j], *gj);
-    }
+  const int e0 = i - sr.ii;
+  for (int o = lane; o < n * L.n_bf; o += WARP) {
+    const int j = o / L.n_bf, mu = o - j * L.n_bf;
+    double* gj = g + (e0 + j) * L.n_bf + mu;
+    *gj = fma(-grow[mu], f[j], *gj);
   }
   for (int o = lane; o < 5 * L.n_max; o += WARP) cache[i * 5 * L.n_max + o] = phi5[o];
   double nu, nucap;
   electron_potentials(S, q, a, lane, nu, nucap);
   if (lane == 0) {
+    double* xo = sm + L.s_xo;
+    xo[0] = x[3 * i]; xo[1] = x[3 * i + 1]; xo[2] = x[3 * i + 2];
     x[3 * i] = q[0];
     x[3 * i + 1] = q[1];
     x[3 * i + 2] = q[2];
@@ -590,18 +821,21 @@ __device__ __forceinline__ void store_block(const Layout& L, double* __restrict_
 
 // Place walkers at x_in (n x n_e x 3), build caches, invert and evaluate.
 __global__ void k_init_walkers(DevSys S, Layout L, double* __restrict__ state, const double* __restrict__ x_in,
-                               const double* __restrict__ w_in, int n, double a, int node_rule) {
+                               const double* __restrict__ w_in, int n, double a, int node_rule, double* scratch) {
   extern __shared__ double smem[];
   const double* T = stage_table(S, smem);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   double* sm = smem + EXP_TAB + wib * L.s_stride;
   const int nwarps = gridDim.x * (blockDim.x >> 5);
-  for (int w = blockIdx.x * (blockDim.x >> 5) + wib; w < n; w += nwarps) {
+  const int slot = blockIdx.x * (blockDim.x >> 5) + wib;
+  Scr scr = warp_scratch(L, scratch, slot);
+  scr.chi = nullptr;
+  for (int w = slot; w < n; w += nwarps) {
     double* gblk = state + (size_t)w * L.g_stride;
     for (int o = lane; o < 3 * L.n_e; o += WARP) sm[L.s_x + o] = x_in[(size_t)w * 3 * L.n_e + o];
     __syncwarp();
     bool sing = false;
-    const EvalOut e = init_walker(S, L, gblk, sm, a, node_rule, T, lane, sing);
+    const EvalOut e = init_walker(S, L, gblk, sm, scr, a, node_rule, T, lane, sing);
     if (lane == 0) {
       double* sc = sm + L.s_sc;
       for (int k = 0; k < SC_COUNT; ++k) sc[k] = 0.0;
@@ -619,20 +853,23 @@ __global__ void k_init_walkers(DevSys S, Layout L, double* __restrict__ state, c
 
 // Evaluate arbitrary configurations without touching the walkers (the orbital
 // cache of each configuration goes to scratch walker blocks).
-__global__ void k_eval_configs(DevSys S, Layout L, double* __restrict__ scratch, const double* __restrict__ x_in,
-                               int n, double a, int node_rule, double* __restrict__ ratios, double* __restrict__ ev,
-                               int32_t* __restrict__ n_node) {
+__global__ void k_eval_configs(DevSys S, Layout L, double* __restrict__ blocks, const double* __restrict__ x_in, int n,
+                               double a, int node_rule, double* __restrict__ ratios, double* __restrict__ ev,
+                               int32_t* __restrict__ n_node, double* scratch) {
   extern __shared__ double smem[];
   const double* T = stage_table(S, smem);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   double* sm = smem + EXP_TAB + wib * L.s_stride;
   const int nwarps = gridDim.x * (blockDim.x >> 5);
-  for (int w = blockIdx.x * (blockDim.x >> 5) + wib; w < n; w += nwarps) {
-    double* gblk = scratch + (size_t)w * L.g_stride;
+  const int slot = blockIdx.x * (blockDim.x >> 5) + wib;
+  Scr scr = warp_scratch(L, scratch, slot);
+  scr.chi = nullptr;
+  for (int w = slot; w < n; w += nwarps) {
+    double* gblk = blocks + (size_t)w * L.g_stride;
     for (int o = lane; o < 3 * L.n_e; o += WARP) sm[L.s_x + o] = x_in[(size_t)w * 3 * L.n_e + o];
     __syncwarp();
     bool sing = false;
-    const EvalOut e = init_walker(S, L, gblk, sm, a, node_rule, T, lane, sing);
+    const EvalOut e = init_walker(S, L, gblk, sm, scr, a, node_rule, T, lane, sing);
     for (int o = lane; o < L.n_hop; o += WARP) ratios[(size_t)w * L.n_hop + o] = sm[L.s_rat + o];
     if (lane == 0) {
       ev[4 * (size_t)w] = e.bbar;
@@ -647,15 +884,18 @@ __global__ void k_eval_configs(DevSys S, Layout L, double* __restrict__ scratch,
 
 // One branching interval for every walker (Algorithm 2 for kind 1,
 // Algorithm 1 for kind 0).  The walker state stays in shared memory for the
-// whole interval.
-__global__ void k_propagate(DevSys S, Layout L, double* __restrict__ state, int n_w, StepParams P) {
+// whole interval; the first hop of an interval evaluates the new
+// configuration in full and fills the caches, later hops update them.
+__global__ void k_propagate(DevSys S, Layout L, double* __restrict__ state, int n_w, StepParams P, double* scratch) {
   extern __shared__ double smem[];
   const double* T = stage_table(S, smem);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   double* sm = smem + EXP_TAB + wib * L.s_stride;
   double* sc = sm + L.s_sc;
   const int nwarps = gridDim.x * (blockDim.x >> 5);
-  for (int w = blockIdx.x * (blockDim.x >> 5) + wib; w < n_w; w += nwarps) {
+  const int slot = blockIdx.x * (blockDim.x >> 5) + wib;
+  const Scr scr = warp_scratch(L, scratch, slot);
+  for (int w = slot; w < n_w; w += nwarps) {
     const unsigned long long t_start = global_ns();
     double* gblk = state + (size_t)w * L.g_stride;
     load_block(L, gblk, sm, lane);
@@ -663,7 +903,7 @@ __global__ void k_propagate(DevSys S, Layout L, double* __restrict__ state, int 
     double bbar = sc[SC_BBAR], Wd = sc[SC_WDIAG], eL = sc[SC_EL];
     uint32_t status = (uint32_t)sc[SC_STATUS];
     int moves = 0, since = (int)sc[SC_SINCE];
-    bool g_valid = false;
+    bool g_valid = false, cached = false;
     for (int k = 0;; ++k) {
       if (P.kind == 1 && k >= P.n_proj) break;
       double u_tau, u_move;
@@ -691,18 +931,25 @@ __global__ void k_propagate(DevSys S, Layout L, double* __restrict__ state, int 
         status |= ST_STUCK;
       } else {
         if (!g_valid) {
-          compute_g(S, L, sm, lane);
+          compute_g(S, L, sm, scr.g, 0, L.n_e, lane);
           g_valid = true;
         }
-        apply_hop(S, L, gblk, sm, p, P.a, g_valid, T, lane);
+        apply_hop(S, L, gblk, sm, scr, p, P.a, T, lane);
         ++moves;
+        bool reinv = false;
         if (++since >= P.reinv_period) {
-          if (reinvert(L, gblk, sm, sm + L.s_g, lane)) status |= ST_SINGULAR;
+          if (reinvert(L, gblk, sm, scr.gj, lane)) status |= ST_SINGULAR;
+          compute_g(S, L, sm, scr.g, 0, L.n_e, lane);
           since = 0;
-          g_valid = false;
+          reinv = true;
         }
-        const EvalOut e = eval_walker(S, L, gblk, sm, P.a, P.node_rule, g_valid, T, lane);
-        g_valid = true;
+        EvalOut e;
+        if (!cached) {
+          e = eval_full(S, L, gblk, sm, scr, P.a, P.node_rule, T, lane);
+          cached = true;
+        } else {
+          e = eval_incr(S, L, gblk, sm, scr, p / 6, reinv, P.a, P.node_rule, T, lane);
+        }
         bbar = e.bbar;
         Wd = e.W;
         eL = e.eL;

@@ -80,7 +80,8 @@ def test_workspace_sizing_and_validation(lib):
     nb = ctypes.c_size_t()
     assert lib.lrdmc_workspace_bytes(ctypes.byref(s), ctypes.byref(w), ctypes.byref(p), ctypes.byref(nb)) == 0
     # two walker buffers dominate: ~2 * 4096 * (walker block) bytes
-    assert 2 * 4096 * 8 * (48 + 128 + 640 + 96) < nb.value < 2 * 4096 * 8 * 2000
+    # plus the per-warp scratch (g, basis values at every hop, Gauss-Jordan matrix)
+    assert 2 * 4096 * 8 * (48 + 128 + 640 + 96) < nb.value < 2 * 4096 * 8 * 2000 + 2368 * 8 * 7000
     for bad in (dict(a=-1.0), dict(node_rule=5), dict(reinv_period=0), dict(precision=2)):
         s, w, p, keep = _structs(W.h2_sto3g(), **bad)
         assert lib.lrdmc_workspace_bytes(ctypes.byref(s), ctypes.byref(w), ctypes.byref(p),
