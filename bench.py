@@ -41,29 +41,50 @@ FP64_PEAK_GFLOPS = 1250.0      # nominal B300 FP64 rate (profiling recipe table)
 SLOT_EXP, SLOT_RSQ, SLOT_RCP, SLOT_SQRT, SLOT_ERF = 10.0, 8.9, 4.9, 11.7, 46.4
 
 
-def algorithmic_slots_per_walker_step(n_e, n_nuc, n_bf, n_prim, n_sig, n_s_shell, n_p_shell, one_body=True):
-    """FP64 work per walker-step of the load-balanced step as formulated in the
-    propagate kernel, in FMA slots (one FP64 add/mul/FMA = 1; a function counts
-    its pipe cost above).
+def full_eval_slots(n_e, n_nuc, n_bf, n_prim, n_sig, n_s_shell, n_p_shell, one_body=True):
+    """FP64 slots of one full evaluation (every hop of every electron).
 
-    Per hop (6 n_e of them): per nucleus the displaced squared distance and
-    offset (2) and, with a one-body Jastrow, its Pade term (rsqrt + reciprocal +
-    5); per primitive one exponential + 2; per s / p shell 1 / 4 for the dot
-    with g_i; per other electron the displaced distance (2) + Pade term; the
-    Jastrow exponential + 2.  Per electron (current configuration): per
-    partner (electrons and nuclei) distance (6), Pade value and derivatives
-    (rsqrt + reciprocal + 12), accumulation (7); determinant derivatives
-    4 n_sig; assembly 25.  Per applied hop: basis value/gradient/Laplacian
-    (exp + 10 per primitive), 5 n_bf n_sig contraction, 2 n_sig^2
-    Sherman-Morrison, n_sig n_bf update of g, potentials (sqrt + erf +
-    2 reciprocals + 6 per nucleus)."""
+    Per hop (6 n_e): per nucleus the displaced squared distance and offset (2)
+    and, with a one-body Jastrow, its Pade term (rsqrt + reciprocal + 5); per
+    primitive one exponential + 2; per s / p shell 1 / 4 for the dot with g_i;
+    per other electron 2 + Pade term; the Jastrow exponential + 2.  Per
+    electron: per partner (electrons and nuclei) distance (6), Pade value and
+    derivatives (rsqrt + reciprocal + 12), accumulation (7); determinant
+    derivatives 4 n_sig; assembly 25."""
     pade = SLOT_RSQ + SLOT_RCP + 5
     per_hop = (n_nuc * (2 + (pade if one_body else 0)) + n_prim * (SLOT_EXP + 2) + n_s_shell + 4 * n_p_shell
                + (n_e - 1) * (2 + pade) + SLOT_EXP + 2)
     per_elec = (n_e - 1 + n_nuc) * (6 + SLOT_RSQ + SLOT_RCP + 12 + 7) + 4 * n_sig + 25
+    return 6 * n_e * per_hop + n_e * per_elec
+
+
+def algorithmic_slots_per_walker_step(n_e, n_nuc, n_bf, n_prim, n_sig, n_s_shell, n_p_shell, one_body=True,
+                                      n_proj=20):
+    """FP64 work per walker-step of the load-balanced step as formulated in the
+    propagate kernel, in FMA slots (one FP64 add/mul/FMA = 1; a function counts
+    its pipe cost above).
+
+    The first hop of an interval is followed by a full evaluation; every other
+    hop of electron m by an incremental one: m's pair and nucleus Jastrow terms
+    with derivatives (A), the other electrons' pair terms with m swapped old ->
+    new (B, two Pade evaluations with derivatives each), determinant
+    derivatives of m's spin block (C, 4 n_sig^2), basis values at m's six hops
+    and their Jastrow terms (D), determinant ratios of the block's hops from the
+    cached basis values (E, 6 n_sig n_bf), the pair Jastrow term with m swapped
+    for the other electrons' hops (F, two Pade values each), every hop's
+    Jastrow exponential (G) and the assembly.  Every hop also pays the move:
+    basis value/gradient/Laplacian at one point, 5 n_bf n_sig contraction,
+    2 n_sig^2 Sherman-Morrison, n_sig n_bf update of g, potentials."""
+    pade = SLOT_RSQ + SLOT_RCP + 5
+    pade_d = 6 + SLOT_RSQ + SLOT_RCP + 12 + 7
+    per = n_e - 1 + n_nuc
+    incr = (per * pade_d + (n_e - 1) * 2 * pade_d + 4 * n_sig * n_sig
+            + 6 * (n_prim * (SLOT_EXP + 2) + 3 * (n_s_shell + n_p_shell) + 3 * n_p_shell) + 6 * per * (pade + 2)
+            + 6 * n_sig * n_bf + 6 * (n_e - 1) * 2 * (pade + 8) + 6 * n_e * (SLOT_EXP + 3) + 30 * n_e)
     move = (n_prim * (SLOT_EXP + 10) + 5 * n_bf * n_sig + 2 * n_sig * n_sig + n_sig * n_bf
             + n_nuc * (SLOT_SQRT + SLOT_ERF + 2 * SLOT_RCP + 6))
-    return 6 * n_e * per_hop + n_e * per_elec + move
+    full = full_eval_slots(n_e, n_nuc, n_bf, n_prim, n_sig, n_s_shell, n_p_shell, one_body) + n_e * n_bf * n_sig
+    return move + ((n_proj - 1) * incr + full) / n_proj
 
 
 # ----------------------------------------------------------------- clocks
@@ -201,7 +222,7 @@ def run_gpu(args, rank, world):
     # roofline of the dominant kernel (the propagate kernel: one launch per step)
     slots = algorithmic_slots_per_walker_step(s.n_elec, s.n_nuc, s.n_bf, s.n_prim_eval, max(s.n_up, s.n_dn),
                                               int(np.sum(s.shell_l == 0)), int(np.sum(s.shell_l == 1)),
-                                              bool(np.any(s.j1_A != 0)))
+                                              bool(np.any(s.j1_A != 0)), N_PROJ)
     prop_s = statistics.mean(prop_ms) / 1e3
     achieved = 2.0 * slots * ws_per_step / prop_s / 1e9      # GFLOP/s, FP64-equivalent
     # conventional schedule at the same mean hops per interval (tau = N_proj / <b_bar>)
