@@ -307,7 +307,8 @@ static lrdmc_status place_walkers(lrdmc_handle h, const double* x, const double*
                                                                             h->prm.a, h->prm.node_rule, h->scr);
   else
     k_init_walkers_m<<<walker_grid(h, P.n_w), h->wpb * 32, smem, h->stream>>>(h->S, P.L, P.M, h->state, dx, dw,
-                                                                              P.n_w, h->prm.a, h->prm.node_rule);
+                                                                              P.n_w, h->prm.a, h->prm.node_rule,
+                                                                              h->scr);
   LAUNCHED(h);
   CK(h, cudaStreamSynchronize(h->stream));
   return LRDMC_OK;
@@ -562,7 +563,7 @@ lrdmc_status lrdmc_propagate(lrdmc_handle h, const lrdmc_schedule* sch) {
                                                                             h->scr);
   else
     k_propagate_m<<<walker_grid(h, h->P.n_w), h->wpb * 32, smem, h->stream>>>(h->S, h->P.L, h->P.M, h->state,
-                                                                              h->P.n_w, sp);
+                                                                              h->P.n_w, sp, h->scr);
   LAUNCHED(h);
   h->last_kind = sch->kind;
   return LRDMC_OK;
@@ -761,7 +762,7 @@ lrdmc_status lrdmc_eval_configs(lrdmc_handle h, int n, const double* x, double* 
   else
     k_eval_configs_m<<<walker_grid(h, n), h->wpb * 32, smem, h->stream>>>(h->S, h->P.L, h->P.M, h->alt, x, n,
                                                                           h->prm.a, h->prm.node_rule, ratios, ev,
-                                                                          n_node);
+                                                                          n_node, h->scr);
   LAUNCHED(h);
   return LRDMC_OK;
 }

@@ -36,14 +36,15 @@ namespace lrdmc {
 // arrays at even offsets).  Per-electron float rows are padded by one word so
 // that lanes working on different electrons hit different banks.
 struct LayoutM {
-  int sc, x, bt, dd, phiv, chiv, u, row;                 // doubles
-  int xf, gf, dl, ej, ep, geo, rt1, pair, hcur, chi5, phi5, bf32;  // floats
+  int sc, x, bt, dd, phiv, chiv, u, row, hj2, xo;                  // doubles
+  int xf, xfo, gf, dl, ej, ep, geo, rt1, pair, hcur, chi5, phi5, bf32, hdm, hj1, tmp;  // floats
   int geo_st, rt1_st, pair_st, hcur_st, stride;
 };
 
 __host__ __device__ inline LayoutM layout_mixed(const Layout& L, int n_nuc, int n_prim) {
   LayoutM M;
-  const int ne = L.n_e, nbt = L.n_up * L.n_up + L.n_dn * L.n_dn, nm = L.n_max, nbf = L.n_bf;
+  const int ne = L.n_e, nbt = L.n_up * L.n_up + L.n_dn * L.n_dn, nm = L.n_max, nbf = L.n_bf, P = L.n_hop;
+  const int per = ne - 1 + n_nuc;
   int o = 0;
   M.sc = o; o += 2 * SC_COUNT;
   M.x = o; o += 2 * 3 * ne;
@@ -53,10 +54,13 @@ __host__ __device__ inline LayoutM layout_mixed(const Layout& L, int n_nuc, int 
   M.chiv = o; o += 2 * nbf;
   M.u = o; o += 2 * nm;
   M.row = o; o += 2 * nm;
+  M.hj2 = o; o += 2 * P;
+  M.xo = o; o += 2 * 4;
   M.xf = o; o += 3 * ne;
+  M.xfo = o; o += 4;
   o = round_up(o, 2);
-  M.gf = o; o += ne * nbf > 4 * nm * nm ? ne * nbf : 4 * nm * nm;   // also FP64 Gauss-Jordan scratch
-  M.dl = o; o += 6 * ne;
+  M.gf = o; o += ne * nbf;
+  M.dl = o; o += P;
   M.ej = o; o += 5 * ne;
   M.ep = o; o += 2 * ne;
   M.geo_st = 4 * n_nuc + 1;
@@ -70,8 +74,18 @@ __host__ __device__ inline LayoutM layout_mixed(const Layout& L, int n_nuc, int 
   M.chi5 = o; o += 5 * nbf > nbt ? 5 * nbf : nbt;      // also the FP32 copy of B^T
   M.phi5 = o; o += 5 * nm;
   M.bf32 = M.chi5;
+  M.hdm = o; o += P;
+  M.hj1 = o; o += P;
+  M.tmp = o; o += 6 * per;
   M.stride = round_up(o, 4);
   return M;
+}
+
+// Per-warp global scratch of the mixed kernels: the differences
+// chi_mu(r_i + hop) - chi_mu(r_i) for every hop, [n_bf][6 n_e] floats, and the
+// FP64 Gauss-Jordan work matrix [n_max][2 n_max].
+__host__ __device__ inline size_t scratch_doubles_m(const Layout& L) {
+  return ((size_t)L.n_bf * L.n_hop + 1) / 2 + 2 * (size_t)L.n_max * L.n_max;
 }
 
 __device__ __forceinline__ double* cache_val(const Layout& L, double* gblk) { return gblk + L.g_cache; }
@@ -215,11 +229,10 @@ __device__ void electron_potentials_f(const DevSys& S, const float q[3], float a
 }
 
 // FP64 re-inversion of the FP64 orbital values (both spin blocks).
-__device__ bool reinvert_m(const Layout& L, const LayoutM& M, double* gblk, float* sm, int lane) {
+__device__ bool reinvert_m(const Layout& L, const LayoutM& M, double* gblk, float* sm, double* scratch, int lane) {
   bool sing = false;
   const double* val = cache_val(L, gblk);
   double* bt = (double*)(sm + M.bt);
-  double* scratch = (double*)(sm + M.gf);
   for (int blk = 0; blk < 2; ++blk) {
     const int n = blk ? L.n_dn : L.n_up;
     const int e0 = blk ? L.n_up : 0;
@@ -229,6 +242,7 @@ __device__ bool reinvert_m(const Layout& L, const LayoutM& M, double* gblk, floa
       const int r = o / (2 * n), c = o - r * 2 * n;
       scratch[o] = c < n ? val[(e0 + r) * L.n_max + c] : (c - n == r ? 1.0 : 0.0);
     }
+    __threadfence_block();
     __syncwarp();
     sing |= warp_gauss_jordan(scratch, n, lane);
     for (int o = lane; o < n * n; o += WARP) {
@@ -260,159 +274,28 @@ __device__ void compute_g_m(const DevSys& S, const Layout& L, const LayoutM& M, 
   __syncwarp();
 }
 
-// Evaluate at the current configuration: hop ratios as r - 1 (FP32) and the
-// FP64 accumulators.  Requires g current.
-__device__ EvalOut eval_walker_m(const DevSys& S, const Layout& L, const LayoutM& M, double* gblk, float* sm,
-                                 double a, int node_rule, int lane) {
-  const int ne = L.n_e, nbf = L.n_bf, nmax = L.n_max, nn = S.n_nuc, np_all = S.n_prim;
-  const float af = (float)a, a2f = af * af;
-  const float* xf = sm + M.xf;
-  const double* bt = (const double*)(sm + M.bt);
-  const float* der = cache_der(L, gblk);
-  const float* g = sm + M.gf;
-  float* dl = sm + M.dl;
-  float* ej = sm + M.ej;     // grad J (3), lap J, half e-e sum
+// ------------------------------------------------------------ evaluation
+// FP32 pair geometry and Pade helpers, written with explicit FMAs so that every
+// call site rounds identically (the incremental swaps subtract exactly the
+// term that was added).
+__device__ __forceinline__ float sqdistf(float dx, float dy, float dz) { return fmaf(dz, dz, fmaf(dy, dy, dx * dx)); }
+// Jastrow difference of a hop, u(r') - u(r) = c del t t' / (r' + r), from the
+// current s = r^2, r, t = 1/(1 + b r) and del = r'^2 - r^2.
+__device__ __forceinline__ float pade_delta(float s, float r, float t, float del, float c, float b) {
+  const float sp = s + del;
+  const float rp = sp * rsqrtf(sp);
+  const float tp = __fdividef(1.f, fmaf(b, rp, 1.f));
+  return c * del * t * __fdividef(tp, rp + r);
+}
+
+// Assembly (FP64) from the r - 1 values, Jastrow and determinant derivatives.
+__device__ EvalOut assemble_m(const DevSys& S, const Layout& L, const LayoutM& M, const float* sm, double a,
+                              int node_rule, int lane) {
+  const int ne = L.n_e;
+  const float* dl = sm + M.dl;
+  const float* ej = sm + M.ej;
   const float* ep = sm + M.ep;
-  double* dd = (double*)(sm + M.dd);
-  float* geo = sm + M.geo;
-  float* rt1 = sm + M.rt1;
-  float* pair = sm + M.pair;
-  float* hcur = sm + M.hcur;
-  const float bj = (float)S.j2_b, cpar = (float)S.j2_par, canti = (float)S.j2_anti;
-  // (1) current configuration: Jastrow derivatives, geometry, primitive values
-  {
-    int npad = 1;
-    while (npad < ne) npad <<= 1;
-    const int G = npad >= WARP ? 1 : WARP / npad;
-    const int per = ne - 1 + nn;
-    for (int base = 0; base < ne; base += WARP / G) {
-      const int e = base + lane / G, sub = lane % G;
-      float gx = 0.f, gy = 0.f, gz = 0.f, LJ = 0.f, vee = 0.f;
-      if (e < ne) {
-        const float xe = xf[3 * e], ye = xf[3 * e + 1], ze = xf[3 * e + 2];
-        const bool up_e = e < L.n_up;
-        for (int t = sub; t < per; t += G) {
-          if (t < ne - 1) {
-            const int j = t < e ? t : t + 1;
-            const float dx = xe - xf[3 * j], dy = ye - xf[3 * j + 1], dz = ze - xf[3 * j + 2];
-            const float s = dx * dx + dy * dy + dz * dz;
-            const float ir = rsqrtf(s), r = s * ir;
-            const float c = (up_e == (j < L.n_up)) ? cpar : canti;
-            const float tt = __fdividef(1.f, fmaf(bj, r, 1.f));
-            float* pp = pair + e * M.pair_st + 3 * j;
-            pp[0] = s; pp[1] = r; pp[2] = tt;
-            const float up = c * tt * tt, upp = -2.f * bj * up * tt, f = up * ir;
-            gx = fmaf(f, dx, gx); gy = fmaf(f, dy, gy); gz = fmaf(f, dz, gz);
-            LJ += upp + 2.f * f;
-            vee = fmaf(0.5f, ir, vee);
-          } else {
-            const int I = t - (ne - 1);
-            const float dx = xe - __ldg(S.Rf + 3 * I), dy = ye - __ldg(S.Rf + 3 * I + 1),
-                        dz = ze - __ldg(S.Rf + 3 * I + 2);
-            const float s = dx * dx + dy * dy + dz * dz;
-            float* gg = geo + e * M.geo_st + 4 * I;
-            gg[0] = dx; gg[1] = dy; gg[2] = dz; gg[3] = s;
-            const float ir = rsqrtf(s), r = s * ir;
-            for (int sh = __ldg(S.atom_sh + I); sh < __ldg(S.atom_sh + I + 1); ++sh) {
-              const int np = __ldg(S.sh_nprim + sh), off = __ldg(S.sh_off + sh);
-              const float arg = __ldg(S.sh_l + sh) == -1 ? r : s;
-              for (int q = 0; q < np; ++q)
-                hcur[e * M.hcur_st + off + q] = __ldg(S.coefsf + off + q) * __expf(-__ldg(S.expsf + off + q) * arg);
-            }
-            const float A = __ldg(S.j1Af + I), B = __ldg(S.j1Bf + I);
-            const float tt = __fdividef(1.f, fmaf(B, r, 1.f));
-            rt1[e * M.rt1_st + 2 * I] = r;
-            rt1[e * M.rt1_st + 2 * I + 1] = tt;
-            if (A != 0.f) {
-              const float vp = -A * tt * tt, vpp = -2.f * B * vp * tt, f = vp * ir;
-              gx = fmaf(f, dx, gx); gy = fmaf(f, dy, gy); gz = fmaf(f, dz, gz);
-              LJ += vpp + 2.f * f;
-            }
-          }
-        }
-      }
-      for (int o = G >> 1; o; o >>= 1) {
-        gx += __shfl_xor_sync(FULL, gx, o);
-        gy += __shfl_xor_sync(FULL, gy, o);
-        gz += __shfl_xor_sync(FULL, gz, o);
-        LJ += __shfl_xor_sync(FULL, LJ, o);
-        vee += __shfl_xor_sync(FULL, vee, o);
-      }
-      if (e < ne && sub == 0) {
-        float* q = ej + 5 * e;
-        q[0] = gx; q[1] = gy; q[2] = gz; q[3] = LJ; q[4] = vee;
-      }
-    }
-  }
-  // (1b) FP64 determinant derivatives from the FP32 derivative cache and FP64 B
-  for (int o = lane; o < 4 * ne; o += WARP) {
-    const int i = o >> 2, c = o & 3;
-    const SpinRef sr = spin_ref(L, i);
-    const double* brow = bt + sr.bt_off + sr.ii * sr.n;
-    const float* ce = der + (i * 4 + c) * nmax;
-    double acc = 0.0;
-    for (int k = 0; k < sr.n; ++k) acc = fma((double)ce[k], brow[k], acc);
-    dd[o] = acc;
-  }
-  __syncwarp();
-  (void)np_all;
-  // (3) every hop, as r - 1, in FP32
-  for (int p = lane; p < 6 * ne; p += WARP) {
-    const int i = p / 6, d = p - 6 * i, ax = d >> 1;
-    const float sa = (d & 1) ? -af : af;
-    const float s2a = sa + sa;
-    const float* gi = g + i * nbf;
-    const float* hc = hcur + i * M.hcur_st;
-    float D = 0.f, dJ = 0.f;
-    for (int I = 0; I < nn; ++I) {
-      const float* gg = geo + i * M.geo_st + 4 * I;
-      const float del = fmaf(s2a, gg[ax], a2f);             // |r'-R|^2 - |r-R|^2
-      const float sp = gg[3] + del;
-      const float r = rt1[i * M.rt1_st + 2 * I];
-      const float rp = sp * rsqrtf(sp);
-      const float A = __ldg(S.j1Af + I);
-      if (A != 0.f) {
-        const float tp = __fdividef(1.f, fmaf(__ldg(S.j1Bf + I), rp, 1.f));
-        dJ -= A * del * rt1[i * M.rt1_st + 2 * I + 1] * __fdividef(tp, rp + r);
-      }
-      for (int sh = __ldg(S.atom_sh + I); sh < __ldg(S.atom_sh + I + 1); ++sh) {
-        const int l = __ldg(S.sh_l + sh), np = __ldg(S.sh_nprim + sh), off = __ldg(S.sh_off + sh),
-                  bf = __ldg(S.sh_bf + sh);
-        const float arg = l == -1 ? __fdividef(del, rp + r) : del;
-        float rd = 0.f, rn = 0.f;   // sums of h' - h and of h'
-        for (int q = 0; q < np; ++q) {
-          const float h = hc[off + q];
-          // the clamp only acts where h has already underflowed to 0
-          const float dh = h * expm1_fast(fminf(-__ldg(S.expsf + off + q) * arg, 80.f));
-          rd += dh;
-          rn += h + dh;
-        }
-        if (l != 1) {
-          D = fmaf(rd, gi[bf], D);
-        } else {
-          const float* g3 = gi + bf;
-          D = fmaf(rd, fmaf(gg[0], g3[0], fmaf(gg[1], g3[1], gg[2] * g3[2])), D);
-          D = fmaf(sa * rn, g3[ax], D);
-        }
-      }
-    }
-    const bool up_i = i < L.n_up;
-    const float xia = xf[3 * i + ax];
-    const float* pr = pair + i * M.pair_st;
-    for (int j = 0; j < ne; ++j) {
-      if (j == i) continue;
-      const float del = fmaf(s2a, xia - xf[3 * j + ax], a2f);
-      const float sp = pr[3 * j] + del;
-      const float rp = sp * rsqrtf(sp);
-      const float tp = __fdividef(1.f, fmaf(bj, rp, 1.f));
-      const float c = (up_i == (j < L.n_up)) ? cpar : canti;
-      dJ = fmaf(c * del * pr[3 * j + 2], __fdividef(tp, rp + pr[3 * j + 1]), dJ);
-    }
-    const float J = expm1_fast(dJ);
-    dl[p] = fmaf(D, J, D + J);
-  }
-  __syncwarp();
-  // (4) fixed-node split and regularised potential per electron, FP64 sums
+  const double* dd = (const double*)(sm + M.dd);
   bool has_node = false;
   for (int i = lane; i < ne; i += WARP)
     for (int d = 0; d < 6; ++d) has_node |= dl[6 * i + d] < -1.f;
@@ -465,8 +348,343 @@ __device__ EvalOut eval_walker_m(const DevSys& S, const Layout& L, const LayoutM
   return e;
 }
 
+// FP64 determinant derivatives for electrons [e0, e1) from the FP32
+// derivative cache and FP64 B.
+__device__ void det_derivs_m(const Layout& L, const LayoutM& M, double* gblk, float* sm, int e0, int e1, int lane) {
+  const double* bt = (const double*)(sm + M.bt);
+  const float* der = cache_der(L, gblk);
+  double* dd = (double*)(sm + M.dd);
+  for (int o = lane + 4 * e0; o < 4 * e1; o += WARP) {
+    const int i = o >> 2, c = o & 3;
+    const SpinRef sr = spin_ref(L, i);
+    const double* brow = bt + sr.bt_off + sr.ii * sr.n;
+    const float* ce = der + (i * 4 + c) * L.n_max;
+    double acc = 0.0;
+    for (int k = 0; k < sr.n; ++k) acc = fma((double)ce[k], brow[k], acc);
+    dd[o] = acc;
+  }
+}
+
+// Geometry, pair data, primitive values and Jastrow derivative sums of one
+// electron e against partner t (an electron for t < n_e - 1, else a nucleus);
+// accumulates into gx, gy, gz, LJ, vee.
+__device__ __forceinline__ void partner_terms(const DevSys& S, const Layout& L, const LayoutM& M, float* sm, int e,
+                                              int t, bool write_pair_both, float& gx, float& gy, float& gz, float& LJ,
+                                              float& vee) {
+  const int ne = L.n_e;
+  const float* xf = sm + M.xf;
+  const float bj = (float)S.j2_b;
+  const float xe = xf[3 * e], ye = xf[3 * e + 1], ze = xf[3 * e + 2];
+  if (t < ne - 1) {
+    const int j = t < e ? t : t + 1;
+    const float dx = xe - xf[3 * j], dy = ye - xf[3 * j + 1], dz = ze - xf[3 * j + 2];
+    const float s = sqdistf(dx, dy, dz);
+    const float ir = rsqrtf(s), r = s * ir;
+    const float c = (float)pair_c(S, L, e, j);
+    const float tt = __fdividef(1.f, fmaf(bj, r, 1.f));
+    float* pp = sm + M.pair + e * M.pair_st + 3 * j;
+    pp[0] = s; pp[1] = r; pp[2] = tt;
+    if (write_pair_both) {
+      float* pq = sm + M.pair + j * M.pair_st + 3 * e;
+      pq[0] = s; pq[1] = r; pq[2] = tt;
+    }
+    const float up = c * tt * tt, upp = -2.f * bj * up * tt, f = up * ir;
+    gx = fmaf(f, dx, gx); gy = fmaf(f, dy, gy); gz = fmaf(f, dz, gz);
+    LJ += upp + 2.f * f;
+    vee = fmaf(0.5f, ir, vee);
+  } else {
+    const int I = t - (ne - 1);
+    const float dx = xe - __ldg(S.Rf + 3 * I), dy = ye - __ldg(S.Rf + 3 * I + 1), dz = ze - __ldg(S.Rf + 3 * I + 2);
+    const float s = sqdistf(dx, dy, dz);
+    float* gg = sm + M.geo + e * M.geo_st + 4 * I;
+    gg[0] = dx; gg[1] = dy; gg[2] = dz; gg[3] = s;
+    const float ir = rsqrtf(s), r = s * ir;
+    float* hc = sm + M.hcur + e * M.hcur_st;
+    for (int sh = __ldg(S.atom_sh + I); sh < __ldg(S.atom_sh + I + 1); ++sh) {
+      const int np = __ldg(S.sh_nprim + sh), off = __ldg(S.sh_off + sh);
+      const float arg = __ldg(S.sh_l + sh) == -1 ? r : s;
+      for (int q = 0; q < np; ++q) hc[off + q] = __ldg(S.coefsf + off + q) * __expf(-__ldg(S.expsf + off + q) * arg);
+    }
+    const float A = __ldg(S.j1Af + I), B = __ldg(S.j1Bf + I);
+    const float tt = __fdividef(1.f, fmaf(B, r, 1.f));
+    sm[M.rt1 + e * M.rt1_st + 2 * I] = r;
+    sm[M.rt1 + e * M.rt1_st + 2 * I + 1] = tt;
+    if (A != 0.f) {
+      const float vp = -A * tt * tt, vpp = -2.f * B * vp * tt, f = vp * ir;
+      gx = fmaf(f, dx, gx); gy = fmaf(f, dy, gy); gz = fmaf(f, dz, gz);
+      LJ += vpp + 2.f * f;
+    }
+  }
+}
+
+// Full evaluation: every hop ratio as r - 1 (FP32), the FP64 accumulators and
+// every cache of the incremental update.  Requires g current.
+__device__ EvalOut eval_full_m(const DevSys& S, const Layout& L, const LayoutM& M, double* gblk, float* sm,
+                               float* dchi, double a, int node_rule, int lane) {
+  const int ne = L.n_e, nbf = L.n_bf, nn = S.n_nuc, P = L.n_hop;
+  const float af = (float)a, a2f = af * af;
+  const float* xf = sm + M.xf;
+  const float* g = sm + M.gf;
+  float* dl = sm + M.dl;
+  float* ej = sm + M.ej;
+  const float* geo = sm + M.geo;
+  const float* rt1 = sm + M.rt1;
+  const float* pair = sm + M.pair;
+  const float* hcur = sm + M.hcur;
+  float* hdm = sm + M.hdm;
+  float* hj1 = sm + M.hj1;
+  double* hj2 = (double*)(sm + M.hj2);
+  const float bj = (float)S.j2_b;
+  // (1) current configuration, G lanes per electron
+  {
+    int npad = 1;
+    while (npad < ne) npad <<= 1;
+    const int G = npad >= WARP ? 1 : WARP / npad;
+    const int per = ne - 1 + nn;
+    for (int base = 0; base < ne; base += WARP / G) {
+      const int e = base + lane / G, sub = lane % G;
+      float gx = 0.f, gy = 0.f, gz = 0.f, LJ = 0.f, vee = 0.f;
+      if (e < ne)
+        for (int t = sub; t < per; t += G) partner_terms(S, L, M, sm, e, t, false, gx, gy, gz, LJ, vee);
+      for (int o = G >> 1; o; o >>= 1) {
+        gx += __shfl_xor_sync(FULL, gx, o);
+        gy += __shfl_xor_sync(FULL, gy, o);
+        gz += __shfl_xor_sync(FULL, gz, o);
+        LJ += __shfl_xor_sync(FULL, LJ, o);
+        vee += __shfl_xor_sync(FULL, vee, o);
+      }
+      if (e < ne && sub == 0) {
+        float* q = ej + 5 * e;
+        q[0] = gx; q[1] = gy; q[2] = gz; q[3] = LJ; q[4] = vee;
+      }
+    }
+  }
+  det_derivs_m(L, M, gblk, sm, 0, ne, lane);
+  __syncwarp();
+  // (3) every hop, as r - 1, in FP32; caches the basis differences and the
+  // one-body / pair Jastrow differences per hop
+  for (int p = lane; p < P; p += WARP) {
+    const int i = p / 6, d = p - 6 * i, ax = d >> 1;
+    const float sa = (d & 1) ? -af : af;
+    const float s2a = sa + sa;
+    const float* gi = g + i * nbf;
+    const float* hc = hcur + i * M.hcur_st;
+    float D = 0.f, J1 = 0.f;
+    for (int I = 0; I < nn; ++I) {
+      const float* gg = geo + i * M.geo_st + 4 * I;
+      const float del = fmaf(s2a, gg[ax], a2f);             // |r'-R|^2 - |r-R|^2
+      const float r = rt1[i * M.rt1_st + 2 * I];
+      const float A = __ldg(S.j1Af + I);
+      if (A != 0.f) J1 += pade_delta(gg[3], r, rt1[i * M.rt1_st + 2 * I + 1], del, -A, __ldg(S.j1Bf + I));
+      const float sp = gg[3] + del;
+      const float rp = sp * rsqrtf(sp);
+      for (int sh = __ldg(S.atom_sh + I); sh < __ldg(S.atom_sh + I + 1); ++sh) {
+        const int l = __ldg(S.sh_l + sh), np = __ldg(S.sh_nprim + sh), off = __ldg(S.sh_off + sh),
+                  bf = __ldg(S.sh_bf + sh);
+        const float arg = l == -1 ? __fdividef(del, rp + r) : del;
+        float rd = 0.f, rn = 0.f;   // sums of h' - h and of h'
+        for (int q = 0; q < np; ++q) {
+          const float h = hc[off + q];
+          // the clamp only acts where h has already underflowed to 0
+          const float dh = h * expm1_fast(fminf(-__ldg(S.expsf + off + q) * arg, 80.f));
+          rd += dh;
+          rn += h + dh;
+        }
+        if (l != 1) {
+          D = fmaf(rd, gi[bf], D);
+          if (dchi) dchi[(size_t)bf * P + p] = rd;
+        } else {
+          float dc[3];
+          for (int k = 0; k < 3; ++k) dc[k] = fmaf(gg[k], rd, k == ax ? sa * rn : 0.f);
+          D = fmaf(dc[0], gi[bf], fmaf(dc[1], gi[bf + 1], fmaf(dc[2], gi[bf + 2], D)));
+          if (dchi)
+            for (int k = 0; k < 3; ++k) dchi[(size_t)(bf + k) * P + p] = dc[k];
+        }
+      }
+    }
+    const float xia = xf[3 * i + ax];
+    const float* pr = pair + i * M.pair_st;
+    double J2 = 0.0;
+    for (int j = 0; j < ne; ++j) {
+      if (j == i) continue;
+      const float del = fmaf(s2a, xia - xf[3 * j + ax], a2f);
+      J2 += (double)pade_delta(pr[3 * j], pr[3 * j + 1], pr[3 * j + 2], del, (float)pair_c(S, L, i, j), bj);
+    }
+    hdm[p] = D;
+    hj1[p] = J1;
+    hj2[p] = J2;
+    const float J = expm1_fast(J1 + (float)J2);
+    dl[p] = fmaf(D, J, D + J);
+  }
+  __threadfence_block();
+  __syncwarp();
+  return assemble_m(S, L, M, sm, a, node_rule, lane);
+}
+
+// Incremental evaluation after electron m hopped (old position at xo/xfo),
+// mirroring eval_incr of the FP64 kernel.
+__device__ EvalOut eval_incr_m(const DevSys& S, const Layout& L, const LayoutM& M, double* gblk, float* sm,
+                               float* dchi, int m, bool all_blocks, double a, int node_rule, int lane) {
+  const int ne = L.n_e, nbf = L.n_bf, nn = S.n_nuc, P = L.n_hop;
+  const int per = ne - 1 + nn;
+  const float af = (float)a, a2f = af * af;
+  const float* xf = sm + M.xf;
+  const float* xfo = sm + M.xfo;
+  const float* g = sm + M.gf;
+  float* dl = sm + M.dl;
+  float* ej = sm + M.ej;
+  const float* geo = sm + M.geo;
+  const float* rt1 = sm + M.rt1;
+  const float* pair = sm + M.pair;
+  float* hdm = sm + M.hdm;
+  float* hj1 = sm + M.hj1;
+  double* hj2 = (double*)(sm + M.hj2);
+  float* tmp = sm + M.tmp;
+  const float bj = (float)S.j2_b;
+  // (A) electron m from scratch (geometry, pair data both ways, primitives, Jastrow sums)
+  {
+    float gx = 0.f, gy = 0.f, gz = 0.f, LJ = 0.f, vee = 0.f;
+    for (int t = lane; t < per; t += WARP) partner_terms(S, L, M, sm, m, t, true, gx, gy, gz, LJ, vee);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      gx += __shfl_xor_sync(FULL, gx, o);
+      gy += __shfl_xor_sync(FULL, gy, o);
+      gz += __shfl_xor_sync(FULL, gz, o);
+      LJ += __shfl_xor_sync(FULL, LJ, o);
+      vee += __shfl_xor_sync(FULL, vee, o);
+    }
+    if (lane == 0) {
+      float* q = ej + 5 * m;
+      q[0] = gx; q[1] = gy; q[2] = gz; q[3] = LJ; q[4] = vee;
+    }
+  }
+  // (B) every other electron: swap its pair derivative terms with m
+  for (int i = lane; i < ne; i += WARP) {
+    if (i == m) continue;
+    const float c = (float)pair_c(S, L, i, m);
+    const float xi = xf[3 * i], yi = xf[3 * i + 1], zi = xf[3 * i + 2];
+    const float ox = xi - xfo[0], oy = yi - xfo[1], oz = zi - xfo[2];
+    const float nx = xi - xf[3 * m], ny = yi - xf[3 * m + 1], nz = zi - xf[3 * m + 2];
+    float f[2], upp[2], ir[2];
+    const float s2[2] = {sqdistf(ox, oy, oz), sqdistf(nx, ny, nz)};
+    for (int k = 0; k < 2; ++k) {
+      ir[k] = rsqrtf(s2[k]);
+      const float r = s2[k] * ir[k];
+      const float tt = __fdividef(1.f, fmaf(bj, r, 1.f));
+      const float up = c * tt * tt;
+      upp[k] = -2.f * bj * up * tt;
+      f[k] = up * ir[k];
+    }
+    float* q = ej + 5 * i;
+    q[0] += f[1] * nx - f[0] * ox;
+    q[1] += f[1] * ny - f[0] * oy;
+    q[2] += f[1] * nz - f[0] * oz;
+    q[3] += (upp[1] + 2.f * f[1]) - (upp[0] + 2.f * f[0]);
+    q[4] += 0.5f * (ir[1] - ir[0]);
+  }
+  // (C) determinant derivatives of the refreshed block(s)
+  const SpinRef srm = spin_ref(L, m);
+  const int b0 = all_blocks ? 0 : m - srm.ii, b1 = all_blocks ? ne : m - srm.ii + srm.n;
+  det_derivs_m(L, M, gblk, sm, b0, b1, lane);
+  __threadfence_block();
+  __syncwarp();
+  // (D) basis differences at m's six hops, one (hop, shell) per lane, and m's
+  // Jastrow differences, one (hop, partner) per lane
+  const float* hc = sm + M.hcur + m * M.hcur_st;
+  for (int o = lane; o < 6 * S.n_shell; o += WARP) {
+    const int d = o / S.n_shell, sh = o - d * S.n_shell, ax = d >> 1;
+    const float sa = (d & 1) ? -af : af;
+    const int I = __ldg(S.sh_atom + sh);
+    const float* gg = geo + m * M.geo_st + 4 * I;
+    const float del = fmaf(sa + sa, gg[ax], a2f);
+    const float r = rt1[m * M.rt1_st + 2 * I];
+    const int l = __ldg(S.sh_l + sh), np = __ldg(S.sh_nprim + sh), off = __ldg(S.sh_off + sh), bf = __ldg(S.sh_bf + sh);
+    const float sp = gg[3] + del;
+    const float arg = l == -1 ? __fdividef(del, sp * rsqrtf(sp) + r) : del;
+    float rd = 0.f, rn = 0.f;
+    for (int q = 0; q < np; ++q) {
+      const float h = hc[off + q];
+      const float dh = h * expm1_fast(fminf(-__ldg(S.expsf + off + q) * arg, 80.f));
+      rd += dh;
+      rn += h + dh;
+    }
+    const int p = 6 * m + d;
+    if (l != 1) {
+      dchi[(size_t)bf * P + p] = rd;
+    } else {
+      for (int k = 0; k < 3; ++k) dchi[(size_t)(bf + k) * P + p] = fmaf(gg[k], rd, k == ax ? sa * rn : 0.f);
+    }
+  }
+  for (int o = lane; o < 6 * per; o += WARP) {
+    const int d = o / per, t = o - d * per, ax = d >> 1;
+    const float sa = (d & 1) ? -af : af;
+    float v = 0.f;
+    if (t < ne - 1) {
+      const int j = t < m ? t : t + 1;
+      const float* pp = pair + m * M.pair_st + 3 * j;
+      const float del = fmaf(sa + sa, xf[3 * m + ax] - xf[3 * j + ax], a2f);
+      v = pade_delta(pp[0], pp[1], pp[2], del, (float)pair_c(S, L, m, j), bj);
+    } else {
+      const int I = t - (ne - 1);
+      const float A = __ldg(S.j1Af + I);
+      const float* gg = geo + m * M.geo_st + 4 * I;
+      if (A != 0.f)
+        v = pade_delta(gg[3], rt1[m * M.rt1_st + 2 * I], rt1[m * M.rt1_st + 2 * I + 1], fmaf(sa + sa, gg[ax], a2f),
+                       -A, __ldg(S.j1Bf + I));
+    }
+    tmp[o] = v;
+  }
+  __threadfence_block();
+  __syncwarp();
+  if (lane < 6) {
+    float J1 = 0.f;
+    double J2 = 0.0;
+    for (int t = 0; t < per; ++t) {
+      if (t < ne - 1) J2 += (double)tmp[lane * per + t];
+      else J1 += tmp[lane * per + t];
+    }
+    hj1[6 * m + lane] = J1;
+    hj2[6 * m + lane] = J2;
+  }
+  // (E) determinant differences of the refreshed block(s) from the cached basis differences
+  for (int p = lane + 6 * b0; p < 6 * b1; p += WARP) {
+    const float* gi = g + (p / 6) * nbf;
+    float D = 0.f;
+    for (int mu = 0; mu < nbf; ++mu) D = fmaf(dchi[(size_t)mu * P + p], gi[mu], D);
+    hdm[p] = D;
+  }
+  // (F) pair Jastrow differences of the other electrons' hops: swap the term with m
+  for (int p = lane; p < P; p += WARP) {
+    const int i = p / 6;
+    if (i == m) continue;
+    const int d = p - 6 * i, ax = d >> 1;
+    const float s2a = (d & 1) ? -2.f * af : 2.f * af;
+    const float c = (float)pair_c(S, L, i, m);
+    const float xia = xf[3 * i + ax];
+    const float ox = xf[3 * i] - xfo[0], oy = xf[3 * i + 1] - xfo[1], oz = xf[3 * i + 2] - xfo[2];
+    const float so = sqdistf(ox, oy, oz);
+    const float iro = rsqrtf(so), ro = so * iro;
+    const float to = __fdividef(1.f, fmaf(bj, ro, 1.f));
+    const float vo = pade_delta(so, ro, to, fmaf(s2a, xia - xfo[ax], a2f), c, bj);
+    const float* pn = pair + i * M.pair_st + 3 * m;
+    const float vn = pade_delta(pn[0], pn[1], pn[2], fmaf(s2a, xia - xf[3 * m + ax], a2f), c, bj);
+    hj2[p] += (double)vn - (double)vo;
+  }
+  __threadfence_block();
+  __syncwarp();
+  // (G) all hops, as r - 1
+  for (int p = lane; p < P; p += WARP) {
+    const float D = hdm[p];
+    const float J = expm1_fast(hj1[p] + (float)hj2[p]);
+    dl[p] = fmaf(D, J, D + J);
+  }
+  __threadfence_block();
+  __syncwarp();
+  return assemble_m(S, L, M, sm, a, node_rule, lane);
+}
+
 __device__ EvalOut init_walker_m(const DevSys& S, const Layout& L, const LayoutM& M, double* gblk, float* sm,
-                                 double a, int node_rule, const double* T, int lane, bool& singular) {
+                                 double* gj, double a, int node_rule, const double* T, int lane, bool& singular) {
   double* val = cache_val(L, gblk);
   float* der = cache_der(L, gblk);
   const double* x = (const double*)(sm + M.x);
@@ -492,9 +710,9 @@ __device__ EvalOut init_walker_m(const DevSys& S, const Layout& L, const LayoutM
     __syncwarp();
   }
   __threadfence_block();
-  singular = reinvert_m(L, M, gblk, sm, lane);
+  singular = reinvert_m(L, M, gblk, sm, gj, lane);
   compute_g_m(S, L, M, sm, 0, L.n_e, lane);
-  return eval_walker_m(S, L, M, gblk, sm, a, node_rule, lane);
+  return eval_full_m(S, L, M, gblk, sm, nullptr, a, node_rule, lane);
 }
 
 // Heat-bath choice from r - 1 values: same order and rule as the FP64 path
@@ -533,7 +751,8 @@ __device__ int choose_hop_m(const float* dl, int n_hop, double u, int lane) {
 }
 
 // Apply hop p: FP64 orbital value row and Sherman-Morrison update of B, FP32
-// derivative rows, g of the moved spin block, potentials and position.
+// derivative rows, g of the moved spin block, potentials and position; the
+// old position goes to xo / xfo.
 __device__ void apply_hop_m(const DevSys& S, const Layout& L, const LayoutM& M, double* gblk, float* sm, int p,
                             double a, const double* T, int lane) {
   double* x = (double*)(sm + M.x);
@@ -573,6 +792,10 @@ __device__ void apply_hop_m(const DevSys& S, const Layout& L, const LayoutM& M, 
   float nu, nucap;
   electron_potentials_f(S, qf, (float)a, lane, nu, nucap);
   if (lane == 0) {
+    double* xo = (double*)(sm + M.xo);
+    float* xfo = sm + M.xfo;
+    xo[0] = x[3 * i]; xo[1] = x[3 * i + 1]; xo[2] = x[3 * i + 2];
+    xfo[0] = xf[3 * i]; xfo[1] = xf[3 * i + 1]; xfo[2] = xf[3 * i + 2];
     x[3 * i] = q[0]; x[3 * i + 1] = q[1]; x[3 * i + 2] = q[2];
     xf[3 * i] = qf[0]; xf[3 * i + 1] = qf[1]; xf[3 * i + 2] = qf[2];
     sm[M.ep + 2 * i] = nu;
@@ -612,9 +835,16 @@ __device__ __forceinline__ void store_block_m(const Layout& L, const LayoutM& M,
   for (int o = lane; o < SC_COUNT; o += WARP) g[L.g_sc + o] = sc[o];
 }
 
+__device__ __forceinline__ float* warp_dchi(const Layout& L, double* scratch, int slot) {
+  return (float*)(scratch + (size_t)slot * scratch_doubles_m(L));
+}
+__device__ __forceinline__ double* warp_gj_m(const Layout& L, double* scratch, int slot) {
+  return scratch + (size_t)slot * scratch_doubles_m(L) + ((size_t)L.n_bf * L.n_hop + 1) / 2;
+}
+
 __global__ void k_init_walkers_m(DevSys S, Layout L, LayoutM M, double* __restrict__ state,
                                  const double* __restrict__ x_in, const double* __restrict__ w_in, int n, double a,
-                                 int node_rule) {
+                                 int node_rule, double* scratch) {
   extern __shared__ double smem[];
   const double* T = stage_table(S, smem);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -622,12 +852,14 @@ __global__ void k_init_walkers_m(DevSys S, Layout L, LayoutM M, double* __restri
   double* x = (double*)(sm + M.x);
   double* sc = (double*)(sm + M.sc);
   const int nwarps = gridDim.x * (blockDim.x >> 5);
-  for (int w = blockIdx.x * (blockDim.x >> 5) + wib; w < n; w += nwarps) {
+  const int slot = blockIdx.x * (blockDim.x >> 5) + wib;
+  double* gj = warp_gj_m(L, scratch, slot);
+  for (int w = slot; w < n; w += nwarps) {
     double* gblk = state + (size_t)w * L.g_stride;
     for (int o = lane; o < 3 * L.n_e; o += WARP) x[o] = x_in[(size_t)w * 3 * L.n_e + o];
     __syncwarp();
     bool sing = false;
-    const EvalOut e = init_walker_m(S, L, M, gblk, sm, a, node_rule, T, lane, sing);
+    const EvalOut e = init_walker_m(S, L, M, gblk, sm, gj, a, node_rule, T, lane, sing);
     if (lane == 0) {
       for (int k = 0; k < SC_COUNT; ++k) sc[k] = 0.0;
       sc[SC_W] = w_in ? w_in[w] : 1.0;
@@ -642,21 +874,24 @@ __global__ void k_init_walkers_m(DevSys S, Layout L, LayoutM M, double* __restri
   }
 }
 
-__global__ void k_eval_configs_m(DevSys S, Layout L, LayoutM M, double* __restrict__ scratch,
+__global__ void k_eval_configs_m(DevSys S, Layout L, LayoutM M, double* __restrict__ blocks,
                                  const double* __restrict__ x_in, int n, double a, int node_rule,
-                                 double* __restrict__ ratios, double* __restrict__ ev, int32_t* __restrict__ n_node) {
+                                 double* __restrict__ ratios, double* __restrict__ ev, int32_t* __restrict__ n_node,
+                                 double* scratch) {
   extern __shared__ double smem[];
   const double* T = stage_table(S, smem);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   float* sm = (float*)(smem + EXP_TAB) + wib * M.stride;
   double* x = (double*)(sm + M.x);
   const int nwarps = gridDim.x * (blockDim.x >> 5);
-  for (int w = blockIdx.x * (blockDim.x >> 5) + wib; w < n; w += nwarps) {
-    double* gblk = scratch + (size_t)w * L.g_stride;
+  const int slot = blockIdx.x * (blockDim.x >> 5) + wib;
+  double* gj = warp_gj_m(L, scratch, slot);
+  for (int w = slot; w < n; w += nwarps) {
+    double* gblk = blocks + (size_t)w * L.g_stride;
     for (int o = lane; o < 3 * L.n_e; o += WARP) x[o] = x_in[(size_t)w * 3 * L.n_e + o];
     __syncwarp();
     bool sing = false;
-    const EvalOut e = init_walker_m(S, L, M, gblk, sm, a, node_rule, T, lane, sing);
+    const EvalOut e = init_walker_m(S, L, M, gblk, sm, gj, a, node_rule, T, lane, sing);
     for (int o = lane; o < L.n_hop; o += WARP) ratios[(size_t)w * L.n_hop + o] = 1.0 + (double)sm[M.dl + o];
     if (lane == 0) {
       ev[4 * (size_t)w] = e.bbar;
@@ -669,14 +904,18 @@ __global__ void k_eval_configs_m(DevSys S, Layout L, LayoutM M, double* __restri
   }
 }
 
-__global__ void k_propagate_m(DevSys S, Layout L, LayoutM M, double* __restrict__ state, int n_w, StepParams P) {
+__global__ void k_propagate_m(DevSys S, Layout L, LayoutM M, double* __restrict__ state, int n_w, StepParams P,
+                              double* scratch) {
   extern __shared__ double smem[];
   const double* T = stage_table(S, smem);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   float* sm = (float*)(smem + EXP_TAB) + wib * M.stride;
   double* sc = (double*)(sm + M.sc);
   const int nwarps = gridDim.x * (blockDim.x >> 5);
-  for (int w = blockIdx.x * (blockDim.x >> 5) + wib; w < n_w; w += nwarps) {
+  const int slot = blockIdx.x * (blockDim.x >> 5) + wib;
+  float* dchi = warp_dchi(L, scratch, slot);
+  double* gj = warp_gj_m(L, scratch, slot);
+  for (int w = slot; w < n_w; w += nwarps) {
     const unsigned long long t_start = global_ns();
     double* gblk = state + (size_t)w * L.g_stride;
     load_block_m(L, M, gblk, sm, lane);
@@ -684,7 +923,7 @@ __global__ void k_propagate_m(DevSys S, Layout L, LayoutM M, double* __restrict_
     double bbar = sc[SC_BBAR], Wd = sc[SC_WDIAG], eL = sc[SC_EL];
     uint32_t status = (uint32_t)sc[SC_STATUS];
     int moves = 0, since = (int)sc[SC_SINCE];
-    bool g_valid = false;
+    bool g_valid = false, cached = false;
     for (int k = 0;; ++k) {
       if (P.kind == 1 && k >= P.n_proj) break;
       double u_tau, u_move;
@@ -711,16 +950,24 @@ __global__ void k_propagate_m(DevSys S, Layout L, LayoutM M, double* __restrict_
       } else {
         apply_hop_m(S, L, M, gblk, sm, p, P.a, T, lane);
         ++moves;
+        bool reinv = false;
         if (++since >= P.reinv_period) {
-          if (reinvert_m(L, M, gblk, sm, lane)) status |= ST_SINGULAR;
+          if (reinvert_m(L, M, gblk, sm, gj, lane)) status |= ST_SINGULAR;
           since = 0;
           g_valid = false;
+          reinv = true;
         }
         if (!g_valid) {
           compute_g_m(S, L, M, sm, 0, L.n_e, lane);
           g_valid = true;
         }
-        const EvalOut e = eval_walker_m(S, L, M, gblk, sm, P.a, P.node_rule, lane);
+        EvalOut e;
+        if (!cached) {
+          e = eval_full_m(S, L, M, gblk, sm, dchi, P.a, P.node_rule, lane);
+          cached = true;
+        } else {
+          e = eval_incr_m(S, L, M, gblk, sm, dchi, p / 6, reinv, P.a, P.node_rule, lane);
+        }
         bbar = e.bbar;
         Wd = e.W;
         eL = e.eL;
