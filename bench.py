@@ -211,14 +211,8 @@ def run_gpu(args, rank, world):
     launches = lr.launch_count() - n0
     step_ms = [e0.elapsed_time(e2) for e0, _, e2 in ev]
     prop_ms = [e0.elapsed_time(e1) for e0, e1, _ in ev]
-    t_total = sum(step_ms) / 1e3
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_total = float(tt.item())
     ws_per_step = N_W * N_PROJ
-    value = world * ws_per_step * args.steps / t_total
+    value, t_total = aggregate_throughput(sum(step_ms) / 1e3, ws_per_step * args.steps, world, dev)
     # roofline of the dominant kernel (the propagate kernel: one launch per step)
     slots = algorithmic_slots_per_walker_step(s.n_elec, s.n_nuc, s.n_bf, s.n_prim_eval, max(s.n_up, s.n_dn),
                                               int(np.sum(s.shell_l == 0)), int(np.sum(s.shell_l == 1)),
@@ -271,6 +265,20 @@ def run_gpu(args, rank, world):
                 launches=launches, achieved=achieved, clocks=clk.summary(), conv_rate=conv_rate,
                 conv_moves=conv_moves, tau=tau, e2e=e2e_value, h2d=h2d, d2h=d2h, slots=slots,
                 energy=lr.energy(), mixed=mixed, imbalance=imbalance)
+
+
+def aggregate_throughput(t_local, units_local, world, device="cpu"):
+    """Whole-job throughput of independent replicas: total work of all ranks
+    divided by the slowest rank's time (MAX over ranks, SUM of units)."""
+    if world <= 1:
+        return units_local / t_local, t_local
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([t_local], dtype=torch.float64, device=device)
+    u = torch.tensor([units_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(u.item()) / float(t.item()), float(t.item())
 
 
 def time_lb_intervals(lr, P, flush, steps, warmup):
