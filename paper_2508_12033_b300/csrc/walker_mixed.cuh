@@ -67,16 +67,20 @@ __host__ __device__ inline LayoutM layout_mixed(const Layout& L, int n_nuc, int 
   M.geo = o; o += ne * M.geo_st;
   M.rt1_st = 2 * n_nuc + 1;
   M.rt1 = o; o += ne * M.rt1_st;
-  M.pair_st = 3 * ne + 1;
+  M.pair_st = 2 * ne + 1;
   M.pair = o; o += ne * M.pair_st;
   M.hcur_st = n_prim + 1;
   M.hcur = o; o += ne * M.hcur_st;
-  M.chi5 = o; o += 5 * nbf > nbt ? 5 * nbf : nbt;      // also the FP32 copy of B^T
-  M.phi5 = o; o += 5 * nm;
+  // move scratch (basis rows, FP32 copy of B^T) and the per-hop Jastrow
+  // scratch of an evaluation share one region: they are never live together
+  int sh = 5 * nbf > nbt ? 5 * nbf : nbt;
+  sh = sh > 6 * per ? sh : 6 * per;
+  M.chi5 = o; o += sh;
   M.bf32 = M.chi5;
+  M.tmp = M.chi5;
+  M.phi5 = o; o += 5 * nm;
   M.hdm = o; o += P;
   M.hj1 = o; o += P;
-  M.tmp = o; o += 6 * per;
   M.stride = round_up(o, 4);
   return M;
 }
@@ -185,20 +189,29 @@ __device__ void orbital_rows_m(const DevSys& S, const Layout& L, const LayoutM& 
     shell_derivs_f(S, s, df, (float)r2, chi5, L.n_bf);
   }
   __syncwarp();
-  for (int o = lane; o < 5 * n_sig; o += WARP) {
-    const int c = o / n_sig, k = o - c * n_sig;
-    if (c == 0) {
-      const double* crow = S.C + (size_t)k * L.n_bf;
+  // FP64 values: n_sig orbitals x n_bf terms spread over all lanes in groups
+  // of G lanes per orbital (strided partial sums, fixed-order xor reduction)
+  {
+    int G = 1;
+    while (G * 2 * n_sig <= WARP) G *= 2;
+    for (int base = 0; base < n_sig; base += WARP / G) {
+      const int k = base + lane / G, sub = lane % G;
       double acc = 0.0;
-      for (int mu = 0; mu < L.n_bf; ++mu) acc = fma(__ldg(crow + mu), chiv[mu], acc);
-      phiv[k] = acc;
-    } else {
-      const float* crow = S.Cf + (size_t)k * L.n_bf;
-      const float* x = chi5 + c * L.n_bf;
-      float acc = 0.f;
-      for (int mu = 0; mu < L.n_bf; ++mu) acc = fmaf(__ldg(crow + mu), x[mu], acc);
-      phi5[(c - 1) * L.n_max + k] = acc;
+      if (k < n_sig) {
+        const double* crow = S.C + (size_t)k * L.n_bf;
+        for (int mu = sub; mu < L.n_bf; mu += G) acc = fma(__ldg(crow + mu), chiv[mu], acc);
+      }
+      for (int o = G >> 1; o; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+      if (k < n_sig && sub == 0) phiv[k] = acc;
     }
+  }
+  for (int o = lane; o < 4 * n_sig; o += WARP) {
+    const int c = 1 + o / n_sig, k = o - (c - 1) * n_sig;
+    const float* crow = S.Cf + (size_t)k * L.n_bf;
+    const float* x = chi5 + c * L.n_bf;
+    float acc = 0.f;
+    for (int mu = 0; mu < L.n_bf; ++mu) acc = fmaf(__ldg(crow + mu), x[mu], acc);
+    phi5[(c - 1) * L.n_max + k] = acc;
   }
   __syncwarp();
 }
@@ -280,9 +293,9 @@ __device__ void compute_g_m(const DevSys& S, const Layout& L, const LayoutM& M, 
 // term that was added).
 __device__ __forceinline__ float sqdistf(float dx, float dy, float dz) { return fmaf(dz, dz, fmaf(dy, dy, dx * dx)); }
 // Jastrow difference of a hop, u(r') - u(r) = c del t t' / (r' + r), from the
-// current s = r^2, r, t = 1/(1 + b r) and del = r'^2 - r^2.
-__device__ __forceinline__ float pade_delta(float s, float r, float t, float del, float c, float b) {
-  const float sp = s + del;
+// current r, t = 1/(1 + b r) and del = r'^2 - r^2 (r'^2 formed as r r + del).
+__device__ __forceinline__ float pade_delta(float r, float t, float del, float c, float b) {
+  const float sp = fmaf(r, r, del);
   const float rp = sp * rsqrtf(sp);
   const float tp = __fdividef(1.f, fmaf(b, rp, 1.f));
   return c * del * t * __fdividef(tp, rp + r);
@@ -382,11 +395,11 @@ __device__ __forceinline__ void partner_terms(const DevSys& S, const Layout& L, 
     const float ir = rsqrtf(s), r = s * ir;
     const float c = (float)pair_c(S, L, e, j);
     const float tt = __fdividef(1.f, fmaf(bj, r, 1.f));
-    float* pp = sm + M.pair + e * M.pair_st + 3 * j;
-    pp[0] = s; pp[1] = r; pp[2] = tt;
+    float* pp = sm + M.pair + e * M.pair_st + 2 * j;
+    pp[0] = r; pp[1] = tt;
     if (write_pair_both) {
-      float* pq = sm + M.pair + j * M.pair_st + 3 * e;
-      pq[0] = s; pq[1] = r; pq[2] = tt;
+      float* pq = sm + M.pair + j * M.pair_st + 2 * e;
+      pq[0] = r; pq[1] = tt;
     }
     const float up = c * tt * tt, upp = -2.f * bj * up * tt, f = up * ir;
     gx = fmaf(f, dx, gx); gy = fmaf(f, dy, gy); gz = fmaf(f, dz, gz);
@@ -475,7 +488,7 @@ __device__ EvalOut eval_full_m(const DevSys& S, const Layout& L, const LayoutM& 
       const float del = fmaf(s2a, gg[ax], a2f);             // |r'-R|^2 - |r-R|^2
       const float r = rt1[i * M.rt1_st + 2 * I];
       const float A = __ldg(S.j1Af + I);
-      if (A != 0.f) J1 += pade_delta(gg[3], r, rt1[i * M.rt1_st + 2 * I + 1], del, -A, __ldg(S.j1Bf + I));
+      if (A != 0.f) J1 += pade_delta(r, rt1[i * M.rt1_st + 2 * I + 1], del, -A, __ldg(S.j1Bf + I));
       const float sp = gg[3] + del;
       const float rp = sp * rsqrtf(sp);
       for (int sh = __ldg(S.atom_sh + I); sh < __ldg(S.atom_sh + I + 1); ++sh) {
@@ -504,16 +517,16 @@ __device__ EvalOut eval_full_m(const DevSys& S, const Layout& L, const LayoutM& 
     }
     const float xia = xf[3 * i + ax];
     const float* pr = pair + i * M.pair_st;
-    double J2 = 0.0;
+    float J2 = 0.f;
     for (int j = 0; j < ne; ++j) {
       if (j == i) continue;
       const float del = fmaf(s2a, xia - xf[3 * j + ax], a2f);
-      J2 += (double)pade_delta(pr[3 * j], pr[3 * j + 1], pr[3 * j + 2], del, (float)pair_c(S, L, i, j), bj);
+      J2 += pade_delta(pr[2 * j], pr[2 * j + 1], del, (float)pair_c(S, L, i, j), bj);
     }
     hdm[p] = D;
     hj1[p] = J1;
-    hj2[p] = J2;
-    const float J = expm1_fast(J1 + (float)J2);
+    hj2[p] = (double)J2;
+    const float J = expm1_fast(J1 + J2);
     dl[p] = fmaf(D, J, D + J);
   }
   __threadfence_block();
@@ -621,30 +634,29 @@ __device__ EvalOut eval_incr_m(const DevSys& S, const Layout& L, const LayoutM& 
     float v = 0.f;
     if (t < ne - 1) {
       const int j = t < m ? t : t + 1;
-      const float* pp = pair + m * M.pair_st + 3 * j;
+      const float* pp = pair + m * M.pair_st + 2 * j;
       const float del = fmaf(sa + sa, xf[3 * m + ax] - xf[3 * j + ax], a2f);
-      v = pade_delta(pp[0], pp[1], pp[2], del, (float)pair_c(S, L, m, j), bj);
+      v = pade_delta(pp[0], pp[1], del, (float)pair_c(S, L, m, j), bj);
     } else {
       const int I = t - (ne - 1);
       const float A = __ldg(S.j1Af + I);
       const float* gg = geo + m * M.geo_st + 4 * I;
       if (A != 0.f)
-        v = pade_delta(gg[3], rt1[m * M.rt1_st + 2 * I], rt1[m * M.rt1_st + 2 * I + 1], fmaf(sa + sa, gg[ax], a2f),
-                       -A, __ldg(S.j1Bf + I));
+        v = pade_delta(rt1[m * M.rt1_st + 2 * I], rt1[m * M.rt1_st + 2 * I + 1], fmaf(sa + sa, gg[ax], a2f), -A,
+                       __ldg(S.j1Bf + I));
     }
     tmp[o] = v;
   }
   __threadfence_block();
   __syncwarp();
   if (lane < 6) {
-    float J1 = 0.f;
-    double J2 = 0.0;
+    float J1 = 0.f, J2 = 0.f;
     for (int t = 0; t < per; ++t) {
-      if (t < ne - 1) J2 += (double)tmp[lane * per + t];
+      if (t < ne - 1) J2 += tmp[lane * per + t];
       else J1 += tmp[lane * per + t];
     }
     hj1[6 * m + lane] = J1;
-    hj2[6 * m + lane] = J2;
+    hj2[6 * m + lane] = (double)J2;
   }
   // (E) determinant differences of the refreshed block(s) from the cached basis differences
   for (int p = lane + 6 * b0; p < 6 * b1; p += WARP) {
@@ -665,9 +677,9 @@ __device__ EvalOut eval_incr_m(const DevSys& S, const Layout& L, const LayoutM& 
     const float so = sqdistf(ox, oy, oz);
     const float iro = rsqrtf(so), ro = so * iro;
     const float to = __fdividef(1.f, fmaf(bj, ro, 1.f));
-    const float vo = pade_delta(so, ro, to, fmaf(s2a, xia - xfo[ax], a2f), c, bj);
-    const float* pn = pair + i * M.pair_st + 3 * m;
-    const float vn = pade_delta(pn[0], pn[1], pn[2], fmaf(s2a, xia - xf[3 * m + ax], a2f), c, bj);
+    const float vo = pade_delta(ro, to, fmaf(s2a, xia - xfo[ax], a2f), c, bj);
+    const float* pn = pair + i * M.pair_st + 2 * m;
+    const float vn = pade_delta(pn[0], pn[1], fmaf(s2a, xia - xf[3 * m + ax], a2f), c, bj);
     hj2[p] += (double)vn - (double)vo;
   }
   __threadfence_block();
