@@ -72,8 +72,9 @@ def v_ii(sys):
     return v
 
 
-def evaluate(sys, x, a, node_rule=0):
-    """All per-configuration quantities at x (..., n_e, 3).
+def evaluate(sys, x, a, node_rule=0, versors=None):
+    """All per-configuration quantities at x (..., n_e, 3); hops along the
+    Cartesian axes or along the rows of ``versors`` (..., 3, 3).
 
     Returns a dict with
       ratios (..., n_e, 6), bbar, vsf, W, eL (...), n_node (...) = number of
@@ -81,7 +82,7 @@ def evaluate(sys, x, a, node_rule=0):
       nu_opt (..., n_e)."""
     x = np.asarray(x, dtype=np.float64)
     ne = sys.n_elec
-    r = wf.hop_ratios(sys, x, a)                               # (..., ne, 6)
+    r = wf.hop_ratios(sys, x, a, versors)                      # (..., ne, 6)
     pos = r > 0.0
     neg = r < 0.0
     inv2a2 = 1.0 / (2.0 * a * a)

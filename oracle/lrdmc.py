@@ -62,6 +62,34 @@ class Walkers:
     moves: np.ndarray      # (n_w,) hops made in the last interval
 
 
+def rotation_matrices(u1, u2, u3):
+    """Uniformly distributed rotations from three uniforms (Shoemake, "Uniform
+    random rotations", Graphics Gems III, 1992): the unit quaternion
+    (x, y, z, w) = (sqrt(1-u1) sin 2 pi u2, sqrt(1-u1) cos 2 pi u2,
+                    sqrt(u1) sin 2 pi u3, sqrt(u1) cos 2 pi u3)
+    and its rotation matrix.  Returns (..., 3, 3); row k is versor k = R e_k."""
+    a, b = np.sqrt(1.0 - u1), np.sqrt(u1)
+    x, y = a * np.sin(2 * np.pi * u2), a * np.cos(2 * np.pi * u2)
+    z, w = b * np.sin(2 * np.pi * u3), b * np.cos(2 * np.pi * u3)
+    R = np.empty(np.shape(u1) + (3, 3))
+    R[..., 0, 0] = 1 - 2 * (y * y + z * z)
+    R[..., 0, 1] = 2 * (x * y - w * z)
+    R[..., 0, 2] = 2 * (x * z + w * y)
+    R[..., 1, 0] = 2 * (x * y + w * z)
+    R[..., 1, 1] = 1 - 2 * (x * x + z * z)
+    R[..., 1, 2] = 2 * (y * z - w * x)
+    R[..., 2, 0] = 2 * (x * z - w * y)
+    R[..., 2, 1] = 2 * (y * z + w * x)
+    R[..., 2, 2] = 1 - 2 * (x * x + y * y)
+    return np.swapaxes(R, -1, -2)          # rows = columns of R = rotated axes
+
+
+def interval_versors(seed, walker_ids, interval):
+    """Hop versors of the randomised lattice (Appendix D): one uniformly random
+    rotation of the three axes per walker and interval."""
+    return rotation_matrices(*philox.rotation_uniforms(seed, walker_ids, interval))
+
+
 def init_walkers(sys, x0, a, node_rule=0):
     x = np.array(x0, dtype=np.float64, copy=True)
     ev = ham.evaluate(sys, x, a, node_rule)
@@ -88,26 +116,42 @@ def choose_hop(ratios, u):
     return np.where(total > 0.0, out, -1).astype(np.int64)
 
 
-def _apply_hops(W: Walkers, sel, hop, a):
+def _apply_hops(W: Walkers, sel, hop, a, versors=None):
     """Move walkers ``sel`` (indices) by hops ``hop`` (same length)."""
     i = hop // 6
     d = hop % 6
-    W.x[sel, i, HOP_AXIS[d]] += HOP_SIGN[d] * a
+    if versors is None:
+        W.x[sel, i, HOP_AXIS[d]] += HOP_SIGN[d] * a
+    else:
+        for k in range(len(sel)):
+            W.x[sel[k], i[k], :] += HOP_SIGN[d[k]] * a * versors[sel[k], HOP_AXIS[d[k]], :]
 
 
-def _reevaluate(sys, W: Walkers, sel, a, node_rule):
+def _reevaluate(sys, W: Walkers, sel, a, node_rule, versors=None):
     if len(sel) == 0:
         return
-    ev = ham.evaluate(sys, W.x[sel], a, node_rule)
+    ev = ham.evaluate(sys, W.x[sel], a, node_rule, None if versors is None else versors[sel])
     for k, v in ev.items():
         W.ev[k][sel] = v
 
 
-def propagate_lb(sys, W: Walkers, a, E0, n_proj, seed, interval, node_rule=0, walker_ids=None):
+def _rotate(sys, W: Walkers, a, node_rule, seed, interval, ids, rotate):
+    """With a randomised lattice, draw this interval's versors and re-evaluate
+    every walker with them (the stored evaluation used the previous axes)."""
+    if not rotate:
+        return None
+    V = interval_versors(seed, ids, interval)
+    _reevaluate(sys, W, np.arange(W.x.shape[0]), a, node_rule, V)
+    return V
+
+
+def propagate_lb(sys, W: Walkers, a, E0, n_proj, seed, interval, node_rule=0, walker_ids=None, rotate=False):
     """One load-balanced interval (Algorithm 2, inner loop) for all walkers.
-    ``walker_ids``: Philox walker slots of the rows of W (default 0..n-1)."""
+    ``walker_ids``: Philox walker slots of the rows of W (default 0..n-1).
+    ``rotate``: randomised lattice, hop versors redrawn for the interval."""
     n = W.x.shape[0]
     ids = np.arange(n) if walker_ids is None else np.asarray(walker_ids)
+    V = _rotate(sys, W, a, node_rule, seed, interval, ids, rotate)
     W.w = np.ones(n)
     W.moves = np.zeros(n, np.int64)
     for k in range(n_proj):
@@ -120,18 +164,20 @@ def propagate_lb(sys, W: Walkers, a, E0, n_proj, seed, interval, node_rule=0, wa
         hop = choose_hop(W.ev["ratios"], u_move)
         W.status |= np.where(hop < 0, ST_STUCK, 0).astype(np.uint32)
         sel = np.nonzero(hop >= 0)[0]
-        _apply_hops(W, sel, hop[sel], a)
+        _apply_hops(W, sel, hop[sel], a, V)
         W.moves[sel] += 1
-        _reevaluate(sys, W, sel, a, node_rule)
+        _reevaluate(sys, W, sel, a, node_rule, V)
     W.status |= np.where(~np.isfinite(W.w) | ~np.isfinite(W.ev["eL"]), ST_NONFINITE, 0).astype(np.uint32)
 
 
 def propagate_conventional(sys, W: Walkers, a, tau, seed, interval, node_rule=0,
-                           max_moves=100000, walker_ids=None):
+                           max_moves=100000, walker_ids=None, rotate=False):
     """One conventional interval (Algorithm 1, inner loop) for all walkers.
-    ``walker_ids``: Philox walker slots of the rows of W (default 0..n-1)."""
+    ``walker_ids``: Philox walker slots of the rows of W (default 0..n-1).
+    ``rotate``: randomised lattice, hop versors redrawn for the interval."""
     n = W.x.shape[0]
     ids = np.arange(n) if walker_ids is None else np.asarray(walker_ids)
+    V = _rotate(sys, W, a, node_rule, seed, interval, ids, rotate)
     W.w = np.ones(n)
     W.moves = np.zeros(n, np.int64)
     tau_left = np.full(n, float(tau))
@@ -154,9 +200,9 @@ def propagate_conventional(sys, W: Walkers, a, tau, seed, interval, node_rule=0,
             hop = choose_hop(W.ev["ratios"][go], u_move[~clipped])
             W.status[go] |= np.where(hop < 0, ST_STUCK, 0).astype(np.uint32)
             ok = hop >= 0
-            _apply_hops(W, go[ok], hop[ok], a)
+            _apply_hops(W, go[ok], hop[ok], a, V)
             W.moves[go[ok]] += 1
-            _reevaluate(sys, W, go[ok], a, node_rule)
+            _reevaluate(sys, W, go[ok], a, node_rule, V)
         k += 1
         if k >= max_moves and np.any(active):
             cap = np.nonzero(active)[0]
@@ -236,7 +282,7 @@ class RunResult:
 
 
 def run(sys, x0, a, schedule, n_branch, seed, n_proj=20, tau=None, node_rule=0,
-        p_gbar=10, n_equil=0, E0=None, max_moves=100000):
+        p_gbar=10, n_equil=0, E0=None, max_moves=100000, rotate=False):
     """Full oracle run (both algorithms' outer loop)."""
     W = init_walkers(sys, x0, a, node_rule)
     if E0 is None:
@@ -244,9 +290,9 @@ def run(sys, x0, a, schedule, n_branch, seed, n_proj=20, tau=None, node_rule=0,
     hist = RunResult([], [], [], [], [], [], 0, float("nan"), float("nan"))
     for j in range(n_branch):
         if schedule == LOAD_BALANCED:
-            propagate_lb(sys, W, a, E0, n_proj, seed, j, node_rule)
+            propagate_lb(sys, W, a, E0, n_proj, seed, j, node_rule, rotate=rotate)
         else:
-            propagate_conventional(sys, W, a, tau, seed, j, node_rule, max_moves)
+            propagate_conventional(sys, W, a, tau, seed, j, node_rule, max_moves, rotate=rotate)
         wbar, ebar = branch_stats(W, E0, schedule)
         hist.wbar.append(wbar)
         hist.ebar.append(ebar)

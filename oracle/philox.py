@@ -92,6 +92,17 @@ def step_uniforms(seed: int, walker, step, interval):
     return uniform53(r0, r1), uniform53(r2, r3)
 
 
+def rotation_uniforms(seed: int, walker, interval):
+    """Three uniforms for the lattice rotation of ``walker`` in ``interval``:
+    counter (walker, 2^32-1, interval, 2) gives u1 (words 0-1) and u2 (words
+    2-3), counter (walker, 2^32-1, interval, 3) gives u3 (words 0-1)."""
+    k0, k1 = seed_key(seed)
+    walker = np.asarray(walker)
+    a0, a1, a2, a3 = philox4x32(walker, 0xFFFFFFFF, interval, 2, k0, k1)
+    b0, b1, _, _ = philox4x32(walker, 0xFFFFFFFF, interval, 3, k0, k1)
+    return uniform53(a0, a1), uniform53(a2, a3), uniform53(b0, b1)
+
+
 def branch_offset32(seed: int, interval: int) -> int:
     """32-bit comb offset xi*2^32 for the reconfiguration ending ``interval``."""
     k0, k1 = seed_key(seed)

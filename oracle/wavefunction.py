@@ -173,22 +173,35 @@ def log_psi(sys, x):
     return sign, logv
 
 
-def displaced(x, a):
+def hop_vector(a, d, versors=None):
+    """Displacement of hop d: HOP_SIGN[d] * a along versor HOP_AXIS[d] (the
+    Cartesian axes, or the rows of ``versors`` (..., 3, 3) when given)."""
+    if versors is None:
+        v = np.zeros(3)
+        v[HOP_AXIS[d]] = HOP_SIGN[d] * a
+        return v
+    return HOP_SIGN[d] * a * versors[..., HOP_AXIS[d], :]
+
+
+def displaced(x, a, versors=None):
     """All 6 n_e single-electron lattice hops: (..., n_e, 6, n_e, 3), hop (i, d)
-    moves electron i by HOP_SIGN[d] * a along axis HOP_AXIS[d]."""
+    moves electron i by HOP_SIGN[d] * a along versor HOP_AXIS[d]."""
     ne = x.shape[-2]
     xd = np.broadcast_to(x[..., None, None, :, :], x.shape[:-2] + (ne, 6, ne, 3)).copy()
     for i in range(ne):
         for d in range(6):
-            xd[..., i, d, i, HOP_AXIS[d]] += HOP_SIGN[d] * a
+            if versors is None:
+                xd[..., i, d, i, HOP_AXIS[d]] += HOP_SIGN[d] * a
+            else:
+                xd[..., i, d, i, :] += hop_vector(a, d, versors)
     return xd
 
 
-def hop_ratios(sys, x, a):
+def hop_ratios(sys, x, a, versors=None):
     """r_{i,d} = Psi_G(x_{i,d}) / Psi_G(x) for every hop, (..., n_e, 6), each from
     freshly computed determinants and Jastrow factors."""
     s0, l0 = log_psi(sys, x)
-    xd = displaced(x, a)
+    xd = displaced(x, a, versors)
     s1, l1 = log_psi(sys, xd)
     return (s1 * s0[..., None, None]) * np.exp(l1 - l0[..., None, None])
 

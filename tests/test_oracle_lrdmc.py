@@ -114,7 +114,7 @@ class _ConstEval:
     def __init__(self, ratio, a, e=0.0):
         self.ratio, self.a, self.e = ratio, a, e
 
-    def __call__(self, sys, x, a, node_rule=0):
+    def __call__(self, sys, x, a, node_rule=0, versors=None):
         n = x.shape[0]
         ne = x.shape[1]
         bbar = 6 * ne * self.ratio / (2 * a * a)
@@ -254,3 +254,32 @@ def test_both_schedules_reach_the_lattice_ground_energy(schedule):
         # the mean weight gained per interval is 1 once equilibrated.
         wb = np.array(h.wbar[30:])
         assert abs(wb.mean() - 1.0) < 5 * wb.std() / math.sqrt(len(wb)) + 2e-3
+
+
+# ----------------------------------------------------------- randomised lattice
+def test_random_versors_are_haar_rotations():
+    """Shoemake's construction: orthonormal rows, determinant +1, and each
+    rotated axis uniformly distributed on the sphere (its z component is
+    uniform on [-1, 1], mean of the matrix 0)."""
+    V = L.interval_versors(7, np.arange(40000), 11)
+    np.testing.assert_allclose(np.einsum("nij,nkj->nik", V, V), np.broadcast_to(np.eye(3), V.shape), atol=1e-14)
+    np.testing.assert_allclose(np.linalg.det(V), 1.0, atol=1e-14)
+    assert np.abs(V.mean(axis=0)).max() < 0.02
+    for k in range(3):
+        assert stats.kstest(V[:, k, 2], "uniform", args=(-1.0, 2.0)).pvalue > 1e-4
+    # different intervals and walkers draw different rotations
+    assert not np.allclose(L.interval_versors(7, [0], 11), L.interval_versors(7, [0], 12))
+
+
+def test_randomised_lattice_keeps_exact_energy_and_hop_length():
+    s = W.hydrogen_atom_sto(1.0)
+    x0 = W.initial_walkers(s, 24, seed=3)
+    for sched in (L.LOAD_BALANCED, L.CONVENTIONAL):
+        h, Wk = L.run(s, x0, 0.25, sched, 4, seed=2, n_proj=6, tau=0.05, rotate=True)
+        assert abs(h.energy + 0.5) < 1e-12
+    # every hop moves an electron by exactly a along one of its interval's versors
+    Wk = L.init_walkers(s, x0, 0.25)
+    before = Wk.x.copy()
+    L.propagate_lb(s, Wk, 0.25, -0.5, 1, seed=2, interval=9, rotate=True)
+    step = np.linalg.norm(Wk.x - before, axis=-1)
+    np.testing.assert_allclose(step, 0.25, rtol=1e-12)
