@@ -98,12 +98,18 @@ typedef enum { LRDMC_CONVENTIONAL = 0, LRDMC_LOAD_BALANCED = 1 } lrdmc_kind;
 
 /* One branching interval.  LOAD_BALANCED: every walker makes n_proj hops
  * (Algorithm 2).  CONVENTIONAL: every walker runs until its projection time tau
- * is used up (Algorithm 1), at most max_moves hops. */
+ * is used up (Algorithm 1), at most max_moves hops.
+ * rotate != 0: randomised lattice (Appendix D): for this interval every walker
+ * hops along its own uniformly random rotation of the three axes (drawn from
+ * Philox counter (walker, 2^32-1, interval, 2..3)); every walker is re-evaluated
+ * with the new versors before its first step.  Precision 0 only (the mixed
+ * path returns LRDMC_ERR_UNSUPPORTED). */
 typedef struct {
     int kind;
     int n_proj;
     double tau;
     int max_moves;
+    int rotate;
 } lrdmc_schedule;
 
 /* Run parameters.

@@ -36,7 +36,8 @@ class _TrialWF(C.Structure):
 
 
 class _Schedule(C.Structure):
-    _fields_ = [("kind", C.c_int), ("n_proj", C.c_int), ("tau", C.c_double), ("max_moves", C.c_int)]
+    _fields_ = [("kind", C.c_int), ("n_proj", C.c_int), ("tau", C.c_double), ("max_moves", C.c_int),
+                ("rotate", C.c_int)]
 
 
 class _Params(C.Structure):
@@ -182,8 +183,8 @@ class Lrdmc:
             pass
 
     # ---------------------------------------------------------------- hot path
-    def propagate(self, kind=LOAD_BALANCED, n_proj=20, tau=0.0, max_moves=100000):
-        s = _Schedule(int(kind), int(n_proj), float(tau), int(max_moves))
+    def propagate(self, kind=LOAD_BALANCED, n_proj=20, tau=0.0, max_moves=100000, rotate=False):
+        s = _Schedule(int(kind), int(n_proj), float(tau), int(max_moves), 1 if rotate else 0)
         self._check(self.lib.lrdmc_propagate(self._h, C.byref(s)))
 
     def branch(self):

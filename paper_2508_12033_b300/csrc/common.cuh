@@ -73,12 +73,13 @@ struct Layout {
   int g_x, g_bt, g_cache, g_rat, g_pot, g_sc, g_stride;
   // shared memory per warp (FP64 kernels): positions, B^T, hop ratios,
   // per-electron Jastrow terms [6], potentials [2], determinant derivatives
-  // [4], electron-nucleus geometry [4], pair distances, per-hop determinant
+  // [4], electron-nucleus geometry [8: d, |d|^2 + a^2, projections on the hop
+  // versors], pair distances, per-hop determinant
   // ratio and one-body / pair Jastrow sums, per-hop scratch (also the moved
   // electron's basis scratch), orbital rows, rank-1 factors, old position of
-  // the moved electron, scalars
+  // the moved electron, hop versors [3][3], scalars
   int s_x, s_bt, s_rat, s_ej, s_ep, s_dd, s_geo, s_pr2, s_hd, s_hj1, s_hj2, s_tmp, s_phi5, s_u, s_row, s_xo,
-      s_sc, s_stride;
+      s_v, s_sc, s_stride;
 };
 
 __host__ __device__ inline int round_up(int v, int m) { return (v + m - 1) / m * m; }

@@ -98,7 +98,7 @@ bool make_plan(const lrdmc_system* sys, const lrdmc_trial_wf* wf, const lrdmc_pa
   L.s_ep = L.s_ej + 6 * P.n_e;
   L.s_dd = L.s_ep + 2 * P.n_e;
   L.s_geo = L.s_dd + 4 * P.n_e;
-  L.s_pr2 = L.s_geo + 4 * P.n_e * P.n_nuc;
+  L.s_pr2 = L.s_geo + 8 * P.n_e * P.n_nuc;
   L.s_hd = L.s_pr2 + P.n_e * P.n_e;
   L.s_hj1 = L.s_hd + L.n_hop;
   L.s_hj2 = L.s_hj1 + L.n_hop;
@@ -107,7 +107,8 @@ bool make_plan(const lrdmc_system* sys, const lrdmc_trial_wf* wf, const lrdmc_pa
   L.s_u = L.s_phi5 + 5 * P.n_max;
   L.s_row = L.s_u + P.n_max;
   L.s_xo = L.s_row + P.n_max;
-  L.s_sc = L.s_xo + 4;
+  L.s_v = L.s_xo + 4;
+  L.s_sc = L.s_v + 12;
   L.s_stride = round_up(L.s_sc + SC_COUNT, 4);
   P.M = layout_mixed(L, P.n_nuc, P.n_prim);
   P.smem_per_warp = P.precision == 0 ? (size_t)L.s_stride * sizeof(double) : (size_t)P.M.stride * sizeof(float);
@@ -276,7 +277,8 @@ static int smem_bytes(lrdmc_handle h) {
 // handle in the process, so it is raised to the device's opt-in maximum (it
 // permits, it reserves nothing); each launch still requests only its own size.
 static lrdmc_status set_kernel_smem(lrdmc_handle h, int optin) {
-  CK(h, cudaFuncSetAttribute(k_propagate, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  CK(h, cudaFuncSetAttribute(k_propagate<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  CK(h, cudaFuncSetAttribute(k_propagate<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   CK(h, cudaFuncSetAttribute(k_init_walkers, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   CK(h, cudaFuncSetAttribute(k_eval_configs, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   CK(h, cudaFuncSetAttribute(k_propagate_m, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
@@ -508,7 +510,7 @@ lrdmc_status lrdmc_create(const lrdmc_system* sys, const lrdmc_trial_wf* wf, con
   if (st != LRDMC_OK) return st;
   int bps = 0;
   if (P.precision == 0)
-    CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_propagate, h->wpb * 32, smem_bytes(h)));
+    CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_propagate<false>, h->wpb * 32, smem_bytes(h)));
   else
     CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_propagate_m, h->wpb * 32, smem_bytes(h)));
   if (bps < 1) return fail(h, LRDMC_ERR_UNSUPPORTED, "propagate kernel does not fit on an SM");
@@ -544,6 +546,8 @@ lrdmc_status lrdmc_propagate(lrdmc_handle h, const lrdmc_schedule* sch) {
   if (sch->kind == LRDMC_LOAD_BALANCED && sch->n_proj < 0) return fail(h, LRDMC_ERR_ARG, "n_proj < 0");
   if (sch->kind == LRDMC_CONVENTIONAL && (!(sch->tau > 0.0) || sch->max_moves < 1))
     return fail(h, LRDMC_ERR_ARG, "conventional schedule needs tau > 0 and max_moves >= 1");
+  if (sch->rotate && h->P.precision != 0)
+    return fail(h, LRDMC_ERR_UNSUPPORTED, "the randomised lattice is implemented for precision 0 only");
   DeviceGuard g(h->device);
   StepParams sp;
   sp.kind = sch->kind;
@@ -557,10 +561,15 @@ lrdmc_status lrdmc_propagate(lrdmc_handle h, const lrdmc_schedule* sch) {
   sp.node_rule = h->prm.node_rule;
   sp.reinv_period = h->prm.reinv_period;
   sp.stamps = h->timing ? h->stamps : nullptr;
+  sp.rotate = sch->rotate != 0;
   const int smem = smem_bytes(h);
   if (h->P.precision == 0)
-    k_propagate<<<walker_grid(h, h->P.n_w), h->wpb * 32, smem, h->stream>>>(h->S, h->P.L, h->state, h->P.n_w, sp,
-                                                                            h->scr);
+    if (sp.rotate)
+      k_propagate<true><<<walker_grid(h, h->P.n_w), h->wpb * 32, smem, h->stream>>>(h->S, h->P.L, h->state,
+                                                                                  h->P.n_w, sp, h->scr);
+    else
+      k_propagate<false><<<walker_grid(h, h->P.n_w), h->wpb * 32, smem, h->stream>>>(h->S, h->P.L, h->state,
+                                                                                   h->P.n_w, sp, h->scr);
   else
     k_propagate_m<<<walker_grid(h, h->P.n_w), h->wpb * 32, smem, h->stream>>>(h->S, h->P.L, h->P.M, h->state,
                                                                               h->P.n_w, sp, h->scr);

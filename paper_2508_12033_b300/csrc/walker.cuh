@@ -268,6 +268,15 @@ __device__ __forceinline__ double pade_value(double s, double c, double b) {
   return c * r * rcp_nr(fma(b, r, 1.0));
 }
 
+// Component of (xi - xj) along hop axis ax: the Cartesian component, or the
+// projection on versor ax of a randomised lattice.
+template <bool ROT>
+__device__ __forceinline__ double proj(const double* xi, const double* xj, const double* V, int ax) {
+  if (!ROT) return xi[ax] - xj[ax];
+  const double dx = xi[0] - xj[0], dy = xi[1] - xj[1], dz = xi[2] - xj[2];
+  return fma(dz, V[3 * ax + 2], fma(dy, V[3 * ax + 1], dx * V[3 * ax]));
+}
+
 // Jastrow pair constant for electrons i, j.
 __device__ __forceinline__ double pair_c(const DevSys& S, const Layout& L, int i, int j) {
   return ((i < L.n_up) == (j < L.n_up)) ? S.j2_par : S.j2_anti;
@@ -351,6 +360,7 @@ __device__ void det_derivs(const Layout& L, const double* __restrict__ gblk, dou
 // Fills the incremental caches: geometry, pair distances, per-electron
 // Jastrow sums and derivatives, per-hop determinant ratio and Jastrow sums,
 // and (when scr.chi is set) the basis values at every hop.
+template <bool ROT>
 __device__ EvalOut eval_full(const DevSys& S, const Layout& L, const double* __restrict__ gblk, double* sm, Scr scr,
                              double a, int node_rule, const double* T, int lane) {
   const int ne = L.n_e, nbf = L.n_bf, nn = S.n_nuc, P = L.n_hop;
@@ -363,6 +373,7 @@ __device__ EvalOut eval_full(const DevSys& S, const Layout& L, const double* __r
   double* hD = sm + L.s_hd;
   double* hJ1 = sm + L.s_hj1;
   double* hJ2 = sm + L.s_hj2;
+  const double* V = sm + L.s_v;
   const double a2 = a * a;
   // (1) current-configuration Jastrow sums/derivatives and geometry; G lanes
   // share one electron, each taking every G-th partner (electrons, then nuclei)
@@ -393,8 +404,10 @@ __device__ EvalOut eval_full(const DevSys& S, const Layout& L, const double* __r
             const double dx = xe - __ldg(S.R + 3 * I), dy = ye - __ldg(S.R + 3 * I + 1),
                          dz = ze - __ldg(S.R + 3 * I + 2);
             const double s = sqdist(dx, dy, dz);
-            double* gg = geo + (e * nn + I) * 4;
+            double* gg = geo + (e * nn + I) * 8;
             gg[0] = dx; gg[1] = dy; gg[2] = dz; gg[3] = s + a2;
+            if (ROT)
+              for (int k = 0; k < 3; ++k) gg[4 + k] = fma(dz, V[3 * k + 2], fma(dy, V[3 * k + 1], dx * V[3 * k]));
             const double A = __ldg(S.j1A + I);
             if (A != 0.0) {
               const Pair p = pade(s, -A, __ldg(S.j1B + I));
@@ -431,10 +444,14 @@ __device__ EvalOut eval_full(const DevSys& S, const Layout& L, const double* __r
     const double* gi = g + i * nbf;
     double det = 0.0, J1 = 0.0, J2 = 0.0;
     for (int I = 0; I < nn; ++I) {
-      const double* gg = geo + (i * nn + I) * 4;
-      const double s = fma(s2a, gg[ax], gg[3]);            // |r' - R_I|^2
+      const double* gg = geo + (i * nn + I) * 8;
+      const double s = fma(s2a, ROT ? gg[4 + ax] : gg[ax], gg[3]);   // |r' - R_I|^2
       double dv[3] = {gg[0], gg[1], gg[2]};
-      dv[ax] += sa;
+      if (ROT) {
+        for (int k = 0; k < 3; ++k) dv[k] = fma(sa, V[3 * ax + k], dv[k]);
+      } else {
+        dv[ax] += sa;
+      }
       const double A = __ldg(S.j1A + I);
       if (A != 0.0) J1 += pade_value(s, -A, __ldg(S.j1B + I));
       for (int sh = __ldg(S.atom_sh + I); sh < __ldg(S.atom_sh + I + 1); ++sh) {
@@ -457,10 +474,9 @@ __device__ EvalOut eval_full(const DevSys& S, const Layout& L, const double* __r
         }
       }
     }
-    const double xia = x[3 * i + ax];
     for (int j = 0; j < ne; ++j) {
       if (j == i) continue;
-      J2 += pade_value(fma(s2a, xia - x[3 * j + ax], pr2[i * ne + j]), pair_c(S, L, i, j), S.j2_b);
+      J2 += pade_value(fma(s2a, proj<ROT>(x + 3 * i, x + 3 * j, V, ax), pr2[i * ne + j]), pair_c(S, L, i, j), S.j2_b);
     }
     hD[p] = det;
     hJ1[p] = J1;
@@ -479,6 +495,7 @@ __device__ EvalOut eval_full(const DevSys& S, const Layout& L, const double* __r
 // all_blocks (after a from-scratch inversion changed B of both blocks) the
 // determinant ratios and derivatives of every electron are refreshed from the
 // cached basis values.
+template <bool ROT>
 __device__ EvalOut eval_incr(const DevSys& S, const Layout& L, const double* __restrict__ gblk, double* sm, Scr scr,
                              int m, bool all_blocks, double a, int node_rule, const double* T, int lane) {
   const int ne = L.n_e, nbf = L.n_bf, nn = S.n_nuc, P = L.n_hop;
@@ -493,6 +510,7 @@ __device__ EvalOut eval_incr(const DevSys& S, const Layout& L, const double* __r
   double* hJ1 = sm + L.s_hj1;
   double* hJ2 = sm + L.s_hj2;
   double* tmp = sm + L.s_tmp;
+  const double* V = sm + L.s_v;
   const double a2 = a * a;
   const int per = ne - 1 + nn;
   const double xm = x[3 * m], ym = x[3 * m + 1], zm = x[3 * m + 2];
@@ -516,8 +534,10 @@ __device__ EvalOut eval_incr(const DevSys& S, const Layout& L, const double* __r
         const int I = t - (ne - 1);
         const double dx = xm - __ldg(S.R + 3 * I), dy = ym - __ldg(S.R + 3 * I + 1), dz = zm - __ldg(S.R + 3 * I + 2);
         const double s = sqdist(dx, dy, dz);
-        double* gg = geo + (m * nn + I) * 4;
+        double* gg = geo + (m * nn + I) * 8;
         gg[0] = dx; gg[1] = dy; gg[2] = dz; gg[3] = s + a2;
+        if (ROT)
+          for (int k = 0; k < 3; ++k) gg[4 + k] = fma(dz, V[3 * k + 2], fma(dy, V[3 * k + 1], dx * V[3 * k]));
         const double A = __ldg(S.j1A + I);
         if (A != 0.0) {
           const Pair p = pade(s, -A, __ldg(S.j1B + I));
@@ -572,8 +592,8 @@ __device__ EvalOut eval_incr(const DevSys& S, const Layout& L, const double* __r
     const int d = o / S.n_shell, sh = o - d * S.n_shell, ax = d >> 1;
     const double sa = (d & 1) ? -a : a;
     const int I = __ldg(S.sh_atom + sh);
-    const double* gg = geo + (m * nn + I) * 4;
-    const double s = fma(sa + sa, gg[ax], gg[3]);
+    const double* gg = geo + (m * nn + I) * 8;
+    const double s = fma(sa + sa, ROT ? gg[4 + ax] : gg[ax], gg[3]);
     const int l = __ldg(S.sh_l + sh), np = __ldg(S.sh_nprim + sh), off = __ldg(S.sh_off + sh), bf = __ldg(S.sh_bf + sh);
     const double arg = l == -1 ? s * rsqrt_nr(s) : s;
     double rad = 0.0;
@@ -582,7 +602,10 @@ __device__ EvalOut eval_incr(const DevSys& S, const Layout& L, const double* __r
     if (l != 1) {
       scr.chi[(size_t)bf * P + p] = rad;
     } else {
-      for (int k = 0; k < 3; ++k) scr.chi[(size_t)(bf + k) * P + p] = (gg[k] + (k == ax ? sa : 0.0)) * rad;
+      for (int k = 0; k < 3; ++k) {
+        const double dk = ROT ? fma(sa, V[3 * ax + k], gg[k]) : gg[k] + (k == ax ? sa : 0.0);
+        scr.chi[(size_t)(bf + k) * P + p] = dk * rad;
+      }
     }
   }
   for (int o = lane; o < 6 * per; o += WARP) {
@@ -591,12 +614,13 @@ __device__ EvalOut eval_incr(const DevSys& S, const Layout& L, const double* __r
     double v = 0.0;
     if (t < ne - 1) {
       const int j = t < m ? t : t + 1;
-      v = pade_value(fma(sa + sa, x[3 * m + ax] - x[3 * j + ax], pr2[m * ne + j]), pair_c(S, L, m, j), S.j2_b);
+      v = pade_value(fma(sa + sa, proj<ROT>(x + 3 * m, x + 3 * j, V, ax), pr2[m * ne + j]), pair_c(S, L, m, j),
+                     S.j2_b);
     } else {
       const int I = t - (ne - 1);
       const double A = __ldg(S.j1A + I);
-      const double* gg = geo + (m * nn + I) * 4;
-      if (A != 0.0) v = pade_value(fma(sa + sa, gg[ax], gg[3]), -A, __ldg(S.j1B + I));
+      const double* gg = geo + (m * nn + I) * 8;
+      if (A != 0.0) v = pade_value(fma(sa + sa, ROT ? gg[4 + ax] : gg[ax], gg[3]), -A, __ldg(S.j1B + I));
     }
     tmp[o] = v;
   }
@@ -626,10 +650,9 @@ __device__ EvalOut eval_incr(const DevSys& S, const Layout& L, const double* __r
     const int d = p - 6 * i, ax = d >> 1;
     const double s2a = (d & 1) ? -2.0 * a : 2.0 * a;
     const double c = pair_c(S, L, i, m);
-    const double xia = x[3 * i + ax];
     const double so = sqdist(x[3 * i] - xo[0], x[3 * i + 1] - xo[1], x[3 * i + 2] - xo[2]) + a2;
-    const double vo = pade_value(fma(s2a, xia - xo[ax], so), c, S.j2_b);
-    const double vn = pade_value(fma(s2a, xia - x[3 * m + ax], pr2[i * ne + m]), c, S.j2_b);
+    const double vo = pade_value(fma(s2a, proj<ROT>(x + 3 * i, xo, V, ax), so), c, S.j2_b);
+    const double vn = pade_value(fma(s2a, proj<ROT>(x + 3 * i, x + 3 * m, V, ax), pr2[i * ne + m]), c, S.j2_b);
     hJ2[p] += vn - vo;
   }
   __threadfence_block();
@@ -666,7 +689,7 @@ __device__ EvalOut init_walker(const DevSys& S, const Layout& L, double* __restr
   __threadfence_block();
   singular = reinvert(L, gblk, sm, scr.gj, lane);
   compute_g(S, L, sm, scr.g, 0, L.n_e, lane);
-  return eval_full(S, L, gblk, sm, scr, a, node_rule, T, lane);
+  return eval_full<false>(S, L, gblk, sm, scr, a, node_rule, T, lane);
 }
 
 // Heat-bath choice over the kept hops (r > 0) in the order p = 6 i + d: the
@@ -707,6 +730,7 @@ __device__ int choose_hop(const double* rat, int n_hop, double u, int lane) {
 // Apply hop p: orbital derivatives at the moved electron, Sherman-Morrison
 // update of its spin block and of g by the same factors, cache, potential and
 // position update; the old position goes to s_xo.
+template <bool ROT>
 __device__ void apply_hop(const DevSys& S, const Layout& L, double* __restrict__ gblk, double* sm, Scr scr, int p,
                           double a, const double* T, int lane) {
   double* x = sm + L.s_x;
@@ -720,7 +744,13 @@ __device__ void apply_hop(const DevSys& S, const Layout& L, double* __restrict__
   double* grow = chi5 + 5 * L.n_bf;
   const int i = p / 6, d = p - 6 * i;
   double q[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
-  q[d >> 1] += (d & 1) ? -a : a;
+  const double sa = (d & 1) ? -a : a;
+  if (ROT) {
+    const double* V = sm + L.s_v;
+    for (int k = 0; k < 3; ++k) q[k] = fma(sa, V[3 * (d >> 1) + k], q[k]);
+  } else {
+    q[d >> 1] += sa;
+  }
   const SpinRef sr = spin_ref(L, i);
   orbital_derivs(S, L, q, sr.n, chi5, phi5, T, lane);
   double* B = bt + sr.bt_off;   // B^T of the spin block: B[j * n + k] = (A^{-1})_{k j}
@@ -779,7 +809,32 @@ struct StepParams {
   int node_rule;
   int reinv_period;
   unsigned long long* stamps;   // optional: per walker (start ns, end ns, SM id)
+  int rotate;                   // randomised lattice: new versors every interval
 };
+
+// Hop versors of walker slot w in an interval (rows of V): one uniformly random
+// rotation of the Cartesian axes (Shoemake, "Uniform random rotations",
+// Graphics Gems III, 1992) from three Philox uniforms: counter
+// (w, 2^32-1, interval, 2) words 0-1 and 2-3, counter (w, 2^32-1, interval, 3)
+// words 0-1.
+__host__ __device__ inline void interval_versors(uint64_t seed, uint32_t w, uint32_t interval, double V[9]) {
+  uint32_t c[4] = {w, 0xFFFFFFFFu, interval, 2u};
+  philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+  const double u1 = uniform53(c[0], c[1]), u2 = uniform53(c[2], c[3]);
+  uint32_t e[4] = {w, 0xFFFFFFFFu, interval, 3u};
+  philox4x32_10(e, (uint32_t)seed, (uint32_t)(seed >> 32));
+  const double u3 = uniform53(e[0], e[1]);
+  const double ta = sqrt(1.0 - u1), tb = sqrt(u1);
+  const double twopi = 6.283185307179586476925286766559;
+  const double qx = ta * sin(twopi * u2), qy = ta * cos(twopi * u2);
+  const double qz = tb * sin(twopi * u3), qw = tb * cos(twopi * u3);
+  // rotation matrix R of the unit quaternion; versor k (row k of V) = R e_k
+  const double R[9] = {1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy),
+                       2 * (qx * qy + qw * qz), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx),
+                       2 * (qx * qz - qw * qy), 2 * (qy * qz + qw * qx), 1 - 2 * (qx * qx + qy * qy)};
+  for (int k = 0; k < 3; ++k)
+    for (int j = 0; j < 3; ++j) V[3 * k + j] = R[3 * j + k];
+}
 
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
@@ -886,6 +941,7 @@ __global__ void k_eval_configs(DevSys S, Layout L, double* __restrict__ blocks, 
 // Algorithm 1 for kind 0).  The walker state stays in shared memory for the
 // whole interval; the first hop of an interval evaluates the new
 // configuration in full and fills the caches, later hops update them.
+template <bool ROT>
 __global__ void k_propagate(DevSys S, Layout L, double* __restrict__ state, int n_w, StepParams P, double* scratch) {
   extern __shared__ double smem[];
   const double* T = stage_table(S, smem);
@@ -899,11 +955,27 @@ __global__ void k_propagate(DevSys S, Layout L, double* __restrict__ state, int 
     const unsigned long long t_start = global_ns();
     double* gblk = state + (size_t)w * L.g_stride;
     load_block(L, gblk, sm, lane);
+    bool g_valid = false, cached = false;
+    if (ROT) {
+      // new versors for this interval: the stored evaluation used the old ones
+      if (lane == 0) interval_versors(P.seed, (uint32_t)w, P.interval, sm + L.s_v);
+      __syncwarp();
+      compute_g(S, L, sm, scr.g, 0, L.n_e, lane);
+      const EvalOut e0 = eval_full<ROT>(S, L, gblk, sm, scr, P.a, P.node_rule, T, lane);
+      g_valid = cached = true;
+      if (lane == 0) {
+        sc[SC_BBAR] = e0.bbar;
+        sc[SC_VSF] = e0.vsf;
+        sc[SC_WDIAG] = e0.W;
+        sc[SC_EL] = e0.eL;
+        sc[SC_NNODE] = e0.n_node;
+      }
+      __syncwarp();
+    }
     double weight = 1.0, tau_left = P.tau;
     double bbar = sc[SC_BBAR], Wd = sc[SC_WDIAG], eL = sc[SC_EL];
     uint32_t status = (uint32_t)sc[SC_STATUS];
     int moves = 0, since = (int)sc[SC_SINCE];
-    bool g_valid = false, cached = false;
     for (int k = 0;; ++k) {
       if (P.kind == 1 && k >= P.n_proj) break;
       double u_tau, u_move;
@@ -934,7 +1006,7 @@ __global__ void k_propagate(DevSys S, Layout L, double* __restrict__ state, int 
           compute_g(S, L, sm, scr.g, 0, L.n_e, lane);
           g_valid = true;
         }
-        apply_hop(S, L, gblk, sm, scr, p, P.a, T, lane);
+        apply_hop<ROT>(S, L, gblk, sm, scr, p, P.a, T, lane);
         ++moves;
         bool reinv = false;
         if (++since >= P.reinv_period) {
@@ -945,10 +1017,10 @@ __global__ void k_propagate(DevSys S, Layout L, double* __restrict__ state, int 
         }
         EvalOut e;
         if (!cached) {
-          e = eval_full(S, L, gblk, sm, scr, P.a, P.node_rule, T, lane);
+          e = eval_full<ROT>(S, L, gblk, sm, scr, P.a, P.node_rule, T, lane);
           cached = true;
         } else {
-          e = eval_incr(S, L, gblk, sm, scr, p / 6, reinv, P.a, P.node_rule, T, lane);
+          e = eval_incr<ROT>(S, L, gblk, sm, scr, p / 6, reinv, P.a, P.node_rule, T, lane);
         }
         bbar = e.bbar;
         Wd = e.W;

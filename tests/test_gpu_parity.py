@@ -289,3 +289,45 @@ def test_checkpoint_resume_is_bit_identical(tmp_path, precision):
     with pytest.raises(P.LrdmcError):
         c = P.Lrdmc(W.water_methane(), W.initial_walkers(W.water_methane(), 64), 0.2)
         c.load(path)
+
+
+@pytest.mark.parametrize("name,sysf,n_w,kind", [("h2", W.h2_sto3g, 64, 1), ("wm", W.water_methane, 32, 1),
+                                                 ("wm", W.water_methane, 32, 0)])
+def test_randomised_lattice_interval_matches_oracle(name, sysf, n_w, kind):
+    """Randomised lattice (one rotation of the hop versors per walker and
+    interval): the rotation comes from sin/cos/sqrt on both sides, so
+    positions agree to rounding (1e-12) rather than bit for bit."""
+    P = lib_or_skip()
+    s = sysf()
+    lr, x0 = _mk(P, s, n_w, reinv_period=7)
+    E0 = lr.e0
+    Wk = OL.init_walkers(s, x0, 0.2)
+    for j in range(2):
+        lr.propagate(kind, n_proj=8, tau=0.006 if name == "wm" else 0.05, max_moves=1000, rotate=True)
+        g = lr.get_walkers()
+        if kind == 1:
+            OL.propagate_lb(s, Wk, 0.2, E0, 8, seed=1, interval=j, rotate=True)
+        else:
+            OL.propagate_conventional(s, Wk, 0.2, 0.006, seed=1, interval=j, max_moves=1000, rotate=True)
+        np.testing.assert_array_equal(g["moves"], Wk.moves)
+        np.testing.assert_allclose(g["x"], Wk.x, rtol=0, atol=1e-12)
+        assert_close(g["w"], Wk.w, what="w")
+        assert_close(g["ev"][:, 3], Wk.ev["eL"], rtol=1e-9, what="eL")
+        assert_close(g["ratios"], Wk.ev["ratios"], rtol=1e-9, what="ratios")
+        # carry the same state into the next interval (no branching in between)
+        lr.set_walkers(g["x"])
+        Wk = OL.init_walkers(s, g["x"], 0.2)
+
+
+def test_randomised_lattice_exact_hydrogen_and_refusal_in_mixed():
+    P = lib_or_skip()
+    s = W.hydrogen_atom_sto(1.0)
+    lr, _ = _mk(P, s, 64)
+    for _ in range(4):
+        lr.propagate(P.LOAD_BALANCED, n_proj=10, rotate=True)
+        lr.branch()
+    assert abs(lr.energy()[0] + 0.5) < 1e-12
+    lm, _ = _mk(P, s, 16, precision=1)
+    with pytest.raises(P.LrdmcError) as e:
+        lm.propagate(P.LOAD_BALANCED, n_proj=2, rotate=True)
+    assert e.value.status == 7
