@@ -303,12 +303,13 @@ def test_randomised_lattice_interval_matches_oracle(name, sysf, n_w, kind):
     E0 = lr.e0
     Wk = OL.init_walkers(s, x0, 0.2)
     for j in range(2):
-        lr.propagate(kind, n_proj=8, tau=0.006 if name == "wm" else 0.05, max_moves=1000, rotate=True)
+        lr.propagate(kind, n_proj=8, tau=0.006, max_moves=1000, rotate=True)
         g = lr.get_walkers()
+        # the library's interval counter advances only at branching: both calls use interval 0
         if kind == 1:
-            OL.propagate_lb(s, Wk, 0.2, E0, 8, seed=1, interval=j, rotate=True)
+            OL.propagate_lb(s, Wk, 0.2, E0, 8, seed=1, interval=0, rotate=True)
         else:
-            OL.propagate_conventional(s, Wk, 0.2, 0.006, seed=1, interval=j, max_moves=1000, rotate=True)
+            OL.propagate_conventional(s, Wk, 0.2, 0.006, seed=1, interval=0, max_moves=1000, rotate=True)
         np.testing.assert_array_equal(g["moves"], Wk.moves)
         np.testing.assert_allclose(g["x"], Wk.x, rtol=0, atol=1e-12)
         assert_close(g["w"], Wk.w, what="w")
