@@ -60,6 +60,7 @@ class Walkers:
     ev: dict               # evaluation at x (ratios, bbar, vsf, W, eL, n_node, ...)
     status: np.ndarray     # (n_w,) uint32, sticky
     moves: np.ndarray      # (n_w,) hops made in the last interval
+    rotated: bool = False  # ev was taken on a randomised lattice (its versors)
 
 
 def rotation_matrices(u1, u2, u3):
@@ -137,11 +138,17 @@ def _reevaluate(sys, W: Walkers, sel, a, node_rule, versors=None):
 
 def _rotate(sys, W: Walkers, a, node_rule, seed, interval, ids, rotate):
     """With a randomised lattice, draw this interval's versors and re-evaluate
-    every walker with them (the stored evaluation used the previous axes)."""
+    every walker with them (the stored evaluation used the previous axes).  On
+    the fixed lattice, an evaluation left by a randomised interval is redone
+    on the Cartesian axes."""
     if not rotate:
+        if W.rotated:
+            _reevaluate(sys, W, np.arange(W.x.shape[0]), a, node_rule, None)
+            W.rotated = False
         return None
     V = interval_versors(seed, ids, interval)
     _reevaluate(sys, W, np.arange(W.x.shape[0]), a, node_rule, V)
+    W.rotated = True
     return V
 
 

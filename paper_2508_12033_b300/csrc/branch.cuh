@@ -164,20 +164,31 @@ __global__ void __launch_bounds__(BR_THREADS) k_reconfigure(const double* __rest
 }
 
 // new[alpha] = old[src[alpha]], weight reset to 1; skipped when status[0] != 0.
+// The walker's cache block (when the layout has one) moves with it.
 __global__ void k_gather(Layout L, const double* __restrict__ old_state, double* __restrict__ new_state,
+                         const double* __restrict__ old_cache, double* __restrict__ new_cache,
                          const int32_t* __restrict__ src, int n_w, const int32_t* __restrict__ status) {
   if (status[0] != 0) return;
   const int per = L.g_stride / 2;   // double2 per walker block (stride is a multiple of 16 doubles)
   const double2* o2 = reinterpret_cast<const double2*>(old_state);
   double2* n2 = reinterpret_cast<double2*>(new_state);
   const size_t total = (size_t)n_w * per;
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (size_t)gridDim.x * blockDim.x) {
+  const size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x, nth = (size_t)gridDim.x * blockDim.x;
+  for (size_t idx = tid; idx < total; idx += nth) {
     const int a = (int)(idx / per);
     const int o = (int)(idx - (size_t)a * per);
     double2 v = o2[(size_t)src[a] * per + o];
     if (2 * o == L.g_sc + SC_W) v.x = 1.0;
     n2[idx] = v;
+  }
+  if (!old_cache || L.c_stride == 0) return;
+  const int cper = L.c_stride / 2;
+  const double2* oc = reinterpret_cast<const double2*>(old_cache);
+  double2* nc = reinterpret_cast<double2*>(new_cache);
+  const size_t ctotal = (size_t)n_w * cper;
+  for (size_t idx = tid; idx < ctotal; idx += nth) {
+    const int a = (int)(idx / cper);
+    nc[idx] = oc[(size_t)src[a] * cper + (idx - (size_t)a * cper)];
   }
 }
 

@@ -29,6 +29,8 @@ enum Scalar : int {
   SC_STATUS = 6,  // sticky status bits
   SC_MOVES = 7,   // hops made in the last interval
   SC_SINCE = 8,   // hops since the last from-scratch inversion
+  SC_CACHE = 9,   // 1: the walker's cache block matches x and B on the fixed lattice
+  SC_ROTATED = 10,  // 1: the stored evaluation was taken on a randomised lattice
   SC_COUNT = 16
 };
 
@@ -38,6 +40,7 @@ struct DevSys {
   const double* R;       // n_nuc x 3
   const double* Z;       // n_nuc
   const double* rc;      // n_nuc
+  const double* irc;     // n_nuc: 1 / rc (erf-screened nuclei)
   const int* kind;       // n_nuc: 0 bare Coulomb, 1 erf-screened
   const double* j1A;     // n_nuc
   const double* j1B;     // n_nuc
@@ -72,14 +75,21 @@ struct Layout {
   // ratios, per-electron potentials (nu_ei, nu^a_ei), scalars
   int g_x, g_bt, g_cache, g_rat, g_pot, g_sc, g_stride;
   // shared memory per warp (FP64 kernels): positions, B^T, hop ratios,
-  // per-electron Jastrow terms [6], potentials [2], determinant derivatives
-  // [4], electron-nucleus geometry [8: d, |d|^2 + a^2, projections on the hop
-  // versors], pair distances, per-hop determinant
-  // ratio and one-body / pair Jastrow sums, per-hop scratch (also the moved
-  // electron's basis scratch), orbital rows, rank-1 factors, old position of
-  // the moved electron, hop versors [3][3], scalars
+  // potentials [2 per electron], per-electron Jastrow terms [6],
+  // determinant derivatives [4], electron-nucleus geometry [4 per (electron,
+  // nucleus): |d|^2 + a^2 and the components of d along the three hop
+  // versors], pair distances, per-hop determinant ratio and one-body / pair
+  // Jastrow sums, per-hop scratch (also the moved electron's basis scratch),
+  // orbital rows, rank-1 factors, old position of the moved electron, hop
+  // versors [3][3], scalars
   int s_x, s_bt, s_rat, s_ej, s_ep, s_dd, s_geo, s_pr2, s_hd, s_hj1, s_hj2, s_tmp, s_phi5, s_u, s_row, s_xo,
       s_v, s_sc, s_stride;
+  // per-walker cache block in global memory (FP64 kernels), kept across
+  // branching intervals: a copy of the shared-memory caches [s_ej, s_tmp),
+  // g_i = C^T B[:, i] [n_e][n_bf], the basis values at every hop [n_bf][6 n_e],
+  // the pair Jastrow term of every hop with every partner [n_e][6 n_e] and the
+  // pair terms at the current positions [n_e][n_e][4]
+  int c_mir, c_g, c_chi, c_u2, c_pt, c_stride;
 };
 
 __host__ __device__ inline int round_up(int v, int m) { return (v + m - 1) / m * m; }

@@ -37,11 +37,11 @@ struct Plan {
   int precision = 0;
   size_t smem_per_warp = 0;
   // workspace offsets (bytes)
-  size_t o_sys = 0, sys_bytes = 0, o_state = 0, o_alt = 0, state_bytes = 0, o_stats = 0, o_q = 0,
-         o_src = 0, o_dstat = 0, o_stamps = 0, o_scr = 0, total = 0;
+  size_t o_sys = 0, sys_bytes = 0, o_state = 0, o_alt = 0, state_bytes = 0, o_cache = 0, o_cache_alt = 0,
+         cache_bytes = 0, o_stats = 0, o_q = 0, o_src = 0, o_dstat = 0, o_stamps = 0, o_scr = 0, total = 0;
   int scratch_warps = 0;
   // system image offsets (bytes, inside the sys block)
-  size_t i_R, i_Z, i_rc, i_j1A, i_j1B, i_exps, i_coefs, i_C, i_kind, i_atom, i_l, i_nprim, i_off, i_bf, i_ash,
+  size_t i_R, i_Z, i_rc, i_irc, i_j1A, i_j1B, i_exps, i_coefs, i_C, i_kind, i_atom, i_l, i_nprim, i_off, i_bf, i_ash,
       i_tab, i_f_R, i_f_Z, i_f_rc, i_f_j1A, i_f_j1B, i_f_exps, i_f_coefs, i_f_C;
   std::string err;
 };
@@ -94,11 +94,11 @@ bool make_plan(const lrdmc_system* sys, const lrdmc_trial_wf* wf, const lrdmc_pa
   L.s_x = 0;
   L.s_bt = 3 * P.n_e;
   L.s_rat = L.s_bt + nbt;
-  L.s_ej = L.s_rat + L.n_hop;
-  L.s_ep = L.s_ej + 6 * P.n_e;
-  L.s_dd = L.s_ep + 2 * P.n_e;
+  L.s_ep = L.s_rat + L.n_hop;
+  L.s_ej = L.s_ep + 2 * P.n_e;
+  L.s_dd = L.s_ej + 6 * P.n_e;
   L.s_geo = L.s_dd + 4 * P.n_e;
-  L.s_pr2 = L.s_geo + 8 * P.n_e * P.n_nuc;
+  L.s_pr2 = L.s_geo + 4 * P.n_e * P.n_nuc;
   L.s_hd = L.s_pr2 + P.n_e * P.n_e;
   L.s_hj1 = L.s_hd + L.n_hop;
   L.s_hj2 = L.s_hj1 + L.n_hop;
@@ -110,6 +110,13 @@ bool make_plan(const lrdmc_system* sys, const lrdmc_trial_wf* wf, const lrdmc_pa
   L.s_v = L.s_xo + 4;
   L.s_sc = L.s_v + 12;
   L.s_stride = round_up(L.s_sc + SC_COUNT, 4);
+  // per-walker cache block (FP64 kernels only)
+  L.c_mir = 0;
+  L.c_g = round_up(L.s_tmp - L.s_ej, 4);
+  L.c_chi = L.c_g + P.n_e * P.n_bf;
+  L.c_u2 = L.c_chi + P.n_bf * L.n_hop;
+  L.c_pt = L.c_u2 + P.n_e * L.n_hop;
+  L.c_stride = P.precision == 0 ? round_up(L.c_pt + 4 * P.n_e * P.n_e, 16) : 0;
   P.M = layout_mixed(L, P.n_nuc, P.n_prim);
   P.smem_per_warp = P.precision == 0 ? (size_t)L.s_stride * sizeof(double) : (size_t)P.M.stride * sizeof(float);
   if (P.smem_per_warp + EXP_TAB * sizeof(double) > 200 * 1024) { P.err = "system too large for the per-warp shared-memory layout"; return false; }
@@ -119,6 +126,7 @@ bool make_plan(const lrdmc_system* sys, const lrdmc_trial_wf* wf, const lrdmc_pa
   P.i_R = take(sizeof(double) * 3 * P.n_nuc);
   P.i_Z = take(sizeof(double) * P.n_nuc);
   P.i_rc = take(sizeof(double) * P.n_nuc);
+  P.i_irc = take(sizeof(double) * P.n_nuc);
   P.i_j1A = take(sizeof(double) * P.n_nuc);
   P.i_j1B = take(sizeof(double) * P.n_nuc);
   P.i_exps = take(sizeof(double) * P.n_prim);
@@ -147,13 +155,17 @@ bool make_plan(const lrdmc_system* sys, const lrdmc_trial_wf* wf, const lrdmc_pa
   P.state_bytes = (size_t)P.n_w * L.g_stride * sizeof(double);
   P.o_state = w; w += align_up(P.state_bytes);
   P.o_alt = w; w += align_up(P.state_bytes);
+  P.cache_bytes = (size_t)P.n_w * L.c_stride * sizeof(double);
+  P.o_cache = w; w += align_up(P.cache_bytes);
+  P.o_cache_alt = w; w += align_up(P.cache_bytes);
   P.o_stats = w; w += align_up(sizeof(double) * BS_COUNT);
   P.o_q = w; w += align_up(sizeof(unsigned long long) * P.n_w);
   P.o_src = w; w += align_up(sizeof(int32_t) * P.n_w);
   P.o_dstat = w; w += align_up(sizeof(int32_t) * 16);
   P.o_stamps = w; w += align_up(sizeof(unsigned long long) * 3 * (size_t)P.n_w);
   P.scratch_warps = round_up(std::min(P.n_w, SCRATCH_WARPS_CAP), 4);
-  P.o_scr = w; w += align_up(sizeof(double) * scratch_doubles(L) * (size_t)P.scratch_warps);
+  const size_t per_warp = P.precision == 0 ? scratch_doubles(L) : scratch_doubles_m(L);
+  P.o_scr = w; w += align_up(sizeof(double) * per_warp * (size_t)P.scratch_warps);
   P.total = w;
   return true;
 }
@@ -227,6 +239,8 @@ struct lrdmc_s {
   lrdmc_params prm{};
   double* state = nullptr;
   double* alt = nullptr;
+  double* cache = nullptr;       // per-walker cache blocks (FP64), null for the mixed kernels
+  double* cache_alt = nullptr;
   double* stats = nullptr;
   unsigned long long* Q = nullptr;
   int32_t* src = nullptr;
@@ -305,8 +319,9 @@ static lrdmc_status place_walkers(lrdmc_handle h, const double* x, const double*
   }
   const int smem = smem_bytes(h);
   if (P.precision == 0)
-    k_init_walkers<<<walker_grid(h, P.n_w), h->wpb * 32, smem, h->stream>>>(h->S, P.L, h->state, dx, dw, P.n_w,
-                                                                            h->prm.a, h->prm.node_rule, h->scr);
+    k_init_walkers<<<walker_grid(h, P.n_w), h->wpb * 32, smem, h->stream>>>(h->S, P.L, h->state, h->cache, dx, dw,
+                                                                            P.n_w, h->prm.a, h->prm.node_rule,
+                                                                            h->scr);
   else
     k_init_walkers_m<<<walker_grid(h, P.n_w), h->wpb * 32, smem, h->stream>>>(h->S, P.L, P.M, h->state, dx, dw,
                                                                               P.n_w, h->prm.a, h->prm.node_rule,
@@ -402,6 +417,11 @@ lrdmc_status lrdmc_create(const lrdmc_system* sys, const lrdmc_trial_wf* wf, con
   putd(P.i_R, sys->R, 3 * (size_t)P.n_nuc);
   putd(P.i_Z, sys->Z, P.n_nuc);
   putd(P.i_rc, sys->r_c, P.n_nuc);
+  {
+    std::vector<double> irc(P.n_nuc);
+    for (int I = 0; I < P.n_nuc; ++I) irc[I] = sys->pot_kind[I] == 1 ? 1.0 / sys->r_c[I] : 0.0;
+    putd(P.i_irc, irc.data(), P.n_nuc);
+  }
   putd(P.i_j1A, wf->j1_A, P.n_nuc);
   putd(P.i_j1B, wf->j1_B, P.n_nuc);
   putd(P.i_exps, wf->exps, P.n_prim);
@@ -458,6 +478,7 @@ lrdmc_status lrdmc_create(const lrdmc_system* sys, const lrdmc_trial_wf* wf, con
   S.R = (const double*)(dsys + P.i_R);
   S.Z = (const double*)(dsys + P.i_Z);
   S.rc = (const double*)(dsys + P.i_rc);
+  S.irc = (const double*)(dsys + P.i_irc);
   S.j1A = (const double*)(dsys + P.i_j1A);
   S.j1B = (const double*)(dsys + P.i_j1B);
   S.exps = (const double*)(dsys + P.i_exps);
@@ -492,6 +513,8 @@ lrdmc_status lrdmc_create(const lrdmc_system* sys, const lrdmc_trial_wf* wf, con
   S.v_ii = vii;
   h->state = (double*)(base + P.o_state);
   h->alt = (double*)(base + P.o_alt);
+  h->cache = P.cache_bytes ? (double*)(base + P.o_cache) : nullptr;
+  h->cache_alt = P.cache_bytes ? (double*)(base + P.o_cache_alt) : nullptr;
   h->stats = (double*)(base + P.o_stats);
   h->Q = (unsigned long long*)(base + P.o_q);
   h->src = (int32_t*)(base + P.o_src);
@@ -502,19 +525,28 @@ lrdmc_status lrdmc_create(const lrdmc_system* sys, const lrdmc_trial_wf* wf, con
   // launch geometry: up to 4 walkers (warps) per CTA within the shared-memory budget
   int smem_optin = 0;
   CK(h, cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
-  h->wpb = 4;
-  while (h->wpb > 1 && (size_t)smem_bytes(h) > (size_t)smem_optin) h->wpb >>= 1;
-  if ((size_t)smem_bytes(h) > (size_t)smem_optin)
-    return fail(h, LRDMC_ERR_UNSUPPORTED, "walker working set exceeds shared memory");
   lrdmc_status st = set_kernel_smem(h, smem_optin);
   if (st != LRDMC_OK) return st;
-  int bps = 0;
-  if (P.precision == 0)
-    CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_propagate<false>, h->wpb * 32, smem_bytes(h)));
-  else
-    CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_propagate_m, h->wpb * 32, smem_bytes(h)));
-  if (bps < 1) return fail(h, LRDMC_ERR_UNSUPPORTED, "propagate kernel does not fit on an SM");
-  h->grid = std::min(bps * h->num_sms, P.scratch_warps / h->wpb);
+  // walkers (warps) per CTA: the count that keeps the most warps resident per
+  // SM (shared memory is the limit; ties go to larger CTAs, fewer table copies)
+  int best_warps = 0, best_wpb = 1, best_bps = 0;
+  for (int wpb = 1; wpb <= 8; ++wpb) {
+    h->wpb = wpb;
+    if ((size_t)smem_bytes(h) > (size_t)smem_optin) break;
+    int bps = 0;
+    if (P.precision == 0)
+      CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_propagate<false>, wpb * 32, smem_bytes(h)));
+    else
+      CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_propagate_m, wpb * 32, smem_bytes(h)));
+    if (bps >= 1 && bps * wpb >= best_warps) {
+      best_warps = bps * wpb;
+      best_wpb = wpb;
+      best_bps = bps;
+    }
+  }
+  if (best_warps == 0) return fail(h, LRDMC_ERR_UNSUPPORTED, "walker working set exceeds shared memory");
+  h->wpb = best_wpb;
+  h->grid = std::max(1, std::min(best_bps * h->num_sms, P.scratch_warps / h->wpb));
   st = place_walkers(h, x0, nullptr);
   if (st != LRDMC_OK) return st;
   std::vector<double> buf;
@@ -566,10 +598,10 @@ lrdmc_status lrdmc_propagate(lrdmc_handle h, const lrdmc_schedule* sch) {
   if (h->P.precision == 0)
     if (sp.rotate)
       k_propagate<true><<<walker_grid(h, h->P.n_w), h->wpb * 32, smem, h->stream>>>(h->S, h->P.L, h->state,
-                                                                                  h->P.n_w, sp, h->scr);
+                                                                                  h->cache, h->P.n_w, sp, h->scr);
     else
       k_propagate<false><<<walker_grid(h, h->P.n_w), h->wpb * 32, smem, h->stream>>>(h->S, h->P.L, h->state,
-                                                                                   h->P.n_w, sp, h->scr);
+                                                                                   h->cache, h->P.n_w, sp, h->scr);
   else
     k_propagate_m<<<walker_grid(h, h->P.n_w), h->wpb * 32, smem, h->stream>>>(h->S, h->P.L, h->P.M, h->state,
                                                                               h->P.n_w, sp, h->scr);
@@ -589,9 +621,10 @@ lrdmc_status lrdmc_branch(lrdmc_handle h) {
   k_reconfigure<<<1, BR_THREADS, 0, h->stream>>>(h->state + P.L.g_sc + SC_W, P.L.g_stride, P.n_w, xi, h->Q,
                                                  h->src, h->dstat, h->stats);
   LAUNCHED(h);
-  const size_t per = (size_t)P.n_w * P.L.g_stride / 2;
+  const size_t per = (size_t)P.n_w * std::max(P.L.g_stride, P.L.c_stride) / 2;
   const int gb = (int)std::min<size_t>((per + 255) / 256, (size_t)h->num_sms * 8);
-  k_gather<<<std::max(1, gb), 256, 0, h->stream>>>(P.L, h->state, h->alt, h->src, P.n_w, h->dstat);
+  k_gather<<<std::max(1, gb), 256, 0, h->stream>>>(P.L, h->state, h->alt, h->cache, h->cache_alt, h->src, P.n_w,
+                                                   h->dstat);
   LAUNCHED(h);
   double hs[BS_COUNT];
   CK(h, cudaMemcpyAsync(hs, h->stats, sizeof hs, cudaMemcpyDeviceToHost, h->stream));
@@ -599,6 +632,7 @@ lrdmc_status lrdmc_branch(lrdmc_handle h) {
   if (hs[BS_BAD] != 0.0)
     return fail(h, LRDMC_ERR_NONFINITE, "weights negative, non-finite or all zero: population unchanged");
   std::swap(h->state, h->alt);
+  std::swap(h->cache, h->cache_alt);
   h->wbar.push_back(hs[BS_SUMW] / (double)P.n_w);
   h->ebar.push_back(hs[BS_SUMFE] / hs[BS_SUMF]);
   h->e0h.push_back(h->E0);
@@ -677,8 +711,8 @@ lrdmc_status lrdmc_set_walkers(lrdmc_handle h, const double* x, const double* w)
 lrdmc_status lrdmc_clear_status(lrdmc_handle h) {
   if (!h || !h->state) return LRDMC_ERR_ARG;
   DeviceGuard g(h->device);
-  k_clear_status<<<std::max(1, std::min(1024, (h->P.n_w + 255) / 256)), 256, 0, h->stream>>>(h->P.L, h->state,
-                                                                                             h->P.n_w);
+  k_set_scalar<<<std::max(1, std::min(1024, (h->P.n_w + 255) / 256)), 256, 0, h->stream>>>(h->P.L, h->state,
+                                                                                           h->P.n_w, SC_STATUS, 0.0);
   LAUNCHED(h);
   return LRDMC_OK;
 }
@@ -688,7 +722,7 @@ constexpr uint64_t CKPT_MAGIC = 0x4c52444d43434b31ull;   // "LRDMCCK1"
 
 struct CkptHeader {
   uint64_t magic;
-  int32_t n_w, n_e, g_stride, precision, n_hist, pad;
+  int32_t n_w, n_e, g_stride, precision, n_hist, c_stride;
   uint64_t seed;
   double a, E0;
   uint32_t interval, last_kind;
@@ -699,17 +733,21 @@ lrdmc_status lrdmc_save(lrdmc_handle h, const char* path) {
   if (!h || !h->state || !path) return LRDMC_ERR_ARG;
   DeviceGuard g(h->device);
   const Plan& P = h->P;
-  std::vector<double> st((size_t)P.n_w * P.L.g_stride);
+  std::vector<double> st((size_t)P.n_w * P.L.g_stride), cs((size_t)P.n_w * P.L.c_stride);
   CK(h, cudaMemcpyAsync(st.data(), h->state, sizeof(double) * st.size(), cudaMemcpyDeviceToHost, h->stream));
+  if (!cs.empty())
+    CK(h, cudaMemcpyAsync(cs.data(), h->cache, sizeof(double) * cs.size(), cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
   CkptHeader hd{};
   hd.magic = CKPT_MAGIC;
   hd.n_w = P.n_w; hd.n_e = P.n_e; hd.g_stride = P.L.g_stride; hd.precision = P.precision;
+  hd.c_stride = P.L.c_stride;
   hd.n_hist = (int32_t)h->wbar.size();
   hd.seed = h->prm.seed; hd.a = h->prm.a; hd.E0 = h->E0; hd.interval = h->interval; hd.last_kind = h->last_kind;
   FILE* f = fopen(path, "wb");
   if (!f) return fail(h, LRDMC_ERR_ARG, std::string("cannot open ") + path);
-  bool ok = fwrite(&hd, sizeof hd, 1, f) == 1 && fwrite(st.data(), sizeof(double), st.size(), f) == st.size();
+  bool ok = fwrite(&hd, sizeof hd, 1, f) == 1 && fwrite(st.data(), sizeof(double), st.size(), f) == st.size() &&
+            fwrite(cs.data(), sizeof(double), cs.size(), f) == cs.size();
   const size_t m = h->wbar.size();
   if (m) {
     ok = ok && fwrite(h->wbar.data(), sizeof(double), m, f) == m && fwrite(h->ebar.data(), sizeof(double), m, f) == m &&
@@ -730,12 +768,13 @@ lrdmc_status lrdmc_load(lrdmc_handle h, const char* path) {
   CkptHeader hd{};
   bool ok = fread(&hd, sizeof hd, 1, f) == 1;
   if (!ok || hd.magic != CKPT_MAGIC || hd.n_w != P.n_w || hd.n_e != P.n_e || hd.g_stride != P.L.g_stride ||
-      hd.precision != P.precision || hd.n_hist < 0) {
+      hd.c_stride != P.L.c_stride || hd.precision != P.precision || hd.n_hist < 0) {
     fclose(f);
     return fail(h, LRDMC_ERR_ARG, "checkpoint does not match this handle");
   }
-  std::vector<double> st((size_t)P.n_w * P.L.g_stride);
-  ok = fread(st.data(), sizeof(double), st.size(), f) == st.size();
+  std::vector<double> st((size_t)P.n_w * P.L.g_stride), cs((size_t)P.n_w * P.L.c_stride);
+  ok = fread(st.data(), sizeof(double), st.size(), f) == st.size() &&
+       fread(cs.data(), sizeof(double), cs.size(), f) == cs.size();
   const size_t m = (size_t)hd.n_hist;
   std::vector<double> wb(m), eb(m), e0(m), mm(m);
   std::vector<int> mx(m), sv(m);
@@ -749,6 +788,8 @@ lrdmc_status lrdmc_load(lrdmc_handle h, const char* path) {
   fclose(f);
   if (!ok) return fail(h, LRDMC_ERR_ARG, "checkpoint truncated");
   CK(h, cudaMemcpyAsync(h->state, st.data(), sizeof(double) * st.size(), cudaMemcpyHostToDevice, h->stream));
+  if (!cs.empty())
+    CK(h, cudaMemcpyAsync(h->cache, cs.data(), sizeof(double) * cs.size(), cudaMemcpyHostToDevice, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
   h->prm.seed = hd.seed;
   h->E0 = hd.E0;

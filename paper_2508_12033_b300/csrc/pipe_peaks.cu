@@ -17,6 +17,21 @@ __global__ void k_dfma(double* out, int iters, double s) {
   if (r == 12345.678) out[0] = r;
 }
 
+// FP64 FMA chains in the first `lanes` lanes of every warp only: whether a
+// partially active warp instruction costs the FP64 pipe less than a full one.
+template <int ILP>
+__global__ void k_dfma_lanes(double* out, int iters, double s, int lanes) {
+  if ((threadIdx.x & 31) >= lanes) return;
+  double a[ILP];
+  for (int j = 0; j < ILP; j++) a[j] = threadIdx.x * 1e-3 + j;
+  for (int i = 0; i < iters; i++)
+#pragma unroll
+    for (int j = 0; j < ILP; j++) a[j] = fma(a[j], s, 0.999);
+  double r = 0;
+  for (int j = 0; j < ILP; j++) r += a[j];
+  if (r == 12345.678) out[0] = r;
+}
+
 template <int ILP>
 __global__ void k_ffma(float* out, int iters, float s) {
   float a[ILP];
@@ -135,6 +150,12 @@ int main() {
   float ms = best_ms([&] { k_dfma<8><<<blocks, threads>>>(dout, it, 1.0000001); });
   const double dfma = n8 * it / (ms * 1e-3);
   printf("DFMA      %12.4g op/s  %8.3f TFLOP/s\n", dfma, 2 * dfma / 1e12);
+  for (int lanes : {1, 8, 16, 24}) {
+    const float ml = best_ms([&] { k_dfma_lanes<8><<<blocks, threads>>>(dout, it, 1.0000001, lanes); });
+    const double active = (double)blocks * (threads / 32) * lanes * 8 * it;
+    printf("DFMA %2d/32 lanes  %10.4g op/s  warp instructions cost %.2fx a full warp's\n", lanes,
+           active / (ml * 1e-3), ml / ms);
+  }
   ms = best_ms([&] { k_ffma<8><<<blocks, threads>>>(fout, it, 1.0000001f); });
   printf("FFMA      %12.4g op/s  %8.3f TFLOP/s  (%.1fx DFMA)\n", n8 * it / (ms * 1e-3), 2 * n8 * it / (ms * 1e-3) / 1e12,
          n8 * it / (ms * 1e-3) / dfma);

@@ -81,6 +81,19 @@ __device__ __forceinline__ void shell_derivs(const DevSys& S, int s, const doubl
   }
 }
 
+// Lanes per dot product when n_out dot products of length len are spread over
+// a warp: S in {1, 2, 4, 8} lanes take consecutive slices of one dot and are
+// combined by shuffles; chosen to minimise (warp passes) x (slice length) +
+// (shuffle levels), the FP64 instruction count of the warp.
+__device__ __forceinline__ int split_factor(int n_out, int len) {
+  int best = 1, cost = 1 << 30;
+  for (int c = 1, lv = 0; c <= 8; c <<= 1, ++lv) {
+    const int k = ((n_out * c + WARP - 1) / WARP) * ((len + c - 1) / c) + lv;
+    if (k < cost) { cost = k; best = c; }
+  }
+  return best;
+}
+
 // Orbital value/gradient/Laplacian of the first n_sig orbitals at point q:
 // phi5[c * n_max + k].  Warp-cooperative; chi5 is scratch of 5 n_bf doubles.
 __device__ void orbital_derivs(const DevSys& S, const Layout& L, const double q[3], int n_sig, double* chi5,
@@ -92,33 +105,42 @@ __device__ void orbital_derivs(const DevSys& S, const Layout& L, const double q[
     shell_derivs(S, s, d, d[0] * d[0] + d[1] * d[1] + d[2] * d[2], chi5, L.n_bf, T);
   }
   __syncwarp();
-  for (int o = lane; o < 5 * n_sig; o += WARP) {
-    const int c = o / n_sig, k = o - c * n_sig;
-    const double* crow = S.C + (size_t)k * L.n_bf;
-    const double* x = chi5 + c * L.n_bf;
+  const int n_out = 5 * n_sig, G = split_factor(n_out, L.n_bf);
+  const int chunk = (L.n_bf + G - 1) / G, n_task = n_out * G;
+  for (int base = 0; base < n_task; base += WARP) {
+    const int task = base + lane, o = task / G, part = task - o * G;
     double acc = 0.0;
-    for (int mu = 0; mu < L.n_bf; ++mu) acc = fma(__ldg(crow + mu), x[mu], acc);
-    phi5[c * L.n_max + k] = acc;
+    if (task < n_task) {
+      const int c = o / n_sig, k = o - c * n_sig;
+      const double* crow = S.C + (size_t)k * L.n_bf;
+      const double* x = chi5 + c * L.n_bf;
+      const int mu1 = min(L.n_bf, (part + 1) * chunk);
+      for (int mu = part * chunk; mu < mu1; ++mu) acc = fma(__ldg(crow + mu), x[mu], acc);
+    }
+    for (int sh = 1; sh < G; sh <<= 1) acc += __shfl_xor_sync(FULL, acc, sh);
+    if (task < n_task && part == 0) phi5[(o / n_sig) * L.n_max + (o % n_sig)] = acc;
   }
   __syncwarp();
 }
 
 // Bare and capped electron-nucleus potentials of one electron (Appendix D:
 // nu_ei and nu^a_ei), warp-cooperative over nuclei; result valid in all lanes.
-__device__ void electron_potentials(const DevSys& S, const double q[3], double a, int lane, double& nu,
+// 1/r from the refined reciprocal square root; ia = 1/a.
+__device__ void electron_potentials(const DevSys& S, const double q[3], double a, double ia, int lane, double& nu,
                                     double& nucap) {
   nu = 0.0;
   nucap = 0.0;
   for (int I = lane; I < S.n_nuc; I += WARP) {
     const double dx = q[0] - __ldg(S.R + 3 * I), dy = q[1] - __ldg(S.R + 3 * I + 1),
                  dz = q[2] - __ldg(S.R + 3 * I + 2);
-    const double r = sqrt(dx * dx + dy * dy + dz * dz);
+    const double s = fma(dz, dz, fma(dy, dy, dx * dx));
+    const double ir = rsqrt_nr(s);
     const double Z = __ldg(S.Z + I);
     if (__ldg(S.kind + I) == 0) {
-      nu -= Z / r;
-      nucap -= Z / fmax(r, a);
+      nu -= Z * ir;
+      nucap -= s >= a * a ? Z * ir : Z * ia;   // Z / max(r, a)
     } else {
-      const double v = -Z * erf(r / __ldg(S.rc + I)) / r;
+      const double v = -Z * erf(s * ir * __ldg(S.irc + I)) * ir;
       nu += v;
       nucap += v;
     }
@@ -174,23 +196,35 @@ __device__ bool warp_gauss_jordan(double* M, int N, int lane) {
   return false;
 }
 
-// Per-warp scratch in global memory (L2 resident): g_i = C^T B[:, i] for every
-// electron [n_e][n_bf], the basis values at every hop position [n_bf][6 n_e]
-// (mu-major so that lanes working on consecutive hops read consecutive words)
-// and the Gauss-Jordan work matrix [n_max][2 n_max].
+// Global-memory working arrays of one walker evaluation.  In the propagate
+// and initialisation kernels g, chi, u2 and pt point into the walker's cache
+// block; configuration evaluation uses per-warp scratch for g and keeps no
+// hop caches (chi, u2, pt null).  gj is per-warp scratch (the Gauss-Jordan
+// work matrix [n_max][2 n_max]).
 struct Scr {
-  double* g;
-  double* chi;
+  double* g;     // [n_e][n_bf]   g_i = C^T B[:, i]
+  double* chi;   // [n_bf][6 n_e] basis values at every hop (mu-major: lanes on consecutive hops read consecutive words)
+  double* u2;    // [n_e][6 n_e]  u2[j][p]: pair Jastrow term of hop p with partner j
+  double* pt;    // [n_e][n_e][4] pair terms at the current positions: u, u'/r, u'' + 2u'/r, 1/(2r)
   double* gj;
 };
 __host__ __device__ inline size_t scratch_doubles(const Layout& L) {
-  return (size_t)L.n_e * L.n_bf + (size_t)L.n_bf * L.n_hop + 2 * (size_t)L.n_max * L.n_max;
+  return (size_t)L.n_e * L.n_bf + 2 * (size_t)L.n_max * L.n_max;
 }
 __device__ __forceinline__ Scr warp_scratch(const Layout& L, double* base, int slot) {
   Scr s;
   s.g = base + (size_t)slot * scratch_doubles(L);
-  s.chi = s.g + (size_t)L.n_e * L.n_bf;
-  s.gj = s.chi + (size_t)L.n_bf * L.n_hop;
+  s.gj = s.g + (size_t)L.n_e * L.n_bf;
+  s.chi = s.u2 = s.pt = nullptr;
+  return s;
+}
+__device__ __forceinline__ Scr walker_scratch(const Layout& L, double* cblk, const Scr& warp) {
+  Scr s;
+  s.g = cblk + L.c_g;
+  s.chi = cblk + L.c_chi;
+  s.u2 = cblk + L.c_u2;
+  s.pt = cblk + L.c_pt;
+  s.gj = warp.gj;
   return s;
 }
 
@@ -394,20 +428,27 @@ __device__ EvalOut eval_full(const DevSys& S, const Layout& L, const double* __r
             const double s = sqdist(dx, dy, dz);
             pr2[e * ne + j] = s + a2;
             const Pair p = pade(s, pair_c(S, L, e, j), S.j2_b);
-            const double f = p.up * p.ir;
+            const double f = p.up * p.ir, lap = p.upp + 2.0 * f, hir = 0.5 * p.ir;
             U += p.u;
             gx = fma(f, dx, gx); gy = fma(f, dy, gy); gz = fma(f, dz, gz);
-            LJ += p.upp + 2.0 * f;
-            vee = fma(0.5, p.ir, vee);
+            LJ += lap;
+            vee += hir;
+            if (scr.pt) {
+              double* pt = scr.pt + 4 * (e * ne + j);
+              pt[0] = p.u; pt[1] = f; pt[2] = lap; pt[3] = hir;
+            }
           } else {
             const int I = t - (ne - 1);
             const double dx = xe - __ldg(S.R + 3 * I), dy = ye - __ldg(S.R + 3 * I + 1),
                          dz = ze - __ldg(S.R + 3 * I + 2);
             const double s = sqdist(dx, dy, dz);
-            double* gg = geo + (e * nn + I) * 8;
-            gg[0] = dx; gg[1] = dy; gg[2] = dz; gg[3] = s + a2;
-            if (ROT)
-              for (int k = 0; k < 3; ++k) gg[4 + k] = fma(dz, V[3 * k + 2], fma(dy, V[3 * k + 1], dx * V[3 * k]));
+            double* gg = geo + (e * nn + I) * 4;
+            gg[0] = s + a2;
+            if (ROT) {
+              for (int k = 0; k < 3; ++k) gg[1 + k] = fma(dz, V[3 * k + 2], fma(dy, V[3 * k + 1], dx * V[3 * k]));
+            } else {
+              gg[1] = dx; gg[2] = dy; gg[3] = dz;
+            }
             const double A = __ldg(S.j1A + I);
             if (A != 0.0) {
               const Pair p = pade(s, -A, __ldg(S.j1B + I));
@@ -444,12 +485,13 @@ __device__ EvalOut eval_full(const DevSys& S, const Layout& L, const double* __r
     const double* gi = g + i * nbf;
     double det = 0.0, J1 = 0.0, J2 = 0.0;
     for (int I = 0; I < nn; ++I) {
-      const double* gg = geo + (i * nn + I) * 8;
-      const double s = fma(s2a, ROT ? gg[4 + ax] : gg[ax], gg[3]);   // |r' - R_I|^2
-      double dv[3] = {gg[0], gg[1], gg[2]};
+      const double* gg = geo + (i * nn + I) * 4;
+      const double s = fma(s2a, gg[1 + ax], gg[0]);   // |r' - R_I|^2
+      double dv[3];
       if (ROT) {
-        for (int k = 0; k < 3; ++k) dv[k] = fma(sa, V[3 * ax + k], dv[k]);
+        for (int k = 0; k < 3; ++k) dv[k] = fma(sa, V[3 * ax + k], x[3 * i + k] - __ldg(S.R + 3 * I + k));
       } else {
+        dv[0] = gg[1]; dv[1] = gg[2]; dv[2] = gg[3];
         dv[ax] += sa;
       }
       const double A = __ldg(S.j1A + I);
@@ -476,7 +518,10 @@ __device__ EvalOut eval_full(const DevSys& S, const Layout& L, const double* __r
     }
     for (int j = 0; j < ne; ++j) {
       if (j == i) continue;
-      J2 += pade_value(fma(s2a, proj<ROT>(x + 3 * i, x + 3 * j, V, ax), pr2[i * ne + j]), pair_c(S, L, i, j), S.j2_b);
+      const double v =
+          pade_value(fma(s2a, proj<ROT>(x + 3 * i, x + 3 * j, V, ax), pr2[i * ne + j]), pair_c(S, L, i, j), S.j2_b);
+      J2 += v;
+      if (scr.u2) scr.u2[(size_t)j * P + p] = v;
     }
     hD[p] = det;
     hJ1[p] = J1;
@@ -494,7 +539,10 @@ __device__ EvalOut eval_full(const DevSys& S, const Layout& L, const double* __r
 // Jastrow sums and, outside m's spin block, their determinant ratios.  With
 // all_blocks (after a from-scratch inversion changed B of both blocks) the
 // determinant ratios and derivatives of every electron are refreshed from the
-// cached basis values.
+// cached basis values.  Pair terms with m are swapped, not recomputed: the old
+// term comes from the caches (scr.pt for the current positions, scr.u2 for
+// the hops) and the new term of hop d of electron i with m equals the term of
+// m's opposite hop (d ^ 1) with i, since r_i + s a e - r_m = -(r_m - s a e - r_i).
 template <bool ROT>
 __device__ EvalOut eval_incr(const DevSys& S, const Layout& L, const double* __restrict__ gblk, double* sm, Scr scr,
                              int m, bool all_blocks, double a, int node_rule, const double* T, int lane) {
@@ -514,37 +562,59 @@ __device__ EvalOut eval_incr(const DevSys& S, const Layout& L, const double* __r
   const double a2 = a * a;
   const int per = ne - 1 + nn;
   const double xm = x[3 * m], ym = x[3 * m + 1], zm = x[3 * m + 2];
-  // (A) electron m: geometry and its Jastrow sums from scratch
+  // (A) electron m: geometry and its Jastrow sums from scratch, one partner
+  // (electron, then nucleus) per lane; (B) the partner electron's sums swap
+  // their term with m (old term from scr.pt)
   {
+    const double xo0 = xo[0], xo1 = xo[1], xo2 = xo[2];
     double U = 0.0, gx = 0.0, gy = 0.0, gz = 0.0, LJ = 0.0, vee = 0.0;
     for (int t = lane; t < per; t += WARP) {
-      if (t < ne - 1) {
-        const int j = t < m ? t : t + 1;
-        const double dx = xm - x[3 * j], dy = ym - x[3 * j + 1], dz = zm - x[3 * j + 2];
-        const double s = sqdist(dx, dy, dz);
+      const bool pair = t < ne - 1;
+      const int j = t < m ? t : t + 1, I = t - (ne - 1);
+      double px, py, pz, c, b;
+      if (pair) {
+        px = x[3 * j]; py = x[3 * j + 1]; pz = x[3 * j + 2];
+        c = pair_c(S, L, m, j);
+        b = S.j2_b;
+      } else {
+        px = __ldg(S.R + 3 * I); py = __ldg(S.R + 3 * I + 1); pz = __ldg(S.R + 3 * I + 2);
+        c = -__ldg(S.j1A + I);
+        b = __ldg(S.j1B + I);
+      }
+      const double dx = xm - px, dy = ym - py, dz = zm - pz;
+      const double s = sqdist(dx, dy, dz);
+      // one Pade evaluation for both kinds; a nucleus without one-body term
+      // (c = 0) contributes zeros and is evaluated at a dummy distance
+      const Pair p = pade(pair || c != 0.0 ? s : 1.0, c, b);
+      const double f = p.up * p.ir, lap = p.upp + 2.0 * f;
+      U += p.u;
+      gx = fma(f, dx, gx); gy = fma(f, dy, gy); gz = fma(f, dz, gz);
+      LJ += lap;
+      if (pair) {
+        const double hir = 0.5 * p.ir;
+        vee += hir;
         pr2[m * ne + j] = s + a2;
         pr2[j * ne + m] = s + a2;
-        const Pair p = pade(s, pair_c(S, L, m, j), S.j2_b);
-        const double f = p.up * p.ir;
-        U += p.u;
-        gx = fma(f, dx, gx); gy = fma(f, dy, gy); gz = fma(f, dz, gz);
-        LJ += p.upp + 2.0 * f;
-        vee = fma(0.5, p.ir, vee);
+        double* pm = scr.pt + 4 * (m * ne + j);
+        double* pj = scr.pt + 4 * (j * ne + m);
+        const double ou = pm[0], of = pm[1], ol = pm[2], oh = pm[3];
+        const double ox = px - xo0, oy = py - xo1, oz = pz - xo2;
+        double* q = ej + 6 * j;
+        q[0] += p.u - ou;
+        q[1] += f * -dx - of * ox;
+        q[2] += f * -dy - of * oy;
+        q[3] += f * -dz - of * oz;
+        q[4] += lap - ol;
+        q[5] += hir - oh;
+        pm[0] = p.u; pm[1] = f; pm[2] = lap; pm[3] = hir;
+        pj[0] = p.u; pj[1] = f; pj[2] = lap; pj[3] = hir;
       } else {
-        const int I = t - (ne - 1);
-        const double dx = xm - __ldg(S.R + 3 * I), dy = ym - __ldg(S.R + 3 * I + 1), dz = zm - __ldg(S.R + 3 * I + 2);
-        const double s = sqdist(dx, dy, dz);
-        double* gg = geo + (m * nn + I) * 8;
-        gg[0] = dx; gg[1] = dy; gg[2] = dz; gg[3] = s + a2;
-        if (ROT)
-          for (int k = 0; k < 3; ++k) gg[4 + k] = fma(dz, V[3 * k + 2], fma(dy, V[3 * k + 1], dx * V[3 * k]));
-        const double A = __ldg(S.j1A + I);
-        if (A != 0.0) {
-          const Pair p = pade(s, -A, __ldg(S.j1B + I));
-          const double f = p.up * p.ir;
-          U += p.u;
-          gx = fma(f, dx, gx); gy = fma(f, dy, gy); gz = fma(f, dz, gz);
-          LJ += p.upp + 2.0 * f;
+        double* gg = geo + (m * nn + I) * 4;
+        gg[0] = s + a2;
+        if (ROT) {
+          for (int k = 0; k < 3; ++k) gg[1 + k] = fma(dz, V[3 * k + 2], fma(dy, V[3 * k + 1], dx * V[3 * k]));
+        } else {
+          gg[1] = dx; gg[2] = dy; gg[3] = dz;
         }
       }
     }
@@ -562,24 +632,6 @@ __device__ EvalOut eval_incr(const DevSys& S, const Layout& L, const double* __r
       q[0] = U; q[1] = gx; q[2] = gy; q[3] = gz; q[4] = LJ; q[5] = vee;
     }
   }
-  // (B) every other electron: swap its pair term with m (old -> new position)
-  for (int i = lane; i < ne; i += WARP) {
-    if (i == m) continue;
-    const double c = pair_c(S, L, i, m);
-    const double xi = x[3 * i], yi = x[3 * i + 1], zi = x[3 * i + 2];
-    const double ox = xi - xo[0], oy = yi - xo[1], oz = zi - xo[2];
-    const double nx = xi - xm, ny = yi - ym, nz = zi - zm;
-    const Pair po = pade(sqdist(ox, oy, oz), c, S.j2_b);
-    const Pair pn = pade(sqdist(nx, ny, nz), c, S.j2_b);
-    const double fo = po.up * po.ir, fn = pn.up * pn.ir;
-    double* q = ej + 6 * i;
-    q[0] += pn.u - po.u;
-    q[1] += fn * nx - fo * ox;
-    q[2] += fn * ny - fo * oy;
-    q[3] += fn * nz - fo * oz;
-    q[4] += (pn.upp + 2.0 * fn) - (po.upp + 2.0 * fo);
-    q[5] += 0.5 * (pn.ir - po.ir);
-  }
   // (C) determinant derivatives of the refreshed spin block(s)
   const SpinRef srm = spin_ref(L, m);
   const int b0 = all_blocks ? 0 : m - srm.ii, b1 = all_blocks ? ne : m - srm.ii + srm.n;
@@ -592,8 +644,8 @@ __device__ EvalOut eval_incr(const DevSys& S, const Layout& L, const double* __r
     const int d = o / S.n_shell, sh = o - d * S.n_shell, ax = d >> 1;
     const double sa = (d & 1) ? -a : a;
     const int I = __ldg(S.sh_atom + sh);
-    const double* gg = geo + (m * nn + I) * 8;
-    const double s = fma(sa + sa, ROT ? gg[4 + ax] : gg[ax], gg[3]);
+    const double* gg = geo + (m * nn + I) * 4;
+    const double s = fma(sa + sa, gg[1 + ax], gg[0]);
     const int l = __ldg(S.sh_l + sh), np = __ldg(S.sh_nprim + sh), off = __ldg(S.sh_off + sh), bf = __ldg(S.sh_bf + sh);
     const double arg = l == -1 ? s * rsqrt_nr(s) : s;
     double rad = 0.0;
@@ -603,7 +655,8 @@ __device__ EvalOut eval_incr(const DevSys& S, const Layout& L, const double* __r
       scr.chi[(size_t)bf * P + p] = rad;
     } else {
       for (int k = 0; k < 3; ++k) {
-        const double dk = ROT ? fma(sa, V[3 * ax + k], gg[k]) : gg[k] + (k == ax ? sa : 0.0);
+        const double dk = ROT ? fma(sa, V[3 * ax + k], x[3 * m + k] - __ldg(S.R + 3 * I + k))
+                              : gg[1 + k] + (k == ax ? sa : 0.0);
         scr.chi[(size_t)(bf + k) * P + p] = dk * rad;
       }
     }
@@ -611,49 +664,71 @@ __device__ EvalOut eval_incr(const DevSys& S, const Layout& L, const double* __r
   for (int o = lane; o < 6 * per; o += WARP) {
     const int d = o / per, t = o - d * per, ax = d >> 1;
     const double sa = (d & 1) ? -a : a;
-    double v = 0.0;
-    if (t < ne - 1) {
-      const int j = t < m ? t : t + 1;
-      v = pade_value(fma(sa + sa, proj<ROT>(x + 3 * m, x + 3 * j, V, ax), pr2[m * ne + j]), pair_c(S, L, m, j),
-                     S.j2_b);
+    const bool pair = t < ne - 1;
+    const int j = t < m ? t : t + 1, I = t - (ne - 1);
+    double s, c, b;
+    if (pair) {
+      s = fma(sa + sa, proj<ROT>(x + 3 * m, x + 3 * j, V, ax), pr2[m * ne + j]);
+      c = pair_c(S, L, m, j);
+      b = S.j2_b;
     } else {
-      const int I = t - (ne - 1);
-      const double A = __ldg(S.j1A + I);
-      const double* gg = geo + (m * nn + I) * 8;
-      if (A != 0.0) v = pade_value(fma(sa + sa, ROT ? gg[4 + ax] : gg[ax], gg[3]), -A, __ldg(S.j1B + I));
+      const double* gg = geo + (m * nn + I) * 4;
+      c = -__ldg(S.j1A + I);
+      b = __ldg(S.j1B + I);
+      s = c != 0.0 ? fma(sa + sa, gg[1 + ax], gg[0]) : 1.0;
     }
+    const double v = pade_value(s, c, b);
     tmp[o] = v;
+    if (pair) scr.u2[(size_t)j * P + 6 * m + d] = v;
   }
   __threadfence_block();
   __syncwarp();
-  if (lane < 6) {
+  {
+    // sums over partners of each of m's hops: four lanes per hop
+    const int d = lane >> 2, sub = lane & 3;
     double J1 = 0.0, J2 = 0.0;
-    for (int t = 0; t < per; ++t) {
-      if (t < ne - 1) J2 += tmp[lane * per + t];
-      else J1 += tmp[lane * per + t];
+    if (d < 6)
+      for (int t = sub; t < per; t += 4) {
+        const double v = tmp[d * per + t];
+        if (t < ne - 1) J2 += v;
+        else J1 += v;
+      }
+    J1 += __shfl_xor_sync(FULL, J1, 1);
+    J2 += __shfl_xor_sync(FULL, J2, 1);
+    J1 += __shfl_xor_sync(FULL, J1, 2);
+    J2 += __shfl_xor_sync(FULL, J2, 2);
+    if (d < 6 && sub == 0) {
+      hJ1[6 * m + d] = J1;
+      hJ2[6 * m + d] = J2;
     }
-    hJ1[6 * m + lane] = J1;
-    hJ2[6 * m + lane] = J2;
   }
-  // (E) determinant ratios of the refreshed block(s) from the cached basis values
-  for (int p = lane + 6 * b0; p < 6 * b1; p += WARP) {
-    const int i = p / 6;
-    const double* gi = g + i * nbf;
-    double det = 0.0;
-    for (int mu = 0; mu < nbf; ++mu) det = fma(scr.chi[(size_t)mu * P + p], gi[mu], det);
-    hD[p] = det;
+  // (E) determinant ratios of the refreshed block(s) from the cached basis
+  // values, each dot product split over G lanes
+  {
+    const int n_out = 6 * (b1 - b0), G = split_factor(n_out, nbf);
+    const int chunk = (nbf + G - 1) / G, n_task = n_out * G;
+    for (int base = 0; base < n_task; base += WARP) {
+      const int task = base + lane, o = task / G, part = task - o * G;
+      const int p = 6 * b0 + o;
+      double det = 0.0;
+      if (task < n_task) {
+        const double* gi = g + (p / 6) * nbf;
+        const int mu1 = min(nbf, (part + 1) * chunk);
+        for (int mu = part * chunk; mu < mu1; ++mu) det = fma(scr.chi[(size_t)mu * P + p], gi[mu], det);
+      }
+      for (int sh = 1; sh < G; sh <<= 1) det += __shfl_xor_sync(FULL, det, sh);
+      if (task < n_task && part == 0) hD[p] = det;
+    }
   }
   // (F) pair Jastrow sums of the other electrons' hops: swap the term with m
   for (int p = lane; p < P; p += WARP) {
     const int i = p / 6;
     if (i == m) continue;
-    const int d = p - 6 * i, ax = d >> 1;
-    const double s2a = (d & 1) ? -2.0 * a : 2.0 * a;
-    const double c = pair_c(S, L, i, m);
-    const double so = sqdist(x[3 * i] - xo[0], x[3 * i + 1] - xo[1], x[3 * i + 2] - xo[2]) + a2;
-    const double vo = pade_value(fma(s2a, proj<ROT>(x + 3 * i, xo, V, ax), so), c, S.j2_b);
-    const double vn = pade_value(fma(s2a, proj<ROT>(x + 3 * i, x + 3 * m, V, ax), pr2[i * ne + m]), c, S.j2_b);
-    hJ2[p] += vn - vo;
+    const int d = p - 6 * i;
+    const double vn = tmp[(d ^ 1) * per + (i < m ? i : i - 1)];
+    double* u = scr.u2 + (size_t)m * P + p;
+    hJ2[p] += vn - *u;
+    *u = vn;
   }
   __threadfence_block();
   __syncwarp();
@@ -673,13 +748,14 @@ __device__ EvalOut init_walker(const DevSys& S, const Layout& L, double* __restr
   double* cache = gblk + L.g_cache;
   const double* x = sm + L.s_x;
   double* ep = sm + L.s_ep;
+  const double ia = 1.0 / a;
   for (int i = 0; i < L.n_e; ++i) {
     const int n = i < L.n_up ? L.n_up : L.n_dn;
     const double q[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
     orbital_derivs(S, L, q, n, chi5, phi5, T, lane);
     for (int o = lane; o < 5 * L.n_max; o += WARP) cache[i * 5 * L.n_max + o] = phi5[o];
     double nu, nucap;
-    electron_potentials(S, q, a, lane, nu, nucap);
+    electron_potentials(S, q, a, ia, lane, nu, nucap);
     if (lane == 0) {
       ep[2 * i] = nu;
       ep[2 * i + 1] = nucap;
@@ -732,7 +808,7 @@ __device__ int choose_hop(const double* rat, int n_hop, double u, int lane) {
 // position update; the old position goes to s_xo.
 template <bool ROT>
 __device__ void apply_hop(const DevSys& S, const Layout& L, double* __restrict__ gblk, double* sm, Scr scr, int p,
-                          double a, const double* T, int lane) {
+                          double a, double ia, const double* T, int lane) {
   double* x = sm + L.s_x;
   double* bt = sm + L.s_bt;
   double* cache = gblk + L.g_cache;
@@ -782,7 +858,7 @@ __device__ void apply_hop(const DevSys& S, const Layout& L, double* __restrict__
   }
   for (int o = lane; o < 5 * L.n_max; o += WARP) cache[i * 5 * L.n_max + o] = phi5[o];
   double nu, nucap;
-  electron_potentials(S, q, a, lane, nu, nucap);
+  electron_potentials(S, q, a, ia, lane, nu, nucap);
   if (lane == 0) {
     double* xo = sm + L.s_xo;
     xo[0] = x[3 * i]; xo[1] = x[3 * i + 1]; xo[2] = x[3 * i + 2];
@@ -874,19 +950,34 @@ __device__ __forceinline__ void store_block(const Layout& L, double* __restrict_
   for (int o = lane; o < SC_COUNT; o += WARP) g[L.g_sc + o] = sm[L.s_sc + o];
 }
 
+// Shared-memory caches [s_ej, s_tmp) from / to the walker's cache block.
+__device__ __forceinline__ void load_mirror(const Layout& L, const double* __restrict__ c, double* sm, int lane) {
+  const int n = L.s_tmp - L.s_ej;
+  for (int o = lane; o < n; o += WARP) sm[L.s_ej + o] = c[L.c_mir + o];
+  __syncwarp();
+}
+
+__device__ __forceinline__ void store_mirror(const Layout& L, double* __restrict__ c, const double* sm, int lane) {
+  __syncwarp();
+  const int n = L.s_tmp - L.s_ej;
+  for (int o = lane; o < n; o += WARP) c[L.c_mir + o] = sm[L.s_ej + o];
+}
+
 // Place walkers at x_in (n x n_e x 3), build caches, invert and evaluate.
-__global__ void k_init_walkers(DevSys S, Layout L, double* __restrict__ state, const double* __restrict__ x_in,
-                               const double* __restrict__ w_in, int n, double a, int node_rule, double* scratch) {
+__global__ void k_init_walkers(DevSys S, Layout L, double* __restrict__ state, double* __restrict__ cache,
+                               const double* __restrict__ x_in, const double* __restrict__ w_in, int n, double a,
+                               int node_rule, double* scratch) {
   extern __shared__ double smem[];
   const double* T = stage_table(S, smem);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   double* sm = smem + EXP_TAB + wib * L.s_stride;
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   const int slot = blockIdx.x * (blockDim.x >> 5) + wib;
-  Scr scr = warp_scratch(L, scratch, slot);
-  scr.chi = nullptr;
+  const Scr wscr = warp_scratch(L, scratch, slot);
   for (int w = slot; w < n; w += nwarps) {
     double* gblk = state + (size_t)w * L.g_stride;
+    double* cblk = cache + (size_t)w * L.c_stride;
+    const Scr scr = walker_scratch(L, cblk, wscr);
     for (int o = lane; o < 3 * L.n_e; o += WARP) sm[L.s_x + o] = x_in[(size_t)w * 3 * L.n_e + o];
     __syncwarp();
     bool sing = false;
@@ -901,8 +992,10 @@ __global__ void k_init_walkers(DevSys S, Layout L, double* __restrict__ state, c
       sc[SC_EL] = e.eL;
       sc[SC_NNODE] = e.n_node;
       sc[SC_STATUS] = sing ? (double)ST_SINGULAR : 0.0;
+      sc[SC_CACHE] = sing ? 0.0 : 1.0;
     }
     store_block(L, gblk, sm, lane);
+    store_mirror(L, cblk, sm, lane);
   }
 }
 
@@ -917,8 +1010,7 @@ __global__ void k_eval_configs(DevSys S, Layout L, double* __restrict__ blocks, 
   double* sm = smem + EXP_TAB + wib * L.s_stride;
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   const int slot = blockIdx.x * (blockDim.x >> 5) + wib;
-  Scr scr = warp_scratch(L, scratch, slot);
-  scr.chi = nullptr;
+  const Scr scr = warp_scratch(L, scratch, slot);
   for (int w = slot; w < n; w += nwarps) {
     double* gblk = blocks + (size_t)w * L.g_stride;
     for (int o = lane; o < 3 * L.n_e; o += WARP) sm[L.s_x + o] = x_in[(size_t)w * 3 * L.n_e + o];
@@ -939,10 +1031,15 @@ __global__ void k_eval_configs(DevSys S, Layout L, double* __restrict__ blocks, 
 
 // One branching interval for every walker (Algorithm 2 for kind 1,
 // Algorithm 1 for kind 0).  The walker state stays in shared memory for the
-// whole interval; the first hop of an interval evaluates the new
-// configuration in full and fills the caches, later hops update them.
+// whole interval.  On the fixed lattice the caches of the incremental
+// evaluation persist in the walker's cache block from one interval to the
+// next, so every hop is evaluated incrementally; without valid caches (new
+// walkers after a failed inversion, or a stored evaluation from a randomised
+// lattice) the first hop evaluates in full.  A randomised interval draws new
+// versors and evaluates in full at its start.
 template <bool ROT>
-__global__ void k_propagate(DevSys S, Layout L, double* __restrict__ state, int n_w, StepParams P, double* scratch) {
+__global__ void k_propagate(DevSys S, Layout L, double* __restrict__ state, double* __restrict__ cache, int n_w,
+                            StepParams P, double* scratch) {
   extern __shared__ double smem[];
   const double* T = stage_table(S, smem);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -950,15 +1047,21 @@ __global__ void k_propagate(DevSys S, Layout L, double* __restrict__ state, int 
   double* sc = sm + L.s_sc;
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   const int slot = blockIdx.x * (blockDim.x >> 5) + wib;
-  const Scr scr = warp_scratch(L, scratch, slot);
+  const Scr wscr = warp_scratch(L, scratch, slot);
+  const double ia = 1.0 / P.a;
   for (int w = slot; w < n_w; w += nwarps) {
     const unsigned long long t_start = global_ns();
     double* gblk = state + (size_t)w * L.g_stride;
+    double* cblk = cache + (size_t)w * L.c_stride;
+    const Scr scr = walker_scratch(L, cblk, wscr);
     load_block(L, gblk, sm, lane);
-    bool g_valid = false, cached = false;
-    if (ROT) {
-      // new versors for this interval: the stored evaluation used the old ones
-      if (lane == 0) interval_versors(P.seed, (uint32_t)w, P.interval, sm + L.s_v);
+    const bool rotated_before = sc[SC_ROTATED] != 0.0;
+    bool cached = !ROT && !rotated_before && sc[SC_CACHE] != 0.0;
+    if (cached) load_mirror(L, cblk, sm, lane);
+    bool g_valid = cached;
+    if (ROT || rotated_before) {
+      // new versors (or the Cartesian axes again): the stored evaluation used others
+      if (ROT && lane == 0) interval_versors(P.seed, (uint32_t)w, P.interval, sm + L.s_v);
       __syncwarp();
       compute_g(S, L, sm, scr.g, 0, L.n_e, lane);
       const EvalOut e0 = eval_full<ROT>(S, L, gblk, sm, scr, P.a, P.node_rule, T, lane);
@@ -1006,7 +1109,7 @@ __global__ void k_propagate(DevSys S, Layout L, double* __restrict__ state, int 
           compute_g(S, L, sm, scr.g, 0, L.n_e, lane);
           g_valid = true;
         }
-        apply_hop<ROT>(S, L, gblk, sm, scr, p, P.a, T, lane);
+        apply_hop<ROT>(S, L, gblk, sm, scr, p, P.a, ia, T, lane);
         ++moves;
         bool reinv = false;
         if (++since >= P.reinv_period) {
@@ -1039,13 +1142,17 @@ __global__ void k_propagate(DevSys S, Layout L, double* __restrict__ state, int 
       }
     }
     if (!isfinite(weight) || !isfinite(eL)) status |= ST_NONFINITE;
+    const bool keep = !ROT && cached && !(status & ST_SINGULAR);
     if (lane == 0) {
       sc[SC_W] = weight;
       sc[SC_STATUS] = (double)status;
       sc[SC_MOVES] = moves;
       sc[SC_SINCE] = since;
+      sc[SC_CACHE] = keep ? 1.0 : 0.0;
+      sc[SC_ROTATED] = ROT ? 1.0 : 0.0;
     }
     store_block(L, gblk, sm, lane);
+    if (keep) store_mirror(L, cblk, sm, lane);
     if (P.stamps && lane == 0) {
       P.stamps[3 * (size_t)w] = t_start;
       P.stamps[3 * (size_t)w + 1] = global_ns();
@@ -1093,9 +1200,10 @@ __global__ void k_fp64math(int n, const double* __restrict__ x, double* __restri
   }
 }
 
-__global__ void k_clear_status(Layout L, double* __restrict__ state, int n_w) {
+// Set walker scalar idx of every walker to v.
+__global__ void k_set_scalar(Layout L, double* __restrict__ state, int n_w, int idx, double v) {
   for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < n_w; a += gridDim.x * blockDim.x)
-    state[(size_t)a * L.g_stride + L.g_sc + SC_STATUS] = 0.0;
+    state[(size_t)a * L.g_stride + L.g_sc + idx] = v;
 }
 
 }  // namespace lrdmc

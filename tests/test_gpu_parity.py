@@ -320,6 +320,29 @@ def test_randomised_lattice_interval_matches_oracle(name, sysf, n_w, kind):
         Wk = OL.init_walkers(s, g["x"], 0.2)
 
 
+@pytest.mark.parametrize("kind", [1, 0])
+def test_fixed_lattice_after_randomised_interval_matches_oracle(kind):
+    """A fixed-lattice interval that follows a randomised one re-evaluates the
+    walkers on the Cartesian axes before its first step (both sides)."""
+    P = lib_or_skip()
+    s = W.water_methane()
+    lr, x0 = _mk(P, s, 24, reinv_period=7)
+    E0 = lr.e0
+    Wk = OL.init_walkers(s, x0, 0.2)
+    for rotate in (True, False, False):
+        lr.propagate(kind, n_proj=6, tau=0.005, max_moves=1000, rotate=rotate)
+        if kind == 1:
+            OL.propagate_lb(s, Wk, 0.2, E0, 6, seed=1, interval=0, rotate=rotate)
+        else:
+            OL.propagate_conventional(s, Wk, 0.2, 0.005, seed=1, interval=0, max_moves=1000, rotate=rotate)
+        g = lr.get_walkers()
+        np.testing.assert_array_equal(g["moves"], Wk.moves)
+        np.testing.assert_allclose(g["x"], Wk.x, rtol=0, atol=1e-12)
+        assert_close(g["w"], Wk.w, rtol=1e-9, what="w")
+        assert_close(g["ev"][:, 3], Wk.ev["eL"], rtol=1e-9, what="eL")
+        assert_close(g["ratios"], Wk.ev["ratios"], rtol=1e-9, what="ratios")
+
+
 def test_randomised_lattice_exact_hydrogen_and_refusal_in_mixed():
     P = lib_or_skip()
     s = W.hydrogen_atom_sto(1.0)

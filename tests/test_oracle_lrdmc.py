@@ -13,6 +13,7 @@ import workloads as W
 from oracle import estimator as est
 from oracle import lrdmc as L
 from oracle import philox
+from oracle import wavefunction as WF
 
 
 # ---------------------------------------------------------------- reconfiguration
@@ -283,3 +284,26 @@ def test_randomised_lattice_keeps_exact_energy_and_hop_length():
     L.propagate_lb(s, Wk, 0.25, -0.5, 1, seed=2, interval=9, rotate=True)
     step = np.linalg.norm(Wk.x - before, axis=-1)
     np.testing.assert_allclose(step, 0.25, rtol=1e-12)
+
+
+def test_fixed_lattice_after_randomised_interval_reevaluates_on_the_axes():
+    """The evaluation a randomised interval leaves behind belongs to its
+    versors; a following fixed-lattice interval starts from the Cartesian
+    evaluation (ratios of the six axis hops, checked against the definition
+    Psi(x')/Psi(x) from fresh log-amplitudes)."""
+    s = W.h2_sto3g()
+    x0 = W.initial_walkers(s, 6, seed=4)
+    Wk = L.init_walkers(s, x0, 0.2)
+    L.propagate_lb(s, Wk, 0.2, -1.0, 2, seed=3, interval=0, rotate=True)
+    assert Wk.rotated
+    L.propagate_lb(s, Wk, 0.2, -1.0, 0, seed=3, interval=1, rotate=False)
+    assert not Wk.rotated
+    for n in range(2):
+        for i in range(s.n_up + s.n_dn):
+            for d in range(6):
+                xp = Wk.x[n].copy()
+                xp[i, d // 2] += 0.2 if d % 2 == 0 else -0.2
+                s1, l1 = WF.log_psi(s, xp)
+                s0, l0 = WF.log_psi(s, Wk.x[n])
+                ref = s1 * s0 * np.exp(l1 - l0)
+                assert abs(Wk.ev["ratios"].reshape(6, -1)[n, 6 * i + d] - ref) <= 1e-10 * max(1.0, abs(ref))
