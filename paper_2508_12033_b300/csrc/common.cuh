@@ -31,6 +31,7 @@ enum Scalar : int {
   SC_SINCE = 8,   // hops since the last from-scratch inversion
   SC_CACHE = 9,   // 1: the walker's cache block matches x and B on the fixed lattice
   SC_ROTATED = 10,  // 1: the stored evaluation was taken on a randomised lattice
+  SC_KEPT = 11,   // sum of the kept hop ratios (2 a^2 b_bar before rounding)
   SC_COUNT = 16
 };
 

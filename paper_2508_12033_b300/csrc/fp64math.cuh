@@ -10,11 +10,13 @@
 //            |r| <= ln2/128, exp(x) = 2^m 2^(j/64) exp(r), exp(r) by its Taylor
 //            polynomial of degree 5 (truncation < 4e-17), the reduction by FMA
 //            against a two-part ln2/64 (Cody-Waite), 2^m applied to the exponent
-//            field.  About 10 FP64 slots.
-//  rcp_nr    hardware reciprocal approximation (rcp.approx.ftz.f64, ~2^-20)
-//            refined by two Newton-Raphson steps t <- t + t (1 - y t).
-//  rsqrt_nr  hardware rsqrt approximation refined by two Newton-Raphson steps
-//            y <- y + y (1 - s y^2) / 2.
+//            field.  Out-of-range and non-finite arguments are sorted out on the
+//            integer image of x, so the FP64 pipe sees 10 operations.
+//  rcp_nr    hardware reciprocal approximation (rcp.approx.ftz.f64, relative
+//            error ~2^-22) refined by one third-order Newton (Householder)
+//            step t <- t (1 + e + e^2), e = 1 - y t, which cubes the error.
+//  rsqrt_nr  hardware rsqrt approximation refined by one third-order step of
+//            the binomial series y <- y (1 + e/2 + 3 e^2/8), e = 1 - s y^2.
 // The reduction constants are ln2/64 split into double hi/lo parts and 64/ln2,
 // evaluated to 200 bits; the table holds 2^(j/64) rounded to double.
 #pragma once
@@ -29,7 +31,8 @@ constexpr double EXP_L_HI = 0x1.62e42fefa39efp-7;     // ln 2 / 64, leading doub
 constexpr double EXP_L_LO = 0x1.abc9e3b39803fp-62;    // ln 2 / 64 - EXP_L_HI
 constexpr double EXP_SHIFTER = 0x1.8p52;              // 1.5 * 2^52: rounds to an integer
 
-// exp(x) for x in [-700, 700]; 0 below -700 (true value < 1e-304), +inf above.
+// exp(x) for |x| < 700; 0 for x <= -700 (true value < 1e-304), +inf for
+// x >= 700, NaN for NaN.
 __device__ __forceinline__ double exp_tab(double x, const double* __restrict__ T) {
   const double t = fma(x, EXP_INV_L, EXP_SHIFTER);
   const int k = (int)__double2loint(t);                 // round(x * 64/ln2), two's complement
@@ -43,9 +46,12 @@ __device__ __forceinline__ double exp_tab(double x, const double* __restrict__ T
   const double p = r * q;                               // exp(r) - 1
   const double tj = T[k & (EXP_TAB - 1)];
   double y = fma(tj, p, tj);
-  y = __longlong_as_double(__double_as_longlong(y) + ((long long)(k >> 6) << 52));
-  y = x < -700.0 ? 0.0 : y;
-  return x > 700.0 ? __longlong_as_double(0x7ff0000000000000ll) : y;
+  y = __longlong_as_double(__double_as_longlong(y) + (long long)((unsigned long long)(long long)(k >> 6) << 52));
+  const unsigned hx = (unsigned)__double2hiint(x), lx = (unsigned)__double2loint(x);
+  const unsigned ax = hx & 0x7fffffffu;
+  const bool nan = ax > 0x7ff00000u || (ax == 0x7ff00000u && lx != 0u);
+  const double big = nan ? x : ((hx >> 31) ? 0.0 : __longlong_as_double(0x7ff0000000000000ll));
+  return ax >= 0x4085e000u ? big : y;                   // 0x4085e000: high word of 700.0
 }
 
 __device__ __forceinline__ double rcp_approx(double x) {
@@ -62,20 +68,16 @@ __device__ __forceinline__ double rsqrt_approx(double x) {
 
 // 1/y for finite y != 0 (normal range).
 __device__ __forceinline__ double rcp_nr(double y) {
-  double t = rcp_approx(y);
-  double e = fma(-y, t, 1.0);
-  t = fma(t, e, t);
-  e = fma(-y, t, 1.0);
-  return fma(t, e, t);
+  const double t = rcp_approx(y);
+  const double e = fma(-y, t, 1.0);
+  return fma(t, fma(e, e, e), t);
 }
 
 // 1/sqrt(s) for s > 0 (normal range).
 __device__ __forceinline__ double rsqrt_nr(double s) {
-  double y = rsqrt_approx(s);
-  double e = fma(-s, y * y, 1.0);
-  y = fma(y * e, 0.5, y);
-  e = fma(-s, y * y, 1.0);
-  return fma(y * e, 0.5, y);
+  const double y = rsqrt_approx(s);
+  const double e = fma(-s, y * y, 1.0);
+  return fma(y * e, fma(e, 0.375, 0.5), y);
 }
 
 }  // namespace lrdmc

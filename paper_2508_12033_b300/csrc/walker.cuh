@@ -280,27 +280,26 @@ __device__ void compute_g(const DevSys& S, const Layout& L, const double* sm, do
 // ------------------------------------------------------------ evaluation
 struct EvalOut {
   double bbar, vsf, W, eL;
+  double kept;   // sum of the kept (positive) hop ratios
   int n_node;
 };
 
-// Pade pair term u = c r/(1 + b r) and its radial derivatives from s = r^2.
+// Pade pair term u = c r/(1 + b r) and its radial derivatives from s = r^2,
+// written with 1/r: u = c q, q = 1/(1/r + b), and 1/(1 + b r) = q / r.
 struct Pair {
   double u, up, upp, ir;
 };
 __device__ __forceinline__ Pair pade(double s, double c, double b) {
   Pair p;
   p.ir = rsqrt_nr(s);
-  const double r = s * p.ir;
-  const double t = rcp_nr(fma(b, r, 1.0));
-  p.u = c * r * t;
+  const double q = rcp_nr(p.ir + b);
+  const double t = p.ir * q;
+  p.u = c * q;
   p.up = c * t * t;
   p.upp = -2.0 * b * p.up * t;
   return p;
 }
-__device__ __forceinline__ double pade_value(double s, double c, double b) {
-  const double r = s * rsqrt_nr(s);
-  return c * r * rcp_nr(fma(b, r, 1.0));
-}
+__device__ __forceinline__ double pade_value(double s, double c, double b) { return c * rcp_nr(rsqrt_nr(s) + b); }
 
 // Component of (xi - xj) along hop axis ax: the Cartesian component, or the
 // projection on versor ax of a randomised lattice.
@@ -317,42 +316,54 @@ __device__ __forceinline__ double pair_c(const DevSys& S, const Layout& L, int i
 }
 
 // (4) fixed-node split and regularised potential per electron, from the hop
-// ratios, the Jastrow and determinant derivatives and the potentials.
+// ratios, the Jastrow and determinant derivatives and the potentials.  G lanes
+// share an electron (G = 2 when n_e <= 16): each sums 6/G of its hop ratios,
+// the pair combines the node test and the ratio sum, and both evaluate the
+// electron's potential terms (one adds them).  For the per-configuration node
+// rule both the capped and the plain sums are kept and chosen at the end.
 __device__ EvalOut assemble(const DevSys& S, const Layout& L, const double* sm, double a, int node_rule, int lane) {
   const int ne = L.n_e;
   const double* rat = sm + L.s_rat;
   const double* ej = sm + L.s_ej;
   const double* ep = sm + L.s_ep;
   const double* dd = sm + L.s_dd;
-  bool has_node = false;
-  for (int i = lane; i < ne; i += WARP)
-    for (int d = 0; d < 6; ++d) has_node |= rat[6 * i + d] < 0.0;
-  const bool any_node = __any_sync(FULL, has_node);
-  double kept = 0.0, negs = 0.0, nuopt = 0.0, vee = 0.0;
+  const int G = ne <= WARP / 2 ? 2 : 1, per_pass = WARP / G, sub = lane % G, nd = 6 / G;
+  double kept = 0.0, negs = 0.0, nuopt = 0.0, nuplain = 0.0, vee = 0.0;
   int nnode = 0;
+  bool any_node = false;
   const double ia2 = 1.0 / (a * a);
-  for (int i = lane; i < ne; i += WARP) {
+  for (int base = 0; base < ne; base += per_pass) {
+    const int i = base + lane / G;
+    const bool valid = i < ne;
     double sr = 0.0;
     bool node = false;
-    for (int d = 0; d < 6; ++d) {
-      const double r = rat[6 * i + d];
-      sr += r;
-      if (r > 0.0) kept += r;
-      if (r < 0.0) { negs -= r; node = true; }
+    if (valid)
+      for (int d = sub * nd; d < (sub + 1) * nd; ++d) {
+        const double r = rat[6 * i + d];
+        sr += r;
+        if (r > 0.0) kept += r;
+        if (r < 0.0) { negs -= r; node = true; }
+      }
+    if (G == 2) {
+      sr += __shfl_xor_sync(FULL, sr, 1);
+      node |= __shfl_xor_sync(FULL, (int)node, 1) != 0;
     }
-    const double* q = ej + 6 * i;
-    const double* dv = dd + 4 * i;
-    const double lap = dv[3] + 2.0 * (dv[0] * q[1] + dv[1] * q[2] + dv[2] * q[3]) + q[4] +
-                       (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
-    const double nu_zv = ep[2 * i] + 0.5 * ((sr - 6.0) * ia2 - lap);
-    bool apply;
-    if (node_rule == 0) apply = node;
-    else if (node_rule == 1) apply = any_node;
-    else if (node_rule == 2) apply = true;
-    else apply = false;
-    nuopt += apply ? fmax(nu_zv, ep[2 * i + 1]) : nu_zv;
-    vee += q[5];
-    nnode += node ? 1 : 0;
+    any_node |= __any_sync(FULL, node);
+    if (valid && sub == 0) {
+      const double* q = ej + 6 * i;
+      const double* dv = dd + 4 * i;
+      const double lap = dv[3] + 2.0 * (dv[0] * q[1] + dv[1] * q[2] + dv[2] * q[3]) + q[4] +
+                         (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+      const double nu_zv = ep[2 * i] + 0.5 * ((sr - 6.0) * ia2 - lap);
+      const double nu_cap = fmax(nu_zv, ep[2 * i + 1]);
+      bool apply;
+      if (node_rule == 0) apply = node;
+      else apply = node_rule >= 1;       // rule 1: capped sum, chosen below
+      nuopt += apply ? nu_cap : nu_zv;
+      nuplain += nu_zv;
+      vee += q[5];
+      nnode += node ? 1 : 0;
+    }
   }
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
@@ -362,8 +373,14 @@ __device__ EvalOut assemble(const DevSys& S, const Layout& L, const double* sm, 
     vee += __shfl_xor_sync(FULL, vee, o);
     nnode += __shfl_xor_sync(FULL, nnode, o);
   }
+  if (node_rule == 1 && !any_node) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) nuplain += __shfl_xor_sync(FULL, nuplain, o);
+    nuopt = nuplain;
+  }
   EvalOut e;
   const double i2a2 = 0.5 * ia2;
+  e.kept = kept;
   e.bbar = kept * i2a2;
   e.vsf = negs * i2a2;
   e.W = 3.0 * ne * ia2 + nuopt + vee + S.v_ii + e.vsf;
@@ -769,18 +786,10 @@ __device__ EvalOut init_walker(const DevSys& S, const Layout& L, double* __restr
 }
 
 // Heat-bath choice over the kept hops (r > 0) in the order p = 6 i + d: the
-// first p whose running sum exceeds u * total; the last kept hop if rounding
-// leaves none; -1 without kept hops.  Running sums by warp scans over chunks
-// of 32 hops.
-__device__ int choose_hop(const double* rat, int n_hop, double u, int lane) {
-  double total = 0.0;
-  for (int c = 0; c < n_hop; c += WARP) {
-    const int p = c + lane;
-    double k = (p < n_hop && rat[p] > 0.0) ? rat[p] : 0.0;
-#pragma unroll
-    for (int o = 16; o; o >>= 1) k += __shfl_xor_sync(FULL, k, o);
-    total += k;
-  }
+// first p whose running sum exceeds u * total (total = the sum of the kept
+// ratios taken by the evaluation); the last kept hop if rounding leaves none;
+// -1 without kept hops.  Running sums by warp scans over chunks of 32 hops.
+__device__ int choose_hop(const double* rat, int n_hop, double u, double total, int lane) {
   if (!(total > 0.0)) return -1;
   const double t = u * total;
   double base = 0.0;
@@ -993,6 +1002,7 @@ __global__ void k_init_walkers(DevSys S, Layout L, double* __restrict__ state, d
       sc[SC_NNODE] = e.n_node;
       sc[SC_STATUS] = sing ? (double)ST_SINGULAR : 0.0;
       sc[SC_CACHE] = sing ? 0.0 : 1.0;
+      sc[SC_KEPT] = e.kept;
     }
     store_block(L, gblk, sm, lane);
     store_mirror(L, cblk, sm, lane);
@@ -1072,11 +1082,12 @@ __global__ void k_propagate(DevSys S, Layout L, double* __restrict__ state, doub
         sc[SC_WDIAG] = e0.W;
         sc[SC_EL] = e0.eL;
         sc[SC_NNODE] = e0.n_node;
+        sc[SC_KEPT] = e0.kept;
       }
       __syncwarp();
     }
     double weight = 1.0, tau_left = P.tau;
-    double bbar = sc[SC_BBAR], Wd = sc[SC_WDIAG], eL = sc[SC_EL];
+    double bbar = sc[SC_BBAR], Wd = sc[SC_WDIAG], eL = sc[SC_EL], kept = sc[SC_KEPT];
     uint32_t status = (uint32_t)sc[SC_STATUS];
     int moves = 0, since = (int)sc[SC_SINCE];
     for (int k = 0;; ++k) {
@@ -1101,7 +1112,7 @@ __global__ void k_propagate(DevSys S, Layout L, double* __restrict__ state, doub
         tau_left -= t;
         if (clipped) break;
       }
-      const int p = choose_hop(sm + L.s_rat, L.n_hop, u_move, lane);
+      const int p = choose_hop(sm + L.s_rat, L.n_hop, u_move, kept, lane);
       if (p < 0) {
         status |= ST_STUCK;
       } else {
@@ -1128,12 +1139,14 @@ __global__ void k_propagate(DevSys S, Layout L, double* __restrict__ state, doub
         bbar = e.bbar;
         Wd = e.W;
         eL = e.eL;
+        kept = e.kept;
         if (lane == 0) {
           sc[SC_BBAR] = e.bbar;
           sc[SC_VSF] = e.vsf;
           sc[SC_WDIAG] = e.W;
           sc[SC_EL] = e.eL;
           sc[SC_NNODE] = e.n_node;
+          sc[SC_KEPT] = e.kept;
         }
       }
       if (P.kind == 0 && k + 1 >= P.max_moves) {

@@ -32,10 +32,14 @@ def test_fp64math_against_cuda():
             ref = torch.exp(xt)
             rel = ((e - ref).abs() / ref).max().item()
             assert rel < 8e-16, rel
-            edge = torch.tensor([-701.0, -1e4, 0.0], dtype=torch.float64, device="cuda")
-            assert f(3, edge.data_ptr(), e.data_ptr(), None, None, s) == 0
+            edge = torch.tensor([-701.0, -1e4, 0.0, float("nan"), float("inf"), -float("inf"), 701.0, -699.9],
+                                dtype=torch.float64, device="cuda")
+            assert f(len(edge), edge.data_ptr(), e.data_ptr(), None, None, s) == 0
             torch.cuda.synchronize()
-            assert e[0].item() == 0.0 and e[1].item() == 0.0 and e[2].item() == 1.0
+            got = e[:len(edge)].cpu().numpy()
+            assert got[0] == 0.0 and got[1] == 0.0 and got[2] == 1.0
+            assert np.isnan(got[3]) and got[4] == np.inf and got[5] == 0.0 and got[6] == np.inf
+            assert abs(got[7] / np.exp(-699.9) - 1.0) < 8e-16
         else:
             rel_r = ((r - 1.0 / xt).abs() * xt).max().item()
             rel_q = ((q - torch.rsqrt(xt)).abs() / torch.rsqrt(xt)).max().item()
