@@ -34,57 +34,39 @@ N_PROJ = 20
 A = 0.2
 SEED = 1
 FP64_PEAK_GFLOPS = 1250.0      # nominal B300 FP64 rate (profiling recipe table)
-# Pipe cost, in FP64 FMA slots, of the FP64 functions as the propagate kernel
-# implements them (measured on B300 by the pipe microbenchmark shipped with the
-# library; see profiles/): table-driven exp, approximate reciprocal / rsqrt plus
-# two Newton steps, and CUDA's sqrt and erf for the moved electron's potential.
-SLOT_EXP, SLOT_RSQ, SLOT_RCP, SLOT_SQRT, SLOT_ERF = 10.0, 8.9, 4.9, 11.7, 46.4
+# FP64 pipe instructions of the functions as the propagate kernel implements
+# them: table-driven exp (10), approximate reciprocal / rsqrt plus one
+# third-order refinement (4 / 6), CUDA's erf (measured pipe cost, see profiles/).
+OP_EXP, OP_RSQ, OP_RCP, OP_ERF = 10.0, 6.0, 4.0, 43.5
+OP_PADE_VALUE = OP_RSQ + 1 + OP_RCP + 1          # u = c / (1/r + b)
+OP_PADE = OP_RSQ + 1 + OP_RCP + 1 + 1 + 2 + 3    # u, u', u'' and 1/r
 
 
-def full_eval_slots(n_e, n_nuc, n_bf, n_prim, n_sig, n_s_shell, n_p_shell, one_body=True):
-    """FP64 slots of one full evaluation (every hop of every electron).
+def algorithmic_ops_per_walker_step(n_e, n_nuc, n_bf, n_prim, n_sig, n_s_shell, n_p_shell):
+    """FP64 operations per walker-step of the load-balanced step as formulated
+    in the propagate kernel (one add/mul/FMA = 1; a function counts its FP64
+    instructions above).  Every walker-step is one hop of an electron m and the
+    incremental evaluation that follows it; the caches persist across
+    branching intervals, so no step pays a full evaluation.
 
-    Per hop (6 n_e): per nucleus the displaced squared distance and offset (2)
-    and, with a one-body Jastrow, its Pade term (rsqrt + reciprocal + 5); per
-    primitive one exponential + 2; per s / p shell 1 / 4 for the dot with g_i;
-    per other electron 2 + Pade term; the Jastrow exponential + 2.  Per
-    electron: per partner (electrons and nuclei) distance (6), Pade value and
-    derivatives (rsqrt + reciprocal + 12), accumulation (7); determinant
-    derivatives 4 n_sig; assembly 25."""
-    pade = SLOT_RSQ + SLOT_RCP + 5
-    per_hop = (n_nuc * (2 + (pade if one_body else 0)) + n_prim * (SLOT_EXP + 2) + n_s_shell + 4 * n_p_shell
-               + (n_e - 1) * (2 + pade) + SLOT_EXP + 2)
-    per_elec = (n_e - 1 + n_nuc) * (6 + SLOT_RSQ + SLOT_RCP + 12 + 7) + 4 * n_sig + 25
-    return 6 * n_e * per_hop + n_e * per_elec
-
-
-def algorithmic_slots_per_walker_step(n_e, n_nuc, n_bf, n_prim, n_sig, n_s_shell, n_p_shell, one_body=True,
-                                      n_proj=20):
-    """FP64 work per walker-step of the load-balanced step as formulated in the
-    propagate kernel, in FMA slots (one FP64 add/mul/FMA = 1; a function counts
-    its pipe cost above).
-
-    The first hop of an interval is followed by a full evaluation; every other
-    hop of electron m by an incremental one: m's pair and nucleus Jastrow terms
-    with derivatives (A), the other electrons' pair terms with m swapped old ->
-    new (B, two Pade evaluations with derivatives each), determinant
-    derivatives of m's spin block (C, 4 n_sig^2), basis values at m's six hops
-    and their Jastrow terms (D), determinant ratios of the block's hops from the
-    cached basis values (E, 6 n_sig n_bf), the pair Jastrow term with m swapped
-    for the other electrons' hops (F, two Pade values each), every hop's
-    Jastrow exponential (G) and the assembly.  Every hop also pays the move:
-    basis value/gradient/Laplacian at one point, 5 n_bf n_sig contraction,
-    2 n_sig^2 Sherman-Morrison, n_sig n_bf update of g, potentials."""
-    pade = SLOT_RSQ + SLOT_RCP + 5
-    pade_d = 6 + SLOT_RSQ + SLOT_RCP + 12 + 7
+    Move: basis value/gradient/Laplacian at the new position (per primitive an
+    exponential + 10), the 5 n_sig x n_bf contraction, Sherman-Morrison
+    (2 n_sig^2) and the n_sig x n_bf update of g, the potentials (per nucleus
+    rsqrt + erf + 8).  Evaluation: m's pair and nucleus terms with derivatives
+    and the partner electrons' swapped terms (Pade + 14 per partner, 14 per
+    swap), determinant derivatives of m's block (4 n_sig^2), basis values at
+    m's six hops (exponential + 2 per primitive, 1 / 4 per s / p shell) and
+    their Jastrow terms (Pade value + 3 per partner), the block's hop
+    determinant ratios from cached basis values (6 n_sig n_bf), the swapped
+    pair terms of the other hops (2 each), every hop's exponential (+3) and the
+    assembly (20 per electron)."""
     per = n_e - 1 + n_nuc
-    incr = (per * pade_d + (n_e - 1) * 2 * pade_d + 4 * n_sig * n_sig
-            + 6 * (n_prim * (SLOT_EXP + 2) + 3 * (n_s_shell + n_p_shell) + 3 * n_p_shell) + 6 * per * (pade + 2)
-            + 6 * n_sig * n_bf + 6 * (n_e - 1) * 2 * (pade + 8) + 6 * n_e * (SLOT_EXP + 3) + 30 * n_e)
-    move = (n_prim * (SLOT_EXP + 10) + 5 * n_bf * n_sig + 2 * n_sig * n_sig + n_sig * n_bf
-            + n_nuc * (SLOT_SQRT + SLOT_ERF + 2 * SLOT_RCP + 6))
-    full = full_eval_slots(n_e, n_nuc, n_bf, n_prim, n_sig, n_s_shell, n_p_shell, one_body) + n_e * n_bf * n_sig
-    return move + ((n_proj - 1) * incr + full) / n_proj
+    move = (n_prim * (OP_EXP + 10) + 5 * n_bf * n_sig + 2 * n_sig * n_sig + n_sig * n_bf
+            + n_nuc * (OP_RSQ + OP_ERF + 8))
+    evaluation = (per * (OP_PADE + 14) + (n_e - 1) * 14 + 4 * n_sig * n_sig
+                  + 6 * (n_prim * (OP_EXP + 2) + n_s_shell + 4 * n_p_shell) + 6 * per * (OP_PADE_VALUE + 3)
+                  + 6 * n_sig * n_bf + 6 * (n_e - 1) * 2 + 6 * n_e * (OP_EXP + 3) + 20 * n_e)
+    return move + evaluation
 
 
 # ----------------------------------------------------------------- clocks
@@ -214,9 +196,8 @@ def run_gpu(args, rank, world):
     ws_per_step = N_W * N_PROJ
     value, t_total = aggregate_throughput(sum(step_ms) / 1e3, ws_per_step * args.steps, world, dev)
     # roofline of the dominant kernel (the propagate kernel: one launch per step)
-    slots = algorithmic_slots_per_walker_step(s.n_elec, s.n_nuc, s.n_bf, s.n_prim_eval, max(s.n_up, s.n_dn),
-                                              int(np.sum(s.shell_l == 0)), int(np.sum(s.shell_l == 1)),
-                                              bool(np.any(s.j1_A != 0)), N_PROJ)
+    slots = algorithmic_ops_per_walker_step(s.n_elec, s.n_nuc, s.n_bf, s.n_prim_eval, max(s.n_up, s.n_dn),
+                                            int(np.sum(s.shell_l == 0)), int(np.sum(s.shell_l == 1)))
     prop_s = statistics.mean(prop_ms) / 1e3
     achieved = 2.0 * slots * ws_per_step / prop_s / 1e9      # GFLOP/s, FP64-equivalent
     # conventional schedule at the same mean hops per interval (tau = N_proj / <b_bar>)
@@ -392,10 +373,10 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload,
             "electron_move_attempts_per_s": res["value"] * 6 * 16,
             "roofline": {"bound": "alu", "kernel": "k_propagate", "achieved": res["achieved"], "peak": peak,
-                         "unit": "GFLOP/s (FP64, functions at measured pipe cost)",
+                         "unit": "GFLOP/s (FP64 operations x 2, functions at their FP64 instruction count)",
                          "frac": res["achieved"] / peak, "traffic": None,
                          "peak_source": "nominal FP64 rate of the recipe table (no FP64 entry measured)",
-                         "kernel_ms": res["prop_ms"], "slots_per_walker_step": res["slots"]},
+                         "kernel_ms": res["prop_ms"], "fp64_ops_per_walker_step": res["slots"]},
             "conventional": {"value": res["conv_rate"], "unit": "walker-steps/s", "tau": res["tau"],
                              "moves_mean_max": res["conv_moves"],
                              "lb_speedup": res["value"] / res["conv_rate"]},

@@ -116,8 +116,9 @@ bool make_plan(const lrdmc_system* sys, const lrdmc_trial_wf* wf, const lrdmc_pa
   L.c_chi = L.c_g + P.n_e * P.n_bf;
   L.c_u2 = L.c_chi + P.n_bf * L.n_hop;
   L.c_pt = L.c_u2 + P.n_e * L.n_hop;
-  L.c_stride = P.precision == 0 ? round_up(L.c_pt + 4 * P.n_e * P.n_e, 16) : 0;
+  L.c_stride = round_up(L.c_pt + 4 * P.n_e * P.n_e, 16);
   P.M = layout_mixed(L, P.n_nuc, P.n_prim);
+  if (P.precision == 1) L.c_stride = round_up((P.M.c_floats + 1) / 2, 16);
   P.smem_per_warp = P.precision == 0 ? (size_t)L.s_stride * sizeof(double) : (size_t)P.M.stride * sizeof(float);
   if (P.smem_per_warp + EXP_TAB * sizeof(double) > 200 * 1024) { P.err = "system too large for the per-warp shared-memory layout"; return false; }
   // system image
@@ -239,7 +240,7 @@ struct lrdmc_s {
   lrdmc_params prm{};
   double* state = nullptr;
   double* alt = nullptr;
-  double* cache = nullptr;       // per-walker cache blocks (FP64), null for the mixed kernels
+  double* cache = nullptr;       // per-walker cache blocks (layout of the precision in use)
   double* cache_alt = nullptr;
   double* stats = nullptr;
   unsigned long long* Q = nullptr;
@@ -323,7 +324,7 @@ static lrdmc_status place_walkers(lrdmc_handle h, const double* x, const double*
                                                                             P.n_w, h->prm.a, h->prm.node_rule,
                                                                             h->scr);
   else
-    k_init_walkers_m<<<walker_grid(h, P.n_w), h->wpb * 32, smem, h->stream>>>(h->S, P.L, P.M, h->state, dx, dw,
+    k_init_walkers_m<<<walker_grid(h, P.n_w), h->wpb * 32, smem, h->stream>>>(h->S, P.L, P.M, h->state, h->cache, dx, dw,
                                                                               P.n_w, h->prm.a, h->prm.node_rule,
                                                                               h->scr);
   LAUNCHED(h);
@@ -604,7 +605,7 @@ lrdmc_status lrdmc_propagate(lrdmc_handle h, const lrdmc_schedule* sch) {
                                                                                    h->cache, h->P.n_w, sp, h->scr);
   else
     k_propagate_m<<<walker_grid(h, h->P.n_w), h->wpb * 32, smem, h->stream>>>(h->S, h->P.L, h->P.M, h->state,
-                                                                              h->P.n_w, sp, h->scr);
+                                                                              h->cache, h->P.n_w, sp, h->scr);
   LAUNCHED(h);
   h->last_kind = sch->kind;
   return LRDMC_OK;

@@ -24,7 +24,9 @@
 // < 2e-8 relative), exp(x) - 1 from the hardware exponential otherwise.
 // Walker block: B^T as doubles (as in the FP64 layout); the cache region holds
 // the FP64 orbital values [n_e][n_max] followed by FP32 gradient/Laplacian
-// rows [n_e][4][n_max].
+// rows [n_e][4][n_max].  As in the FP64 kernels, the caches of the incremental
+// evaluation persist in a per-walker cache block across branching intervals,
+// and pair terms are swapped from cached values rather than recomputed.
 #pragma once
 
 #include "common.cuh"
@@ -34,11 +36,21 @@ namespace lrdmc {
 
 // Shared-memory layout of one warp for the mixed kernels, in floats (double
 // arrays at even offsets).  Per-electron float rows are padded by one word so
-// that lanes working on different electrons hit different banks.
+// that lanes working on different electrons hit different banks.  The range
+// [mir, mir_end) holds everything the incremental evaluation keeps between
+// hops and is copied to / from the walker's cache block.
 struct LayoutM {
-  int sc, x, bt, dd, phiv, chiv, u, row, hj2, xo;                  // doubles
-  int xf, xfo, gf, dl, ej, ep, geo, rt1, pair, hcur, chi5, phi5, bf32, hdm, hj1, tmp;  // floats
+  int sc, x, bt, phiv, chiv, u, row, xo;                               // doubles
+  int dd, hj2;                                                         // doubles, kept
+  int dl, ej, ep, geo, rt1, pair, hcur, hdm, hj1;                      // floats, kept
+  int xf, xfo, chi5, phi5, bf32, tmp;                                  // floats
   int geo_st, rt1_st, pair_st, hcur_st, stride;
+  int mir, mir_end;
+  // walker cache block, in floats: the shared-memory copy, g_i = C^T B[:, i]
+  // [n_e][n_bf], the basis differences at every hop [n_bf][6 n_e], the pair
+  // Jastrow difference of every hop with every partner [n_e][6 n_e] and the
+  // pair derivative terms at the current positions [n_e][n_e][3]
+  int c_gf, c_dchi, c_u2, c_pt, c_floats;
 };
 
 __host__ __device__ inline LayoutM layout_mixed(const Layout& L, int n_nuc, int n_prim) {
@@ -49,17 +61,14 @@ __host__ __device__ inline LayoutM layout_mixed(const Layout& L, int n_nuc, int 
   M.sc = o; o += 2 * SC_COUNT;
   M.x = o; o += 2 * 3 * ne;
   M.bt = o; o += 2 * nbt;
-  M.dd = o; o += 2 * 4 * ne;
   M.phiv = o; o += 2 * nm;
   M.chiv = o; o += 2 * nbf;
   M.u = o; o += 2 * nm;
   M.row = o; o += 2 * nm;
-  M.hj2 = o; o += 2 * P;
   M.xo = o; o += 2 * 4;
-  M.xf = o; o += 3 * ne;
-  M.xfo = o; o += 4;
-  o = round_up(o, 2);
-  M.gf = o; o += ne * nbf;
+  M.mir = o;
+  M.dd = o; o += 2 * 4 * ne;
+  M.hj2 = o; o += 2 * P;
   M.dl = o; o += P;
   M.ej = o; o += 5 * ne;
   M.ep = o; o += 2 * ne;
@@ -71,6 +80,12 @@ __host__ __device__ inline LayoutM layout_mixed(const Layout& L, int n_nuc, int 
   M.pair = o; o += ne * M.pair_st;
   M.hcur_st = n_prim + 1;
   M.hcur = o; o += ne * M.hcur_st;
+  M.hdm = o; o += P;
+  M.hj1 = o; o += P;
+  o = round_up(o, 2);
+  M.mir_end = o;
+  M.xf = o; o += 3 * ne;
+  M.xfo = o; o += 4;
   // move scratch (basis rows, FP32 copy of B^T) and the per-hop Jastrow
   // scratch of an evaluation share one region: they are never live together
   int sh = 5 * nbf > nbt ? 5 * nbf : nbt;
@@ -79,17 +94,49 @@ __host__ __device__ inline LayoutM layout_mixed(const Layout& L, int n_nuc, int 
   M.bf32 = M.chi5;
   M.tmp = M.chi5;
   M.phi5 = o; o += 5 * nm;
-  M.hdm = o; o += P;
-  M.hj1 = o; o += P;
   M.stride = round_up(o, 4);
+  int c = round_up(M.mir_end - M.mir, 4);
+  M.c_gf = c; c += round_up(ne * nbf, 4);
+  M.c_dchi = c; c += round_up(nbf * P, 4);
+  M.c_u2 = c; c += round_up(ne * P, 4);
+  M.c_pt = c; c += round_up(3 * ne * ne, 4);
+  M.c_floats = c;
   return M;
 }
 
-// Per-warp global scratch of the mixed kernels: the differences
-// chi_mu(r_i + hop) - chi_mu(r_i) for every hop, [n_bf][6 n_e] floats, and the
-// FP64 Gauss-Jordan work matrix [n_max][2 n_max].
+// Per-warp global scratch of the mixed kernels: g [n_e][n_bf] floats for
+// configuration evaluation (the walkers keep theirs in the cache block) and
+// the FP64 Gauss-Jordan work matrix [n_max][2 n_max].
 __host__ __device__ inline size_t scratch_doubles_m(const Layout& L) {
-  return ((size_t)L.n_bf * L.n_hop + 1) / 2 + 2 * (size_t)L.n_max * L.n_max;
+  return ((size_t)L.n_e * L.n_bf + 1) / 2 + 2 * (size_t)L.n_max * L.n_max;
+}
+
+// Global working arrays of one mixed evaluation (see LayoutM for the layouts);
+// dchi, u2 and pt are null for configuration evaluation.
+struct ScrM {
+  float* gf;
+  float* dchi;
+  float* u2;
+  float* pt;
+  double* gj;
+};
+__device__ __forceinline__ ScrM warp_scratch_m(const Layout& L, double* scratch, int slot) {
+  ScrM s;
+  double* base = scratch + (size_t)slot * scratch_doubles_m(L);
+  s.gf = (float*)base;
+  s.gj = base + ((size_t)L.n_e * L.n_bf + 1) / 2;
+  s.dchi = s.u2 = s.pt = nullptr;
+  return s;
+}
+__device__ __forceinline__ ScrM walker_scratch_m(const LayoutM& M, double* cblk, const ScrM& warp) {
+  ScrM s;
+  float* c = (float*)cblk;
+  s.gf = c + M.c_gf;
+  s.dchi = c + M.c_dchi;
+  s.u2 = c + M.c_u2;
+  s.pt = c + M.c_pt;
+  s.gj = warp.gj;
+  return s;
 }
 
 __device__ __forceinline__ double* cache_val(const Layout& L, double* gblk) { return gblk + L.g_cache; }
@@ -268,11 +315,10 @@ __device__ bool reinvert_m(const Layout& L, const LayoutM& M, double* gblk, floa
 }
 
 // g_i = C^T B[:, i] in FP32 from B rounded to FP32, for electrons [e0, e1).
-__device__ void compute_g_m(const DevSys& S, const Layout& L, const LayoutM& M, float* sm, int e0, int e1,
+__device__ void compute_g_m(const DevSys& S, const Layout& L, const LayoutM& M, float* sm, float* g, int e0, int e1,
                             int lane) {
   const double* bt = (const double*)(sm + M.bt);
   float* b32 = sm + M.bf32;
-  float* g = sm + M.gf;
   const int nbt = L.n_up * L.n_up + L.n_dn * L.n_dn;
   for (int o = lane; o < nbt; o += WARP) b32[o] = (float)bt[o];
   __syncwarp();
@@ -284,6 +330,7 @@ __device__ void compute_g_m(const DevSys& S, const Layout& L, const LayoutM& M, 
     for (int k = 0; k < sr.n; ++k) acc = fmaf(__ldg(S.Cf + (size_t)k * L.n_bf + mu), brow[k], acc);
     g[o] = acc;
   }
+  __threadfence_block();
   __syncwarp();
 }
 
@@ -353,6 +400,7 @@ __device__ EvalOut assemble_m(const DevSys& S, const Layout& L, const LayoutM& M
   }
   EvalOut e;
   const double i2a2 = 0.5 * ia2;
+  e.kept = kept;
   e.bbar = kept * i2a2;
   e.vsf = negs * i2a2;
   e.W = 3.0 * ne * ia2 + nuopt + vee + S.v_ii + e.vsf;
@@ -380,9 +428,10 @@ __device__ void det_derivs_m(const Layout& L, const LayoutM& M, double* gblk, fl
 
 // Geometry, pair data, primitive values and Jastrow derivative sums of one
 // electron e against partner t (an electron for t < n_e - 1, else a nucleus);
-// accumulates into gx, gy, gz, LJ, vee.
+// accumulates into gx, gy, gz, LJ, vee.  With pt set, the pair's derivative
+// terms (u'/r, u'' + 2u'/r, 1/(2r)) go to pt[e][j].
 __device__ __forceinline__ void partner_terms(const DevSys& S, const Layout& L, const LayoutM& M, float* sm, int e,
-                                              int t, bool write_pair_both, float& gx, float& gy, float& gz, float& LJ,
+                                              int t, float* pt, float& gx, float& gy, float& gz, float& LJ,
                                               float& vee) {
   const int ne = L.n_e;
   const float* xf = sm + M.xf;
@@ -397,14 +446,15 @@ __device__ __forceinline__ void partner_terms(const DevSys& S, const Layout& L, 
     const float tt = __fdividef(1.f, fmaf(bj, r, 1.f));
     float* pp = sm + M.pair + e * M.pair_st + 2 * j;
     pp[0] = r; pp[1] = tt;
-    if (write_pair_both) {
-      float* pq = sm + M.pair + j * M.pair_st + 2 * e;
-      pq[0] = r; pq[1] = tt;
-    }
     const float up = c * tt * tt, upp = -2.f * bj * up * tt, f = up * ir;
+    const float lap = upp + 2.f * f, hir = 0.5f * ir;
     gx = fmaf(f, dx, gx); gy = fmaf(f, dy, gy); gz = fmaf(f, dz, gz);
-    LJ += upp + 2.f * f;
-    vee = fmaf(0.5f, ir, vee);
+    LJ += lap;
+    vee += hir;
+    if (pt) {
+      float* q = pt + 3 * (e * ne + j);
+      q[0] = f; q[1] = lap; q[2] = hir;
+    }
   } else {
     const int I = t - (ne - 1);
     const float dx = xe - __ldg(S.Rf + 3 * I), dy = ye - __ldg(S.Rf + 3 * I + 1), dz = ze - __ldg(S.Rf + 3 * I + 2);
@@ -431,13 +481,15 @@ __device__ __forceinline__ void partner_terms(const DevSys& S, const Layout& L, 
 }
 
 // Full evaluation: every hop ratio as r - 1 (FP32), the FP64 accumulators and
-// every cache of the incremental update.  Requires g current.
+// every cache of the incremental update (the hop caches in scr when set).
+// Requires g current in scr.gf.
 __device__ EvalOut eval_full_m(const DevSys& S, const Layout& L, const LayoutM& M, double* gblk, float* sm,
-                               float* dchi, double a, int node_rule, int lane) {
+                               const ScrM& scr, double a, int node_rule, int lane) {
   const int ne = L.n_e, nbf = L.n_bf, nn = S.n_nuc, P = L.n_hop;
   const float af = (float)a, a2f = af * af;
   const float* xf = sm + M.xf;
-  const float* g = sm + M.gf;
+  const float* g = scr.gf;
+  float* dchi = scr.dchi;
   float* dl = sm + M.dl;
   float* ej = sm + M.ej;
   const float* geo = sm + M.geo;
@@ -458,7 +510,7 @@ __device__ EvalOut eval_full_m(const DevSys& S, const Layout& L, const LayoutM& 
       const int e = base + lane / G, sub = lane % G;
       float gx = 0.f, gy = 0.f, gz = 0.f, LJ = 0.f, vee = 0.f;
       if (e < ne)
-        for (int t = sub; t < per; t += G) partner_terms(S, L, M, sm, e, t, false, gx, gy, gz, LJ, vee);
+        for (int t = sub; t < per; t += G) partner_terms(S, L, M, sm, e, t, scr.pt, gx, gy, gz, LJ, vee);
       for (int o = G >> 1; o; o >>= 1) {
         gx += __shfl_xor_sync(FULL, gx, o);
         gy += __shfl_xor_sync(FULL, gy, o);
@@ -517,16 +569,18 @@ __device__ EvalOut eval_full_m(const DevSys& S, const Layout& L, const LayoutM& 
     }
     const float xia = xf[3 * i + ax];
     const float* pr = pair + i * M.pair_st;
-    float J2 = 0.f;
+    double J2 = 0.0;
     for (int j = 0; j < ne; ++j) {
       if (j == i) continue;
       const float del = fmaf(s2a, xia - xf[3 * j + ax], a2f);
-      J2 += pade_delta(pr[2 * j], pr[2 * j + 1], del, (float)pair_c(S, L, i, j), bj);
+      const float v = pade_delta(pr[2 * j], pr[2 * j + 1], del, (float)pair_c(S, L, i, j), bj);
+      J2 += (double)v;
+      if (scr.u2) scr.u2[(size_t)j * P + p] = v;
     }
     hdm[p] = D;
     hj1[p] = J1;
-    hj2[p] = (double)J2;
-    const float J = expm1_fast(J1 + J2);
+    hj2[p] = J2;
+    const float J = expm1_fast(J1 + (float)J2);
     dl[p] = fmaf(D, J, D + J);
   }
   __threadfence_block();
@@ -535,29 +589,69 @@ __device__ EvalOut eval_full_m(const DevSys& S, const Layout& L, const LayoutM& 
 }
 
 // Incremental evaluation after electron m hopped (old position at xo/xfo),
-// mirroring eval_incr of the FP64 kernel.
+// mirroring eval_incr of the FP64 kernel: m's terms from scratch, the other
+// electrons' pair terms with m swapped using the cached old terms (scr.pt for
+// the derivative sums, scr.u2 for the hop differences; the new difference of
+// hop d of electron i with m is m's opposite hop d ^ 1 with i).
 __device__ EvalOut eval_incr_m(const DevSys& S, const Layout& L, const LayoutM& M, double* gblk, float* sm,
-                               float* dchi, int m, bool all_blocks, double a, int node_rule, int lane) {
+                               const ScrM& scr, int m, bool all_blocks, double a, int node_rule, int lane) {
   const int ne = L.n_e, nbf = L.n_bf, nn = S.n_nuc, P = L.n_hop;
   const int per = ne - 1 + nn;
   const float af = (float)a, a2f = af * af;
   const float* xf = sm + M.xf;
   const float* xfo = sm + M.xfo;
-  const float* g = sm + M.gf;
+  const float* g = scr.gf;
+  float* dchi = scr.dchi;
   float* dl = sm + M.dl;
   float* ej = sm + M.ej;
   const float* geo = sm + M.geo;
   const float* rt1 = sm + M.rt1;
-  const float* pair = sm + M.pair;
+  float* pair = sm + M.pair;
   float* hdm = sm + M.hdm;
   float* hj1 = sm + M.hj1;
   double* hj2 = (double*)(sm + M.hj2);
   float* tmp = sm + M.tmp;
   const float bj = (float)S.j2_b;
-  // (A) electron m from scratch (geometry, pair data both ways, primitives, Jastrow sums)
+  // (A) electron m from scratch (geometry, pair data both ways, primitives,
+  // Jastrow sums); (B) the partner electron's sums swap their term with m
   {
+    const float xm = xf[3 * m], ym = xf[3 * m + 1], zm = xf[3 * m + 2];
+    const float xo0 = xfo[0], xo1 = xfo[1], xo2 = xfo[2];
     float gx = 0.f, gy = 0.f, gz = 0.f, LJ = 0.f, vee = 0.f;
-    for (int t = lane; t < per; t += WARP) partner_terms(S, L, M, sm, m, t, true, gx, gy, gz, LJ, vee);
+    for (int t = lane; t < per; t += WARP) {
+      if (t < ne - 1) {
+        const int j = t < m ? t : t + 1;
+        const float pxj = xf[3 * j], pyj = xf[3 * j + 1], pzj = xf[3 * j + 2];
+        const float dx = xm - pxj, dy = ym - pyj, dz = zm - pzj;
+        const float s = sqdistf(dx, dy, dz);
+        const float ir = rsqrtf(s), r = s * ir;
+        const float c = (float)pair_c(S, L, m, j);
+        const float tt = __fdividef(1.f, fmaf(bj, r, 1.f));
+        float* pp = pair + m * M.pair_st + 2 * j;
+        float* pq = pair + j * M.pair_st + 2 * m;
+        pp[0] = r; pp[1] = tt;
+        pq[0] = r; pq[1] = tt;
+        const float up = c * tt * tt, upp = -2.f * bj * up * tt, f = up * ir;
+        const float lap = upp + 2.f * f, hir = 0.5f * ir;
+        gx = fmaf(f, dx, gx); gy = fmaf(f, dy, gy); gz = fmaf(f, dz, gz);
+        LJ += lap;
+        vee += hir;
+        float* pm = scr.pt + 3 * (m * ne + j);
+        float* pj = scr.pt + 3 * (j * ne + m);
+        const float of = pm[0], ol = pm[1], oh = pm[2];
+        const float ox = pxj - xo0, oy = pyj - xo1, oz = pzj - xo2;
+        float* q = ej + 5 * j;
+        q[0] += f * -dx - of * ox;
+        q[1] += f * -dy - of * oy;
+        q[2] += f * -dz - of * oz;
+        q[3] += lap - ol;
+        q[4] += hir - oh;
+        pm[0] = f; pm[1] = lap; pm[2] = hir;
+        pj[0] = f; pj[1] = lap; pj[2] = hir;
+      } else {
+        partner_terms(S, L, M, sm, m, t, nullptr, gx, gy, gz, LJ, vee);
+      }
+    }
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
       gx += __shfl_xor_sync(FULL, gx, o);
@@ -570,30 +664,6 @@ __device__ EvalOut eval_incr_m(const DevSys& S, const Layout& L, const LayoutM& 
       float* q = ej + 5 * m;
       q[0] = gx; q[1] = gy; q[2] = gz; q[3] = LJ; q[4] = vee;
     }
-  }
-  // (B) every other electron: swap its pair derivative terms with m
-  for (int i = lane; i < ne; i += WARP) {
-    if (i == m) continue;
-    const float c = (float)pair_c(S, L, i, m);
-    const float xi = xf[3 * i], yi = xf[3 * i + 1], zi = xf[3 * i + 2];
-    const float ox = xi - xfo[0], oy = yi - xfo[1], oz = zi - xfo[2];
-    const float nx = xi - xf[3 * m], ny = yi - xf[3 * m + 1], nz = zi - xf[3 * m + 2];
-    float f[2], upp[2], ir[2];
-    const float s2[2] = {sqdistf(ox, oy, oz), sqdistf(nx, ny, nz)};
-    for (int k = 0; k < 2; ++k) {
-      ir[k] = rsqrtf(s2[k]);
-      const float r = s2[k] * ir[k];
-      const float tt = __fdividef(1.f, fmaf(bj, r, 1.f));
-      const float up = c * tt * tt;
-      upp[k] = -2.f * bj * up * tt;
-      f[k] = up * ir[k];
-    }
-    float* q = ej + 5 * i;
-    q[0] += f[1] * nx - f[0] * ox;
-    q[1] += f[1] * ny - f[0] * oy;
-    q[2] += f[1] * nz - f[0] * oz;
-    q[3] += (upp[1] + 2.f * f[1]) - (upp[0] + 2.f * f[0]);
-    q[4] += 0.5f * (ir[1] - ir[0]);
   }
   // (C) determinant derivatives of the refreshed block(s)
   const SpinRef srm = spin_ref(L, m);
@@ -637,6 +707,7 @@ __device__ EvalOut eval_incr_m(const DevSys& S, const Layout& L, const LayoutM& 
       const float* pp = pair + m * M.pair_st + 2 * j;
       const float del = fmaf(sa + sa, xf[3 * m + ax] - xf[3 * j + ax], a2f);
       v = pade_delta(pp[0], pp[1], del, (float)pair_c(S, L, m, j), bj);
+      scr.u2[(size_t)j * P + 6 * m + d] = v;
     } else {
       const int I = t - (ne - 1);
       const float A = __ldg(S.j1Af + I);
@@ -649,38 +720,53 @@ __device__ EvalOut eval_incr_m(const DevSys& S, const Layout& L, const LayoutM& 
   }
   __threadfence_block();
   __syncwarp();
-  if (lane < 6) {
-    float J1 = 0.f, J2 = 0.f;
-    for (int t = 0; t < per; ++t) {
-      if (t < ne - 1) J2 += tmp[lane * per + t];
-      else J1 += tmp[lane * per + t];
+  {
+    // sums over partners of each of m's hops: four lanes per hop; the pair sum in FP64
+    const int d = lane >> 2, sub = lane & 3;
+    float J1 = 0.f;
+    double J2 = 0.0;
+    if (d < 6)
+      for (int t = sub; t < per; t += 4) {
+        const float v = tmp[d * per + t];
+        if (t < ne - 1) J2 += (double)v;
+        else J1 += v;
+      }
+    J1 += __shfl_xor_sync(FULL, J1, 1);
+    J2 += __shfl_xor_sync(FULL, J2, 1);
+    J1 += __shfl_xor_sync(FULL, J1, 2);
+    J2 += __shfl_xor_sync(FULL, J2, 2);
+    if (d < 6 && sub == 0) {
+      hj1[6 * m + d] = J1;
+      hj2[6 * m + d] = J2;
     }
-    hj1[6 * m + lane] = J1;
-    hj2[6 * m + lane] = (double)J2;
   }
-  // (E) determinant differences of the refreshed block(s) from the cached basis differences
-  for (int p = lane + 6 * b0; p < 6 * b1; p += WARP) {
-    const float* gi = g + (p / 6) * nbf;
-    float D = 0.f;
-    for (int mu = 0; mu < nbf; ++mu) D = fmaf(dchi[(size_t)mu * P + p], gi[mu], D);
-    hdm[p] = D;
+  // (E) determinant differences of the refreshed block(s) from the cached
+  // basis differences, each dot product split over G lanes
+  {
+    const int n_out = 6 * (b1 - b0), G = split_factor(n_out, nbf);
+    const int chunk = (nbf + G - 1) / G, n_task = n_out * G;
+    for (int base = 0; base < n_task; base += WARP) {
+      const int task = base + lane, o = task / G, part = task - o * G;
+      const int p = 6 * b0 + o;
+      float D = 0.f;
+      if (task < n_task) {
+        const float* gi = g + (p / 6) * nbf;
+        const int mu1 = min(nbf, (part + 1) * chunk);
+        for (int mu = part * chunk; mu < mu1; ++mu) D = fmaf(dchi[(size_t)mu * P + p], gi[mu], D);
+      }
+      for (int sh = 1; sh < G; sh <<= 1) D += __shfl_xor_sync(FULL, D, sh);
+      if (task < n_task && part == 0) hdm[p] = D;
+    }
   }
   // (F) pair Jastrow differences of the other electrons' hops: swap the term with m
   for (int p = lane; p < P; p += WARP) {
     const int i = p / 6;
     if (i == m) continue;
-    const int d = p - 6 * i, ax = d >> 1;
-    const float s2a = (d & 1) ? -2.f * af : 2.f * af;
-    const float c = (float)pair_c(S, L, i, m);
-    const float xia = xf[3 * i + ax];
-    const float ox = xf[3 * i] - xfo[0], oy = xf[3 * i + 1] - xfo[1], oz = xf[3 * i + 2] - xfo[2];
-    const float so = sqdistf(ox, oy, oz);
-    const float iro = rsqrtf(so), ro = so * iro;
-    const float to = __fdividef(1.f, fmaf(bj, ro, 1.f));
-    const float vo = pade_delta(ro, to, fmaf(s2a, xia - xfo[ax], a2f), c, bj);
-    const float* pn = pair + i * M.pair_st + 2 * m;
-    const float vn = pade_delta(pn[0], pn[1], fmaf(s2a, xia - xf[3 * m + ax], a2f), c, bj);
-    hj2[p] += (double)vn - (double)vo;
+    const int d = p - 6 * i;
+    const float vn = tmp[(d ^ 1) * per + (i < m ? i : i - 1)];
+    float* u = scr.u2 + (size_t)m * P + p;
+    hj2[p] += (double)vn - (double)*u;
+    *u = vn;
   }
   __threadfence_block();
   __syncwarp();
@@ -696,7 +782,7 @@ __device__ EvalOut eval_incr_m(const DevSys& S, const Layout& L, const LayoutM& 
 }
 
 __device__ EvalOut init_walker_m(const DevSys& S, const Layout& L, const LayoutM& M, double* gblk, float* sm,
-                                 double* gj, double a, int node_rule, const double* T, int lane, bool& singular) {
+                                 const ScrM& scr, double a, int node_rule, const double* T, int lane, bool& singular) {
   double* val = cache_val(L, gblk);
   float* der = cache_der(L, gblk);
   const double* x = (const double*)(sm + M.x);
@@ -722,26 +808,18 @@ __device__ EvalOut init_walker_m(const DevSys& S, const Layout& L, const LayoutM
     __syncwarp();
   }
   __threadfence_block();
-  singular = reinvert_m(L, M, gblk, sm, gj, lane);
-  compute_g_m(S, L, M, sm, 0, L.n_e, lane);
-  return eval_full_m(S, L, M, gblk, sm, nullptr, a, node_rule, lane);
+  singular = reinvert_m(L, M, gblk, sm, scr.gj, lane);
+  compute_g_m(S, L, M, sm, scr.gf, 0, L.n_e, lane);
+  return eval_full_m(S, L, M, gblk, sm, scr, a, node_rule, lane);
 }
 
 // Heat-bath choice from r - 1 values: same order and rule as the FP64 path
 // (first hop whose running sum of kept ratios exceeds u * total, last kept hop
 // if rounding leaves none), with the running sums formed by warp scans over
-// chunks of 32 hops in FP32.
-__device__ int choose_hop_m(const float* dl, int n_hop, double u, int lane) {
-  float total = 0.f;
-  for (int c = 0; c < n_hop; c += WARP) {
-    const int p = c + lane;
-    float k = (p < n_hop && dl[p] > -1.f) ? 1.f + dl[p] : 0.f;
-#pragma unroll
-    for (int o = 16; o; o >>= 1) k += __shfl_xor_sync(FULL, k, o);
-    total += k;
-  }
-  if (!(total > 0.f)) return -1;
-  const float t = (float)u * total;
+// chunks of 32 hops in FP32; total is the evaluation's sum of kept ratios.
+__device__ int choose_hop_m(const float* dl, int n_hop, double u, double total, int lane) {
+  if (!(total > 0.0)) return -1;
+  const float t = (float)(u * total);
   float base = 0.f;
   int last = -1;
   for (int c = 0; c < n_hop; c += WARP) {
@@ -765,8 +843,8 @@ __device__ int choose_hop_m(const float* dl, int n_hop, double u, int lane) {
 // Apply hop p: FP64 orbital value row and Sherman-Morrison update of B, FP32
 // derivative rows, g of the moved spin block, potentials and position; the
 // old position goes to xo / xfo.
-__device__ void apply_hop_m(const DevSys& S, const Layout& L, const LayoutM& M, double* gblk, float* sm, int p,
-                            double a, const double* T, int lane) {
+__device__ void apply_hop_m(const DevSys& S, const Layout& L, const LayoutM& M, double* gblk, float* sm, float* gf,
+                            int p, double a, const double* T, int lane) {
   double* x = (double*)(sm + M.x);
   float* xf = sm + M.xf;
   double* bt = (double*)(sm + M.bt);
@@ -815,7 +893,7 @@ __device__ void apply_hop_m(const DevSys& S, const Layout& L, const LayoutM& M, 
   }
   __threadfence_block();
   __syncwarp();
-  compute_g_m(S, L, M, sm, i - sr.ii, i - sr.ii + n, lane);
+  compute_g_m(S, L, M, sm, gf, i - sr.ii, i - sr.ii + n, lane);
 }
 
 __device__ __forceinline__ void load_block_m(const Layout& L, const LayoutM& M, const double* __restrict__ g,
@@ -847,14 +925,22 @@ __device__ __forceinline__ void store_block_m(const Layout& L, const LayoutM& M,
   for (int o = lane; o < SC_COUNT; o += WARP) g[L.g_sc + o] = sc[o];
 }
 
-__device__ __forceinline__ float* warp_dchi(const Layout& L, double* scratch, int slot) {
-  return (float*)(scratch + (size_t)slot * scratch_doubles_m(L));
-}
-__device__ __forceinline__ double* warp_gj_m(const Layout& L, double* scratch, int slot) {
-  return scratch + (size_t)slot * scratch_doubles_m(L) + ((size_t)L.n_bf * L.n_hop + 1) / 2;
+// Shared-memory caches [mir, mir_end) from / to the walker's cache block.
+__device__ __forceinline__ void load_mirror_m(const LayoutM& M, const double* __restrict__ c, float* sm, int lane) {
+  double* d = (double*)(sm + M.mir);
+  const int n = (M.mir_end - M.mir) / 2;
+  for (int o = lane; o < n; o += WARP) d[o] = c[o];
+  __syncwarp();
 }
 
-__global__ void k_init_walkers_m(DevSys S, Layout L, LayoutM M, double* __restrict__ state,
+__device__ __forceinline__ void store_mirror_m(const LayoutM& M, double* __restrict__ c, const float* sm, int lane) {
+  __syncwarp();
+  const double* d = (const double*)(sm + M.mir);
+  const int n = (M.mir_end - M.mir) / 2;
+  for (int o = lane; o < n; o += WARP) c[o] = d[o];
+}
+
+__global__ void k_init_walkers_m(DevSys S, Layout L, LayoutM M, double* __restrict__ state, double* __restrict__ cache,
                                  const double* __restrict__ x_in, const double* __restrict__ w_in, int n, double a,
                                  int node_rule, double* scratch) {
   extern __shared__ double smem[];
@@ -865,13 +951,15 @@ __global__ void k_init_walkers_m(DevSys S, Layout L, LayoutM M, double* __restri
   double* sc = (double*)(sm + M.sc);
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   const int slot = blockIdx.x * (blockDim.x >> 5) + wib;
-  double* gj = warp_gj_m(L, scratch, slot);
+  const ScrM wscr = warp_scratch_m(L, scratch, slot);
   for (int w = slot; w < n; w += nwarps) {
     double* gblk = state + (size_t)w * L.g_stride;
+    double* cblk = cache + (size_t)w * L.c_stride;
+    const ScrM scr = walker_scratch_m(M, cblk, wscr);
     for (int o = lane; o < 3 * L.n_e; o += WARP) x[o] = x_in[(size_t)w * 3 * L.n_e + o];
     __syncwarp();
     bool sing = false;
-    const EvalOut e = init_walker_m(S, L, M, gblk, sm, gj, a, node_rule, T, lane, sing);
+    const EvalOut e = init_walker_m(S, L, M, gblk, sm, scr, a, node_rule, T, lane, sing);
     if (lane == 0) {
       for (int k = 0; k < SC_COUNT; ++k) sc[k] = 0.0;
       sc[SC_W] = w_in ? w_in[w] : 1.0;
@@ -881,8 +969,11 @@ __global__ void k_init_walkers_m(DevSys S, Layout L, LayoutM M, double* __restri
       sc[SC_EL] = e.eL;
       sc[SC_NNODE] = e.n_node;
       sc[SC_STATUS] = sing ? (double)ST_SINGULAR : 0.0;
+      sc[SC_CACHE] = sing ? 0.0 : 1.0;
+      sc[SC_KEPT] = e.kept;
     }
     store_block_m(L, M, gblk, sm, lane);
+    store_mirror_m(M, cblk, sm, lane);
   }
 }
 
@@ -897,13 +988,13 @@ __global__ void k_eval_configs_m(DevSys S, Layout L, LayoutM M, double* __restri
   double* x = (double*)(sm + M.x);
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   const int slot = blockIdx.x * (blockDim.x >> 5) + wib;
-  double* gj = warp_gj_m(L, scratch, slot);
+  const ScrM scr = warp_scratch_m(L, scratch, slot);
   for (int w = slot; w < n; w += nwarps) {
     double* gblk = blocks + (size_t)w * L.g_stride;
     for (int o = lane; o < 3 * L.n_e; o += WARP) x[o] = x_in[(size_t)w * 3 * L.n_e + o];
     __syncwarp();
     bool sing = false;
-    const EvalOut e = init_walker_m(S, L, M, gblk, sm, gj, a, node_rule, T, lane, sing);
+    const EvalOut e = init_walker_m(S, L, M, gblk, sm, scr, a, node_rule, T, lane, sing);
     for (int o = lane; o < L.n_hop; o += WARP) ratios[(size_t)w * L.n_hop + o] = 1.0 + (double)sm[M.dl + o];
     if (lane == 0) {
       ev[4 * (size_t)w] = e.bbar;
@@ -916,8 +1007,10 @@ __global__ void k_eval_configs_m(DevSys S, Layout L, LayoutM M, double* __restri
   }
 }
 
-__global__ void k_propagate_m(DevSys S, Layout L, LayoutM M, double* __restrict__ state, int n_w, StepParams P,
-                              double* scratch) {
+// One branching interval for every walker (mixed precision); the caches of
+// the incremental evaluation persist in the walker's cache block.
+__global__ void k_propagate_m(DevSys S, Layout L, LayoutM M, double* __restrict__ state, double* __restrict__ cache,
+                              int n_w, StepParams P, double* scratch) {
   extern __shared__ double smem[];
   const double* T = stage_table(S, smem);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -925,17 +1018,20 @@ __global__ void k_propagate_m(DevSys S, Layout L, LayoutM M, double* __restrict_
   double* sc = (double*)(sm + M.sc);
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   const int slot = blockIdx.x * (blockDim.x >> 5) + wib;
-  float* dchi = warp_dchi(L, scratch, slot);
-  double* gj = warp_gj_m(L, scratch, slot);
+  const ScrM wscr = warp_scratch_m(L, scratch, slot);
   for (int w = slot; w < n_w; w += nwarps) {
     const unsigned long long t_start = global_ns();
     double* gblk = state + (size_t)w * L.g_stride;
+    double* cblk = cache + (size_t)w * L.c_stride;
+    const ScrM scr = walker_scratch_m(M, cblk, wscr);
     load_block_m(L, M, gblk, sm, lane);
+    bool cached = sc[SC_CACHE] != 0.0;
+    if (cached) load_mirror_m(M, cblk, sm, lane);
+    bool g_valid = cached;
     double weight = 1.0, tau_left = P.tau;
-    double bbar = sc[SC_BBAR], Wd = sc[SC_WDIAG], eL = sc[SC_EL];
+    double bbar = sc[SC_BBAR], Wd = sc[SC_WDIAG], eL = sc[SC_EL], kept = sc[SC_KEPT];
     uint32_t status = (uint32_t)sc[SC_STATUS];
     int moves = 0, since = (int)sc[SC_SINCE];
-    bool g_valid = false, cached = false;
     for (int k = 0;; ++k) {
       if (P.kind == 1 && k >= P.n_proj) break;
       double u_tau, u_move;
@@ -956,39 +1052,41 @@ __global__ void k_propagate_m(DevSys S, Layout L, LayoutM M, double* __restrict_
         tau_left -= t;
         if (clipped) break;
       }
-      const int p = choose_hop_m(sm + M.dl, L.n_hop, u_move, lane);
+      const int p = choose_hop_m(sm + M.dl, L.n_hop, u_move, kept, lane);
       if (p < 0) {
         status |= ST_STUCK;
       } else {
-        apply_hop_m(S, L, M, gblk, sm, p, P.a, T, lane);
+        apply_hop_m(S, L, M, gblk, sm, scr.gf, p, P.a, T, lane);
         ++moves;
         bool reinv = false;
         if (++since >= P.reinv_period) {
-          if (reinvert_m(L, M, gblk, sm, gj, lane)) status |= ST_SINGULAR;
+          if (reinvert_m(L, M, gblk, sm, scr.gj, lane)) status |= ST_SINGULAR;
           since = 0;
           g_valid = false;
           reinv = true;
         }
         if (!g_valid) {
-          compute_g_m(S, L, M, sm, 0, L.n_e, lane);
+          compute_g_m(S, L, M, sm, scr.gf, 0, L.n_e, lane);
           g_valid = true;
         }
         EvalOut e;
         if (!cached) {
-          e = eval_full_m(S, L, M, gblk, sm, dchi, P.a, P.node_rule, lane);
+          e = eval_full_m(S, L, M, gblk, sm, scr, P.a, P.node_rule, lane);
           cached = true;
         } else {
-          e = eval_incr_m(S, L, M, gblk, sm, dchi, p / 6, reinv, P.a, P.node_rule, lane);
+          e = eval_incr_m(S, L, M, gblk, sm, scr, p / 6, reinv, P.a, P.node_rule, lane);
         }
         bbar = e.bbar;
         Wd = e.W;
         eL = e.eL;
+        kept = e.kept;
         if (lane == 0) {
           sc[SC_BBAR] = e.bbar;
           sc[SC_VSF] = e.vsf;
           sc[SC_WDIAG] = e.W;
           sc[SC_EL] = e.eL;
           sc[SC_NNODE] = e.n_node;
+          sc[SC_KEPT] = e.kept;
         }
       }
       if (P.kind == 0 && k + 1 >= P.max_moves) {
@@ -997,13 +1095,16 @@ __global__ void k_propagate_m(DevSys S, Layout L, LayoutM M, double* __restrict_
       }
     }
     if (!isfinite(weight) || !isfinite(eL)) status |= ST_NONFINITE;
+    const bool keep = cached && !(status & ST_SINGULAR);
     if (lane == 0) {
       sc[SC_W] = weight;
       sc[SC_STATUS] = (double)status;
       sc[SC_MOVES] = moves;
       sc[SC_SINCE] = since;
+      sc[SC_CACHE] = keep ? 1.0 : 0.0;
     }
     store_block_m(L, M, gblk, sm, lane);
+    if (keep) store_mirror_m(M, cblk, sm, lane);
     if (P.stamps && lane == 0) {
       P.stamps[3 * (size_t)w] = t_start;
       P.stamps[3 * (size_t)w + 1] = global_ns();
