@@ -42,15 +42,14 @@ namespace lrdmc {
 struct LayoutM {
   int sc, x, bt, phiv, chiv, u, row, xo;                               // doubles
   int dd, hj2;                                                         // doubles, kept
-  int dl, ej, ep, geo, rt1, pair, hcur, hdm, hj1;                      // floats, kept
-  int xf, xfo, chi5, phi5, bf32, tmp;                                  // floats
+  int dl, ej, ep, geo, rt1, pair, hcur, hdm, hj1, dph;                 // floats, kept
+  int xf, xfo, b32, chi5, phi5, tmp;                                   // floats
   int geo_st, rt1_st, pair_st, hcur_st, stride;
   int mir, mir_end;
-  // walker cache block, in floats: the shared-memory copy, g_i = C^T B[:, i]
-  // [n_e][n_bf], the basis differences at every hop [n_bf][6 n_e], the pair
-  // Jastrow difference of every hop with every partner [n_e][6 n_e] and the
-  // pair derivative terms at the current positions [n_e][n_e][3]
-  int c_gf, c_dchi, c_u2, c_pt, c_floats;
+  // walker cache block, in floats: the shared-memory copy, the pair Jastrow
+  // difference of every hop with every partner [n_e][6 n_e] and the pair
+  // derivative terms at the current positions [n_e][n_e][3]
+  int c_u2, c_pt, c_floats;
 };
 
 __host__ __device__ inline LayoutM layout_mixed(const Layout& L, int n_nuc, int n_prim) {
@@ -82,40 +81,38 @@ __host__ __device__ inline LayoutM layout_mixed(const Layout& L, int n_nuc, int 
   M.hcur = o; o += ne * M.hcur_st;
   M.hdm = o; o += P;
   M.hj1 = o; o += P;
+  M.dph = o; o += P * nm;      // orbital differences at every hop [6 n_e][n_max]
   o = round_up(o, 2);
   M.mir_end = o;
   M.xf = o; o += 3 * ne;
   M.xfo = o; o += 4;
-  // move scratch (basis rows, FP32 copy of B^T) and the per-hop Jastrow
-  // scratch of an evaluation share one region: they are never live together
-  int sh = 5 * nbf > nbt ? 5 * nbf : nbt;
-  sh = sh > 6 * per ? sh : 6 * per;
+  M.b32 = o; o += nbt;         // FP32 copy of B^T
+  // move scratch (basis rows), the basis differences at the moved electron's
+  // six hops [n_bf][6] and the per-hop Jastrow scratch of an evaluation share
+  // one region: they are never live together
+  int sh = 6 * nbf > 6 * per ? 6 * nbf : 6 * per;
   M.chi5 = o; o += sh;
-  M.bf32 = M.chi5;
   M.tmp = M.chi5;
   M.phi5 = o; o += 5 * nm;
   M.stride = round_up(o, 4);
   int c = round_up(M.mir_end - M.mir, 4);
-  M.c_gf = c; c += round_up(ne * nbf, 4);
-  M.c_dchi = c; c += round_up(nbf * P, 4);
   M.c_u2 = c; c += round_up(ne * P, 4);
   M.c_pt = c; c += round_up(3 * ne * ne, 4);
   M.c_floats = c;
   return M;
 }
 
-// Per-warp global scratch of the mixed kernels: g [n_e][n_bf] floats for
-// configuration evaluation (the walkers keep theirs in the cache block) and
-// the FP64 Gauss-Jordan work matrix [n_max][2 n_max].
+// Per-warp global scratch of the mixed kernels: the basis differences at every
+// hop [n_bf][6 n_e] floats (live only during a full evaluation) and the FP64
+// Gauss-Jordan work matrix [n_max][2 n_max].
 __host__ __device__ inline size_t scratch_doubles_m(const Layout& L) {
-  return ((size_t)L.n_e * L.n_bf + 1) / 2 + 2 * (size_t)L.n_max * L.n_max;
+  return ((size_t)L.n_bf * L.n_hop + 1) / 2 + 2 * (size_t)L.n_max * L.n_max;
 }
 
 // Global working arrays of one mixed evaluation (see LayoutM for the layouts);
-// dchi, u2 and pt are null for configuration evaluation.
+// u2 and pt are null for configuration evaluation.
 struct ScrM {
-  float* gf;
-  float* dchi;
+  float* dchi;   // per-warp scratch of a full evaluation
   float* u2;
   float* pt;
   double* gj;
@@ -123,16 +120,15 @@ struct ScrM {
 __device__ __forceinline__ ScrM warp_scratch_m(const Layout& L, double* scratch, int slot) {
   ScrM s;
   double* base = scratch + (size_t)slot * scratch_doubles_m(L);
-  s.gf = (float*)base;
-  s.gj = base + ((size_t)L.n_e * L.n_bf + 1) / 2;
-  s.dchi = s.u2 = s.pt = nullptr;
+  s.dchi = (float*)base;
+  s.gj = base + ((size_t)L.n_bf * L.n_hop + 1) / 2;
+  s.u2 = s.pt = nullptr;
   return s;
 }
 __device__ __forceinline__ ScrM walker_scratch_m(const LayoutM& M, double* cblk, const ScrM& warp) {
   ScrM s;
   float* c = (float*)cblk;
-  s.gf = c + M.c_gf;
-  s.dchi = c + M.c_dchi;
+  s.dchi = warp.dchi;
   s.u2 = c + M.c_u2;
   s.pt = c + M.c_pt;
   s.gj = warp.gj;
@@ -314,23 +310,55 @@ __device__ bool reinvert_m(const Layout& L, const LayoutM& M, double* gblk, floa
   return sing;
 }
 
-// g_i = C^T B[:, i] in FP32 from B rounded to FP32, for electrons [e0, e1).
-__device__ void compute_g_m(const DevSys& S, const Layout& L, const LayoutM& M, float* sm, float* g, int e0, int e1,
-                            int lane) {
+// FP32 copy of B^T for the spin blocks of electrons [e0, e1) (whole blocks).
+__device__ void refresh_b32(const Layout& L, const LayoutM& M, float* sm, int e0, int e1, int lane) {
   const double* bt = (const double*)(sm + M.bt);
-  float* b32 = sm + M.bf32;
-  const int nbt = L.n_up * L.n_up + L.n_dn * L.n_dn;
-  for (int o = lane; o < nbt; o += WARP) b32[o] = (float)bt[o];
+  float* b32 = sm + M.b32;
+  const int o0 = e0 < L.n_up ? 0 : L.n_up * L.n_up;
+  const int o1 = e1 <= L.n_up ? L.n_up * L.n_up : L.n_up * L.n_up + L.n_dn * L.n_dn;
+  for (int o = o0 + lane; o < o1; o += WARP) b32[o] = (float)bt[o];
   __syncwarp();
-  for (int o = lane + e0 * L.n_bf; o < e1 * L.n_bf; o += WARP) {
-    const int i = o / L.n_bf, mu = o - i * L.n_bf;
-    const SpinRef sr = spin_ref(L, i);
-    const float* brow = b32 + sr.bt_off + sr.ii * sr.n;
+}
+
+// Orbital differences dph[p][k] = sum_mu C_k,mu dchi_mu(p) of the hops
+// p = p0 + c, c in [0, n_hops), read from dchi[mu * ld + c]; k over the
+// electron's spin block, each dot split over G lanes.
+__device__ void orbital_diffs(const DevSys& S, const Layout& L, const LayoutM& M, float* sm, const float* dchi,
+                              int ld, int p0, int n_hops, int lane) {
+  float* dph = sm + M.dph;
+  const int nm = L.n_max, nbf = L.n_bf;
+  const int n_out = n_hops * nm, G = split_factor(n_out, nbf);
+  const int chunk = (nbf + G - 1) / G, n_task = n_out * G;
+  for (int base = 0; base < n_task; base += WARP) {
+    const int task = base + lane, o = task / G, part = task - o * G;
+    const int c = o / nm, k = o - c * nm;
+    const int p = p0 + c;
+    const int nsig = (p / 6) < L.n_up ? L.n_up : L.n_dn;
     float acc = 0.f;
-    for (int k = 0; k < sr.n; ++k) acc = fmaf(__ldg(S.Cf + (size_t)k * L.n_bf + mu), brow[k], acc);
-    g[o] = acc;
+    if (task < n_task && k < nsig) {
+      const float* crow = S.Cf + (size_t)k * nbf;
+      const int mu1 = min(nbf, (part + 1) * chunk);
+      for (int mu = part * chunk; mu < mu1; ++mu) acc = fmaf(__ldg(crow + mu), dchi[(size_t)mu * ld + c], acc);
+    }
+    for (int sh = 1; sh < G; sh <<= 1) acc += __shfl_xor_sync(FULL, acc, sh);
+    if (task < n_task && part == 0) dph[p * nm + k] = acc;
   }
-  __threadfence_block();
+  __syncwarp();
+}
+
+// Determinant ratio minus one of hops [p0, p1): dph[p] . B[:, i] (FP32 B).
+__device__ void det_diffs(const Layout& L, const LayoutM& M, float* sm, int p0, int p1, int lane) {
+  const float* dph = sm + M.dph;
+  const float* b32 = sm + M.b32;
+  float* hdm = sm + M.hdm;
+  for (int p = p0 + lane; p < p1; p += WARP) {
+    const SpinRef sr = spin_ref(L, p / 6);
+    const float* brow = b32 + sr.bt_off + sr.ii * sr.n;
+    const float* f = dph + p * L.n_max;
+    float D = 0.f;
+    for (int k = 0; k < sr.n; ++k) D = fmaf(f[k], brow[k], D);
+    hdm[p] = D;
+  }
   __syncwarp();
 }
 
@@ -481,14 +509,13 @@ __device__ __forceinline__ void partner_terms(const DevSys& S, const Layout& L, 
 }
 
 // Full evaluation: every hop ratio as r - 1 (FP32), the FP64 accumulators and
-// every cache of the incremental update (the hop caches in scr when set).
-// Requires g current in scr.gf.
+// every cache of the incremental update (the pair caches in scr when set).
+// Requires the FP32 copy of B current.
 __device__ EvalOut eval_full_m(const DevSys& S, const Layout& L, const LayoutM& M, double* gblk, float* sm,
                                const ScrM& scr, double a, int node_rule, int lane) {
-  const int ne = L.n_e, nbf = L.n_bf, nn = S.n_nuc, P = L.n_hop;
+  const int ne = L.n_e, nn = S.n_nuc, P = L.n_hop;
   const float af = (float)a, a2f = af * af;
   const float* xf = sm + M.xf;
-  const float* g = scr.gf;
   float* dchi = scr.dchi;
   float* dl = sm + M.dl;
   float* ej = sm + M.ej;
@@ -526,15 +553,14 @@ __device__ EvalOut eval_full_m(const DevSys& S, const Layout& L, const LayoutM& 
   }
   det_derivs_m(L, M, gblk, sm, 0, ne, lane);
   __syncwarp();
-  // (3) every hop, as r - 1, in FP32; caches the basis differences and the
-  // one-body / pair Jastrow differences per hop
+  // (3) every hop: basis differences (to scratch) and the one-body / pair
+  // Jastrow differences
   for (int p = lane; p < P; p += WARP) {
     const int i = p / 6, d = p - 6 * i, ax = d >> 1;
     const float sa = (d & 1) ? -af : af;
     const float s2a = sa + sa;
-    const float* gi = g + i * nbf;
     const float* hc = hcur + i * M.hcur_st;
-    float D = 0.f, J1 = 0.f;
+    float J1 = 0.f;
     for (int I = 0; I < nn; ++I) {
       const float* gg = geo + i * M.geo_st + 4 * I;
       const float del = fmaf(s2a, gg[ax], a2f);             // |r'-R|^2 - |r-R|^2
@@ -556,14 +582,9 @@ __device__ EvalOut eval_full_m(const DevSys& S, const Layout& L, const LayoutM& 
           rn += h + dh;
         }
         if (l != 1) {
-          D = fmaf(rd, gi[bf], D);
-          if (dchi) dchi[(size_t)bf * P + p] = rd;
+          dchi[(size_t)bf * P + p] = rd;
         } else {
-          float dc[3];
-          for (int k = 0; k < 3; ++k) dc[k] = fmaf(gg[k], rd, k == ax ? sa * rn : 0.f);
-          D = fmaf(dc[0], gi[bf], fmaf(dc[1], gi[bf + 1], fmaf(dc[2], gi[bf + 2], D)));
-          if (dchi)
-            for (int k = 0; k < 3; ++k) dchi[(size_t)(bf + k) * P + p] = dc[k];
+          for (int k = 0; k < 3; ++k) dchi[(size_t)(bf + k) * P + p] = fmaf(gg[k], rd, k == ax ? sa * rn : 0.f);
         }
       }
     }
@@ -577,13 +598,19 @@ __device__ EvalOut eval_full_m(const DevSys& S, const Layout& L, const LayoutM& 
       J2 += (double)v;
       if (scr.u2) scr.u2[(size_t)j * P + p] = v;
     }
-    hdm[p] = D;
     hj1[p] = J1;
     hj2[p] = J2;
-    const float J = expm1_fast(J1 + (float)J2);
-    dl[p] = fmaf(D, J, D + J);
   }
   __threadfence_block();
+  __syncwarp();
+  // (4) orbital differences of every hop and the determinant ratios
+  orbital_diffs(S, L, M, sm, dchi, P, 0, P, lane);
+  det_diffs(L, M, sm, 0, P, lane);
+  for (int p = lane; p < P; p += WARP) {
+    const float D = hdm[p];
+    const float J = expm1_fast(hj1[p] + (float)hj2[p]);
+    dl[p] = fmaf(D, J, D + J);
+  }
   __syncwarp();
   return assemble_m(S, L, M, sm, a, node_rule, lane);
 }
@@ -595,13 +622,12 @@ __device__ EvalOut eval_full_m(const DevSys& S, const Layout& L, const LayoutM& 
 // hop d of electron i with m is m's opposite hop d ^ 1 with i).
 __device__ EvalOut eval_incr_m(const DevSys& S, const Layout& L, const LayoutM& M, double* gblk, float* sm,
                                const ScrM& scr, int m, bool all_blocks, double a, int node_rule, int lane) {
-  const int ne = L.n_e, nbf = L.n_bf, nn = S.n_nuc, P = L.n_hop;
+  const int ne = L.n_e, nn = S.n_nuc, P = L.n_hop;
   const int per = ne - 1 + nn;
   const float af = (float)a, a2f = af * af;
   const float* xf = sm + M.xf;
   const float* xfo = sm + M.xfo;
-  const float* g = scr.gf;
-  float* dchi = scr.dchi;
+  float* dc6 = sm + M.chi5;     // basis differences at m's hops [n_bf][6]
   float* dl = sm + M.dl;
   float* ej = sm + M.ej;
   const float* geo = sm + M.geo;
@@ -691,13 +717,14 @@ __device__ EvalOut eval_incr_m(const DevSys& S, const Layout& L, const LayoutM& 
       rd += dh;
       rn += h + dh;
     }
-    const int p = 6 * m + d;
     if (l != 1) {
-      dchi[(size_t)bf * P + p] = rd;
+      dc6[bf * 6 + d] = rd;
     } else {
-      for (int k = 0; k < 3; ++k) dchi[(size_t)(bf + k) * P + p] = fmaf(gg[k], rd, k == ax ? sa * rn : 0.f);
+      for (int k = 0; k < 3; ++k) dc6[(bf + k) * 6 + d] = fmaf(gg[k], rd, k == ax ? sa * rn : 0.f);
     }
   }
+  __syncwarp();
+  orbital_diffs(S, L, M, sm, dc6, 6, 6 * m, 6, lane);
   for (int o = lane; o < 6 * per; o += WARP) {
     const int d = o / per, t = o - d * per, ax = d >> 1;
     const float sa = (d & 1) ? -af : af;
@@ -741,23 +768,8 @@ __device__ EvalOut eval_incr_m(const DevSys& S, const Layout& L, const LayoutM& 
     }
   }
   // (E) determinant differences of the refreshed block(s) from the cached
-  // basis differences, each dot product split over G lanes
-  {
-    const int n_out = 6 * (b1 - b0), G = split_factor(n_out, nbf);
-    const int chunk = (nbf + G - 1) / G, n_task = n_out * G;
-    for (int base = 0; base < n_task; base += WARP) {
-      const int task = base + lane, o = task / G, part = task - o * G;
-      const int p = 6 * b0 + o;
-      float D = 0.f;
-      if (task < n_task) {
-        const float* gi = g + (p / 6) * nbf;
-        const int mu1 = min(nbf, (part + 1) * chunk);
-        for (int mu = part * chunk; mu < mu1; ++mu) D = fmaf(dchi[(size_t)mu * P + p], gi[mu], D);
-      }
-      for (int sh = 1; sh < G; sh <<= 1) D += __shfl_xor_sync(FULL, D, sh);
-      if (task < n_task && part == 0) hdm[p] = D;
-    }
-  }
+  // orbital differences
+  det_diffs(L, M, sm, 6 * b0, 6 * b1, lane);
   // (F) pair Jastrow differences of the other electrons' hops: swap the term with m
   for (int p = lane; p < P; p += WARP) {
     const int i = p / 6;
@@ -809,7 +821,7 @@ __device__ EvalOut init_walker_m(const DevSys& S, const Layout& L, const LayoutM
   }
   __threadfence_block();
   singular = reinvert_m(L, M, gblk, sm, scr.gj, lane);
-  compute_g_m(S, L, M, sm, scr.gf, 0, L.n_e, lane);
+  refresh_b32(L, M, sm, 0, L.n_e, lane);
   return eval_full_m(S, L, M, gblk, sm, scr, a, node_rule, lane);
 }
 
@@ -843,8 +855,8 @@ __device__ int choose_hop_m(const float* dl, int n_hop, double u, double total, 
 // Apply hop p: FP64 orbital value row and Sherman-Morrison update of B, FP32
 // derivative rows, g of the moved spin block, potentials and position; the
 // old position goes to xo / xfo.
-__device__ void apply_hop_m(const DevSys& S, const Layout& L, const LayoutM& M, double* gblk, float* sm, float* gf,
-                            int p, double a, const double* T, int lane) {
+__device__ void apply_hop_m(const DevSys& S, const Layout& L, const LayoutM& M, double* gblk, float* sm, int p,
+                            double a, const double* T, int lane) {
   double* x = (double*)(sm + M.x);
   float* xf = sm + M.xf;
   double* bt = (double*)(sm + M.bt);
@@ -893,7 +905,7 @@ __device__ void apply_hop_m(const DevSys& S, const Layout& L, const LayoutM& M, 
   }
   __threadfence_block();
   __syncwarp();
-  compute_g_m(S, L, M, sm, gf, i - sr.ii, i - sr.ii + n, lane);
+  refresh_b32(L, M, sm, i - sr.ii, i - sr.ii + n, lane);
 }
 
 __device__ __forceinline__ void load_block_m(const Layout& L, const LayoutM& M, const double* __restrict__ g,
@@ -1027,7 +1039,7 @@ __global__ void k_propagate_m(DevSys S, Layout L, LayoutM M, double* __restrict_
     load_block_m(L, M, gblk, sm, lane);
     bool cached = sc[SC_CACHE] != 0.0;
     if (cached) load_mirror_m(M, cblk, sm, lane);
-    bool g_valid = cached;
+    refresh_b32(L, M, sm, 0, L.n_e, lane);
     double weight = 1.0, tau_left = P.tau;
     double bbar = sc[SC_BBAR], Wd = sc[SC_WDIAG], eL = sc[SC_EL], kept = sc[SC_KEPT];
     uint32_t status = (uint32_t)sc[SC_STATUS];
@@ -1056,18 +1068,14 @@ __global__ void k_propagate_m(DevSys S, Layout L, LayoutM M, double* __restrict_
       if (p < 0) {
         status |= ST_STUCK;
       } else {
-        apply_hop_m(S, L, M, gblk, sm, scr.gf, p, P.a, T, lane);
+        apply_hop_m(S, L, M, gblk, sm, p, P.a, T, lane);
         ++moves;
         bool reinv = false;
         if (++since >= P.reinv_period) {
           if (reinvert_m(L, M, gblk, sm, scr.gj, lane)) status |= ST_SINGULAR;
+          refresh_b32(L, M, sm, 0, L.n_e, lane);
           since = 0;
-          g_valid = false;
           reinv = true;
-        }
-        if (!g_valid) {
-          compute_g_m(S, L, M, sm, scr.gf, 0, L.n_e, lane);
-          g_valid = true;
         }
         EvalOut e;
         if (!cached) {

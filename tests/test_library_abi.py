@@ -85,11 +85,13 @@ def test_workspace_sizing_and_validation(lib):
     # 16 x 16 x 4, g 16 x 56, shared-memory mirror); plus the per-warp scratch
     assert 2 * 4096 * 8 * (48 + 128 + 640 + 96 + 5376 + 1536 + 1024 + 896) < nb.value \
         < 2 * 4096 * 8 * (2000 + 12000) + 2368 * 8 * 2000
-    # mixed precision: two cache-block buffers hold the FP32 basis differences
-    # at every hop (56 x 96 floats) and the hop pair terms (16 x 96) per walker
+    # mixed precision: two cache-block buffers hold the FP32 orbital
+    # differences at every hop (96 x 8 floats) and the hop pair terms (16 x 96)
+    # per walker; the per-warp scratch holds the basis differences of a full
+    # evaluation (56 x 96 floats) for each of the 148 x 16 scratch warps
     s, w, p, keep = _structs(W.water_methane(), n_w=4096, precision=1)
     assert lib.lrdmc_workspace_bytes(ctypes.byref(s), ctypes.byref(w), ctypes.byref(p), ctypes.byref(nb)) == 0
-    assert nb.value > 2 * 4096 * 8 * (48 + 128 + 640 + 96) + 2 * 4096 * 4 * (56 * 96 + 16 * 96)
+    assert nb.value > 2 * 4096 * 8 * (48 + 128 + 640 + 96) + 2 * 4096 * 4 * (96 * 8 + 16 * 96) + 2368 * 4 * 56 * 96
     for bad in (dict(a=-1.0), dict(node_rule=5), dict(reinv_period=0), dict(precision=2)):
         s, w, p, keep = _structs(W.h2_sto3g(), **bad)
         assert lib.lrdmc_workspace_bytes(ctypes.byref(s), ctypes.byref(w), ctypes.byref(p),
