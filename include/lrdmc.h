@@ -179,6 +179,23 @@ lrdmc_status lrdmc_branch(lrdmc_handle h);
  * (largest over block lengths 1, 2, 4, ... with >= 8 blocks; NaN if too few). */
 lrdmc_status lrdmc_energy(lrdmc_handle h, double* E, double* err);
 
+/* Lattice-space extrapolation (Sec. II: the LRDMC energy carries an O(a^2)
+ * bias and is extrapolated to a -> 0 from runs at several spacings).  Weighted
+ * least-squares fit of E(a) = sum_{j=0..order} coef[j] a^(2j) to the n points
+ * (a[k], E[k]) with standard errors err[k] (weights 1/err^2), by Householder QR
+ * of the weighted design matrix.  coef[0] is the a -> 0 energy.  Host-only
+ * arrays, no handle and no device work.
+ *   order   1 (E_0 + c a^2) to 3
+ *   coef    out, order + 1 values
+ *   cov     out or NULL, (order + 1)^2 covariance of coef, row-major
+ *           (sqrt(cov[0]) is the standard error of the a -> 0 energy)
+ *   chi2    out or NULL, weighted residual sum of squares
+ * LRDMC_ERR_ARG: NULL inputs, order outside 1..3, n < order + 1, a non-finite
+ * or non-positive a or err, non-finite E, or a rank-deficient design (fewer
+ * than order + 1 distinct spacings). */
+lrdmc_status lrdmc_extrapolate_a(int n, const double* a, const double* E, const double* err, int order,
+                                 double* coef, double* cov, double* chi2);
+
 /* Branching history: up to cap entries of wbar_n, ebar_n, the E_0 used in
  * interval n, the mean and max hops per walker, the number of distinct walkers
  * that survived reconfiguration and the OR of all walkers' status bits before

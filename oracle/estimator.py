@@ -59,3 +59,21 @@ def energy_error(wbar, ebar, p, n_equil=0, min_blocks=8):
         B *= 2
     del num_all, den_all
     return best
+
+
+def extrapolate_a(a, E, err, order=1):
+    """Lattice-space extrapolation (Sec. II: the LRDMC energy has an O(a^2)
+    bias; runs at several a are extrapolated to a -> 0).  Weighted least
+    squares for E(a) = sum_{j<=order} c_j a^(2j) with weights 1/err^2, written
+    as the ordinary least-squares problem of the rows divided by err and solved
+    by numpy's lstsq; the covariance is (X_w^T X_w)^-1.
+    Returns (coef, cov, chi2)."""
+    a = np.asarray(a, dtype=np.float64)
+    E = np.asarray(E, dtype=np.float64)
+    err = np.asarray(err, dtype=np.float64)
+    X = np.stack([a ** (2 * j) for j in range(order + 1)], axis=1) / err[:, None]
+    y = E / err
+    coef, *_ = np.linalg.lstsq(X, y, rcond=None)
+    cov = np.linalg.inv(X.T @ X)
+    chi2 = float(np.sum((y - X @ coef) ** 2))
+    return coef, cov, chi2

@@ -85,6 +85,8 @@ def load_library():
         "lrdmc_interval_timing": [P, c_double_p],
         "lrdmc_load": [P, C.c_char_p],
         "lrdmc_stream": [P, C.POINTER(P)],
+        "lrdmc_extrapolate_a": [C.c_int, c_double_p, c_double_p, c_double_p, C.c_int, c_double_p, c_double_p,
+                                c_double_p],
     }
     for name, args in sigs.items():
         f = getattr(lib, name)
@@ -297,6 +299,27 @@ def reconfigure_indices(w, xi32, stream=None):
     s.synchronize()
     del scratch
     return src, st
+
+
+def extrapolate_a(a, E, err, order=1):
+    """a -> 0 extrapolation of energies at lattice spacings a (standard errors
+    err): weighted least squares E(a) = sum_j coef[j] a^(2j), j <= order.
+    Returns (coef, cov, chi2); coef[0] is the extrapolated energy, sqrt(cov[0, 0])
+    its standard error."""
+    lib = load_library()
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    err = np.ascontiguousarray(err, dtype=np.float64)
+    if not (a.shape == E.shape == err.shape and a.ndim == 1):
+        raise ValueError("a, E and err must be 1-D arrays of one length")
+    coef = np.zeros(order + 1)
+    cov = np.zeros((order + 1, order + 1))
+    chi2 = C.c_double()
+    r = lib.lrdmc_extrapolate_a(len(a), _dptr(a), _dptr(E), _dptr(err), int(order), _dptr(coef), _dptr(cov),
+                                C.byref(chi2))
+    if r != 0:
+        raise LrdmcError(r, "lrdmc_extrapolate_a: invalid points or order")
+    return coef, cov, chi2.value
 
 
 def philox4x32(seed, ctr):

@@ -652,6 +652,83 @@ lrdmc_status lrdmc_energy(lrdmc_handle h, double* E, double* err) {
   return LRDMC_OK;
 }
 
+lrdmc_status lrdmc_extrapolate_a(int n, const double* a, const double* E, const double* err, int order,
+                                 double* coef, double* cov, double* chi2) {
+  if (!a || !E || !err || !coef || order < 1 || order > 3 || n < order + 1) return LRDMC_ERR_ARG;
+  const int m = order + 1;
+  for (int k = 0; k < n; ++k)
+    if (!(std::isfinite(a[k]) && a[k] > 0.0 && std::isfinite(err[k]) && err[k] > 0.0 && std::isfinite(E[k])))
+      return LRDMC_ERR_ARG;
+  // weighted design X[k][j] = a_k^(2j) / err_k and right-hand side E_k / err_k
+  std::vector<double> X((size_t)n * m), y(n);
+  for (int k = 0; k < n; ++k) {
+    double p = 1.0;
+    for (int j = 0; j < m; ++j) {
+      X[(size_t)k * m + j] = p / err[k];
+      p *= a[k] * a[k];
+    }
+    y[k] = E[k] / err[k];
+  }
+  // Householder QR: column j is reflected onto e_j; the same reflections act on y
+  std::vector<double> R((size_t)m * m, 0.0);
+  double scale = 0.0;
+  for (int j = 0; j < m; ++j)
+    for (int k = 0; k < n; ++k) scale = std::max(scale, std::fabs(X[(size_t)k * m + j]));
+  for (int j = 0; j < m; ++j) {
+    double norm = 0.0;
+    for (int k = j; k < n; ++k) norm += X[(size_t)k * m + j] * X[(size_t)k * m + j];
+    norm = std::sqrt(norm);
+    if (!(norm > 1e-13 * scale)) return LRDMC_ERR_ARG;
+    const double alpha = X[(size_t)j * m + j] > 0.0 ? -norm : norm;
+    std::vector<double> v(n, 0.0);
+    for (int k = j; k < n; ++k) v[k] = X[(size_t)k * m + j];
+    v[j] -= alpha;
+    double vv = 0.0;
+    for (int k = j; k < n; ++k) vv += v[k] * v[k];
+    for (int c = j; c < m; ++c) {
+      double d = 0.0;
+      for (int k = j; k < n; ++k) d += v[k] * X[(size_t)k * m + c];
+      const double f = 2.0 * d / vv;
+      for (int k = j; k < n; ++k) X[(size_t)k * m + c] -= f * v[k];
+    }
+    double d = 0.0;
+    for (int k = j; k < n; ++k) d += v[k] * y[k];
+    const double f = 2.0 * d / vv;
+    for (int k = j; k < n; ++k) y[k] -= f * v[k];
+  }
+  for (int j = 0; j < m; ++j)
+    for (int c = j; c < m; ++c) R[(size_t)j * m + c] = X[(size_t)j * m + c];
+  // back substitution R coef = (Q^T y)[0..m)
+  for (int j = m - 1; j >= 0; --j) {
+    double s = y[j];
+    for (int c = j + 1; c < m; ++c) s -= R[(size_t)j * m + c] * coef[c];
+    coef[j] = s / R[(size_t)j * m + j];
+  }
+  if (chi2) {
+    double r2 = 0.0;
+    for (int k = m; k < n; ++k) r2 += y[k] * y[k];
+    *chi2 = r2;
+  }
+  if (cov) {
+    // cov = R^-1 R^-T
+    std::vector<double> Ri((size_t)m * m, 0.0);
+    for (int c = 0; c < m; ++c) {
+      for (int j = m - 1; j >= 0; --j) {
+        double s = (j == c) ? 1.0 : 0.0;
+        for (int q = j + 1; q < m; ++q) s -= R[(size_t)j * m + q] * Ri[(size_t)q * m + c];
+        Ri[(size_t)j * m + c] = s / R[(size_t)j * m + j];
+      }
+    }
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) {
+        double s = 0.0;
+        for (int q = 0; q < m; ++q) s += Ri[(size_t)i * m + q] * Ri[(size_t)j * m + q];
+        cov[(size_t)i * m + j] = s;
+      }
+  }
+  return LRDMC_OK;
+}
+
 lrdmc_status lrdmc_history(lrdmc_handle h, int cap, int* n, double* wbar, double* ebar, double* e0,
                            double* moves_mean, int* moves_max, int* survivors, uint32_t* status_or) {
   if (!h) return LRDMC_ERR_ARG;
