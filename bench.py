@@ -242,10 +242,11 @@ def run_gpu(args, rank, world):
     d2h = 8 * (N_W * (3 * s.n_elec + 6 * s.n_elec + 7))
     e2e_value = world * ws_per_step / (statistics.mean(e2e_ms) / 1e3)
     mixed = run_mixed(args, P, s, x0, lr, flush, rank) if not args.no_mixed else None
+    a_scan = run_a_scan(P) if rank == 0 and not args.no_a_scan else None
     return dict(value=value, t_total=t_total, step_ms=statistics.mean(step_ms), prop_ms=statistics.mean(prop_ms),
                 launches=launches, achieved=achieved, clocks=clk.summary(), conv_rate=conv_rate,
                 conv_moves=conv_moves, tau=tau, e2e=e2e_value, h2d=h2d, d2h=d2h, slots=slots,
-                energy=lr.energy(), mixed=mixed, imbalance=imbalance)
+                energy=lr.energy(), mixed=mixed, imbalance=imbalance, a_scan=a_scan)
 
 
 def aggregate_throughput(t_local, units_local, world, device="cpu"):
@@ -281,6 +282,33 @@ def time_lb_intervals(lr, P, flush, steps, warmup):
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
     return statistics.mean(ms)
+
+
+def run_a_scan(P):
+    """Lattice-space extrapolation: load-balanced LRDMC of the hydrogen atom
+    (Slater guiding function exp(-0.8 r), walkers on the lattice a (Z^3 + 1/2))
+    at four spacings, fitted to E_0 + c_2 a^2 + c_4 a^4; the continuum value is
+    -1/2 Ha.  Reports the energies, the fit and the wall time of the scan."""
+    import torch
+    import workloads as W
+    s = W.hydrogen_atom_sto(0.8)
+    a_list, E_list, err_list = [0.3, 0.4, 0.5, 0.6], [], []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for a in a_list:
+        lr = P.Lrdmc(s, W.lattice_walkers(2048, a, seed=4, spread=3), a, seed=11, p_gbar=20, n_equil=20)
+        for _ in range(140):
+            lr.propagate(P.LOAD_BALANCED, n_proj=15)
+            lr.branch()
+        E, err = lr.energy()
+        E_list.append(E)
+        err_list.append(err)
+        del lr
+    wall = time.perf_counter() - t0
+    coef, cov, chi2 = P.extrapolate_a(a_list, E_list, err_list, 2)
+    return {"system": "H atom, Slater guide exp(-0.8 r), 2048 walkers, 140 intervals x 15 hops per spacing",
+            "a": a_list, "E": E_list, "err": err_list, "E0": float(coef[0]), "E0_err": float(np.sqrt(cov[0, 0])),
+            "chi2": chi2, "exact_continuum": -0.5, "wall_s": wall}
 
 
 def run_mixed(args, P, s, x0, lr64, flush, rank):
@@ -323,6 +351,7 @@ def main():
     ap.add_argument("--impl", default="lrdmc", choices=["lrdmc", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-a-scan", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -385,6 +414,7 @@ def main():
             "e2e": {"value": res["e2e"], "unit": "walker-steps/s", "h2d_bytes_per_step": res["h2d"],
                     "d2h_bytes_per_step": res["d2h"]},
             "mixed": dict(res["mixed"], speedup_vs_fp64=res["mixed"]["value"] / res["value"]) if res["mixed"] else None,
+            "a_scan": res["a_scan"],
             "gpu_launches": res["launches"],
             "clocks": res["clocks"],
             "energy": {"E": res["energy"][0], "err": res["energy"][1]},
