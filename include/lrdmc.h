@@ -125,9 +125,12 @@ typedef struct {
  *   p_gbar       length p of the global population factor (Sec. II.A)
  *   n_equil      branchings discarded by lrdmc_energy
  *   precision    0 = FP64 throughout; 1 = mixed: FP32 evaluation of every hop
- *                ratio (as r - 1), Jastrow, basis, Sherman-Morrison and caches,
- *                FP64 positions, weights, b_bar / W / e_L accumulators and
- *                Gauss-Jordan re-inversion every reinv_period hops            */
+ *                ratio (as r - 1: basis and orbital differences, Jastrow
+ *                differences) and of the orbital derivative cache; FP64
+ *                positions, orbital values (rows of A), B = A^-1 with its
+ *                Sherman-Morrison updates and Gauss-Jordan re-inversion every
+ *                reinv_period hops, determinant derivatives, weights and the
+ *                b_bar / W / e_L accumulators                                  */
 typedef struct {
     double a;
     int n_w;
@@ -310,6 +313,70 @@ lrdmc_status lrdmc_stream(lrdmc_handle h, void** stream);
 
 const char* lrdmc_last_error(lrdmc_handle h);
 const char* lrdmc_status_string(lrdmc_status s);
+
+/* ------------------------------------------------------------------ batches
+ * Several independent systems (each with its own walkers, E_0 and history, as
+ * in Sec. II) propagated by ONE persistent kernel launch per interval and
+ * branched by one batched launch of each branching kernel.  Each system k is
+ * described exactly as for lrdmc_create (sys[k], wf[k], prm[k] with its own
+ * n_w and seed, x0[k] a host array n_w x N_e x 3) and owns an ordinary handle
+ * (lrdmc_batch_handle) for readback, energies, history and checkpoints; the
+ * batch owns those handles.  All systems must use the same precision and the
+ * same CUDA device; the stream is shared.  A system's walkers follow exactly
+ * the trajectory they would follow in their own handle: the batch changes only
+ * which warp runs which walker. */
+typedef struct lrdmc_batch_s* lrdmc_batch;
+
+/* Create the batch (allocates each system's workspace with cudaMalloc).
+ * LRDMC_ERR_ARG for n_sys < 1, NULL arrays or mixed precisions; otherwise the
+ * status of the first system that fails to create (its message is kept). */
+lrdmc_status lrdmc_batch_create(int n_sys, const lrdmc_system* sys, const lrdmc_trial_wf* wf,
+                                const lrdmc_params* prm, const double* const* x0, void* stream, lrdmc_batch* out);
+lrdmc_status lrdmc_batch_destroy(lrdmc_batch b);
+
+/* The handle of system k (owned by the batch: do not destroy it; its
+ * propagate/branch calls remain valid and act on that system alone). */
+lrdmc_status lrdmc_batch_handle(lrdmc_batch b, int k, lrdmc_handle* h);
+
+/* One interval for every walker of every system: a single launch of the
+ * persistent batched kernel (sch as for lrdmc_propagate; the randomised
+ * lattice is refused with LRDMC_ERR_UNSUPPORTED). */
+lrdmc_status lrdmc_batch_propagate(lrdmc_batch b, const lrdmc_schedule* sch);
+
+/* Branch every system: one launch each of the batched reduction, comb and
+ * gather kernels and one readback of all systems' statistics; each system's
+ * history and E_0 are updated as by lrdmc_branch.  A system whose weights are
+ * invalid keeps its population and history and makes the call return
+ * LRDMC_ERR_NONFINITE after the other systems are branched. */
+lrdmc_status lrdmc_batch_branch(lrdmc_batch b);
+
+/* Order in which the persistent kernel hands out walkers: 0 = system by system
+ * in creation order, 1 (default) = systems by decreasing estimated cost per
+ * walker (N_e (N_bf + N_nuc + N_e)), the longest jobs first. */
+lrdmc_status lrdmc_batch_set_order(lrdmc_batch b, int policy);
+
+/* Autotuner of the launch shape.  The batched kernel runs persistent CTAs; a
+ * CTA takes an item (system k, up to c_k consecutive walkers), gives each warp
+ * one walker and splits its shared memory into c_k regions of system k's
+ * per-walker size, so c_k follows the CTA's shared-memory size.  Candidates:
+ * 1, 2, 3 or 4 CTAs per SM (each CTA with 1/1, 1/2, 1/3, 1/4 of the opt-in
+ * shared memory; candidates where some system does not fit are skipped).  The
+ * tuner times one interval of schedule sch with each candidate, restoring every
+ * walker and cache after each trial, and keeps the fastest.  times_ms (may be
+ * NULL) receives the 4 timings (0 where the candidate does not fit);
+ * *best_ctas (may be NULL) the chosen CTAs per SM. */
+lrdmc_status lrdmc_batch_tune(lrdmc_batch b, const lrdmc_schedule* sch, double times_ms[4], int* best_ctas);
+
+/* Timing of the last batched interval over all systems (requires
+ * lrdmc_batch_set_timing(b, 1) before it): out[0] span ms, out[1] mean and
+ * out[2] max walker ms, out[3] busy fraction = total walker time / (span x
+ * resident warps), out[4] resident warps, out[5] walkers. */
+lrdmc_status lrdmc_batch_set_timing(lrdmc_batch b, int enable);
+lrdmc_status lrdmc_batch_timing(lrdmc_batch b, double out[6]);
+
+/* Kernels launched by the batch's own entry points. */
+lrdmc_status lrdmc_batch_launch_count(lrdmc_batch b, int64_t* n);
+const char* lrdmc_batch_last_error(lrdmc_batch b);
 
 #ifdef __cplusplus
 }

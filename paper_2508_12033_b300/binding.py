@@ -87,6 +87,17 @@ def load_library():
         "lrdmc_stream": [P, C.POINTER(P)],
         "lrdmc_extrapolate_a": [C.c_int, c_double_p, c_double_p, c_double_p, C.c_int, c_double_p, c_double_p,
                                 c_double_p],
+        "lrdmc_batch_create": [C.c_int, C.POINTER(_System), C.POINTER(_TrialWF), C.POINTER(_Params),
+                               C.POINTER(c_double_p), P, C.POINTER(P)],
+        "lrdmc_batch_destroy": [P],
+        "lrdmc_batch_handle": [P, C.c_int, C.POINTER(P)],
+        "lrdmc_batch_propagate": [P, C.POINTER(_Schedule)],
+        "lrdmc_batch_branch": [P],
+        "lrdmc_batch_set_order": [P, C.c_int],
+        "lrdmc_batch_tune": [P, C.POINTER(_Schedule), c_double_p, c_int_p],
+        "lrdmc_batch_set_timing": [P, C.c_int],
+        "lrdmc_batch_timing": [P, c_double_p],
+        "lrdmc_batch_launch_count": [P, C.POINTER(C.c_int64)],
     }
     for name, args in sigs.items():
         f = getattr(lib, name)
@@ -98,6 +109,8 @@ def load_library():
     lib.lrdmc_philox4x32.restype = None
     lib.lrdmc_last_error.argtypes = [P]
     lib.lrdmc_last_error.restype = C.c_char_p
+    lib.lrdmc_batch_last_error.argtypes = [P]
+    lib.lrdmc_batch_last_error.restype = C.c_char_p
     _LIB = lib
     return lib
 
@@ -175,8 +188,25 @@ class Lrdmc:
 
     def close(self):
         if getattr(self, "_h", None):
-            self.lib.lrdmc_destroy(self._h)
+            if getattr(self, "_owned", True):
+                self.lib.lrdmc_destroy(self._h)
             self._h = None
+
+    @classmethod
+    def _view(cls, lib, h, n_w, n_e, device, stream, owner):
+        """A non-owning view of a handle that belongs to a batch."""
+        import torch
+        obj = cls.__new__(cls)
+        obj._torch = torch
+        obj.lib = lib
+        obj._h = h
+        obj.n_w, obj.n_e = int(n_w), int(n_e)
+        obj.device = device
+        obj.stream = stream
+        obj._owned = False
+        obj._owner = owner
+        obj._keep = {}
+        return obj
 
     def __del__(self):
         try:
@@ -299,6 +329,119 @@ def reconfigure_indices(w, xi32, stream=None):
     s.synchronize()
     del scratch
     return src, st
+
+
+class LrdmcBatch:
+    """Several independent LRDMC populations propagated by one persistent
+    kernel launch per interval and branched by batched launches.
+
+    ``systems``: list of system objects (as for ``Lrdmc``); ``x0s``: list of
+    initial positions (n_w_k, n_e_k, 3); ``seeds``: one seed per system.
+    ``handle(k)`` gives an ``Lrdmc`` view of system k (readback, energy,
+    history; owned by the batch)."""
+
+    def __init__(self, systems, x0s, a, seeds, node_rule=0, reinv_period=100, p_gbar=10, n_equil=0,
+                 device=None, stream=None, precision=0):
+        import torch
+        lib = load_library()
+        self.lib = lib
+        self.device = torch.device(device if device is not None else "cuda")
+        n = len(systems)
+        assert len(x0s) == n and len(seeds) == n
+        keep = []
+
+        def d(v):
+            arr = np.ascontiguousarray(v, dtype=np.float64).reshape(-1)
+            keep.append(arr)
+            return _dptr(arr)
+
+        def i(v):
+            arr = np.ascontiguousarray(v, dtype=np.int32).reshape(-1)
+            keep.append(arr)
+            return _iptr(arr)
+
+        sys_arr = (_System * n)()
+        wf_arr = (_TrialWF * n)()
+        prm_arr = (_Params * n)()
+        x_ptrs = (c_double_p * n)()
+        self._shapes = []
+        for k, (sy, x0) in enumerate(zip(systems, x0s)):
+            x0 = np.ascontiguousarray(x0, dtype=np.float64)
+            keep.append(x0)
+            self._shapes.append((int(x0.shape[0]), int(x0.shape[1])))
+            sys_arr[k] = _System(len(sy.Z), d(sy.R), d(sy.Z), i(sy.pot_kind), d(sy.r_c), int(sy.n_up), int(sy.n_dn))
+            wf_arr[k] = _TrialWF(len(sy.shell_l), i(sy.shell_atom), i(sy.shell_l), i(sy.shell_nprim), d(sy.exps),
+                                 d(sy.coefs), int(sy.C.shape[0]), d(sy.C), float(sy.j2_anti), float(sy.j2_par),
+                                 float(sy.j2_b), d(sy.j1_A), d(sy.j1_B))
+            prm_arr[k] = _Params(float(a), int(x0.shape[0]), int(seeds[k]) & (2**64 - 1), int(node_rule),
+                                 int(reinv_period), int(p_gbar), int(n_equil), int(precision))
+            x_ptrs[k] = _dptr(x0)
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            b = C.c_void_p()
+            st = lib.lrdmc_batch_create(n, sys_arr, wf_arr, prm_arr, x_ptrs, C.c_void_p(self.stream.cuda_stream),
+                                        C.byref(b))
+        self._b = b
+        self._keep = keep
+        self._check(st)
+        self.handles = []
+        for k in range(n):
+            h = C.c_void_p()
+            self._check(lib.lrdmc_batch_handle(self._b, k, C.byref(h)))
+            self.handles.append(Lrdmc._view(lib, h, self._shapes[k][0], self._shapes[k][1], self.device,
+                                            self.stream, self))
+
+    def _check(self, status):
+        if status != 0:
+            msg = self.lib.lrdmc_batch_last_error(self._b).decode() if self._b else ""
+            raise LrdmcError(status, msg)
+
+    def close(self):
+        if getattr(self, "_b", None):
+            for v in getattr(self, "handles", []):
+                v._h = None
+            self.lib.lrdmc_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def handle(self, k):
+        return self.handles[k]
+
+    def propagate(self, kind=LOAD_BALANCED, n_proj=20, tau=0.0, max_moves=100000):
+        s = _Schedule(int(kind), int(n_proj), float(tau), int(max_moves), 0)
+        self._check(self.lib.lrdmc_batch_propagate(self._b, C.byref(s)))
+
+    def branch(self):
+        self._check(self.lib.lrdmc_batch_branch(self._b))
+
+    def set_order(self, policy):
+        self._check(self.lib.lrdmc_batch_set_order(self._b, int(policy)))
+
+    def tune(self, kind=LOAD_BALANCED, n_proj=20, tau=0.0, max_moves=100000):
+        s = _Schedule(int(kind), int(n_proj), float(tau), int(max_moves), 0)
+        times = np.zeros(4)
+        best = C.c_int()
+        self._check(self.lib.lrdmc_batch_tune(self._b, C.byref(s), _dptr(times), C.byref(best)))
+        return best.value, dict(zip((1, 2, 3, 4), times))
+
+    def set_timing(self, enable=True):
+        self._check(self.lib.lrdmc_batch_set_timing(self._b, 1 if enable else 0))
+
+    def timing(self):
+        out = np.zeros(6)
+        self._check(self.lib.lrdmc_batch_timing(self._b, _dptr(out)))
+        return dict(span_ms=out[0], walker_ms_mean=out[1], walker_ms_max=out[2], busy_fraction=out[3],
+                    resident_warps=int(out[4]), walkers=int(out[5]))
+
+    def launch_count(self):
+        v = C.c_int64()
+        self._check(self.lib.lrdmc_batch_launch_count(self._b, C.byref(v)))
+        return v.value
 
 
 def extrapolate_a(a, E, err, order=1):

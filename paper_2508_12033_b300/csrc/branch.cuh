@@ -26,9 +26,8 @@ enum BranchStat : int {
 
 // One CTA of BR_THREADS threads.  Each thread accumulates a strided subset in
 // index order, then the partials are combined by a fixed tree.
-__global__ void __launch_bounds__(BR_THREADS) k_branch_reduce(Layout L, const double* __restrict__ state,
-                                                              int n_w, double E0, int lb,
-                                                              double* __restrict__ out) {
+__device__ void branch_reduce_body(const Layout& L, const double* __restrict__ state, int n_w, double E0, int lb,
+                                   double* __restrict__ out) {
   __shared__ double s_buf[BR_THREADS];
   __shared__ unsigned s_or[BR_THREADS];
   const int t = threadIdx.x;
@@ -74,14 +73,17 @@ __global__ void __launch_bounds__(BR_THREADS) k_branch_reduce(Layout L, const do
   }
 }
 
+__global__ void __launch_bounds__(BR_THREADS) k_branch_reduce(Layout L, const double* __restrict__ state,
+                                                              int n_w, double E0, int lb,
+                                                              double* __restrict__ out) {
+  branch_reduce_body(L, state, n_w, E0, lb, out);
+}
+
 // Integer comb.  Weights are read as w[a * w_stride]; Q is uint64 scratch of
 // n entries.  status[0] = 0 ok / 1 invalid weights; status[1] = survivors.
-__global__ void __launch_bounds__(BR_THREADS) k_reconfigure(const double* __restrict__ w, int w_stride,
-                                                            int n, uint32_t xi32,
-                                                            unsigned long long* __restrict__ Q,
-                                                            int32_t* __restrict__ src,
-                                                            int32_t* __restrict__ status,
-                                                            double* __restrict__ stats_out) {
+__device__ void reconfigure_body(const double* __restrict__ w, int w_stride, int n, uint32_t xi32,
+                                 unsigned long long* __restrict__ Q, int32_t* __restrict__ src,
+                                 int32_t* __restrict__ status, double* __restrict__ stats_out) {
   __shared__ double s_max[BR_THREADS];
   __shared__ int s_bad[BR_THREADS];
   __shared__ unsigned long long s_sum[BR_THREADS];
@@ -163,17 +165,27 @@ __global__ void __launch_bounds__(BR_THREADS) k_reconfigure(const double* __rest
   }
 }
 
+__global__ void __launch_bounds__(BR_THREADS) k_reconfigure(const double* __restrict__ w, int w_stride,
+                                                            int n, uint32_t xi32,
+                                                            unsigned long long* __restrict__ Q,
+                                                            int32_t* __restrict__ src,
+                                                            int32_t* __restrict__ status,
+                                                            double* __restrict__ stats_out) {
+  reconfigure_body(w, w_stride, n, xi32, Q, src, status, stats_out);
+}
+
 // new[alpha] = old[src[alpha]], weight reset to 1; skipped when status[0] != 0.
-// The walker's cache block (when the layout has one) moves with it.
-__global__ void k_gather(Layout L, const double* __restrict__ old_state, double* __restrict__ new_state,
-                         const double* __restrict__ old_cache, double* __restrict__ new_cache,
-                         const int32_t* __restrict__ src, int n_w, const int32_t* __restrict__ status) {
+// The walker's cache block (when the layout has one) moves with it.  Threads
+// tid, tid + nth, ... of the launch take the copies.
+__device__ void gather_body(const Layout& L, const double* __restrict__ old_state, double* __restrict__ new_state,
+                            const double* __restrict__ old_cache, double* __restrict__ new_cache,
+                            const int32_t* __restrict__ src, int n_w, const int32_t* __restrict__ status,
+                            size_t tid, size_t nth) {
   if (status[0] != 0) return;
   const int per = L.g_stride / 2;   // double2 per walker block (stride is a multiple of 16 doubles)
   const double2* o2 = reinterpret_cast<const double2*>(old_state);
   double2* n2 = reinterpret_cast<double2*>(new_state);
   const size_t total = (size_t)n_w * per;
-  const size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x, nth = (size_t)gridDim.x * blockDim.x;
   for (size_t idx = tid; idx < total; idx += nth) {
     const int a = (int)(idx / per);
     const int o = (int)(idx - (size_t)a * per);
@@ -190,6 +202,48 @@ __global__ void k_gather(Layout L, const double* __restrict__ old_state, double*
     const int a = (int)(idx / cper);
     nc[idx] = oc[(size_t)src[a] * cper + (idx - (size_t)a * cper)];
   }
+}
+
+__global__ void k_gather(Layout L, const double* __restrict__ old_state, double* __restrict__ new_state,
+                         const double* __restrict__ old_cache, double* __restrict__ new_cache,
+                         const int32_t* __restrict__ src, int n_w, const int32_t* __restrict__ status) {
+  gather_body(L, old_state, new_state, old_cache, new_cache, src, n_w, status,
+              blockIdx.x * (size_t)blockDim.x + threadIdx.x, (size_t)gridDim.x * blockDim.x);
+}
+
+// ------------------------------------------------------------ batches
+// One system of a batch at branching time.
+struct BranchJob {
+  Layout L;
+  const double* state;
+  double* alt;
+  const double* cache;
+  double* cache_alt;
+  int n_w, lb;
+  double E0;
+  uint32_t xi32;
+  unsigned long long* Q;
+  int32_t* src;
+  int32_t* status;   // [2] per job
+  double* stats;     // [BS_COUNT] per job
+};
+
+// Block b reduces, or reconfigures, system b; the gather takes blockIdx.y as
+// the system.
+__global__ void __launch_bounds__(BR_THREADS) k_branch_reduce_batch(const BranchJob* __restrict__ jobs) {
+  const BranchJob& J = jobs[blockIdx.x];
+  branch_reduce_body(J.L, J.state, J.n_w, J.E0, J.lb, J.stats);
+}
+
+__global__ void __launch_bounds__(BR_THREADS) k_reconfigure_batch(const BranchJob* __restrict__ jobs) {
+  const BranchJob& J = jobs[blockIdx.x];
+  reconfigure_body(J.state + J.L.g_sc + SC_W, J.L.g_stride, J.n_w, J.xi32, J.Q, J.src, J.status, J.stats);
+}
+
+__global__ void k_gather_batch(const BranchJob* __restrict__ jobs) {
+  const BranchJob& J = jobs[blockIdx.y];
+  gather_body(J.L, J.state, J.alt, J.cache, J.cache_alt, J.src, J.n_w, J.status,
+              blockIdx.x * (size_t)blockDim.x + threadIdx.x, (size_t)gridDim.x * blockDim.x);
 }
 
 }  // namespace lrdmc

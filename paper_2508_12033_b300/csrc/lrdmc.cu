@@ -11,6 +11,7 @@
 #include <string>
 #include <vector>
 
+#include "batch.cuh"
 #include "branch.cuh"
 #include "common.cuh"
 #include "walker.cuh"
@@ -348,6 +349,223 @@ static lrdmc_status extract(lrdmc_handle h, std::vector<double>& buf) {
   return LRDMC_OK;
 }
 
+// Host side of a branching after the statistics hs of the handle's population
+// are read back: swap in the gathered population, extend the history, advance
+// the interval and (load-balanced) update E_0.
+static lrdmc_status finish_branch(lrdmc_handle h, const double* hs) {
+  const Plan& P = h->P;
+  if (hs[BS_BAD] != 0.0)
+    return fail(h, LRDMC_ERR_NONFINITE, "weights negative, non-finite or all zero: population unchanged");
+  const int lb = h->last_kind == LRDMC_LOAD_BALANCED;
+  std::swap(h->state, h->alt);
+  std::swap(h->cache, h->cache_alt);
+  h->wbar.push_back(hs[BS_SUMW] / (double)P.n_w);
+  h->ebar.push_back(hs[BS_SUMFE] / hs[BS_SUMF]);
+  h->e0h.push_back(h->E0);
+  h->mmean.push_back(hs[BS_MOVES] / (double)P.n_w);
+  h->mmax.push_back((int)hs[BS_MOVESMAX]);
+  h->surv.push_back((int)hs[BS_SURV]);
+  h->stor.push_back((uint32_t)hs[BS_STATUS]);
+  ++h->interval;
+  if (lb) h->E0 = estimate(h->wbar, h->ebar, h->prm.p_gbar, 0, nullptr);
+  return LRDMC_OK;
+}
+
+// Step parameters of one interval of handle h under schedule sch.
+static StepParams step_params(lrdmc_handle h, const lrdmc_schedule* sch) {
+  StepParams sp;
+  sp.kind = sch->kind;
+  sp.n_proj = sch->n_proj;
+  sp.tau = sch->tau;
+  sp.max_moves = sch->max_moves;
+  sp.E0 = h->E0;
+  sp.seed = h->prm.seed;
+  sp.interval = h->interval;
+  sp.a = h->prm.a;
+  sp.node_rule = h->prm.node_rule;
+  sp.reinv_period = h->prm.reinv_period;
+  sp.stamps = h->timing ? h->stamps : nullptr;
+  sp.rotate = sch->rotate != 0;
+  return sp;
+}
+
+// Schedule arguments shared by the single and batched entry points.
+static const char* check_schedule(const lrdmc_schedule* sch) {
+  if (!sch) return "NULL schedule";
+  if (sch->kind != LRDMC_CONVENTIONAL && sch->kind != LRDMC_LOAD_BALANCED) return "schedule kind must be 0 or 1";
+  if (sch->kind == LRDMC_LOAD_BALANCED && sch->n_proj < 0) return "n_proj < 0";
+  if (sch->kind == LRDMC_CONVENTIONAL && (!(sch->tau > 0.0) || sch->max_moves < 1))
+    return "conventional schedule needs tau > 0 and max_moves >= 1";
+  return nullptr;
+}
+
+// ------------------------------------------------------------------ batches
+struct lrdmc_batch_s {
+  std::vector<lrdmc_handle> h;
+  int precision = 0, device = 0, num_sms = 1, smem_optin = 0;
+  int max_threads = 1024;        // of the batched kernel (its register use)
+  cudaStream_t stream = nullptr;
+  int policy = 1;
+  size_t cta_dyn = 0;            // dynamic shared bytes per CTA of the current launch shape
+  int wmax = 1, grid = 1;        // warps per CTA, CTAs
+  std::vector<int> fit;          // walkers per item, per system, for the current shape
+  size_t scratch_per_warp = 0;   // global scratch doubles per warp
+  size_t scratch_warps = 0;      // warps the scratch is sized for
+  int total = 0, n_items = 0;    // walkers over all systems; items of the current shape
+  PropJob* d_jobs = nullptr;
+  BranchJob* d_bjobs = nullptr;
+  int4* d_items = nullptr;
+  unsigned* d_counter = nullptr;
+  double* d_scratch = nullptr;
+  double* d_stats = nullptr;     // [n][BS_COUNT]
+  int32_t* d_status = nullptr;   // [n][2]
+  std::vector<PropJob> jobs;
+  std::vector<BranchJob> bjobs;
+  bool timing = false;
+  int64_t launches = 0;
+  std::string err;
+};
+
+static lrdmc_status bfail(lrdmc_batch b, lrdmc_status s, const std::string& msg) {
+  if (b) b->err = msg;
+  return s;
+}
+
+#define BCK(b, call)                                                   \
+  do {                                                                 \
+    cudaError_t e_ = (call);                                           \
+    if (e_ != cudaSuccess) {                                           \
+      char buf_[512];                                                  \
+      snprintf(buf_, sizeof buf_, "%s: %s", #call, cudaGetErrorString(e_)); \
+      return bfail(b, LRDMC_ERR_CUDA, buf_);                           \
+    }                                                                  \
+  } while (0)
+
+#define BLAUNCHED(b)                                                   \
+  do {                                                                 \
+    ++(b)->launches;                                                   \
+    cudaError_t e_ = cudaGetLastError();                               \
+    if (e_ != cudaSuccess) return bfail(b, LRDMC_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+// Shared doubles one walker of handle h needs in a batched CTA.
+static int batch_region(lrdmc_handle h) {
+  const Plan& P = h->P;
+  return round_up(P.precision == 0 ? P.L.s_stride : (P.M.stride + 1) / 2, 2);
+}
+
+// Launch shape for cta_dyn dynamic shared bytes per CTA: walkers per item of
+// every system, warps per CTA and CTAs per SM.  *ok = false when a system
+// does not fit or the kernel does not fit on an SM.
+static lrdmc_status batch_shape(lrdmc_batch b, size_t cta_dyn, bool* ok, std::vector<int>& fit, int* wmax,
+                                int* bps) {
+  *ok = false;
+  const long avail = (long)cta_dyn / (long)sizeof(double) - EXP_TAB - JOB_WORDS;
+  const int cap = std::max(1, b->max_threads / 32);
+  fit.assign(b->h.size(), 0);
+  int w = 0;
+  for (size_t k = 0; k < b->h.size(); ++k) {
+    const long n = avail / batch_region(b->h[k]);
+    if (n < 1) return LRDMC_OK;
+    fit[k] = (int)std::min<long>(std::min<long>(n, cap), b->h[k]->P.n_w);
+    w = std::max(w, fit[k]);
+  }
+  *wmax = w;
+  if (b->precision == 0)
+    BCK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_propagate_batch<0>, w * 32, cta_dyn));
+  else
+    BCK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_propagate_batch<1>, w * 32, cta_dyn));
+  *ok = *bps >= 1;
+  return LRDMC_OK;
+}
+
+// Work items (system, first walker, count) in the order of the current policy.
+static lrdmc_status batch_items(lrdmc_batch b) {
+  const int n = (int)b->h.size();
+  std::vector<int> order(n);
+  for (int k = 0; k < n; ++k) order[k] = k;
+  if (b->policy == 1) {
+    auto cost = [&](int k) {
+      const Plan& P = b->h[k]->P;
+      return (double)P.n_e * (double)(P.n_bf + P.n_nuc + P.n_e);
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost(x) > cost(y); });
+  }
+  std::vector<int4> items;
+  for (int k : order)
+    for (int w0 = 0; w0 < b->h[k]->P.n_w; w0 += b->fit[k])
+      items.push_back(make_int4(k, w0, std::min(b->fit[k], b->h[k]->P.n_w - w0), 0));
+  b->n_items = (int)items.size();
+  BCK(b, cudaMemcpyAsync(b->d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, b->stream));
+  BCK(b, cudaStreamSynchronize(b->stream));
+  return LRDMC_OK;
+}
+
+// Adopt the launch shape for cta_dyn bytes (it must fit) and rebuild the items.
+static lrdmc_status batch_use(lrdmc_batch b, size_t cta_dyn) {
+  bool ok = false;
+  std::vector<int> fit;
+  int w = 0, bps = 0;
+  lrdmc_status st = batch_shape(b, cta_dyn, &ok, fit, &w, &bps);
+  if (st != LRDMC_OK) return st;
+  if (!ok) return bfail(b, LRDMC_ERR_UNSUPPORTED, "batched launch shape does not fit");
+  const int grid = std::max(1, std::min(bps * b->num_sms, (int)(b->scratch_warps / w)));
+  b->cta_dyn = cta_dyn;
+  b->fit = fit;
+  b->wmax = w;
+  b->grid = grid;
+  return batch_items(b);
+}
+
+// Candidate shapes: the CTA's dynamic shared memory is the opt-in maximum or
+// its half, third or quarter (one to four CTAs per SM).
+static size_t batch_candidate(lrdmc_batch b, int c) {
+  const size_t top = (size_t)b->smem_optin - 1024;   // room for the static shared word
+  return top / (size_t)(c + 1) / 16 * 16;
+}
+
+static void batch_free(lrdmc_batch b) {
+  cudaFree(b->d_jobs);
+  cudaFree(b->d_bjobs);
+  cudaFree(b->d_items);
+  cudaFree(b->d_counter);
+  cudaFree(b->d_scratch);
+  cudaFree(b->d_stats);
+  cudaFree(b->d_status);
+  for (lrdmc_handle h : b->h) lrdmc_destroy(h);
+  b->h.clear();
+}
+
+// One batched interval with the current launch shape (no argument checks).
+static lrdmc_status batch_launch(lrdmc_batch b, const lrdmc_schedule* sch) {
+  const int n = (int)b->h.size();
+  for (int k = 0; k < n; ++k) {
+    lrdmc_handle h = b->h[k];
+    PropJob& J = b->jobs[k];
+    J.S = h->S;
+    J.L = h->P.L;
+    J.M = h->P.M;
+    J.P = step_params(h, sch);
+    J.state = h->state;
+    J.cache = h->cache;
+    J.n_w = h->P.n_w;
+    J.region = batch_region(h);
+    h->last_kind = sch->kind;
+  }
+  BCK(b, cudaMemcpyAsync(b->d_jobs, b->jobs.data(), sizeof(PropJob) * n, cudaMemcpyHostToDevice, b->stream));
+  BCK(b, cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned), b->stream));
+  if (b->precision == 0)
+    k_propagate_batch<0><<<b->grid, b->wmax * 32, b->cta_dyn, b->stream>>>(b->d_jobs, b->d_items, b->n_items,
+                                                                           b->d_counter, b->d_scratch,
+                                                                           b->scratch_per_warp);
+  else
+    k_propagate_batch<1><<<b->grid, b->wmax * 32, b->cta_dyn, b->stream>>>(b->d_jobs, b->d_items, b->n_items,
+                                                                           b->d_counter, b->d_scratch,
+                                                                           b->scratch_per_warp);
+  BLAUNCHED(b);
+  return LRDMC_OK;
+}
+
 extern "C" {
 
 const char* lrdmc_status_string(lrdmc_status s) {
@@ -573,28 +791,11 @@ lrdmc_status lrdmc_destroy(lrdmc_handle h) {
 
 lrdmc_status lrdmc_propagate(lrdmc_handle h, const lrdmc_schedule* sch) {
   if (!h || !h->state) return LRDMC_ERR_ARG;
-  if (!sch) return fail(h, LRDMC_ERR_ARG, "NULL schedule");
-  if (sch->kind != LRDMC_CONVENTIONAL && sch->kind != LRDMC_LOAD_BALANCED)
-    return fail(h, LRDMC_ERR_ARG, "schedule kind must be 0 or 1");
-  if (sch->kind == LRDMC_LOAD_BALANCED && sch->n_proj < 0) return fail(h, LRDMC_ERR_ARG, "n_proj < 0");
-  if (sch->kind == LRDMC_CONVENTIONAL && (!(sch->tau > 0.0) || sch->max_moves < 1))
-    return fail(h, LRDMC_ERR_ARG, "conventional schedule needs tau > 0 and max_moves >= 1");
+  if (const char* bad = check_schedule(sch)) return fail(h, LRDMC_ERR_ARG, bad);
   if (sch->rotate && h->P.precision != 0)
     return fail(h, LRDMC_ERR_UNSUPPORTED, "the randomised lattice is implemented for precision 0 only");
   DeviceGuard g(h->device);
-  StepParams sp;
-  sp.kind = sch->kind;
-  sp.n_proj = sch->n_proj;
-  sp.tau = sch->tau;
-  sp.max_moves = sch->max_moves;
-  sp.E0 = h->E0;
-  sp.seed = h->prm.seed;
-  sp.interval = h->interval;
-  sp.a = h->prm.a;
-  sp.node_rule = h->prm.node_rule;
-  sp.reinv_period = h->prm.reinv_period;
-  sp.stamps = h->timing ? h->stamps : nullptr;
-  sp.rotate = sch->rotate != 0;
+  const StepParams sp = step_params(h, sch);
   const int smem = smem_bytes(h);
   if (h->P.precision == 0)
     if (sp.rotate)
@@ -630,20 +831,7 @@ lrdmc_status lrdmc_branch(lrdmc_handle h) {
   double hs[BS_COUNT];
   CK(h, cudaMemcpyAsync(hs, h->stats, sizeof hs, cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
-  if (hs[BS_BAD] != 0.0)
-    return fail(h, LRDMC_ERR_NONFINITE, "weights negative, non-finite or all zero: population unchanged");
-  std::swap(h->state, h->alt);
-  std::swap(h->cache, h->cache_alt);
-  h->wbar.push_back(hs[BS_SUMW] / (double)P.n_w);
-  h->ebar.push_back(hs[BS_SUMFE] / hs[BS_SUMF]);
-  h->e0h.push_back(h->E0);
-  h->mmean.push_back(hs[BS_MOVES] / (double)P.n_w);
-  h->mmax.push_back((int)hs[BS_MOVESMAX]);
-  h->surv.push_back((int)hs[BS_SURV]);
-  h->stor.push_back((uint32_t)hs[BS_STATUS]);
-  ++h->interval;
-  if (lb) h->E0 = estimate(h->wbar, h->ebar, h->prm.p_gbar, 0, nullptr);
-  return LRDMC_OK;
+  return finish_branch(h, hs);
 }
 
 lrdmc_status lrdmc_energy(lrdmc_handle h, double* E, double* err) {
@@ -1044,5 +1232,252 @@ lrdmc_status lrdmc_stream(lrdmc_handle h, void** stream) {
   *stream = (void*)h->stream;
   return LRDMC_OK;
 }
+
+lrdmc_status lrdmc_batch_create(int n_sys, const lrdmc_system* sys, const lrdmc_trial_wf* wf,
+                                const lrdmc_params* prm, const double* const* x0, void* stream, lrdmc_batch* out) {
+  if (!out) return LRDMC_ERR_ARG;
+  *out = nullptr;
+  if (n_sys < 1 || !sys || !wf || !prm || !x0) return LRDMC_ERR_ARG;
+  for (int k = 1; k < n_sys; ++k)
+    if (prm[k].precision != prm[0].precision) return LRDMC_ERR_ARG;
+  lrdmc_batch b = new lrdmc_batch_s();
+  *out = b;   // kept on failure so that the caller can read the message; destroy frees it
+  b->stream = (cudaStream_t)stream;
+  b->precision = prm[0].precision;
+  BCK(b, cudaGetDevice(&b->device));
+  BCK(b, cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device));
+  BCK(b, cudaDeviceGetAttribute(&b->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device));
+  for (int k = 0; k < n_sys; ++k) {
+    lrdmc_handle h = nullptr;
+    const lrdmc_status st = lrdmc_create(&sys[k], &wf[k], &prm[k], x0[k], nullptr, 0, stream, &h);
+    if (st != LRDMC_OK) {
+      const std::string msg = "system " + std::to_string(k) + ": " + (h ? h->err : std::string("create failed"));
+      if (h) lrdmc_destroy(h);
+      return bfail(b, st, msg);
+    }
+    b->h.push_back(h);
+    const Plan& P = h->P;
+    b->total += P.n_w;
+    b->scratch_per_warp =
+        std::max(b->scratch_per_warp, P.precision == 0 ? scratch_doubles(P.L) : scratch_doubles_m(P.L));
+  }
+  b->scratch_per_warp = (b->scratch_per_warp + 1) / 2 * 2;
+  BCK(b, cudaFuncSetAttribute(k_propagate_batch<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)batch_candidate(b, 0)));
+  BCK(b, cudaFuncSetAttribute(k_propagate_batch<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)batch_candidate(b, 0)));
+  cudaFuncAttributes fa{};
+  if (b->precision == 0) BCK(b, cudaFuncGetAttributes(&fa, k_propagate_batch<0>));
+  else BCK(b, cudaFuncGetAttributes(&fa, k_propagate_batch<1>));
+  b->max_threads = fa.maxThreadsPerBlock;
+  // scratch for the largest grid x warps of any candidate shape; default shape:
+  // the candidate with the most resident warps
+  int best = -1, best_warps = 0;
+  for (int c = 0; c < 4; ++c) {
+    bool ok = false;
+    std::vector<int> fit;
+    int w = 0, bps = 0;
+    lrdmc_status st = batch_shape(b, batch_candidate(b, c), &ok, fit, &w, &bps);
+    if (st != LRDMC_OK) return st;
+    if (!ok) continue;
+    b->scratch_warps = std::max(b->scratch_warps, (size_t)bps * b->num_sms * w);
+    if (bps * w > best_warps) { best_warps = bps * w; best = c; }
+  }
+  if (best < 0) return bfail(b, LRDMC_ERR_UNSUPPORTED, "largest system exceeds a CTA's shared memory");
+  b->jobs.resize(n_sys);
+  b->bjobs.resize(n_sys);
+  BCK(b, cudaMalloc(&b->d_jobs, sizeof(PropJob) * n_sys));
+  BCK(b, cudaMalloc(&b->d_bjobs, sizeof(BranchJob) * n_sys));
+  BCK(b, cudaMalloc(&b->d_items, sizeof(int4) * (size_t)b->total));
+  BCK(b, cudaMalloc(&b->d_counter, sizeof(unsigned)));
+  BCK(b, cudaMalloc(&b->d_scratch, sizeof(double) * b->scratch_per_warp * b->scratch_warps));
+  BCK(b, cudaMalloc(&b->d_stats, sizeof(double) * BS_COUNT * n_sys));
+  BCK(b, cudaMalloc(&b->d_status, sizeof(int32_t) * 2 * n_sys));
+  BCK(b, cudaMemsetAsync(b->d_status, 0, sizeof(int32_t) * 2 * n_sys, b->stream));
+  return batch_use(b, batch_candidate(b, best));
+}
+
+lrdmc_status lrdmc_batch_destroy(lrdmc_batch b) {
+  if (!b) return LRDMC_ERR_ARG;
+  {
+    DeviceGuard g(b->device);
+    cudaStreamSynchronize(b->stream);
+    batch_free(b);
+  }
+  delete b;
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_batch_handle(lrdmc_batch b, int k, lrdmc_handle* h) {
+  if (!b || !h || k < 0 || k >= (int)b->h.size()) return LRDMC_ERR_ARG;
+  *h = b->h[k];
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_batch_propagate(lrdmc_batch b, const lrdmc_schedule* sch) {
+  if (!b || b->h.empty()) return LRDMC_ERR_ARG;
+  if (const char* bad = check_schedule(sch)) return bfail(b, LRDMC_ERR_ARG, bad);
+  if (sch->rotate) return bfail(b, LRDMC_ERR_UNSUPPORTED, "the randomised lattice is not batched");
+  DeviceGuard g(b->device);
+  return batch_launch(b, sch);
+}
+
+lrdmc_status lrdmc_batch_branch(lrdmc_batch b) {
+  if (!b || b->h.empty()) return LRDMC_ERR_ARG;
+  DeviceGuard g(b->device);
+  const int n = (int)b->h.size();
+  size_t most = 1;
+  for (int k = 0; k < n; ++k) {
+    lrdmc_handle h = b->h[k];
+    const Plan& P = h->P;
+    BranchJob& J = b->bjobs[k];
+    J.L = P.L;
+    J.state = h->state;
+    J.alt = h->alt;
+    J.cache = h->cache;
+    J.cache_alt = h->cache_alt;
+    J.n_w = P.n_w;
+    J.lb = h->last_kind == LRDMC_LOAD_BALANCED;
+    J.E0 = h->E0;
+    J.xi32 = branch_offset32(h->prm.seed, h->interval);
+    J.Q = h->Q;
+    J.src = h->src;
+    J.status = b->d_status + 2 * k;
+    J.stats = b->d_stats + (size_t)BS_COUNT * k;
+    most = std::max(most, (size_t)P.n_w * std::max(P.L.g_stride, P.L.c_stride) / 2);
+  }
+  BCK(b, cudaMemcpyAsync(b->d_bjobs, b->bjobs.data(), sizeof(BranchJob) * n, cudaMemcpyHostToDevice, b->stream));
+  k_branch_reduce_batch<<<n, BR_THREADS, 0, b->stream>>>(b->d_bjobs);
+  BLAUNCHED(b);
+  k_reconfigure_batch<<<n, BR_THREADS, 0, b->stream>>>(b->d_bjobs);
+  BLAUNCHED(b);
+  const int gx = (int)std::max<size_t>(1, std::min<size_t>((most + 255) / 256, (size_t)b->num_sms * 8));
+  k_gather_batch<<<dim3(gx, n), 256, 0, b->stream>>>(b->d_bjobs);
+  BLAUNCHED(b);
+  std::vector<double> hs((size_t)BS_COUNT * n);
+  BCK(b, cudaMemcpyAsync(hs.data(), b->d_stats, sizeof(double) * hs.size(), cudaMemcpyDeviceToHost, b->stream));
+  BCK(b, cudaStreamSynchronize(b->stream));
+  lrdmc_status worst = LRDMC_OK;
+  std::string msg;
+  for (int k = 0; k < n; ++k) {
+    const lrdmc_status st = finish_branch(b->h[k], hs.data() + (size_t)BS_COUNT * k);
+    if (st != LRDMC_OK) {
+      if (worst == LRDMC_OK) worst = st;
+      msg += "system " + std::to_string(k) + ": " + b->h[k]->err + "; ";
+    }
+  }
+  if (worst != LRDMC_OK) return bfail(b, worst, msg);
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_batch_set_order(lrdmc_batch b, int policy) {
+  if (!b || (policy != 0 && policy != 1)) return LRDMC_ERR_ARG;
+  DeviceGuard g(b->device);
+  b->policy = policy;
+  return batch_items(b);
+}
+
+lrdmc_status lrdmc_batch_tune(lrdmc_batch b, const lrdmc_schedule* sch, double times_ms[4], int* best_ctas) {
+  if (!b || b->h.empty()) return LRDMC_ERR_ARG;
+  if (const char* bad = check_schedule(sch)) return bfail(b, LRDMC_ERR_ARG, bad);
+  if (sch->rotate) return bfail(b, LRDMC_ERR_UNSUPPORTED, "the randomised lattice is not batched");
+  DeviceGuard g(b->device);
+  cudaEvent_t e0, e1;
+  BCK(b, cudaEventCreate(&e0));
+  BCK(b, cudaEventCreate(&e1));
+  int best = -1;
+  float best_ms = 1e30f;
+  lrdmc_status st = LRDMC_OK;
+  for (int c = 0; c < 4 && st == LRDMC_OK; ++c) {
+    if (times_ms) times_ms[c] = 0.0;
+    bool ok = false;
+    std::vector<int> fit;
+    int w = 0, bps = 0;
+    st = batch_shape(b, batch_candidate(b, c), &ok, fit, &w, &bps);
+    if (st != LRDMC_OK || !ok) continue;
+    st = batch_use(b, batch_candidate(b, c));
+    if (st != LRDMC_OK) break;
+    // keep every walker (and its caches) to restore after the trial
+    for (lrdmc_handle h : b->h) {
+      if (cudaMemcpyAsync(h->alt, h->state, h->P.state_bytes, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess ||
+          cudaMemcpyAsync(h->cache_alt, h->cache, h->P.cache_bytes, cudaMemcpyDeviceToDevice, b->stream) !=
+              cudaSuccess) {
+        st = bfail(b, LRDMC_ERR_CUDA, "snapshot copy failed");
+        break;
+      }
+    }
+    if (st != LRDMC_OK) break;
+    cudaEventRecord(e0, b->stream);
+    st = batch_launch(b, sch);
+    cudaEventRecord(e1, b->stream);
+    if (st != LRDMC_OK) break;
+    for (lrdmc_handle h : b->h) {
+      if (cudaMemcpyAsync(h->state, h->alt, h->P.state_bytes, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess ||
+          cudaMemcpyAsync(h->cache, h->cache_alt, h->P.cache_bytes, cudaMemcpyDeviceToDevice, b->stream) !=
+              cudaSuccess) {
+        st = bfail(b, LRDMC_ERR_CUDA, "restore copy failed");
+        break;
+      }
+    }
+    if (st != LRDMC_OK) break;
+    if (cudaEventSynchronize(e1) != cudaSuccess) { st = bfail(b, LRDMC_ERR_CUDA, "tuning launch failed"); break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (times_ms) times_ms[c] = ms;
+    if (ms < best_ms) { best_ms = ms; best = c; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != LRDMC_OK) return st;
+  if (best < 0) return bfail(b, LRDMC_ERR_UNSUPPORTED, "no launch shape fits");
+  if (best_ctas) *best_ctas = best + 1;
+  return batch_use(b, batch_candidate(b, best));
+}
+
+lrdmc_status lrdmc_batch_set_timing(lrdmc_batch b, int enable) {
+  if (!b) return LRDMC_ERR_ARG;
+  b->timing = enable != 0;
+  for (lrdmc_handle h : b->h) h->timing = b->timing;
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_batch_timing(lrdmc_batch b, double out[6]) {
+  if (!b || !out || b->h.empty()) return LRDMC_ERR_ARG;
+  if (!b->timing) return bfail(b, LRDMC_ERR_ARG, "timing is not enabled");
+  DeviceGuard g(b->device);
+  unsigned long long t0 = ~0ull, t1 = 0;
+  double sum = 0.0, mx = 0.0;
+  for (lrdmc_handle h : b->h) {
+    const int n = h->P.n_w;
+    std::vector<unsigned long long> st(3 * (size_t)n);
+    BCK(b, cudaMemcpyAsync(st.data(), h->stamps, sizeof(unsigned long long) * st.size(), cudaMemcpyDeviceToHost,
+                           b->stream));
+    BCK(b, cudaStreamSynchronize(b->stream));
+    for (int a = 0; a < n; ++a) {
+      t0 = std::min(t0, st[3 * a]);
+      t1 = std::max(t1, st[3 * a + 1]);
+      const double d = (double)(st[3 * a + 1] - st[3 * a]) * 1e-6;
+      sum += d;
+      mx = std::max(mx, d);
+    }
+  }
+  const double span = t1 > t0 ? (double)(t1 - t0) * 1e-6 : 0.0;
+  const int resident = std::min(b->total, b->grid * b->wmax);
+  out[0] = span;
+  out[1] = sum / b->total;
+  out[2] = mx;
+  out[3] = span > 0.0 ? sum / (span * resident) : 0.0;
+  out[4] = resident;
+  out[5] = b->total;
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_batch_launch_count(lrdmc_batch b, int64_t* n) {
+  if (!b || !n) return LRDMC_ERR_ARG;
+  *n = b->launches;
+  return LRDMC_OK;
+}
+
+const char* lrdmc_batch_last_error(lrdmc_batch b) { return b ? b->err.c_str() : "NULL batch"; }
 
 }  // extern "C"

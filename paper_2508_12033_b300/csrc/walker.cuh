@@ -211,12 +211,16 @@ struct Scr {
 __host__ __device__ inline size_t scratch_doubles(const Layout& L) {
   return (size_t)L.n_e * L.n_bf + 2 * (size_t)L.n_max * L.n_max;
 }
-__device__ __forceinline__ Scr warp_scratch(const Layout& L, double* base, int slot) {
+// Per-warp scratch starting at base (a region of scratch_doubles(L) doubles).
+__device__ __forceinline__ Scr warp_scratch_at(const Layout& L, double* base) {
   Scr s;
-  s.g = base + (size_t)slot * scratch_doubles(L);
+  s.g = base;
   s.gj = s.g + (size_t)L.n_e * L.n_bf;
   s.chi = s.u2 = s.pt = nullptr;
   return s;
+}
+__device__ __forceinline__ Scr warp_scratch(const Layout& L, double* base, int slot) {
+  return warp_scratch_at(L, base + (size_t)slot * scratch_doubles(L));
 }
 __device__ __forceinline__ Scr walker_scratch(const Layout& L, double* cblk, const Scr& warp) {
   Scr s;
@@ -1047,19 +1051,15 @@ __global__ void k_eval_configs(DevSys S, Layout L, double* __restrict__ blocks, 
 // walkers after a failed inversion, or a stored evaluation from a randomised
 // lattice) the first hop evaluates in full.  A randomised interval draws new
 // versors and evaluates in full at its start.
+// One walker's interval (the body of k_propagate, also run by the batched
+// kernel): w is the walker index within its system, sm the warp's region.
 template <bool ROT>
-__global__ void k_propagate(DevSys S, Layout L, double* __restrict__ state, double* __restrict__ cache, int n_w,
-                            StepParams P, double* scratch) {
-  extern __shared__ double smem[];
-  const double* T = stage_table(S, smem);
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  double* sm = smem + EXP_TAB + wib * L.s_stride;
+__device__ void propagate_walker(const DevSys& S, const Layout& L, double* __restrict__ state,
+                                 double* __restrict__ cache, int w, const StepParams& P, const double* T, double* sm,
+                                 const Scr& wscr, int lane) {
   double* sc = sm + L.s_sc;
-  const int nwarps = gridDim.x * (blockDim.x >> 5);
-  const int slot = blockIdx.x * (blockDim.x >> 5) + wib;
-  const Scr wscr = warp_scratch(L, scratch, slot);
   const double ia = 1.0 / P.a;
-  for (int w = slot; w < n_w; w += nwarps) {
+  {
     const unsigned long long t_start = global_ns();
     double* gblk = state + (size_t)w * L.g_stride;
     double* cblk = cache + (size_t)w * L.c_stride;
@@ -1172,6 +1172,19 @@ __global__ void k_propagate(DevSys S, Layout L, double* __restrict__ state, doub
       P.stamps[3 * (size_t)w + 2] = sm_id();
     }
   }
+}
+
+template <bool ROT>
+__global__ void k_propagate(DevSys S, Layout L, double* __restrict__ state, double* __restrict__ cache, int n_w,
+                            StepParams P, double* scratch) {
+  extern __shared__ double smem[];
+  const double* T = stage_table(S, smem);
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  double* sm = smem + EXP_TAB + wib * L.s_stride;
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  const int slot = blockIdx.x * (blockDim.x >> 5) + wib;
+  const Scr wscr = warp_scratch(L, scratch, slot);
+  for (int w = slot; w < n_w; w += nwarps) propagate_walker<ROT>(S, L, state, cache, w, P, T, sm, wscr, lane);
 }
 
 // Compact copies of walker fields (for host readback).

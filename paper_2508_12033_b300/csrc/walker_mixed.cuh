@@ -117,6 +117,13 @@ struct ScrM {
   float* pt;
   double* gj;
 };
+__device__ __forceinline__ ScrM warp_scratch_m_at(const Layout& L, double* base) {
+  ScrM s;
+  s.dchi = (float*)base;
+  s.gj = base + ((size_t)L.n_bf * L.n_hop + 1) / 2;
+  s.u2 = s.pt = nullptr;
+  return s;
+}
 __device__ __forceinline__ ScrM warp_scratch_m(const Layout& L, double* scratch, int slot) {
   ScrM s;
   double* base = scratch + (size_t)slot * scratch_doubles_m(L);
@@ -1021,17 +1028,13 @@ __global__ void k_eval_configs_m(DevSys S, Layout L, LayoutM M, double* __restri
 
 // One branching interval for every walker (mixed precision); the caches of
 // the incremental evaluation persist in the walker's cache block.
-__global__ void k_propagate_m(DevSys S, Layout L, LayoutM M, double* __restrict__ state, double* __restrict__ cache,
-                              int n_w, StepParams P, double* scratch) {
-  extern __shared__ double smem[];
-  const double* T = stage_table(S, smem);
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  float* sm = (float*)(smem + EXP_TAB) + wib * M.stride;
+// One walker's interval (the body of k_propagate_m, also run by the batched
+// kernel).
+__device__ void propagate_walker_m(const DevSys& S, const Layout& L, const LayoutM& M, double* __restrict__ state,
+                                   double* __restrict__ cache, int w, const StepParams& P, const double* T, float* sm,
+                                   const ScrM& wscr, int lane) {
   double* sc = (double*)(sm + M.sc);
-  const int nwarps = gridDim.x * (blockDim.x >> 5);
-  const int slot = blockIdx.x * (blockDim.x >> 5) + wib;
-  const ScrM wscr = warp_scratch_m(L, scratch, slot);
-  for (int w = slot; w < n_w; w += nwarps) {
+  {
     const unsigned long long t_start = global_ns();
     double* gblk = state + (size_t)w * L.g_stride;
     double* cblk = cache + (size_t)w * L.c_stride;
@@ -1119,6 +1122,18 @@ __global__ void k_propagate_m(DevSys S, Layout L, LayoutM M, double* __restrict_
       P.stamps[3 * (size_t)w + 2] = sm_id();
     }
   }
+}
+
+__global__ void k_propagate_m(DevSys S, Layout L, LayoutM M, double* __restrict__ state, double* __restrict__ cache,
+                              int n_w, StepParams P, double* scratch) {
+  extern __shared__ double smem[];
+  const double* T = stage_table(S, smem);
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  float* sm = (float*)(smem + EXP_TAB) + wib * M.stride;
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  const int slot = blockIdx.x * (blockDim.x >> 5) + wib;
+  const ScrM wscr = warp_scratch_m(L, scratch, slot);
+  for (int w = slot; w < n_w; w += nwarps) propagate_walker_m(S, L, M, state, cache, w, P, T, sm, wscr, lane);
 }
 
 }  // namespace lrdmc

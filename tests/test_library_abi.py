@@ -108,3 +108,25 @@ def test_reconfigure_rejects_bad_arguments(lib):
     assert lib.lrdmc_reconfigure_indices(0, None, 0, None, None, 0, None, None) == 1
     assert lib.lrdmc_reconfigure_scratch_bytes(0) == 0
     assert lib.lrdmc_reconfigure_scratch_bytes(1000) >= 8000
+
+
+def test_batch_entry_points_validate_arguments_without_a_gpu(lib):
+    names = declared_functions()
+    for n in ("lrdmc_batch_create", "lrdmc_batch_propagate", "lrdmc_batch_branch", "lrdmc_batch_tune",
+              "lrdmc_batch_destroy", "lrdmc_batch_handle"):
+        assert n in names
+    out = ctypes.c_void_p()
+    assert lib.lrdmc_batch_create(0, None, None, None, None, None, ctypes.byref(out)) == 1
+    assert not out.value
+    # systems of different precisions cannot share a batch
+    s0, w0, p0, k0 = _structs(W.h2_sto3g(), precision=0)
+    s1, w1, p1, k1 = _structs(W.h2_sto3g(), precision=1)
+    from paper_2508_12033_b300 import binding as B
+    sa = (B._System * 2)(s0, s1)
+    wa = (B._TrialWF * 2)(w0, w1)
+    pa = (B._Params * 2)(p0, p1)
+    x = np.zeros((64, 2, 3))
+    xp = (B.c_double_p * 2)(x.ctypes.data_as(B.c_double_p), x.ctypes.data_as(B.c_double_p))
+    assert lib.lrdmc_batch_create(2, sa, wa, pa, xp, None, ctypes.byref(out)) == 1
+    assert lib.lrdmc_batch_destroy(None) == 1
+    assert lib.lrdmc_batch_propagate(None, None) == 1

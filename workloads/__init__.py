@@ -7,9 +7,9 @@ values, ratios, energies, weights or branching), so that the CPU oracle and the
 CUDA path can both consume it without sharing any of the method.
 """
 from .systems import (System, hydrogen_atom_sto, hydrogen_atom_gauss, h2_sto3g,
-                      water_methane, hydrogen_chain, by_name)
+                      water_methane, hydrogen_chain, hydrogen_cluster, by_name)
 from .walkers import initial_walkers, lattice_walkers
 
 __all__ = ["System", "hydrogen_atom_sto", "hydrogen_atom_gauss", "h2_sto3g",
-           "water_methane", "hydrogen_chain", "by_name", "initial_walkers",
+           "water_methane", "hydrogen_chain", "hydrogen_cluster", "by_name", "initial_walkers",
            "lattice_walkers"]

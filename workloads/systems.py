@@ -220,6 +220,35 @@ def hydrogen_chain(n_atoms: int = 128, spacing: float = 1.8, mo_seed: int = 5,
                   0.25, 1.0, [0.0] * n_atoms, [1.0] * n_atoms)
 
 
+def hydrogen_cluster(n_atoms: int, seed: int = 0, min_spacing: float = 1.4, density: float = 0.125,
+                     mo_seed: int | None = None, s_exp: float = 1.0, p_exp: float = 0.8) -> System:
+    """Seeded hydrogen cluster: n_atoms protons at random positions in a sphere
+    holding `density` atoms per bohr^3, no two closer than min_spacing (bohr,
+    rejection sampling); one s + one p single-primitive shell per atom, seeded
+    orthonormalised MOs, spins balanced, bare Coulomb nuclei, e-e Pade Jastrow."""
+    rng = np.random.default_rng(seed)
+    radius = (3.0 * n_atoms / (4.0 * math.pi * density)) ** (1.0 / 3.0)
+    R: list = []
+    while len(R) < n_atoms:
+        p = rng.uniform(-radius, radius, 3)
+        if np.dot(p, p) > radius * radius:
+            continue
+        if all(np.linalg.norm(p - q) >= min_spacing for q in R):
+            R.append(p)
+    shells = []
+    for I in range(n_atoms):
+        shells.append((I, 0, [(s_exp, 1.0)]))
+        shells.append((I, 1, [(p_exp, 1.0)]))
+    n_bf = 4 * n_atoms
+    n_up = n_atoms // 2
+    n_occ = max(n_up, n_atoms - n_up)
+    mrng = np.random.default_rng(seed + 1000 if mo_seed is None else mo_seed)
+    Q, _ = np.linalg.qr(mrng.standard_normal((n_bf, n_occ)))
+    return _build(f"H{n_atoms}-cluster-{seed}", [list(p) for p in R], [1.0] * n_atoms, [0] * n_atoms,
+                  [0.0] * n_atoms, n_up, n_atoms - n_up, shells, Q.T.copy(), 0.5, 0.25, 1.0,
+                  [0.0] * n_atoms, [1.0] * n_atoms)
+
+
 def by_name(name: str) -> System:
     table = {"h_sto": hydrogen_atom_sto, "h_gauss": hydrogen_atom_gauss,
              "h2": h2_sto3g, "wm": water_methane}
