@@ -243,10 +243,13 @@ def run_gpu(args, rank, world):
     e2e_value = world * ws_per_step / (statistics.mean(e2e_ms) / 1e3)
     mixed = run_mixed(args, P, s, x0, lr, flush, rank) if not args.no_mixed else None
     a_scan = run_a_scan(P) if rank == 0 and not args.no_a_scan else None
+    batch = None
+    if rank == 0 and not args.no_batch:
+        batch = {"mixed": run_batch(P, 1), "fp64": run_batch(P, 0)}
     return dict(value=value, t_total=t_total, step_ms=statistics.mean(step_ms), prop_ms=statistics.mean(prop_ms),
                 launches=launches, achieved=achieved, clocks=clk.summary(), conv_rate=conv_rate,
                 conv_moves=conv_moves, tau=tau, e2e=e2e_value, h2d=h2d, d2h=d2h, slots=slots,
-                energy=lr.energy(), mixed=mixed, imbalance=imbalance, a_scan=a_scan)
+                energy=lr.energy(), mixed=mixed, imbalance=imbalance, a_scan=a_scan, batch=batch)
 
 
 def aggregate_throughput(t_local, units_local, world, device="cpu"):
@@ -311,6 +314,63 @@ def run_a_scan(P):
             "chi2": chi2, "exact_continuum": -0.5, "wall_s": wall}
 
 
+def run_batch(P, precision, steps=3):
+    """Batched multi-system propagation: 64 seeded hydrogen clusters with N_e
+    uniform in 16..56 (the shared-memory walker layout holds up to 58-62
+    electrons), 256 walkers each, a = 0.25, one persistent launch per interval.
+    Walker-steps/s of load-balanced intervals (N_proj = 20) with each item order,
+    the autotuned launch shape, and the SM idle time of a load-balanced and a
+    conventional interval of equal mean hop count (the in-GPU image of the
+    paper's weak-scaling loss)."""
+    import torch
+    import workloads as W
+    rng = np.random.default_rng(3)
+    ne = [int(v) for v in rng.integers(16, 57, size=64)]
+    systems = [W.hydrogen_cluster(n, seed=100 + k) for k, n in enumerate(ne)]
+    x0s = [W.initial_walkers(s, 256, seed=k) for k, s in enumerate(systems)]
+    b = P.LrdmcBatch(systems, x0s, 0.25, list(range(1, 65)), reinv_period=50, precision=precision)
+    best, tune_ms = b.tune(P.LOAD_BALANCED, n_proj=20)
+    b.set_timing(True)
+    out = {"systems": 64, "n_e": [min(ne), max(ne)], "walkers": 64 * 256, "precision": precision,
+           "tuned_ctas_per_sm": best, "tune_ms": tune_ms}
+    walker_steps = 64 * 256 * 20
+    for pol in (1, 0):
+        b.set_order(pol)
+        b.propagate(P.LOAD_BALANCED, n_proj=20)
+        b.branch()
+        ms = []
+        for _ in range(steps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(b.stream)
+            b.propagate(P.LOAD_BALANCED, n_proj=20)
+            b.branch()
+            e1.record(b.stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        t = b.timing()
+        key = "cost_order" if pol == 1 else "system_order"
+        out[key] = {"value": walker_steps / (statistics.mean(ms) / 1e3), "unit": "walker-steps/s",
+                    "ms_per_step": statistics.mean(ms), "lb_timing": t}
+    # conventional interval with the same mean hop count per walker
+    b.set_order(1)
+    bbar = [float(np.mean(h.get_walkers()["ev"][:, 0])) for h in b.handles]
+    tau = 20.0 / float(np.mean(bbar))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(b.stream)
+    b.propagate(P.CONVENTIONAL, tau=tau, max_moves=2000)
+    e1.record(b.stream)
+    torch.cuda.synchronize()
+    t = b.timing()
+    mv = np.concatenate([h.get_walkers()["moves"] for h in b.handles])
+    out["conventional"] = {"tau": tau, "ms": e0.elapsed_time(e1), "moves_mean": float(mv.mean()),
+                           "moves_max": int(mv.max()), "timing": t}
+    b.branch()
+    b.close()
+    return out
+
+
 def run_mixed(args, P, s, x0, lr64, flush, rank):
     """Mixed-precision form: throughput at the benchmark size and at 51200
     walkers, and its energy bias against FP64 by correlated sampling on the
@@ -352,6 +412,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-a-scan", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -415,6 +476,7 @@ def main():
                     "d2h_bytes_per_step": res["d2h"]},
             "mixed": dict(res["mixed"], speedup_vs_fp64=res["mixed"]["value"] / res["value"]) if res["mixed"] else None,
             "a_scan": res["a_scan"],
+            "batch": res["batch"],
             "gpu_launches": res["launches"],
             "clocks": res["clocks"],
             "energy": {"E": res["energy"][0], "err": res["energy"][1]},

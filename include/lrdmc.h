@@ -322,9 +322,11 @@ const char* lrdmc_status_string(lrdmc_status s);
  * n_w and seed, x0[k] a host array n_w x N_e x 3) and owns an ordinary handle
  * (lrdmc_batch_handle) for readback, energies, history and checkpoints; the
  * batch owns those handles.  All systems must use the same precision and the
- * same CUDA device; the stream is shared.  A system's walkers follow exactly
- * the trajectory they would follow in their own handle: the batch changes only
- * which warp runs which walker. */
+ * same CUDA device; the stream is shared.  A system's walkers follow the
+ * trajectory they would follow in their own handle (the batch changes only
+ * which warp runs which walker): the same hops and positions, with weights and
+ * energies equal up to rounding (the batched kernel is compiled separately
+ * and may fuse the same operations differently). */
 typedef struct lrdmc_batch_s* lrdmc_batch;
 
 /* Create the batch (allocates each system's workspace with cudaMalloc).
@@ -368,11 +370,16 @@ lrdmc_status lrdmc_batch_set_order(lrdmc_batch b, int policy);
 lrdmc_status lrdmc_batch_tune(lrdmc_batch b, const lrdmc_schedule* sch, double times_ms[4], int* best_ctas);
 
 /* Timing of the last batched interval over all systems (requires
- * lrdmc_batch_set_timing(b, 1) before it): out[0] span ms, out[1] mean and
- * out[2] max walker ms, out[3] busy fraction = total walker time / (span x
- * resident warps), out[4] resident warps, out[5] walkers. */
+ * lrdmc_batch_set_timing(b, 1) before it), from every walker's start and stop
+ * time and SM: out[0] span ms, out[1] mean and out[2] max walker ms, out[3] SM
+ * idle fraction = 1 - (time each SM runs at least one walker, summed over SMs)
+ * / (span x SMs), out[4] mean idle tail ms per SM (span end - its last
+ * walker's end), out[5] walker-slot busy fraction = total walker time /
+ * sum over items of (walkers in the item x item duration) — the warps of a
+ * CTA wait at the end of an item for its slowest walker — out[6] walkers,
+ * out[7] items. */
 lrdmc_status lrdmc_batch_set_timing(lrdmc_batch b, int enable);
-lrdmc_status lrdmc_batch_timing(lrdmc_batch b, double out[6]);
+lrdmc_status lrdmc_batch_timing(lrdmc_batch b, double out[8]);
 
 /* Kernels launched by the batch's own entry points. */
 lrdmc_status lrdmc_batch_launch_count(lrdmc_batch b, int64_t* n);

@@ -433,10 +433,10 @@ class LrdmcBatch:
         self._check(self.lib.lrdmc_batch_set_timing(self._b, 1 if enable else 0))
 
     def timing(self):
-        out = np.zeros(6)
+        out = np.zeros(8)
         self._check(self.lib.lrdmc_batch_timing(self._b, _dptr(out)))
-        return dict(span_ms=out[0], walker_ms_mean=out[1], walker_ms_max=out[2], busy_fraction=out[3],
-                    resident_warps=int(out[4]), walkers=int(out[5]))
+        return dict(span_ms=out[0], walker_ms_mean=out[1], walker_ms_max=out[2], sm_idle_fraction=out[3],
+                    sm_idle_tail_ms=out[4], slot_busy_fraction=out[5], walkers=int(out[6]), items=int(out[7]))
 
     def launch_count(self):
         v = C.c_int64()

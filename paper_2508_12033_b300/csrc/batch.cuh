@@ -61,7 +61,7 @@ __global__ void k_propagate_batch(const PropJob* __restrict__ jobs, const int4* 
     if (wib < it.z) {
       double* sm = regions + (size_t)wib * J->region;
       if (PREC == 0) {
-        const Scr ws = warp_scratch_at(J->L, wscr);
+        const Scr ws = warp_scratch_at(J->L, J->S.n_nuc, wscr);
         propagate_walker<false>(J->S, J->L, J->state, J->cache, it.y + wib, J->P, T, sm, ws, lane);
       } else {
         const ScrM ws = warp_scratch_m_at(J->L, wscr);

@@ -91,6 +91,10 @@ struct Layout {
   // the pair Jastrow term of every hop with every partner [n_e][6 n_e] and the
   // pair terms at the current positions [n_e][n_e][4]
   int c_mir, c_g, c_chi, c_u2, c_pt, c_stride;
+  // large systems: the electron-nucleus geometry [n_e][n_nuc][4] and the pair
+  // distances [n_e][n_e] live in the cache block (c_geo, c_pr2) instead of
+  // shared memory (s_geo, s_pr2 then have no extent)
+  int geo_glob, c_geo, c_pr2;
 };
 
 __host__ __device__ inline int round_up(int v, int m) { return (v + m - 1) / m * m; }

@@ -26,6 +26,9 @@ constexpr int MAX_WALKERS = 1 << 24;
 // Upper bound of resident warps that get per-warp scratch (148 SMs x 16 warps);
 // the launch grid is clamped to it.
 constexpr int SCRATCH_WARPS_CAP = 148 * 16;
+// FP64 walkers whose shared-memory layout would exceed this keep their geometry
+// caches in the cache block (see make_plan).
+constexpr size_t GEO_GLOBAL_BYTES = 32 * 1024;
 
 size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
@@ -91,33 +94,42 @@ bool make_plan(const lrdmc_system* sys, const lrdmc_trial_wf* wf, const lrdmc_pa
   L.g_pot = L.g_rat + L.n_hop;
   L.g_sc = round_up(L.g_pot + 2 * P.n_e, 16);
   L.g_stride = round_up(L.g_sc + SC_COUNT, 16);
-  // per-warp shared memory
-  L.s_x = 0;
-  L.s_bt = 3 * P.n_e;
-  L.s_rat = L.s_bt + nbt;
-  L.s_ep = L.s_rat + L.n_hop;
-  L.s_ej = L.s_ep + 2 * P.n_e;
-  L.s_dd = L.s_ej + 6 * P.n_e;
-  L.s_geo = L.s_dd + 4 * P.n_e;
-  L.s_pr2 = L.s_geo + 4 * P.n_e * P.n_nuc;
-  L.s_hd = L.s_pr2 + P.n_e * P.n_e;
-  L.s_hj1 = L.s_hd + L.n_hop;
-  L.s_hj2 = L.s_hj1 + L.n_hop;
-  L.s_tmp = L.s_hj2 + L.n_hop;
-  L.s_phi5 = L.s_tmp + std::max(6 * (P.n_e - 1 + P.n_nuc), 6 * P.n_bf);
-  L.s_u = L.s_phi5 + 5 * P.n_max;
-  L.s_row = L.s_u + P.n_max;
-  L.s_xo = L.s_row + P.n_max;
-  L.s_v = L.s_xo + 4;
-  L.s_sc = L.s_v + 12;
-  L.s_stride = round_up(L.s_sc + SC_COUNT, 4);
-  // per-walker cache block (FP64 kernels only)
-  L.c_mir = 0;
-  L.c_g = round_up(L.s_tmp - L.s_ej, 4);
-  L.c_chi = L.c_g + P.n_e * P.n_bf;
-  L.c_u2 = L.c_chi + P.n_bf * L.n_hop;
-  L.c_pt = L.c_u2 + P.n_e * L.n_hop;
-  L.c_stride = round_up(L.c_pt + 4 * P.n_e * P.n_e, 16);
+  // per-warp shared memory; a large FP64 system keeps its electron-nucleus
+  // geometry and pair distances (O(N_e N_nuc + N_e^2)) in the cache block
+  // instead, so that several of its walkers share an SM
+  auto fp64_layout = [&](int geo_glob) {
+    L.geo_glob = geo_glob;
+    L.s_x = 0;
+    L.s_bt = 3 * P.n_e;
+    L.s_rat = L.s_bt + nbt;
+    L.s_ep = L.s_rat + L.n_hop;
+    L.s_ej = L.s_ep + 2 * P.n_e;
+    L.s_dd = L.s_ej + 6 * P.n_e;
+    L.s_geo = L.s_dd + 4 * P.n_e;
+    L.s_pr2 = L.s_geo + (geo_glob ? 0 : 4 * P.n_e * P.n_nuc);
+    L.s_hd = L.s_pr2 + (geo_glob ? 0 : P.n_e * P.n_e);
+    L.s_hj1 = L.s_hd + L.n_hop;
+    L.s_hj2 = L.s_hj1 + L.n_hop;
+    L.s_tmp = L.s_hj2 + L.n_hop;
+    L.s_phi5 = L.s_tmp + std::max(6 * (P.n_e - 1 + P.n_nuc), 6 * P.n_bf);
+    L.s_u = L.s_phi5 + 5 * P.n_max;
+    L.s_row = L.s_u + P.n_max;
+    L.s_xo = L.s_row + P.n_max;
+    L.s_v = L.s_xo + 4;
+    L.s_sc = L.s_v + 12;
+    L.s_stride = round_up(L.s_sc + SC_COUNT, 4);
+    // per-walker cache block
+    L.c_mir = 0;
+    L.c_g = round_up(L.s_tmp - L.s_ej, 4);
+    L.c_chi = L.c_g + P.n_e * P.n_bf;
+    L.c_u2 = L.c_chi + P.n_bf * L.n_hop;
+    L.c_pt = L.c_u2 + P.n_e * L.n_hop;
+    L.c_geo = L.c_pt + 4 * P.n_e * P.n_e;
+    L.c_pr2 = L.c_geo + (geo_glob ? 4 * P.n_e * P.n_nuc : 0);
+    L.c_stride = round_up(L.c_pr2 + (geo_glob ? P.n_e * P.n_e : 0), 16);
+  };
+  fp64_layout(0);
+  if (P.precision == 0 && (size_t)L.s_stride * sizeof(double) > GEO_GLOBAL_BYTES) fp64_layout(1);
   P.M = layout_mixed(L, P.n_nuc, P.n_prim);
   if (P.precision == 1) L.c_stride = round_up((P.M.c_floats + 1) / 2, 16);
   P.smem_per_warp = P.precision == 0 ? (size_t)L.s_stride * sizeof(double) : (size_t)P.M.stride * sizeof(float);
@@ -166,7 +178,7 @@ bool make_plan(const lrdmc_system* sys, const lrdmc_trial_wf* wf, const lrdmc_pa
   P.o_dstat = w; w += align_up(sizeof(int32_t) * 16);
   P.o_stamps = w; w += align_up(sizeof(unsigned long long) * 3 * (size_t)P.n_w);
   P.scratch_warps = round_up(std::min(P.n_w, SCRATCH_WARPS_CAP), 4);
-  const size_t per_warp = P.precision == 0 ? scratch_doubles(L) : scratch_doubles_m(L);
+  const size_t per_warp = P.precision == 0 ? scratch_doubles(L, P.n_nuc) : scratch_doubles_m(L);
   P.o_scr = w; w += align_up(sizeof(double) * per_warp * (size_t)P.scratch_warps);
   P.total = w;
   return true;
@@ -1259,7 +1271,7 @@ lrdmc_status lrdmc_batch_create(int n_sys, const lrdmc_system* sys, const lrdmc_
     const Plan& P = h->P;
     b->total += P.n_w;
     b->scratch_per_warp =
-        std::max(b->scratch_per_warp, P.precision == 0 ? scratch_doubles(P.L) : scratch_doubles_m(P.L));
+        std::max(b->scratch_per_warp, P.precision == 0 ? scratch_doubles(P.L, P.n_nuc) : scratch_doubles_m(P.L));
   }
   b->scratch_per_warp = (b->scratch_per_warp + 1) / 2 * 2;
   BCK(b, cudaFuncSetAttribute(k_propagate_batch<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1441,13 +1453,17 @@ lrdmc_status lrdmc_batch_set_timing(lrdmc_batch b, int enable) {
   return LRDMC_OK;
 }
 
-lrdmc_status lrdmc_batch_timing(lrdmc_batch b, double out[6]) {
+lrdmc_status lrdmc_batch_timing(lrdmc_batch b, double out[8]) {
   if (!b || !out || b->h.empty()) return LRDMC_ERR_ARG;
   if (!b->timing) return bfail(b, LRDMC_ERR_ARG, "timing is not enabled");
   DeviceGuard g(b->device);
   unsigned long long t0 = ~0ull, t1 = 0;
   double sum = 0.0, mx = 0.0;
-  for (lrdmc_handle h : b->h) {
+  std::vector<std::vector<std::pair<unsigned long long, unsigned long long>>> per_sm(b->num_sms);
+  double slot_busy = 0.0, slot_cap = 0.0;
+  int n_items = 0;
+  for (size_t k = 0; k < b->h.size(); ++k) {
+    lrdmc_handle h = b->h[k];
     const int n = h->P.n_w;
     std::vector<unsigned long long> st(3 * (size_t)n);
     BCK(b, cudaMemcpyAsync(st.data(), h->stamps, sizeof(unsigned long long) * st.size(), cudaMemcpyDeviceToHost,
@@ -1459,16 +1475,46 @@ lrdmc_status lrdmc_batch_timing(lrdmc_batch b, double out[6]) {
       const double d = (double)(st[3 * a + 1] - st[3 * a]) * 1e-6;
       sum += d;
       mx = std::max(mx, d);
+      const unsigned sm = (unsigned)st[3 * a + 2];
+      if (sm < per_sm.size()) per_sm[sm].push_back({st[3 * a], st[3 * a + 1]});
+    }
+    // items of this system: fit[k] consecutive walkers run together in one CTA
+    for (int w0 = 0; w0 < n; w0 += b->fit[k]) {
+      const int c = std::min(b->fit[k], n - w0);
+      unsigned long long s0 = ~0ull, s1 = 0;
+      for (int a = w0; a < w0 + c; ++a) {
+        s0 = std::min(s0, st[3 * a]);
+        s1 = std::max(s1, st[3 * a + 1]);
+        slot_busy += (double)(st[3 * a + 1] - st[3 * a]);
+      }
+      slot_cap += (double)c * (double)(s1 - s0);
+      ++n_items;
     }
   }
   const double span = t1 > t0 ? (double)(t1 - t0) * 1e-6 : 0.0;
-  const int resident = std::min(b->total, b->grid * b->wmax);
+  // per SM: time covered by at least one walker, and the idle tail after its last walker
+  double covered = 0.0, tail = 0.0;
+  for (auto& v : per_sm) {
+    if (v.empty()) { tail += span; continue; }
+    std::sort(v.begin(), v.end());
+    unsigned long long cs = v[0].first, ce = v[0].second, busy = 0, last = 0;
+    for (const auto& iv : v) {
+      if (iv.first > ce) { busy += ce - cs; cs = iv.first; ce = iv.second; }
+      else ce = std::max(ce, iv.second);
+      last = std::max(last, iv.second);
+    }
+    busy += ce - cs;
+    covered += (double)busy * 1e-6;
+    tail += (double)(t1 - last) * 1e-6;
+  }
   out[0] = span;
   out[1] = sum / b->total;
   out[2] = mx;
-  out[3] = span > 0.0 ? sum / (span * resident) : 0.0;
-  out[4] = resident;
-  out[5] = b->total;
+  out[3] = span > 0.0 ? 1.0 - covered / (span * per_sm.size()) : 0.0;
+  out[4] = tail / per_sm.size();
+  out[5] = slot_cap > 0.0 ? slot_busy / slot_cap : 0.0;
+  out[6] = b->total;
+  out[7] = n_items;
   return LRDMC_OK;
 }
 

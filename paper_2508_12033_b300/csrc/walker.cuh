@@ -207,20 +207,27 @@ struct Scr {
   double* u2;    // [n_e][6 n_e]  u2[j][p]: pair Jastrow term of hop p with partner j
   double* pt;    // [n_e][n_e][4] pair terms at the current positions: u, u'/r, u'' + 2u'/r, 1/(2r)
   double* gj;
+  double* geo;   // global geometry and pair distances of a large system (null: shared memory)
+  double* pr2;
 };
-__host__ __device__ inline size_t scratch_doubles(const Layout& L) {
-  return (size_t)L.n_e * L.n_bf + 2 * (size_t)L.n_max * L.n_max;
+__host__ __device__ inline size_t geo_doubles(const Layout& L, int n_nuc) {
+  return L.geo_glob ? 4 * (size_t)L.n_e * n_nuc + (size_t)L.n_e * L.n_e : 0;
+}
+__host__ __device__ inline size_t scratch_doubles(const Layout& L, int n_nuc) {
+  return (size_t)L.n_e * L.n_bf + 2 * (size_t)L.n_max * L.n_max + geo_doubles(L, n_nuc);
 }
 // Per-warp scratch starting at base (a region of scratch_doubles(L) doubles).
-__device__ __forceinline__ Scr warp_scratch_at(const Layout& L, double* base) {
+__device__ __forceinline__ Scr warp_scratch_at(const Layout& L, int n_nuc, double* base) {
   Scr s;
   s.g = base;
   s.gj = s.g + (size_t)L.n_e * L.n_bf;
   s.chi = s.u2 = s.pt = nullptr;
+  s.geo = L.geo_glob ? s.gj + 2 * (size_t)L.n_max * L.n_max : nullptr;
+  s.pr2 = L.geo_glob ? s.geo + 4 * (size_t)L.n_e * n_nuc : nullptr;
   return s;
 }
-__device__ __forceinline__ Scr warp_scratch(const Layout& L, double* base, int slot) {
-  return warp_scratch_at(L, base + (size_t)slot * scratch_doubles(L));
+__device__ __forceinline__ Scr warp_scratch(const Layout& L, int n_nuc, double* base, int slot) {
+  return warp_scratch_at(L, n_nuc, base + (size_t)slot * scratch_doubles(L, n_nuc));
 }
 __device__ __forceinline__ Scr walker_scratch(const Layout& L, double* cblk, const Scr& warp) {
   Scr s;
@@ -229,6 +236,8 @@ __device__ __forceinline__ Scr walker_scratch(const Layout& L, double* cblk, con
   s.u2 = cblk + L.c_u2;
   s.pt = cblk + L.c_pt;
   s.gj = warp.gj;
+  s.geo = L.geo_glob ? cblk + L.c_geo : nullptr;
+  s.pr2 = L.geo_glob ? cblk + L.c_pr2 : nullptr;
   return s;
 }
 
@@ -423,8 +432,8 @@ __device__ EvalOut eval_full(const DevSys& S, const Layout& L, const double* __r
   const double* g = scr.g;
   double* rat = sm + L.s_rat;
   double* ej = sm + L.s_ej;
-  double* geo = sm + L.s_geo;
-  double* pr2 = sm + L.s_pr2;
+  double* geo = scr.geo ? scr.geo : sm + L.s_geo;
+  double* pr2 = scr.pr2 ? scr.pr2 : sm + L.s_pr2;
   double* hD = sm + L.s_hd;
   double* hJ1 = sm + L.s_hj1;
   double* hJ2 = sm + L.s_hj2;
@@ -573,8 +582,8 @@ __device__ EvalOut eval_incr(const DevSys& S, const Layout& L, const double* __r
   const double* g = scr.g;
   double* rat = sm + L.s_rat;
   double* ej = sm + L.s_ej;
-  double* geo = sm + L.s_geo;
-  double* pr2 = sm + L.s_pr2;
+  double* geo = scr.geo ? scr.geo : sm + L.s_geo;
+  double* pr2 = scr.pr2 ? scr.pr2 : sm + L.s_pr2;
   double* hD = sm + L.s_hd;
   double* hJ1 = sm + L.s_hj1;
   double* hJ2 = sm + L.s_hj2;
@@ -986,7 +995,7 @@ __global__ void k_init_walkers(DevSys S, Layout L, double* __restrict__ state, d
   double* sm = smem + EXP_TAB + wib * L.s_stride;
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   const int slot = blockIdx.x * (blockDim.x >> 5) + wib;
-  const Scr wscr = warp_scratch(L, scratch, slot);
+  const Scr wscr = warp_scratch(L, S.n_nuc, scratch, slot);
   for (int w = slot; w < n; w += nwarps) {
     double* gblk = state + (size_t)w * L.g_stride;
     double* cblk = cache + (size_t)w * L.c_stride;
@@ -1024,7 +1033,7 @@ __global__ void k_eval_configs(DevSys S, Layout L, double* __restrict__ blocks, 
   double* sm = smem + EXP_TAB + wib * L.s_stride;
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   const int slot = blockIdx.x * (blockDim.x >> 5) + wib;
-  const Scr scr = warp_scratch(L, scratch, slot);
+  const Scr scr = warp_scratch(L, S.n_nuc, scratch, slot);
   for (int w = slot; w < n; w += nwarps) {
     double* gblk = blocks + (size_t)w * L.g_stride;
     for (int o = lane; o < 3 * L.n_e; o += WARP) sm[L.s_x + o] = x_in[(size_t)w * 3 * L.n_e + o];
@@ -1183,7 +1192,7 @@ __global__ void k_propagate(DevSys S, Layout L, double* __restrict__ state, doub
   double* sm = smem + EXP_TAB + wib * L.s_stride;
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   const int slot = blockIdx.x * (blockDim.x >> 5) + wib;
-  const Scr wscr = warp_scratch(L, scratch, slot);
+  const Scr wscr = warp_scratch(L, S.n_nuc, scratch, slot);
   for (int w = slot; w < n_w; w += nwarps) propagate_walker<ROT>(S, L, state, cache, w, P, T, sm, wscr, lane);
 }
 

@@ -1,9 +1,11 @@
 """Batched multi-system propagation: one persistent launch per interval for
 several systems of different sizes.  A walker's trajectory does not depend on
-which warp or CTA runs it, so every system of a batch must follow, bit for bit,
-the trajectory of the same system in its own handle (which the single-system
-parity tests tie to the oracle); one system is also compared with the oracle
-directly."""
+which warp or CTA runs it, so every system of a batch must follow the
+trajectory of the same system in its own handle (which the single-system
+parity tests tie to the oracle): the same hops, positions, hop counts and
+status bits, and weights, energies and ratios equal up to the rounding of the
+two kernels' compiled arithmetic (the same source, fused differently by the
+compiler: 1e-10).  One system is also compared with the oracle directly."""
 import numpy as np
 import pytest
 
@@ -31,11 +33,15 @@ def _run(obj, P, n_lb=3):
 
 def _same(a, b):
     ga, gb = a.get_walkers(), b.get_walkers()
-    for k in ("x", "w", "ev", "ratios", "status", "moves"):
+    for k in ("x", "status", "moves"):
         np.testing.assert_array_equal(ga[k], gb[k], err_msg=k)
+    for k in ("w", "ev", "ratios"):
+        assert_close(ga[k], gb[k], what=k)
     ha, hb = a.history(), b.history()
-    for k in ha:
+    for k in ("moves_mean", "moves_max", "survivors", "status_or"):
         np.testing.assert_array_equal(ha[k], hb[k], err_msg=k)
+    for k in ("wbar", "ebar", "e0"):
+        assert_close(ha[k], hb[k], what=k)
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -90,8 +96,10 @@ def test_batch_timing_and_refusals():
     batch.set_timing(True)
     batch.propagate(P.LOAD_BALANCED, n_proj=5)
     t = batch.timing()
-    assert t["walkers"] == 192 and 0.0 < t["busy_fraction"] <= 1.0 + 1e-9
+    assert t["walkers"] == 192 and 0.0 <= t["sm_idle_fraction"] < 1.0
     assert t["walker_ms_max"] <= t["span_ms"] + 1e-9
+    assert 0.0 <= t["sm_idle_tail_ms"] <= t["span_ms"] + 1e-9
+    assert 0.0 < t["slot_busy_fraction"] <= 1.0 + 1e-9 and t["items"] >= 3
     with pytest.raises(P.LrdmcError) as e:
         batch.propagate(P.CONVENTIONAL, tau=-1.0)
     assert e.value.status == 1

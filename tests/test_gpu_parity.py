@@ -20,8 +20,10 @@ def _mk(P, sys_, n_w, a=0.2, seed=1, **kw):
     return P.Lrdmc(sys_, x0, a, seed=seed, **kw), x0
 
 
+# h24: a system large enough that its geometry caches live in global memory
 CASES = [("h_sto", W.hydrogen_atom_sto, 70), ("h2", W.h2_sto3g, 300), ("wm", W.water_methane, 37),
-         ("h6", lambda: W.hydrogen_chain(6, spacing=1.6, mo_seed=3), 45)]
+         ("h6", lambda: W.hydrogen_chain(6, spacing=1.6, mo_seed=3), 45),
+         ("h24", lambda: W.hydrogen_cluster(24, seed=5), 16)]
 
 
 @pytest.mark.parametrize("name,sysf,n", CASES)
@@ -61,7 +63,8 @@ def _oracle_walkers(s, g, a=0.2):
     return Wk
 
 
-@pytest.mark.parametrize("name,sysf,n_w", [("h2", W.h2_sto3g, 77), ("wm", W.water_methane, 40)])
+@pytest.mark.parametrize("name,sysf,n_w", [("h2", W.h2_sto3g, 77), ("wm", W.water_methane, 40),
+                                           ("h24", lambda: W.hydrogen_cluster(24, seed=5), 12)])
 def test_load_balanced_interval_matches_oracle(name, sysf, n_w):
     P = lib_or_skip()
     s = sysf()
