@@ -64,7 +64,7 @@ __global__ void k_propagate_batch(const PropJob* __restrict__ jobs, const int4* 
         const Scr ws = warp_scratch_at(J->L, J->S.n_nuc, wscr);
         propagate_walker<false>(J->S, J->L, J->state, J->cache, it.y + wib, J->P, T, sm, ws, lane);
       } else {
-        const ScrM ws = warp_scratch_m_at(J->L, wscr);
+        const ScrM ws = warp_scratch_m_at(J->L, J->M, wscr);
         propagate_walker_m(J->S, J->L, J->M, J->state, J->cache, it.y + wib, J->P, T, reinterpret_cast<float*>(sm),
                            ws, lane);
       }

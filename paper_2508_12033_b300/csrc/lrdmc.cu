@@ -131,6 +131,9 @@ bool make_plan(const lrdmc_system* sys, const lrdmc_trial_wf* wf, const lrdmc_pa
   fp64_layout(0);
   if (P.precision == 0 && (size_t)L.s_stride * sizeof(double) > GEO_GLOBAL_BYTES) fp64_layout(1);
   P.M = layout_mixed(L, P.n_nuc, P.n_prim);
+  // a large mixed-precision system keeps its O(N^2) arrays in global memory
+  if (P.precision == 1 && (size_t)P.M.stride * sizeof(float) > GEO_GLOBAL_BYTES)
+    P.M = layout_mixed(L, P.n_nuc, P.n_prim, 1);
   if (P.precision == 1) L.c_stride = round_up((P.M.c_floats + 1) / 2, 16);
   P.smem_per_warp = P.precision == 0 ? (size_t)L.s_stride * sizeof(double) : (size_t)P.M.stride * sizeof(float);
   if (P.smem_per_warp + EXP_TAB * sizeof(double) > 200 * 1024) { P.err = "system too large for the per-warp shared-memory layout"; return false; }
@@ -178,7 +181,7 @@ bool make_plan(const lrdmc_system* sys, const lrdmc_trial_wf* wf, const lrdmc_pa
   P.o_dstat = w; w += align_up(sizeof(int32_t) * 16);
   P.o_stamps = w; w += align_up(sizeof(unsigned long long) * 3 * (size_t)P.n_w);
   P.scratch_warps = round_up(std::min(P.n_w, SCRATCH_WARPS_CAP), 4);
-  const size_t per_warp = P.precision == 0 ? scratch_doubles(L, P.n_nuc) : scratch_doubles_m(L);
+  const size_t per_warp = P.precision == 0 ? scratch_doubles(L, P.n_nuc) : scratch_doubles_m(L, P.M);
   P.o_scr = w; w += align_up(sizeof(double) * per_warp * (size_t)P.scratch_warps);
   P.total = w;
   return true;
@@ -1271,7 +1274,7 @@ lrdmc_status lrdmc_batch_create(int n_sys, const lrdmc_system* sys, const lrdmc_
     const Plan& P = h->P;
     b->total += P.n_w;
     b->scratch_per_warp =
-        std::max(b->scratch_per_warp, P.precision == 0 ? scratch_doubles(P.L, P.n_nuc) : scratch_doubles_m(P.L));
+        std::max(b->scratch_per_warp, P.precision == 0 ? scratch_doubles(P.L, P.n_nuc) : scratch_doubles_m(P.L, P.M));
   }
   b->scratch_per_warp = (b->scratch_per_warp + 1) / 2 * 2;
   BCK(b, cudaFuncSetAttribute(k_propagate_batch<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,

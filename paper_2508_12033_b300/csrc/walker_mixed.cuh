@@ -50,10 +50,16 @@ struct LayoutM {
   // difference of every hop with every partner [n_e][6 n_e] and the pair
   // derivative terms at the current positions [n_e][n_e][3]
   int c_u2, c_pt, c_floats;
+  // large systems (glob): the O(N^2) arrays geo, rt1, pair, hcur and dph live
+  // in global memory (the cache block at c_big, or per-warp scratch for
+  // configuration evaluation) at offsets g_* from that base, big_floats in all;
+  // their shared-memory extents are then zero
+  int glob, c_big, g_geo, g_rt1, g_pair, g_hcur, g_dph, big_floats;
 };
 
-__host__ __device__ inline LayoutM layout_mixed(const Layout& L, int n_nuc, int n_prim) {
+__host__ __device__ inline LayoutM layout_mixed(const Layout& L, int n_nuc, int n_prim, int glob = 0) {
   LayoutM M;
+  M.glob = glob;
   const int ne = L.n_e, nbt = L.n_up * L.n_up + L.n_dn * L.n_dn, nm = L.n_max, nbf = L.n_bf, P = L.n_hop;
   const int per = ne - 1 + n_nuc;
   int o = 0;
@@ -72,16 +78,24 @@ __host__ __device__ inline LayoutM layout_mixed(const Layout& L, int n_nuc, int 
   M.ej = o; o += 5 * ne;
   M.ep = o; o += 2 * ne;
   M.geo_st = 4 * n_nuc + 1;
-  M.geo = o; o += ne * M.geo_st;
   M.rt1_st = 2 * n_nuc + 1;
-  M.rt1 = o; o += ne * M.rt1_st;
   M.pair_st = 2 * ne + 1;
-  M.pair = o; o += ne * M.pair_st;
   M.hcur_st = n_prim + 1;
-  M.hcur = o; o += ne * M.hcur_st;
+  const int sz_geo = ne * M.geo_st, sz_rt1 = ne * M.rt1_st, sz_pair = ne * M.pair_st, sz_hcur = ne * M.hcur_st;
+  const int sz_dph = P * nm;   // orbital differences at every hop [6 n_e][n_max]
+  M.g_geo = 0;
+  M.g_rt1 = M.g_geo + sz_geo;
+  M.g_pair = M.g_rt1 + sz_rt1;
+  M.g_hcur = M.g_pair + sz_pair;
+  M.g_dph = M.g_hcur + sz_hcur;
+  M.big_floats = glob ? round_up(M.g_dph + sz_dph, 4) : 0;
+  M.geo = o; o += glob ? 0 : sz_geo;
+  M.rt1 = o; o += glob ? 0 : sz_rt1;
+  M.pair = o; o += glob ? 0 : sz_pair;
+  M.hcur = o; o += glob ? 0 : sz_hcur;
   M.hdm = o; o += P;
   M.hj1 = o; o += P;
-  M.dph = o; o += P * nm;      // orbital differences at every hop [6 n_e][n_max]
+  M.dph = o; o += glob ? 0 : sz_dph;
   o = round_up(o, 2);
   M.mir_end = o;
   M.xf = o; o += 3 * ne;
@@ -98,6 +112,7 @@ __host__ __device__ inline LayoutM layout_mixed(const Layout& L, int n_nuc, int 
   int c = round_up(M.mir_end - M.mir, 4);
   M.c_u2 = c; c += round_up(ne * P, 4);
   M.c_pt = c; c += round_up(3 * ne * ne, 4);
+  M.c_big = c; c += M.big_floats;
   M.c_floats = c;
   return M;
 }
@@ -105,32 +120,30 @@ __host__ __device__ inline LayoutM layout_mixed(const Layout& L, int n_nuc, int 
 // Per-warp global scratch of the mixed kernels: the basis differences at every
 // hop [n_bf][6 n_e] floats (live only during a full evaluation) and the FP64
 // Gauss-Jordan work matrix [n_max][2 n_max].
-__host__ __device__ inline size_t scratch_doubles_m(const Layout& L) {
-  return ((size_t)L.n_bf * L.n_hop + 1) / 2 + 2 * (size_t)L.n_max * L.n_max;
+__host__ __device__ inline size_t scratch_doubles_m(const Layout& L, const LayoutM& M) {
+  return ((size_t)L.n_bf * L.n_hop + 1) / 2 + 2 * (size_t)L.n_max * L.n_max + ((size_t)M.big_floats + 1) / 2;
 }
 
 // Global working arrays of one mixed evaluation (see LayoutM for the layouts);
-// u2 and pt are null for configuration evaluation.
+// u2 and pt are null for configuration evaluation; big is the base of the
+// global O(N^2) arrays of a large system (null otherwise).
 struct ScrM {
   float* dchi;   // per-warp scratch of a full evaluation
   float* u2;
   float* pt;
   double* gj;
+  float* big;
 };
-__device__ __forceinline__ ScrM warp_scratch_m_at(const Layout& L, double* base) {
+__device__ __forceinline__ ScrM warp_scratch_m_at(const Layout& L, const LayoutM& M, double* base) {
   ScrM s;
   s.dchi = (float*)base;
   s.gj = base + ((size_t)L.n_bf * L.n_hop + 1) / 2;
   s.u2 = s.pt = nullptr;
+  s.big = M.glob ? (float*)(s.gj + 2 * (size_t)L.n_max * L.n_max) : nullptr;
   return s;
 }
-__device__ __forceinline__ ScrM warp_scratch_m(const Layout& L, double* scratch, int slot) {
-  ScrM s;
-  double* base = scratch + (size_t)slot * scratch_doubles_m(L);
-  s.dchi = (float*)base;
-  s.gj = base + ((size_t)L.n_bf * L.n_hop + 1) / 2;
-  s.u2 = s.pt = nullptr;
-  return s;
+__device__ __forceinline__ ScrM warp_scratch_m(const Layout& L, const LayoutM& M, double* scratch, int slot) {
+  return warp_scratch_m_at(L, M, scratch + (size_t)slot * scratch_doubles_m(L, M));
 }
 __device__ __forceinline__ ScrM walker_scratch_m(const LayoutM& M, double* cblk, const ScrM& warp) {
   ScrM s;
@@ -139,7 +152,34 @@ __device__ __forceinline__ ScrM walker_scratch_m(const LayoutM& M, double* cblk,
   s.u2 = c + M.c_u2;
   s.pt = c + M.c_pt;
   s.gj = warp.gj;
+  s.big = M.glob ? c + M.c_big : nullptr;
   return s;
+}
+
+// Where the O(N^2) arrays of one walker are: shared memory or global.
+struct MArr {
+  float* geo;
+  float* rt1;
+  float* pair;
+  float* hcur;
+  float* dph;
+};
+__device__ __forceinline__ MArr marr(const LayoutM& M, float* sm, const ScrM& scr) {
+  MArr A;
+  if (scr.big) {
+    A.geo = scr.big + M.g_geo;
+    A.rt1 = scr.big + M.g_rt1;
+    A.pair = scr.big + M.g_pair;
+    A.hcur = scr.big + M.g_hcur;
+    A.dph = scr.big + M.g_dph;
+  } else {
+    A.geo = sm + M.geo;
+    A.rt1 = sm + M.rt1;
+    A.pair = sm + M.pair;
+    A.hcur = sm + M.hcur;
+    A.dph = sm + M.dph;
+  }
+  return A;
 }
 
 __device__ __forceinline__ double* cache_val(const Layout& L, double* gblk) { return gblk + L.g_cache; }
@@ -330,9 +370,8 @@ __device__ void refresh_b32(const Layout& L, const LayoutM& M, float* sm, int e0
 // Orbital differences dph[p][k] = sum_mu C_k,mu dchi_mu(p) of the hops
 // p = p0 + c, c in [0, n_hops), read from dchi[mu * ld + c]; k over the
 // electron's spin block, each dot split over G lanes.
-__device__ void orbital_diffs(const DevSys& S, const Layout& L, const LayoutM& M, float* sm, const float* dchi,
-                              int ld, int p0, int n_hops, int lane) {
-  float* dph = sm + M.dph;
+__device__ void orbital_diffs(const DevSys& S, const Layout& L, float* dph, const float* dchi, int ld, int p0,
+                              int n_hops, int lane) {
   const int nm = L.n_max, nbf = L.n_bf;
   const int n_out = n_hops * nm, G = split_factor(n_out, nbf);
   const int chunk = (nbf + G - 1) / G, n_task = n_out * G;
@@ -354,8 +393,7 @@ __device__ void orbital_diffs(const DevSys& S, const Layout& L, const LayoutM& M
 }
 
 // Determinant ratio minus one of hops [p0, p1): dph[p] . B[:, i] (FP32 B).
-__device__ void det_diffs(const Layout& L, const LayoutM& M, float* sm, int p0, int p1, int lane) {
-  const float* dph = sm + M.dph;
+__device__ void det_diffs(const Layout& L, const LayoutM& M, float* sm, const float* dph, int p0, int p1, int lane) {
   const float* b32 = sm + M.b32;
   float* hdm = sm + M.hdm;
   for (int p = p0 + lane; p < p1; p += WARP) {
@@ -465,9 +503,9 @@ __device__ void det_derivs_m(const Layout& L, const LayoutM& M, double* gblk, fl
 // electron e against partner t (an electron for t < n_e - 1, else a nucleus);
 // accumulates into gx, gy, gz, LJ, vee.  With pt set, the pair's derivative
 // terms (u'/r, u'' + 2u'/r, 1/(2r)) go to pt[e][j].
-__device__ __forceinline__ void partner_terms(const DevSys& S, const Layout& L, const LayoutM& M, float* sm, int e,
-                                              int t, float* pt, float& gx, float& gy, float& gz, float& LJ,
-                                              float& vee) {
+__device__ __forceinline__ void partner_terms(const DevSys& S, const Layout& L, const LayoutM& M, float* sm,
+                                              const MArr& AR, int e, int t, float* pt, float& gx, float& gy, float& gz,
+                                              float& LJ, float& vee) {
   const int ne = L.n_e;
   const float* xf = sm + M.xf;
   const float bj = (float)S.j2_b;
@@ -479,7 +517,7 @@ __device__ __forceinline__ void partner_terms(const DevSys& S, const Layout& L, 
     const float ir = rsqrtf(s), r = s * ir;
     const float c = (float)pair_c(S, L, e, j);
     const float tt = __fdividef(1.f, fmaf(bj, r, 1.f));
-    float* pp = sm + M.pair + e * M.pair_st + 2 * j;
+    float* pp = AR.pair + e * M.pair_st + 2 * j;
     pp[0] = r; pp[1] = tt;
     const float up = c * tt * tt, upp = -2.f * bj * up * tt, f = up * ir;
     const float lap = upp + 2.f * f, hir = 0.5f * ir;
@@ -494,10 +532,10 @@ __device__ __forceinline__ void partner_terms(const DevSys& S, const Layout& L, 
     const int I = t - (ne - 1);
     const float dx = xe - __ldg(S.Rf + 3 * I), dy = ye - __ldg(S.Rf + 3 * I + 1), dz = ze - __ldg(S.Rf + 3 * I + 2);
     const float s = sqdistf(dx, dy, dz);
-    float* gg = sm + M.geo + e * M.geo_st + 4 * I;
+    float* gg = AR.geo + e * M.geo_st + 4 * I;
     gg[0] = dx; gg[1] = dy; gg[2] = dz; gg[3] = s;
     const float ir = rsqrtf(s), r = s * ir;
-    float* hc = sm + M.hcur + e * M.hcur_st;
+    float* hc = AR.hcur + e * M.hcur_st;
     for (int sh = __ldg(S.atom_sh + I); sh < __ldg(S.atom_sh + I + 1); ++sh) {
       const int np = __ldg(S.sh_nprim + sh), off = __ldg(S.sh_off + sh);
       const float arg = __ldg(S.sh_l + sh) == -1 ? r : s;
@@ -505,8 +543,8 @@ __device__ __forceinline__ void partner_terms(const DevSys& S, const Layout& L, 
     }
     const float A = __ldg(S.j1Af + I), B = __ldg(S.j1Bf + I);
     const float tt = __fdividef(1.f, fmaf(B, r, 1.f));
-    sm[M.rt1 + e * M.rt1_st + 2 * I] = r;
-    sm[M.rt1 + e * M.rt1_st + 2 * I + 1] = tt;
+    AR.rt1[e * M.rt1_st + 2 * I] = r;
+    AR.rt1[e * M.rt1_st + 2 * I + 1] = tt;
     if (A != 0.f) {
       const float vp = -A * tt * tt, vpp = -2.f * B * vp * tt, f = vp * ir;
       gx = fmaf(f, dx, gx); gy = fmaf(f, dy, gy); gz = fmaf(f, dz, gz);
@@ -526,10 +564,11 @@ __device__ EvalOut eval_full_m(const DevSys& S, const Layout& L, const LayoutM& 
   float* dchi = scr.dchi;
   float* dl = sm + M.dl;
   float* ej = sm + M.ej;
-  const float* geo = sm + M.geo;
-  const float* rt1 = sm + M.rt1;
-  const float* pair = sm + M.pair;
-  const float* hcur = sm + M.hcur;
+  const MArr AR = marr(M, sm, scr);
+  const float* geo = AR.geo;
+  const float* rt1 = AR.rt1;
+  const float* pair = AR.pair;
+  const float* hcur = AR.hcur;
   float* hdm = sm + M.hdm;
   float* hj1 = sm + M.hj1;
   double* hj2 = (double*)(sm + M.hj2);
@@ -544,7 +583,7 @@ __device__ EvalOut eval_full_m(const DevSys& S, const Layout& L, const LayoutM& 
       const int e = base + lane / G, sub = lane % G;
       float gx = 0.f, gy = 0.f, gz = 0.f, LJ = 0.f, vee = 0.f;
       if (e < ne)
-        for (int t = sub; t < per; t += G) partner_terms(S, L, M, sm, e, t, scr.pt, gx, gy, gz, LJ, vee);
+        for (int t = sub; t < per; t += G) partner_terms(S, L, M, sm, AR, e, t, scr.pt, gx, gy, gz, LJ, vee);
       for (int o = G >> 1; o; o >>= 1) {
         gx += __shfl_xor_sync(FULL, gx, o);
         gy += __shfl_xor_sync(FULL, gy, o);
@@ -611,8 +650,8 @@ __device__ EvalOut eval_full_m(const DevSys& S, const Layout& L, const LayoutM& 
   __threadfence_block();
   __syncwarp();
   // (4) orbital differences of every hop and the determinant ratios
-  orbital_diffs(S, L, M, sm, dchi, P, 0, P, lane);
-  det_diffs(L, M, sm, 0, P, lane);
+  orbital_diffs(S, L, AR.dph, dchi, P, 0, P, lane);
+  det_diffs(L, M, sm, AR.dph, 0, P, lane);
   for (int p = lane; p < P; p += WARP) {
     const float D = hdm[p];
     const float J = expm1_fast(hj1[p] + (float)hj2[p]);
@@ -637,9 +676,10 @@ __device__ EvalOut eval_incr_m(const DevSys& S, const Layout& L, const LayoutM& 
   float* dc6 = sm + M.chi5;     // basis differences at m's hops [n_bf][6]
   float* dl = sm + M.dl;
   float* ej = sm + M.ej;
-  const float* geo = sm + M.geo;
-  const float* rt1 = sm + M.rt1;
-  float* pair = sm + M.pair;
+  const MArr AR = marr(M, sm, scr);
+  const float* geo = AR.geo;
+  const float* rt1 = AR.rt1;
+  float* pair = AR.pair;
   float* hdm = sm + M.hdm;
   float* hj1 = sm + M.hj1;
   double* hj2 = (double*)(sm + M.hj2);
@@ -682,7 +722,7 @@ __device__ EvalOut eval_incr_m(const DevSys& S, const Layout& L, const LayoutM& 
         pm[0] = f; pm[1] = lap; pm[2] = hir;
         pj[0] = f; pj[1] = lap; pj[2] = hir;
       } else {
-        partner_terms(S, L, M, sm, m, t, nullptr, gx, gy, gz, LJ, vee);
+        partner_terms(S, L, M, sm, AR, m, t, nullptr, gx, gy, gz, LJ, vee);
       }
     }
 #pragma unroll
@@ -706,7 +746,7 @@ __device__ EvalOut eval_incr_m(const DevSys& S, const Layout& L, const LayoutM& 
   __syncwarp();
   // (D) basis differences at m's six hops, one (hop, shell) per lane, and m's
   // Jastrow differences, one (hop, partner) per lane
-  const float* hc = sm + M.hcur + m * M.hcur_st;
+  const float* hc = AR.hcur + m * M.hcur_st;
   for (int o = lane; o < 6 * S.n_shell; o += WARP) {
     const int d = o / S.n_shell, sh = o - d * S.n_shell, ax = d >> 1;
     const float sa = (d & 1) ? -af : af;
@@ -731,7 +771,7 @@ __device__ EvalOut eval_incr_m(const DevSys& S, const Layout& L, const LayoutM& 
     }
   }
   __syncwarp();
-  orbital_diffs(S, L, M, sm, dc6, 6, 6 * m, 6, lane);
+  orbital_diffs(S, L, AR.dph, dc6, 6, 6 * m, 6, lane);
   for (int o = lane; o < 6 * per; o += WARP) {
     const int d = o / per, t = o - d * per, ax = d >> 1;
     const float sa = (d & 1) ? -af : af;
@@ -776,7 +816,7 @@ __device__ EvalOut eval_incr_m(const DevSys& S, const Layout& L, const LayoutM& 
   }
   // (E) determinant differences of the refreshed block(s) from the cached
   // orbital differences
-  det_diffs(L, M, sm, 6 * b0, 6 * b1, lane);
+  det_diffs(L, M, sm, AR.dph, 6 * b0, 6 * b1, lane);
   // (F) pair Jastrow differences of the other electrons' hops: swap the term with m
   for (int p = lane; p < P; p += WARP) {
     const int i = p / 6;
@@ -970,7 +1010,7 @@ __global__ void k_init_walkers_m(DevSys S, Layout L, LayoutM M, double* __restri
   double* sc = (double*)(sm + M.sc);
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   const int slot = blockIdx.x * (blockDim.x >> 5) + wib;
-  const ScrM wscr = warp_scratch_m(L, scratch, slot);
+  const ScrM wscr = warp_scratch_m(L, M, scratch, slot);
   for (int w = slot; w < n; w += nwarps) {
     double* gblk = state + (size_t)w * L.g_stride;
     double* cblk = cache + (size_t)w * L.c_stride;
@@ -1007,7 +1047,7 @@ __global__ void k_eval_configs_m(DevSys S, Layout L, LayoutM M, double* __restri
   double* x = (double*)(sm + M.x);
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   const int slot = blockIdx.x * (blockDim.x >> 5) + wib;
-  const ScrM scr = warp_scratch_m(L, scratch, slot);
+  const ScrM scr = warp_scratch_m(L, M, scratch, slot);
   for (int w = slot; w < n; w += nwarps) {
     double* gblk = blocks + (size_t)w * L.g_stride;
     for (int o = lane; o < 3 * L.n_e; o += WARP) x[o] = x_in[(size_t)w * 3 * L.n_e + o];
@@ -1132,7 +1172,7 @@ __global__ void k_propagate_m(DevSys S, Layout L, LayoutM M, double* __restrict_
   float* sm = (float*)(smem + EXP_TAB) + wib * M.stride;
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   const int slot = blockIdx.x * (blockDim.x >> 5) + wib;
-  const ScrM wscr = warp_scratch_m(L, scratch, slot);
+  const ScrM wscr = warp_scratch_m(L, M, scratch, slot);
   for (int w = slot; w < n_w; w += nwarps) propagate_walker_m(S, L, M, state, cache, w, P, T, sm, wscr, lane);
 }
 

@@ -20,7 +20,9 @@ pytestmark = pytest.mark.gpu
 @pytest.mark.parametrize("name,sysf,n,rat_tol,el_tol", [
     ("h_sto", W.hydrogen_atom_sto, 64, 1e-6, 1e-5),
     ("h2", W.h2_sto3g, 256, 1e-6, 2e-5),
-    ("wm", W.water_methane, 256, 1e-4, 1e-2)])
+    ("wm", W.water_methane, 256, 1e-4, 1e-2),
+    # 24 electrons: the mixed layout keeps its O(N^2) arrays in global memory
+    ("h24", lambda: W.hydrogen_cluster(24, seed=5), 64, 1e-4, 2e-2)])
 def test_mixed_eval_against_oracle(name, sysf, n, rat_tol, el_tol):
     import torch
     from gpu_helpers import assert_close, lib_or_skip
@@ -38,14 +40,15 @@ def test_mixed_eval_against_oracle(name, sysf, n, rat_tol, el_tol):
     assert np.mean(nn.cpu().numpy() != ref["n_node"]) <= 0.01
 
 
-def test_mixed_interval_tracks_fp64_path():
+@pytest.mark.parametrize("sysf", [W.water_methane, lambda: W.hydrogen_cluster(24, seed=5)])
+def test_mixed_interval_tracks_fp64_path(sysf):
     """Same start, same random streams: after a 20-hop load-balanced interval
     almost every walker made the same hops as in FP64 (a hop choice can flip
     only when the uniform falls within ~1e-7 of a cumulative boundary), and
     those walkers carry the same weight to FP32 accuracy."""
     from gpu_helpers import lib_or_skip
     P = lib_or_skip()
-    s = W.water_methane()
+    s = sysf()
     x0 = W.initial_walkers(s, 512, seed=21)
     g = {}
     for prec in (0, 1):

@@ -98,17 +98,16 @@ def test_workspace_sizing_and_validation(lib):
                                          ctypes.byref(nb)) == 1
     s, w, p, keep = _structs(W.h2_sto3g(), n_w=0)
     assert lib.lrdmc_workspace_bytes(ctypes.byref(s), ctypes.byref(w), ctypes.byref(p), ctypes.byref(nb)) == 1
-    # H128: the FP64 layout keeps its O(N^2) geometry caches in global memory and
-    # accepts it; the mixed layout (O(N^2) shared arrays) refuses it, and so does
-    # the FP64 layout for 256 electrons (B^T alone exceeds shared memory)
-    s, w, p, keep = _structs(W.hydrogen_chain(128), n_w=16)
-    assert lib.lrdmc_workspace_bytes(ctypes.byref(s), ctypes.byref(w), ctypes.byref(p), ctypes.byref(nb)) == 0
-    s, w, p, keep = _structs(W.hydrogen_chain(128), n_w=16, precision=1)
-    assert lib.lrdmc_workspace_bytes(ctypes.byref(s), ctypes.byref(w), ctypes.byref(p),
-                                     ctypes.byref(nb)) == 7
-    s, w, p, keep = _structs(W.hydrogen_chain(256), n_w=16)
-    assert lib.lrdmc_workspace_bytes(ctypes.byref(s), ctypes.byref(w), ctypes.byref(p),
-                                     ctypes.byref(nb)) == 7
+    # H128: both layouts keep their O(N^2) geometry and pair caches in global
+    # memory for large systems and accept it; 256 electrons are refused (B^T
+    # alone exceeds the per-walker shared-memory budget)
+    for prec in (0, 1):
+        s, w, p, keep = _structs(W.hydrogen_chain(128), n_w=16, precision=prec)
+        assert lib.lrdmc_workspace_bytes(ctypes.byref(s), ctypes.byref(w), ctypes.byref(p),
+                                         ctypes.byref(nb)) == 0
+        s, w, p, keep = _structs(W.hydrogen_chain(256), n_w=16, precision=prec)
+        assert lib.lrdmc_workspace_bytes(ctypes.byref(s), ctypes.byref(w), ctypes.byref(p),
+                                         ctypes.byref(nb)) == 7
 
 
 def test_reconfigure_rejects_bad_arguments(lib):
