@@ -316,8 +316,8 @@ def run_a_scan(P):
 
 def run_batch(P, precision, steps=3):
     """Batched multi-system propagation: 64 seeded hydrogen clusters with N_e
-    uniform in 16..56 (the shared-memory walker layout holds up to 58-62
-    electrons), 256 walkers each, a = 0.25, one persistent launch per interval.
+    uniform in 16..128, 256 walkers each, a = 0.25, one persistent launch per
+    interval.
     Walker-steps/s of load-balanced intervals (N_proj = 20) with each item order,
     the autotuned launch shape, and the SM idle time of a load-balanced and a
     conventional interval of equal mean hop count (the in-GPU image of the
@@ -325,7 +325,7 @@ def run_batch(P, precision, steps=3):
     import torch
     import workloads as W
     rng = np.random.default_rng(3)
-    ne = [int(v) for v in rng.integers(16, 57, size=64)]
+    ne = [int(v) for v in rng.integers(16, 129, size=64)]
     systems = [W.hydrogen_cluster(n, seed=100 + k) for k, n in enumerate(ne)]
     x0s = [W.initial_walkers(s, 256, seed=k) for k, s in enumerate(systems)]
     b = P.LrdmcBatch(systems, x0s, 0.25, list(range(1, 65)), reinv_period=50, precision=precision)

@@ -22,7 +22,8 @@ pytestmark = pytest.mark.gpu
     ("h2", W.h2_sto3g, 256, 1e-6, 2e-5),
     ("wm", W.water_methane, 256, 1e-4, 1e-2),
     # 24 electrons: the mixed layout keeps its O(N^2) arrays in global memory
-    ("h24", lambda: W.hydrogen_cluster(24, seed=5), 64, 1e-4, 2e-2)])
+    ("h24", lambda: W.hydrogen_cluster(24, seed=5), 64, 1e-4, 2e-2),
+    ("h64", lambda: W.hydrogen_cluster(64, seed=6), 4, 1e-4, 5e-2)])
 def test_mixed_eval_against_oracle(name, sysf, n, rat_tol, el_tol):
     import torch
     from gpu_helpers import assert_close, lib_or_skip
@@ -36,8 +37,9 @@ def test_mixed_eval_against_oracle(name, sysf, n, rat_tol, el_tol):
     assert_close(ratios.cpu().numpy(), ref["ratios"], rtol=rat_tol, what="ratios")
     el = ev[:, 3].cpu().numpy()
     assert np.max(np.abs(el - ref["eL"])) <= el_tol
-    assert abs(np.mean(el - ref["eL"])) <= 1e-4                      # energy bias below 0.1 mHa
-    assert np.mean(nn.cpu().numpy() != ref["n_node"]) <= 0.01
+    if n >= 64:   # statistics over enough configurations
+        assert abs(np.mean(el - ref["eL"])) <= 1e-4                  # energy bias below 0.1 mHa
+        assert np.mean(nn.cpu().numpy() != ref["n_node"]) <= 0.01
 
 
 @pytest.mark.parametrize("sysf", [W.water_methane, lambda: W.hydrogen_cluster(24, seed=5)])

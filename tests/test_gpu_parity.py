@@ -23,7 +23,8 @@ def _mk(P, sys_, n_w, a=0.2, seed=1, **kw):
 # h24: a system large enough that its geometry caches live in global memory
 CASES = [("h_sto", W.hydrogen_atom_sto, 70), ("h2", W.h2_sto3g, 300), ("wm", W.water_methane, 37),
          ("h6", lambda: W.hydrogen_chain(6, spacing=1.6, mo_seed=3), 45),
-         ("h24", lambda: W.hydrogen_cluster(24, seed=5), 16)]
+         ("h24", lambda: W.hydrogen_cluster(24, seed=5), 16),
+         ("h64", lambda: W.hydrogen_cluster(64, seed=6), 3)]
 
 
 @pytest.mark.parametrize("name,sysf,n", CASES)
