@@ -9,7 +9,10 @@ and from the plain definitions of the trial-wavefunction quantities:
 * ``wavefunction`` Slater-Jastrow values, ratios by freshly computed determinants
 * ``hamiltonian``  lattice-regularised fixed-node Hamiltonian: hops, V_sf, W, e_L
 * ``lrdmc``        load-balanced and conventional steps, reconfiguration, run loop
-* ``estimator``    global population factor, weighted energy, blocked error bar
+* ``estimator``    global population factor, weighted energy, blocked error bar,
+                   a -> 0 extrapolation
+* ``adjoint``      e_L and log|Psi_G| restated with PyTorch CPU tensors and
+                   differentiated by autograd (nuclear coordinates, Jastrow)
 
 It shares no code with the CUDA library and never imports it.  Only the test
 suite, the smoke check and the benchmark's CPU-baseline leg may import it; the
