@@ -182,6 +182,34 @@ lrdmc_status lrdmc_branch(lrdmc_handle h);
  * (largest over block lengths 1, 2, 4, ... with >= 8 blocks; NaN if too few). */
 lrdmc_status lrdmc_energy(lrdmc_handle h, double* E, double* err);
 
+/* ------------------------------------------------------------ derivatives
+ * Parameters differentiated by lrdmc_local_energy_grad, as one vector theta of
+ * lrdmc_param_count = 5 n_nuc + 3 values: R (n_nuc x 3, bohr), j2_anti,
+ * j2_par, j2_b, j1_A (n_nuc), j1_B (n_nuc). */
+lrdmc_status lrdmc_param_count(lrdmc_handle h, int* n);
+lrdmc_status lrdmc_get_params(lrdmc_handle h, double* theta);
+
+/* Replace the handle's nuclear positions and Jastrow parameters (host theta);
+ * V_ii is recomputed and every walker is re-placed at its current position
+ * and weight (re-inverted and re-evaluated).  Synchronises. */
+lrdmc_status lrdmc_set_params(lrdmc_handle h, const double* theta);
+
+/* Hand-written adjoint of the lattice-regularised local energy e_L = W - b_bar
+ * (Appendix D, the handle's node rule) and of log|Psi_G| at n <= n_w
+ * configurations (device x, n x n_e x 3), with respect to theta:
+ *   eL, logpsi          device, n (or NULL)
+ *   grad_eL, grad_logpsi device, n x lrdmc_param_count (or NULL)
+ * A configuration with a singular Slater matrix gets NaN values.  Precision 0
+ * only (LRDMC_ERR_UNSUPPORTED otherwise).  Does not touch the walkers.
+ * Asynchronous. */
+lrdmc_status lrdmc_local_energy_grad(lrdmc_handle h, int n, const double* x, double* eL, double* logpsi,
+                                     double* grad_eL, double* grad_logpsi);
+
+/* out[j] = sum_k w[k] rows[k m + j] (device arrays; summation in the order
+ * k = 0, 1, ...): the vector-Jacobian product of per-configuration gradient
+ * rows.  Asynchronous. */
+lrdmc_status lrdmc_weighted_rows(lrdmc_handle h, int n, int m, const double* rows, const double* w, double* out);
+
 /* Lattice-space extrapolation (Sec. II: the LRDMC energy carries an O(a^2)
  * bias and is extrapolated to a -> 0 from runs at several spacings).  Weighted
  * least-squares fit of E(a) = sum_{j=0..order} coef[j] a^(2j) to the n points

@@ -87,6 +87,11 @@ def load_library():
         "lrdmc_stream": [P, C.POINTER(P)],
         "lrdmc_extrapolate_a": [C.c_int, c_double_p, c_double_p, c_double_p, C.c_int, c_double_p, c_double_p,
                                 c_double_p],
+        "lrdmc_param_count": [P, c_int_p],
+        "lrdmc_get_params": [P, c_double_p],
+        "lrdmc_set_params": [P, c_double_p],
+        "lrdmc_local_energy_grad": [P, C.c_int, P, P, P, P, P],
+        "lrdmc_weighted_rows": [P, C.c_int, C.c_int, P, P, P],
         "lrdmc_batch_create": [C.c_int, C.POINTER(_System), C.POINTER(_TrialWF), C.POINTER(_Params),
                                C.POINTER(c_double_p), P, C.POINTER(P)],
         "lrdmc_batch_destroy": [P],
@@ -283,6 +288,45 @@ class Lrdmc:
         self._check(self.lib.lrdmc_eval_configs(self._h, n, _tptr(x), _tptr(ratios), _tptr(ev), _tptr(nn)))
         return ratios, ev, nn
 
+    # ---------------------------------------------------------------- derivatives
+    def param_count(self):
+        n = C.c_int()
+        self._check(self.lib.lrdmc_param_count(self._h, C.byref(n)))
+        return n.value
+
+    def params(self):
+        """theta = (R (n_nuc x 3), j2_anti, j2_par, j2_b, j1_A (n_nuc), j1_B (n_nuc))."""
+        th = np.zeros(self.param_count())
+        self._check(self.lib.lrdmc_get_params(self._h, _dptr(th)))
+        return th
+
+    def set_params(self, theta):
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        assert th.shape == (self.param_count(),)
+        self._check(self.lib.lrdmc_set_params(self._h, _dptr(th)))
+
+    def local_energy_grad(self, x):
+        """x: CUDA float64 tensor (n, n_e, 3) -> (e_L (n,), log|Psi| (n,), d e_L/d theta (n, m),
+        d log|Psi|/d theta (n, m))."""
+        torch = self._torch
+        assert x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()
+        n, m = int(x.shape[0]), self.param_count()
+        eL = torch.empty(n, dtype=torch.float64, device=x.device)
+        lp = torch.empty(n, dtype=torch.float64, device=x.device)
+        ge = torch.empty((n, m), dtype=torch.float64, device=x.device)
+        gl = torch.empty((n, m), dtype=torch.float64, device=x.device)
+        self._check(self.lib.lrdmc_local_energy_grad(self._h, n, _tptr(x), _tptr(eL), _tptr(lp), _tptr(ge),
+                                                     _tptr(gl)))
+        return eL, lp, ge, gl
+
+    def weighted_rows(self, rows, w):
+        torch = self._torch
+        rows, w = rows.contiguous(), w.contiguous().to(torch.float64)
+        out = torch.empty(rows.shape[1], dtype=torch.float64, device=rows.device)
+        self._check(self.lib.lrdmc_weighted_rows(self._h, int(rows.shape[0]), int(rows.shape[1]), _tptr(rows),
+                                                 _tptr(w), _tptr(out)))
+        return out
+
     def set_timing(self, enable=True):
         self._check(self.lib.lrdmc_set_timing(self._h, 1 if enable else 0))
 
@@ -442,6 +486,52 @@ class LrdmcBatch:
         v = C.c_int64()
         self._check(self.lib.lrdmc_batch_launch_count(self._b, C.byref(v)))
         return v.value
+
+
+def _autograd_function():
+    import torch
+
+    class LocalEnergy(torch.autograd.Function):
+        """(e_L, log|Psi_G|) at configurations x as functions of theta (the
+        handle's nuclear coordinates and Jastrow parameters), with the
+        library's hand-written adjoint as the backward pass (no gradient for x)."""
+
+        @staticmethod
+        def forward(ctx, theta, x, lr):
+            th = theta.detach().cpu().numpy().astype(np.float64)
+            if not np.array_equal(th, lr.params()):
+                lr.set_params(th)
+            eL, lp, ge, gl = lr.local_energy_grad(x.detach().contiguous())
+            ctx.save_for_backward(ge, gl)
+            ctx.lr = lr
+            ctx.theta_device = theta.device
+            return eL, lp
+
+        @staticmethod
+        def backward(ctx, g_e, g_l):
+            ge, gl = ctx.saved_tensors
+            lr = ctx.lr
+            grad = None
+            if g_e is not None:
+                grad = lr.weighted_rows(ge, g_e)
+            if g_l is not None:
+                gg = lr.weighted_rows(gl, g_l)
+                grad = gg if grad is None else grad + gg
+            return grad.to(ctx.theta_device), None, None
+
+    return LocalEnergy
+
+
+_LOCAL_ENERGY = None
+
+
+def local_energy(lr, theta, x):
+    """torch.autograd entry: (e_L, log|Psi_G|) at x with gradients to theta
+    (a float64 tensor of lr.param_count() values)."""
+    global _LOCAL_ENERGY
+    if _LOCAL_ENERGY is None:
+        _LOCAL_ENERGY = _autograd_function()
+    return _LOCAL_ENERGY.apply(theta, x, lr)
 
 
 def extrapolate_a(a, E, err, order=1):

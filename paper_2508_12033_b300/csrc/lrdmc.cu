@@ -11,6 +11,7 @@
 #include <string>
 #include <vector>
 
+#include "adjoint.cuh"
 #include "batch.cuh"
 #include "branch.cuh"
 #include "common.cuh"
@@ -257,6 +258,9 @@ struct lrdmc_s {
   double* state = nullptr;
   double* alt = nullptr;
   double* cache = nullptr;       // per-walker cache blocks (layout of the precision in use)
+  std::vector<double> hR, hZ, hA, hB;   // host copies of the differentiable system parameters
+  double* gscr = nullptr;        // per-warp scratch of the adjoint kernel (allocated on first use)
+  size_t gscr_per_warp = 0;
   double* cache_alt = nullptr;
   double* stats = nullptr;
   unsigned long long* Q = nullptr;
@@ -312,6 +316,7 @@ static lrdmc_status set_kernel_smem(lrdmc_handle h, int optin) {
   CK(h, cudaFuncSetAttribute(k_propagate<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   CK(h, cudaFuncSetAttribute(k_init_walkers, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   CK(h, cudaFuncSetAttribute(k_eval_configs, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  CK(h, cudaFuncSetAttribute(k_eloc_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   CK(h, cudaFuncSetAttribute(k_propagate_m, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   CK(h, cudaFuncSetAttribute(k_init_walkers_m, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   CK(h, cudaFuncSetAttribute(k_eval_configs_m, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
@@ -745,6 +750,10 @@ lrdmc_status lrdmc_create(const lrdmc_system* sys, const lrdmc_trial_wf* wf, con
       vii += sys->Z[I] * sys->Z[J] / std::sqrt(dx * dx + dy * dy + dz * dz);
     }
   S.v_ii = vii;
+  h->hR.assign(sys->R, sys->R + 3 * (size_t)P.n_nuc);
+  h->hZ.assign(sys->Z, sys->Z + P.n_nuc);
+  h->hA.assign(wf->j1_A, wf->j1_A + P.n_nuc);
+  h->hB.assign(wf->j1_B, wf->j1_B + P.n_nuc);
   h->state = (double*)(base + P.o_state);
   h->alt = (double*)(base + P.o_alt);
   h->cache = P.cache_bytes ? (double*)(base + P.o_cache) : nullptr;
@@ -799,6 +808,11 @@ lrdmc_status lrdmc_destroy(lrdmc_handle h) {
     DeviceGuard g(h->device);
     cudaStreamSynchronize(h->stream);
     cudaFree(h->ws);
+  }
+  if (h->gscr) {
+    DeviceGuard g(h->device);
+    cudaStreamSynchronize(h->stream);
+    cudaFree(h->gscr);
   }
   delete h;
   return LRDMC_OK;
@@ -1190,6 +1204,98 @@ lrdmc_status lrdmc_fp64math(int n, const double* x, double* exp_out, double* rcp
   k_fp64math<<<std::min(1024, (n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(n, x, exp_out, rcp_out, rsqrt_out,
                                                                                 d_tab[dev]);
   return cudaGetLastError() == cudaSuccess ? LRDMC_OK : LRDMC_ERR_CUDA;
+}
+
+lrdmc_status lrdmc_param_count(lrdmc_handle h, int* n) {
+  if (!h || !n) return LRDMC_ERR_ARG;
+  *n = param_count(h->P.n_nuc);
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_get_params(lrdmc_handle h, double* theta) {
+  if (!h || !theta) return LRDMC_ERR_ARG;
+  const int nn = h->P.n_nuc;
+  for (int k = 0; k < 3 * nn; ++k) theta[k] = h->hR[k];
+  theta[3 * nn] = h->S.j2_anti;
+  theta[3 * nn + 1] = h->S.j2_par;
+  theta[3 * nn + 2] = h->S.j2_b;
+  for (int I = 0; I < nn; ++I) {
+    theta[3 * nn + 3 + I] = h->hA[I];
+    theta[4 * nn + 3 + I] = h->hB[I];
+  }
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_set_params(lrdmc_handle h, const double* theta) {
+  if (!h || !h->state || !theta) return LRDMC_ERR_ARG;
+  const Plan& P = h->P;
+  const int nn = P.n_nuc;
+  for (int k = 0; k < param_count(nn); ++k)
+    if (!std::isfinite(theta[k])) return fail(h, LRDMC_ERR_ARG, "non-finite parameter");
+  DeviceGuard g(h->device);
+  std::vector<double> x, w;
+  {
+    std::vector<double> buf;
+    lrdmc_status st = extract(h, buf);   // current positions and weights (synchronises)
+    if (st != LRDMC_OK) return st;
+    const size_t nx = (size_t)P.n_w * 3 * P.n_e;
+    x.assign(buf.begin(), buf.begin() + nx);
+    w.assign(buf.begin() + nx, buf.begin() + nx + P.n_w);
+  }
+  h->hR.assign(theta, theta + 3 * nn);
+  h->S.j2_anti = theta[3 * nn];
+  h->S.j2_par = theta[3 * nn + 1];
+  h->S.j2_b = theta[3 * nn + 2];
+  h->hA.assign(theta + 3 * nn + 3, theta + 4 * nn + 3);
+  h->hB.assign(theta + 4 * nn + 3, theta + 5 * nn + 3);
+  std::vector<float> fR(3 * nn), fA(nn), fB(nn);
+  for (int k = 0; k < 3 * nn; ++k) fR[k] = (float)h->hR[k];
+  for (int I = 0; I < nn; ++I) { fA[I] = (float)h->hA[I]; fB[I] = (float)h->hB[I]; }
+  char* dsys = (char*)h->ws + P.o_sys;
+  CK(h, cudaMemcpyAsync(dsys + P.i_R, h->hR.data(), sizeof(double) * 3 * nn, cudaMemcpyHostToDevice, h->stream));
+  CK(h, cudaMemcpyAsync(dsys + P.i_j1A, h->hA.data(), sizeof(double) * nn, cudaMemcpyHostToDevice, h->stream));
+  CK(h, cudaMemcpyAsync(dsys + P.i_j1B, h->hB.data(), sizeof(double) * nn, cudaMemcpyHostToDevice, h->stream));
+  CK(h, cudaMemcpyAsync(dsys + P.i_f_R, fR.data(), sizeof(float) * 3 * nn, cudaMemcpyHostToDevice, h->stream));
+  CK(h, cudaMemcpyAsync(dsys + P.i_f_j1A, fA.data(), sizeof(float) * nn, cudaMemcpyHostToDevice, h->stream));
+  CK(h, cudaMemcpyAsync(dsys + P.i_f_j1B, fB.data(), sizeof(float) * nn, cudaMemcpyHostToDevice, h->stream));
+  double vii = 0.0;
+  for (int I = 0; I < nn; ++I)
+    for (int J = I + 1; J < nn; ++J) {
+      const double dx = h->hR[3 * I] - h->hR[3 * J], dy = h->hR[3 * I + 1] - h->hR[3 * J + 1],
+                   dz = h->hR[3 * I + 2] - h->hR[3 * J + 2];
+      vii += h->hZ[I] * h->hZ[J] / std::sqrt(dx * dx + dy * dy + dz * dz);
+    }
+  h->S.v_ii = vii;
+  CK(h, cudaStreamSynchronize(h->stream));
+  return place_walkers(h, x.data(), w.data());
+}
+
+lrdmc_status lrdmc_local_energy_grad(lrdmc_handle h, int n, const double* x, double* eL, double* logpsi,
+                                     double* grad_eL, double* grad_logpsi) {
+  if (!h || !h->state) return LRDMC_ERR_ARG;
+  if (h->P.precision != 0) return fail(h, LRDMC_ERR_UNSUPPORTED, "gradients are implemented for precision 0");
+  if (n < 0 || n > h->P.n_w) return fail(h, LRDMC_ERR_ARG, "n must be in [0, n_w]");
+  if (n == 0) return LRDMC_OK;
+  if (!x) return fail(h, LRDMC_ERR_ARG, "NULL device pointer");
+  DeviceGuard g(h->device);
+  const Plan& P = h->P;
+  if (!h->gscr) {
+    h->gscr_per_warp = (adj_scratch_doubles(P.L, P.n_shell) + 1) / 2 * 2;
+    CK(h, cudaMalloc(&h->gscr, sizeof(double) * h->gscr_per_warp * (size_t)h->grid * h->wpb));
+  }
+  k_eloc_grad<<<walker_grid(h, n), h->wpb * 32, smem_bytes(h), h->stream>>>(
+      h->S, P.L, h->alt, x, n, h->prm.a, h->prm.node_rule, h->scr, h->gscr, h->gscr_per_warp, eL, logpsi, grad_eL,
+      grad_logpsi);
+  LAUNCHED(h);
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_weighted_rows(lrdmc_handle h, int n, int m, const double* rows, const double* w, double* out) {
+  if (!h || n < 0 || m < 1 || !rows || !w || !out) return LRDMC_ERR_ARG;
+  DeviceGuard g(h->device);
+  k_weighted_rows<<<std::max(1, std::min(1024, (m + 255) / 256)), 256, 0, h->stream>>>(n, m, rows, w, out);
+  LAUNCHED(h);
+  return LRDMC_OK;
 }
 
 lrdmc_status lrdmc_set_timing(lrdmc_handle h, int enable) {

@@ -155,8 +155,9 @@ __device__ void electron_potentials(const DevSys& S, const double q[3], double a
 // ------------------------------------------------------------ Gauss-Jordan
 // In-place inversion of the N x N matrix held as the left half of M = [A | I]
 // (N x 2N, row-major) with partial pivoting; afterwards the right half is
-// A^{-1}.  Returns true on a zero (or non-finite) pivot.
-__device__ bool warp_gauss_jordan(double* M, int N, int lane) {
+// A^{-1}.  Returns true on a zero (or non-finite) pivot.  With logdet set,
+// adds log|det A| (the sum of log|pivot|) to it.
+__device__ bool warp_gauss_jordan(double* M, int N, int lane, double* logdet = nullptr) {
   const int W2 = 2 * N;
   for (int c = 0; c < N; ++c) {
     double best = -1.0;
@@ -180,7 +181,9 @@ __device__ bool warp_gauss_jordan(double* M, int N, int lane) {
       }
     }
     __syncwarp();
-    const double inv = 1.0 / M[c * W2 + c];
+    const double piv = M[c * W2 + c];
+    const double inv = 1.0 / piv;
+    if (logdet) *logdet += log(fabs(piv));
     __syncwarp();
     for (int j = lane; j < W2; j += WARP) M[c * W2 + j] *= inv;
     __syncwarp();
@@ -249,7 +252,8 @@ __device__ __forceinline__ double sqdist(double dx, double dy, double dz) {
 
 // B^T of both spin blocks from the cached orbital values A[i][k] = phi_k(r_i)
 // (walker block in global memory).  Returns true if a block is singular.
-__device__ bool reinvert(const Layout& L, const double* __restrict__ gblk, double* sm, double* scratch, int lane) {
+__device__ bool reinvert(const Layout& L, const double* __restrict__ gblk, double* sm, double* scratch, int lane,
+                         double* logdet = nullptr) {
   bool sing = false;
   const double* cache = gblk + L.g_cache;
   double* bt = sm + L.s_bt;
@@ -264,7 +268,7 @@ __device__ bool reinvert(const Layout& L, const double* __restrict__ gblk, doubl
     }
     __threadfence_block();
     __syncwarp();
-    sing |= warp_gauss_jordan(scratch, n, lane);
+    sing |= warp_gauss_jordan(scratch, n, lane, logdet);
     for (int o = lane; o < n * n; o += WARP) {
       const int i = o / n, k = o - i * n;
       bt[bto + o] = scratch[k * 2 * n + n + i];
@@ -772,7 +776,8 @@ __device__ EvalOut eval_incr(const DevSys& S, const Layout& L, const double* __r
 // Build the orbital cache and potentials at every electron, invert both
 // Slater blocks and evaluate.  x must already be in shared memory.
 __device__ EvalOut init_walker(const DevSys& S, const Layout& L, double* __restrict__ gblk, double* sm, Scr scr,
-                               double a, int node_rule, const double* T, int lane, bool& singular) {
+                               double a, int node_rule, const double* T, int lane, bool& singular,
+                               double* logdet = nullptr) {
   double* chi5 = sm + L.s_tmp;     // scratch while no evaluation is in progress
   double* phi5 = sm + L.s_phi5;
   double* cache = gblk + L.g_cache;
@@ -793,7 +798,7 @@ __device__ EvalOut init_walker(const DevSys& S, const Layout& L, double* __restr
     __syncwarp();
   }
   __threadfence_block();
-  singular = reinvert(L, gblk, sm, scr.gj, lane);
+  singular = reinvert(L, gblk, sm, scr.gj, lane, logdet);
   compute_g(S, L, sm, scr.g, 0, L.n_e, lane);
   return eval_full<false>(S, L, gblk, sm, scr, a, node_rule, T, lane);
 }
