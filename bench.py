@@ -243,13 +243,14 @@ def run_gpu(args, rank, world):
     e2e_value = world * ws_per_step / (statistics.mean(e2e_ms) / 1e3)
     mixed = run_mixed(args, P, s, x0, lr, flush, rank) if not args.no_mixed else None
     a_scan = run_a_scan(P) if rank == 0 and not args.no_a_scan else None
+    adjoint = run_adjoint(P) if rank == 0 and not args.no_adjoint else None
     batch = None
     if rank == 0 and not args.no_batch:
         batch = {"mixed": run_batch(P, 1), "fp64": run_batch(P, 0)}
     return dict(value=value, t_total=t_total, step_ms=statistics.mean(step_ms), prop_ms=statistics.mean(prop_ms),
                 launches=launches, achieved=achieved, clocks=clk.summary(), conv_rate=conv_rate,
                 conv_moves=conv_moves, tau=tau, e2e=e2e_value, h2d=h2d, d2h=d2h, slots=slots,
-                energy=lr.energy(), mixed=mixed, imbalance=imbalance, a_scan=a_scan, batch=batch)
+                energy=lr.energy(), mixed=mixed, imbalance=imbalance, a_scan=a_scan, batch=batch, adjoint=adjoint)
 
 
 def aggregate_throughput(t_local, units_local, world, device="cpu"):
@@ -312,6 +313,28 @@ def run_a_scan(P):
     return {"system": "H atom, Slater guide exp(-0.8 r), 2048 walkers, 140 intervals x 15 hops per spacing",
             "a": a_list, "E": E_list, "err": err_list, "E0": float(coef[0]), "E0_err": float(np.sqrt(cov[0, 0])),
             "chi2": chi2, "exact_continuum": -0.5, "wall_s": wall}
+
+
+def run_adjoint(P):
+    """Hand-written adjoint: e_L, log|Psi| and their gradients with respect to
+    all 384 nuclear coordinates and the 259 Jastrow parameters of the H128 chain
+    (spacing 1.8 bohr, s + p GTO per atom, seeded MOs, a = 0.25) at 8192 seeded
+    configurations, evaluated in launches of 1024 (the handle's walkers)."""
+    import torch
+    import workloads as W
+    s = W.hydrogen_chain(128)
+    lr = P.Lrdmc(s, W.initial_walkers(s, 1024, seed=5), 0.25)
+    x = torch.tensor(W.initial_walkers(s, 8192, seed=6), device="cuda")
+    lr.local_energy_grad(x[:1024].contiguous())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    eL, lp, ge, gl = lr.local_energy_grad(x)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    finite = bool(torch.isfinite(eL).all() and torch.isfinite(ge).all() and torch.isfinite(gl).all())
+    return {"system": "H128 chain, 8192 configurations, FP64", "parameters": lr.param_count(),
+            "ms": dt * 1e3, "configurations_per_s": 8192 / dt,
+            "gradient_components_per_s": 2 * 8192 * lr.param_count() / dt, "all_finite": finite}
 
 
 def run_batch(P, precision, steps=3):
@@ -413,6 +436,7 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-a-scan", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -477,6 +501,7 @@ def main():
             "mixed": dict(res["mixed"], speedup_vs_fp64=res["mixed"]["value"] / res["value"]) if res["mixed"] else None,
             "a_scan": res["a_scan"],
             "batch": res["batch"],
+            "adjoint": res["adjoint"],
             "gpu_launches": res["launches"],
             "clocks": res["clocks"],
             "energy": {"E": res["energy"][0], "err": res["energy"][1]},

@@ -195,8 +195,9 @@ lrdmc_status lrdmc_get_params(lrdmc_handle h, double* theta);
 lrdmc_status lrdmc_set_params(lrdmc_handle h, const double* theta);
 
 /* Hand-written adjoint of the lattice-regularised local energy e_L = W - b_bar
- * (Appendix D, the handle's node rule) and of log|Psi_G| at n <= n_w
- * configurations (device x, n x n_e x 3), with respect to theta:
+ * (Appendix D, the handle's node rule) and of log|Psi_G| at n configurations
+ * (device x, n x n_e x 3; processed in launches of at most n_w), with
+ * respect to theta:
  *   eL, logpsi          device, n (or NULL)
  *   grad_eL, grad_logpsi device, n x lrdmc_param_count (or NULL)
  * A configuration with a singular Slater matrix gets NaN values.  Precision 0

@@ -1274,7 +1274,7 @@ lrdmc_status lrdmc_local_energy_grad(lrdmc_handle h, int n, const double* x, dou
                                      double* grad_eL, double* grad_logpsi) {
   if (!h || !h->state) return LRDMC_ERR_ARG;
   if (h->P.precision != 0) return fail(h, LRDMC_ERR_UNSUPPORTED, "gradients are implemented for precision 0");
-  if (n < 0 || n > h->P.n_w) return fail(h, LRDMC_ERR_ARG, "n must be in [0, n_w]");
+  if (n < 0) return fail(h, LRDMC_ERR_ARG, "n < 0");
   if (n == 0) return LRDMC_OK;
   if (!x) return fail(h, LRDMC_ERR_ARG, "NULL device pointer");
   DeviceGuard g(h->device);
@@ -1283,10 +1283,16 @@ lrdmc_status lrdmc_local_energy_grad(lrdmc_handle h, int n, const double* x, dou
     h->gscr_per_warp = (adj_scratch_doubles(P.L, P.n_shell) + 1) / 2 * 2;
     CK(h, cudaMalloc(&h->gscr, sizeof(double) * h->gscr_per_warp * (size_t)h->grid * h->wpb));
   }
-  k_eloc_grad<<<walker_grid(h, n), h->wpb * 32, smem_bytes(h), h->stream>>>(
-      h->S, P.L, h->alt, x, n, h->prm.a, h->prm.node_rule, h->scr, h->gscr, h->gscr_per_warp, eL, logpsi, grad_eL,
-      grad_logpsi);
-  LAUNCHED(h);
+  // chunks of at most n_w configurations (the alternate walker buffer holds their evaluations)
+  const int np = param_count(P.n_nuc);
+  for (int off = 0; off < n; off += P.n_w) {
+    const int c = std::min(P.n_w, n - off);
+    k_eloc_grad<<<walker_grid(h, c), h->wpb * 32, smem_bytes(h), h->stream>>>(
+        h->S, P.L, h->alt, x + (size_t)off * 3 * P.n_e, c, h->prm.a, h->prm.node_rule, h->scr, h->gscr,
+        h->gscr_per_warp, eL ? eL + off : nullptr, logpsi ? logpsi + off : nullptr,
+        grad_eL ? grad_eL + (size_t)off * np : nullptr, grad_logpsi ? grad_logpsi + (size_t)off * np : nullptr);
+    LAUNCHED(h);
+  }
   return LRDMC_OK;
 }
 

@@ -88,3 +88,19 @@ def test_autograd_entry_accumulates_weighted_gradients():
     e2, _ = P.local_energy(lr, th2, x)
     assert not torch.allclose(e2, eL)
     np.testing.assert_array_equal(lr.params(), th2.numpy())
+
+
+def test_large_system_and_chunked_configurations():
+    """24 electrons (geometry caches in global memory) against the oracle, with
+    more configurations than walkers (two launches)."""
+    import torch
+    P = lib_or_skip()
+    s = W.hydrogen_cluster(24, seed=5)
+    x = W.initial_walkers(s, 3, seed=12)
+    lr = P.Lrdmc(s, W.initial_walkers(s, 2, seed=1), 0.2)
+    eL, lp, ge, gl = lr.local_energy_grad(torch.tensor(x, device="cuda"))
+    torch.cuda.synchronize()
+    e_ref, l_ref, ge_ref, gl_ref = AD.gradients(s, x, 0.2, 0)
+    assert _rel(eL.cpu().numpy(), e_ref) < 1e-10
+    assert _rel(ge.cpu().numpy(), ge_ref) < 1e-8
+    assert _rel(gl.cpu().numpy(), gl_ref) < 1e-10
