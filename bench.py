@@ -34,6 +34,10 @@ N_PROJ = 20
 A = 0.2
 SEED = 1
 FP64_PEAK_GFLOPS = 1250.0      # nominal B300 FP64 rate (profiling recipe table)
+# DRAM bytes (read + write) of one k_propagate launch of this workload, from the
+# ncu capture summarised in profiles/k_propagate_wm4096_full.md (to be re-taken
+# whenever the kernel changes)
+PROPAGATE_TRAFFIC_BYTES = 1.168309e9 + 0.654011e9
 # FP64 pipe instructions of the functions as the propagate kernel implements
 # them: table-driven exp (10), approximate reciprocal / rsqrt plus one
 # third-order refinement (4 / 6), CUDA's erf (measured pipe cost, see profiles/).
@@ -488,7 +492,8 @@ def main():
             "electron_move_attempts_per_s": res["value"] * 6 * 16,
             "roofline": {"bound": "alu", "kernel": "k_propagate", "achieved": res["achieved"], "peak": peak,
                          "unit": "GFLOP/s (FP64 operations x 2, functions at their FP64 instruction count)",
-                         "frac": res["achieved"] / peak, "traffic": None,
+                         "frac": res["achieved"] / peak, "traffic": PROPAGATE_TRAFFIC_BYTES,
+                         "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                          "peak_source": "nominal FP64 rate of the recipe table (no FP64 entry measured)",
                          "kernel_ms": res["prop_ms"], "fp64_ops_per_walker_step": res["slots"]},
             "conventional": {"value": res["conv_rate"], "unit": "walker-steps/s", "tau": res["tau"],

@@ -428,7 +428,7 @@ __device__ void det_derivs(const Layout& L, const double* __restrict__ gblk, dou
 // Fills the incremental caches: geometry, pair distances, per-electron
 // Jastrow sums and derivatives, per-hop determinant ratio and Jastrow sums,
 // and (when scr.chi is set) the basis values at every hop.
-template <bool ROT>
+template <bool ROT, bool GG>
 __device__ EvalOut eval_full(const DevSys& S, const Layout& L, const double* __restrict__ gblk, double* sm, Scr scr,
                              double a, int node_rule, const double* T, int lane) {
   const int ne = L.n_e, nbf = L.n_bf, nn = S.n_nuc, P = L.n_hop;
@@ -436,8 +436,10 @@ __device__ EvalOut eval_full(const DevSys& S, const Layout& L, const double* __r
   const double* g = scr.g;
   double* rat = sm + L.s_rat;
   double* ej = sm + L.s_ej;
-  double* geo = scr.geo ? scr.geo : sm + L.s_geo;
-  double* pr2 = scr.pr2 ? scr.pr2 : sm + L.s_pr2;
+  // GG: a large system's geometry caches in global memory (compile-time
+  // choice, so that the shared-memory form keeps shared-memory accesses)
+  double* geo = GG ? scr.geo : sm + L.s_geo;
+  double* pr2 = GG ? scr.pr2 : sm + L.s_pr2;
   double* hD = sm + L.s_hd;
   double* hJ1 = sm + L.s_hj1;
   double* hJ2 = sm + L.s_hj2;
@@ -577,7 +579,7 @@ __device__ EvalOut eval_full(const DevSys& S, const Layout& L, const double* __r
 // term comes from the caches (scr.pt for the current positions, scr.u2 for
 // the hops) and the new term of hop d of electron i with m equals the term of
 // m's opposite hop (d ^ 1) with i, since r_i + s a e - r_m = -(r_m - s a e - r_i).
-template <bool ROT>
+template <bool ROT, bool GG>
 __device__ EvalOut eval_incr(const DevSys& S, const Layout& L, const double* __restrict__ gblk, double* sm, Scr scr,
                              int m, bool all_blocks, double a, int node_rule, const double* T, int lane) {
   const int ne = L.n_e, nbf = L.n_bf, nn = S.n_nuc, P = L.n_hop;
@@ -586,8 +588,10 @@ __device__ EvalOut eval_incr(const DevSys& S, const Layout& L, const double* __r
   const double* g = scr.g;
   double* rat = sm + L.s_rat;
   double* ej = sm + L.s_ej;
-  double* geo = scr.geo ? scr.geo : sm + L.s_geo;
-  double* pr2 = scr.pr2 ? scr.pr2 : sm + L.s_pr2;
+  // GG: a large system's geometry caches in global memory (compile-time
+  // choice, so that the shared-memory form keeps shared-memory accesses)
+  double* geo = GG ? scr.geo : sm + L.s_geo;
+  double* pr2 = GG ? scr.pr2 : sm + L.s_pr2;
   double* hD = sm + L.s_hd;
   double* hJ1 = sm + L.s_hj1;
   double* hJ2 = sm + L.s_hj2;
@@ -800,7 +804,8 @@ __device__ EvalOut init_walker(const DevSys& S, const Layout& L, double* __restr
   __threadfence_block();
   singular = reinvert(L, gblk, sm, scr.gj, lane, logdet);
   compute_g(S, L, sm, scr.g, 0, L.n_e, lane);
-  return eval_full<false>(S, L, gblk, sm, scr, a, node_rule, T, lane);
+  return L.geo_glob ? eval_full<false, true>(S, L, gblk, sm, scr, a, node_rule, T, lane)
+                    : eval_full<false, false>(S, L, gblk, sm, scr, a, node_rule, T, lane);
 }
 
 // Heat-bath choice over the kept hops (r > 0) in the order p = 6 i + d: the
@@ -1067,10 +1072,10 @@ __global__ void k_eval_configs(DevSys S, Layout L, double* __restrict__ blocks, 
 // versors and evaluates in full at its start.
 // One walker's interval (the body of k_propagate, also run by the batched
 // kernel): w is the walker index within its system, sm the warp's region.
-template <bool ROT>
-__device__ void propagate_walker(const DevSys& S, const Layout& L, double* __restrict__ state,
-                                 double* __restrict__ cache, int w, const StepParams& P, const double* T, double* sm,
-                                 const Scr& wscr, int lane) {
+template <bool ROT, bool GG>
+__device__ void propagate_walker_impl(const DevSys& S, const Layout& L, double* __restrict__ state,
+                                      double* __restrict__ cache, int w, const StepParams& P, const double* T,
+                                      double* sm, const Scr& wscr, int lane) {
   double* sc = sm + L.s_sc;
   const double ia = 1.0 / P.a;
   {
@@ -1088,7 +1093,7 @@ __device__ void propagate_walker(const DevSys& S, const Layout& L, double* __res
       if (ROT && lane == 0) interval_versors(P.seed, (uint32_t)w, P.interval, sm + L.s_v);
       __syncwarp();
       compute_g(S, L, sm, scr.g, 0, L.n_e, lane);
-      const EvalOut e0 = eval_full<ROT>(S, L, gblk, sm, scr, P.a, P.node_rule, T, lane);
+      const EvalOut e0 = eval_full<ROT, GG>(S, L, gblk, sm, scr, P.a, P.node_rule, T, lane);
       g_valid = cached = true;
       if (lane == 0) {
         sc[SC_BBAR] = e0.bbar;
@@ -1145,10 +1150,10 @@ __device__ void propagate_walker(const DevSys& S, const Layout& L, double* __res
         }
         EvalOut e;
         if (!cached) {
-          e = eval_full<ROT>(S, L, gblk, sm, scr, P.a, P.node_rule, T, lane);
+          e = eval_full<ROT, GG>(S, L, gblk, sm, scr, P.a, P.node_rule, T, lane);
           cached = true;
         } else {
-          e = eval_incr<ROT>(S, L, gblk, sm, scr, p / 6, reinv, P.a, P.node_rule, T, lane);
+          e = eval_incr<ROT, GG>(S, L, gblk, sm, scr, p / 6, reinv, P.a, P.node_rule, T, lane);
         }
         bbar = e.bbar;
         Wd = e.W;
@@ -1186,6 +1191,14 @@ __device__ void propagate_walker(const DevSys& S, const Layout& L, double* __res
       P.stamps[3 * (size_t)w + 2] = sm_id();
     }
   }
+}
+
+template <bool ROT>
+__device__ __forceinline__ void propagate_walker(const DevSys& S, const Layout& L, double* __restrict__ state,
+                                                 double* __restrict__ cache, int w, const StepParams& P,
+                                                 const double* T, double* sm, const Scr& wscr, int lane) {
+  if (L.geo_glob) propagate_walker_impl<ROT, true>(S, L, state, cache, w, P, T, sm, wscr, lane);
+  else propagate_walker_impl<ROT, false>(S, L, state, cache, w, P, T, sm, wscr, lane);
 }
 
 template <bool ROT>
