@@ -27,9 +27,14 @@ constexpr int MAX_WALKERS = 1 << 24;
 // Upper bound of resident warps that get per-warp scratch (148 SMs x 16 warps);
 // the launch grid is clamped to it.
 constexpr int SCRATCH_WARPS_CAP = 148 * 16;
-// FP64 walkers whose shared-memory layout would exceed this keep their geometry
-// caches in the cache block (see make_plan).
+// Walkers whose shared-memory layout would exceed these sizes keep their O(N^2)
+// caches in the cache block (see make_plan).  Measured on water-methane: the
+// FP64 kernel, bound by the FP64 pipe, is faster with its geometry in shared
+// memory (17.9 M against 14.8 M walker-steps/s); the latency-bound mixed kernel
+// is faster with more resident warps and its O(N^2) arrays in global memory
+// (38.9 M against 32.7 M).
 constexpr size_t GEO_GLOBAL_BYTES = 32 * 1024;
+constexpr size_t GEO_GLOBAL_BYTES_MIXED = 8 * 1024;
 
 size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
@@ -133,7 +138,7 @@ bool make_plan(const lrdmc_system* sys, const lrdmc_trial_wf* wf, const lrdmc_pa
   if (P.precision == 0 && (size_t)L.s_stride * sizeof(double) > GEO_GLOBAL_BYTES) fp64_layout(1);
   P.M = layout_mixed(L, P.n_nuc, P.n_prim);
   // a large mixed-precision system keeps its O(N^2) arrays in global memory
-  if (P.precision == 1 && (size_t)P.M.stride * sizeof(float) > GEO_GLOBAL_BYTES)
+  if (P.precision == 1 && (size_t)P.M.stride * sizeof(float) > GEO_GLOBAL_BYTES_MIXED)
     P.M = layout_mixed(L, P.n_nuc, P.n_prim, 1);
   if (P.precision == 1) L.c_stride = round_up((P.M.c_floats + 1) / 2, 16);
   P.smem_per_warp = P.precision == 0 ? (size_t)L.s_stride * sizeof(double) : (size_t)P.M.stride * sizeof(float);
