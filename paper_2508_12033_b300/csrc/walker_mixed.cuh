@@ -23,8 +23,9 @@
 // exp(x) - 1 in FP32: Taylor polynomial of degree 6 for |x| < 1/4 (truncation
 // < 2e-8 relative), exp(x) - 1 from the hardware exponential otherwise.
 // Walker block: B^T as doubles (as in the FP64 layout); the cache region holds
-// the FP64 orbital values [n_e][n_max] followed by FP32 gradient/Laplacian
-// rows [n_e][4][n_max].  As in the FP64 kernels, the caches of the incremental
+// the FP64 orbital values [n_e][n_max] followed by the gradient/Laplacian
+// rows [n_e][4][n_max] (evaluated in FP32, stored as doubles so that the FP64
+// determinant derivatives read them without conversions).  As in the FP64 kernels, the caches of the incremental
 // evaluation persist in a per-walker cache block across branching intervals,
 // and pair terms are swapped from cached values rather than recomputed.
 #pragma once
@@ -41,8 +42,8 @@ namespace lrdmc {
 // hops and is copied to / from the walker's cache block.
 struct LayoutM {
   int sc, x, bt, phiv, chiv, u, row, xo;                               // doubles
-  int dd, hj2;                                                         // doubles, kept
-  int dl, ej, ep, geo, rt1, pair, hcur, hdm, hj1, dph;                 // floats, kept
+  int dd;                                                              // doubles, kept
+  int dl, ej, ep, geo, rt1, pair, hcur, hdm, hj1, hj2, dph;            // floats, kept
   int xf, xfo, b32, chi5, phi5, tmp;                                   // floats
   int geo_st, rt1_st, pair_st, hcur_st, stride;
   int mir, mir_end;
@@ -73,7 +74,6 @@ __host__ __device__ inline LayoutM layout_mixed(const Layout& L, int n_nuc, int 
   M.xo = o; o += 2 * 4;
   M.mir = o;
   M.dd = o; o += 2 * 4 * ne;
-  M.hj2 = o; o += 2 * P;
   M.dl = o; o += P;
   M.ej = o; o += 5 * ne;
   M.ep = o; o += 2 * ne;
@@ -95,6 +95,7 @@ __host__ __device__ inline LayoutM layout_mixed(const Layout& L, int n_nuc, int 
   M.hcur = o; o += glob ? 0 : sz_hcur;
   M.hdm = o; o += P;
   M.hj1 = o; o += P;
+  M.hj2 = o; o += P;
   M.dph = o; o += glob ? 0 : sz_dph;
   o = round_up(o, 2);
   M.mir_end = o;
@@ -183,8 +184,8 @@ __device__ __forceinline__ MArr marr(const LayoutM& M, float* sm, const ScrM& sc
 }
 
 __device__ __forceinline__ double* cache_val(const Layout& L, double* gblk) { return gblk + L.g_cache; }
-__device__ __forceinline__ float* cache_der(const Layout& L, double* gblk) {
-  return (float*)(gblk + L.g_cache + L.n_e * L.n_max);
+__device__ __forceinline__ double* cache_der(const Layout& L, double* gblk) {
+  return gblk + L.g_cache + L.n_e * L.n_max;
 }
 
 // exp(x) - 1 in FP32 (see the header comment).
@@ -433,8 +434,10 @@ __device__ EvalOut assemble_m(const DevSys& S, const Layout& L, const LayoutM& M
   for (int i = lane; i < ne; i += WARP)
     for (int d = 0; d < 6; ++d) has_node |= dl[6 * i + d] < -1.f;
   const bool any_node = __any_sync(FULL, has_node);
-  double kept = 0.0, negs = 0.0, nuopt = 0.0, vee = 0.0;
-  int nnode = 0;
+  // FP64 accumulators: kept ratios, node-crossing ratios, and the potential
+  // part of W (sum of nu_opt and the e-e terms)
+  double kept = 0.0, negs = 0.0, pot = 0.0;
+  int nnode = 0, nkept = 0;
   const double ia2 = 1.0 / (a * a);
   for (int i = lane; i < ne; i += WARP) {
     float sd = 0.f, skd = 0.f, sneg = 0.f;
@@ -446,37 +449,39 @@ __device__ EvalOut assemble_m(const DevSys& S, const Layout& L, const LayoutM& M
       if (x1 > -1.f) { skd += x1; ++nk; }
       if (x1 < -1.f) { sneg -= 1.f + x1; node = true; }
     }
-    kept += (double)nk + (double)skd;
+    nkept += nk;
+    kept += (double)skd;
     negs += (double)sneg;
     const float* q = ej + 5 * i;
     const double* dv = dd + 4 * i;
-    const double gJx = q[0], gJy = q[1], gJz = q[2];
-    const double lap = dv[3] + 2.0 * (dv[0] * gJx + dv[1] * gJy + dv[2] * gJz) + (double)q[3] +
-                       (gJx * gJx + gJy * gJy + gJz * gJz);
+    // Jastrow part of the Laplacian in FP32, determinant parts in FP64
+    const float jl = fmaf(q[0], q[0], fmaf(q[1], q[1], fmaf(q[2], q[2], q[3])));
+    const double cross = dv[0] * (double)q[0] + dv[1] * (double)q[1] + dv[2] * (double)q[2];
+    const double lap = dv[3] + 2.0 * cross + (double)jl;
     const double nu_zv = (double)ep[2 * i] + 0.5 * ((double)sd * ia2 - lap);
     bool apply;
     if (node_rule == 0) apply = node;
     else if (node_rule == 1) apply = any_node;
     else if (node_rule == 2) apply = true;
     else apply = false;
-    nuopt += apply ? fmax(nu_zv, (double)ep[2 * i + 1]) : nu_zv;
-    vee += (double)q[4];
+    pot += (apply ? fmax(nu_zv, (double)ep[2 * i + 1]) : nu_zv) + (double)q[4];
     nnode += node ? 1 : 0;
   }
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
     kept += __shfl_xor_sync(FULL, kept, o);
     negs += __shfl_xor_sync(FULL, negs, o);
-    nuopt += __shfl_xor_sync(FULL, nuopt, o);
-    vee += __shfl_xor_sync(FULL, vee, o);
+    pot += __shfl_xor_sync(FULL, pot, o);
     nnode += __shfl_xor_sync(FULL, nnode, o);
+    nkept += __shfl_xor_sync(FULL, nkept, o);
   }
+  kept += (double)nkept;
   EvalOut e;
   const double i2a2 = 0.5 * ia2;
   e.kept = kept;
   e.bbar = kept * i2a2;
   e.vsf = negs * i2a2;
-  e.W = 3.0 * ne * ia2 + nuopt + vee + S.v_ii + e.vsf;
+  e.W = 3.0 * ne * ia2 + pot + S.v_ii + e.vsf;
   e.eL = e.W - e.bbar;
   e.n_node = nnode;
   return e;
@@ -486,15 +491,15 @@ __device__ EvalOut assemble_m(const DevSys& S, const Layout& L, const LayoutM& M
 // derivative cache and FP64 B.
 __device__ void det_derivs_m(const Layout& L, const LayoutM& M, double* gblk, float* sm, int e0, int e1, int lane) {
   const double* bt = (const double*)(sm + M.bt);
-  const float* der = cache_der(L, gblk);
+  const double* der = cache_der(L, gblk);
   double* dd = (double*)(sm + M.dd);
   for (int o = lane + 4 * e0; o < 4 * e1; o += WARP) {
     const int i = o >> 2, c = o & 3;
     const SpinRef sr = spin_ref(L, i);
     const double* brow = bt + sr.bt_off + sr.ii * sr.n;
-    const float* ce = der + (i * 4 + c) * L.n_max;
+    const double* ce = der + (i * 4 + c) * L.n_max;
     double acc = 0.0;
-    for (int k = 0; k < sr.n; ++k) acc = fma((double)ce[k], brow[k], acc);
+    for (int k = 0; k < sr.n; ++k) acc = fma(ce[k], brow[k], acc);
     dd[o] = acc;
   }
 }
@@ -571,7 +576,7 @@ __device__ EvalOut eval_full_m(const DevSys& S, const Layout& L, const LayoutM& 
   const float* hcur = AR.hcur;
   float* hdm = sm + M.hdm;
   float* hj1 = sm + M.hj1;
-  double* hj2 = (double*)(sm + M.hj2);
+  float* hj2 = sm + M.hj2;
   const float bj = (float)S.j2_b;
   // (1) current configuration, G lanes per electron
   {
@@ -636,12 +641,12 @@ __device__ EvalOut eval_full_m(const DevSys& S, const Layout& L, const LayoutM& 
     }
     const float xia = xf[3 * i + ax];
     const float* pr = pair + i * M.pair_st;
-    double J2 = 0.0;
+    float J2 = 0.f;
     for (int j = 0; j < ne; ++j) {
       if (j == i) continue;
       const float del = fmaf(s2a, xia - xf[3 * j + ax], a2f);
       const float v = pade_delta(pr[2 * j], pr[2 * j + 1], del, (float)pair_c(S, L, i, j), bj);
-      J2 += (double)v;
+      J2 += v;
       if (scr.u2) scr.u2[(size_t)j * P + p] = v;
     }
     hj1[p] = J1;
@@ -654,7 +659,7 @@ __device__ EvalOut eval_full_m(const DevSys& S, const Layout& L, const LayoutM& 
   det_diffs(L, M, sm, AR.dph, 0, P, lane);
   for (int p = lane; p < P; p += WARP) {
     const float D = hdm[p];
-    const float J = expm1_fast(hj1[p] + (float)hj2[p]);
+    const float J = expm1_fast(hj1[p] + hj2[p]);
     dl[p] = fmaf(D, J, D + J);
   }
   __syncwarp();
@@ -682,7 +687,7 @@ __device__ EvalOut eval_incr_m(const DevSys& S, const Layout& L, const LayoutM& 
   float* pair = AR.pair;
   float* hdm = sm + M.hdm;
   float* hj1 = sm + M.hj1;
-  double* hj2 = (double*)(sm + M.hj2);
+  float* hj2 = sm + M.hj2;
   float* tmp = sm + M.tmp;
   const float bj = (float)S.j2_b;
   // (A) electron m from scratch (geometry, pair data both ways, primitives,
@@ -795,14 +800,13 @@ __device__ EvalOut eval_incr_m(const DevSys& S, const Layout& L, const LayoutM& 
   __threadfence_block();
   __syncwarp();
   {
-    // sums over partners of each of m's hops: four lanes per hop; the pair sum in FP64
+    // sums over partners of each of m's hops: four lanes per hop
     const int d = lane >> 2, sub = lane & 3;
-    float J1 = 0.f;
-    double J2 = 0.0;
+    float J1 = 0.f, J2 = 0.f;
     if (d < 6)
       for (int t = sub; t < per; t += 4) {
         const float v = tmp[d * per + t];
-        if (t < ne - 1) J2 += (double)v;
+        if (t < ne - 1) J2 += v;
         else J1 += v;
       }
     J1 += __shfl_xor_sync(FULL, J1, 1);
@@ -824,7 +828,7 @@ __device__ EvalOut eval_incr_m(const DevSys& S, const Layout& L, const LayoutM& 
     const int d = p - 6 * i;
     const float vn = tmp[(d ^ 1) * per + (i < m ? i : i - 1)];
     float* u = scr.u2 + (size_t)m * P + p;
-    hj2[p] += (double)vn - (double)*u;
+    hj2[p] += vn - *u;
     *u = vn;
   }
   __threadfence_block();
@@ -832,7 +836,7 @@ __device__ EvalOut eval_incr_m(const DevSys& S, const Layout& L, const LayoutM& 
   // (G) all hops, as r - 1
   for (int p = lane; p < P; p += WARP) {
     const float D = hdm[p];
-    const float J = expm1_fast(hj1[p] + (float)hj2[p]);
+    const float J = expm1_fast(hj1[p] + hj2[p]);
     dl[p] = fmaf(D, J, D + J);
   }
   __threadfence_block();
@@ -843,7 +847,7 @@ __device__ EvalOut eval_incr_m(const DevSys& S, const Layout& L, const LayoutM& 
 __device__ EvalOut init_walker_m(const DevSys& S, const Layout& L, const LayoutM& M, double* gblk, float* sm,
                                  const ScrM& scr, double a, int node_rule, const double* T, int lane, bool& singular) {
   double* val = cache_val(L, gblk);
-  float* der = cache_der(L, gblk);
+  double* der = cache_der(L, gblk);
   const double* x = (const double*)(sm + M.x);
   float* xf = sm + M.xf;
   float* ep = sm + M.ep;
@@ -908,7 +912,7 @@ __device__ void apply_hop_m(const DevSys& S, const Layout& L, const LayoutM& M, 
   float* xf = sm + M.xf;
   double* bt = (double*)(sm + M.bt);
   double* val = cache_val(L, gblk);
-  float* der = cache_der(L, gblk);
+  double* der = cache_der(L, gblk);
   const double* phiv = (const double*)(sm + M.phiv);
   const float* phi5 = sm + M.phi5;
   double* f = (double*)(sm + M.u);
