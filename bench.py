@@ -37,7 +37,7 @@ FP64_PEAK_GFLOPS = 1250.0      # nominal B300 FP64 rate (profiling recipe table)
 # DRAM bytes (read + write) of one k_propagate launch of this workload, from the
 # ncu capture summarised in profiles/k_propagate_wm4096_full.md (to be re-taken
 # whenever the kernel changes)
-PROPAGATE_TRAFFIC_BYTES = 1.168309e9 + 0.654011e9
+PROPAGATE_TRAFFIC_BYTES = 1.175490e9 + 0.657476e9
 # FP64 pipe instructions of the functions as the propagate kernel implements
 # them: table-driven exp (10), approximate reciprocal / rsqrt plus one
 # third-order refinement (4 / 6), CUDA's erf (measured pipe cost, see profiles/).
@@ -56,7 +56,8 @@ def algorithmic_ops_per_walker_step(n_e, n_nuc, n_bf, n_prim, n_sig, n_s_shell, 
     Move: basis value/gradient/Laplacian at the new position (per primitive an
     exponential + 10), the 5 n_sig x n_bf contraction, Sherman-Morrison
     (2 n_sig^2) and the n_sig x n_bf update of g, the potentials (per nucleus
-    rsqrt + erf + 8).  Evaluation: m's pair and nucleus terms with derivatives
+    erf + 8; the 1/r is shared with m's one-body Jastrow term).  Evaluation:
+    m's pair and nucleus terms with derivatives
     and the partner electrons' swapped terms (Pade + 14 per partner, 14 per
     swap), determinant derivatives of m's block (4 n_sig^2), basis values at
     m's six hops (exponential + 2 per primitive, 1 / 4 per s / p shell) and
@@ -66,7 +67,7 @@ def algorithmic_ops_per_walker_step(n_e, n_nuc, n_bf, n_prim, n_sig, n_s_shell, 
     assembly (20 per electron)."""
     per = n_e - 1 + n_nuc
     move = (n_prim * (OP_EXP + 10) + 5 * n_bf * n_sig + 2 * n_sig * n_sig + n_sig * n_bf
-            + n_nuc * (OP_RSQ + OP_ERF + 8))
+            + n_nuc * (OP_ERF + 8))
     evaluation = (per * (OP_PADE + 14) + (n_e - 1) * 14 + 4 * n_sig * n_sig
                   + 6 * (n_prim * (OP_EXP + 2) + n_s_shell + 4 * n_p_shell) + 6 * per * (OP_PADE_VALUE + 3)
                   + 6 * n_sig * n_bf + 6 * (n_e - 1) * 2 + 6 * n_e * (OP_EXP + 3) + 20 * n_e)
@@ -230,20 +231,30 @@ def run_gpu(args, rank, world):
         lr.branch()
     lr.set_timing(False)
     # end to end through the public API with host buffers: upload the walkers
-    # from pinned host memory, one interval + branching, read them back
-    xh = torch.from_numpy(lr.get_walkers()["x"]).pin_memory()
+    # from pinned host memory (re-initialising them), one interval + branching,
+    # read back the population (positions, weights, b_bar / V_sf / W / e_L,
+    # status, moves) into pinned host memory
+    def pinned(shape, dt):
+        return torch.empty(shape, dtype=dt).pin_memory().numpy()
+    ne = s.n_elec
+    host = dict(x=pinned((N_W, ne, 3), torch.float64), w=pinned((N_W,), torch.float64),
+                ev=pinned((N_W, 4), torch.float64), status=pinned((N_W,), torch.int32).view(np.uint32),
+                moves=pinned((N_W,), torch.int32))
+    xh = pinned((N_W, ne, 3), torch.float64)
+    xh[:] = lr.get_walkers(("x",))["x"]
+    fields = tuple(host)
     e2e_ms = []
     for k in range(max(2, args.steps // 2)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        lr.set_walkers(xh.numpy())
+        lr.set_walkers(xh)
         lr.propagate(P.LOAD_BALANCED, n_proj=N_PROJ)
         lr.branch()
-        out = lr.get_walkers()
+        lr.get_walkers(fields, out=host)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-        xh.copy_(torch.from_numpy(out["x"]))
-    h2d = N_W * s.n_elec * 3 * 8
-    d2h = 8 * (N_W * (3 * s.n_elec + 6 * s.n_elec + 7))
+        xh[:] = host["x"]
+    h2d = xh.nbytes
+    d2h = sum(a.nbytes for a in host.values())
     e2e_value = world * ws_per_step / (statistics.mean(e2e_ms) / 1e3)
     mixed = run_mixed(args, P, s, x0, lr, flush, rank) if not args.no_mixed else None
     a_scan = run_a_scan(P) if rank == 0 and not args.no_a_scan else None

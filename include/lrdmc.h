@@ -239,7 +239,9 @@ lrdmc_status lrdmc_history(lrdmc_handle h, int cap, int* n, double* wbar, double
 lrdmc_status lrdmc_get_e0(lrdmc_handle h, double* e0);
 lrdmc_status lrdmc_set_e0(lrdmc_handle h, double e0);
 
-/* Copy walker state to the host (synchronises).  Any pointer may be NULL.
+/* Copy walker state to the host (synchronises).  Any pointer may be NULL, and
+ * a NULL field is neither gathered nor copied; each requested field is copied
+ * straight into the caller's buffer (pinned buffers take the fast DMA path).
  *   x (n_w x n_e x 3), w (n_w), ev (n_w x 4: b_bar, V_sf, W, e_L at the current
  *   configuration), ratios (n_w x 6 n_e: Psi_G(x_p)/Psi_G(x)), status (n_w),
  *   moves (n_w: hops in the last interval). */

@@ -255,15 +255,29 @@ class Lrdmc:
                                            out["status_or"].ctypes.data_as(C.POINTER(C.c_uint32))))
         return out
 
-    def get_walkers(self):
+    WALKER_FIELDS = ("x", "w", "ev", "ratios", "status", "moves")
+
+    def get_walkers(self, fields=WALKER_FIELDS, out=None):
+        """Walker fields on the host: x (n_w, n_e, 3), w, ev (b_bar, V_sf, W, e_L),
+        ratios (n_w, n_e, 6), status, moves.  ``fields`` selects what is copied;
+        ``out`` may supply destination arrays (e.g. views of pinned memory) by
+        name, which are filled in place."""
         n, ne = self.n_w, self.n_e
-        out = dict(x=np.zeros((n, ne, 3)), w=np.zeros(n), ev=np.zeros((n, 4)), ratios=np.zeros((n, ne, 6)),
-                   status=np.zeros(n, np.uint32), moves=np.zeros(n, np.int32))
-        self._check(self.lib.lrdmc_get_walkers(self._h, _dptr(out["x"]), _dptr(out["w"]), _dptr(out["ev"]),
-                                               _dptr(out["ratios"]),
-                                               out["status"].ctypes.data_as(C.POINTER(C.c_uint32)),
-                                               out["moves"].ctypes.data_as(C.POINTER(C.c_int32))))
-        return out
+        shapes = dict(x=((n, ne, 3), np.float64), w=((n,), np.float64), ev=((n, 4), np.float64),
+                      ratios=((n, ne, 6), np.float64), status=((n,), np.uint32), moves=((n,), np.int32))
+        res = {}
+        for f in fields:
+            shp, dt = shapes[f]
+            a = (out or {}).get(f)
+            if a is None:
+                a = np.zeros(shp, dt)
+            assert a.shape == shp and a.dtype == dt and a.flags.c_contiguous
+            res[f] = a
+        ptr = lambda f, t: res[f].ctypes.data_as(C.POINTER(t)) if f in res else None
+        self._check(self.lib.lrdmc_get_walkers(self._h, ptr("x", C.c_double), ptr("w", C.c_double),
+                                               ptr("ev", C.c_double), ptr("ratios", C.c_double),
+                                               ptr("status", C.c_uint32), ptr("moves", C.c_int32)))
+        return res
 
     def set_walkers(self, x, w=None):
         x = np.ascontiguousarray(x, dtype=np.float64)

@@ -24,9 +24,9 @@ namespace {
 
 constexpr size_t ALIGN = 256;
 constexpr int MAX_WALKERS = 1 << 24;
-// Upper bound of resident warps that get per-warp scratch (148 SMs x 16 warps);
+// Upper bound of resident warps that get per-warp scratch (148 SMs x 32 warps);
 // the launch grid is clamped to it.
-constexpr int SCRATCH_WARPS_CAP = 148 * 16;
+constexpr int SCRATCH_WARPS_CAP = 148 * 32;
 // Walkers whose shared-memory layout would exceed these sizes keep their O(N^2)
 // caches in the cache block (see make_plan).  Measured on water-methane: the
 // FP64 kernel, bound by the FP64 pipe, is faster with its geometry in shared
@@ -358,18 +358,30 @@ static lrdmc_status place_walkers(lrdmc_handle h, const double* x, const double*
   return LRDMC_OK;
 }
 
-// Copy compact walker fields to host vectors (uses the alternate buffer).
-static lrdmc_status extract(lrdmc_handle h, std::vector<double>& buf) {
+// Copy the requested walker fields to host memory (any pointer may be null):
+// one gather kernel into the alternate buffer, one copy per field straight
+// into the caller's buffer, then a synchronisation.
+static lrdmc_status fetch(lrdmc_handle h, double* x, double* w, double* ev, double* ratios, uint32_t* status,
+                          int32_t* moves) {
   const Plan& P = h->P;
   const size_t nx = (size_t)P.n_w * 3 * P.n_e, nr = (size_t)P.n_w * P.L.n_hop, nw = P.n_w;
-  const size_t tot = nx + nr + 7 * nw;
-  buf.resize(tot);
   double* b = h->alt;
-  k_extract<<<std::min(1024, (int)((tot + 255) / 256)), 256, 0, h->stream>>>(
-      P.L, h->state, P.n_w, b, b + nx, b + nx + nw, b + nx + 5 * nw, b + nx + 5 * nw + nr,
-      b + nx + 6 * nw + nr);
+  double* dx = x ? b : nullptr;
+  double* dw = w ? b + nx : nullptr;
+  double* dev = ev ? b + nx + nw : nullptr;
+  double* drat = ratios ? b + nx + 5 * nw : nullptr;
+  uint32_t* dst = status ? (uint32_t*)(b + nx + 5 * nw + nr) : nullptr;
+  int32_t* dmv = moves ? (int32_t*)(b + nx + 5 * nw + nr) + nw : nullptr;
+  const size_t tot = (x ? nx : 0) + (ratios ? nr : 0) + nw;
+  k_extract<<<std::max(1, std::min(1024, (int)((tot + 255) / 256))), 256, 0, h->stream>>>(P.L, h->state, P.n_w, dx,
+                                                                                        dw, dev, drat, dst, dmv);
   LAUNCHED(h);
-  CK(h, cudaMemcpyAsync(buf.data(), b, sizeof(double) * tot, cudaMemcpyDeviceToHost, h->stream));
+  if (x) CK(h, cudaMemcpyAsync(x, dx, sizeof(double) * nx, cudaMemcpyDeviceToHost, h->stream));
+  if (w) CK(h, cudaMemcpyAsync(w, dw, sizeof(double) * nw, cudaMemcpyDeviceToHost, h->stream));
+  if (ev) CK(h, cudaMemcpyAsync(ev, dev, sizeof(double) * 4 * nw, cudaMemcpyDeviceToHost, h->stream));
+  if (ratios) CK(h, cudaMemcpyAsync(ratios, drat, sizeof(double) * nr, cudaMemcpyDeviceToHost, h->stream));
+  if (status) CK(h, cudaMemcpyAsync(status, dst, sizeof(uint32_t) * nw, cudaMemcpyDeviceToHost, h->stream));
+  if (moves) CK(h, cudaMemcpyAsync(moves, dmv, sizeof(int32_t) * nw, cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
   return LRDMC_OK;
 }
@@ -797,13 +809,12 @@ lrdmc_status lrdmc_create(const lrdmc_system* sys, const lrdmc_trial_wf* wf, con
   h->grid = std::max(1, std::min(best_bps * h->num_sms, P.scratch_warps / h->wpb));
   st = place_walkers(h, x0, nullptr);
   if (st != LRDMC_OK) return st;
-  std::vector<double> buf;
-  st = extract(h, buf);
+  std::vector<double> ev(4 * (size_t)P.n_w);
+  st = fetch(h, nullptr, nullptr, ev.data(), nullptr, nullptr, nullptr);
   if (st != LRDMC_OK) return st;
-  const size_t nx = (size_t)P.n_w * 3 * P.n_e, nw = P.n_w;
   double s = 0.0;
-  for (size_t a = 0; a < nw; ++a) s += buf[nx + nw + 4 * a + 3];
-  h->E0 = s / (double)nw;
+  for (int a = 0; a < P.n_w; ++a) s += ev[4 * (size_t)a + 3];
+  h->E0 = s / (double)P.n_w;
   return LRDMC_OK;
 }
 
@@ -985,20 +996,7 @@ lrdmc_status lrdmc_get_walkers(lrdmc_handle h, double* x, double* w, double* ev,
                                int32_t* moves) {
   if (!h || !h->state) return LRDMC_ERR_ARG;
   DeviceGuard g(h->device);
-  std::vector<double> buf;
-  lrdmc_status st = extract(h, buf);
-  if (st != LRDMC_OK) return st;
-  const Plan& P = h->P;
-  const size_t nx = (size_t)P.n_w * 3 * P.n_e, nr = (size_t)P.n_w * P.L.n_hop, nw = P.n_w;
-  if (x) memcpy(x, buf.data(), nx * sizeof(double));
-  if (w) memcpy(w, buf.data() + nx, nw * sizeof(double));
-  if (ev) memcpy(ev, buf.data() + nx + nw, 4 * nw * sizeof(double));
-  if (ratios) memcpy(ratios, buf.data() + nx + 5 * nw, nr * sizeof(double));
-  for (size_t a = 0; a < nw; ++a) {
-    if (status) status[a] = (uint32_t)buf[nx + 5 * nw + nr + a];
-    if (moves) moves[a] = (int32_t)buf[nx + 6 * nw + nr + a];
-  }
-  return LRDMC_OK;
+  return fetch(h, x, w, ev, ratios, status, moves);
 }
 
 lrdmc_status lrdmc_set_walkers(lrdmc_handle h, const double* x, const double* w) {
@@ -1238,14 +1236,10 @@ lrdmc_status lrdmc_set_params(lrdmc_handle h, const double* theta) {
   for (int k = 0; k < param_count(nn); ++k)
     if (!std::isfinite(theta[k])) return fail(h, LRDMC_ERR_ARG, "non-finite parameter");
   DeviceGuard g(h->device);
-  std::vector<double> x, w;
+  std::vector<double> x((size_t)P.n_w * 3 * P.n_e), w(P.n_w);
   {
-    std::vector<double> buf;
-    lrdmc_status st = extract(h, buf);   // current positions and weights (synchronises)
+    lrdmc_status st = fetch(h, x.data(), w.data(), nullptr, nullptr, nullptr, nullptr);   // synchronises
     if (st != LRDMC_OK) return st;
-    const size_t nx = (size_t)P.n_w * 3 * P.n_e;
-    x.assign(buf.begin(), buf.begin() + nx);
-    w.assign(buf.begin() + nx, buf.begin() + nx + P.n_w);
   }
   h->hR.assign(theta, theta + 3 * nn);
   h->S.j2_anti = theta[3 * nn];
@@ -1323,8 +1317,8 @@ lrdmc_status lrdmc_interval_timing(lrdmc_handle h, double out[6]) {
   std::vector<unsigned long long> st(3 * (size_t)n);
   CK(h, cudaMemcpyAsync(st.data(), h->stamps, sizeof(unsigned long long) * st.size(), cudaMemcpyDeviceToHost,
                         h->stream));
-  std::vector<double> buf;
-  lrdmc_status s = extract(h, buf);   // synchronises
+  std::vector<int32_t> mvs(n);
+  lrdmc_status s = fetch(h, nullptr, nullptr, nullptr, nullptr, nullptr, mvs.data());   // synchronises
   if (s != LRDMC_OK) return s;
   unsigned long long t0 = ~0ull, t1 = 0;
   double sum = 0.0, mx = 0.0;
@@ -1337,10 +1331,9 @@ lrdmc_status lrdmc_interval_timing(lrdmc_handle h, double out[6]) {
   }
   const double span = (double)(t1 - t0) * 1e-6;
   const int resident = std::min(n, h->grid * h->wpb);
-  const size_t nx = (size_t)n * 3 * h->P.n_e, nr = (size_t)n * h->P.L.n_hop;
   double mv = 0.0, mvmax = 0.0;
   for (int a = 0; a < n; ++a) {
-    const double m = buf[nx + 6 * (size_t)n + nr + a];
+    const double m = mvs[a];
     mv += m;
     mvmax = std::max(mvmax, m);
   }

@@ -94,6 +94,45 @@ __device__ __forceinline__ int split_factor(int n_out, int len) {
   return best;
 }
 
+// Warp sums of several values per lane by recursive halving: at each of the
+// first levels a lane keeps half of its values, adds the partner's copy of that
+// half and hands over the other half, so that k values cost k - 1 additions
+// plus one per remaining level instead of k per level.
+// warp_sum8: lane l returns the warp total of v[(l >> 2) & 7].
+__device__ __forceinline__ double warp_sum8(const double v[8], int lane) {
+  const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4;
+  double w[4], u[2];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const double keep = h4 ? v[j + 4] : v[j], give = h4 ? v[j] : v[j + 4];
+    w[j] = keep + __shfl_xor_sync(FULL, give, 16);
+  }
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const double keep = h3 ? w[j + 2] : w[j], give = h3 ? w[j] : w[j + 2];
+    u[j] = keep + __shfl_xor_sync(FULL, give, 8);
+  }
+  double t = (h2 ? u[1] : u[0]) + __shfl_xor_sync(FULL, h2 ? u[0] : u[1], 4);
+  t += __shfl_xor_sync(FULL, t, 2);
+  t += __shfl_xor_sync(FULL, t, 1);
+  return t;
+}
+// warp_sum4: lane l returns the warp total of v[(l >> 3) & 3].
+__device__ __forceinline__ double warp_sum4(const double v[4], int lane) {
+  const bool h4 = lane & 16, h3 = lane & 8;
+  double w[2];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const double keep = h4 ? v[j + 2] : v[j], give = h4 ? v[j] : v[j + 2];
+    w[j] = keep + __shfl_xor_sync(FULL, give, 16);
+  }
+  double t = (h3 ? w[1] : w[0]) + __shfl_xor_sync(FULL, h3 ? w[0] : w[1], 8);
+  t += __shfl_xor_sync(FULL, t, 4);
+  t += __shfl_xor_sync(FULL, t, 2);
+  t += __shfl_xor_sync(FULL, t, 1);
+  return t;
+}
+
 // Orbital value/gradient/Laplacian of the first n_sig orbitals at point q:
 // phi5[c * n_max + k].  Warp-cooperative; chi5 is scratch of 5 n_bf doubles.
 __device__ void orbital_derivs(const DevSys& S, const Layout& L, const double q[3], int n_sig, double* chi5,
@@ -150,6 +189,46 @@ __device__ void electron_potentials(const DevSys& S, const double q[3], double a
     nu += __shfl_xor_sync(FULL, nu, o);
     nucap += __shfl_xor_sync(FULL, nucap, o);
   }
+}
+
+// Bare and capped potentials of every electron (ep[2 i], ep[2 i + 1]): G lanes
+// per electron (the largest power of two with n_e G <= 32), each taking every
+// G-th nucleus, combined by shuffles.
+__device__ void all_potentials(const DevSys& S, const Layout& L, const double* x, double* ep, double a, double ia,
+                               int lane) {
+  const int ne = L.n_e;
+  int G = 1;
+  while (G < WARP && ne * 2 * G <= WARP) G <<= 1;
+  const double a2 = a * a;
+  for (int base = 0; base < ne; base += WARP / G) {
+    const int e = base + lane / G, sub = lane % G;
+    double nu = 0.0, nucap = 0.0;
+    if (e < ne)
+      for (int I = sub; I < S.n_nuc; I += G) {
+        const double dx = x[3 * e] - __ldg(S.R + 3 * I), dy = x[3 * e + 1] - __ldg(S.R + 3 * I + 1),
+                     dz = x[3 * e + 2] - __ldg(S.R + 3 * I + 2);
+        const double s = fma(dz, dz, fma(dy, dy, dx * dx));
+        const double ir = rsqrt_nr(s);
+        const double Z = __ldg(S.Z + I);
+        if (__ldg(S.kind + I) == 0) {
+          nu -= Z * ir;
+          nucap -= s >= a2 ? Z * ir : Z * ia;
+        } else {
+          const double v = -Z * erf(s * ir * __ldg(S.irc + I)) * ir;
+          nu += v;
+          nucap += v;
+        }
+      }
+    for (int o = G >> 1; o; o >>= 1) {
+      nu += __shfl_xor_sync(FULL, nu, o);
+      nucap += __shfl_xor_sync(FULL, nucap, o);
+    }
+    if (e < ne && sub == 0) {
+      ep[2 * e] = nu;
+      ep[2 * e + 1] = nucap;
+    }
+  }
+  __syncwarp();
 }
 
 // ------------------------------------------------------------ Gauss-Jordan
@@ -306,9 +385,9 @@ struct EvalOut {
 struct Pair {
   double u, up, upp, ir;
 };
-__device__ __forceinline__ Pair pade(double s, double c, double b) {
+__device__ __forceinline__ Pair pade_ir(double ir, double c, double b) {
   Pair p;
-  p.ir = rsqrt_nr(s);
+  p.ir = ir;
   const double q = rcp_nr(p.ir + b);
   const double t = p.ir * q;
   p.u = c * q;
@@ -316,6 +395,7 @@ __device__ __forceinline__ Pair pade(double s, double c, double b) {
   p.upp = -2.0 * b * p.up * t;
   return p;
 }
+__device__ __forceinline__ Pair pade(double s, double c, double b) { return pade_ir(rsqrt_nr(s), c, b); }
 __device__ __forceinline__ double pade_value(double s, double c, double b) { return c * rcp_nr(rsqrt_nr(s) + b); }
 
 // Component of (xi - xj) along hop axis ax: the Cartesian component, or the
@@ -379,16 +459,16 @@ __device__ EvalOut assemble(const DevSys& S, const Layout& L, const double* sm, 
       nuopt += apply ? nu_cap : nu_zv;
       nuplain += nu_zv;
       vee += q[5];
-      nnode += node ? 1 : 0;
     }
+    nnode += __popc(__ballot_sync(FULL, valid && sub == 0 && node));
   }
-#pragma unroll
-  for (int o = 16; o; o >>= 1) {
-    kept += __shfl_xor_sync(FULL, kept, o);
-    negs += __shfl_xor_sync(FULL, negs, o);
-    nuopt += __shfl_xor_sync(FULL, nuopt, o);
-    vee += __shfl_xor_sync(FULL, vee, o);
-    nnode += __shfl_xor_sync(FULL, nnode, o);
+  {
+    const double v[4] = {kept, negs, nuopt, vee};
+    const double t = warp_sum4(v, lane);
+    kept = __shfl_sync(FULL, t, 0);
+    negs = __shfl_sync(FULL, t, 8);
+    nuopt = __shfl_sync(FULL, t, 16);
+    vee = __shfl_sync(FULL, t, 24);
   }
   if (node_rule == 1 && !any_node) {
 #pragma unroll
@@ -579,9 +659,11 @@ __device__ EvalOut eval_full(const DevSys& S, const Layout& L, const double* __r
 // term comes from the caches (scr.pt for the current positions, scr.u2 for
 // the hops) and the new term of hop d of electron i with m equals the term of
 // m's opposite hop (d ^ 1) with i, since r_i + s a e - r_m = -(r_m - s a e - r_i).
+// Electron m's bare and capped potentials are evaluated here too, on the lanes
+// that hold its distances to the nuclei (ia = 1/a).
 template <bool ROT, bool GG>
 __device__ EvalOut eval_incr(const DevSys& S, const Layout& L, const double* __restrict__ gblk, double* sm, Scr scr,
-                             int m, bool all_blocks, double a, int node_rule, const double* T, int lane) {
+                             int m, bool all_blocks, double a, double ia, int node_rule, const double* T, int lane) {
   const int ne = L.n_e, nbf = L.n_bf, nn = S.n_nuc, P = L.n_hop;
   const double* x = sm + L.s_x;
   const double* xo = sm + L.s_xo;
@@ -600,12 +682,14 @@ __device__ EvalOut eval_incr(const DevSys& S, const Layout& L, const double* __r
   const double a2 = a * a;
   const int per = ne - 1 + nn;
   const double xm = x[3 * m], ym = x[3 * m + 1], zm = x[3 * m + 2];
-  // (A) electron m: geometry and its Jastrow sums from scratch, one partner
-  // (electron, then nucleus) per lane; (B) the partner electron's sums swap
-  // their term with m (old term from scr.pt)
+  // (A) electron m: geometry, its Jastrow sums and its bare and capped
+  // potentials from scratch, one partner (electron, then nucleus) per lane;
+  // (B) the partner electron's sums swap their term with m (old term from
+  // scr.pt)
   {
     const double xo0 = xo[0], xo1 = xo[1], xo2 = xo[2];
-    double U = 0.0, gx = 0.0, gy = 0.0, gz = 0.0, LJ = 0.0, vee = 0.0;
+    // U, grad (3), lap, e-e, nu, nu capped
+    double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     for (int t = lane; t < per; t += WARP) {
       const bool pair = t < ne - 1;
       const int j = t < m ? t : t + 1, I = t - (ne - 1);
@@ -621,16 +705,17 @@ __device__ EvalOut eval_incr(const DevSys& S, const Layout& L, const double* __r
       }
       const double dx = xm - px, dy = ym - py, dz = zm - pz;
       const double s = sqdist(dx, dy, dz);
+      const double ir = rsqrt_nr(s);
       // one Pade evaluation for both kinds; a nucleus without one-body term
       // (c = 0) contributes zeros and is evaluated at a dummy distance
-      const Pair p = pade(pair || c != 0.0 ? s : 1.0, c, b);
+      const Pair p = pade_ir(pair || c != 0.0 ? ir : 1.0, c, b);
       const double f = p.up * p.ir, lap = p.upp + 2.0 * f;
-      U += p.u;
-      gx = fma(f, dx, gx); gy = fma(f, dy, gy); gz = fma(f, dz, gz);
-      LJ += lap;
+      acc[0] += p.u;
+      acc[1] = fma(f, dx, acc[1]); acc[2] = fma(f, dy, acc[2]); acc[3] = fma(f, dz, acc[3]);
+      acc[4] += lap;
       if (pair) {
         const double hir = 0.5 * p.ir;
-        vee += hir;
+        acc[5] += hir;
         pr2[m * ne + j] = s + a2;
         pr2[j * ne + m] = s + a2;
         double* pm = scr.pt + 4 * (m * ne + j);
@@ -654,20 +739,24 @@ __device__ EvalOut eval_incr(const DevSys& S, const Layout& L, const double* __r
         } else {
           gg[1] = dx; gg[2] = dy; gg[3] = dz;
         }
+        // nu_ei and nu^a_ei (Appendix D): -Z/r and -Z/max(r, a), or the
+        // screened -Z erf(r/r_c)/r for both
+        const double Z = __ldg(S.Z + I);
+        if (__ldg(S.kind + I) == 0) {
+          acc[6] -= Z * ir;
+          acc[7] -= s >= a2 ? Z * ir : Z * ia;
+        } else {
+          const double v = -Z * erf(s * ir * __ldg(S.irc + I)) * ir;
+          acc[6] += v;
+          acc[7] += v;
+        }
       }
     }
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-      U += __shfl_xor_sync(FULL, U, o);
-      gx += __shfl_xor_sync(FULL, gx, o);
-      gy += __shfl_xor_sync(FULL, gy, o);
-      gz += __shfl_xor_sync(FULL, gz, o);
-      LJ += __shfl_xor_sync(FULL, LJ, o);
-      vee += __shfl_xor_sync(FULL, vee, o);
-    }
-    if (lane == 0) {
-      double* q = ej + 6 * m;
-      q[0] = U; q[1] = gx; q[2] = gy; q[3] = gz; q[4] = LJ; q[5] = vee;
+    const double tot = warp_sum8(acc, lane);
+    const int k = (lane >> 2) & 7;
+    if ((lane & 3) == 0) {
+      if (k < 6) ej[6 * m + k] = tot;
+      else sm[L.s_ep + 2 * m + (k - 6)] = tot;
     }
   }
   // (C) determinant derivatives of the refreshed spin block(s)
@@ -793,14 +882,9 @@ __device__ EvalOut init_walker(const DevSys& S, const Layout& L, double* __restr
     const double q[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
     orbital_derivs(S, L, q, n, chi5, phi5, T, lane);
     for (int o = lane; o < 5 * L.n_max; o += WARP) cache[i * 5 * L.n_max + o] = phi5[o];
-    double nu, nucap;
-    electron_potentials(S, q, a, ia, lane, nu, nucap);
-    if (lane == 0) {
-      ep[2 * i] = nu;
-      ep[2 * i + 1] = nucap;
-    }
     __syncwarp();
   }
+  all_potentials(S, L, x, ep, a, ia, lane);
   __threadfence_block();
   singular = reinvert(L, gblk, sm, scr.gj, lane, logdet);
   compute_g(S, L, sm, scr.g, 0, L.n_e, lane);
@@ -836,11 +920,12 @@ __device__ int choose_hop(const double* rat, int n_hop, double u, double total, 
 }
 
 // Apply hop p: orbital derivatives at the moved electron, Sherman-Morrison
-// update of its spin block and of g by the same factors, cache, potential and
-// position update; the old position goes to s_xo.
+// update of its spin block and of g by the same factors, cache and position
+// update (the old position goes to s_xo), and with pots the moved electron's
+// potentials (otherwise the incremental evaluation that follows sets them).
 template <bool ROT>
 __device__ void apply_hop(const DevSys& S, const Layout& L, double* __restrict__ gblk, double* sm, Scr scr, int p,
-                          double a, double ia, const double* T, int lane) {
+                          double a, double ia, bool pots, const double* T, int lane) {
   double* x = sm + L.s_x;
   double* bt = sm + L.s_bt;
   double* cache = gblk + L.g_cache;
@@ -889,16 +974,18 @@ __device__ void apply_hop(const DevSys& S, const Layout& L, double* __restrict__
     *gj = fma(-grow[mu], f[j], *gj);
   }
   for (int o = lane; o < 5 * L.n_max; o += WARP) cache[i * 5 * L.n_max + o] = phi5[o];
-  double nu, nucap;
-  electron_potentials(S, q, a, ia, lane, nu, nucap);
+  double nu = 0.0, nucap = 0.0;
+  if (pots) electron_potentials(S, q, a, ia, lane, nu, nucap);
   if (lane == 0) {
     double* xo = sm + L.s_xo;
     xo[0] = x[3 * i]; xo[1] = x[3 * i + 1]; xo[2] = x[3 * i + 2];
     x[3 * i] = q[0];
     x[3 * i + 1] = q[1];
     x[3 * i + 2] = q[2];
-    sm[L.s_ep + 2 * i] = nu;
-    sm[L.s_ep + 2 * i + 1] = nucap;
+    if (pots) {
+      sm[L.s_ep + 2 * i] = nu;
+      sm[L.s_ep + 2 * i + 1] = nucap;
+    }
   }
   __threadfence_block();
   __syncwarp();
@@ -1139,7 +1226,7 @@ __device__ void propagate_walker_impl(const DevSys& S, const Layout& L, double* 
           compute_g(S, L, sm, scr.g, 0, L.n_e, lane);
           g_valid = true;
         }
-        apply_hop<ROT>(S, L, gblk, sm, scr, p, P.a, ia, T, lane);
+        apply_hop<ROT>(S, L, gblk, sm, scr, p, P.a, ia, !cached, T, lane);
         ++moves;
         bool reinv = false;
         if (++since >= P.reinv_period) {
@@ -1153,7 +1240,7 @@ __device__ void propagate_walker_impl(const DevSys& S, const Layout& L, double* 
           e = eval_full<ROT, GG>(S, L, gblk, sm, scr, P.a, P.node_rule, T, lane);
           cached = true;
         } else {
-          e = eval_incr<ROT, GG>(S, L, gblk, sm, scr, p / 6, reinv, P.a, P.node_rule, T, lane);
+          e = eval_incr<ROT, GG>(S, L, gblk, sm, scr, p / 6, reinv, P.a, ia, P.node_rule, T, lane);
         }
         bbar = e.bbar;
         Wd = e.W;
@@ -1214,29 +1301,33 @@ __global__ void k_propagate(DevSys S, Layout L, double* __restrict__ state, doub
   for (int w = slot; w < n_w; w += nwarps) propagate_walker<ROT>(S, L, state, cache, w, P, T, sm, wscr, lane);
 }
 
-// Compact copies of walker fields (for host readback).
+// Compact copies of walker fields (for host readback); a null output is skipped.
 __global__ void k_extract(Layout L, const double* __restrict__ state, int n_w, double* __restrict__ x,
                           double* __restrict__ w, double* __restrict__ ev, double* __restrict__ rat,
-                          double* __restrict__ st, double* __restrict__ mv) {
+                          uint32_t* __restrict__ st, int32_t* __restrict__ mv) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int nth = gridDim.x * blockDim.x;
-  for (int idx = tid; idx < n_w * 3 * L.n_e; idx += nth) {
-    const int a = idx / (3 * L.n_e), o = idx - a * 3 * L.n_e;
-    x[idx] = state[(size_t)a * L.g_stride + L.g_x + o];
-  }
-  for (int idx = tid; idx < n_w * L.n_hop; idx += nth) {
-    const int a = idx / L.n_hop, o = idx - a * L.n_hop;
-    rat[idx] = state[(size_t)a * L.g_stride + L.g_rat + o];
-  }
+  if (x)
+    for (int idx = tid; idx < n_w * 3 * L.n_e; idx += nth) {
+      const int a = idx / (3 * L.n_e), o = idx - a * 3 * L.n_e;
+      x[idx] = state[(size_t)a * L.g_stride + L.g_x + o];
+    }
+  if (rat)
+    for (int idx = tid; idx < n_w * L.n_hop; idx += nth) {
+      const int a = idx / L.n_hop, o = idx - a * L.n_hop;
+      rat[idx] = state[(size_t)a * L.g_stride + L.g_rat + o];
+    }
   for (int a = tid; a < n_w; a += nth) {
     const double* sc = state + (size_t)a * L.g_stride + L.g_sc;
-    w[a] = sc[SC_W];
-    ev[4 * a] = sc[SC_BBAR];
-    ev[4 * a + 1] = sc[SC_VSF];
-    ev[4 * a + 2] = sc[SC_WDIAG];
-    ev[4 * a + 3] = sc[SC_EL];
-    st[a] = sc[SC_STATUS];
-    mv[a] = sc[SC_MOVES];
+    if (w) w[a] = sc[SC_W];
+    if (ev) {
+      ev[4 * a] = sc[SC_BBAR];
+      ev[4 * a + 1] = sc[SC_VSF];
+      ev[4 * a + 2] = sc[SC_WDIAG];
+      ev[4 * a + 3] = sc[SC_EL];
+    }
+    if (st) st[a] = (uint32_t)sc[SC_STATUS];
+    if (mv) mv[a] = (int32_t)sc[SC_MOVES];
   }
 }
 

@@ -1168,8 +1168,11 @@ __device__ void propagate_walker_m(const DevSys& S, const Layout& L, const Layou
   }
 }
 
-__global__ void k_propagate_m(DevSys S, Layout L, LayoutM M, double* __restrict__ state, double* __restrict__ cache,
-                              int n_w, StepParams P, double* scratch) {
+// At most 72 registers per thread (8 bytes spilled): the kernel is latency
+// bound, and 28 resident warps per SM (4096 walkers in one wave on 148 SMs)
+// run it faster than the 20 that its unconstrained 94 registers allow.
+__global__ void __maxnreg__(72) k_propagate_m(DevSys S, Layout L, LayoutM M, double* __restrict__ state,
+                                              double* __restrict__ cache, int n_w, StepParams P, double* scratch) {
   extern __shared__ double smem[];
   const double* T = stage_table(S, smem);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
