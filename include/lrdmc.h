@@ -325,6 +325,18 @@ void lrdmc_philox4x32(uint64_t seed, const uint32_t ctr[4], uint32_t out[4]);
 lrdmc_status lrdmc_fp64math(int n, const double* x, double* exp_out, double* rcp_out, double* rsqrt_out,
                             void* stream);
 
+/* Testing aids for the screened potential -Z erf(r/r_c)/r of Appendix D's
+ * local potential.  The library evaluates erf(r/r_c)/r = F(t)/r_c,
+ * F(t) = erf(sqrt t)/sqrt t, t = r^2/r_c^2, from a table of one polynomial per
+ * interval of width 1/2 in t (centred at k/2, k = 0 .. n_int - 1, powers of
+ * t - k/2, lowest first, n_coef per interval), and as 1/r beyond the table.
+ * lrdmc_erf_ratio_table writes the n_int x n_coef coefficients to out (host;
+ * out may be NULL to query the sizes).  lrdmc_erf_over_r evaluates
+ * erf(r/r_c)/r on the device for n device doubles s = r^2 (asynchronous on
+ * stream); LRDMC_ERR_ARG for n < 0, NULL arrays or r_c <= 0. */
+lrdmc_status lrdmc_erf_ratio_table(double* out, int* n_int, int* n_coef);
+lrdmc_status lrdmc_erf_over_r(int n, const double* s, double r_c, double* out, void* stream);
+
 /* Load-imbalance measurement (the in-GPU image of the paper's argument that
  * a synchronised interval waits for its slowest walker).  With timing enabled
  * every propagate records, per walker, its start and stop time and SM;

@@ -42,6 +42,7 @@ struct DevSys {
   const double* Z;       // n_nuc
   const double* rc;      // n_nuc
   const double* irc;     // n_nuc: 1 / rc (erf-screened nuclei)
+  const double* irc2;    // n_nuc: 1 / rc^2
   const int* kind;       // n_nuc: 0 bare Coulomb, 1 erf-screened
   const double* j1A;     // n_nuc
   const double* j1B;     // n_nuc
@@ -52,6 +53,7 @@ struct DevSys {
   const int* sh_bf;      // n_shell: first basis function
   const int* atom_sh;    // n_nuc + 1: shells are grouped by nucleus, atom I owns [atom_sh[I], atom_sh[I+1])
   const double* exptab;  // 64: 2^(j/64) for the table-driven exponential
+  const double* erftab;  // ERF_INT x ERF_NC: polynomials of erf(sqrt t)/sqrt t (fp64math.cuh)
   const double* exps;    // n_prim
   const double* coefs;   // n_prim
   const double* C;       // n_orb x n_bf

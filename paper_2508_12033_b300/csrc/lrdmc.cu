@@ -38,6 +38,57 @@ constexpr size_t GEO_GLOBAL_BYTES_MIXED = 8 * 1024;
 
 size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
+// F(t) = erf(sqrt t) / sqrt t in long double, for t >= -1 (F is entire:
+// F(t) = (2/sqrt pi) sum_n (-t)^n / (n! (2n + 1)), used for |t| < 2).
+long double erf_ratio_ld(long double t) {
+  if (fabsl(t) < 2.0L) {
+    long double term = 1.0L, sum = 0.0L;   // term = (-t)^n / n!
+    for (int n = 0; n < 60; ++n) {
+      sum += term / (2 * n + 1);
+      term *= -t / (n + 1);
+    }
+    return sum * 1.12837916709551257389615890312154517L;   // 2 / sqrt(pi)
+  }
+  const long double r = sqrtl(t);
+  return erfl(r) / r;
+}
+
+// Coefficients of the erf_over_r table (fp64math.cuh): for interval k, the
+// degree-(ERF_NC - 1) polynomial in u = t - k/2, |u| <= 1/4, that interpolates
+// F at the ERF_NC Chebyshev points of the interval; computed in long double
+// (Chebyshev coefficients by the discrete cosine sums, then rewritten in powers
+// of u through the three-term recurrence of the Chebyshev polynomials).
+void erf_ratio_table(double* out) {
+  const int N = ERF_NC;
+  const long double pi = 3.14159265358979323846264338327950288L, h = 0.25L;
+  for (int k = 0; k < ERF_INT; ++k) {
+    const long double c = 0.5L * k;
+    long double f[ERF_NC], a[ERF_NC];
+    for (int i = 0; i < N; ++i) f[i] = erf_ratio_ld(c + h * cosl(pi * (i + 0.5L) / N));
+    for (int j = 0; j < N; ++j) {
+      long double sum = 0.0L;
+      for (int i = 0; i < N; ++i) sum += f[i] * cosl(pi * j * (i + 0.5L) / N);
+      a[j] = (j == 0 ? 1.0L : 2.0L) * sum / N;
+    }
+    // power-basis coefficients in x = u / h: sum_j a_j T_j(x)
+    long double px[ERF_NC] = {0}, tm[ERF_NC] = {0}, t0[ERF_NC] = {0}, t1[ERF_NC] = {0};
+    t0[0] = 1.0L;   // T_0
+    t1[1] = 1.0L;   // T_1
+    for (int i = 0; i < N; ++i) px[i] += a[0] * t0[i];
+    if (N > 1)
+      for (int i = 0; i < N; ++i) px[i] += a[1] * t1[i];
+    for (int j = 2; j < N; ++j) {
+      for (int i = 0; i < N; ++i) tm[i] = (i ? 2.0L * t1[i - 1] : 0.0L) - t0[i];   // T_j = 2 x T_{j-1} - T_{j-2}
+      for (int i = 0; i < N; ++i) { px[i] += a[j] * tm[i]; t0[i] = t1[i]; t1[i] = tm[i]; }
+    }
+    long double sc = 1.0L;
+    for (int i = 0; i < N; ++i) {
+      out[k * N + i] = (double)(px[i] * sc);
+      sc /= h;
+    }
+  }
+}
+
 // Everything derived from the inputs before any device work.
 struct Plan {
   int n_nuc = 0, n_shell = 0, n_prim = 0, n_bf = 0, n_orb = 0, n_up = 0, n_dn = 0, n_e = 0, n_max = 0;
@@ -52,7 +103,7 @@ struct Plan {
   int scratch_warps = 0;
   // system image offsets (bytes, inside the sys block)
   size_t i_R, i_Z, i_rc, i_irc, i_j1A, i_j1B, i_exps, i_coefs, i_C, i_kind, i_atom, i_l, i_nprim, i_off, i_bf, i_ash,
-      i_tab, i_f_R, i_f_Z, i_f_rc, i_f_j1A, i_f_j1B, i_f_exps, i_f_coefs, i_f_C;
+      i_tab, i_f_R, i_f_Z, i_f_rc, i_f_j1A, i_f_j1B, i_f_exps, i_f_coefs, i_f_C, i_irc2, i_erf;
   std::string err;
 };
 
@@ -163,6 +214,8 @@ bool make_plan(const lrdmc_system* sys, const lrdmc_trial_wf* wf, const lrdmc_pa
   P.i_bf = take(sizeof(int) * P.n_shell);
   P.i_ash = take(sizeof(int) * (P.n_nuc + 1));
   P.i_tab = take(sizeof(double) * EXP_TAB);
+  P.i_irc2 = take(sizeof(double) * P.n_nuc);
+  P.i_erf = take(sizeof(double) * ERF_INT * ERF_NC);
   P.i_f_R = take(sizeof(float) * 3 * P.n_nuc);
   P.i_f_Z = take(sizeof(float) * P.n_nuc);
   P.i_f_rc = take(sizeof(float) * P.n_nuc);
@@ -676,7 +729,15 @@ lrdmc_status lrdmc_create(const lrdmc_system* sys, const lrdmc_trial_wf* wf, con
   {
     std::vector<double> irc(P.n_nuc);
     for (int I = 0; I < P.n_nuc; ++I) irc[I] = sys->pot_kind[I] == 1 ? 1.0 / sys->r_c[I] : 0.0;
-    putd(P.i_irc, irc.data(), P.n_nuc);
+    putd(P.i_irc, irc.data(), irc.size());
+    for (int I = 0; I < P.n_nuc; ++I)
+      irc[I] = sys->pot_kind[I] == 1 ? (double)(1.0L / ((long double)sys->r_c[I] * sys->r_c[I])) : 0.0;
+    putd(P.i_irc2, irc.data(), irc.size());
+  }
+  {
+    std::vector<double> et(ERF_INT * ERF_NC);
+    erf_ratio_table(et.data());
+    putd(P.i_erf, et.data(), et.size());
   }
   putd(P.i_j1A, wf->j1_A, P.n_nuc);
   putd(P.i_j1B, wf->j1_B, P.n_nuc);
@@ -748,6 +809,8 @@ lrdmc_status lrdmc_create(const lrdmc_system* sys, const lrdmc_trial_wf* wf, con
   S.sh_bf = (const int*)(dsys + P.i_bf);
   S.atom_sh = (const int*)(dsys + P.i_ash);
   S.exptab = (const double*)(dsys + P.i_tab);
+  S.irc2 = (const double*)(dsys + P.i_irc2);
+  S.erftab = (const double*)(dsys + P.i_erf);
   S.Rf = (const float*)(dsys + P.i_f_R);
   S.Zf = (const float*)(dsys + P.i_f_Z);
   S.rcf = (const float*)(dsys + P.i_f_rc);
@@ -1206,6 +1269,32 @@ lrdmc_status lrdmc_fp64math(int n, const double* x, double* exp_out, double* rcp
   }
   k_fp64math<<<std::min(1024, (n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(n, x, exp_out, rcp_out, rsqrt_out,
                                                                                 d_tab[dev]);
+  return cudaGetLastError() == cudaSuccess ? LRDMC_OK : LRDMC_ERR_CUDA;
+}
+
+lrdmc_status lrdmc_erf_ratio_table(double* out, int* n_int, int* n_coef) {
+  if (n_int) *n_int = ERF_INT;
+  if (n_coef) *n_coef = ERF_NC;
+  if (out) erf_ratio_table(out);
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_erf_over_r(int n, const double* s, double r_c, double* out, void* stream) {
+  if (n < 0 || (n > 0 && (!s || !out)) || !(r_c > 0.0)) return LRDMC_ERR_ARG;
+  if (n == 0) return LRDMC_OK;
+  static double* d_tab[64] = {nullptr};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return LRDMC_ERR_CUDA;
+  if (!d_tab[dev]) {
+    std::vector<double> tab(ERF_INT * ERF_NC);
+    erf_ratio_table(tab.data());
+    if (cudaMalloc(&d_tab[dev], sizeof(double) * tab.size()) != cudaSuccess) return LRDMC_ERR_CUDA;
+    if (cudaMemcpy(d_tab[dev], tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      return LRDMC_ERR_CUDA;
+  }
+  const double irc2 = (double)(1.0L / ((long double)r_c * r_c));
+  k_erf_over_r<<<std::min(1024, (n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(n, s, 1.0 / r_c, irc2, out,
+                                                                                  d_tab[dev]);
   return cudaGetLastError() == cudaSuccess ? LRDMC_OK : LRDMC_ERR_CUDA;
 }
 

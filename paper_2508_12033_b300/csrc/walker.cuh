@@ -179,7 +179,7 @@ __device__ void electron_potentials(const DevSys& S, const double q[3], double a
       nu -= Z * ir;
       nucap -= s >= a * a ? Z * ir : Z * ia;   // Z / max(r, a)
     } else {
-      const double v = -Z * erf(s * ir * __ldg(S.irc + I)) * ir;
+      const double v = -Z * erf_over_r(s, ir, __ldg(S.irc + I), __ldg(S.irc2 + I), S.erftab);
       nu += v;
       nucap += v;
     }
@@ -214,7 +214,7 @@ __device__ void all_potentials(const DevSys& S, const Layout& L, const double* x
           nu -= Z * ir;
           nucap -= s >= a2 ? Z * ir : Z * ia;
         } else {
-          const double v = -Z * erf(s * ir * __ldg(S.irc + I)) * ir;
+          const double v = -Z * erf_over_r(s, ir, __ldg(S.irc + I), __ldg(S.irc2 + I), S.erftab);
           nu += v;
           nucap += v;
         }
@@ -746,7 +746,7 @@ __device__ EvalOut eval_incr(const DevSys& S, const Layout& L, const double* __r
           acc[6] -= Z * ir;
           acc[7] -= s >= a2 ? Z * ir : Z * ia;
         } else {
-          const double v = -Z * erf(s * ir * __ldg(S.irc + I)) * ir;
+          const double v = -Z * erf_over_r(s, ir, __ldg(S.irc + I), __ldg(S.irc2 + I), S.erftab);
           acc[6] += v;
           acc[7] += v;
         }
@@ -1342,6 +1342,13 @@ __global__ void k_fp64math(int n, const double* __restrict__ x, double* __restri
     if (r) r[k] = rcp_nr(v);
     if (q) q[k] = rsqrt_nr(v);
   }
+}
+
+// erf(r/r_c)/r at s = r^2 through the table of erf_over_r (testing aid).
+__global__ void k_erf_over_r(int n, const double* __restrict__ s, double irc, double irc2, double* __restrict__ out,
+                             const double* __restrict__ C) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+    out[k] = erf_over_r(s[k], rsqrt_nr(s[k]), irc, irc2, C);
 }
 
 // Set walker scalar idx of every walker to v.

@@ -44,3 +44,32 @@ def test_fp64math_against_cuda():
             rel_r = ((r - 1.0 / xt).abs() * xt).max().item()
             rel_q = ((q - torch.rsqrt(xt)).abs() / torch.rsqrt(xt)).max().item()
             assert rel_r < 4e-16 and rel_q < 6e-16, (rel_r, rel_q)
+
+
+def test_screened_potential_against_cuda_erf():
+    """erf(r/r_c)/r from the library's table against CUDA's erf on the same GPU,
+    over r from 1e-6 to 10 r_c and beyond the table, and at r = 0."""
+    import torch
+    from gpu_helpers import lib_or_skip
+    P = lib_or_skip()
+    lib = P.load_library()
+    f = lib.lrdmc_erf_over_r
+    f.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    rng = np.random.default_rng(3)
+    stream = torch.cuda.current_stream().cuda_stream
+    for rc in (0.5, 1.3):
+        r = np.concatenate([np.exp(rng.uniform(np.log(1e-6), np.log(10 * rc), 1 << 18)),
+                            rng.uniform(0, 7 * rc, 1 << 18)])
+        s = torch.tensor(r * r, device="cuda")
+        out = torch.empty_like(s)
+        assert f(len(r), s.data_ptr(), rc, out.data_ptr(), stream) == 0
+        torch.cuda.synchronize()
+        rr = torch.sqrt(s)
+        ref = torch.special.erf(rr / rc) / rr
+        assert ((out - ref).abs() / ref).max().item() < 2e-15
+        z = torch.zeros(1, dtype=torch.float64, device="cuda")
+        assert f(1, z.data_ptr(), rc, out.data_ptr(), stream) == 0
+        torch.cuda.synchronize()
+        assert abs(out[0].item() * rc * np.sqrt(np.pi) / 2 - 1.0) < 1e-15
+    assert f(1, s.data_ptr(), 0.0, out.data_ptr(), stream) == 1

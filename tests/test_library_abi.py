@@ -136,3 +136,25 @@ def test_batch_entry_points_validate_arguments_without_a_gpu(lib):
     assert lib.lrdmc_batch_create(2, sa, wa, pa, xp, None, ctypes.byref(out)) == 1
     assert lib.lrdmc_batch_destroy(None) == 1
     assert lib.lrdmc_batch_propagate(None, None) == 1
+
+
+def test_screened_potential_table_matches_erf(lib):
+    """The per-interval polynomials behind erf(r/r_c)/r reproduce
+    F(t) = erf(sqrt t)/sqrt t to a few ulp over the whole table, and erf(sqrt t)
+    is exactly 1 in double where the table ends (so 1/r is exact there)."""
+    import math
+    n_int, n_coef = ctypes.c_int(), ctypes.c_int()
+    assert lib.lrdmc_erf_ratio_table(None, ctypes.byref(n_int), ctypes.byref(n_coef)) == 0
+    ni, nc = n_int.value, n_coef.value
+    C = np.zeros((ni, nc))
+    assert lib.lrdmc_erf_ratio_table(C.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), None, None) == 0
+    t = np.concatenate([np.linspace(0.0, (ni - 0.5) / 2, 20011), [0.0, 1e-300, 1e-12, 0.2499999, 0.25, 36.0]])
+    t = t[t < (ni - 0.5) / 2]
+    k = np.rint(2 * t).astype(int)
+    u = t - 0.5 * k
+    p = np.zeros_like(t)
+    for j in range(nc - 1, -1, -1):
+        p = p * u + C[k, j]
+    ref = np.array([2 / math.sqrt(math.pi) if x == 0 else math.erf(math.sqrt(x)) / math.sqrt(x) for x in t])
+    assert np.max(np.abs(p - ref) / ref) < 2e-15
+    assert math.erf(math.sqrt((ni - 1) / 2)) == 1.0 and ni == 73
