@@ -27,6 +27,9 @@ constexpr int MAX_WALKERS = 1 << 24;
 // Upper bound of resident warps that get per-warp scratch (148 SMs x 32 warps);
 // the launch grid is clamped to it.
 constexpr int SCRATCH_WARPS_CAP = 148 * 32;
+// Status words (int32) of a handle: [0, 2) reconfiguration status, DSTAT_NEXT
+// the propagate kernels' work counter.
+constexpr int DSTAT_NEXT = 8;
 // Walkers whose shared-memory layout would exceed these sizes keep their O(N^2)
 // caches in the cache block (see make_plan).  Measured on water-methane: the
 // FP64 kernel, bound by the FP64 pipe, is faster with its geometry in shared
@@ -476,6 +479,7 @@ static StepParams step_params(lrdmc_handle h, const lrdmc_schedule* sch) {
   sp.reinv_period = h->prm.reinv_period;
   sp.stamps = h->timing ? h->stamps : nullptr;
   sp.rotate = sch->rotate != 0;
+  sp.next = nullptr;
   return sp;
 }
 
@@ -903,7 +907,10 @@ lrdmc_status lrdmc_propagate(lrdmc_handle h, const lrdmc_schedule* sch) {
   if (sch->rotate && h->P.precision != 0)
     return fail(h, LRDMC_ERR_UNSUPPORTED, "the randomised lattice is implemented for precision 0 only");
   DeviceGuard g(h->device);
-  const StepParams sp = step_params(h, sch);
+  StepParams sp = step_params(h, sch);
+  // dynamic walker assignment: the work counter (status word 8) starts at zero
+  sp.next = (unsigned*)(h->dstat + DSTAT_NEXT);
+  CK(h, cudaMemsetAsync(sp.next, 0, sizeof(unsigned), h->stream));
   const int smem = smem_bytes(h);
   if (h->P.precision == 0)
     if (sp.rotate)

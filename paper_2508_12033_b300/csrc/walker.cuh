@@ -437,9 +437,10 @@ __device__ EvalOut assemble(const DevSys& S, const Layout& L, const double* sm, 
     if (valid)
       for (int d = sub * nd; d < (sub + 1) * nd; ++d) {
         const double r = rat[6 * i + d];
+        const long long b = __double_as_longlong(r);
         sr += r;
-        if (r > 0.0) kept += r;
-        if (r < 0.0) { negs -= r; node = true; }
+        if (b > 0) kept += r;                               // r > 0
+        if (b < 0 && (b << 1) != 0) { negs -= r; node = true; }   // r < 0 (not -0)
       }
     if (G == 2) {
       sr += __shfl_xor_sync(FULL, sr, 1);
@@ -895,28 +896,43 @@ __device__ EvalOut init_walker(const DevSys& S, const Layout& L, double* __restr
 // Heat-bath choice over the kept hops (r > 0) in the order p = 6 i + d: the
 // first p whose running sum exceeds u * total (total = the sum of the kept
 // ratios taken by the evaluation); the last kept hop if rounding leaves none;
-// -1 without kept hops.  Running sums by warp scans over chunks of 32 hops.
+// -1 without kept hops.  Each lane owns a contiguous run of hops: lane sums,
+// one warp scan of them, then each lane continues the running sum over its own
+// hops.  Signs and the comparisons of non-negative sums are taken on the
+// integer images (the order of non-negative doubles is that of their bits), so
+// the FP64 pipe sees only the additions.
+__device__ __forceinline__ bool positive(double r) { return __double_as_longlong(r) > 0; }
+
 __device__ int choose_hop(const double* rat, int n_hop, double u, double total, int lane) {
   if (!(total > 0.0)) return -1;
-  const double t = u * total;
-  double base = 0.0;
-  int last = -1;
-  for (int c = 0; c < n_hop; c += WARP) {
-    const int p = c + lane;
-    const double k = (p < n_hop && rat[p] > 0.0) ? rat[p] : 0.0;
-    double incl = k;
-#pragma unroll
-    for (int o = 1; o < WARP; o <<= 1) {
-      const double v = __shfl_up_sync(FULL, incl, o);
-      if (lane >= o) incl += v;
-    }
-    const unsigned hit = __ballot_sync(FULL, base + incl > t);
-    if (hit) return c + __ffs(hit) - 1;
-    const unsigned kept = __ballot_sync(FULL, k > 0.0);
-    if (kept) last = c + 31 - __clz(kept);
-    base += __shfl_sync(FULL, incl, WARP - 1);
+  const long long t = __double_as_longlong(u * total);
+  const int per = (n_hop + WARP - 1) / WARP, p0 = lane * per, p1 = min(n_hop, p0 + per);
+  double own = 0.0;
+  for (int p = p0; p < p1; ++p) {
+    const double r = rat[p];
+    if (positive(r)) own += r;
   }
-  return last;
+  double incl = own;
+#pragma unroll
+  for (int o = 1; o < WARP; o <<= 1) {
+    const double v = __shfl_up_sync(FULL, incl, o);
+    if (lane >= o) incl += v;
+  }
+  double run = __shfl_up_sync(FULL, incl, 1);
+  if (lane == 0) run = 0.0;
+  int hit = -1, last = -1;
+  for (int p = p0; p < p1; ++p) {
+    const double r = rat[p];
+    if (positive(r)) {
+      run += r;
+      last = p;
+      if (hit < 0 && __double_as_longlong(run) > t) hit = p;
+    }
+  }
+  const unsigned hm = __ballot_sync(FULL, hit >= 0);
+  if (hm) return __shfl_sync(FULL, hit, __ffs(hm) - 1);
+  const unsigned km = __ballot_sync(FULL, last >= 0);
+  return km ? __shfl_sync(FULL, last, 31 - __clz(km)) : -1;
 }
 
 // Apply hop p: orbital derivatives at the moved electron, Sherman-Morrison
@@ -948,11 +964,20 @@ __device__ void apply_hop(const DevSys& S, const Layout& L, double* __restrict__
   orbital_derivs(S, L, q, sr.n, chi5, phi5, T, lane);
   double* B = bt + sr.bt_off;   // B^T of the spin block: B[j * n + k] = (A^{-1})_{k j}
   const int n = sr.n;
-  // u_j = phi(r') . B[:, j]; the determinant ratio is u_ii
-  for (int j = lane; j < n; j += WARP) {
-    double acc = 0.0;
-    for (int k = 0; k < n; ++k) acc = fma(phi5[k], B[j * n + k], acc);
-    f[j] = acc;
+  // u_j = phi(r') . B[:, j]; the determinant ratio is u_ii.  Each dot is split
+  // over G lanes (consecutive slices of k) and combined by shuffles.
+  {
+    const int G = split_factor(n, n), chunk = (n + G - 1) / G, n_task = n * G;
+    for (int base = 0; base < n_task; base += WARP) {
+      const int task = base + lane, j = task / G, part = task - j * G;
+      double acc = 0.0;
+      if (task < n_task) {
+        const int k1 = min(n, (part + 1) * chunk);
+        for (int k = part * chunk; k < k1; ++k) acc = fma(phi5[k], B[j * n + k], acc);
+      }
+      for (int sh = 1; sh < G; sh <<= 1) acc += __shfl_xor_sync(FULL, acc, sh);
+      if (task < n_task && part == 0) f[j] = acc;
+    }
   }
   for (int k = lane; k < n; k += WARP) row[k] = B[sr.ii * n + k];
   for (int mu = lane; mu < L.n_bf; mu += WARP) grow[mu] = g[i * L.n_bf + mu];
@@ -1005,7 +1030,18 @@ struct StepParams {
   int reinv_period;
   unsigned long long* stamps;   // optional: per walker (start ns, end ns, SM id)
   int rotate;                   // randomised lattice: new versors every interval
+  unsigned* next;               // optional: zeroed work counter; warps past their first walker take the next
+                                // unclaimed one from it (dynamic assignment), else walkers go round-robin
 };
+
+// Next walker of a warp after w: from the work counter (first-come order,
+// which evens out walkers of unequal cost) or round-robin.
+__device__ __forceinline__ int next_walker(const StepParams& P, int w, int nwarps, int lane) {
+  if (!P.next) return w + nwarps;
+  unsigned v = 0;
+  if (lane == 0) v = atomicAdd(P.next, 1u);
+  return nwarps + (int)__shfl_sync(FULL, v, 0);
+}
 
 // Hop versors of walker slot w in an interval (rows of V): one uniformly random
 // rotation of the Cartesian axes (Shoemake, "Uniform random rotations",
@@ -1298,7 +1334,8 @@ __global__ void k_propagate(DevSys S, Layout L, double* __restrict__ state, doub
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   const int slot = blockIdx.x * (blockDim.x >> 5) + wib;
   const Scr wscr = warp_scratch(L, S.n_nuc, scratch, slot);
-  for (int w = slot; w < n_w; w += nwarps) propagate_walker<ROT>(S, L, state, cache, w, P, T, sm, wscr, lane);
+  for (int w = slot; w < n_w; w = next_walker(P, w, nwarps, lane))
+    propagate_walker<ROT>(S, L, state, cache, w, P, T, sm, wscr, lane);
 }
 
 // Compact copies of walker fields (for host readback); a null output is skipped.

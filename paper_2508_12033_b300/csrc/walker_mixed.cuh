@@ -1180,7 +1180,8 @@ __global__ void __maxnreg__(72) k_propagate_m(DevSys S, Layout L, LayoutM M, dou
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   const int slot = blockIdx.x * (blockDim.x >> 5) + wib;
   const ScrM wscr = warp_scratch_m(L, M, scratch, slot);
-  for (int w = slot; w < n_w; w += nwarps) propagate_walker_m(S, L, M, state, cache, w, P, T, sm, wscr, lane);
+  for (int w = slot; w < n_w; w = next_walker(P, w, nwarps, lane))
+    propagate_walker_m(S, L, M, state, cache, w, P, T, sm, wscr, lane);
 }
 
 }  // namespace lrdmc
