@@ -815,12 +815,10 @@ __device__ EvalOut eval_incr(const DevSys& S, const Layout& L, const double* __r
     // sums over partners of each of m's hops: four lanes per hop
     const int d = lane >> 2, sub = lane & 3;
     double J1 = 0.0, J2 = 0.0;
-    if (d < 6)
-      for (int t = sub; t < per; t += 4) {
-        const double v = tmp[d * per + t];
-        if (t < ne - 1) J2 += v;
-        else J1 += v;
-      }
+    if (d < 6) {
+      for (int t = sub; t < ne - 1; t += 4) J2 += tmp[d * per + t];
+      for (int t = ne - 1 + sub; t < per; t += 4) J1 += tmp[d * per + t];
+    }
     J1 += __shfl_xor_sync(FULL, J1, 1);
     J2 += __shfl_xor_sync(FULL, J2, 1);
     J1 += __shfl_xor_sync(FULL, J1, 2);
