@@ -335,7 +335,7 @@ def run_adjoint(P):
     """Hand-written adjoint: e_L, log|Psi| and their gradients with respect to
     all 384 nuclear coordinates and the 259 Jastrow parameters of the H128 chain
     (spacing 1.8 bohr, s + p GTO per atom, seeded MOs, a = 0.25) at 8192 seeded
-    configurations, evaluated in launches of 1024 (the handle's walkers)."""
+    configurations, evaluated in one launch."""
     import torch
     import workloads as W
     s = W.hydrogen_chain(128)

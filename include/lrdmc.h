@@ -196,7 +196,9 @@ lrdmc_status lrdmc_set_params(lrdmc_handle h, const double* theta);
 
 /* Hand-written adjoint of the lattice-regularised local energy e_L = W - b_bar
  * (Appendix D, the handle's node rule) and of log|Psi_G| at n configurations
- * (device x, n x n_e x 3; processed in launches of at most n_w), with
+ * (device x, n x n_e x 3; one launch, each warp evaluating its configurations
+ * in a walker block of its own; large systems keep the per-warp working set in
+ * global memory, allocated with that scratch on the first call), with
  * respect to theta:
  *   eL, logpsi          device, n (or NULL)
  *   grad_eL, grad_logpsi device, n x lrdmc_param_count (or NULL)

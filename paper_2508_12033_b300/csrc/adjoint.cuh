@@ -116,14 +116,23 @@ __device__ void basis_values_at(const DevSys& S, const Layout& L, const double q
 //   du'/dc = t^2, du''/dc = -2 b t^3, du'/db = -2 c r t^3, du''/db = -2 c t^3 + 6 b c r t^4
 
 // One configuration per warp: e_L, log|Psi_G| and their gradient rows.
-__global__ void k_eloc_grad(DevSys S, Layout L, double* __restrict__ blocks, const double* __restrict__ x_in, int n,
+// GSM: the warp's working set (the shared-memory layout of the propagate
+// kernels) lives in global memory at gsm + slot * s_stride instead of shared
+// memory.  Large systems use it: a 128-electron working set fills an SM's
+// shared memory for a single warp, while from global memory (L1 / L2 resident)
+// as many warps share an SM as their registers allow: at most 128 registers
+// per thread (16 bytes spilled) let 16 warps share an SM, against 9 with the
+// 216 the kernel takes unconstrained.
+template <bool GSM>
+__global__ void __maxnreg__(128) k_eloc_grad(DevSys S, Layout L, double* __restrict__ blocks, const double* __restrict__ x_in, int n,
                             double a, int node_rule, double* scratch, double* gscr, size_t gscr_per_warp,
                             double* __restrict__ eL_out, double* __restrict__ lp_out, double* __restrict__ ge_out,
-                            double* __restrict__ gl_out) {
+                            double* __restrict__ gl_out, double* gsm) {
   extern __shared__ double smem[];
   const double* T = stage_table(S, smem);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  double* sm = smem + EXP_TAB + wib * L.s_stride;
+  double* sm = GSM ? gsm + (size_t)(blockIdx.x * (blockDim.x >> 5) + wib) * L.s_stride
+                   : smem + EXP_TAB + wib * L.s_stride;
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   const int slot = blockIdx.x * (blockDim.x >> 5) + wib;
   const Scr scr = warp_scratch(L, S.n_nuc, scratch, slot);
@@ -140,7 +149,7 @@ __global__ void k_eloc_grad(DevSys S, Layout L, double* __restrict__ blocks, con
   double* phih = chih + nbf;        // orbital values at one hop
   const double ia2 = 1.0 / (a * a), s_bar = -0.5 * ia2;
   for (int w = slot; w < n; w += nwarps) {
-    double* gblk = blocks + (size_t)w * L.g_stride;
+    double* gblk = blocks + (size_t)slot * L.g_stride;   // the warp's own walker block
     double* ge = ge_out ? ge_out + (size_t)w * np : nullptr;
     double* gl = gl_out ? gl_out + (size_t)w * np : nullptr;
     for (int o = lane; o < 3 * ne; o += WARP) sm[L.s_x + o] = x_in[(size_t)w * 3 * ne + o];

@@ -30,6 +30,9 @@ constexpr int SCRATCH_WARPS_CAP = 148 * 32;
 // Status words (int32) of a handle: [0, 2) reconfiguration status, DSTAT_NEXT
 // the propagate kernels' work counter.
 constexpr int DSTAT_NEXT = 8;
+// The gradient kernel keeps its working sets in global memory when shared
+// memory would hold fewer than this many of them per SM.
+constexpr int ADJ_MIN_WARPS = 8;
 // Walkers whose shared-memory layout would exceed these sizes keep their O(N^2)
 // caches in the cache block (see make_plan).  Measured on water-methane: the
 // FP64 kernel, bound by the FP64 pipe, is faster with its geometry in shared
@@ -322,6 +325,13 @@ struct lrdmc_s {
   std::vector<double> hR, hZ, hA, hB;   // host copies of the differentiable system parameters
   double* gscr = nullptr;        // per-warp scratch of the adjoint kernel (allocated on first use)
   size_t gscr_per_warp = 0;
+  // adjoint launch shape; with adj_gsm set the working sets live in global
+  // memory (adj_gsm, with their own per-warp scratch adj_scr)
+  int adj_grid = 0, adj_wpb = 0;
+  int sm_warps = 0;              // working sets per SM that shared memory holds (launch shape of create)
+  double* adj_gsm = nullptr;
+  double* adj_scr = nullptr;
+  double* adj_blk = nullptr;     // per-warp walker blocks of the gradient kernel
   double* cache_alt = nullptr;
   double* stats = nullptr;
   unsigned long long* Q = nullptr;
@@ -377,7 +387,7 @@ static lrdmc_status set_kernel_smem(lrdmc_handle h, int optin) {
   CK(h, cudaFuncSetAttribute(k_propagate<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   CK(h, cudaFuncSetAttribute(k_init_walkers, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   CK(h, cudaFuncSetAttribute(k_eval_configs, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-  CK(h, cudaFuncSetAttribute(k_eloc_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  CK(h, cudaFuncSetAttribute(k_eloc_grad<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   CK(h, cudaFuncSetAttribute(k_propagate_m, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   CK(h, cudaFuncSetAttribute(k_init_walkers_m, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   CK(h, cudaFuncSetAttribute(k_eval_configs_m, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
@@ -873,6 +883,7 @@ lrdmc_status lrdmc_create(const lrdmc_system* sys, const lrdmc_trial_wf* wf, con
   }
   if (best_warps == 0) return fail(h, LRDMC_ERR_UNSUPPORTED, "walker working set exceeds shared memory");
   h->wpb = best_wpb;
+  h->sm_warps = best_warps;
   h->grid = std::max(1, std::min(best_bps * h->num_sms, P.scratch_warps / h->wpb));
   st = place_walkers(h, x0, nullptr);
   if (st != LRDMC_OK) return st;
@@ -896,6 +907,12 @@ lrdmc_status lrdmc_destroy(lrdmc_handle h) {
     DeviceGuard g(h->device);
     cudaStreamSynchronize(h->stream);
     cudaFree(h->gscr);
+  }
+  if (h->adj_gsm || h->adj_blk) {
+    DeviceGuard g(h->device);
+    cudaStreamSynchronize(h->stream);
+    if (h->adj_gsm) cudaFree(h->adj_gsm);
+    if (h->adj_blk) cudaFree(h->adj_blk);
   }
   delete h;
   return LRDMC_OK;
@@ -1376,18 +1393,39 @@ lrdmc_status lrdmc_local_energy_grad(lrdmc_handle h, int n, const double* x, dou
   const Plan& P = h->P;
   if (!h->gscr) {
     h->gscr_per_warp = (adj_scratch_doubles(P.L, P.n_shell) + 1) / 2 * 2;
-    CK(h, cudaMalloc(&h->gscr, sizeof(double) * h->gscr_per_warp * (size_t)h->grid * h->wpb));
+    if (h->sm_warps < ADJ_MIN_WARPS) {
+      // fewer than ADJ_MIN_WARPS shared-memory working sets per SM: working
+      // sets in global memory, as many warps as the registers allow
+      int bps = 0;
+      h->adj_wpb = 4;
+      CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_eloc_grad<true>, h->adj_wpb * 32,
+                                                          EXP_TAB * sizeof(double)));
+      if (bps < 1) return fail(h, LRDMC_ERR_UNSUPPORTED, "gradient kernel does not fit an SM");
+      h->adj_grid = bps * h->num_sms;
+      const size_t nw = (size_t)h->adj_grid * h->adj_wpb;
+      // the kernel addresses working sets at slot * s_stride and scratch at
+      // slot * scratch_doubles
+      CK(h, cudaMalloc(&h->adj_gsm, sizeof(double) * nw * ((size_t)P.L.s_stride + scratch_doubles(P.L, P.n_nuc))));
+      h->adj_scr = h->adj_gsm + nw * (size_t)P.L.s_stride;
+    } else {
+      h->adj_grid = h->grid;
+      h->adj_wpb = h->wpb;
+    }
+    const size_t nw = (size_t)h->adj_grid * h->adj_wpb;
+    CK(h, cudaMalloc(&h->adj_blk, sizeof(double) * nw * (size_t)P.L.g_stride));
+    CK(h, cudaMalloc(&h->gscr, sizeof(double) * h->gscr_per_warp * nw));
   }
-  // chunks of at most n_w configurations (the alternate walker buffer holds their evaluations)
-  const int np = param_count(P.n_nuc);
-  for (int off = 0; off < n; off += P.n_w) {
-    const int c = std::min(P.n_w, n - off);
-    k_eloc_grad<<<walker_grid(h, c), h->wpb * 32, smem_bytes(h), h->stream>>>(
-        h->S, P.L, h->alt, x + (size_t)off * 3 * P.n_e, c, h->prm.a, h->prm.node_rule, h->scr, h->gscr,
-        h->gscr_per_warp, eL ? eL + off : nullptr, logpsi ? logpsi + off : nullptr,
-        grad_eL ? grad_eL + (size_t)off * np : nullptr, grad_logpsi ? grad_logpsi + (size_t)off * np : nullptr);
-    LAUNCHED(h);
-  }
+  // one launch; each warp evaluates its configurations in its own walker block
+  const int grid = std::max(1, std::min(h->adj_grid, (n + h->adj_wpb - 1) / h->adj_wpb));
+  if (h->adj_gsm)
+    k_eloc_grad<true><<<grid, h->adj_wpb * 32, EXP_TAB * sizeof(double), h->stream>>>(
+        h->S, P.L, h->adj_blk, x, n, h->prm.a, h->prm.node_rule, h->adj_scr, h->gscr, h->gscr_per_warp, eL, logpsi,
+        grad_eL, grad_logpsi, h->adj_gsm);
+  else
+    k_eloc_grad<false><<<grid, h->adj_wpb * 32, smem_bytes(h), h->stream>>>(
+        h->S, P.L, h->adj_blk, x, n, h->prm.a, h->prm.node_rule, h->scr, h->gscr, h->gscr_per_warp, eL, logpsi,
+        grad_eL, grad_logpsi, nullptr);
+  LAUNCHED(h);
   return LRDMC_OK;
 }
 

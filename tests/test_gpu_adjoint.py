@@ -90,9 +90,10 @@ def test_autograd_entry_accumulates_weighted_gradients():
     np.testing.assert_array_equal(lr.params(), th2.numpy())
 
 
-def test_large_system_and_chunked_configurations():
-    """24 electrons (geometry caches in global memory) against the oracle, with
-    more configurations than walkers (two launches)."""
+def test_large_system_and_more_configurations_than_walkers():
+    """24 electrons (geometry caches and, for the gradient kernel, the whole
+    working set in global memory) against the oracle, with more configurations
+    than the handle has walkers."""
     import torch
     P = lib_or_skip()
     s = W.hydrogen_cluster(24, seed=5)
