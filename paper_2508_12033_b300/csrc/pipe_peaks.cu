@@ -32,6 +32,30 @@ __global__ void k_dfma_lanes(double* out, int iters, double s, int lanes) {
   if (r == 12345.678) out[0] = r;
 }
 
+// FP64 tensor-core MMA (m8n8k4, 512 FLOP per warp instruction) in ILP
+// independent accumulator chains; with NF > 0 every MMA is accompanied by NF
+// independent DFMAs per lane, to see whether the two share the FP64 pipe.
+template <int ILP, int NF>
+__global__ void k_dmma(double* out, int iters) {
+  const double a = (threadIdx.x & 31) * 1e-3, b = 0.999;
+  double c[ILP][2], f[NF > 0 ? NF : 1];
+  for (int j = 0; j < ILP; j++) { c[j][0] = j; c[j][1] = j + 0.5; }
+  for (int j = 0; j < (NF > 0 ? NF : 1); j++) f[j] = threadIdx.x * 1e-3 + j;
+  for (int i = 0; i < iters; i++) {
+#pragma unroll
+    for (int j = 0; j < ILP; j++)
+      asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+                   : "+d"(c[j][0]), "+d"(c[j][1])
+                   : "d"(a), "d"(b));
+#pragma unroll
+    for (int j = 0; j < NF; j++) f[j] = fma(f[j], 1.0000001, 0.999);
+  }
+  double r = 0;
+  for (int j = 0; j < ILP; j++) r += c[j][0] + c[j][1];
+  for (int j = 0; j < NF; j++) r += f[j];
+  if (r == 12345.678) out[0] = r;
+}
+
 template <int ILP>
 __global__ void k_ffma(float* out, int iters, float s) {
   float a[ILP];
@@ -155,6 +179,17 @@ int main() {
     const double active = (double)blocks * (threads / 32) * lanes * 8 * it;
     printf("DFMA %2d/32 lanes  %10.4g op/s  warp instructions cost %.2fx a full warp's\n", lanes,
            active / (ml * 1e-3), ml / ms);
+  }
+  {
+    // per warp instruction: 8 x 8 x 4 FMA = 256 FMA = 512 FLOP
+    const double warps = (double)blocks * threads / 32;
+    const float m0 = best_ms([&] { k_dmma<4, 0><<<blocks, threads>>>(dout, it / 4); });
+    const double dmma = warps * 4 * (it / 4) * 256 / (m0 * 1e-3);
+    printf("DMMA m8n8k4  %10.4g FMA/s  %8.3f TFLOP/s  (%.2fx DFMA)\n", dmma, 2 * dmma / 1e12, dmma / dfma);
+    const float m1 = best_ms([&] { k_dmma<4, 8><<<blocks, threads>>>(dout, it / 4); });
+    const float m2 = best_ms([&] { k_dfma<8><<<blocks, threads>>>(dout, it / 4, 1.0000001); });
+    printf("DMMA x4 + DFMA x8 per iteration: %.3f ms; DMMA alone %.3f ms, DFMA alone %.3f ms (sum %.3f)\n", m1, m0,
+           m2, m0 + m2);
   }
   ms = best_ms([&] { k_ffma<8><<<blocks, threads>>>(fout, it, 1.0000001f); });
   printf("FFMA      %12.4g op/s  %8.3f TFLOP/s  (%.1fx DFMA)\n", n8 * it / (ms * 1e-3), 2 * n8 * it / (ms * 1e-3) / 1e12,
