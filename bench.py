@@ -434,8 +434,14 @@ def run_mixed(args, P, s, x0, lr64, flush, rank):
     lb = P.Lrdmc(s, xb, A, seed=SEED + rank, reinv_period=50, p_gbar=10, precision=1)
     ms_big = time_lb_intervals(lb, P, flush, max(2, args.steps // 3), 2)
     lb.close()
+    # the FP64 form at the same size, the reference of the speed-up at 51200 walkers
+    lf = P.Lrdmc(s, xb, A, seed=SEED + rank, reinv_period=100, p_gbar=10)
+    ms_big64 = time_lb_intervals(lf, P, flush, max(2, args.steps // 3), 2)
+    lf.close()
     return {"value": N_W * N_PROJ / (ms / 1e3), "unit": "walker-steps/s", "ms_per_step": ms,
-            "n_w_51200": {"value": big * N_PROJ / (ms_big / 1e3), "ms_per_step": ms_big},
+            "n_w_51200": {"value": big * N_PROJ / (ms_big / 1e3), "ms_per_step": ms_big,
+                          "fp64_value": big * N_PROJ / (ms_big64 / 1e3), "fp64_ms_per_step": ms_big64,
+                          "speedup_vs_fp64": ms_big64 / ms_big},
             "energy_bias_mHa": 1e3 * bias, "energy_bias_err_mHa": 1e3 * err,
             "bias_sample": f"{N_W} equilibrated FP64 configurations, weights 1/(W - E0)",
             "max_abs_eL_diff_Ha": float(np.max(np.abs(d))),

@@ -924,10 +924,19 @@ __device__ void apply_hop_m(const DevSys& S, const Layout& L, const LayoutM& M, 
   orbital_rows_m(S, L, M, q, sr.n, sm, T, lane);
   double* B = bt + sr.bt_off;
   const int n = sr.n;
-  for (int j = lane; j < n; j += WARP) {
-    double acc = 0.0;
-    for (int k = 0; k < n; ++k) acc = fma(phiv[k], B[j * n + k], acc);
-    f[j] = acc;
+  {
+    // u_j = phi(r') . B[:, j], each dot split over G lanes
+    const int G = split_factor(n, n), chunk = (n + G - 1) / G, n_task = n * G;
+    for (int base = 0; base < n_task; base += WARP) {
+      const int task = base + lane, j = task / G, part = task - j * G;
+      double acc = 0.0;
+      if (task < n_task) {
+        const int k1 = min(n, (part + 1) * chunk);
+        for (int k = part * chunk; k < k1; ++k) acc = fma(phiv[k], B[j * n + k], acc);
+      }
+      for (int sh = 1; sh < G; sh <<= 1) acc += __shfl_xor_sync(FULL, acc, sh);
+      if (task < n_task && part == 0) f[j] = acc;
+    }
   }
   for (int k = lane; k < n; k += WARP) row[k] = B[sr.ii * n + k];
   __syncwarp();
