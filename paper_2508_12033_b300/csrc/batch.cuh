@@ -7,9 +7,12 @@
 // k's descriptor into its shared memory, partitions the rest of its shared
 // memory into count regions of system k's per-walker size and runs one walker
 // per warp with the same per-walker interval as the single-system kernels.
-// Small systems therefore run many warps per SM and large ones few, inside the
-// same launch; count is chosen by the host as the number of system-k regions
-// that fit in the CTA's shared memory.  The item order is chosen by the host
+// Small systems therefore run many warps per SM, inside the same launch; count
+// is chosen by the host as the number of system-k regions that fit in the
+// CTA's shared memory.  A system of which fewer than a few walkers would fit
+// (its O(N^2) caches already in global memory) instead keeps every walker's
+// working set in global memory (gsm_buf, gsm_stride doubles per warp of the
+// grid) and runs one walker on each of the CTA's warps.  The item order is chosen by the host
 // (systems in order, or the most expensive systems first so that the longest
 // items start early and the queue drains evenly).
 #pragma once
@@ -30,6 +33,7 @@ struct alignas(16) PropJob {
   double* cache;
   int n_w;
   int region;   // shared doubles per walker (even)
+  int gsm;      // 1: the walkers' working sets live in global memory (system too large to share a CTA)
 };
 constexpr int JOB_WORDS = (int)(sizeof(PropJob) / sizeof(double));
 static_assert(sizeof(PropJob) % 16 == 0, "PropJob must be a whole number of 16-byte words");
@@ -40,7 +44,7 @@ static_assert(sizeof(PropJob) % 16 == 0, "PropJob must be a whole number of 16-b
 template <int PREC>
 __global__ void k_propagate_batch(const PropJob* __restrict__ jobs, const int4* __restrict__ items, int n_items,
                                   unsigned* __restrict__ counter, double* __restrict__ scratch,
-                                  size_t scratch_per_warp) {
+                                  size_t scratch_per_warp, double* gsm_buf, size_t gsm_stride) {
   extern __shared__ double smem[];
   __shared__ int s_item;
   // the exponential table is the same constant table in every system image
@@ -59,14 +63,27 @@ __global__ void k_propagate_batch(const PropJob* __restrict__ jobs, const int4* 
     for (int o = threadIdx.x; o < JOB_WORDS; o += blockDim.x) reinterpret_cast<double*>(J)[o] = src[o];
     __syncthreads();
     if (wib < it.z) {
-      double* sm = regions + (size_t)wib * J->region;
-      if (PREC == 0) {
-        const Scr ws = warp_scratch_at(J->L, J->S.n_nuc, wscr);
-        propagate_walker<false>(J->S, J->L, J->state, J->cache, it.y + wib, J->P, T, sm, ws, lane);
+      const int w = it.y + wib;
+      if (J->gsm) {
+        double* sm = gsm_buf + ((size_t)blockIdx.x * (blockDim.x >> 5) + wib) * gsm_stride;
+        if (PREC == 0) {
+          const Scr ws = warp_scratch_at(J->L, J->S.n_nuc, wscr);
+          propagate_walker_impl<false, true>(J->S, J->L, J->state, J->cache, w, J->P, T, sm, ws, lane);
+        } else {
+          const ScrM ws = warp_scratch_m_at(J->L, J->M, wscr);
+          propagate_walker_m(J->S, J->L, J->M, J->state, J->cache, w, J->P, T, reinterpret_cast<float*>(sm), ws,
+                             lane);
+        }
       } else {
-        const ScrM ws = warp_scratch_m_at(J->L, J->M, wscr);
-        propagate_walker_m(J->S, J->L, J->M, J->state, J->cache, it.y + wib, J->P, T, reinterpret_cast<float*>(sm),
-                           ws, lane);
+        double* sm = regions + (size_t)wib * J->region;
+        if (PREC == 0) {
+          const Scr ws = warp_scratch_at(J->L, J->S.n_nuc, wscr);
+          propagate_walker<false>(J->S, J->L, J->state, J->cache, w, J->P, T, sm, ws, lane);
+        } else {
+          const ScrM ws = warp_scratch_m_at(J->L, J->M, wscr);
+          propagate_walker_m(J->S, J->L, J->M, J->state, J->cache, w, J->P, T, reinterpret_cast<float*>(sm), ws,
+                             lane);
+        }
       }
     }
     __syncthreads();   // the descriptor and s_item are rewritten for the next item

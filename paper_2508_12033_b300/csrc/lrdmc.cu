@@ -33,6 +33,10 @@ constexpr int DSTAT_NEXT = 8;
 // The gradient kernel keeps its working sets in global memory when shared
 // memory would hold fewer than this many of them per SM.
 constexpr int ADJ_MIN_WARPS = 8;
+// A batched system of which fewer walkers than this fit in a CTA's shared
+// memory (and whose O(N^2) caches are in global memory) runs with its working
+// sets in global memory, one walker on each of the CTA's warps.
+constexpr int BATCH_GSM_FIT = 4;
 // Walkers whose shared-memory layout would exceed these sizes keep their O(N^2)
 // caches in the cache block (see make_plan).  Measured on water-methane: the
 // FP64 kernel, bound by the FP64 pipe, is faster with its geometry in shared
@@ -513,6 +517,9 @@ struct lrdmc_batch_s {
   size_t cta_dyn = 0;            // dynamic shared bytes per CTA of the current launch shape
   int wmax = 1, grid = 1;        // warps per CTA, CTAs
   std::vector<int> fit;          // walkers per item, per system, for the current shape
+  std::vector<int> gsm;          // per system: working sets in global memory (current shape)
+  double* d_gsm = nullptr;       // those working sets: grid x wmax warps x gsm_stride doubles
+  size_t gsm_stride = 0, gsm_cap = 0;
   size_t scratch_per_warp = 0;   // global scratch doubles per warp
   size_t scratch_warps = 0;      // warps the scratch is sized for
   int total = 0, n_items = 0;    // walkers over all systems; items of the current shape
@@ -562,16 +569,25 @@ static int batch_region(lrdmc_handle h) {
 // every system, warps per CTA and CTAs per SM.  *ok = false when a system
 // does not fit or the kernel does not fit on an SM.
 static lrdmc_status batch_shape(lrdmc_batch b, size_t cta_dyn, bool* ok, std::vector<int>& fit, int* wmax,
-                                int* bps) {
+                                int* bps, std::vector<int>* gsm = nullptr) {
   *ok = false;
   const long avail = (long)cta_dyn / (long)sizeof(double) - EXP_TAB - JOB_WORDS;
   const int cap = std::max(1, b->max_threads / 32);
   fit.assign(b->h.size(), 0);
+  if (gsm) gsm->assign(b->h.size(), 0);
   int w = 0;
   for (size_t k = 0; k < b->h.size(); ++k) {
+    const Plan& P = b->h[k]->P;
     const long n = avail / batch_region(b->h[k]);
-    if (n < 1) return LRDMC_OK;
-    fit[k] = (int)std::min<long>(std::min<long>(n, cap), b->h[k]->P.n_w);
+    const bool glob = P.precision == 0 ? P.L.geo_glob != 0 : P.M.glob != 0;
+    if (n < BATCH_GSM_FIT && glob) {
+      // too large to share a CTA's shared memory: global working sets, one walker per warp
+      fit[k] = std::min(cap, P.n_w);
+      if (gsm) (*gsm)[k] = 1;
+    } else {
+      if (n < 1) return LRDMC_OK;
+      fit[k] = (int)std::min<long>(std::min<long>(n, cap), P.n_w);
+    }
     w = std::max(w, fit[k]);
   }
   *wmax = w;
@@ -608,14 +624,29 @@ static lrdmc_status batch_items(lrdmc_batch b) {
 // Adopt the launch shape for cta_dyn bytes (it must fit) and rebuild the items.
 static lrdmc_status batch_use(lrdmc_batch b, size_t cta_dyn) {
   bool ok = false;
-  std::vector<int> fit;
+  std::vector<int> fit, gsm;
   int w = 0, bps = 0;
-  lrdmc_status st = batch_shape(b, cta_dyn, &ok, fit, &w, &bps);
+  lrdmc_status st = batch_shape(b, cta_dyn, &ok, fit, &w, &bps, &gsm);
   if (st != LRDMC_OK) return st;
   if (!ok) return bfail(b, LRDMC_ERR_UNSUPPORTED, "batched launch shape does not fit");
   const int grid = std::max(1, std::min(bps * b->num_sms, (int)(b->scratch_warps / w)));
+  // global working sets of the systems that do not share a CTA (grown, never shrunk)
+  size_t stride = 0;
+  for (size_t k = 0; k < b->h.size(); ++k)
+    if (gsm[k]) stride = std::max(stride, (size_t)batch_region(b->h[k]));
+  const size_t need = stride * (size_t)grid * w;
+  if (need > b->gsm_cap) {
+    BCK(b, cudaStreamSynchronize(b->stream));
+    if (b->d_gsm) BCK(b, cudaFree(b->d_gsm));
+    b->d_gsm = nullptr;
+    b->gsm_cap = 0;
+    BCK(b, cudaMalloc(&b->d_gsm, sizeof(double) * need));
+    b->gsm_cap = need;
+  }
+  b->gsm_stride = stride;
   b->cta_dyn = cta_dyn;
   b->fit = fit;
+  b->gsm = gsm;
   b->wmax = w;
   b->grid = grid;
   return batch_items(b);
@@ -636,6 +667,7 @@ static void batch_free(lrdmc_batch b) {
   cudaFree(b->d_scratch);
   cudaFree(b->d_stats);
   cudaFree(b->d_status);
+  cudaFree(b->d_gsm);
   for (lrdmc_handle h : b->h) lrdmc_destroy(h);
   b->h.clear();
 }
@@ -654,18 +686,17 @@ static lrdmc_status batch_launch(lrdmc_batch b, const lrdmc_schedule* sch) {
     J.cache = h->cache;
     J.n_w = h->P.n_w;
     J.region = batch_region(h);
+    J.gsm = b->gsm[k];
     h->last_kind = sch->kind;
   }
   BCK(b, cudaMemcpyAsync(b->d_jobs, b->jobs.data(), sizeof(PropJob) * n, cudaMemcpyHostToDevice, b->stream));
   BCK(b, cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned), b->stream));
   if (b->precision == 0)
-    k_propagate_batch<0><<<b->grid, b->wmax * 32, b->cta_dyn, b->stream>>>(b->d_jobs, b->d_items, b->n_items,
-                                                                           b->d_counter, b->d_scratch,
-                                                                           b->scratch_per_warp);
+    k_propagate_batch<0><<<b->grid, b->wmax * 32, b->cta_dyn, b->stream>>>(
+        b->d_jobs, b->d_items, b->n_items, b->d_counter, b->d_scratch, b->scratch_per_warp, b->d_gsm, b->gsm_stride);
   else
-    k_propagate_batch<1><<<b->grid, b->wmax * 32, b->cta_dyn, b->stream>>>(b->d_jobs, b->d_items, b->n_items,
-                                                                           b->d_counter, b->d_scratch,
-                                                                           b->scratch_per_warp);
+    k_propagate_batch<1><<<b->grid, b->wmax * 32, b->cta_dyn, b->stream>>>(
+        b->d_jobs, b->d_items, b->n_items, b->d_counter, b->d_scratch, b->scratch_per_warp, b->d_gsm, b->gsm_stride);
   BLAUNCHED(b);
   return LRDMC_OK;
 }

@@ -106,3 +106,21 @@ def test_batch_timing_and_refusals():
     import ctypes
     s = P.binding._Schedule(1, 5, 0.0, 10, 1)
     assert batch.lib.lrdmc_batch_propagate(batch._b, ctypes.byref(s)) == 7
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_large_system_with_global_working_sets_follows_its_single_trajectory(precision):
+    """A 96-electron cluster: its working set (about 70 KB in FP64) leaves fewer
+    than four walkers per CTA at every launch shape, so the batched kernel runs
+    it with the working sets in global memory, one walker per warp, next to a
+    small system that shares CTAs in shared memory."""
+    P = lib_or_skip()
+    systems = [(W.hydrogen_cluster(96, seed=4), 10, 13), (W.h2_sto3g(), 24, 3)]
+    x0s = [W.initial_walkers(s, n, seed=sd + 20) for s, n, sd in systems]
+    batch = P.LrdmcBatch([s for s, _, _ in systems], x0s, A, [sd for _, _, sd in systems], reinv_period=7,
+                         precision=precision)
+    _run(batch, P, n_lb=2)
+    for (s, n, sd), x0, h in zip(systems, x0s, batch.handles):
+        single = P.Lrdmc(s, x0, A, seed=sd, reinv_period=7, precision=precision)
+        _run(single, P, n_lb=2)
+        _same(h, single)
