@@ -77,31 +77,85 @@ def algorithmic_ops_per_walker_step(n_e, n_nuc, n_bf, n_prim, n_sig, n_s_shell, 
 
 # ----------------------------------------------------------------- clocks
 class ClockSampler:
+    """SM clock and clock-event reasons during a timed region: NVML every 5 ms
+    from a thread (the GPU found by the CUDA device's PCI bus id), else
+    nvidia-smi every 200 ms."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = (("hw_slowdown", 0x8), ("hw_thermal_slowdown", 0x40), ("sw_thermal_slowdown", 0x20),
+               ("sw_power_cap", 0x4))
 
     def __init__(self, gpu_index=0):
         self.rows = []
         self.proc = None
         self.gpu = gpu_index
+        self.nvml = None
+        self.stop = threading.Event()
+        self.source = None
+
+    def _nvml_handle(self):
+        """NVML through the driver's libnvidia-ml (public C API, read-only calls)."""
+        import ctypes
+        import torch
+        nv = ctypes.CDLL("libnvidia-ml.so.1")
+        if nv.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        pr = torch.cuda.get_device_properties(self.gpu)
+        h = ctypes.c_void_p()
+        bus = b"%08X:%02X:%02X.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
+        if nv.nvmlDeviceGetHandleByPciBusId_v2(ctypes.c_char_p(bus), ctypes.byref(h)) != 0:
+            raise OSError("no NVML device at " + bus.decode())
+        return nv, h
 
     def __enter__(self):
+        try:
+            nv, h = self._nvml_handle()
+            self.nvml = (nv, h)
+            self.source = "nvml"
+            self.t = threading.Thread(target=self._poll, daemon=True)
+            self.t.start()
+            return self
+        except Exception:
+            self.nvml = None
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.source = "nvidia-smi"
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except OSError:
             self.proc = None
         return self
 
+    def _poll(self):
+        import ctypes
+        nv, h = self.nvml
+        NVML_CLOCK_SM = 1
+        clk, mx, bits = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        if nv.nvmlDeviceGetMaxClockInfo(h, NVML_CLOCK_SM, ctypes.byref(mx)) != 0:
+            return
+        while not self.stop.is_set():
+            if (nv.nvmlDeviceGetClockInfo(h, NVML_CLOCK_SM, ctypes.byref(clk)) != 0 or
+                    nv.nvmlDeviceGetCurrentClocksThrottleReasons(h, ctypes.byref(bits)) != 0):
+                break
+            self.rows.append((float(clk.value), float(mx.value),
+                              [nm for nm, b in self.REASONS if bits.value & b]))
+            self.stop.wait(0.005)
+
     def _read(self):
+        names = [nm for nm, _ in self.REASONS]
         for line in self.proc.stdout:
-            self.rows.append([v.strip() for v in line.split(",")])
+            r = [v.strip() for v in line.split(",")]
+            if len(r) >= 9 and r[1].replace(".", "").isdigit() and r[2].replace(".", "").isdigit():
+                self.rows.append((float(r[1]), float(r[2]),
+                                  [nm for k, nm in enumerate(names) if r[5 + k].lower().startswith("active")]))
 
     def __exit__(self, *a):
+        self.stop.set()
+        if self.nvml:
+            self.t.join(timeout=5)
         if self.proc:
             self.proc.terminate()
             try:
@@ -110,17 +164,11 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = set()
-        for r in self.rows:
-            if len(r) >= 9:
-                for k, nm in enumerate(names):
-                    if r[5 + k].lower().startswith("active"):
-                        reasons.add(nm)
+        sm = [r[0] for r in self.rows]
+        mx = [r[1] for r in self.rows]
+        reasons = sorted({nm for r in self.rows for nm in r[2]})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": reasons, "samples": len(sm), "source": self.source}
 
 
 # ----------------------------------------------------------------- oracle baseline
