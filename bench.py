@@ -308,13 +308,15 @@ def run_gpu(args, rank, world):
     mixed = run_mixed(args, P, s, x0, lr, flush, rank) if not args.no_mixed else None
     a_scan = run_a_scan(P) if rank == 0 and not args.no_a_scan else None
     adjoint = run_adjoint(P) if rank == 0 and not args.no_adjoint else None
+    large = run_large(P, flush) if rank == 0 and not args.no_large else None
     batch = None
     if rank == 0 and not args.no_batch:
         batch = {"mixed": run_batch(P, 1), "fp64": run_batch(P, 0)}
     return dict(value=value, t_total=t_total, step_ms=statistics.mean(step_ms), prop_ms=statistics.mean(prop_ms),
                 launches=launches, achieved=achieved, clocks=clk.summary(), conv_rate=conv_rate,
                 conv_moves=conv_moves, tau=tau, e2e=e2e_value, h2d=h2d, d2h=d2h, slots=slots,
-                energy=lr.energy(), mixed=mixed, imbalance=imbalance, a_scan=a_scan, batch=batch, adjoint=adjoint)
+                energy=lr.energy(), mixed=mixed, imbalance=imbalance, a_scan=a_scan, batch=batch, adjoint=adjoint,
+                large=large)
 
 
 def aggregate_throughput(t_local, units_local, world, device="cpu"):
@@ -399,6 +401,25 @@ def run_adjoint(P):
     return {"system": "H128 chain, 8192 configurations, FP64", "parameters": lr.param_count(),
             "ms": dt * 1e3, "configurations_per_s": 8192 / dt,
             "gradient_components_per_s": 2 * 8192 * lr.param_count() / dt, "all_finite": finite}
+
+
+def run_large(P, flush, steps=3):
+    """Single large systems: hydrogen clusters of 64 and 128 atoms (all-electron,
+    s + p GTO per atom) at a = 0.25, load-balanced intervals of 20 hops, FP64 and
+    mixed.  Their shared-memory layouts would leave fewer than 8 warps per SM,
+    so both kernels run with the working sets in global memory."""
+    import workloads as W
+    out = {}
+    for n_atoms, n_w in ((64, 4096), (128, 1024)):
+        s = W.hydrogen_cluster(n_atoms, seed=3)
+        x0 = W.initial_walkers(s, n_w, seed=11)
+        for prec, name in ((0, "fp64"), (1, "mixed")):
+            lr = P.Lrdmc(s, x0, 0.25, seed=SEED, reinv_period=50, p_gbar=10, precision=prec)
+            ms = time_lb_intervals(lr, P, flush, steps, 2)
+            lr.close()
+            out[f"H{n_atoms}_{name}"] = {"n_e": s.n_elec, "n_w": n_w, "ms_per_step": ms,
+                                         "value": n_w * N_PROJ / (ms / 1e3), "unit": "walker-steps/s"}
+    return out
 
 
 def run_batch(P, precision, steps=3):
@@ -507,6 +528,7 @@ def main():
     ap.add_argument("--no-a-scan", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-large", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -573,6 +595,7 @@ def main():
             "a_scan": res["a_scan"],
             "batch": res["batch"],
             "adjoint": res["adjoint"],
+            "large_systems": res["large"],
             "gpu_launches": res["launches"],
             "clocks": res["clocks"],
             "energy": {"E": res["energy"][0], "err": res["energy"][1]},

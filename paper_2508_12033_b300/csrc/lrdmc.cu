@@ -37,6 +37,10 @@ constexpr int ADJ_MIN_WARPS = 8;
 // memory (and whose O(N^2) caches are in global memory) runs with its working
 // sets in global memory, one walker on each of the CTA's warps.
 constexpr int BATCH_GSM_FIT = 4;
+// Single-system propagation keeps the working sets in global memory when
+// shared memory (SMEM_PER_SM per SM) would hold fewer than PROP_MIN_WARPS of them.
+constexpr int PROP_MIN_WARPS = 8;
+constexpr size_t SMEM_PER_SM = 227 * 1024;
 // Walkers whose shared-memory layout would exceed these sizes keep their O(N^2)
 // caches in the cache block (see make_plan).  Measured on water-methane: the
 // FP64 kernel, bound by the FP64 pipe, is faster with its geometry in shared
@@ -109,8 +113,10 @@ struct Plan {
   size_t smem_per_warp = 0;
   // workspace offsets (bytes)
   size_t o_sys = 0, sys_bytes = 0, o_state = 0, o_alt = 0, state_bytes = 0, o_cache = 0, o_cache_alt = 0,
-         cache_bytes = 0, o_stats = 0, o_q = 0, o_src = 0, o_dstat = 0, o_stamps = 0, o_scr = 0, total = 0;
+         cache_bytes = 0, o_stats = 0, o_q = 0, o_src = 0, o_dstat = 0, o_stamps = 0, o_scr = 0, o_gsm = 0,
+         total = 0;
   int scratch_warps = 0;
+  bool gsm = false;   // propagate with the working sets in global memory (large systems)
   // system image offsets (bytes, inside the sys block)
   size_t i_R, i_Z, i_rc, i_irc, i_j1A, i_j1B, i_exps, i_coefs, i_C, i_kind, i_atom, i_l, i_nprim, i_off, i_bf, i_ash,
       i_tab, i_f_R, i_f_Z, i_f_rc, i_f_j1A, i_f_j1B, i_f_exps, i_f_coefs, i_f_C, i_irc2, i_erf;
@@ -252,6 +258,12 @@ bool make_plan(const lrdmc_system* sys, const lrdmc_trial_wf* wf, const lrdmc_pa
   P.scratch_warps = round_up(std::min(P.n_w, SCRATCH_WARPS_CAP), 4);
   const size_t per_warp = P.precision == 0 ? scratch_doubles(L, P.n_nuc) : scratch_doubles_m(L, P.M);
   P.o_scr = w; w += align_up(sizeof(double) * per_warp * (size_t)P.scratch_warps);
+  // a system whose shared layout leaves fewer than PROP_MIN_WARPS warps per SM
+  // (and whose O(N^2) caches are already in global memory) is propagated with
+  // the working sets in global memory, one region per scratch warp
+  const bool glob = P.precision == 0 ? L.geo_glob != 0 : P.M.glob != 0;
+  P.gsm = glob && P.smem_per_warp * PROP_MIN_WARPS > SMEM_PER_SM;
+  if (P.gsm) { P.o_gsm = w; w += align_up(P.smem_per_warp * (size_t)P.scratch_warps); }
   P.total = w;
   return true;
 }
@@ -333,6 +345,8 @@ struct lrdmc_s {
   // memory (adj_gsm, with their own per-warp scratch adj_scr)
   int adj_grid = 0, adj_wpb = 0;
   int sm_warps = 0;              // working sets per SM that shared memory holds (launch shape of create)
+  int prop_grid = 0, prop_wpb = 0;   // propagate launch shape (differs from grid/wpb with P.gsm)
+  void* gsm = nullptr;           // P.gsm: the propagate kernels' working sets
   double* adj_gsm = nullptr;
   double* adj_scr = nullptr;
   double* adj_blk = nullptr;     // per-warp walker blocks of the gradient kernel
@@ -387,12 +401,12 @@ static int smem_bytes(lrdmc_handle h) {
 // handle in the process, so it is raised to the device's opt-in maximum (it
 // permits, it reserves nothing); each launch still requests only its own size.
 static lrdmc_status set_kernel_smem(lrdmc_handle h, int optin) {
-  CK(h, cudaFuncSetAttribute(k_propagate<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-  CK(h, cudaFuncSetAttribute(k_propagate<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  CK(h, cudaFuncSetAttribute(k_propagate<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  CK(h, cudaFuncSetAttribute(k_propagate<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   CK(h, cudaFuncSetAttribute(k_init_walkers, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   CK(h, cudaFuncSetAttribute(k_eval_configs, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   CK(h, cudaFuncSetAttribute(k_eloc_grad<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-  CK(h, cudaFuncSetAttribute(k_propagate_m, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  CK(h, cudaFuncSetAttribute(k_propagate_m<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   CK(h, cudaFuncSetAttribute(k_init_walkers_m, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   CK(h, cudaFuncSetAttribute(k_eval_configs_m, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   return LRDMC_OK;
@@ -889,6 +903,7 @@ lrdmc_status lrdmc_create(const lrdmc_system* sys, const lrdmc_trial_wf* wf, con
   h->dstat = (int32_t*)(base + P.o_dstat);
   h->stamps = (unsigned long long*)(base + P.o_stamps);
   h->scr = (double*)(base + P.o_scr);
+  h->gsm = P.gsm ? (void*)(base + P.o_gsm) : nullptr;
   CK(h, cudaMemsetAsync(h->dstat, 0, sizeof(int32_t) * 16, h->stream));
   // launch geometry: up to 4 walkers (warps) per CTA within the shared-memory budget
   int smem_optin = 0;
@@ -903,9 +918,9 @@ lrdmc_status lrdmc_create(const lrdmc_system* sys, const lrdmc_trial_wf* wf, con
     if ((size_t)smem_bytes(h) > (size_t)smem_optin) break;
     int bps = 0;
     if (P.precision == 0)
-      CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_propagate<false>, wpb * 32, smem_bytes(h)));
+      CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_propagate<false, false>, wpb * 32, smem_bytes(h)));
     else
-      CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_propagate_m, wpb * 32, smem_bytes(h)));
+      CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_propagate_m<false>, wpb * 32, smem_bytes(h)));
     if (bps >= 1 && bps * wpb >= best_warps) {
       best_warps = bps * wpb;
       best_wpb = wpb;
@@ -916,6 +931,21 @@ lrdmc_status lrdmc_create(const lrdmc_system* sys, const lrdmc_trial_wf* wf, con
   h->wpb = best_wpb;
   h->sm_warps = best_warps;
   h->grid = std::max(1, std::min(best_bps * h->num_sms, P.scratch_warps / h->wpb));
+  h->prop_wpb = h->wpb;
+  h->prop_grid = h->grid;
+  if (P.gsm) {
+    // working sets in global memory: as many 4-warp CTAs as the registers allow
+    int bps = 0;
+    h->prop_wpb = 4;
+    if (P.precision == 0)
+      CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_propagate<false, true>, 4 * 32,
+                                                          EXP_TAB * sizeof(double)));
+    else
+      CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_propagate_m<true>, 4 * 32,
+                                                          EXP_TAB * sizeof(double)));
+    if (bps < 1) return fail(h, LRDMC_ERR_UNSUPPORTED, "propagate kernel does not fit an SM");
+    h->prop_grid = std::max(1, std::min(bps * h->num_sms, P.scratch_warps / h->prop_wpb));
+  }
   st = place_walkers(h, x0, nullptr);
   if (st != LRDMC_OK) return st;
   std::vector<double> ev(4 * (size_t)P.n_w);
@@ -959,17 +989,36 @@ lrdmc_status lrdmc_propagate(lrdmc_handle h, const lrdmc_schedule* sch) {
   // dynamic walker assignment: the work counter (status word 8) starts at zero
   sp.next = (unsigned*)(h->dstat + DSTAT_NEXT);
   CK(h, cudaMemsetAsync(sp.next, 0, sizeof(unsigned), h->stream));
-  const int smem = smem_bytes(h);
-  if (h->P.precision == 0)
-    if (sp.rotate)
-      k_propagate<true><<<walker_grid(h, h->P.n_w), h->wpb * 32, smem, h->stream>>>(h->S, h->P.L, h->state,
-                                                                                  h->cache, h->P.n_w, sp, h->scr);
+  const Plan& P = h->P;
+  const int grid = std::max(1, std::min(h->prop_grid, (P.n_w + h->prop_wpb - 1) / h->prop_wpb));
+  const int threads = h->prop_wpb * 32;
+  const int smem = P.gsm ? (int)(EXP_TAB * sizeof(double)) : smem_bytes(h);
+  double* gd = (double*)h->gsm;
+  float* gf = (float*)h->gsm;
+  if (P.precision == 0) {
+    if (sp.rotate) {
+      if (P.gsm)
+        k_propagate<true, true><<<grid, threads, smem, h->stream>>>(h->S, P.L, h->state, h->cache, P.n_w, sp, h->scr,
+                                                                    gd);
+      else
+        k_propagate<true, false><<<grid, threads, smem, h->stream>>>(h->S, P.L, h->state, h->cache, P.n_w, sp,
+                                                                     h->scr, nullptr);
+    } else {
+      if (P.gsm)
+        k_propagate<false, true><<<grid, threads, smem, h->stream>>>(h->S, P.L, h->state, h->cache, P.n_w, sp,
+                                                                     h->scr, gd);
+      else
+        k_propagate<false, false><<<grid, threads, smem, h->stream>>>(h->S, P.L, h->state, h->cache, P.n_w, sp,
+                                                                      h->scr, nullptr);
+    }
+  } else {
+    if (P.gsm)
+      k_propagate_m<true><<<grid, threads, smem, h->stream>>>(h->S, P.L, P.M, h->state, h->cache, P.n_w, sp, h->scr,
+                                                              gf);
     else
-      k_propagate<false><<<walker_grid(h, h->P.n_w), h->wpb * 32, smem, h->stream>>>(h->S, h->P.L, h->state,
-                                                                                   h->cache, h->P.n_w, sp, h->scr);
-  else
-    k_propagate_m<<<walker_grid(h, h->P.n_w), h->wpb * 32, smem, h->stream>>>(h->S, h->P.L, h->P.M, h->state,
-                                                                              h->cache, h->P.n_w, sp, h->scr);
+      k_propagate_m<false><<<grid, threads, smem, h->stream>>>(h->S, P.L, P.M, h->state, h->cache, P.n_w, sp,
+                                                               h->scr, nullptr);
+  }
   LAUNCHED(h);
   h->last_kind = sch->kind;
   return LRDMC_OK;
@@ -1495,7 +1544,7 @@ lrdmc_status lrdmc_interval_timing(lrdmc_handle h, double out[6]) {
     mx = std::max(mx, d);
   }
   const double span = (double)(t1 - t0) * 1e-6;
-  const int resident = std::min(n, h->grid * h->wpb);
+  const int resident = std::min(n, h->prop_grid * h->prop_wpb);
   double mv = 0.0, mvmax = 0.0;
   for (int a = 0; a < n; ++a) {
     const double m = mvs[a];

@@ -1322,15 +1322,18 @@ __device__ __forceinline__ void propagate_walker(const DevSys& S, const Layout& 
   else propagate_walker_impl<ROT, false>(S, L, state, cache, w, P, T, sm, wscr, lane);
 }
 
-template <bool ROT>
+// GSM: the warps' working sets live in global memory (gsm + slot * s_stride)
+// instead of shared memory; used for systems whose shared layout would let
+// only a few warps share an SM (their O(N^2) caches are in global memory too).
+template <bool ROT, bool GSM>
 __global__ void k_propagate(DevSys S, Layout L, double* __restrict__ state, double* __restrict__ cache, int n_w,
-                            StepParams P, double* scratch) {
+                            StepParams P, double* scratch, double* gsm) {
   extern __shared__ double smem[];
   const double* T = stage_table(S, smem);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  double* sm = smem + EXP_TAB + wib * L.s_stride;
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   const int slot = blockIdx.x * (blockDim.x >> 5) + wib;
+  double* sm = GSM ? gsm + (size_t)slot * L.s_stride : smem + EXP_TAB + wib * L.s_stride;
   const Scr wscr = warp_scratch(L, S.n_nuc, scratch, slot);
   for (int w = slot; w < n_w; w = next_walker(P, w, nwarps, lane))
     propagate_walker<ROT>(S, L, state, cache, w, P, T, sm, wscr, lane);

@@ -1180,14 +1180,18 @@ __device__ void propagate_walker_m(const DevSys& S, const Layout& L, const Layou
 // At most 72 registers per thread (8 bytes spilled): the kernel is latency
 // bound, and 28 resident warps per SM (4096 walkers in one wave on 148 SMs)
 // run it faster than the 20 that its unconstrained 94 registers allow.
+// GSM: working sets in global memory (gsm + slot * M.stride floats), as in
+// the FP64 kernel.
+template <bool GSM>
 __global__ void __maxnreg__(72) k_propagate_m(DevSys S, Layout L, LayoutM M, double* __restrict__ state,
-                                              double* __restrict__ cache, int n_w, StepParams P, double* scratch) {
+                                              double* __restrict__ cache, int n_w, StepParams P, double* scratch,
+                                              float* gsm) {
   extern __shared__ double smem[];
   const double* T = stage_table(S, smem);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  float* sm = (float*)(smem + EXP_TAB) + wib * M.stride;
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   const int slot = blockIdx.x * (blockDim.x >> 5) + wib;
+  float* sm = GSM ? gsm + (size_t)slot * M.stride : (float*)(smem + EXP_TAB) + wib * M.stride;
   const ScrM wscr = warp_scratch_m(L, M, scratch, slot);
   for (int w = slot; w < n_w; w = next_walker(P, w, nwarps, lane))
     propagate_walker_m(S, L, M, state, cache, w, P, T, sm, wscr, lane);
