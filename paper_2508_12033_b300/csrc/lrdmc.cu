@@ -119,7 +119,7 @@ struct Plan {
   bool gsm = false;   // propagate with the working sets in global memory (large systems)
   // system image offsets (bytes, inside the sys block)
   size_t i_R, i_Z, i_rc, i_irc, i_j1A, i_j1B, i_exps, i_coefs, i_C, i_kind, i_atom, i_l, i_nprim, i_off, i_bf, i_ash,
-      i_tab, i_f_R, i_f_Z, i_f_rc, i_f_j1A, i_f_j1B, i_f_exps, i_f_coefs, i_f_C, i_irc2, i_erf;
+      i_tab, i_f_R, i_f_Z, i_f_rc, i_f_j1A, i_f_j1B, i_f_exps, i_f_coefs, i_f_C, i_irc2, i_erf, i_ord;
   std::string err;
 };
 
@@ -229,6 +229,7 @@ bool make_plan(const lrdmc_system* sys, const lrdmc_trial_wf* wf, const lrdmc_pa
   P.i_off = take(sizeof(int) * P.n_shell);
   P.i_bf = take(sizeof(int) * P.n_shell);
   P.i_ash = take(sizeof(int) * (P.n_nuc + 1));
+  P.i_ord = take(sizeof(int) * P.n_shell);
   P.i_tab = take(sizeof(double) * EXP_TAB);
   P.i_irc2 = take(sizeof(double) * P.n_nuc);
   P.i_erf = take(sizeof(double) * ERF_INT * ERF_NC);
@@ -829,6 +830,16 @@ lrdmc_status lrdmc_create(const lrdmc_system* sys, const lrdmc_trial_wf* wf, con
   puti(P.i_off, r_off.data(), P.n_shell);
   puti(P.i_bf, r_bf.data(), P.n_shell);
   puti(P.i_ash, ash.data(), P.n_nuc + 1);
+  {
+    // shells in the order the per-hop basis pass takes them: non-p first, so
+    // that lanes of one warp pass mostly share a shell kind
+    std::vector<int> ord;
+    for (int k = 0; k < P.n_shell; ++k)
+      if (r_l[k] != 1) ord.push_back(k);
+    for (int k = 0; k < P.n_shell; ++k)
+      if (r_l[k] == 1) ord.push_back(k);
+    puti(P.i_ord, ord.data(), ord.size());
+  }
   double tab[EXP_TAB];
   for (int j = 0; j < EXP_TAB; ++j) tab[j] = (double)exp2l((long double)j / EXP_TAB);
   putd(P.i_tab, tab, EXP_TAB);
@@ -867,6 +878,7 @@ lrdmc_status lrdmc_create(const lrdmc_system* sys, const lrdmc_trial_wf* wf, con
   S.sh_off = (const int*)(dsys + P.i_off);
   S.sh_bf = (const int*)(dsys + P.i_bf);
   S.atom_sh = (const int*)(dsys + P.i_ash);
+  S.sh_ord = (const int*)(dsys + P.i_ord);
   S.exptab = (const double*)(dsys + P.i_tab);
   S.irc2 = (const double*)(dsys + P.i_irc2);
   S.erftab = (const double*)(dsys + P.i_erf);

@@ -35,44 +35,34 @@ __device__ __forceinline__ void shell_derivs(const DevSys& S, int s, const doubl
   const int np = __ldg(S.sh_nprim + s);
   const int off = __ldg(S.sh_off + s);
   const int bf = __ldg(S.sh_bf + s);
-  if (l == -1) {
-    // h = c exp(-z r): grad = h' d / r, lap = (z^2 - 2 z / r) h
-    const double ir = rsqrt_nr(r2);
-    const double r = r2 * ir;
-    double v = 0.0, dr = 0.0, lp = 0.0;
-    for (int q = 0; q < np; ++q) {
-      const double z = __ldg(S.exps + off + q);
-      const double h = __ldg(S.coefs + off + q) * exp_tab(-z * r, T);
-      v += h;
-      dr += -z * h;
-      lp += (z * z - 2.0 * z * ir) * h;
-    }
-    out[bf] = v;
-    for (int m = 0; m < 3; ++m) out[(1 + m) * n_bf + bf] = dr * d[m] * ir;
-    out[4 * n_bf + bf] = lp;
-  } else if (l == 0) {
-    // h = c exp(-a r^2): grad = -2a d h, lap = (4 a^2 r^2 - 6 a) h
-    double v = 0.0, gs = 0.0, lp = 0.0;
-    for (int q = 0; q < np; ++q) {
-      const double al = __ldg(S.exps + off + q);
-      const double h = __ldg(S.coefs + off + q) * exp_tab(-al * r2, T);
-      v += h;
-      gs += -2.0 * al * h;
-      lp += (4.0 * al * al * r2 - 6.0 * al) * h;
-    }
-    out[bf] = v;
-    for (int m = 0; m < 3; ++m) out[(1 + m) * n_bf + bf] = gs * d[m];
-    out[4 * n_bf + bf] = lp;
+  // one primitive loop for every shell kind (so that a warp with mixed kinds
+  // evaluates the exponentials once): h = c exp(-z r) for the Slater 1s kind,
+  // c exp(-a r^2) for Gaussians; s0 = sum h, s1 = sum c1 h, s2 = sum c2 h with
+  //   Slater: c1 = -z, c2 = z^2 - 2 z / r           (h' and lap h)
+  //   s:      c1 = -2a, c2 = 4 a^2 r^2 - 6 a        (grad = c1 h d, lap h)
+  //   p:      c1 = -2a, c2 = 4 a^2 r^2 - 10 a       (d_m times the radial part)
+  const bool sl = l == -1;
+  const double ir = sl ? rsqrt_nr(r2) : 0.0;
+  const double arg = sl ? r2 * ir : r2;
+  const double k6 = l == 1 ? 10.0 : 6.0;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  for (int q = 0; q < np; ++q) {
+    const double z = __ldg(S.exps + off + q);
+    const double h = __ldg(S.coefs + off + q) * exp_tab(-z * arg, T);
+    const double c1 = sl ? -z : -2.0 * z;
+    const double c2 = sl ? z * z - 2.0 * z * ir : (4.0 * z * z * r2 - k6 * z);
+    s0 += h;
+    s1 = fma(c1, h, s1);
+    s2 = fma(c2, h, s2);
+  }
+  if (l != 1) {
+    // Slater: grad = h' d / r; s: grad = c1 h d
+    const double g = sl ? s1 * ir : s1;
+    out[bf] = s0;
+    for (int m = 0; m < 3; ++m) out[(1 + m) * n_bf + bf] = g * d[m];
+    out[4 * n_bf + bf] = s2;
   } else {
     // d_m h: grad_n = delta_mn h - 2a d_m d_n h, lap = d_m (4a^2 r^2 - 10 a) h
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-    for (int q = 0; q < np; ++q) {
-      const double al = __ldg(S.exps + off + q);
-      const double h = __ldg(S.coefs + off + q) * exp_tab(-al * r2, T);
-      s0 += h;
-      s1 += -2.0 * al * h;
-      s2 += (4.0 * al * al * r2 - 10.0 * al) * h;
-    }
     for (int m = 0; m < 3; ++m) {
       out[bf + m] = d[m] * s0;
       for (int n = 0; n < 3; ++n) out[(1 + n) * n_bf + bf + m] = (m == n ? s0 : 0.0) + d[m] * d[n] * s1;
@@ -766,10 +756,11 @@ __device__ EvalOut eval_incr(const DevSys& S, const Layout& L, const double* __r
   det_derivs(L, gblk, sm, b0, b1, lane);
   __threadfence_block();
   __syncwarp();
-  // (D) basis values at m's six hops, one (hop, shell) per lane, and m's
-  // Jastrow pair / one-body terms, one (hop, partner) per lane
+  // (D) basis values at m's six hops, one (shell, hop) per lane with the
+  // shells in kind order (a warp pass mostly meets one kind), and m's Jastrow
+  // pair / one-body terms, one (hop, partner) per lane
   for (int o = lane; o < 6 * S.n_shell; o += WARP) {
-    const int d = o / S.n_shell, sh = o - d * S.n_shell, ax = d >> 1;
+    const int k = o / 6, d = o - 6 * k, sh = __ldg(S.sh_ord + k), ax = d >> 1;
     const double sa = (d & 1) ? -a : a;
     const int I = __ldg(S.sh_atom + sh);
     const double* gg = geo + (m * nn + I) * 4;
