@@ -68,6 +68,7 @@ struct DevSys {
   const float* coefsf;
   const float* Cf;
   double j2_anti, j2_par, j2_b;
+  float j2_antif, j2_parf, j2_bf;   // FP32 copies (mixed kernels)
   double v_ii;           // nucleus-nucleus repulsion
 };
 

@@ -893,6 +893,9 @@ lrdmc_status lrdmc_create(const lrdmc_system* sys, const lrdmc_trial_wf* wf, con
   S.j2_anti = wf->j2_anti;
   S.j2_par = wf->j2_par;
   S.j2_b = wf->j2_b;
+  S.j2_antif = (float)S.j2_anti;
+  S.j2_parf = (float)S.j2_par;
+  S.j2_bf = (float)S.j2_b;
   double vii = 0.0;
   for (int I = 0; I < P.n_nuc; ++I)
     for (int J = I + 1; J < P.n_nuc; ++J) {
@@ -1450,6 +1453,9 @@ lrdmc_status lrdmc_set_params(lrdmc_handle h, const double* theta) {
   h->S.j2_anti = theta[3 * nn];
   h->S.j2_par = theta[3 * nn + 1];
   h->S.j2_b = theta[3 * nn + 2];
+  h->S.j2_antif = (float)h->S.j2_anti;
+  h->S.j2_parf = (float)h->S.j2_par;
+  h->S.j2_bf = (float)h->S.j2_b;
   h->hA.assign(theta + 3 * nn + 3, theta + 4 * nn + 3);
   h->hB.assign(theta + 4 * nn + 3, theta + 5 * nn + 3);
   std::vector<float> fR(3 * nn), fA(nn), fB(nn);

@@ -408,7 +408,8 @@ __device__ __forceinline__ double pair_c(const DevSys& S, const Layout& L, int i
 // the pair combines the node test and the ratio sum, and both evaluate the
 // electron's potential terms (one adds them).  For the per-configuration node
 // rule both the capped and the plain sums are kept and chosen at the end.
-__device__ EvalOut assemble(const DevSys& S, const Layout& L, const double* sm, double a, int node_rule, int lane) {
+__device__ EvalOut assemble(const DevSys& S, const Layout& L, const double* sm, double ia2, int node_rule,
+                            int lane) {
   const int ne = L.n_e;
   const double* rat = sm + L.s_rat;
   const double* ej = sm + L.s_ej;
@@ -418,7 +419,6 @@ __device__ EvalOut assemble(const DevSys& S, const Layout& L, const double* sm, 
   double kept = 0.0, negs = 0.0, nuopt = 0.0, nuplain = 0.0, vee = 0.0;
   int nnode = 0;
   bool any_node = false;
-  const double ia2 = 1.0 / (a * a);
   for (int base = 0; base < ne; base += per_pass) {
     const int i = base + lane / G;
     const bool valid = i < ne;
@@ -637,7 +637,7 @@ __device__ EvalOut eval_full(const DevSys& S, const Layout& L, const double* __r
   }
   __threadfence_block();
   __syncwarp();
-  return assemble(S, L, sm, a, node_rule, lane);
+  return assemble(S, L, sm, 1.0 / (a * a), node_rule, lane);
 }
 
 // Incremental evaluation after electron m hopped from xo (kept at s_xo) to its
@@ -853,7 +853,7 @@ __device__ EvalOut eval_incr(const DevSys& S, const Layout& L, const double* __r
   for (int p = lane; p < P; p += WARP) rat[p] = hD[p] * exp_tab(hJ1[p] + hJ2[p] - ej[6 * (p / 6)], T);
   __threadfence_block();
   __syncwarp();
-  return assemble(S, L, sm, a, node_rule, lane);
+  return assemble(S, L, sm, ia * ia, node_rule, lane);
 }
 
 // Build the orbital cache and potentials at every electron, invert both
@@ -972,7 +972,7 @@ __device__ void apply_hop(const DevSys& S, const Layout& L, double* __restrict__
   for (int mu = lane; mu < L.n_bf; mu += WARP) grow[mu] = g[i * L.n_bf + mu];
   __threadfence_block();
   __syncwarp();
-  const double invR = 1.0 / f[sr.ii];
+  const double invR = rcp_nr(f[sr.ii]);   // u_ii > 0: the chosen hop is a kept one
   __syncwarp();
   // A' = A + e_i (phi' - phi)^T  =>  B' = B - B e_i (u - e_i)^T / u_i
   for (int j = lane; j < n; j += WARP) f[j] = (f[j] - (j == sr.ii ? 1.0 : 0.0)) * invR;

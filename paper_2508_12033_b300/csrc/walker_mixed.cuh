@@ -246,6 +246,22 @@ __device__ __forceinline__ void shell_derivs_f(const DevSys& S, int s, const flo
   }
 }
 
+// FP32 Jastrow pair constant for electrons i, j.
+__device__ __forceinline__ float pair_cf(const DevSys& S, const Layout& L, int i, int j) {
+  return ((i < L.n_up) == (j < L.n_up)) ? S.j2_parf : S.j2_antif;
+}
+
+// float -> double on the integer pipe (a hardware conversion occupies the FP64
+// pipe on this part): exact for normal floats, zeros, infinities and NaNs;
+// denormal floats (below 1.2e-38) become zero.
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned long long de = e == 0u ? 0ull : (e == 0xffu ? 0x7ffull : (unsigned long long)(e + 896u));
+  const unsigned long long mant = e == 0u ? 0ull : (unsigned long long)(u & 0x7fffffu) << 29;
+  return __longlong_as_double((long long)(((unsigned long long)(u & 0x80000000u) << 32) | (de << 52) | mant));
+}
+
 // FP64 values of the functions of shell s (for the rows of A).
 __device__ __forceinline__ void shell_values_d(const DevSys& S, int s, const double d[3], double r2,
                                                double* __restrict__ out, const double* T) {
@@ -423,7 +439,7 @@ __device__ __forceinline__ float pade_delta(float r, float t, float del, float c
 }
 
 // Assembly (FP64) from the r - 1 values, Jastrow and determinant derivatives.
-__device__ EvalOut assemble_m(const DevSys& S, const Layout& L, const LayoutM& M, const float* sm, double a,
+__device__ EvalOut assemble_m(const DevSys& S, const Layout& L, const LayoutM& M, const float* sm, double ia2,
                               int node_rule, int lane) {
   const int ne = L.n_e;
   const float* dl = sm + M.dl;
@@ -438,7 +454,6 @@ __device__ EvalOut assemble_m(const DevSys& S, const Layout& L, const LayoutM& M
   // part of W (sum of nu_opt and the e-e terms)
   double kept = 0.0, negs = 0.0, pot = 0.0;
   int nnode = 0, nkept = 0;
-  const double ia2 = 1.0 / (a * a);
   for (int i = lane; i < ne; i += WARP) {
     float sd = 0.f, skd = 0.f, sneg = 0.f;
     int nk = 0;
@@ -450,28 +465,32 @@ __device__ EvalOut assemble_m(const DevSys& S, const Layout& L, const LayoutM& M
       if (x1 < -1.f) { sneg -= 1.f + x1; node = true; }
     }
     nkept += nk;
-    kept += (double)skd;
-    negs += (double)sneg;
+    kept += f2d(skd);
+    negs += f2d(sneg);
     const float* q = ej + 5 * i;
     const double* dv = dd + 4 * i;
     // Jastrow part of the Laplacian in FP32, determinant parts in FP64
     const float jl = fmaf(q[0], q[0], fmaf(q[1], q[1], fmaf(q[2], q[2], q[3])));
-    const double cross = dv[0] * (double)q[0] + dv[1] * (double)q[1] + dv[2] * (double)q[2];
-    const double lap = dv[3] + 2.0 * cross + (double)jl;
-    const double nu_zv = (double)ep[2 * i] + 0.5 * ((double)sd * ia2 - lap);
+    const double cross = dv[0] * f2d(q[0]) + dv[1] * f2d(q[1]) + dv[2] * f2d(q[2]);
+    const double lap = dv[3] + 2.0 * cross + f2d(jl);
+    const double nu_zv = f2d(ep[2 * i]) + 0.5 * (f2d(sd) * ia2 - lap);
     bool apply;
     if (node_rule == 0) apply = node;
     else if (node_rule == 1) apply = any_node;
     else if (node_rule == 2) apply = true;
     else apply = false;
-    pot += (apply ? fmax(nu_zv, (double)ep[2 * i + 1]) : nu_zv) + (double)q[4];
+    pot += (apply ? fmax(nu_zv, f2d(ep[2 * i + 1])) : nu_zv) + f2d(q[4]);
     nnode += node ? 1 : 0;
+  }
+  {
+    const double v[4] = {kept, negs, pot, 0.0};
+    const double t = warp_sum4(v, lane);
+    kept = __shfl_sync(FULL, t, 0);
+    negs = __shfl_sync(FULL, t, 8);
+    pot = __shfl_sync(FULL, t, 16);
   }
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
-    kept += __shfl_xor_sync(FULL, kept, o);
-    negs += __shfl_xor_sync(FULL, negs, o);
-    pot += __shfl_xor_sync(FULL, pot, o);
     nnode += __shfl_xor_sync(FULL, nnode, o);
     nkept += __shfl_xor_sync(FULL, nkept, o);
   }
@@ -513,14 +532,14 @@ __device__ __forceinline__ void partner_terms(const DevSys& S, const Layout& L, 
                                               float& LJ, float& vee) {
   const int ne = L.n_e;
   const float* xf = sm + M.xf;
-  const float bj = (float)S.j2_b;
+  const float bj = S.j2_bf;
   const float xe = xf[3 * e], ye = xf[3 * e + 1], ze = xf[3 * e + 2];
   if (t < ne - 1) {
     const int j = t < e ? t : t + 1;
     const float dx = xe - xf[3 * j], dy = ye - xf[3 * j + 1], dz = ze - xf[3 * j + 2];
     const float s = sqdistf(dx, dy, dz);
     const float ir = rsqrtf(s), r = s * ir;
-    const float c = (float)pair_c(S, L, e, j);
+    const float c = pair_cf(S, L, e, j);
     const float tt = __fdividef(1.f, fmaf(bj, r, 1.f));
     float* pp = AR.pair + e * M.pair_st + 2 * j;
     pp[0] = r; pp[1] = tt;
@@ -577,7 +596,7 @@ __device__ EvalOut eval_full_m(const DevSys& S, const Layout& L, const LayoutM& 
   float* hdm = sm + M.hdm;
   float* hj1 = sm + M.hj1;
   float* hj2 = sm + M.hj2;
-  const float bj = (float)S.j2_b;
+  const float bj = S.j2_bf;
   // (1) current configuration, G lanes per electron
   {
     int npad = 1;
@@ -645,7 +664,7 @@ __device__ EvalOut eval_full_m(const DevSys& S, const Layout& L, const LayoutM& 
     for (int j = 0; j < ne; ++j) {
       if (j == i) continue;
       const float del = fmaf(s2a, xia - xf[3 * j + ax], a2f);
-      const float v = pade_delta(pr[2 * j], pr[2 * j + 1], del, (float)pair_c(S, L, i, j), bj);
+      const float v = pade_delta(pr[2 * j], pr[2 * j + 1], del, pair_cf(S, L, i, j), bj);
       J2 += v;
       if (scr.u2) scr.u2[(size_t)j * P + p] = v;
     }
@@ -663,7 +682,7 @@ __device__ EvalOut eval_full_m(const DevSys& S, const Layout& L, const LayoutM& 
     dl[p] = fmaf(D, J, D + J);
   }
   __syncwarp();
-  return assemble_m(S, L, M, sm, a, node_rule, lane);
+  return assemble_m(S, L, M, sm, 1.0 / (a * a), node_rule, lane);
 }
 
 // Incremental evaluation after electron m hopped (old position at xo/xfo),
@@ -672,7 +691,8 @@ __device__ EvalOut eval_full_m(const DevSys& S, const Layout& L, const LayoutM& 
 // the derivative sums, scr.u2 for the hop differences; the new difference of
 // hop d of electron i with m is m's opposite hop d ^ 1 with i).
 __device__ EvalOut eval_incr_m(const DevSys& S, const Layout& L, const LayoutM& M, double* gblk, float* sm,
-                               const ScrM& scr, int m, bool all_blocks, double a, int node_rule, int lane) {
+                               const ScrM& scr, int m, bool all_blocks, double a, double ia2, int node_rule,
+                               int lane) {
   const int ne = L.n_e, nn = S.n_nuc, P = L.n_hop;
   const int per = ne - 1 + nn;
   const float af = (float)a, a2f = af * af;
@@ -689,7 +709,7 @@ __device__ EvalOut eval_incr_m(const DevSys& S, const Layout& L, const LayoutM& 
   float* hj1 = sm + M.hj1;
   float* hj2 = sm + M.hj2;
   float* tmp = sm + M.tmp;
-  const float bj = (float)S.j2_b;
+  const float bj = S.j2_bf;
   // (A) electron m from scratch (geometry, pair data both ways, primitives,
   // Jastrow sums); (B) the partner electron's sums swap their term with m
   {
@@ -703,7 +723,7 @@ __device__ EvalOut eval_incr_m(const DevSys& S, const Layout& L, const LayoutM& 
         const float dx = xm - pxj, dy = ym - pyj, dz = zm - pzj;
         const float s = sqdistf(dx, dy, dz);
         const float ir = rsqrtf(s), r = s * ir;
-        const float c = (float)pair_c(S, L, m, j);
+        const float c = pair_cf(S, L, m, j);
         const float tt = __fdividef(1.f, fmaf(bj, r, 1.f));
         float* pp = pair + m * M.pair_st + 2 * j;
         float* pq = pair + j * M.pair_st + 2 * m;
@@ -785,7 +805,7 @@ __device__ EvalOut eval_incr_m(const DevSys& S, const Layout& L, const LayoutM& 
       const int j = t < m ? t : t + 1;
       const float* pp = pair + m * M.pair_st + 2 * j;
       const float del = fmaf(sa + sa, xf[3 * m + ax] - xf[3 * j + ax], a2f);
-      v = pade_delta(pp[0], pp[1], del, (float)pair_c(S, L, m, j), bj);
+      v = pade_delta(pp[0], pp[1], del, pair_cf(S, L, m, j), bj);
       scr.u2[(size_t)j * P + 6 * m + d] = v;
     } else {
       const int I = t - (ne - 1);
@@ -841,7 +861,7 @@ __device__ EvalOut eval_incr_m(const DevSys& S, const Layout& L, const LayoutM& 
   }
   __threadfence_block();
   __syncwarp();
-  return assemble_m(S, L, M, sm, a, node_rule, lane);
+  return assemble_m(S, L, M, sm, ia2, node_rule, lane);
 }
 
 __device__ EvalOut init_walker_m(const DevSys& S, const Layout& L, const LayoutM& M, double* gblk, float* sm,
@@ -940,7 +960,7 @@ __device__ void apply_hop_m(const DevSys& S, const Layout& L, const LayoutM& M, 
   }
   for (int k = lane; k < n; k += WARP) row[k] = B[sr.ii * n + k];
   __syncwarp();
-  const double invR = 1.0 / f[sr.ii];
+  const double invR = rcp_nr(f[sr.ii]);   // u_ii > 0: the chosen hop is a kept one
   __syncwarp();
   for (int j = lane; j < n; j += WARP) f[j] = (f[j] - (j == sr.ii ? 1.0 : 0.0)) * invR;
   __syncwarp();
@@ -1087,6 +1107,7 @@ __device__ void propagate_walker_m(const DevSys& S, const Layout& L, const Layou
                                    double* __restrict__ cache, int w, const StepParams& P, const double* T, float* sm,
                                    const ScrM& wscr, int lane) {
   double* sc = (double*)(sm + M.sc);
+  const double ia2 = 1.0 / (P.a * P.a);
   {
     const unsigned long long t_start = global_ns();
     double* gblk = state + (size_t)w * L.g_stride;
@@ -1138,7 +1159,7 @@ __device__ void propagate_walker_m(const DevSys& S, const Layout& L, const Layou
           e = eval_full_m(S, L, M, gblk, sm, scr, P.a, P.node_rule, lane);
           cached = true;
         } else {
-          e = eval_incr_m(S, L, M, gblk, sm, scr, p / 6, reinv, P.a, P.node_rule, lane);
+          e = eval_incr_m(S, L, M, gblk, sm, scr, p / 6, reinv, P.a, ia2, P.node_rule, lane);
         }
         bbar = e.bbar;
         Wd = e.W;
