@@ -65,6 +65,31 @@ def test_mixed_interval_tracks_fp64_path(sysf):
     assert np.median(rel) < 1e-5
 
 
+def test_mixed_tracks_fp64_at_the_largest_size():
+    """51,200 water-methane walkers, the launch configuration of the speed-up
+    measurement (mixed re-inverting every 50 hops, FP64 every 100): after one
+    20-hop interval almost every walker made the same hops in both precisions,
+    with weights equal to FP32 accuracy, and local energies within the
+    per-configuration bound above."""
+    from gpu_helpers import lib_or_skip
+    P = lib_or_skip()
+    s = W.water_methane()
+    x0 = W.initial_walkers(s, 51200, seed=21)
+    g = {}
+    for prec, k in ((0, 100), (1, 50)):
+        lr = P.Lrdmc(s, x0, 0.2, seed=4, precision=prec, reinv_period=k)
+        lr.e0 = -20.0
+        lr.propagate(P.LOAD_BALANCED, n_proj=20)
+        g[prec] = lr.get_walkers()
+        lr.close()
+    same = np.all(g[0]["x"] == g[1]["x"], axis=(1, 2))
+    assert same.mean() >= 0.95
+    rel = np.abs(g[1]["w"][same] - g[0]["w"][same]) / np.abs(g[0]["w"][same])
+    assert np.median(rel) < 1e-5
+    de = np.abs(g[1]["ev"][same, 3] - g[0]["ev"][same, 3])
+    assert np.median(de) < 1e-3 and np.max(de) < 5e-2
+
+
 def test_mixed_run_reaches_exact_hydrogen_energy():
     from gpu_helpers import lib_or_skip
     P = lib_or_skip()

@@ -264,6 +264,32 @@ def test_full_size_sampled_walkers():
     assert np.all(np.abs(hop - np.round(hop)) < 1e-9)       # walkers stay on their lattices
 
 
+def test_largest_size_sampled_walkers():
+    """At the largest benchmarked size (water-methane, 51,200 walkers: more than
+    twelve waves of resident warps, walkers handed out by the work counter,
+    re-inversion every 100 hops as bench.py runs it) sampled walkers of a
+    second interval, after a branching, replayed by the oracle from the GPU's
+    own post-branching positions reproduce positions, weights and energies."""
+    P = lib_or_skip()
+    s = W.water_methane()
+    n_w = 51200
+    lr, x0 = _mk(P, s, n_w, reinv_period=100)
+    lr.propagate(P.LOAD_BALANCED, n_proj=20)
+    lr.branch()
+    g0 = lr.get_walkers()
+    E0 = lr.e0
+    lr.propagate(P.LOAD_BALANCED, n_proj=20)
+    g = lr.get_walkers()
+    ids = np.array([0, 4143, 4144, 20000, 25600, 40961, 51198, 51199])
+    Wk = OL.init_walkers(s, g0["x"][ids], 0.2)
+    OL.propagate_lb(s, Wk, 0.2, E0, 20, seed=1, interval=1, walker_ids=ids)
+    np.testing.assert_array_equal(g["x"][ids], Wk.x)
+    assert_close(g["w"][ids], Wk.w, what="w")
+    assert_close(g["ev"][ids, 3], Wk.ev["eL"], what="eL")
+    assert np.all(g["moves"] == 20)
+    lr.close()
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_checkpoint_resume_is_bit_identical(tmp_path, precision):
     P = lib_or_skip()
