@@ -42,7 +42,10 @@ def test_mixed_eval_against_oracle(name, sysf, n, rat_tol, el_tol):
         assert np.mean(nn.cpu().numpy() != ref["n_node"]) <= 0.01
 
 
-@pytest.mark.parametrize("sysf", [W.water_methane, lambda: W.hydrogen_cluster(24, seed=5)])
+# h64: both precisions keep their working sets in global memory (fewer than
+# 8 shared-memory working sets would fit per SM)
+@pytest.mark.parametrize("sysf", [W.water_methane, lambda: W.hydrogen_cluster(24, seed=5),
+                                  lambda: W.hydrogen_cluster(64, seed=6)])
 def test_mixed_interval_tracks_fp64_path(sysf):
     """Same start, same random streams: after a 20-hop load-balanced interval
     almost every walker made the same hops as in FP64 (a hop choice can flip
