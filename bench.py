@@ -38,6 +38,9 @@ FP64_PEAK_GFLOPS = 1250.0      # nominal B300 FP64 rate (profiling recipe table)
 # ncu capture summarised in profiles/k_propagate_wm4096_full.md (to be re-taken
 # whenever the kernel changes)
 PROPAGATE_TRAFFIC_BYTES = 1.179323e9 + 0.653197e9
+# FP64 pipe busy fraction of the same capture (sm__inst_executed_pipe_fp64,
+# % of peak sustained active); re-taken with the traffic
+PROPAGATE_FP64_PIPE_BUSY = 0.818
 # FP64 pipe instructions of the functions as the propagate kernel implements
 # them: table-driven exp (10), approximate reciprocal / rsqrt plus one
 # third-order refinement (4 / 6), tabulated erf(r/r_c)/r (index 3, Horner 10,
@@ -583,7 +586,11 @@ def main():
                          "frac": res["achieved"] / peak, "traffic": PROPAGATE_TRAFFIC_BYTES,
                          "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                          "peak_source": "nominal FP64 rate of the recipe table (no FP64 entry measured)",
-                         "kernel_ms": res["prop_ms"], "fp64_ops_per_walker_step": res["slots"]},
+                         "kernel_ms": res["prop_ms"], "fp64_ops_per_walker_step": res["slots"],
+                         "fp64_pipe_busy_ncu": PROPAGATE_FP64_PIPE_BUSY,
+                         "peak_from_unit_counts": 148 * 2 * 2 * 2.032,
+                         "peak_from_unit_counts_note": "GFLOP/s: 148 SMs x 2 FP64 FMA per clock (ncu peak "
+                                                       "sustained) x 2 FLOP x 2.032 GHz"},
             "conventional": {"value": res["conv_rate"], "unit": "walker-steps/s", "tau": res["tau"],
                              "moves_mean_max": res["conv_moves"],
                              "lb_speedup": res["value"] / res["conv_rate"]},
