@@ -264,13 +264,37 @@ def branch_stats(W: Walkers, E0, schedule):
     return wbar, ebar
 
 
+def slot_assignment(src):
+    """Slot of every copy of the reconfigured population.  The comb of
+    Sec. II.A fixes how many copies each walker gets, not where they are
+    stored; here each selected walker keeps its own slot for its first copy,
+    and its further copies, taken in the comb's order alpha, fill the slots of
+    the walkers that were not selected, in increasing slot order.  Returns
+    slot -> source walker."""
+    src = np.asarray(src, dtype=np.int64)
+    n = len(src)
+    out = np.arange(n, dtype=np.int64)
+    if n == 0:
+        return out
+    selected = np.zeros(n, bool)
+    selected[src] = True
+    free = np.flatnonzero(~selected)
+    extra = src[1:][src[1:] == src[:-1]]
+    assert len(extra) == len(free)
+    out[free] = extra
+    return out
+
+
 def reconfigure(W: Walkers, seed, interval):
+    """Integer comb, then the copies stored by ``slot_assignment``; returns the
+    comb's source indices."""
     xi32 = philox.branch_offset32(seed, interval)
     src = reconfigure_indices(W.w, xi32)
-    W.x = W.x[src].copy()
-    W.ev = {k: v[src].copy() for k, v in W.ev.items()}
-    W.status = W.status[src].copy()
-    W.moves = W.moves[src].copy()
+    slot = slot_assignment(src)
+    W.x = W.x[slot].copy()
+    W.ev = {k: v[slot].copy() for k, v in W.ev.items()}
+    W.status = W.status[slot].copy()
+    W.moves = W.moves[slot].copy()
     W.w = np.ones(len(src))
     return src
 

@@ -165,23 +165,89 @@ __device__ void reconfigure_body(const double* __restrict__ w, int w_stride, int
   }
 }
 
+// Exclusive prefix count over the block of the flags f(i), i in [0, n), in
+// contiguous per-thread chunks: returns this thread's chunk [lo, hi) and the
+// number of flagged items before lo; s_cnt is BR_THREADS ints of scratch.
+template <typename F>
+__device__ __forceinline__ int chunk_offset(int n, F f, int* s_cnt, int& lo, int& hi) {
+  const int t = threadIdx.x, chunk = (n + BR_THREADS - 1) / BR_THREADS;
+  lo = min(n, t * chunk);
+  hi = min(n, lo + chunk);
+  int c = 0;
+  for (int i = lo; i < hi; ++i) c += f(i) ? 1 : 0;
+  s_cnt[t] = c;
+  __syncthreads();
+  for (int off = 1; off < BR_THREADS; off <<= 1) {
+    const int v = t >= off ? s_cnt[t - off] : 0;
+    __syncthreads();
+    s_cnt[t] += v;
+    __syncthreads();
+  }
+  const int before = s_cnt[t] - c;
+  __syncthreads();
+  return before;
+}
+
+// Where the copies of the comb are stored: src (comb order, non-decreasing)
+// becomes slot -> source walker.  A selected walker keeps its own slot for its
+// first copy; its further copies, in comb order, fill the slots of the walkers
+// that were not selected, in increasing slot order.  So only those slots need
+// a copy.  scratch holds 2 n ints.  Nothing happens when status[0] != 0.
+__device__ void slot_body(int n, int32_t* __restrict__ src, int32_t* __restrict__ scratch,
+                          const int32_t* __restrict__ status) {
+  __shared__ int s_cnt[BR_THREADS];
+  if (status && status[0] != 0) return;
+  int32_t* A = scratch;        // selected flags, then slot -> source
+  int32_t* X = scratch + n;    // further copies' sources, in comb order
+  const int t = threadIdx.x;
+  for (int k = t; k < n; k += BR_THREADS) A[k] = 0;
+  __syncthreads();
+  for (int al = t; al < n; al += BR_THREADS) A[src[al]] = 1;
+  __syncthreads();
+  // further copies in comb order
+  int lo, hi;
+  int r = chunk_offset(n, [&](int al) { return al > 0 && src[al] == src[al - 1]; }, s_cnt, lo, hi);
+  for (int al = lo; al < hi; ++al)
+    if (al > 0 && src[al] == src[al - 1]) X[r++] = src[al];
+  __syncthreads();
+  // unselected slots in increasing order, listed in src (no longer needed)
+  r = chunk_offset(n, [&](int k) { return A[k] == 0; }, s_cnt, lo, hi);
+  for (int k = lo; k < hi; ++k)
+    if (A[k] == 0) src[r++] = k;
+  const int n_free = s_cnt[BR_THREADS - 1];
+  __syncthreads();
+  for (int k = t; k < n; k += BR_THREADS) A[k] = A[k] ? k : -1;
+  __syncthreads();
+  for (int j = t; j < n_free; j += BR_THREADS) A[src[j]] = X[j];
+  __syncthreads();
+  for (int k = t; k < n; k += BR_THREADS) src[k] = A[k];
+}
+
+// With slots set, src leaves as slot -> source walker (slot_body), else as
+// the comb's indices.
 __global__ void __launch_bounds__(BR_THREADS) k_reconfigure(const double* __restrict__ w, int w_stride,
                                                             int n, uint32_t xi32,
                                                             unsigned long long* __restrict__ Q,
                                                             int32_t* __restrict__ src,
                                                             int32_t* __restrict__ status,
-                                                            double* __restrict__ stats_out) {
+                                                            double* __restrict__ stats_out, int slots) {
   reconfigure_body(w, w_stride, n, xi32, Q, src, status, stats_out);
+  if (!slots) return;
+  __syncthreads();
+  slot_body(n, src, reinterpret_cast<int32_t*>(Q), status);
 }
 
 // new[alpha] = old[src[alpha]], weight reset to 1; skipped when status[0] != 0.
 // The walker's cache block (when the layout has one) moves with it.  Threads
-// tid, tid + nth, ... of the launch take the copies.
-__device__ void gather_body(const Layout& L, const double* __restrict__ old_state, double* __restrict__ new_state,
-                            const double* __restrict__ old_cache, double* __restrict__ new_cache,
+// tid, tid + nth, ... of the launch take the copies.  In place (new == old,
+// src a slot assignment of slot_body) only the slots with src[alpha] != alpha
+// are written; they are never the source of a copy.
+__device__ void gather_body(const Layout& L, const double* old_state, double* new_state,
+                            const double* old_cache, double* new_cache,
                             const int32_t* __restrict__ src, int n_w, const int32_t* __restrict__ status,
                             size_t tid, size_t nth) {
   if (status[0] != 0) return;
+  const bool inplace = new_state == old_state;
   const int per = L.g_stride / 2;   // double2 per walker block (stride is a multiple of 16 doubles)
   const double2* o2 = reinterpret_cast<const double2*>(old_state);
   double2* n2 = reinterpret_cast<double2*>(new_state);
@@ -189,10 +255,15 @@ __device__ void gather_body(const Layout& L, const double* __restrict__ old_stat
   for (size_t idx = tid; idx < total; idx += nth) {
     const int a = (int)(idx / per);
     const int o = (int)(idx - (size_t)a * per);
-    double2 v = o2[(size_t)src[a] * per + o];
+    const int sa = src[a];
+    if (inplace && sa == a) continue;
+    double2 v = o2[(size_t)sa * per + o];
     if (2 * o == L.g_sc + SC_W) v.x = 1.0;
     n2[idx] = v;
   }
+  if (inplace)
+    for (size_t a = tid; a < (size_t)n_w; a += nth)
+      if (src[a] == (int)a) new_state[a * L.g_stride + L.g_sc + SC_W] = 1.0;
   if (!old_cache || L.c_stride == 0) return;
   const int cper = L.c_stride / 2;
   const double2* oc = reinterpret_cast<const double2*>(old_cache);
@@ -200,13 +271,15 @@ __device__ void gather_body(const Layout& L, const double* __restrict__ old_stat
   const size_t ctotal = (size_t)n_w * cper;
   for (size_t idx = tid; idx < ctotal; idx += nth) {
     const int a = (int)(idx / cper);
-    nc[idx] = oc[(size_t)src[a] * cper + (idx - (size_t)a * cper)];
+    const int sa = src[a];
+    if (inplace && sa == a) continue;
+    nc[idx] = oc[(size_t)sa * cper + (idx - (size_t)a * cper)];
   }
 }
 
-__global__ void k_gather(Layout L, const double* __restrict__ old_state, double* __restrict__ new_state,
-                         const double* __restrict__ old_cache, double* __restrict__ new_cache,
-                         const int32_t* __restrict__ src, int n_w, const int32_t* __restrict__ status) {
+__global__ void k_gather(Layout L, const double* old_state, double* new_state, const double* old_cache,
+                         double* new_cache, const int32_t* __restrict__ src, int n_w,
+                         const int32_t* __restrict__ status) {
   gather_body(L, old_state, new_state, old_cache, new_cache, src, n_w, status,
               blockIdx.x * (size_t)blockDim.x + threadIdx.x, (size_t)gridDim.x * blockDim.x);
 }
@@ -238,6 +311,8 @@ __global__ void __launch_bounds__(BR_THREADS) k_branch_reduce_batch(const Branch
 __global__ void __launch_bounds__(BR_THREADS) k_reconfigure_batch(const BranchJob* __restrict__ jobs) {
   const BranchJob& J = jobs[blockIdx.x];
   reconfigure_body(J.state + J.L.g_sc + SC_W, J.L.g_stride, J.n_w, J.xi32, J.Q, J.src, J.status, J.stats);
+  __syncthreads();
+  slot_body(J.n_w, J.src, reinterpret_cast<int32_t*>(J.Q), J.status);
 }
 
 __global__ void k_gather_batch(const BranchJob* __restrict__ jobs) {

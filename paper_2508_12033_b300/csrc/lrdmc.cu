@@ -472,15 +472,18 @@ static lrdmc_status fetch(lrdmc_handle h, double* x, double* w, double* ev, doub
 }
 
 // Host side of a branching after the statistics hs of the handle's population
-// are read back: swap in the gathered population, extend the history, advance
-// the interval and (load-balanced) update E_0.
-static lrdmc_status finish_branch(lrdmc_handle h, const double* hs) {
+// are read back: swap in the gathered population (swap: gathered into the
+// alternate buffers; else in place), extend the history, advance the interval
+// and (load-balanced) update E_0.
+static lrdmc_status finish_branch(lrdmc_handle h, const double* hs, bool swap) {
   const Plan& P = h->P;
   if (hs[BS_BAD] != 0.0)
     return fail(h, LRDMC_ERR_NONFINITE, "weights negative, non-finite or all zero: population unchanged");
   const int lb = h->last_kind == LRDMC_LOAD_BALANCED;
-  std::swap(h->state, h->alt);
-  std::swap(h->cache, h->cache_alt);
+  if (swap) {
+    std::swap(h->state, h->alt);
+    std::swap(h->cache, h->cache_alt);
+  }
   h->wbar.push_back(hs[BS_SUMW] / (double)P.n_w);
   h->ebar.push_back(hs[BS_SUMFE] / hs[BS_SUMF]);
   h->e0h.push_back(h->E0);
@@ -1048,17 +1051,18 @@ lrdmc_status lrdmc_branch(lrdmc_handle h) {
   LAUNCHED(h);
   const uint32_t xi = branch_offset32(h->prm.seed, h->interval);
   k_reconfigure<<<1, BR_THREADS, 0, h->stream>>>(h->state + P.L.g_sc + SC_W, P.L.g_stride, P.n_w, xi, h->Q,
-                                                 h->src, h->dstat, h->stats);
+                                                 h->src, h->dstat, h->stats, 1);
   LAUNCHED(h);
+  // in place: only the slots of walkers the comb did not select receive a copy
   const size_t per = (size_t)P.n_w * std::max(P.L.g_stride, P.L.c_stride) / 2;
   const int gb = (int)std::min<size_t>((per + 255) / 256, (size_t)h->num_sms * 8);
-  k_gather<<<std::max(1, gb), 256, 0, h->stream>>>(P.L, h->state, h->alt, h->cache, h->cache_alt, h->src, P.n_w,
+  k_gather<<<std::max(1, gb), 256, 0, h->stream>>>(P.L, h->state, h->state, h->cache, h->cache, h->src, P.n_w,
                                                    h->dstat);
   LAUNCHED(h);
   double hs[BS_COUNT];
   CK(h, cudaMemcpyAsync(hs, h->stats, sizeof hs, cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
-  return finish_branch(h, hs);
+  return finish_branch(h, hs, false);
 }
 
 lrdmc_status lrdmc_energy(lrdmc_handle h, double* E, double* err) {
@@ -1308,7 +1312,7 @@ lrdmc_status lrdmc_reconfigure_indices(int n, const double* w, uint32_t xi32, in
   if (scratch_bytes < lrdmc_reconfigure_scratch_bytes(n) || (uintptr_t)scratch % ALIGN) return LRDMC_ERR_ARG;
   unsigned long long* Q = (unsigned long long*)scratch;
   int32_t* st = (int32_t*)((char*)scratch + align_up(sizeof(unsigned long long) * (size_t)n));
-  k_reconfigure<<<1, BR_THREADS, 0, (cudaStream_t)stream>>>(w, 1, n, xi32, Q, src, st, nullptr);
+  k_reconfigure<<<1, BR_THREADS, 0, (cudaStream_t)stream>>>(w, 1, n, xi32, Q, src, st, nullptr, 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return LRDMC_ERR_CUDA;
   if (status_out) {
@@ -1364,7 +1368,7 @@ lrdmc_status lrdmc_reconfigure_indices_noalloc(int n, const double* w, uint32_t 
   unsigned long long* q = nullptr;
   if (noalloc_scratch(&q) != cudaSuccess) return LRDMC_ERR_CUDA;
   int32_t* st = (int32_t*)(q + NOALLOC_Q_WORDS);
-  k_reconfigure<<<1, BR_THREADS, 0, (cudaStream_t)stream>>>(w, 1, n, xi32, q, src, st, nullptr);
+  k_reconfigure<<<1, BR_THREADS, 0, (cudaStream_t)stream>>>(w, 1, n, xi32, q, src, st, nullptr, 0);
   if (cudaGetLastError() != cudaSuccess) return LRDMC_ERR_CUDA;
   if (status_out &&
       cudaMemcpyAsync(status_out, st, 2 * sizeof(int32_t), cudaMemcpyDeviceToDevice, (cudaStream_t)stream) !=
@@ -1690,9 +1694,9 @@ lrdmc_status lrdmc_batch_branch(lrdmc_batch b) {
     BranchJob& J = b->bjobs[k];
     J.L = P.L;
     J.state = h->state;
-    J.alt = h->alt;
+    J.alt = h->state;           // in place: only unselected slots receive a copy
     J.cache = h->cache;
-    J.cache_alt = h->cache_alt;
+    J.cache_alt = h->cache;
     J.n_w = P.n_w;
     J.lb = h->last_kind == LRDMC_LOAD_BALANCED;
     J.E0 = h->E0;
@@ -1717,7 +1721,7 @@ lrdmc_status lrdmc_batch_branch(lrdmc_batch b) {
   lrdmc_status worst = LRDMC_OK;
   std::string msg;
   for (int k = 0; k < n; ++k) {
-    const lrdmc_status st = finish_branch(b->h[k], hs.data() + (size_t)BS_COUNT * k);
+    const lrdmc_status st = finish_branch(b->h[k], hs.data() + (size_t)BS_COUNT * k, false);
     if (st != LRDMC_OK) {
       if (worst == LRDMC_OK) worst = st;
       msg += "system " + std::to_string(k) + ": " + b->h[k]->err + "; ";

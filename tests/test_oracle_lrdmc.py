@@ -31,6 +31,27 @@ def test_reconfiguration_invariants(n):
     assert np.all(counts >= np.floor(expect - 1e-9)) and np.all(counts <= np.ceil(expect + 1e-9))
 
 
+@pytest.mark.parametrize("n", [1, 2, 7, 100, 4096])
+def test_slot_assignment_keeps_survivors_in_place(n):
+    """The stored population holds every walker as often as the comb copies it;
+    a selected walker stays in its own slot; only unselected slots change, and
+    they receive the further copies in comb order; equal weights move nothing."""
+    rng = np.random.default_rng(n + 7)
+    w = rng.lognormal(0.0, 0.7, n)
+    src = L.reconfigure_indices(w, int(rng.integers(0, 2**32)))
+    slot = L.slot_assignment(src)
+    np.testing.assert_array_equal(np.bincount(slot, minlength=n), np.bincount(src, minlength=n))
+    selected = np.bincount(src, minlength=n) > 0
+    np.testing.assert_array_equal(slot[selected], np.flatnonzero(selected))
+    free = np.flatnonzero(~selected)
+    extra = [src[a] for a in range(1, n) if src[a] == src[a - 1]]     # second, third, ... copies
+    np.testing.assert_array_equal(slot[free], extra)
+    np.testing.assert_array_equal(L.slot_assignment(np.arange(n)), np.arange(n))
+    # a hand-worked case: walker 1 copied three times, 0 and 2 not selected, 3 once
+    np.testing.assert_array_equal(L.slot_assignment(np.array([1, 1, 1, 3])), [1, 1, 1, 3])
+    np.testing.assert_array_equal(L.slot_assignment(np.array([0, 0, 2, 2, 2, 4])), [0, 0, 2, 2, 4, 2])
+
+
 def test_reconfiguration_equal_weights_is_identity():
     for n in (1, 5, 1000):
         for xi in (0, 1, 2**31, 2**32 - 1):
