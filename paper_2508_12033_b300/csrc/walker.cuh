@@ -225,8 +225,10 @@ __device__ void all_potentials(const DevSys& S, const Layout& L, const double* x
 // In-place inversion of the N x N matrix held as the left half of M = [A | I]
 // (N x 2N, row-major) with partial pivoting; afterwards the right half is
 // A^{-1}.  Returns true on a zero (or non-finite) pivot.  With logdet set,
-// adds log|det A| (the sum of log|pivot|) to it.
-__device__ bool warp_gauss_jordan(double* M, int N, int lane, double* logdet = nullptr) {
+// adds log|det A| (the sum of log|pivot|) to it.  f is scratch of N doubles:
+// the elimination factors of a column are recorded first, so that all rows are
+// then updated in one pass over (row, column) pairs.
+__device__ bool warp_gauss_jordan(double* M, int N, int lane, double* f, double* logdet = nullptr) {
   const int W2 = 2 * N;
   for (int c = 0; c < N; ++c) {
     double best = -1.0;
@@ -254,16 +256,16 @@ __device__ bool warp_gauss_jordan(double* M, int N, int lane, double* logdet = n
     const double inv = 1.0 / piv;
     if (logdet) *logdet += log(fabs(piv));
     __syncwarp();
+    // scale the pivot row; record the other rows' factors (other rows: no conflict)
     for (int j = lane; j < W2; j += WARP) M[c * W2 + j] *= inv;
+    for (int r = lane; r < N; r += WARP) f[r] = r == c ? 0.0 : M[r * W2 + c];
     __syncwarp();
-    for (int r = 0; r < N; ++r) {
-      if (r == c) continue;
-      const double f = M[r * W2 + c];
-      __syncwarp();
-      if (f != 0.0)
-        for (int j = lane; j < W2; j += WARP) M[r * W2 + j] -= f * M[c * W2 + j];
-      __syncwarp();
+    for (int t = lane; t < N * W2; t += WARP) {
+      const int r = t / W2, j = t - r * W2;
+      const double fr = f[r];
+      if (fr != 0.0) M[t] -= fr * M[c * W2 + j];
     }
+    __syncwarp();
   }
   return false;
 }
@@ -326,6 +328,9 @@ __device__ bool reinvert(const Layout& L, const double* __restrict__ gblk, doubl
   bool sing = false;
   const double* cache = gblk + L.g_cache;
   double* bt = sm + L.s_bt;
+  // the work matrix in the per-hop scratch region of the working set when it
+  // fits (free between hops), else in the global scratch
+  if (2 * L.n_max * L.n_max <= L.s_phi5 - L.s_tmp) scratch = sm + L.s_tmp;
   for (int blk = 0; blk < 2; ++blk) {
     const int n = blk ? L.n_dn : L.n_up;
     const int e0 = blk ? L.n_up : 0;
@@ -337,7 +342,7 @@ __device__ bool reinvert(const Layout& L, const double* __restrict__ gblk, doubl
     }
     __threadfence_block();
     __syncwarp();
-    sing |= warp_gauss_jordan(scratch, n, lane, logdet);
+    sing |= warp_gauss_jordan(scratch, n, lane, sm + L.s_row, logdet);
     for (int o = lane; o < n * n; o += WARP) {
       const int i = o / n, k = o - i * n;
       bt[bto + o] = scratch[k * 2 * n + n + i];

@@ -353,6 +353,9 @@ __device__ bool reinvert_m(const Layout& L, const LayoutM& M, double* gblk, floa
   bool sing = false;
   const double* val = cache_val(L, gblk);
   double* bt = (double*)(sm + M.bt);
+  // the work matrix in the move scratch region (free between hops) when it fits
+  // and is 8-byte aligned, else in the global scratch
+  if ((M.chi5 & 1) == 0 && 4 * L.n_max * L.n_max <= M.phi5 - M.chi5) scratch = (double*)(sm + M.chi5);
   for (int blk = 0; blk < 2; ++blk) {
     const int n = blk ? L.n_dn : L.n_up;
     const int e0 = blk ? L.n_up : 0;
@@ -364,7 +367,7 @@ __device__ bool reinvert_m(const Layout& L, const LayoutM& M, double* gblk, floa
     }
     __threadfence_block();
     __syncwarp();
-    sing |= warp_gauss_jordan(scratch, n, lane);
+    sing |= warp_gauss_jordan(scratch, n, lane, (double*)(sm + M.row));
     for (int o = lane; o < n * n; o += WARP) {
       const int i = o / n, k = o - i * n;
       bt[bto + o] = scratch[k * 2 * n + n + i];
