@@ -402,6 +402,17 @@ __device__ __forceinline__ double proj(const double* xi, const double* xj, const
   return fma(dz, V[3 * ax + 2], fma(dy, V[3 * ax + 1], dx * V[3 * ax]));
 }
 
+// Unordered pair q (0 <= q < n (n - 1) / 2, row-major over i < j) -> (i, j).
+__device__ __forceinline__ void pair_index(int q, int n, int& i, int& j) {
+  const float b = 2.f * n - 1.f;
+  int r = (int)((b - sqrtf(fmaxf(b * b - 8.f * q, 0.f))) * 0.5f);
+  r = max(0, min(r, n - 2));
+  while (r > 0 && r * (2 * n - r - 1) / 2 > q) --r;
+  while (r < n - 2 && (r + 1) * (2 * n - r - 2) / 2 <= q) ++r;
+  i = r;
+  j = q - r * (2 * n - r - 1) / 2 + r + 1;
+}
+
 // Jastrow pair constant for electrons i, j.
 __device__ __forceinline__ double pair_c(const DevSys& S, const Layout& L, int i, int j) {
   return ((i < L.n_up) == (j < L.n_up)) ? S.j2_par : S.j2_anti;
@@ -588,6 +599,24 @@ __device__ EvalOut eval_full(const DevSys& S, const Layout& L, const double* __r
   }
   det_derivs(L, gblk, sm, 0, ne, lane);
   __syncwarp();
+  // (3a) with hop caches: the pair Jastrow term of every hop, each unordered
+  // pair once (the term of hop (i, d) with partner j is the term of hop
+  // (j, d ^ 1) with i, bit for bit), into scr.u2
+  if (scr.u2) {
+    const int n_task = 3 * ne * (ne - 1);
+    for (int t = lane; t < n_task; t += WARP) {
+      const int q = t / 6, d = t - 6 * q, ax = d >> 1;
+      int i, j;
+      pair_index(q, ne, i, j);
+      const double sa = (d & 1) ? -a : a;
+      const double v =
+          pade_value(fma(sa + sa, proj<ROT>(x + 3 * i, x + 3 * j, V, ax), pr2[i * ne + j]), pair_c(S, L, i, j), S.j2_b);
+      scr.u2[(size_t)j * P + 6 * i + d] = v;
+      scr.u2[(size_t)i * P + 6 * j + (d ^ 1)] = v;
+    }
+    __threadfence_block();
+    __syncwarp();
+  }
   // (3) every hop: basis values (kept in scr.chi), determinant ratio
   // chi(r') . g_i, one-body and pair Jastrow sums
   for (int p = lane; p < P; p += WARP) {
@@ -630,10 +659,9 @@ __device__ EvalOut eval_full(const DevSys& S, const Layout& L, const double* __r
     }
     for (int j = 0; j < ne; ++j) {
       if (j == i) continue;
-      const double v =
-          pade_value(fma(s2a, proj<ROT>(x + 3 * i, x + 3 * j, V, ax), pr2[i * ne + j]), pair_c(S, L, i, j), S.j2_b);
-      J2 += v;
-      if (scr.u2) scr.u2[(size_t)j * P + p] = v;
+      J2 += scr.u2 ? scr.u2[(size_t)j * P + p]
+                   : pade_value(fma(s2a, proj<ROT>(x + 3 * i, x + 3 * j, V, ax), pr2[i * ne + j]), pair_c(S, L, i, j),
+                                S.j2_b);
     }
     hD[p] = det;
     hJ1[p] = J1;
