@@ -105,3 +105,39 @@ def test_large_system_and_more_configurations_than_walkers():
     assert _rel(eL.cpu().numpy(), e_ref) < 1e-10
     assert _rel(ge.cpu().numpy(), ge_ref) < 1e-8
     assert _rel(gl.cpu().numpy(), gl_ref) < 1e-10
+
+
+def test_global_working_set_path_matches_finite_differences():
+    """A 64-electron cluster: its shared-memory layout would hold fewer than 8
+    working sets per SM, so the gradient kernel keeps them in global memory.
+    Gradients against central differences (h = 1e-4, one Richardson step) of
+    the GPU's own energies, for nuclear coordinates and Jastrow parameters."""
+    import torch
+    P = lib_or_skip()
+    s = W.hydrogen_cluster(64, seed=6)
+    x = torch.tensor(W.initial_walkers(s, 3, seed=9), device="cuda")
+    lr = P.Lrdmc(s, W.initial_walkers(s, 2, seed=1), 0.2)
+    th0 = lr.params()
+    _, _, ge, gl = lr.local_energy_grad(x)
+    ge, gl = ge.cpu().numpy(), gl.cpu().numpy()
+    nn = s.n_nuc
+
+    def energies(th):
+        lr.set_params(th)
+        e, l, _, _ = lr.local_energy_grad(x)
+        torch.cuda.synchronize()
+        return e.cpu().numpy(), l.cpu().numpy()
+
+    for k in (0, 3 * nn - 2, 3 * nn, 3 * nn + 2, 3 * nn + 3 + nn // 2, 4 * nn + 3 + nn - 1):
+        fd = {}
+        for h in (1e-4, 5e-5):
+            tp, tm = th0.copy(), th0.copy()
+            tp[k] += h
+            tm[k] -= h
+            ep, lp_ = energies(tp)
+            em, lm = energies(tm)
+            fd[h] = ((ep - em) / (2 * h), (lp_ - lm) / (2 * h))
+        for q, g in ((0, ge[:, k]), (1, gl[:, k])):
+            rich = (4 * fd[5e-5][q] - fd[1e-4][q]) / 3
+            assert np.all(np.abs(rich - g) <= 1e-6 * np.maximum(1.0, np.abs(g))), (k, q, rich, g)
+    lr.set_params(th0)
