@@ -25,12 +25,14 @@ enum BranchStat : int {
 };
 
 // One CTA of BR_THREADS threads.  Each thread accumulates a strided subset in
-// index order, then the partials are combined by a fixed tree.
+// index order; the partials are combined by a fixed tree: xor-shuffles within
+// each warp, then the warps' results by the first warp.
 __device__ void branch_reduce_body(const Layout& L, const double* __restrict__ state, int n_w, double E0, int lb,
                                    double* __restrict__ out) {
-  __shared__ double s_buf[BR_THREADS];
-  __shared__ unsigned s_or[BR_THREADS];
-  const int t = threadIdx.x;
+  constexpr int NW = BR_THREADS / 32;
+  __shared__ double s_part[6][NW];
+  __shared__ unsigned s_or[NW];
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};   // w, w e, f, f e, moves, max moves
   unsigned orv = 0u;
   for (int a = t; a < n_w; a += BR_THREADS) {
@@ -45,31 +47,38 @@ __device__ void branch_reduce_body(const Layout& L, const double* __restrict__ s
     acc[5] = fmax(acc[5], sc[SC_MOVES]);
     orv |= (unsigned)sc[SC_STATUS];
   }
-  double res[6];
-  for (int k = 0; k < 6; ++k) {
-    s_buf[t] = acc[k];
-    __syncthreads();
-    for (int s = BR_THREADS / 2; s > 0; s >>= 1) {
-      if (t < s) s_buf[t] = (k == 5) ? fmax(s_buf[t], s_buf[t + s]) : s_buf[t] + s_buf[t + s];
-      __syncthreads();
-    }
-    res[k] = s_buf[0];
-    __syncthreads();
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) acc[k] += __shfl_xor_sync(FULL, acc[k], o);
+    acc[5] = fmax(acc[5], __shfl_xor_sync(FULL, acc[5], o));
+    orv |= __shfl_xor_sync(FULL, orv, o);
   }
-  s_or[t] = orv;
+  if (lane == 0) {
+    for (int k = 0; k < 6; ++k) s_part[k][wid] = acc[k];
+    s_or[wid] = orv;
+  }
   __syncthreads();
-  for (int s = BR_THREADS / 2; s > 0; s >>= 1) {
-    if (t < s) s_or[t] |= s_or[t + s];
-    __syncthreads();
-  }
-  if (t == 0) {
-    out[BS_SUMW] = res[0];
-    out[BS_SUMWE] = res[1];
-    out[BS_SUMF] = res[2];
-    out[BS_SUMFE] = res[3];
-    out[BS_MOVES] = res[4];
-    out[BS_MOVESMAX] = res[5];
-    out[BS_STATUS] = (double)s_or[0];
+  if (wid == 0) {
+    double r[6];
+    for (int k = 0; k < 6; ++k) r[k] = lane < NW ? s_part[k][lane] : 0.0;
+    unsigned ro = lane < NW ? s_or[lane] : 0u;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+#pragma unroll
+      for (int k = 0; k < 5; ++k) r[k] += __shfl_xor_sync(FULL, r[k], o);
+      r[5] = fmax(r[5], __shfl_xor_sync(FULL, r[5], o));
+      ro |= __shfl_xor_sync(FULL, ro, o);
+    }
+    if (lane == 0) {
+      out[BS_SUMW] = r[0];
+      out[BS_SUMWE] = r[1];
+      out[BS_SUMF] = r[2];
+      out[BS_SUMFE] = r[3];
+      out[BS_MOVES] = r[4];
+      out[BS_MOVESMAX] = r[5];
+      out[BS_STATUS] = (double)ro;
+    }
   }
 }
 
@@ -137,17 +146,27 @@ __device__ void reconfigure_body(const double* __restrict__ w, int w_stride, int
   }
   __syncthreads();
   const unsigned long long tot = s_sum[BR_THREADS - 1];
-  // (3) comb: first b with (xi32 + alpha 2^32) tot < n 2^32 Q_b
+  // (3) comb: first b with (xi32 + alpha 2^32) tot < n 2^32 Q_b.  Thread t
+  // takes the contiguous slots [lo, hi): a binary search for the first, then,
+  // since the answer does not decrease with alpha, a forward walk for the rest.
   const unsigned __int128 n32 = (unsigned __int128)(unsigned)n << 32;
-  for (int al = t; al < n; al += BR_THREADS) {
-    const unsigned __int128 lhs = ((unsigned __int128)xi32 + ((unsigned __int128)(unsigned)al << 32)) *
-                                  (unsigned __int128)tot;
-    int b0 = 0, b1 = n - 1;   // condition holds at b = n - 1
-    while (b0 < b1) {
-      const int mid = (b0 + b1) >> 1;
-      if (lhs < n32 * (unsigned __int128)Q[mid]) b1 = mid; else b0 = mid + 1;
+  {
+    int b = 0;
+    for (int al = lo; al < hi; ++al) {
+      const unsigned __int128 lhs = ((unsigned __int128)xi32 + ((unsigned __int128)(unsigned)al << 32)) *
+                                    (unsigned __int128)tot;
+      if (al == lo) {
+        int b0 = 0, b1 = n - 1;   // condition holds at b = n - 1
+        while (b0 < b1) {
+          const int mid = (b0 + b1) >> 1;
+          if (lhs < n32 * (unsigned __int128)Q[mid]) b1 = mid; else b0 = mid + 1;
+        }
+        b = b0;
+      } else {
+        while (b < n - 1 && !(lhs < n32 * (unsigned __int128)Q[b])) ++b;
+      }
+      src[al] = b;
     }
-    src[al] = b0;
   }
   __syncthreads();
   // (4) distinct survivors (src is non-decreasing)
