@@ -6,7 +6,8 @@
 //  k_reconfigure     integer comb: q_b = floor(w_b / w_max 2^S), exact uint64
 //                    prefix sum, and for every slot alpha the first b with
 //                    (xi32 + alpha 2^32) Q_total < N 2^32 Q_b (128-bit test)
-//  k_gather          new walker alpha = copy of old walker s(alpha), w = 1
+//  slot_body         where each copy is stored (selected walkers keep their slots)
+//  k_gather_slots    in place: unselected slots receive a copy of their source, w = 1
 //
 // The reduction and the comb run in one CTA: N_w is at most a few 10^5 and the
 // work is O(N_w) integer/FP64 operations, far below one microsecond per 10^4
@@ -296,12 +297,33 @@ __device__ void gather_body(const Layout& L, const double* old_state, double* ne
   }
 }
 
-__global__ void k_gather(Layout L, const double* old_state, double* new_state, const double* old_cache,
-                         double* new_cache, const int32_t* __restrict__ src, int n_w,
-                         const int32_t* __restrict__ status) {
-  gather_body(L, old_state, new_state, old_cache, new_cache, src, n_w, status,
-              blockIdx.x * (size_t)blockDim.x + threadIdx.x, (size_t)gridDim.x * blockDim.x);
+// In-place gather after slot_body: one CTA per slot; the slot of a selected
+// walker only has its weight reset, the slot of an unselected one receives a
+// copy of its source's walker and cache blocks (weight 1).  Sources are always
+// selected walkers, so no source is overwritten.
+__global__ void k_gather_slots(Layout L, double* state, double* cache, const int32_t* __restrict__ src,
+                               const int32_t* __restrict__ status) {
+  if (status[0] != 0) return;
+  const int a = blockIdx.x, sa = src[a];
+  if (sa == a) {
+    if (threadIdx.x == 0) state[(size_t)a * L.g_stride + L.g_sc + SC_W] = 1.0;
+    return;
+  }
+  const int per = L.g_stride / 2;
+  const double2* o2 = reinterpret_cast<const double2*>(state + (size_t)sa * L.g_stride);
+  double2* n2 = reinterpret_cast<double2*>(state + (size_t)a * L.g_stride);
+  for (int o = threadIdx.x; o < per; o += blockDim.x) {
+    double2 v = o2[o];
+    if (2 * o == L.g_sc + SC_W) v.x = 1.0;
+    n2[o] = v;
+  }
+  if (!cache || L.c_stride == 0) return;
+  const int cper = L.c_stride / 2;
+  const double2* oc = reinterpret_cast<const double2*>(cache + (size_t)sa * L.c_stride);
+  double2* nc = reinterpret_cast<double2*>(cache + (size_t)a * L.c_stride);
+  for (int o = threadIdx.x; o < cper; o += blockDim.x) nc[o] = oc[o];
 }
+
 
 // ------------------------------------------------------------ batches
 // One system of a batch at branching time.

@@ -1054,10 +1054,7 @@ lrdmc_status lrdmc_branch(lrdmc_handle h) {
                                                  h->src, h->dstat, h->stats, 1);
   LAUNCHED(h);
   // in place: only the slots of walkers the comb did not select receive a copy
-  const size_t per = (size_t)P.n_w * std::max(P.L.g_stride, P.L.c_stride) / 2;
-  const int gb = (int)std::min<size_t>((per + 255) / 256, (size_t)h->num_sms * 8);
-  k_gather<<<std::max(1, gb), 256, 0, h->stream>>>(P.L, h->state, h->state, h->cache, h->cache, h->src, P.n_w,
-                                                   h->dstat);
+  k_gather_slots<<<P.n_w, 256, 0, h->stream>>>(P.L, h->state, h->cache, h->src, h->dstat);
   LAUNCHED(h);
   double hs[BS_COUNT];
   CK(h, cudaMemcpyAsync(hs, h->stats, sizeof hs, cudaMemcpyDeviceToHost, h->stream));
