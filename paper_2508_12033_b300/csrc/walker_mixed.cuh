@@ -251,17 +251,6 @@ __device__ __forceinline__ float pair_cf(const DevSys& S, const Layout& L, int i
   return ((i < L.n_up) == (j < L.n_up)) ? S.j2_parf : S.j2_antif;
 }
 
-// float -> double on the integer pipe (a hardware conversion occupies the FP64
-// pipe on this part): exact for normal floats, zeros, infinities and NaNs;
-// denormal floats (below 1.2e-38) become zero.
-__device__ __forceinline__ double f2d(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned e = (u >> 23) & 0xffu;
-  const unsigned long long de = e == 0u ? 0ull : (e == 0xffu ? 0x7ffull : (unsigned long long)(e + 896u));
-  const unsigned long long mant = e == 0u ? 0ull : (unsigned long long)(u & 0x7fffffu) << 29;
-  return __longlong_as_double((long long)(((unsigned long long)(u & 0x80000000u) << 32) | (de << 52) | mant));
-}
-
 // FP64 values of the functions of shell s (for the rows of A).
 __device__ __forceinline__ void shell_values_d(const DevSys& S, int s, const double d[3], double r2,
                                                double* __restrict__ out, const double* T) {
@@ -468,21 +457,21 @@ __device__ EvalOut assemble_m(const DevSys& S, const Layout& L, const LayoutM& M
       if (x1 < -1.f) { sneg -= 1.f + x1; node = true; }
     }
     nkept += nk;
-    kept += f2d(skd);
-    negs += f2d(sneg);
+    kept += (double)skd;
+    negs += (double)sneg;
     const float* q = ej + 5 * i;
     const double* dv = dd + 4 * i;
     // Jastrow part of the Laplacian in FP32, determinant parts in FP64
     const float jl = fmaf(q[0], q[0], fmaf(q[1], q[1], fmaf(q[2], q[2], q[3])));
-    const double cross = dv[0] * f2d(q[0]) + dv[1] * f2d(q[1]) + dv[2] * f2d(q[2]);
-    const double lap = dv[3] + 2.0 * cross + f2d(jl);
-    const double nu_zv = f2d(ep[2 * i]) + 0.5 * (f2d(sd) * ia2 - lap);
+    const double cross = dv[0] * (double)q[0] + dv[1] * (double)q[1] + dv[2] * (double)q[2];
+    const double lap = dv[3] + 2.0 * cross + (double)jl;
+    const double nu_zv = (double)ep[2 * i] + 0.5 * ((double)sd * ia2 - lap);
     bool apply;
     if (node_rule == 0) apply = node;
     else if (node_rule == 1) apply = any_node;
     else if (node_rule == 2) apply = true;
     else apply = false;
-    pot += (apply ? fmax(nu_zv, f2d(ep[2 * i + 1])) : nu_zv) + f2d(q[4]);
+    pot += (apply ? fmax(nu_zv, (double)ep[2 * i + 1]) : nu_zv) + (double)q[4];
     nnode += node ? 1 : 0;
   }
   {
