@@ -1,23 +1,27 @@
 // Warp-per-walker FP64 kernels of the LRDMC projection step.
 //
 // One warp owns one walker at a time.  Its working set (positions, the
-// transposed inverse Slater matrices B^T, g_i = C^T B[:, i] for every
-// electron, the 6 N_e hop ratios, per-electron Jastrow/potential terms and the
+// transposed inverse Slater matrices B^T, the 6 N_e hop ratios and their
+// determinant / Jastrow parts, per-electron Jastrow / potential terms and the
 // electron-nucleus / electron-electron geometry of the current configuration)
-// lives in shared memory for a whole branching interval.  The orbital
-// value/gradient/Laplacian cache stays in the walker's global block (L2
-// resident during the interval).  The FP64 pipe is the bound, so the
-// formulation minimises FP64 work:
+// lives in shared memory for a whole branching interval (in global memory for
+// systems too large for that).  The walker's cache block in global memory
+// keeps, across intervals, the orbital value/gradient/Laplacian rows of every
+// electron, g_i = C^T B[:, i], the basis values at every hop and the pair
+// Jastrow terms of every hop and of every pair.  The FP64 pipe is the bound,
+// so the formulation minimises FP64 work:
 //   * determinant ratio of hop (i, d) = chi(r') . g_i (one N_bf dot per hop);
 //     g is updated by the same rank-1 factors as B after each hop;
+//   * every hop re-evaluates only what depends on the moved electron; the
+//     other electrons' pair terms with it are swapped from the caches;
 //   * |r' - R|^2 = (|r - R|^2 + a^2) + 2 (+-a) (r - R)_axis: distances are
 //     formed once per (electron, nucleus) and per electron pair and shared by
 //     the 6 hops and all shells on a nucleus;
-//   * only the hopping electron's Jastrow pair terms enter its ratio;
 //   * the pseudopotential of an electron is recomputed only when it hops;
 //   * Sherman-Morrison keeps B = A^{-1} current, with a from-scratch
 //     Gauss-Jordan inversion every reinv_period hops;
-//   * exp / sqrt / reciprocal use the reduced-slot forms of fp64math.cuh.
+//   * exp / rsqrt / reciprocal / erf(r/r_c)/r use the reduced-slot forms of
+//     fp64math.cuh.
 #pragma once
 
 #include "common.cuh"

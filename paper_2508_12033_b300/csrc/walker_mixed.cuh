@@ -10,12 +10,14 @@
 //         is ill-conditioned and an FP32 A or B would carry cond(A) * 1e-7
 //         relative errors into every ratio; in FP64 they stay negligible.
 //   FP32  every hop ratio (6 N_e per step, the bulk of the work): basis and
-//         Jastrow values, g_i = C^T B[:, i] (from B rounded to FP32), the
-//         orbital gradient/Laplacian cache, potentials, heat-bath sums.
+//         Jastrow differences, the orbital differences of every hop, an FP32
+//         copy of B for the hop determinants, the orbital gradient/Laplacian
+//         rows, potentials, heat-bath sums.
 // Each hop ratio is produced directly as r - 1 ("delta form") so that the
 // kinetic sums of Appendix D never subtract two O(3 N_e / a^2) numbers in FP32:
-//   * determinant: chi(r_i) . g_i = 1 exactly, so det - 1 = sum_mu
-//     [chi_mu(r') - chi_mu(r_i)] g_mu, every Gaussian difference formed as
+//   * determinant: phi(r_i) . B[:, i] = 1 exactly, so det - 1 = sum_k
+//     [phi_k(r') - phi_k(r_i)] B_ki, the orbital differences contracted from
+//     basis differences, every Gaussian difference formed as
 //     h (exp(-alpha delta) - 1), delta = |r'-R|^2 - |r_i-R|^2 = 2 (+-a) d_axis + a^2;
 //   * Jastrow: u(r') - u(r) = c delta t t' / (r' + r), t = 1/(1 + b r),
 //     delta = 2 (+-a) (r_i - r_j)_axis + a^2;
@@ -25,9 +27,10 @@
 // Walker block: B^T as doubles (as in the FP64 layout); the cache region holds
 // the FP64 orbital values [n_e][n_max] followed by the gradient/Laplacian
 // rows [n_e][4][n_max] (evaluated in FP32, stored as doubles so that the FP64
-// determinant derivatives read them without conversions).  As in the FP64 kernels, the caches of the incremental
-// evaluation persist in a per-walker cache block across branching intervals,
-// and pair terms are swapped from cached values rather than recomputed.
+// determinant derivatives read them without conversions).  As in the FP64
+// kernels, the caches of the incremental evaluation persist in a per-walker
+// cache block across branching intervals, and pair terms are swapped from
+// cached values rather than recomputed.
 #pragma once
 
 #include "common.cuh"
