@@ -402,8 +402,8 @@ static int smem_bytes(lrdmc_handle h) {
 // handle in the process, so it is raised to the device's opt-in maximum (it
 // permits, it reserves nothing); each launch still requests only its own size.
 static lrdmc_status set_kernel_smem(lrdmc_handle h, int optin) {
-  CK(h, cudaFuncSetAttribute(k_propagate<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-  CK(h, cudaFuncSetAttribute(k_propagate<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  CK(h, cudaFuncSetAttribute(k_propagate<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  CK(h, cudaFuncSetAttribute(k_propagate<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   CK(h, cudaFuncSetAttribute(k_init_walkers, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   CK(h, cudaFuncSetAttribute(k_eval_configs, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   CK(h, cudaFuncSetAttribute(k_eloc_grad<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
@@ -936,7 +936,7 @@ lrdmc_status lrdmc_create(const lrdmc_system* sys, const lrdmc_trial_wf* wf, con
     if ((size_t)smem_bytes(h) > (size_t)smem_optin) break;
     int bps = 0;
     if (P.precision == 0)
-      CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_propagate<false, false>, wpb * 32, smem_bytes(h)));
+      CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_propagate<false>, wpb * 32, smem_bytes(h)));
     else
       CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_propagate_m<false>, wpb * 32, smem_bytes(h)));
     if (bps >= 1 && bps * wpb >= best_warps) {
@@ -956,7 +956,7 @@ lrdmc_status lrdmc_create(const lrdmc_system* sys, const lrdmc_trial_wf* wf, con
     int bps = 0;
     h->prop_wpb = 4;
     if (P.precision == 0)
-      CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_propagate<false, true>, 4 * 32,
+      CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_propagate_g<false>, 4 * 32,
                                                           EXP_TAB * sizeof(double)));
     else
       CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_propagate_m<true>, 4 * 32,
@@ -1016,18 +1016,16 @@ lrdmc_status lrdmc_propagate(lrdmc_handle h, const lrdmc_schedule* sch) {
   if (P.precision == 0) {
     if (sp.rotate) {
       if (P.gsm)
-        k_propagate<true, true><<<grid, threads, smem, h->stream>>>(h->S, P.L, h->state, h->cache, P.n_w, sp, h->scr,
-                                                                    gd);
+        k_propagate_g<true><<<grid, threads, smem, h->stream>>>(h->S, P.L, h->state, h->cache, P.n_w, sp, h->scr,
+                                                                gd);
       else
-        k_propagate<true, false><<<grid, threads, smem, h->stream>>>(h->S, P.L, h->state, h->cache, P.n_w, sp,
-                                                                     h->scr, nullptr);
+        k_propagate<true><<<grid, threads, smem, h->stream>>>(h->S, P.L, h->state, h->cache, P.n_w, sp, h->scr);
     } else {
       if (P.gsm)
-        k_propagate<false, true><<<grid, threads, smem, h->stream>>>(h->S, P.L, h->state, h->cache, P.n_w, sp,
-                                                                     h->scr, gd);
+        k_propagate_g<false><<<grid, threads, smem, h->stream>>>(h->S, P.L, h->state, h->cache, P.n_w, sp, h->scr,
+                                                                 gd);
       else
-        k_propagate<false, false><<<grid, threads, smem, h->stream>>>(h->S, P.L, h->state, h->cache, P.n_w, sp,
-                                                                      h->scr, nullptr);
+        k_propagate<false><<<grid, threads, smem, h->stream>>>(h->S, P.L, h->state, h->cache, P.n_w, sp, h->scr);
     }
   } else {
     if (P.gsm)

@@ -1350,12 +1350,14 @@ __device__ __forceinline__ void propagate_walker(const DevSys& S, const Layout& 
   else propagate_walker_impl<ROT, false>(S, L, state, cache, w, P, T, sm, wscr, lane);
 }
 
-// GSM: the warps' working sets live in global memory (gsm + slot * s_stride)
-// instead of shared memory; used for systems whose shared layout would let
-// only a few warps share an SM (their O(N^2) caches are in global memory too).
+// Body of the propagate kernels.  GSM: the warps' working sets live in global
+// memory (gsm + slot * s_stride) instead of shared memory; used for systems
+// whose shared layout would let only a few warps share an SM (their O(N^2)
+// caches are in global memory too).
 template <bool ROT, bool GSM>
-__global__ void k_propagate(DevSys S, Layout L, double* __restrict__ state, double* __restrict__ cache, int n_w,
-                            StepParams P, double* scratch, double* gsm) {
+__device__ __forceinline__ void propagate_kernel_body(const DevSys& S, const Layout& L, double* __restrict__ state,
+                                                      double* __restrict__ cache, int n_w, const StepParams& P,
+                                                      double* scratch, double* gsm) {
   extern __shared__ double smem[];
   const double* T = stage_table(S, smem);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -1365,6 +1367,21 @@ __global__ void k_propagate(DevSys S, Layout L, double* __restrict__ state, doub
   const Scr wscr = warp_scratch(L, S.n_nuc, scratch, slot);
   for (int w = slot; w < n_w; w = next_walker(P, w, nwarps, lane))
     propagate_walker<ROT>(S, L, state, cache, w, P, T, sm, wscr, lane);
+}
+
+template <bool ROT>
+__global__ void k_propagate(DevSys S, Layout L, double* __restrict__ state, double* __restrict__ cache, int n_w,
+                            StepParams P, double* scratch) {
+  propagate_kernel_body<ROT, false>(S, L, state, cache, n_w, P, scratch, nullptr);
+}
+
+// Working sets in global memory: 4-warp CTAs, as many as the registers allow;
+// at most 128 registers per thread keep 4 CTAs (16 warps) per SM.
+template <bool ROT>
+__global__ void __maxnreg__(128) k_propagate_g(DevSys S, Layout L, double* __restrict__ state,
+                                               double* __restrict__ cache, int n_w, StepParams P, double* scratch,
+                                               double* gsm) {
+  propagate_kernel_body<ROT, true>(S, L, state, cache, n_w, P, scratch, gsm);
 }
 
 // Compact copies of walker fields (for host readback); a null output is skipped.
