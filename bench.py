@@ -37,15 +37,15 @@ FP64_PEAK_GFLOPS = 1250.0      # nominal B300 FP64 rate (profiling recipe table)
 # DRAM bytes (read + write) of one k_propagate launch of this workload, from the
 # ncu capture summarised in profiles/k_propagate_wm4096_full.md (to be re-taken
 # whenever the kernel changes)
-PROPAGATE_TRAFFIC_BYTES = 1.177876e9 + 0.653575e9
+PROPAGATE_TRAFFIC_BYTES = 1.175875e9 + 0.652870e9
 # FP64 pipe busy fraction of the same capture (sm__inst_executed_pipe_fp64,
 # % of peak sustained active); re-taken with the traffic
-PROPAGATE_FP64_PIPE_BUSY = 0.822
+PROPAGATE_FP64_PIPE_BUSY = 0.818
 # FP64 pipe instructions of the functions as the propagate kernel implements
 # them: table-driven exp (10), approximate reciprocal / rsqrt plus one
 # third-order refinement (4 / 6), tabulated erf(r/r_c)/r (index 3, Horner 10,
 # scalings 2).
-OP_EXP, OP_RSQ, OP_RCP, OP_ERF = 10.0, 6.0, 4.0, 15.0
+OP_EXP, OP_RSQ, OP_RCP, OP_ERF = 9.0, 6.0, 4.0, 15.0
 OP_PADE_VALUE = OP_RSQ + 1 + OP_RCP + 1          # u = c / (1/r + b)
 OP_PADE = OP_RSQ + 1 + OP_RCP + 1 + 1 + 2 + 3    # u, u', u'' and 1/r
 

@@ -6,12 +6,13 @@
 //
 //  exp_tab   table-driven exponential after P. T. P. Tang, "Table-driven
 //            implementation of the exponential function in IEEE floating-point
-//            arithmetic", ACM TOMS 15 (1989): x = (64 m + j) ln2/64 + r with
-//            |r| <= ln2/128, exp(x) = 2^m 2^(j/64) exp(r), exp(r) by its Taylor
-//            polynomial of degree 5 (truncation < 4e-17), the reduction by FMA
-//            against a two-part ln2/64 (Cody-Waite), 2^m applied to the exponent
-//            field.  Out-of-range and non-finite arguments are sorted out on the
-//            integer image of x, so the FP64 pipe sees 10 operations.
+//            arithmetic", ACM TOMS 15 (1989), with a 256-entry table:
+//            x = (256 m + j) ln2/256 + r with |r| <= ln2/512, exp(x) =
+//            2^m 2^(j/256) exp(r), exp(r) - 1 by its Taylor polynomial of degree 4
+//            (truncation |r|^5/120 < 4e-17), the reduction by FMA against a
+//            two-part ln2/256 (Cody-Waite), 2^m applied to the exponent field.
+//            Out-of-range and non-finite arguments are sorted out on the integer
+//            image of x, so the FP64 pipe sees 9 operations.
 //  rcp_nr    hardware reciprocal approximation (rcp.approx.ftz.f64, relative
 //            error ~2^-22) refined by one third-order Newton (Householder)
 //            step t <- t (1 + e + e^2), e = 1 - y t, which cubes the error.
@@ -26,36 +27,36 @@
 //            1e-18), evaluated by Horner; beyond t = 36.25 erf(sqrt t) rounds to
 //            1 in double and the result is 1/r itself.  About 15 FP64 operations
 //            against ~45 for erf and the divisions.
-// The reduction constants are ln2/64 split into double hi/lo parts and 64/ln2,
-// evaluated to 200 bits; the table holds 2^(j/64) rounded to double.
+// The reduction constants are ln2/256 split into double hi/lo parts and
+// 256/ln2, evaluated to 300 bits; the table holds 2^(j/256) rounded to double.
 #pragma once
 
 #include <cstdint>
 
 namespace lrdmc {
 
-constexpr int EXP_TAB = 64;
-constexpr double EXP_INV_L = 0x1.71547652b82fep+6;    // 64 / ln 2
-constexpr double EXP_L_HI = 0x1.62e42fefa39efp-7;     // ln 2 / 64, leading double
-constexpr double EXP_L_LO = 0x1.abc9e3b39803fp-62;    // ln 2 / 64 - EXP_L_HI
+constexpr int EXP_TAB = 256;
+constexpr int EXP_TAB_BITS = 8;                       // EXP_TAB = 2^EXP_TAB_BITS
+constexpr double EXP_INV_L = 0x1.71547652b82fep+8;    // 256 / ln 2
+constexpr double EXP_L_HI = 0x1.62e42fefa39efp-9;     // ln 2 / 256, leading double
+constexpr double EXP_L_LO = 0x1.abc9e3b39803fp-64;    // ln 2 / 256 - EXP_L_HI
 constexpr double EXP_SHIFTER = 0x1.8p52;              // 1.5 * 2^52: rounds to an integer
 
 // exp(x) for |x| < 700; 0 for x <= -700 (true value < 1e-304), +inf for
 // x >= 700, NaN for NaN.
 __device__ __forceinline__ double exp_tab(double x, const double* __restrict__ T) {
   const double t = fma(x, EXP_INV_L, EXP_SHIFTER);
-  const int k = (int)__double2loint(t);                 // round(x * 64/ln2), two's complement
+  const int k = (int)__double2loint(t);                 // round(x * 256/ln2), two's complement
   const double kd = t - EXP_SHIFTER;
   double r = fma(kd, -EXP_L_HI, x);
   r = fma(kd, -EXP_L_LO, r);
-  double q = fma(r, 1.0 / 120.0, 1.0 / 24.0);
-  q = fma(r, q, 1.0 / 6.0);
+  double q = fma(r, 1.0 / 24.0, 1.0 / 6.0);
   q = fma(r, q, 0.5);
   q = fma(r, q, 1.0);
   const double p = r * q;                               // exp(r) - 1
   const double tj = T[k & (EXP_TAB - 1)];
   double y = fma(tj, p, tj);
-  y = __longlong_as_double(__double_as_longlong(y) + (long long)((unsigned long long)(long long)(k >> 6) << 52));
+  y = __longlong_as_double(__double_as_longlong(y) + (long long)((unsigned long long)(long long)(k >> EXP_TAB_BITS) << 52));
   const unsigned hx = (unsigned)__double2hiint(x), lx = (unsigned)__double2loint(x);
   const unsigned ax = hx & 0x7fffffffu;
   const bool nan = ax > 0x7ff00000u || (ax == 0x7ff00000u && lx != 0u);

@@ -256,7 +256,9 @@ bool make_plan(const lrdmc_system* sys, const lrdmc_trial_wf* wf, const lrdmc_pa
   P.o_src = w; w += align_up(sizeof(int32_t) * P.n_w);
   P.o_dstat = w; w += align_up(sizeof(int32_t) * 16);
   P.o_stamps = w; w += align_up(sizeof(unsigned long long) * 3 * (size_t)P.n_w);
-  P.scratch_warps = round_up(std::min(P.n_w, SCRATCH_WARPS_CAP), 4);
+  // scratch for at least ceil(n / wpb) CTAs of wpb <= 8 warps (n = min(n_w, cap)), so
+  // that a launch of one walker per warp never leaves a walker for a second round
+  P.scratch_warps = round_up(std::min(P.n_w, SCRATCH_WARPS_CAP) + 7, 4);
   const size_t per_warp = P.precision == 0 ? scratch_doubles(L, P.n_nuc) : scratch_doubles_m(L, P.M);
   P.o_scr = w; w += align_up(sizeof(double) * per_warp * (size_t)P.scratch_warps);
   // a system whose shared layout leaves fewer than PROP_MIN_WARPS warps per SM
@@ -394,8 +396,12 @@ static lrdmc_status cuda_fail(lrdmc_handle h, const char* what, cudaError_t e) {
     if (e_ != cudaSuccess) return cuda_fail(h, "kernel launch", e_); \
   } while (0)
 
+// Shared memory of a walker kernel's CTA: the exponential table (FP64 kernels
+// only; the mixed kernels read it through L1) and one working set per warp.
+static int table_bytes(const Plan& P) { return P.precision == 0 ? (int)(EXP_TAB * sizeof(double)) : 0; }
+
 static int smem_bytes(lrdmc_handle h) {
-  return (int)(EXP_TAB * sizeof(double) + h->wpb * h->P.smem_per_warp);
+  return (int)(table_bytes(h->P) + h->wpb * h->P.smem_per_warp);
 }
 
 // The dynamic shared-memory limit is a per-kernel attribute shared by every
@@ -407,7 +413,8 @@ static lrdmc_status set_kernel_smem(lrdmc_handle h, int optin) {
   CK(h, cudaFuncSetAttribute(k_init_walkers, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   CK(h, cudaFuncSetAttribute(k_eval_configs, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   CK(h, cudaFuncSetAttribute(k_eloc_grad<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-  CK(h, cudaFuncSetAttribute(k_propagate_m<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  CK(h, cudaFuncSetAttribute(k_propagate_m<false, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  CK(h, cudaFuncSetAttribute(k_propagate_m<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   CK(h, cudaFuncSetAttribute(k_init_walkers_m, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   CK(h, cudaFuncSetAttribute(k_eval_configs_m, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   return LRDMC_OK;
@@ -938,7 +945,8 @@ lrdmc_status lrdmc_create(const lrdmc_system* sys, const lrdmc_trial_wf* wf, con
     if (P.precision == 0)
       CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_propagate<false>, wpb * 32, smem_bytes(h)));
     else
-      CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_propagate_m<false>, wpb * 32, smem_bytes(h)));
+      CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &bps, P.M.glob ? k_propagate_m<false, 1> : k_propagate_m<false, 0>, wpb * 32, smem_bytes(h)));
     if (bps >= 1 && bps * wpb >= best_warps) {
       best_warps = bps * wpb;
       best_wpb = wpb;
@@ -959,8 +967,7 @@ lrdmc_status lrdmc_create(const lrdmc_system* sys, const lrdmc_trial_wf* wf, con
       CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_propagate_g<false>, 4 * 32,
                                                           EXP_TAB * sizeof(double)));
     else
-      CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_propagate_m<true>, 4 * 32,
-                                                          EXP_TAB * sizeof(double)));
+      CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_propagate_m<true, -1>, 4 * 32, 0));
     if (bps < 1) return fail(h, LRDMC_ERR_UNSUPPORTED, "propagate kernel does not fit an SM");
     h->prop_grid = std::max(1, std::min(bps * h->num_sms, P.scratch_warps / h->prop_wpb));
   }
@@ -1010,7 +1017,7 @@ lrdmc_status lrdmc_propagate(lrdmc_handle h, const lrdmc_schedule* sch) {
   const Plan& P = h->P;
   const int grid = std::max(1, std::min(h->prop_grid, (P.n_w + h->prop_wpb - 1) / h->prop_wpb));
   const int threads = h->prop_wpb * 32;
-  const int smem = P.gsm ? (int)(EXP_TAB * sizeof(double)) : smem_bytes(h);
+  const int smem = P.gsm ? table_bytes(P) : smem_bytes(h);
   double* gd = (double*)h->gsm;
   float* gf = (float*)h->gsm;
   if (P.precision == 0) {
@@ -1029,11 +1036,14 @@ lrdmc_status lrdmc_propagate(lrdmc_handle h, const lrdmc_schedule* sch) {
     }
   } else {
     if (P.gsm)
-      k_propagate_m<true><<<grid, threads, smem, h->stream>>>(h->S, P.L, P.M, h->state, h->cache, P.n_w, sp, h->scr,
-                                                              gf);
+      k_propagate_m<true, -1><<<grid, threads, smem, h->stream>>>(h->S, P.L, P.M, h->state, h->cache, P.n_w, sp,
+                                                                  h->scr, gf);
+    else if (P.M.glob)
+      k_propagate_m<false, 1><<<grid, threads, smem, h->stream>>>(h->S, P.L, P.M, h->state, h->cache, P.n_w, sp,
+                                                                  h->scr, nullptr);
     else
-      k_propagate_m<false><<<grid, threads, smem, h->stream>>>(h->S, P.L, P.M, h->state, h->cache, P.n_w, sp,
-                                                               h->scr, nullptr);
+      k_propagate_m<false, 0><<<grid, threads, smem, h->stream>>>(h->S, P.L, P.M, h->state, h->cache, P.n_w, sp,
+                                                                  h->scr, nullptr);
   }
   LAUNCHED(h);
   h->last_kind = sch->kind;

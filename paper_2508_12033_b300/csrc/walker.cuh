@@ -1266,7 +1266,8 @@ __device__ void propagate_walker_impl(const DevSys& S, const Layout& L, double* 
         // w <- w b_x, b_x = b_bar / (W - E_0)
         const double den = Wd - P.E0;
         if (den > 0.0) {
-          weight *= bbar / den;
+          // refined reciprocal (a few ulp) instead of the FP64 division's longer sequence
+          weight *= den >= 0x1p-1000 ? bbar * rcp_nr(den) : bbar / den;
         } else {
           weight *= 0.0;
           status |= ST_NEG_DIAG;

@@ -160,7 +160,10 @@ __device__ __forceinline__ ScrM walker_scratch_m(const LayoutM& M, double* cblk,
   return s;
 }
 
-// Where the O(N^2) arrays of one walker are: shared memory or global.
+// Where the O(N^2) arrays of one walker are: shared memory or global.  BIG
+// fixes the placement at compile time (1 global, 0 shared), so that the
+// compiler sees plain global or shared accesses that cannot alias the
+// shared-memory scratch of the same loop; -1 decides at run time.
 struct MArr {
   float* geo;
   float* rt1;
@@ -168,9 +171,10 @@ struct MArr {
   float* hcur;
   float* dph;
 };
+template <int BIG = -1>
 __device__ __forceinline__ MArr marr(const LayoutM& M, float* sm, const ScrM& scr) {
   MArr A;
-  if (scr.big) {
+  if (BIG == 1 || (BIG < 0 && scr.big)) {
     A.geo = scr.big + M.g_geo;
     A.rt1 = scr.big + M.g_rt1;
     A.pair = scr.big + M.g_pair;
@@ -575,6 +579,7 @@ __device__ __forceinline__ void partner_terms(const DevSys& S, const Layout& L, 
 // Full evaluation: every hop ratio as r - 1 (FP32), the FP64 accumulators and
 // every cache of the incremental update (the pair caches in scr when set).
 // Requires the FP32 copy of B current.
+template <int BIG = -1>
 __device__ EvalOut eval_full_m(const DevSys& S, const Layout& L, const LayoutM& M, double* gblk, float* sm,
                                const ScrM& scr, double a, int node_rule, int lane) {
   const int ne = L.n_e, nn = S.n_nuc, P = L.n_hop;
@@ -583,7 +588,7 @@ __device__ EvalOut eval_full_m(const DevSys& S, const Layout& L, const LayoutM& 
   float* dchi = scr.dchi;
   float* dl = sm + M.dl;
   float* ej = sm + M.ej;
-  const MArr AR = marr(M, sm, scr);
+  const MArr AR = marr<BIG>(M, sm, scr);
   const float* geo = AR.geo;
   const float* rt1 = AR.rt1;
   const float* pair = AR.pair;
@@ -685,6 +690,7 @@ __device__ EvalOut eval_full_m(const DevSys& S, const Layout& L, const LayoutM& 
 // electrons' pair terms with m swapped using the cached old terms (scr.pt for
 // the derivative sums, scr.u2 for the hop differences; the new difference of
 // hop d of electron i with m is m's opposite hop d ^ 1 with i).
+template <int BIG = -1>
 __device__ EvalOut eval_incr_m(const DevSys& S, const Layout& L, const LayoutM& M, double* gblk, float* sm,
                                const ScrM& scr, int m, bool all_blocks, double a, double ia2, int node_rule,
                                int lane) {
@@ -696,7 +702,7 @@ __device__ EvalOut eval_incr_m(const DevSys& S, const Layout& L, const LayoutM& 
   float* dc6 = sm + M.chi5;     // basis differences at m's hops [n_bf][6]
   float* dl = sm + M.dl;
   float* ej = sm + M.ej;
-  const MArr AR = marr(M, sm, scr);
+  const MArr AR = marr<BIG>(M, sm, scr);
   const float* geo = AR.geo;
   const float* rt1 = AR.rt1;
   float* pair = AR.pair;
@@ -1031,9 +1037,9 @@ __global__ void k_init_walkers_m(DevSys S, Layout L, LayoutM M, double* __restri
                                  const double* __restrict__ x_in, const double* __restrict__ w_in, int n, double a,
                                  int node_rule, double* scratch) {
   extern __shared__ double smem[];
-  const double* T = stage_table(S, smem);
+  const double* T = S.exptab;   // few FP64 exponentials: the table is read through L1
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  float* sm = (float*)(smem + EXP_TAB) + wib * M.stride;
+  float* sm = (float*)smem + wib * M.stride;
   double* x = (double*)(sm + M.x);
   double* sc = (double*)(sm + M.sc);
   const int nwarps = gridDim.x * (blockDim.x >> 5);
@@ -1069,9 +1075,9 @@ __global__ void k_eval_configs_m(DevSys S, Layout L, LayoutM M, double* __restri
                                  double* __restrict__ ratios, double* __restrict__ ev, int32_t* __restrict__ n_node,
                                  double* scratch) {
   extern __shared__ double smem[];
-  const double* T = stage_table(S, smem);
+  const double* T = S.exptab;   // few FP64 exponentials: the table is read through L1
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  float* sm = (float*)(smem + EXP_TAB) + wib * M.stride;
+  float* sm = (float*)smem + wib * M.stride;
   double* x = (double*)(sm + M.x);
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   const int slot = blockIdx.x * (blockDim.x >> 5) + wib;
@@ -1098,6 +1104,7 @@ __global__ void k_eval_configs_m(DevSys S, Layout L, LayoutM M, double* __restri
 // the incremental evaluation persist in the walker's cache block.
 // One walker's interval (the body of k_propagate_m, also run by the batched
 // kernel).
+template <int BIG = -1>
 __device__ void propagate_walker_m(const DevSys& S, const Layout& L, const LayoutM& M, double* __restrict__ state,
                                    double* __restrict__ cache, int w, const StepParams& P, const double* T, float* sm,
                                    const ScrM& wscr, int lane) {
@@ -1123,7 +1130,8 @@ __device__ void propagate_walker_m(const DevSys& S, const Layout& L, const Layou
       if (P.kind == 1) {
         const double den = Wd - P.E0;
         if (den > 0.0) {
-          weight *= bbar / den;
+          // refined reciprocal (a few ulp) instead of the FP64 division's longer sequence
+          weight *= den >= 0x1p-1000 ? bbar * rcp_nr(den) : bbar / den;
         } else {
           weight *= 0.0;
           status |= ST_NEG_DIAG;
@@ -1151,10 +1159,10 @@ __device__ void propagate_walker_m(const DevSys& S, const Layout& L, const Layou
         }
         EvalOut e;
         if (!cached) {
-          e = eval_full_m(S, L, M, gblk, sm, scr, P.a, P.node_rule, lane);
+          e = eval_full_m<BIG>(S, L, M, gblk, sm, scr, P.a, P.node_rule, lane);
           cached = true;
         } else {
-          e = eval_incr_m(S, L, M, gblk, sm, scr, p / 6, reinv, P.a, ia2, P.node_rule, lane);
+          e = eval_incr_m<BIG>(S, L, M, gblk, sm, scr, p / 6, reinv, P.a, ia2, P.node_rule, lane);
         }
         bbar = e.bbar;
         Wd = e.W;
@@ -1197,20 +1205,21 @@ __device__ void propagate_walker_m(const DevSys& S, const Layout& L, const Layou
 // bound, and 28 resident warps per SM (4096 walkers in one wave on 148 SMs)
 // run it faster than the 20 that its unconstrained 94 registers allow.
 // GSM: working sets in global memory (gsm + slot * M.stride floats), as in
-// the FP64 kernel.
-template <bool GSM>
+// the FP64 kernel.  BIG: placement of the O(N^2) arrays (LayoutM::glob; -1:
+// decided at run time).
+template <bool GSM, int BIG>
 __global__ void __maxnreg__(72) k_propagate_m(DevSys S, Layout L, LayoutM M, double* __restrict__ state,
                                               double* __restrict__ cache, int n_w, StepParams P, double* scratch,
                                               float* gsm) {
   extern __shared__ double smem[];
-  const double* T = stage_table(S, smem);
+  const double* T = S.exptab;   // few FP64 exponentials: the table is read through L1
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   const int slot = blockIdx.x * (blockDim.x >> 5) + wib;
-  float* sm = GSM ? gsm + (size_t)slot * M.stride : (float*)(smem + EXP_TAB) + wib * M.stride;
+  float* sm = GSM ? gsm + (size_t)slot * M.stride : (float*)smem + wib * M.stride;
   const ScrM wscr = warp_scratch_m(L, M, scratch, slot);
   for (int w = slot; w < n_w; w = next_walker(P, w, nwarps, lane))
-    propagate_walker_m(S, L, M, state, cache, w, P, T, sm, wscr, lane);
+    propagate_walker_m<BIG>(S, L, M, state, cache, w, P, T, sm, wscr, lane);
 }
 
 }  // namespace lrdmc
