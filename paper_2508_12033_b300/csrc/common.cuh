@@ -158,9 +158,19 @@ __host__ __device__ inline void philox4x32_10(uint32_t c[4], uint32_t k0, uint32
 }
 
 // Uniform in [0,1): top 32 bits from hi, next 21 from the top of lo, times 2^-53.
+// On the device the exact value is assembled from bits: 0.5 + x 2^-53 has the
+// bit pattern 0x3FE0000000000000 + x for x < 2^52, so v 2^-53 is that pattern
+// with x = v - 2^52 when v >= 2^52, else that pattern with x = v, minus 0.5
+// (exact by Sterbenz's lemma); one FP64 addition at most instead of an
+// integer-to-double conversion and a multiplication.
 __host__ __device__ inline double uniform53(uint32_t hi, uint32_t lo) {
   uint64_t v = ((uint64_t)hi << 21) | (uint64_t)(lo >> 11);
+#ifdef __CUDA_ARCH__
+  const double h = __longlong_as_double((long long)(0x3FE0000000000000ull + (v & 0xFFFFFFFFFFFFFull)));
+  return (v >> 52) ? h : h - 0.5;
+#else
   return (double)v * 0x1p-53;
+#endif
 }
 
 // Stream layout: counter (walker slot, step, interval, 0) gives the persistence

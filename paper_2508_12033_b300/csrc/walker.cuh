@@ -231,23 +231,31 @@ __device__ void all_potentials(const DevSys& S, const Layout& L, const double* x
 // A^{-1}.  Returns true on a zero (or non-finite) pivot.  With logdet set,
 // adds log|det A| (the sum of log|pivot|) to it.  f is scratch of N doubles:
 // the elimination factors of a column are recorded first, so that all rows are
-// then updated in one pass over (row, column) pairs.
+// then updated in one pass over (row, column) pairs.  The pivot search
+// compares |a| on the integer images of the doubles (a NaN never wins; the
+// lowest row wins ties), over as many butterfly levels as the candidate lanes
+// need, and 1/pivot is the refined reciprocal, so that the FP64 pipe sees only
+// the row scaling and the elimination.
 __device__ bool warp_gauss_jordan(double* M, int N, int lane, double* f, double* logdet = nullptr) {
   const int W2 = 2 * N;
+  int npad = 1;
+  while (npad < N && npad < WARP) npad <<= 1;
+  constexpr long long ABS = 0x7fffffffffffffffll, INF = 0x7ff0000000000000ll;
   for (int c = 0; c < N; ++c) {
-    double best = -1.0;
+    long long best = -1;   // |a| as a non-negative integer image; -1: no candidate
     int bi = N;
     for (int r = c + lane; r < N; r += WARP) {
-      const double v = fabs(M[r * W2 + c]);
-      if (v > best || (v == best && r < bi)) { best = v; bi = r; }
+      const long long v = __double_as_longlong(M[r * W2 + c]) & ABS;
+      if (v <= INF && (v > best || (v == best && r < bi))) { best = v; bi = r; }
     }
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-      const double ob = __shfl_xor_sync(FULL, best, o);
+    for (int o = npad >> 1; o; o >>= 1) {
+      const long long ob = __shfl_xor_sync(FULL, best, o);
       const int oi = __shfl_xor_sync(FULL, bi, o);
       if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
     }
-    if (!(best > 0.0) || !isfinite(best)) return true;
+    best = __shfl_sync(FULL, best, 0);
+    bi = __shfl_sync(FULL, bi, 0);
+    if (best <= 0 || best >= INF) return true;    // zero, no candidate or infinite
     if (bi != c) {
       for (int j = lane; j < W2; j += WARP) {
         const double t = M[c * W2 + j];
@@ -257,7 +265,9 @@ __device__ bool warp_gauss_jordan(double* M, int N, int lane, double* f, double*
     }
     __syncwarp();
     const double piv = M[c * W2 + c];
-    const double inv = 1.0 / piv;
+    // refined reciprocal inside the normal range, the division outside it
+    const int ex = (int)(best >> 52);
+    const double inv = ex > 24 && ex < 2000 ? rcp_nr(piv) : 1.0 / piv;
     if (logdet) *logdet += log(fabs(piv));
     __syncwarp();
     // scale the pivot row; record the other rows' factors (other rows: no conflict)
@@ -267,7 +277,7 @@ __device__ bool warp_gauss_jordan(double* M, int N, int lane, double* f, double*
     for (int t = lane; t < N * W2; t += WARP) {
       const int r = t / W2, j = t - r * W2;
       const double fr = f[r];
-      if (fr != 0.0) M[t] -= fr * M[c * W2 + j];
+      if ((__double_as_longlong(fr) << 1) != 0) M[t] -= fr * M[c * W2 + j];   // fr != 0
     }
     __syncwarp();
   }

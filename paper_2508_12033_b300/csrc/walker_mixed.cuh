@@ -965,9 +965,13 @@ __device__ void apply_hop_m(const DevSys& S, const Layout& L, const LayoutM& M, 
   __syncwarp();
   for (int j = lane; j < n; j += WARP) f[j] = (f[j] - (j == sr.ii ? 1.0 : 0.0)) * invR;
   __syncwarp();
+  // B and its FP32 copy (same layout) in one pass
+  float* b32 = sm + M.b32 + sr.bt_off;
   for (int o = lane; o < n * n; o += WARP) {
     const int j = o / n, k = o - j * n;
-    B[o] = fma(-row[k], f[j], B[o]);
+    const double nb = fma(-row[k], f[j], B[o]);
+    B[o] = nb;
+    b32[o] = (float)nb;
   }
   for (int o = lane; o < L.n_max; o += WARP) val[i * L.n_max + o] = phiv[o];
   for (int o = lane; o < 4 * L.n_max; o += WARP) der[i * 4 * L.n_max + o] = phi5[o];
@@ -986,7 +990,6 @@ __device__ void apply_hop_m(const DevSys& S, const Layout& L, const LayoutM& M, 
   }
   __threadfence_block();
   __syncwarp();
-  refresh_b32(L, M, sm, i - sr.ii, i - sr.ii + n, lane);
 }
 
 __device__ __forceinline__ void load_block_m(const Layout& L, const LayoutM& M, const double* __restrict__ g,
