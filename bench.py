@@ -37,10 +37,10 @@ FP64_PEAK_GFLOPS = 1250.0      # nominal B300 FP64 rate (profiling recipe table)
 # DRAM bytes (read + write) of one k_propagate launch of this workload, from the
 # ncu capture summarised in profiles/k_propagate_wm4096_full.md (to be re-taken
 # whenever the kernel changes)
-PROPAGATE_TRAFFIC_BYTES = 1.175875e9 + 0.652870e9
+PROPAGATE_TRAFFIC_BYTES = 1.176977e9 + 0.652905e9
 # FP64 pipe busy fraction of the same capture (sm__inst_executed_pipe_fp64,
 # % of peak sustained active); re-taken with the traffic
-PROPAGATE_FP64_PIPE_BUSY = 0.818
+PROPAGATE_FP64_PIPE_BUSY = 0.819
 # FP64 pipe instructions of the functions as the propagate kernel implements
 # them: table-driven exp (10), approximate reciprocal / rsqrt plus one
 # third-order refinement (4 / 6), tabulated erf(r/r_c)/r (index 3, Horner 10,
