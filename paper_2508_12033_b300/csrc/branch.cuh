@@ -1,6 +1,6 @@
 // Branching (reconfiguration) kernels, Sec. II.A of the paper.
 //
-//  k_branch_reduce   per-interval sums in a fixed order (deterministic):
+//  branch_reduce_body per-interval sums in a fixed order (deterministic):
 //                    sum w, sum w e_L, sum f, sum f e_L with f = w/(W - E_0),
 //                    max w, OR of status bits, hop statistics
 //  k_reconfigure     integer comb: q_b = floor(w_b / w_max 2^S), exact uint64
@@ -9,9 +9,11 @@
 //  slot_body         where each copy is stored (selected walkers keep their slots)
 //  k_gather_slots    in place: unselected slots receive a copy of their source, w = 1
 //
-// The reduction and the comb run in one CTA: N_w is at most a few 10^5 and the
-// work is O(N_w) integer/FP64 operations, far below one microsecond per 10^4
-// walkers; the gather moves the walker blocks and is HBM-bound.
+// A single system's branching spreads the per-walker FP64 work over the grid
+// (k_branch_partials, k_branch_combine, k_quantise) and keeps the integer scan,
+// comb and slot assignment in one CTA (k_reconfigure_q); the one-CTA bodies
+// serve the batched path (one CTA per system) and the comb entry points.  The
+// gather moves the walker blocks and is HBM-bound.
 #pragma once
 
 #include "common.cuh"
@@ -83,10 +85,51 @@ __device__ void branch_reduce_body(const Layout& L, const double* __restrict__ s
   }
 }
 
-__global__ void __launch_bounds__(BR_THREADS) k_branch_reduce(Layout L, const double* __restrict__ state,
-                                                              int n_w, double E0, int lb,
-                                                              double* __restrict__ out) {
-  branch_reduce_body(L, state, n_w, E0, lb, out);
+// Comb over the inclusive prefix sums Q of the quantised weights (total tot):
+// src[alpha] = the first b with (xi32 + alpha 2^32) tot < n 2^32 Q_b, for
+// the slots [lo, hi) of this thread; then the number of distinct survivors
+// and the status words.
+__device__ void comb_body(int n, uint32_t xi32, const unsigned long long* __restrict__ Q, unsigned long long tot,
+                          int lo, int hi, int32_t* __restrict__ src, int32_t* __restrict__ status,
+                          double* __restrict__ stats_out, double wmax) {
+  __shared__ int s_cnt[BR_THREADS];
+  const int t = threadIdx.x;
+  // (3) comb: first b with (xi32 + alpha 2^32) tot < n 2^32 Q_b.  Thread t
+  // takes the contiguous slots [lo, hi): a binary search for the first, then,
+  // since the answer does not decrease with alpha, a forward walk for the rest.
+  const unsigned __int128 n32 = (unsigned __int128)(unsigned)n << 32;
+  {
+    int b = 0;
+    for (int al = lo; al < hi; ++al) {
+      const unsigned __int128 lhs = ((unsigned __int128)xi32 + ((unsigned __int128)(unsigned)al << 32)) *
+                                    (unsigned __int128)tot;
+      if (al == lo) {
+        int b0 = 0, b1 = n - 1;   // condition holds at b = n - 1
+        while (b0 < b1) {
+          const int mid = (b0 + b1) >> 1;
+          if (lhs < n32 * (unsigned __int128)Q[mid]) b1 = mid; else b0 = mid + 1;
+        }
+        b = b0;
+      } else {
+        while (b < n - 1 && !(lhs < n32 * (unsigned __int128)Q[b])) ++b;
+      }
+      src[al] = b;
+    }
+  }
+  __syncthreads();
+  // (4) distinct survivors (src is non-decreasing)
+  int cnt = 0;
+  for (int al = t; al < n; al += BR_THREADS) cnt += (al == 0 || src[al] != src[al - 1]) ? 1 : 0;
+  s_cnt[t] = cnt;
+  __syncthreads();
+  for (int s = BR_THREADS / 2; s > 0; s >>= 1) {
+    if (t < s) s_cnt[t] += s_cnt[t + s];
+    __syncthreads();
+  }
+  if (t == 0) {
+    if (status) { status[0] = 0; status[1] = s_cnt[0]; }
+    if (stats_out) { stats_out[BS_BAD] = 0.0; stats_out[BS_WMAX] = wmax; stats_out[BS_SURV] = s_cnt[0]; }
+  }
 }
 
 // Integer comb.  Weights are read as w[a * w_stride]; Q is uint64 scratch of
@@ -97,7 +140,6 @@ __device__ void reconfigure_body(const double* __restrict__ w, int w_stride, int
   __shared__ double s_max[BR_THREADS];
   __shared__ int s_bad[BR_THREADS];
   __shared__ unsigned long long s_sum[BR_THREADS];
-  __shared__ int s_cnt[BR_THREADS];
   const int t = threadIdx.x;
   // (1) max weight and validity
   double m = 0.0;
@@ -147,42 +189,7 @@ __device__ void reconfigure_body(const double* __restrict__ w, int w_stride, int
   }
   __syncthreads();
   const unsigned long long tot = s_sum[BR_THREADS - 1];
-  // (3) comb: first b with (xi32 + alpha 2^32) tot < n 2^32 Q_b.  Thread t
-  // takes the contiguous slots [lo, hi): a binary search for the first, then,
-  // since the answer does not decrease with alpha, a forward walk for the rest.
-  const unsigned __int128 n32 = (unsigned __int128)(unsigned)n << 32;
-  {
-    int b = 0;
-    for (int al = lo; al < hi; ++al) {
-      const unsigned __int128 lhs = ((unsigned __int128)xi32 + ((unsigned __int128)(unsigned)al << 32)) *
-                                    (unsigned __int128)tot;
-      if (al == lo) {
-        int b0 = 0, b1 = n - 1;   // condition holds at b = n - 1
-        while (b0 < b1) {
-          const int mid = (b0 + b1) >> 1;
-          if (lhs < n32 * (unsigned __int128)Q[mid]) b1 = mid; else b0 = mid + 1;
-        }
-        b = b0;
-      } else {
-        while (b < n - 1 && !(lhs < n32 * (unsigned __int128)Q[b])) ++b;
-      }
-      src[al] = b;
-    }
-  }
-  __syncthreads();
-  // (4) distinct survivors (src is non-decreasing)
-  int cnt = 0;
-  for (int al = t; al < n; al += BR_THREADS) cnt += (al == 0 || src[al] != src[al - 1]) ? 1 : 0;
-  s_cnt[t] = cnt;
-  __syncthreads();
-  for (int s = BR_THREADS / 2; s > 0; s >>= 1) {
-    if (t < s) s_cnt[t] += s_cnt[t + s];
-    __syncthreads();
-  }
-  if (t == 0) {
-    if (status) { status[0] = 0; status[1] = s_cnt[0]; }
-    if (stats_out) { stats_out[BS_BAD] = 0.0; stats_out[BS_WMAX] = wmax; stats_out[BS_SURV] = s_cnt[0]; }
-  }
+  comb_body(n, xi32, Q, tot, lo, hi, src, status, stats_out, wmax);
 }
 
 // Exclusive prefix count over the block of the flags f(i), i in [0, n), in
@@ -253,6 +260,182 @@ __global__ void __launch_bounds__(BR_THREADS) k_reconfigure(const double* __rest
                                                             double* __restrict__ stats_out, int slots) {
   reconfigure_body(w, w_stride, n, xi32, Q, src, status, stats_out);
   if (!slots) return;
+  __syncthreads();
+  slot_body(n, src, reinterpret_cast<int32_t*>(Q), status);
+}
+
+// ------------------------------------------------------------ grid-wide passes
+// A single system's branching at large N_w: the per-walker FP64 work (the
+// load-balanced weight w / (W - E_0) in the sums, w_b / w_max in the
+// quantisation) exceeds what one SM's FP64 pipe does in a few microseconds,
+// so it is spread over the grid and the one-CTA kernel keeps only integer work:
+//  k_branch_partials  CTA c reduces the contiguous walkers [c C, (c + 1) C)
+//                     in a fixed order (same quantities as branch_reduce_body,
+//                     plus max w and the invalid-weight flag)
+//  k_branch_combine   one warp adds the CTA partials in index order
+//  k_quantise         q_b = floor(w_b / w_max 2^S) for every walker, into Q
+//  k_reconfigure_q    prefix sums of q, comb, survivors, slot assignment
+// q_b, its prefix sums and the comb are the integers reconfigure_body forms
+// (max and integer sums do not depend on order, q_b is the same expression);
+// the FP64 sums are deterministic, in their own fixed order.
+constexpr int BP_THREADS = 256;
+constexpr int BP_MAX_CTAS = 1024;
+constexpr int BP_STRIDE = 16;   // doubles per CTA partial
+enum BranchPart : int {
+  BP_SUMW = 0, BP_SUMWE = 1, BP_SUMF = 2, BP_SUMFE = 3, BP_MOVES = 4, BP_MOVESMAX = 5, BP_STATUS = 6,
+  BP_WMAX = 7, BP_BAD = 8
+};
+
+__host__ __device__ inline int branch_part_ctas(int n) {
+  const int c = (n + BP_THREADS - 1) / BP_THREADS;
+  return c < 1 ? 1 : (c > BP_MAX_CTAS ? BP_MAX_CTAS : c);
+}
+
+__global__ void __launch_bounds__(BP_THREADS) k_branch_partials(Layout L, const double* __restrict__ state,
+                                                                int n_w, double E0, int lb,
+                                                                double* __restrict__ part) {
+  constexpr int NW = BP_THREADS / 32;
+  __shared__ double s_part[8][NW];
+  __shared__ unsigned s_or[NW], s_bad[NW];
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  const int C = (n_w + gridDim.x - 1) / gridDim.x;
+  const int lo = min(n_w, (int)blockIdx.x * C), hi = min(n_w, lo + C);
+  // w, w e, f, f e, moves, max moves, (unused), max w
+  double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  unsigned orv = 0u, bad = 0u;
+  for (int a = lo + t; a < hi; a += BP_THREADS) {
+    const double* sc = state + (size_t)a * L.g_stride + L.g_sc;
+    const double w = sc[SC_W], e = sc[SC_EL];
+    acc[0] += w;
+    acc[1] += w * e;
+    const double f = lb ? w / (sc[SC_WDIAG] - E0) : w;
+    acc[2] += f;
+    acc[3] += f * e;
+    acc[4] += sc[SC_MOVES];
+    acc[5] = fmax(acc[5], sc[SC_MOVES]);
+    orv |= (unsigned)sc[SC_STATUS];
+    if (!isfinite(w) || w < 0.0) bad = 1u;
+    acc[7] = fmax(acc[7], w);
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) acc[k] += __shfl_xor_sync(FULL, acc[k], o);
+    acc[5] = fmax(acc[5], __shfl_xor_sync(FULL, acc[5], o));
+    acc[7] = fmax(acc[7], __shfl_xor_sync(FULL, acc[7], o));
+    orv |= __shfl_xor_sync(FULL, orv, o);
+    bad |= __shfl_xor_sync(FULL, bad, o);
+  }
+  if (lane == 0) {
+    for (int k = 0; k < 8; ++k) s_part[k][wid] = acc[k];
+    s_or[wid] = orv;
+    s_bad[wid] = bad;
+  }
+  __syncthreads();
+  if (t == 0) {
+    double r[8];
+    unsigned ro = 0u, rb = 0u;
+    for (int k = 0; k < 8; ++k) r[k] = s_part[k][0];
+    for (int v = 1; v < NW; ++v) {
+      for (int k = 0; k < 5; ++k) r[k] += s_part[k][v];
+      r[5] = fmax(r[5], s_part[5][v]);
+      r[7] = fmax(r[7], s_part[7][v]);
+    }
+    for (int v = 0; v < NW; ++v) { ro |= s_or[v]; rb |= s_bad[v]; }
+    double* out = part + (size_t)blockIdx.x * BP_STRIDE;
+    for (int k = 0; k < 6; ++k) out[k] = r[k];
+    out[BP_STATUS] = (double)ro;
+    out[BP_WMAX] = r[7];
+    out[BP_BAD] = (double)rb;
+  }
+}
+
+// One warp: the n_part CTA partials, lane l taking l, l + 32, ... in order,
+// then a fixed xor tree.  Writes the branching statistics, w_max and the
+// invalid-weight flag (negative or non-finite weights, or all zero).
+__global__ void __launch_bounds__(32) k_branch_combine(const double* __restrict__ part, int n_part,
+                                                       double* __restrict__ out) {
+  const int lane = threadIdx.x;
+  double r[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  double wm = 0.0;
+  unsigned ro = 0u, rb = 0u;
+  for (int c = lane; c < n_part; c += 32) {
+    const double* p = part + (size_t)c * BP_STRIDE;
+    for (int k = 0; k < 5; ++k) r[k] += p[k];
+    r[5] = fmax(r[5], p[BP_MOVESMAX]);
+    wm = fmax(wm, p[BP_WMAX]);
+    ro |= (unsigned)p[BP_STATUS];
+    rb |= p[BP_BAD] != 0.0 ? 1u : 0u;
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) r[k] += __shfl_xor_sync(FULL, r[k], o);
+    r[5] = fmax(r[5], __shfl_xor_sync(FULL, r[5], o));
+    wm = fmax(wm, __shfl_xor_sync(FULL, wm, o));
+    ro |= __shfl_xor_sync(FULL, ro, o);
+    rb |= __shfl_xor_sync(FULL, rb, o);
+  }
+  if (lane == 0) {
+    out[BS_SUMW] = r[0];
+    out[BS_SUMWE] = r[1];
+    out[BS_SUMF] = r[2];
+    out[BS_SUMFE] = r[3];
+    out[BS_MOVES] = r[4];
+    out[BS_MOVESMAX] = r[5];
+    out[BS_STATUS] = (double)ro;
+    out[BS_WMAX] = wm;
+    out[BS_BAD] = (rb || !(wm > 0.0)) ? 1.0 : 0.0;
+  }
+}
+
+// Q[b] = floor(w_b / w_max 2^S), S = 62 - bitlength(n); nothing when the
+// weights are invalid.
+__global__ void __launch_bounds__(BP_THREADS) k_quantise(const double* __restrict__ w, int w_stride, int n,
+                                                         const double* __restrict__ stats,
+                                                         unsigned long long* __restrict__ Q) {
+  if (stats[BS_BAD] != 0.0) return;
+  const double wmax = stats[BS_WMAX];
+  int nbits = 0;
+  for (int v = n; v; v >>= 1) ++nbits;
+  const double scale = ldexp(1.0, 62 - nbits);
+  for (int a = blockIdx.x * BP_THREADS + threadIdx.x; a < n; a += gridDim.x * BP_THREADS)
+    Q[a] = (unsigned long long)floor((w[(size_t)a * w_stride] / wmax) * scale);
+}
+
+// One CTA: Q holds q_b on entry and the inclusive prefix sums after the scan;
+// then the comb and, as in k_reconfigure with slots set, the slot assignment.
+// Q doubles as the slot assignment's scratch.
+__global__ void __launch_bounds__(BR_THREADS) k_reconfigure_q(int n, uint32_t xi32,
+                                                              unsigned long long* __restrict__ Q,
+                                                              int32_t* __restrict__ src,
+                                                              int32_t* __restrict__ status,
+                                                              double* __restrict__ stats) {
+  __shared__ unsigned long long s_sum[BR_THREADS];
+  const int t = threadIdx.x;
+  if (stats[BS_BAD] != 0.0) {
+    if (t == 0) { status[0] = 1; status[1] = 0; }
+    return;
+  }
+  const int chunk = (n + BR_THREADS - 1) / BR_THREADS;
+  const int lo = min(n, t * chunk), hi = min(n, lo + chunk);
+  unsigned long long loc = 0ull;
+  for (int a = lo; a < hi; ++a) loc += Q[a];
+  s_sum[t] = loc;
+  __syncthreads();
+  for (int off = 1; off < BR_THREADS; off <<= 1) {
+    const unsigned long long v = t >= off ? s_sum[t - off] : 0ull;
+    __syncthreads();
+    s_sum[t] += v;
+    __syncthreads();
+  }
+  unsigned long long run = t ? s_sum[t - 1] : 0ull;
+  for (int a = lo; a < hi; ++a) {
+    run += Q[a];
+    Q[a] = run;
+  }
+  __syncthreads();
+  comb_body(n, xi32, Q, s_sum[BR_THREADS - 1], lo, hi, src, status, stats, stats[BS_WMAX]);
   __syncthreads();
   slot_body(n, src, reinterpret_cast<int32_t*>(Q), status);
 }

@@ -113,7 +113,7 @@ struct Plan {
   size_t smem_per_warp = 0;
   // workspace offsets (bytes)
   size_t o_sys = 0, sys_bytes = 0, o_state = 0, o_alt = 0, state_bytes = 0, o_cache = 0, o_cache_alt = 0,
-         cache_bytes = 0, o_stats = 0, o_q = 0, o_src = 0, o_dstat = 0, o_stamps = 0, o_scr = 0, o_gsm = 0,
+         cache_bytes = 0, o_stats = 0, o_part = 0, o_q = 0, o_src = 0, o_dstat = 0, o_stamps = 0, o_scr = 0, o_gsm = 0,
          total = 0;
   int scratch_warps = 0;
   bool gsm = false;   // propagate with the working sets in global memory (large systems)
@@ -252,6 +252,7 @@ bool make_plan(const lrdmc_system* sys, const lrdmc_trial_wf* wf, const lrdmc_pa
   P.o_cache = w; w += align_up(P.cache_bytes);
   P.o_cache_alt = w; w += align_up(P.cache_bytes);
   P.o_stats = w; w += align_up(sizeof(double) * BS_COUNT);
+  P.o_part = w; w += align_up(sizeof(double) * BP_STRIDE * (size_t)branch_part_ctas(P.n_w));
   P.o_q = w; w += align_up(sizeof(unsigned long long) * P.n_w);
   P.o_src = w; w += align_up(sizeof(int32_t) * P.n_w);
   P.o_dstat = w; w += align_up(sizeof(int32_t) * 16);
@@ -355,6 +356,7 @@ struct lrdmc_s {
   double* adj_blk = nullptr;     // per-warp walker blocks of the gradient kernel
   double* cache_alt = nullptr;
   double* stats = nullptr;
+  double* part = nullptr;        // branching: per-CTA partial sums
   unsigned long long* Q = nullptr;
   int32_t* src = nullptr;
   int32_t* dstat = nullptr;
@@ -923,6 +925,7 @@ lrdmc_status lrdmc_create(const lrdmc_system* sys, const lrdmc_trial_wf* wf, con
   h->cache = P.cache_bytes ? (double*)(base + P.o_cache) : nullptr;
   h->cache_alt = P.cache_bytes ? (double*)(base + P.o_cache_alt) : nullptr;
   h->stats = (double*)(base + P.o_stats);
+  h->part = (double*)(base + P.o_part);
   h->Q = (unsigned long long*)(base + P.o_q);
   h->src = (int32_t*)(base + P.o_src);
   h->dstat = (int32_t*)(base + P.o_dstat);
@@ -1055,11 +1058,16 @@ lrdmc_status lrdmc_branch(lrdmc_handle h) {
   DeviceGuard g(h->device);
   const Plan& P = h->P;
   const int lb = h->last_kind == LRDMC_LOAD_BALANCED;
-  k_branch_reduce<<<1, BR_THREADS, 0, h->stream>>>(P.L, h->state, P.n_w, h->E0, lb, h->stats);
+  // per-walker FP64 work over the grid, the integer comb in one CTA
+  const int nc = branch_part_ctas(P.n_w);
+  k_branch_partials<<<nc, BP_THREADS, 0, h->stream>>>(P.L, h->state, P.n_w, h->E0, lb, h->part);
+  LAUNCHED(h);
+  k_branch_combine<<<1, 32, 0, h->stream>>>(h->part, nc, h->stats);
+  LAUNCHED(h);
+  k_quantise<<<nc, BP_THREADS, 0, h->stream>>>(h->state + P.L.g_sc + SC_W, P.L.g_stride, P.n_w, h->stats, h->Q);
   LAUNCHED(h);
   const uint32_t xi = branch_offset32(h->prm.seed, h->interval);
-  k_reconfigure<<<1, BR_THREADS, 0, h->stream>>>(h->state + P.L.g_sc + SC_W, P.L.g_stride, P.n_w, xi, h->Q,
-                                                 h->src, h->dstat, h->stats, 1);
+  k_reconfigure_q<<<1, BR_THREADS, 0, h->stream>>>(P.n_w, xi, h->Q, h->src, h->dstat, h->stats);
   LAUNCHED(h);
   // in place: only the slots of walkers the comb did not select receive a copy
   k_gather_slots<<<P.n_w, 256, 0, h->stream>>>(P.L, h->state, h->cache, h->src, h->dstat);

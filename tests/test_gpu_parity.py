@@ -147,11 +147,13 @@ def test_reconfigure_rejects_invalid_weights():
         assert st.cpu().numpy()[0] == 1
 
 
+# 1283 walkers: the grid-wide partial sums run in six CTAs, the last one ragged
+@pytest.mark.parametrize("n_w", [129, 1283])
 @pytest.mark.parametrize("kind", [1, 0])
-def test_branch_matches_oracle(kind):
+def test_branch_matches_oracle(kind, n_w):
     P = lib_or_skip()
     s = W.h2_sto3g()
-    lr, x0 = _mk(P, s, 129)
+    lr, x0 = _mk(P, s, n_w)
     E0 = lr.e0
     if kind == 1:
         lr.propagate(P.LOAD_BALANCED, n_proj=12)
