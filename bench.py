@@ -34,13 +34,18 @@ N_PROJ = 20
 A = 0.2
 SEED = 1
 FP64_PEAK_GFLOPS = 1250.0      # nominal B300 FP64 rate (profiling recipe table)
-# DRAM bytes (read + write) of one k_propagate launch of this workload, from the
-# ncu capture summarised in profiles/k_propagate_wm4096_full.md (to be re-taken
-# whenever the kernel changes)
+# FP64 rate from unit counts: 148 SMs x 2 FP64 FMA lanes per clock (the peak
+# ncu reports for the FP64 pipe) x 2 FLOP x 2.032 GHz maximum SM clock
+FP64_UNIT_COUNT_GFLOPS = 148 * 2 * 2 * 2.032
+# DRAM bytes (read + write) of one k_propagate launch of this workload and the
+# FP64 pipe busy fraction, from one ncu capture of the propagate kernel
+# (second launch of `bench.py --steps 2 --warmup 1` with every extra section
+# off); None when the kernel has changed since that capture
 PROPAGATE_TRAFFIC_BYTES = 1.176977e9 + 0.652905e9
-# FP64 pipe busy fraction of the same capture (sm__inst_executed_pipe_fp64,
-# % of peak sustained active); re-taken with the traffic
 PROPAGATE_FP64_PIPE_BUSY = 0.819
+# walkers per host process in the oracle sample (cpu_baseline and the
+# reference arm): one warm-up interval, then one timed 20-hop interval
+ORACLE_WALKERS_PER_PROC = 8
 # FP64 pipe instructions of the functions as the propagate kernel implements
 # them: table-driven exp (10), approximate reciprocal / rsqrt plus one
 # third-order refinement (4 / 6), tabulated erf(r/r_c)/r (index 3, Horner 10,
@@ -176,33 +181,74 @@ class ClockSampler:
 
 # ----------------------------------------------------------------- oracle baseline
 def _oracle_chunk(args):
-    ids, n_proj, interval = args
+    """One host process's share of the oracle sample: its walkers are set up
+    and run one load-balanced warm-up interval untimed, then one timed
+    20-hop interval (steady state, as the GPU's timed intervals are)."""
+    ids, n_proj = args
     import workloads as W
     from oracle import lrdmc as L
     s = W.water_methane()
     x = W.initial_walkers(s, N_W, seed=SEED + 10)[ids]
     Wk = L.init_walkers(s, x, A)
     E0 = float(np.mean(Wk.ev["eL"]))
+    L.propagate_lb(s, Wk, A, E0, n_proj, SEED, 0, walker_ids=ids)
     t = time.perf_counter()
-    L.propagate_lb(s, Wk, A, E0, n_proj, SEED, interval, walker_ids=ids)
+    L.propagate_lb(s, Wk, A, E0, n_proj, SEED, 1, walker_ids=ids)
     return time.perf_counter() - t, len(ids) * n_proj
 
 
-def oracle_rate(n_walkers_per_proc=48, n_proj=N_PROJ, procs=None):
-    """Walker-steps/s of the CPU oracle on a bounded sample, all host cores
-    (one spawned process per core, each on its own walker slots)."""
-    import multiprocessing as mp
-    procs = procs or os.cpu_count() or 1
-    jobs = [(np.arange(k * n_walkers_per_proc, (k + 1) * n_walkers_per_proc) % N_W, n_proj, 0)
-            for k in range(procs)]
-    ctx = mp.get_context("spawn")
-    t0 = time.perf_counter()
-    with ctx.Pool(procs) as pool:
-        res = pool.map(_oracle_chunk, jobs)
-    wall = time.perf_counter() - t0
-    steps = sum(r[1] for r in res)
-    slowest = max(r[0] for r in res)
-    return steps / slowest, procs, steps, wall
+class OracleSample:
+    """The CPU oracle timed on all host cores: one spawned process per core,
+    each on its own ORACLE_WALKERS_PER_PROC walker slots of the benchmark
+    population.  One sample = one timed 20-hop interval of every process
+    (after its untimed set-up and warm-up interval); its time is the slowest
+    process's interval and its rate the walker-steps of all processes over
+    that time."""
+
+    def __init__(self, procs=None):
+        import multiprocessing as mp
+        self.procs = procs or os.cpu_count() or 1
+        self.pool = mp.get_context("spawn").Pool(self.procs)
+
+    def describe(self):
+        return (f"{self.procs} processes x {ORACLE_WALKERS_PER_PROC} walkers, one timed {N_PROJ}-hop "
+                f"load-balanced interval each after one untimed warm-up interval "
+                f"({self.procs * ORACLE_WALKERS_PER_PROC * N_PROJ} walker-steps per sample)")
+
+    def run(self, k=0):
+        n = ORACLE_WALKERS_PER_PROC
+        jobs = [((np.arange(n) + (j * n + k * self.procs * n)) % N_W, N_PROJ) for j in range(self.procs)]
+        res = self.pool.map(_oracle_chunk, jobs)
+        steps = sum(r[1] for r in res)
+        slowest = max(r[0] for r in res)
+        return steps / slowest, slowest, steps
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def measure_fp64_peak(dev_index=0):
+    """FP64 FMA peak of this GPU from bench_fp64_peak.cu (built here with nvcc
+    into _build/, run under the clock sampler); None if it cannot be built."""
+    src = os.path.join(ROOT, "bench_fp64_peak.cu")
+    out_dir = os.path.join(ROOT, "_build")
+    exe = os.path.join(out_dir, "bench_fp64_peak")
+    try:
+        if not os.path.exists(exe) or os.path.getmtime(exe) < os.path.getmtime(src):
+            os.makedirs(out_dir, exist_ok=True)
+            from paper_2508_12033_b300.build import nvcc_path, ARCH
+            subprocess.run([nvcc_path(), "-O3", "-gencode", ARCH, "-o", exe + ".tmp", src], check=True,
+                           capture_output=True)
+            os.replace(exe + ".tmp", exe)
+        env = dict(os.environ, CUDA_VISIBLE_DEVICES=os.environ.get("CUDA_VISIBLE_DEVICES", str(dev_index)))
+        with ClockSampler(dev_index) as clk:
+            r = subprocess.run([exe], check=True, capture_output=True, text=True, env=env, timeout=120)
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+        d["clocks"] = clk.summary()
+        return d
+    except Exception as e:      # noqa: BLE001 (reported in the JSON line)
+        return {"error": f"{type(e).__name__}: {e}"[:200]}
 
 
 # ----------------------------------------------------------------- GPU arm
@@ -545,19 +591,23 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        rates = []
         t0 = time.perf_counter()
+        orc = OracleSample()
+        rates, times = [], []
         for k in range(args.warmup + args.steps):
-            r, procs, steps, _ = oracle_rate(n_walkers_per_proc=8, n_proj=4)
+            r, slowest, steps = orc.run(k)
             if k >= args.warmup:
                 rates.append(r)
+                times.append(slowest)
+        orc.close()
         v = statistics.mean(rates)
         line = {"impl": "reference", "metric": metric, "value": v, "unit": "walker-steps/s", "n_gpus": args.gpus,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * N_W * N_PROJ / v,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic", "config": workload,
-                "cpu_baseline": {"value": v, "unit": "walker-steps/s", "cores": procs, "kind": "oracle",
-                                 "sample": f"{procs} processes x 8 walkers x 4 hops per step"},
+                "step": "one oracle sample (not the GPU arm's 4096-walker step): " + orc.describe(),
+                "cpu_baseline": {"value": v, "unit": "walker-steps/s", "cores": orc.procs, "kind": "oracle",
+                                 "sample": orc.describe()},
                 "e2e": {"value": v, "unit": "walker-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
                 "wall_s": time.perf_counter() - t0}
         print(json.dumps(line))
@@ -569,13 +619,18 @@ def main():
         dist.init_process_group("nccl")
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        r, procs, steps, wall = oracle_rate()
-        cpu = {"value": r, "unit": "walker-steps/s", "cores": procs, "kind": "oracle",
-               "sample": f"{procs} processes x 48 walkers x {N_PROJ} hops (one interval, load-balanced), "
-                         f"{steps} walker-steps, {wall:.1f} s wall"}
+        t0 = time.perf_counter()
+        orc = OracleSample()
+        r, slowest, steps = orc.run(0)
+        orc.close()
+        cpu = {"value": r, "unit": "walker-steps/s", "cores": orc.procs, "kind": "oracle",
+               "sample": orc.describe() + f"; {time.perf_counter() - t0:.1f} s wall with process start-up"}
     res = run_gpu(args, rank, world)
     if rank == 0:
         peak = FP64_PEAK_GFLOPS
+        fp64 = measure_fp64_peak(int(os.environ.get("LOCAL_RANK", 0)))
+        measured = fp64.get("dfma_gflops")
+        mixed = res["mixed"]
         line = {
             "metric": metric, "value": res["value"], "unit": "walker-steps/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["step_ms"], "higher_is_better": True,
@@ -585,12 +640,15 @@ def main():
                          "unit": "GFLOP/s (FP64 operations x 2, functions at their FP64 instruction count)",
                          "frac": res["achieved"] / peak, "traffic": PROPAGATE_TRAFFIC_BYTES,
                          "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
-                         "peak_source": "nominal FP64 rate of the recipe table (no FP64 entry measured)",
+                         "peak_source": "nominal FP64 rate of the recipe table (the largest of the three FP64 "
+                                        "peaks here; MEASURED_PEAKS has no FP64 entry)",
                          "kernel_ms": res["prop_ms"], "fp64_ops_per_walker_step": res["slots"],
                          "fp64_pipe_busy_ncu": PROPAGATE_FP64_PIPE_BUSY,
-                         "peak_from_unit_counts": 148 * 2 * 2 * 2.032,
-                         "peak_from_unit_counts_note": "GFLOP/s: 148 SMs x 2 FP64 FMA per clock (ncu peak "
-                                                       "sustained) x 2 FLOP x 2.032 GHz"},
+                         "peak_unit_count": FP64_UNIT_COUNT_GFLOPS,
+                         "frac_vs_unit_count": res["achieved"] / FP64_UNIT_COUNT_GFLOPS,
+                         "peak_measured_dfma": measured,
+                         "frac_vs_measured_dfma": res["achieved"] / measured if measured else None,
+                         "fp64_peak_run": fp64},
             "conventional": {"value": res["conv_rate"], "unit": "walker-steps/s", "tau": res["tau"],
                              "moves_mean_max": res["conv_moves"],
                              "lb_speedup": res["value"] / res["conv_rate"]},
@@ -598,7 +656,12 @@ def main():
             "cpu_baseline": cpu,
             "e2e": {"value": res["e2e"], "unit": "walker-steps/s", "h2d_bytes_per_step": res["h2d"],
                     "d2h_bytes_per_step": res["d2h"]},
-            "mixed": dict(res["mixed"], speedup_vs_fp64=res["mixed"]["value"] / res["value"]) if res["mixed"] else None,
+            "mixed": dict(mixed, speedup_vs_fp64=mixed["value"] / res["value"]) if mixed else None,
+            "fp64_51200": mixed["n_w_51200"]["fp64_value"] if mixed else None,
+            "mixed_51200": mixed["n_w_51200"]["value"] if mixed else None,
+            "mixed_speedup_51200": mixed["n_w_51200"]["speedup_vs_fp64"] if mixed else None,
+            "mixed_bias_mHa": mixed["energy_bias_mHa"] if mixed else None,
+            "mixed_bias_err_mHa": mixed["energy_bias_err_mHa"] if mixed else None,
             "a_scan": res["a_scan"],
             "batch": res["batch"],
             "adjoint": res["adjoint"],

@@ -182,6 +182,19 @@ lrdmc_status lrdmc_branch(lrdmc_handle h);
  * (largest over block lengths 1, 2, 4, ... with >= 8 blocks; NaN if too few). */
 lrdmc_status lrdmc_energy(lrdmc_handle h, double* E, double* err);
 
+/* The estimator of lrdmc_energy over a caller-supplied branching history
+ * (Sec. II.A: Gbar_n^p-weighted mean of ebar_n; the same block-jackknife
+ * error), host arrays, no handle and no device work.
+ *   wbar, ebar  n mean weights (> 0, finite) and walker-averaged local
+ *               energies (finite) of consecutive branchings
+ *   p_gbar      factors of Gbar_n^p; n_equil  branchings discarded
+ *   E           out: the estimate (NaN if n <= n_equil)
+ *   err         out or NULL: the error bar (NaN with fewer than 16 kept branchings)
+ * LRDMC_ERR_ARG: n < 0, NULL arrays with n > 0, negative p_gbar or n_equil,
+ * a non-positive or non-finite wbar, a non-finite ebar. */
+lrdmc_status lrdmc_estimate(int n, const double* wbar, const double* ebar, int p_gbar, int n_equil, double* E,
+                            double* err);
+
 /* ------------------------------------------------------------ derivatives
  * Parameters differentiated by lrdmc_local_energy_grad, as one vector theta of
  * lrdmc_param_count = 5 n_nuc + 3 values: R (n_nuc x 3, bohr), j2_anti,
@@ -262,7 +275,13 @@ lrdmc_status lrdmc_clear_status(lrdmc_handle h);
  * created for the same system, trial function and parameters.  Because every
  * random number is keyed by (seed, walker slot, step, interval), a run resumed
  * from a checkpoint continues bit for bit like the uninterrupted run.
- * Returns LRDMC_ERR_ARG if the file does not match the handle's layout. */
+ * The file records the lattice spacing a, the node rule and a 64-bit FNV-1a
+ * fingerprint of the system and trial wavefunction (nuclei, potentials, basis,
+ * orbital coefficients, Jastrow parameters): the stored walkers' cached
+ * ratios, W and e_L belong to that Hamiltonian, so lrdmc_load returns
+ * LRDMC_ERR_ARG, and leaves the handle unchanged, for a file whose layout, a,
+ * node rule or fingerprint differs from the handle's, whose size disagrees
+ * with its header (a corrupt history length), or that is truncated. */
 lrdmc_status lrdmc_save(lrdmc_handle h, const char* path);
 lrdmc_status lrdmc_load(lrdmc_handle h, const char* path);
 
@@ -294,9 +313,9 @@ lrdmc_status lrdmc_reconfigure_indices(int n, const double* w, uint32_t xi32, in
 
 /* Allocation-free variant of lrdmc_reconfigure_indices (the paper has no
  * counterpart; this is a library convenience).  It is meant for callers that
- * cannot call cudaMalloc -- for example code running inside a CUDA graph that
- * is being captured, a host with a custom or exhausted device allocator, or an
- * embedding runtime that forbids allocation on its hot path.  Instead of a
+ * cannot call cudaMalloc -- for example a host whose device memory is managed
+ * by its own (or an exhausted) allocator, or an embedding runtime that forbids
+ * allocation on its hot path.  Instead of a
  * caller-provided scratch buffer it uses one fixed array in the library's
  * device memory, sized for LRDMC_NOALLOC_MAX_WALKERS walkers (about 2 MiB,
  * held on every GPU that loads the library until the process exits).
@@ -307,7 +326,10 @@ lrdmc_status lrdmc_reconfigure_indices(int n, const double* w, uint32_t xi32, in
  *     LRDMC_ERR_ARG.
  *   - The first call on a device looks up that device's copy of the array
  *     (a one-time set-up with that device current); make that first call
- *     before any stream capture.
+ *     before any stream capture.  The address is kept for the life of the
+ *     process: after cudaDeviceReset on a device (which unloads the library's
+ *     device code there) it is stale, so do not call this entry point on that
+ *     device again.
  *   - All calls share the one array and it keeps the last call's contents;
  *     the kernel overwrites every scratch word before reading it.  Calls that
  *     overlap on the GPU (e.g. on two streams at once) race on the array and
@@ -322,8 +344,9 @@ void lrdmc_philox4x32(uint64_t seed, const uint32_t ctr[4], uint32_t out[4]);
 
 /* Testing aid: the library's reduced-slot FP64 exp, reciprocal and reciprocal
  * square root (table-driven exponential after Tang 1989; hardware approximations
- * refined by two Newton steps) applied elementwise to n device doubles.  Any
- * output may be NULL.  Asynchronous on stream. */
+ * refined by one third-order step) applied elementwise to n device doubles.  Any
+ * output may be NULL.  Asynchronous on stream.  The first call on a device
+ * copies the 2 KB exponential table to it (synchronous, under a lock). */
 lrdmc_status lrdmc_fp64math(int n, const double* x, double* exp_out, double* rcp_out, double* rsqrt_out,
                             void* stream);
 

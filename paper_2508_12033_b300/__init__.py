@@ -7,9 +7,10 @@ The binding only marshals arguments; every step runs in the CUDA kernels of
 this package does not load the library; the first use does, and raises if the
 library is missing -- there is no CPU fallback.
 """
-from .binding import (CONVENTIONAL, LOAD_BALANCED, LrdmcError, Lrdmc, LrdmcBatch, extrapolate_a, load_library,
+from .binding import (CONVENTIONAL, LOAD_BALANCED, LrdmcError, Lrdmc, LrdmcBatch, estimate, extrapolate_a,
+                      load_library,
                       local_energy,
                       philox4x32, reconfigure_indices)
 
-__all__ = ["Lrdmc", "LrdmcBatch", "LrdmcError", "local_energy", "LOAD_BALANCED", "CONVENTIONAL", "extrapolate_a", "load_library",
+__all__ = ["Lrdmc", "LrdmcBatch", "LrdmcError", "local_energy", "LOAD_BALANCED", "CONVENTIONAL", "estimate", "extrapolate_a", "load_library",
            "philox4x32", "reconfigure_indices"]

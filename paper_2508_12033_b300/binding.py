@@ -85,6 +85,7 @@ def load_library():
         "lrdmc_interval_timing": [P, c_double_p],
         "lrdmc_load": [P, C.c_char_p],
         "lrdmc_stream": [P, C.POINTER(P)],
+        "lrdmc_estimate": [C.c_int, c_double_p, c_double_p, C.c_int, C.c_int, c_double_p, c_double_p],
         "lrdmc_extrapolate_a": [C.c_int, c_double_p, c_double_p, c_double_p, C.c_int, c_double_p, c_double_p,
                                 c_double_p],
         "lrdmc_param_count": [P, c_int_p],
@@ -567,6 +568,21 @@ def extrapolate_a(a, E, err, order=1):
     if r != 0:
         raise LrdmcError(r, "lrdmc_extrapolate_a: invalid points or order")
     return coef, cov, chi2.value
+
+
+def estimate(wbar, ebar, p_gbar=10, n_equil=0):
+    """The library's energy estimator (lrdmc_estimate) over a branching
+    history: returns (E, err)."""
+    lib = load_library()
+    wbar = np.ascontiguousarray(wbar, dtype=np.float64)
+    ebar = np.ascontiguousarray(ebar, dtype=np.float64)
+    if wbar.shape != ebar.shape or wbar.ndim != 1:
+        raise ValueError("wbar and ebar must be 1-D arrays of one length")
+    E, err = C.c_double(), C.c_double()
+    r = lib.lrdmc_estimate(len(wbar), _dptr(wbar), _dptr(ebar), int(p_gbar), int(n_equil), C.byref(E), C.byref(err))
+    if r != 0:
+        raise LrdmcError(r, "lrdmc_estimate: invalid history")
+    return E.value, err.value
 
 
 def philox4x32(seed, ctr):

@@ -10,13 +10,11 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "liblrdmc.so")
-PEAKS = os.path.join(PKG, "pipe_peaks")
 ARCH = "arch=compute_103a,code=sm_103a"
 
 
 def _sources():
-    out = [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC))
-           if f.endswith((".cu", ".cuh")) and f != "pipe_peaks.cu"]
+    out = [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC)) if f.endswith((".cu", ".cuh"))]
     out.append(os.path.join(INCLUDE, "lrdmc.h"))
     return out
 
@@ -51,10 +49,6 @@ def build(force: bool = False, verbose: bool = False) -> str:
             print(" ".join(cmd))
         subprocess.run(cmd, check=True)
         os.replace(LIB + ".tmp", LIB)
-    peaks_src = os.path.join(CSRC, "pipe_peaks.cu")
-    if force or not os.path.exists(PEAKS) or os.path.getmtime(PEAKS) < os.path.getmtime(peaks_src):
-        subprocess.run([nvcc_path(), "-O3", "-gencode", ARCH, "-o", PEAKS + ".tmp", peaks_src], check=True)
-        os.replace(PEAKS + ".tmp", PEAKS)
     return LIB
 
 

@@ -53,7 +53,7 @@ struct DevSys {
   const int* sh_bf;      // n_shell: first basis function
   const int* atom_sh;    // n_nuc + 1: shells are grouped by nucleus, atom I owns [atom_sh[I], atom_sh[I+1])
   const int* sh_ord;     // n_shell: shell indices, every non-p shell before every p shell
-  const double* exptab;  // 64: 2^(j/64) for the table-driven exponential
+  const double* exptab;  // EXP_TAB = 256 entries 2^(j/256) for the table-driven exponential
   const double* erftab;  // ERF_INT x ERF_NC: polynomials of erf(sqrt t)/sqrt t (fp64math.cuh)
   const double* exps;    // n_prim
   const double* coefs;   // n_prim

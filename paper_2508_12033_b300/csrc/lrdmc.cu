@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <atomic>
 #include <mutex>
+#include <new>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -370,6 +371,7 @@ struct lrdmc_s {
   std::vector<double> wbar, ebar, e0h, mmean;
   std::vector<int> mmax, surv;
   std::vector<uint32_t> stor;
+  std::vector<char> img;         // host copy of the device system image (kept current by set_params)
   int64_t launches = 0;
   std::string err;
 };
@@ -870,7 +872,8 @@ lrdmc_status lrdmc_create(const lrdmc_system* sys, const lrdmc_trial_wf* wf, con
   putf(P.i_f_coefs, wf->coefs, P.n_prim);
   putf(P.i_f_C, wf->C, (size_t)P.n_orb * P.n_bf);
   char* dsys = base + P.o_sys;
-  CK(h, cudaMemcpyAsync(dsys, img.data(), P.sys_bytes, cudaMemcpyHostToDevice, h->stream));
+  h->img = img;
+  CK(h, cudaMemcpyAsync(dsys, h->img.data(), P.sys_bytes, cudaMemcpyHostToDevice, h->stream));
   DevSys& S = h->S;
   S.n_nuc = P.n_nuc; S.n_shell = P.n_shell; S.n_prim = P.n_prim; S.n_bf = P.n_bf; S.n_orb = P.n_orb;
   S.n_up = P.n_up; S.n_dn = P.n_dn; S.n_e = P.n_e; S.n_max = P.n_max;
@@ -1084,6 +1087,16 @@ lrdmc_status lrdmc_energy(lrdmc_handle h, double* E, double* err) {
   return LRDMC_OK;
 }
 
+lrdmc_status lrdmc_estimate(int n, const double* wbar, const double* ebar, int p_gbar, int n_equil, double* E,
+                            double* err) {
+  if (n < 0 || (n > 0 && (!wbar || !ebar)) || p_gbar < 0 || n_equil < 0 || !E) return LRDMC_ERR_ARG;
+  for (int k = 0; k < n; ++k)
+    if (!(wbar[k] > 0.0) || !std::isfinite(wbar[k]) || !std::isfinite(ebar[k])) return LRDMC_ERR_ARG;
+  const std::vector<double> wb(wbar, wbar + n), eb(ebar, ebar + n);
+  *E = estimate(wb, eb, p_gbar, n_equil, err);
+  return LRDMC_OK;
+}
+
 lrdmc_status lrdmc_extrapolate_a(int n, const double* a, const double* E, const double* err, int order,
                                  double* coef, double* cov, double* chi2) {
   if (!a || !E || !err || !coef || order < 1 || order > 3 || n < order + 1) return LRDMC_ERR_ARG;
@@ -1215,7 +1228,7 @@ lrdmc_status lrdmc_clear_status(lrdmc_handle h) {
 }
 
 namespace {
-constexpr uint64_t CKPT_MAGIC = 0x4c52444d43434b31ull;   // "LRDMCCK1"
+constexpr uint64_t CKPT_MAGIC = 0x4c52444d43434b32ull;   // "LRDMCCK2"
 
 struct CkptHeader {
   uint64_t magic;
@@ -1223,7 +1236,27 @@ struct CkptHeader {
   uint64_t seed;
   double a, E0;
   uint32_t interval, last_kind;
+  int32_t node_rule, n_up;
+  uint64_t fingerprint;   // FNV-1a of the system image and the pair Jastrow parameters
 };
+// Bytes of one branching-history record in the file (wbar, ebar, E0, mean
+// moves, max moves, survivors, stored slots).
+constexpr size_t CKPT_HIST_BYTES = 4 * sizeof(double) + 2 * sizeof(int) + sizeof(uint32_t);
+
+uint64_t fnv1a(uint64_t h, const void* p, size_t n) {
+  const unsigned char* c = (const unsigned char*)p;
+  for (size_t k = 0; k < n; ++k) { h ^= c[k]; h *= 0x100000001b3ull; }
+  return h;
+}
+
+// Fingerprint of what the cached walker evaluations depend on besides a and
+// the node rule: nuclei, potentials, basis, orbitals and every Jastrow
+// parameter (the system image holds all but the pair Jastrow constants).
+uint64_t system_fingerprint(lrdmc_handle h) {
+  uint64_t f = fnv1a(0xcbf29ce484222325ull, h->img.data(), h->img.size());
+  const double j2[3] = {h->S.j2_anti, h->S.j2_par, h->S.j2_b};
+  return fnv1a(f, j2, sizeof j2);
+}
 }  // namespace
 
 lrdmc_status lrdmc_save(lrdmc_handle h, const char* path) {
@@ -1241,6 +1274,8 @@ lrdmc_status lrdmc_save(lrdmc_handle h, const char* path) {
   hd.c_stride = P.L.c_stride;
   hd.n_hist = (int32_t)h->wbar.size();
   hd.seed = h->prm.seed; hd.a = h->prm.a; hd.E0 = h->E0; hd.interval = h->interval; hd.last_kind = h->last_kind;
+  hd.node_rule = h->prm.node_rule; hd.n_up = P.n_up;
+  hd.fingerprint = system_fingerprint(h);
   FILE* f = fopen(path, "wb");
   if (!f) return fail(h, LRDMC_ERR_ARG, std::string("cannot open ") + path);
   bool ok = fwrite(&hd, sizeof hd, 1, f) == 1 && fwrite(st.data(), sizeof(double), st.size(), f) == st.size() &&
@@ -1264,18 +1299,47 @@ lrdmc_status lrdmc_load(lrdmc_handle h, const char* path) {
   if (!f) return fail(h, LRDMC_ERR_ARG, std::string("cannot open ") + path);
   CkptHeader hd{};
   bool ok = fread(&hd, sizeof hd, 1, f) == 1;
-  if (!ok || hd.magic != CKPT_MAGIC || hd.n_w != P.n_w || hd.n_e != P.n_e || hd.g_stride != P.L.g_stride ||
-      hd.c_stride != P.L.c_stride || hd.precision != P.precision || hd.n_hist < 0) {
+  if (!ok || hd.magic != CKPT_MAGIC || hd.n_w != P.n_w || hd.n_e != P.n_e || hd.n_up != P.n_up ||
+      hd.g_stride != P.L.g_stride || hd.c_stride != P.L.c_stride || hd.precision != P.precision ||
+      hd.n_hist < 0) {
     fclose(f);
-    return fail(h, LRDMC_ERR_ARG, "checkpoint does not match this handle");
+    return fail(h, LRDMC_ERR_ARG, "checkpoint does not match this handle's layout");
   }
-  std::vector<double> st((size_t)P.n_w * P.L.g_stride), cs((size_t)P.n_w * P.L.c_stride);
+  // the cached ratios, W and e_L of every walker belong to one Hamiltonian:
+  // refuse a checkpoint of another lattice spacing, node rule, system or
+  // trial function
+  if (memcmp(&hd.a, &h->prm.a, sizeof(double)) != 0 || hd.node_rule != h->prm.node_rule ||
+      hd.fingerprint != system_fingerprint(h)) {
+    fclose(f);
+    return fail(h, LRDMC_ERR_ARG, "checkpoint was written for another lattice spacing, node rule, system or "
+                                  "trial wavefunction");
+  }
+  const size_t nst = (size_t)P.n_w * P.L.g_stride, ncs = (size_t)P.n_w * P.L.c_stride;
+  const size_t m = (size_t)hd.n_hist;
+  {
+    // the history length must agree with the file's size before it sizes any buffer
+    long here = ftell(f);
+    if (here < 0 || fseek(f, 0, SEEK_END) != 0) { fclose(f); return fail(h, LRDMC_ERR_ARG, "checkpoint not seekable"); }
+    const long end = ftell(f);
+    if (end < here || fseek(f, here, SEEK_SET) != 0) { fclose(f); return fail(h, LRDMC_ERR_ARG, "checkpoint not seekable"); }
+    const size_t rest = (size_t)(end - here), need = sizeof(double) * (nst + ncs);
+    if (rest < need || (rest - need) != m * CKPT_HIST_BYTES) {
+      fclose(f);
+      return fail(h, LRDMC_ERR_ARG, "checkpoint size does not match its header");
+    }
+  }
+  std::vector<double> st, cs, wb, eb, e0, mm;
+  std::vector<int> mx, sv;
+  std::vector<uint32_t> so;
+  try {
+    st.resize(nst); cs.resize(ncs);
+    wb.resize(m); eb.resize(m); e0.resize(m); mm.resize(m); mx.resize(m); sv.resize(m); so.resize(m);
+  } catch (const std::bad_alloc&) {
+    fclose(f);
+    return fail(h, LRDMC_ERR_ARG, "checkpoint too large for host memory");
+  }
   ok = fread(st.data(), sizeof(double), st.size(), f) == st.size() &&
        fread(cs.data(), sizeof(double), cs.size(), f) == cs.size();
-  const size_t m = (size_t)hd.n_hist;
-  std::vector<double> wb(m), eb(m), e0(m), mm(m);
-  std::vector<int> mx(m), sv(m);
-  std::vector<uint32_t> so(m);
   if (m) {
     ok = ok && fread(wb.data(), sizeof(double), m, f) == m && fread(eb.data(), sizeof(double), m, f) == m &&
          fread(e0.data(), sizeof(double), m, f) == m && fread(mm.data(), sizeof(double), m, f) == m &&
@@ -1390,21 +1454,50 @@ lrdmc_status lrdmc_reconfigure_indices_noalloc(int n, const double* w, uint32_t 
   return LRDMC_OK;
 }
 
+}  // extern "C"
+
+namespace {
+// Per-device constant table of a testing aid, built on the device's first
+// call.  The table pointer is published (under a lock) only after its copy
+// succeeded, so a failed set-up leaves no pointer to uninitialised memory and
+// the next call tries again.
+std::mutex g_tab_mutex;
+cudaError_t device_table(double* (&slot)[64], const std::vector<double>& host, double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_tab_mutex);
+  if (!slot[dev]) {
+    double* d = nullptr;
+    e = cudaMalloc(&d, sizeof(double) * host.size());
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpy(d, host.data(), sizeof(double) * host.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(d);
+      return e;
+    }
+    slot[dev] = d;
+  }
+  *out = slot[dev];
+  return cudaSuccess;
+}
+double* g_exp_tab[64] = {nullptr};
+double* g_erf_tab[64] = {nullptr};
+}  // namespace
+
+extern "C" {
+
 lrdmc_status lrdmc_fp64math(int n, const double* x, double* exp_out, double* rcp_out, double* rsqrt_out,
                             void* stream) {
   if (n < 0 || (n > 0 && !x)) return LRDMC_ERR_ARG;
   if (n == 0) return LRDMC_OK;
-  static double* d_tab[64] = {nullptr};
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return LRDMC_ERR_CUDA;
-  if (!d_tab[dev]) {
-    double tab[EXP_TAB];
-    for (int j = 0; j < EXP_TAB; ++j) tab[j] = (double)exp2l((long double)j / EXP_TAB);
-    if (cudaMalloc(&d_tab[dev], sizeof tab) != cudaSuccess) return LRDMC_ERR_CUDA;
-    if (cudaMemcpy(d_tab[dev], tab, sizeof tab, cudaMemcpyHostToDevice) != cudaSuccess) return LRDMC_ERR_CUDA;
-  }
+  std::vector<double> tab(EXP_TAB);
+  for (int j = 0; j < EXP_TAB; ++j) tab[j] = (double)exp2l((long double)j / EXP_TAB);
+  double* d_tab = nullptr;
+  if (device_table(g_exp_tab, tab, &d_tab) != cudaSuccess) return LRDMC_ERR_CUDA;
   k_fp64math<<<std::min(1024, (n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(n, x, exp_out, rcp_out, rsqrt_out,
-                                                                                d_tab[dev]);
+                                                                                d_tab);
   return cudaGetLastError() == cudaSuccess ? LRDMC_OK : LRDMC_ERR_CUDA;
 }
 
@@ -1418,19 +1511,13 @@ lrdmc_status lrdmc_erf_ratio_table(double* out, int* n_int, int* n_coef) {
 lrdmc_status lrdmc_erf_over_r(int n, const double* s, double r_c, double* out, void* stream) {
   if (n < 0 || (n > 0 && (!s || !out)) || !(r_c > 0.0)) return LRDMC_ERR_ARG;
   if (n == 0) return LRDMC_OK;
-  static double* d_tab[64] = {nullptr};
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return LRDMC_ERR_CUDA;
-  if (!d_tab[dev]) {
-    std::vector<double> tab(ERF_INT * ERF_NC);
-    erf_ratio_table(tab.data());
-    if (cudaMalloc(&d_tab[dev], sizeof(double) * tab.size()) != cudaSuccess) return LRDMC_ERR_CUDA;
-    if (cudaMemcpy(d_tab[dev], tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice) != cudaSuccess)
-      return LRDMC_ERR_CUDA;
-  }
+  std::vector<double> tab(ERF_INT * ERF_NC);
+  erf_ratio_table(tab.data());
+  double* d_tab = nullptr;
+  if (device_table(g_erf_tab, tab, &d_tab) != cudaSuccess) return LRDMC_ERR_CUDA;
   const double irc2 = (double)(1.0L / ((long double)r_c * r_c));
   k_erf_over_r<<<std::min(1024, (n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(n, s, 1.0 / r_c, irc2, out,
-                                                                                  d_tab[dev]);
+                                                                                  d_tab);
   return cudaGetLastError() == cudaSuccess ? LRDMC_OK : LRDMC_ERR_CUDA;
 }
 
@@ -1479,6 +1566,12 @@ lrdmc_status lrdmc_set_params(lrdmc_handle h, const double* theta) {
   for (int k = 0; k < 3 * nn; ++k) fR[k] = (float)h->hR[k];
   for (int I = 0; I < nn; ++I) { fA[I] = (float)h->hA[I]; fB[I] = (float)h->hB[I]; }
   char* dsys = (char*)h->ws + P.o_sys;
+  memcpy(h->img.data() + P.i_R, h->hR.data(), sizeof(double) * 3 * nn);
+  memcpy(h->img.data() + P.i_j1A, h->hA.data(), sizeof(double) * nn);
+  memcpy(h->img.data() + P.i_j1B, h->hB.data(), sizeof(double) * nn);
+  memcpy(h->img.data() + P.i_f_R, fR.data(), sizeof(float) * 3 * nn);
+  memcpy(h->img.data() + P.i_f_j1A, fA.data(), sizeof(float) * nn);
+  memcpy(h->img.data() + P.i_f_j1B, fB.data(), sizeof(float) * nn);
   CK(h, cudaMemcpyAsync(dsys + P.i_R, h->hR.data(), sizeof(double) * 3 * nn, cudaMemcpyHostToDevice, h->stream));
   CK(h, cudaMemcpyAsync(dsys + P.i_j1A, h->hA.data(), sizeof(double) * nn, cudaMemcpyHostToDevice, h->stream));
   CK(h, cudaMemcpyAsync(dsys + P.i_j1B, h->hB.data(), sizeof(double) * nn, cudaMemcpyHostToDevice, h->stream));

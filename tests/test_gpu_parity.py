@@ -323,6 +323,48 @@ def test_checkpoint_resume_is_bit_identical(tmp_path, precision):
         c.load(path)
 
 
+def test_checkpoint_refuses_another_hamiltonian(tmp_path):
+    """A checkpoint's cached ratios, W and e_L belong to one lattice
+    Hamiltonian: loading it into a handle of another a, node rule, trial
+    function or system of the same shape is refused, as is a file whose
+    history length disagrees with its size; the refused handle keeps its own
+    walkers."""
+    P = lib_or_skip()
+    s = W.h2_sto3g()
+    x0 = W.initial_walkers(s, 64, seed=5)
+    a = P.Lrdmc(s, x0, 0.2, seed=3)
+    a.propagate(P.LOAD_BALANCED, n_proj=6)
+    a.branch()
+    path = str(tmp_path / "ck.bin")
+    a.save(path)
+    x1 = W.initial_walkers(s, 64, seed=99)
+    s2 = W.h2_sto3g()
+    s2.j2_anti = 0.6                  # another pair Jastrow: same shape, other wavefunction
+    s3 = W.h2_sto3g()
+    s3.R = s3.R * 1.01                # another geometry
+    for kw, sysk in ((dict(a=0.25), s), (dict(node_rule=2), s), ({}, s2), ({}, s3)):
+        b = P.Lrdmc(sysk, x1, kw.get("a", 0.2), seed=3, node_rule=kw.get("node_rule", 0))
+        before = b.get_walkers()["x"]
+        with pytest.raises(P.LrdmcError):
+            b.load(path)
+        np.testing.assert_array_equal(b.get_walkers()["x"], before)
+        b.close()
+    # a corrupt history length (header field) is refused before it sizes anything
+    raw = bytearray(open(path, "rb").read())
+    import struct
+    struct.pack_into("<i", raw, 8 + 4 * 4, 2 ** 30)     # n_hist
+    bad = tmp_path / "bad.bin"
+    bad.write_bytes(bytes(raw))
+    b = P.Lrdmc(s, x1, 0.2, seed=3)
+    with pytest.raises(P.LrdmcError):
+        b.load(str(bad))
+    (tmp_path / "short.bin").write_bytes(bytes(raw[: len(raw) // 2]))
+    with pytest.raises(P.LrdmcError):
+        b.load(str(tmp_path / "short.bin"))
+    b.load(path)                       # the matching file still loads
+    np.testing.assert_array_equal(b.get_walkers()["x"], a.get_walkers()["x"])
+
+
 @pytest.mark.parametrize("name,sysf,n_w,kind", [("h2", W.h2_sto3g, 64, 1), ("wm", W.water_methane, 32, 1),
                                                  ("wm", W.water_methane, 32, 0)])
 def test_randomised_lattice_interval_matches_oracle(name, sysf, n_w, kind):
@@ -387,3 +429,24 @@ def test_randomised_lattice_exact_hydrogen_and_refusal_in_mixed():
     with pytest.raises(P.LrdmcError) as e:
         lm.propagate(P.LOAD_BALANCED, n_proj=2, rotate=True)
     assert e.value.status == 7
+
+
+def test_energy_error_bar_matches_oracle_on_a_gpu_history():
+    """lrdmc_energy's E and error bar against the oracle's estimator
+    (oracle.estimator.energy / energy_error, Sec. II.A) fed the branching
+    history the GPU run itself recorded: equal to 1e-12 relative."""
+    from oracle import estimator as OE
+    P = lib_or_skip()
+    s = W.h2_sto3g()
+    lr = P.Lrdmc(s, W.initial_walkers(s, 128, seed=8), 0.2, seed=4, p_gbar=5, n_equil=4)
+    for _ in range(40):
+        lr.propagate(P.LOAD_BALANCED, n_proj=10)
+        lr.branch()
+    h = lr.history()
+    E, err = lr.energy()
+    Eo = OE.energy(h["wbar"], h["ebar"], 5, 4)
+    erro = OE.energy_error(h["wbar"], h["ebar"], 5, 4)
+    assert np.isfinite(err) and err > 0
+    assert abs(E - Eo) <= 1e-12 * max(1.0, abs(Eo))
+    assert abs(err - erro) <= 1e-12 * max(1.0, abs(erro))
+    lr.close()

@@ -158,3 +158,37 @@ def test_screened_potential_table_matches_erf(lib):
     ref = np.array([2 / math.sqrt(math.pi) if x == 0 else math.erf(math.sqrt(x)) / math.sqrt(x) for x in t])
     assert np.max(np.abs(p - ref) / ref) < 2e-15
     assert math.erf(math.sqrt((ni - 1) / 2)) == 1.0 and ni == 73
+
+
+def test_estimator_matches_oracle_on_the_same_history(lib):
+    """The library's energy estimator (lrdmc_estimate, the code behind
+    lrdmc_energy) and the oracle's (Sec. II.A: Gbar_n^p-weighted mean, block
+    jackknife error) on identical branching histories: equal E and error to
+    1e-12 relative, NaN in the same cases (no kept branchings; fewer than 16
+    for the error)."""
+    import paper_2508_12033_b300 as P
+    from oracle import estimator as OE
+    rng = np.random.default_rng(77)
+    for n in (0, 1, 5, 15, 16, 17, 40, 100, 257):
+        for p in (0, 1, 10):
+            for n_eq in (0, 3, 20):
+                wbar = rng.lognormal(0.0, 0.05, n)
+                ebar = -1.17 + 0.01 * rng.standard_normal(n) + 0.002 * np.sin(np.arange(n) / 7.0)
+                E, err = P.estimate(wbar, ebar, p, n_eq)
+                Eo = OE.energy(wbar, ebar, p, n_eq)
+                erro = OE.energy_error(wbar, ebar, p, n_eq)
+                for got, want in ((E, Eo), (err, erro)):
+                    if np.isnan(want):
+                        assert np.isnan(got), (n, p, n_eq)
+                    else:
+                        assert abs(got - want) <= 1e-12 * max(1.0, abs(want)), (n, p, n_eq, got, want)
+
+
+def test_estimator_rejects_invalid_histories(lib):
+    import paper_2508_12033_b300 as P
+    with pytest.raises(P.LrdmcError):
+        P.estimate([1.0, 0.0], [1.0, 2.0])          # a zero mean weight
+    with pytest.raises(P.LrdmcError):
+        P.estimate([1.0, 1.0], [1.0, np.nan])       # a non-finite energy
+    with pytest.raises(P.LrdmcError):
+        P.estimate([1.0], [1.0], p_gbar=-1)

@@ -2,8 +2,9 @@
 the regular one.
 
 lrdmc_reconfigure_indices_noalloc exists for callers that cannot allocate
-device memory when they call the library (graph capture in progress, a custom
-or exhausted allocator, an embedding runtime that forbids allocation).  It
+device memory when they call the library (device memory held by the host's
+own or an exhausted allocator, an embedding runtime that forbids allocation
+on its hot path).  It
 uses a fixed device array inside the library instead of caller scratch, so
 this test calls both entry points through the C ABI on the same weights, twice
 in a row with different sizes (the shared array keeps the previous call's
@@ -67,3 +68,34 @@ def test_noalloc_rejects_sizes_beyond_its_array():
     src = torch.empty(4, dtype=torch.int32, device="cuda")
     assert f((1 << 18) + 1, w.data_ptr(), 0, src.data_ptr(), None, None) == 7    # LRDMC_ERR_UNSUPPORTED
     assert f(0, w.data_ptr(), 0, src.data_ptr(), None, None) == 1                 # LRDMC_ERR_ARG
+
+
+def test_noalloc_refuses_invalid_weights_like_the_regular_entry_point():
+    """A NaN weight: both entry points report status word 0 = 1 (invalid
+    weights) and leave the source indices untouched."""
+    import torch
+    lib = _lib()
+    f = lib.lrdmc_reconfigure_indices_noalloc
+    f.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
+                  ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    stream = torch.cuda.current_stream()
+    n = 777
+    w = torch.ones(n, dtype=torch.float64, device="cuda")
+    w[100] = float("nan")
+    src_a = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+    st_a = torch.full((2,), -7, dtype=torch.int32, device="cuda")
+    assert f(n, w.data_ptr(), 12345, src_a.data_ptr(), st_a.data_ptr(), stream.cuda_stream) == 0
+    nb = lib.lrdmc_reconfigure_scratch_bytes(n)
+    scratch = torch.empty(nb + 256, dtype=torch.uint8, device="cuda")
+    sp = (scratch.data_ptr() + 255) // 256 * 256
+    src_b = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+    st_b = torch.full((2,), -9, dtype=torch.int32, device="cuda")
+    assert lib.lrdmc_reconfigure_indices(n, ctypes.c_void_p(w.data_ptr()), 12345,
+                                         ctypes.c_void_p(src_b.data_ptr()), ctypes.c_void_p(sp),
+                                         ctypes.c_size_t(nb), ctypes.c_void_p(st_b.data_ptr()),
+                                         ctypes.c_void_p(stream.cuda_stream)) == 0
+    torch.cuda.synchronize()
+    assert int(st_a[0]) == 1 and int(st_b[0]) == 1
+    assert torch.equal(st_a, st_b)
+    assert bool((src_a == -7).all()) and bool((src_b == -7).all())
