@@ -41,8 +41,8 @@ FP64_UNIT_COUNT_GFLOPS = 148 * 2 * 2 * 2.032
 # FP64 pipe busy fraction, from one ncu capture of the propagate kernel
 # (second launch of `bench.py --steps 2 --warmup 1` with every extra section
 # off); None when the kernel has changed since that capture
-PROPAGATE_TRAFFIC_BYTES = 1.176977e9 + 0.652905e9
-PROPAGATE_FP64_PIPE_BUSY = 0.819
+PROPAGATE_TRAFFIC_BYTES = None
+PROPAGATE_FP64_PIPE_BUSY = None
 # walkers per host process in the oracle sample (cpu_baseline and the
 # reference arm): one warm-up interval, then one timed 20-hop interval
 ORACLE_WALKERS_PER_PROC = 8
@@ -69,16 +69,21 @@ def algorithmic_ops_per_walker_step(n_e, n_nuc, n_bf, n_prim, n_sig, n_s_shell, 
     m's pair and nucleus terms with derivatives
     and the partner electrons' swapped terms (Pade + 14 per partner, 14 per
     swap), determinant derivatives of m's block (4 n_sig^2), basis values at
-    m's six hops (exponential + 2 per primitive, 1 / 4 per s / p shell) and
-    their Jastrow terms (Pade value + 3 per partner), the block's hop
+    m's six hops (below) and their Jastrow terms (Pade value + 3 per partner), the block's hop
     determinant ratios from cached basis values (6 n_sig n_bf), the swapped
     pair terms of the other hops (2 each), every hop's exponential (+3) and the
-    assembly (20 per electron)."""
+    assembly (20 per electron).  The basis values at m's six hops factor per
+    Gaussian primitive into exp(-z (d^2 + a^2)) and, per hop axis,
+    exp(-2 z a |d_k|) and its reciprocal (4 exponentials, 3 reciprocals and
+    18 other operations per primitive), plus the 18 Cartesian factors
+    (2 operations each) of every p shell."""
+    del n_s_shell
     per = n_e - 1 + n_nuc
     move = (n_prim * (OP_EXP + 10) + 5 * n_bf * n_sig + 2 * n_sig * n_sig + n_sig * n_bf
             + n_nuc * (OP_ERF + 8))
+    hop_basis = n_prim * (OP_EXP + 3 + 3 * (OP_EXP + OP_RCP + 5)) + 18 * 2 * n_p_shell
     evaluation = (per * (OP_PADE + 14) + (n_e - 1) * 14 + 4 * n_sig * n_sig
-                  + 6 * (n_prim * (OP_EXP + 2) + n_s_shell + 4 * n_p_shell) + 6 * per * (OP_PADE_VALUE + 3)
+                  + hop_basis + 6 * per * (OP_PADE_VALUE + 3)
                   + 6 * n_sig * n_bf + 6 * (n_e - 1) * 2 + 6 * n_e * (OP_EXP + 3) + 20 * n_e)
     return move + evaluation
 

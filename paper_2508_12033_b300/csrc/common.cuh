@@ -38,6 +38,7 @@ enum Scalar : int {
 // System and trial-wavefunction tables in device memory (read-only).
 struct DevSys {
   int n_nuc, n_shell, n_prim, n_bf, n_orb, n_up, n_dn, n_e, n_max;
+  int n_shell_np;         // shells that are not p shells (sh_ord lists them first)
   const double* R;       // n_nuc x 3
   const double* Z;       // n_nuc
   const double* rc;      // n_nuc

@@ -850,6 +850,7 @@ lrdmc_status lrdmc_create(const lrdmc_system* sys, const lrdmc_trial_wf* wf, con
     std::vector<int> ord;
     for (int k = 0; k < P.n_shell; ++k)
       if (r_l[k] != 1) ord.push_back(k);
+    h->S.n_shell_np = (int)ord.size();
     for (int k = 0; k < P.n_shell; ++k)
       if (r_l[k] == 1) ord.push_back(k);
     puti(P.i_ord, ord.data(), ord.size());

@@ -803,29 +803,79 @@ __device__ EvalOut eval_incr(const DevSys& S, const Layout& L, const double* __r
   det_derivs(L, gblk, sm, b0, b1, lane);
   __threadfence_block();
   __syncwarp();
-  // (D) basis values at m's six hops, one (shell, hop) per lane with the
-  // shells in kind order (a warp pass mostly meets one kind), and m's Jastrow
-  // pair / one-body terms, one (hop, partner) per lane
-  for (int o = lane; o < 6 * S.n_shell; o += WARP) {
-    const int k = o / 6, d = o - 6 * k, sh = __ldg(S.sh_ord + k), ax = d >> 1;
-    const double sa = (d & 1) ? -a : a;
-    const int I = __ldg(S.sh_atom + sh);
-    const double* gg = geo + (m * nn + I) * 4;
-    const double s = fma(sa + sa, gg[1 + ax], gg[0]);
-    const int l = __ldg(S.sh_l + sh), np = __ldg(S.sh_nprim + sh), off = __ldg(S.sh_off + sh), bf = __ldg(S.sh_bf + sh);
-    const double arg = l == -1 ? s * rsqrt_nr(s) : s;
-    double rad = 0.0;
-    for (int q = 0; q < np; ++q) rad = fma(__ldg(S.coefs + off + q), exp_tab(-__ldg(S.exps + off + q) * arg, T), rad);
-    const int p = 6 * m + d;
-    if (l != 1) {
-      scr.chi[(size_t)bf * P + p] = rad;
-    } else {
-      for (int k = 0; k < 3; ++k) {
-        const double dk = ROT ? fma(sa, V[3 * ax + k], x[3 * m + k] - __ldg(S.R + 3 * I + k))
-                              : gg[1 + k] + (k == ax ? sa : 0.0);
-        scr.chi[(size_t)(bf + k) * P + p] = dk * rad;
+  // (D) basis values at m's six hops.  A Gaussian primitive factors over the
+  // hop: with g = gg[1 + k] the component of r_m - R along hop versor k,
+  // |r_m +- a v_k - R|^2 = (|r_m - R|^2 + a^2) +- 2 a g, so
+  // exp(-z |r' - R|^2) = E0 t^(+-1), E0 = exp(-z (|r_m - R|^2 + a^2)),
+  // t = exp(-2 z a |g|) <= 1: the hop away from the nucleus takes E0 t, the
+  // hop towards it E0 / t.  One lane per shell; a primitive costs 4
+  // exponentials and 3 reciprocals instead of 6 exponentials.  The radial
+  // values of p shells go to the per-hop scratch (free until the Jastrow pass
+  // below) and their Cartesian factors are applied in a second, uniform pass
+  // over (p shell, component, hop).  Slater 1s shells (not separable) evaluate
+  // their six hops directly, as does a hop towards a nucleus more than
+  // 650 / (2 z a) bohr away (t would underflow).
+  {
+    double* radp = tmp;   // [n_shell][6]
+    for (int sh = lane; sh < S.n_shell; sh += WARP) {
+      const int I = __ldg(S.sh_atom + sh);
+      const double* gg = geo + (m * nn + I) * 4;
+      const int l = __ldg(S.sh_l + sh), np = __ldg(S.sh_nprim + sh), off = __ldg(S.sh_off + sh),
+                bf = __ldg(S.sh_bf + sh);
+      double rad[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+      if (l == -1) {
+        for (int d = 0; d < 6; ++d) {
+          const double sa = (d & 1) ? -a : a;
+          const double s = fma(sa + sa, gg[1 + (d >> 1)], gg[0]);
+          const double r = s * rsqrt_nr(s);
+          for (int q = 0; q < np; ++q)
+            rad[d] = fma(__ldg(S.coefs + off + q), exp_tab(-__ldg(S.exps + off + q) * r, T), rad[d]);
+        }
+      } else {
+        const double g3[3] = {gg[1], gg[2], gg[3]};
+        for (int q = 0; q < np; ++q) {
+          const double z = __ldg(S.exps + off + q);
+          const double e0 = __ldg(S.coefs + off + q) * exp_tab(-z * gg[0], T);
+          const double tza = -(a + a) * z;
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const double x = tza * fabs(g3[k]);
+            const double t = exp_tab(x, T);
+            const double away = e0 * t;
+            double toward;
+            // |x| < 650 and g >= 0 are tested on the integer images (no FP64 compare)
+            if ((__double_as_longlong(x) & 0x7fffffffffffffffll) < 0x4084500000000000ll) {
+              toward = e0 * rcp_nr(t);
+            } else {
+              toward = __ldg(S.coefs + off + q) * exp_tab(-z * fma(-(a + a), fabs(g3[k]), gg[0]), T);
+            }
+            // hop 2k moves by +a along v_k, hop 2k + 1 by -a (g = -0 counts as
+            // negative: both hops then take e0)
+            const bool pos = __double_as_longlong(g3[k]) >= 0;
+            rad[2 * k] += pos ? away : toward;
+            rad[2 * k + 1] += pos ? toward : away;
+          }
+        }
+      }
+      if (l == 1) {
+        for (int d = 0; d < 6; ++d) radp[6 * sh + d] = rad[d];
+      } else {
+        for (int d = 0; d < 6; ++d) scr.chi[(size_t)bf * P + 6 * m + d] = rad[d];
       }
     }
+    __syncwarp();
+    const int n_pt = 18 * (S.n_shell - S.n_shell_np);
+    for (int o = lane; o < n_pt; o += WARP) {
+      const int kk = o / 18, r = o - 18 * kk, k = r / 6, d = r - 6 * k, ax = d >> 1;
+      const int sh = __ldg(S.sh_ord + S.n_shell_np + kk);
+      const int I = __ldg(S.sh_atom + sh), bf = __ldg(S.sh_bf + sh);
+      const double sa = (d & 1) ? -a : a;
+      const double* gg = geo + (m * nn + I) * 4;
+      const double dk = ROT ? fma(sa, V[3 * ax + k], x[3 * m + k] - __ldg(S.R + 3 * I + k))
+                            : gg[1 + k] + (k == ax ? sa : 0.0);
+      scr.chi[(size_t)(bf + k) * P + 6 * m + d] = dk * radp[6 * sh + d];
+    }
+    __syncwarp();
   }
   for (int o = lane; o < 6 * per; o += WARP) {
     const int d = o / per, t = o - d * per, ax = d >> 1;
