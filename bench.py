@@ -561,6 +561,25 @@ def run_mixed(args, P, s, x0, lr64, flush, rank):
     lf = P.Lrdmc(s, xb, A, seed=SEED + rank, reinv_period=100, p_gbar=10)
     ms_big64 = time_lb_intervals(lf, P, flush, max(2, args.steps // 3), 2)
     lf.close()
+    # the FP32 orbital contractions on the tensor cores: TF32, BF16 and split
+    # TF32 (precision 2, 3, 4), speed at both sizes and the same correlated bias
+    tc = {}
+    for prec, name in ((2, "tf32"), (3, "bf16"), (4, "split_tf32")):
+        lt = P.Lrdmc(s, x0, A, seed=SEED + rank, reinv_period=50, p_gbar=10, precision=prec)
+        ms_t = time_lb_intervals(lt, P, flush, max(2, args.steps // 2), 2)
+        _, evt, _ = lt.eval_configs(x)
+        torch.cuda.synchronize()
+        dt = evt.cpu().numpy()[:, 3] - ev64[:, 3]
+        lt.close()
+        lt = P.Lrdmc(s, xb, A, seed=SEED + rank, reinv_period=50, p_gbar=10, precision=prec)
+        ms_tb = time_lb_intervals(lt, P, flush, max(2, args.steps // 3), 2)
+        lt.close()
+        tc[name] = {"precision": prec, "value_4096": N_W * N_PROJ / (ms_t / 1e3),
+                    "value_51200": big * N_PROJ / (ms_tb / 1e3), "speedup_vs_fp64_51200": ms_big64 / ms_tb,
+                    "speedup_vs_mixed_fp32_51200": ms_big / ms_tb,
+                    "energy_bias_mHa": 1e3 * float(np.sum(f * dt) / np.sum(f)),
+                    "energy_bias_err_mHa": 1e3 * float(np.std(dt) * np.sqrt(np.sum(f * f)) / np.sum(f)),
+                    "max_abs_eL_diff_Ha": float(np.max(np.abs(dt)))}
     return {"value": N_W * N_PROJ / (ms / 1e3), "unit": "walker-steps/s", "ms_per_step": ms,
             "n_w_51200": {"value": big * N_PROJ / (ms_big / 1e3), "ms_per_step": ms_big,
                           "fp64_value": big * N_PROJ / (ms_big64 / 1e3), "fp64_ms_per_step": ms_big64,
@@ -568,7 +587,8 @@ def run_mixed(args, P, s, x0, lr64, flush, rank):
             "energy_bias_mHa": 1e3 * bias, "energy_bias_err_mHa": 1e3 * err,
             "bias_sample": f"{N_W} equilibrated FP64 configurations, weights 1/(W - E0)",
             "max_abs_eL_diff_Ha": float(np.max(np.abs(d))),
-            "precision": "FP32 hop ratios / basis / Jastrow; FP64 A rows, B, Sherman-Morrison, accumulators"}
+            "precision": "FP32 hop ratios / basis / Jastrow; FP64 A rows, B, Sherman-Morrison, accumulators",
+            "tensor_core": tc}
 
 
 def main():
@@ -667,6 +687,9 @@ def main():
             "mixed_speedup_51200": mixed["n_w_51200"]["speedup_vs_fp64"] if mixed else None,
             "mixed_bias_mHa": mixed["energy_bias_mHa"] if mixed else None,
             "mixed_bias_err_mHa": mixed["energy_bias_err_mHa"] if mixed else None,
+            "tensor_core_51200": {k: {"value": v["value_51200"], "bias_mHa": v["energy_bias_mHa"],
+                                      "bias_err_mHa": v["energy_bias_err_mHa"]}
+                                  for k, v in mixed["tensor_core"].items()} if mixed else None,
             "a_scan": res["a_scan"],
             "batch": res["batch"],
             "adjoint": res["adjoint"],

@@ -130,7 +130,15 @@ typedef struct {
  *                positions, orbital values (rows of A), B = A^-1 with its
  *                Sherman-Morrison updates and Gauss-Jordan re-inversion every
  *                reinv_period hops, determinant derivatives, weights and the
- *                b_bar / W / e_L accumulators                                  */
+ *                b_bar / W / e_L accumulators; 2 and 3 = mixed with the two
+ *                FP32 orbital contractions against the MO coefficients (the
+ *                moved electron's gradient/Laplacian rows and the orbital
+ *                differences of its six hops, rows x N_bf x N_orb) on the tensor
+ *                cores: warp-level mma.sync with TF32 (2) or BF16 (3) operands
+ *                and FP32 accumulation (north star, precision direction); 4 =
+ *                as 2 with each FP32 operand split into two TF32 parts and
+ *                three MMAs per product (hi*hi + hi*lo + lo*hi), close to
+ *                FP32 accuracy on the tensor cores                            */
 typedef struct {
     double a;
     int n_w;

@@ -134,7 +134,11 @@ bool make_plan(const lrdmc_system* sys, const lrdmc_trial_wf* wf, const lrdmc_pa
       prm->node_rule < -1 || prm->node_rule > 2 || prm->p_gbar < 0 || prm->n_equil < 0) {
     P.err = "bad run parameters"; return false;
   }
-  if (prm->precision != 0 && prm->precision != 1) { P.err = "precision must be 0 (FP64) or 1 (mixed)"; return false; }
+  if (prm->precision < 0 || prm->precision > 4) {
+    P.err = "precision must be 0 (FP64), 1 (mixed), 2 (mixed, TF32 tensor cores), 3 (mixed, BF16 tensor cores) "
+            "or 4 (mixed, split-TF32 tensor cores)";
+    return false;
+  }
   P.precision = prm->precision;
   P.n_nuc = sys->n_nuc;
   P.n_up = sys->n_up;
@@ -206,9 +210,12 @@ bool make_plan(const lrdmc_system* sys, const lrdmc_trial_wf* wf, const lrdmc_pa
   if (P.precision == 0 && (size_t)L.s_stride * sizeof(double) > GEO_GLOBAL_BYTES) fp64_layout(1);
   P.M = layout_mixed(L, P.n_nuc, P.n_prim);
   // a large mixed-precision system keeps its O(N^2) arrays in global memory
-  if (P.precision == 1 && (size_t)P.M.stride * sizeof(float) > GEO_GLOBAL_BYTES_MIXED)
+  if (P.precision != 0 && (size_t)P.M.stride * sizeof(float) > GEO_GLOBAL_BYTES_MIXED)
     P.M = layout_mixed(L, P.n_nuc, P.n_prim, 1);
-  if (P.precision == 1) L.c_stride = round_up((P.M.c_floats + 1) / 2, 16);
+  // precision 2 / 3 / 4: the FP32 orbital contractions on the tensor cores
+  // (TF32 / BF16 / three TF32 products of split operands)
+  P.M.tc = P.precision >= 2 ? P.precision - 1 : 0;
+  if (P.precision != 0) L.c_stride = round_up((P.M.c_floats + 1) / 2, 16);
   P.smem_per_warp = P.precision == 0 ? (size_t)L.s_stride * sizeof(double) : (size_t)P.M.stride * sizeof(float);
   if (P.smem_per_warp + EXP_TAB * sizeof(double) > 200 * 1024) { P.err = "system too large for the per-warp shared-memory layout"; return false; }
   // system image

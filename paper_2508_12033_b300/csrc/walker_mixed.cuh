@@ -33,6 +33,8 @@
 // cached values rather than recomputed.
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 #include "walker.cuh"
 
@@ -59,11 +61,16 @@ struct LayoutM {
   // configuration evaluation) at offsets g_* from that base, big_floats in all;
   // their shared-memory extents are then zero
   int glob, c_big, g_geo, g_rt1, g_pair, g_hcur, g_dph, big_floats;
+  // FP32 orbital contractions (basis rows x C^T): 0 FP32 FMA on the CUDA
+  // cores, 1 TF32 tensor-core MMA, 2 BF16 tensor-core MMA, 3 three TF32 MMAs
+  // per step on split operands (FP32 accumulation in all)
+  int tc;
 };
 
 __host__ __device__ inline LayoutM layout_mixed(const Layout& L, int n_nuc, int n_prim, int glob = 0) {
   LayoutM M;
   M.glob = glob;
+  M.tc = 0;
   const int ne = L.n_e, nbt = L.n_up * L.n_up + L.n_dn * L.n_dn, nm = L.n_max, nbf = L.n_bf, P = L.n_hop;
   const int per = ne - 1 + n_nuc;
   int o = 0;
@@ -274,6 +281,105 @@ __device__ __forceinline__ void shell_values_d(const DevSys& S, int s, const dou
   }
 }
 
+// ------------------------------------------------------------ tensor cores
+// Warp-level tensor-core form of the FP32 orbital contractions: D[r][k] =
+// sum_mu A(r, mu) C[k][mu] for rows r < nr and orbitals k < nk, with
+// A(r, mu) = a[r * rs + mu * ms] in shared memory and C the FP32 copy of the
+// MO coefficients (n_orb x n_bf, read through L1).  The rows go through the
+// 16-row M dimension of mma.sync, the orbitals through its 8-column N
+// dimension and the basis functions through K; rows, orbitals and basis
+// functions past the ends are zero operands.  tc = 1: m16n8k8 with both
+// operands rounded to TF32 (cvt.rna, 10 explicit mantissa bits); tc = 2:
+// m16n8k16 with BF16 operands (round to nearest even, 7 bits).  Accumulation
+// is FP32 in both.  tc = 3: each FP32 operand x is split into TF32 parts
+// hi = tf32(x), lo = tf32(x - hi) and the product formed as
+// lo_a hi_b + hi_a lo_b + hi_a hi_b (three m16n8k8 MMAs, the small terms
+// first; lo_a lo_b ~ 2^-22 |a b| is dropped), which restores close to FP32
+// accuracy on the tensor cores.  Fragment layouts (g = lane / 4, t = lane % 4):
+//   TF32 A: (g, t) (g + 8, t) (g, t + 4) (g + 8, t + 4); B: (k = t, n = g) (t + 4, g)
+//   BF16 A: pairs (g, 2t..2t+1) (g + 8, 2t..) (g, 2t+8..2t+9) (g + 8, 2t+8..);
+//        B: pairs (k = 2t..2t+1, n = g) (2t+8..2t+9, g), the lower k in the low half
+//   D (both): (g, 2t) (g, 2t + 1) (g + 8, 2t) (g + 8, 2t + 1)
+// store(r, k, v) receives every (r < nr, k < nk) result once.
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void mma_tf32(float& d0, float& d1, float& d2, float& d3, const uint32_t a[4],
+                                         const uint32_t b[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(d0), "+f"(d1), "+f"(d2), "+f"(d3)
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+template <class Store>
+__device__ __forceinline__ void tc_contract(int tc, const float* a, int rs, int ms, int nr, const float* __restrict__ Cf,
+                                            int nbf, int nk, int lane, Store store) {
+  const int g = lane >> 2, t = lane & 3;
+  auto A = [&](int r, int mu) { return (r < nr && mu < nbf) ? a[r * rs + mu * ms] : 0.f; };
+  auto B = [&](int k, int mu) { return (k < nk && mu < nbf) ? __ldg(Cf + (size_t)k * nbf + mu) : 0.f; };
+  for (int r0 = 0; r0 < nr; r0 += 16) {
+    for (int n0 = 0; n0 < nk; n0 += 8) {
+      float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
+      if (tc == 1) {
+        for (int k0 = 0; k0 < nbf; k0 += 8) {
+          const uint32_t av[4] = {to_tf32(A(r0 + g, k0 + t)), to_tf32(A(r0 + g + 8, k0 + t)),
+                                  to_tf32(A(r0 + g, k0 + t + 4)), to_tf32(A(r0 + g + 8, k0 + t + 4))};
+          const uint32_t bv[2] = {to_tf32(B(n0 + g, k0 + t)), to_tf32(B(n0 + g, k0 + t + 4))};
+          mma_tf32(d0, d1, d2, d3, av, bv);
+        }
+      } else if (tc == 3) {
+        for (int k0 = 0; k0 < nbf; k0 += 8) {
+          const float af[4] = {A(r0 + g, k0 + t), A(r0 + g + 8, k0 + t), A(r0 + g, k0 + t + 4),
+                               A(r0 + g + 8, k0 + t + 4)};
+          const float bf[2] = {B(n0 + g, k0 + t), B(n0 + g, k0 + t + 4)};
+          uint32_t ah[4], al[4], bh[2], bl[2];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            ah[j] = to_tf32(af[j]);
+            al[j] = to_tf32(af[j] - __uint_as_float(ah[j]));
+          }
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            bh[j] = to_tf32(bf[j]);
+            bl[j] = to_tf32(bf[j] - __uint_as_float(bh[j]));
+          }
+          mma_tf32(d0, d1, d2, d3, al, bh);
+          mma_tf32(d0, d1, d2, d3, ah, bl);
+          mma_tf32(d0, d1, d2, d3, ah, bh);
+        }
+      } else {
+        for (int k0 = 0; k0 < nbf; k0 += 16) {
+          const int c0 = k0 + 2 * t, c1 = k0 + 2 * t + 8;
+          const uint32_t a0 = pack_bf16(A(r0 + g, c0), A(r0 + g, c0 + 1)),
+                         a1 = pack_bf16(A(r0 + g + 8, c0), A(r0 + g + 8, c0 + 1)),
+                         a2 = pack_bf16(A(r0 + g, c1), A(r0 + g, c1 + 1)),
+                         a3 = pack_bf16(A(r0 + g + 8, c1), A(r0 + g + 8, c1 + 1));
+          const uint32_t b0 = pack_bf16(B(n0 + g, c0), B(n0 + g, c0 + 1)),
+                         b1 = pack_bf16(B(n0 + g, c1), B(n0 + g, c1 + 1));
+          asm volatile(
+              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+              "{%0, %1, %2, %3};"
+              : "+f"(d0), "+f"(d1), "+f"(d2), "+f"(d3)
+              : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+        }
+      }
+      const int ra = r0 + g, rb = r0 + g + 8, ka = n0 + 2 * t, kb = n0 + 2 * t + 1;
+      if (ra < nr && ka < nk) store(ra, ka, d0);
+      if (ra < nr && kb < nk) store(ra, kb, d1);
+      if (rb < nr && ka < nk) store(rb, ka, d2);
+      if (rb < nr && kb < nk) store(rb, kb, d3);
+    }
+  }
+}
+
 // Orbital rows at one point q: FP64 values phiv[k] and FP32 gradient /
 // Laplacian phi5[(c-1) * n_max + k], c = 1..4, for the first n_sig orbitals.
 __device__ void orbital_rows_m(const DevSys& S, const Layout& L, const LayoutM& M, const double q[3], int n_sig,
@@ -308,13 +414,19 @@ __device__ void orbital_rows_m(const DevSys& S, const Layout& L, const LayoutM& 
       if (k < n_sig && sub == 0) phiv[k] = acc;
     }
   }
-  for (int o = lane; o < 4 * n_sig; o += WARP) {
-    const int c = 1 + o / n_sig, k = o - (c - 1) * n_sig;
-    const float* crow = S.Cf + (size_t)k * L.n_bf;
-    const float* x = chi5 + c * L.n_bf;
-    float acc = 0.f;
-    for (int mu = 0; mu < L.n_bf; ++mu) acc = fmaf(__ldg(crow + mu), x[mu], acc);
-    phi5[(c - 1) * L.n_max + k] = acc;
+  if (M.tc) {
+    // the four derivative rows (chi5 rows 1..4) as one tensor-core tile
+    tc_contract(M.tc, chi5 + L.n_bf, L.n_bf, 1, 4, S.Cf, L.n_bf, n_sig, lane,
+                [&](int r, int k, float v) { phi5[r * L.n_max + k] = v; });
+  } else {
+    for (int o = lane; o < 4 * n_sig; o += WARP) {
+      const int c = 1 + o / n_sig, k = o - (c - 1) * n_sig;
+      const float* crow = S.Cf + (size_t)k * L.n_bf;
+      const float* x = chi5 + c * L.n_bf;
+      float acc = 0.f;
+      for (int mu = 0; mu < L.n_bf; ++mu) acc = fmaf(__ldg(crow + mu), x[mu], acc);
+      phi5[(c - 1) * L.n_max + k] = acc;
+    }
   }
   __syncwarp();
 }
@@ -387,8 +499,19 @@ __device__ void refresh_b32(const Layout& L, const LayoutM& M, float* sm, int e0
 // p = p0 + c, c in [0, n_hops), read from dchi[mu * ld + c]; k over the
 // electron's spin block, each dot split over G lanes.
 __device__ void orbital_diffs(const DevSys& S, const Layout& L, float* dph, const float* dchi, int ld, int p0,
-                              int n_hops, int lane) {
+                              int n_hops, int lane, int tc = 0) {
   const int nm = L.n_max, nbf = L.n_bf;
+  if (tc) {
+    // hops through the M dimension (16 per tile), orbitals of the larger spin
+    // block through N; orbitals past a hop's own block are stored as zeros
+    tc_contract(tc, dchi, 1, ld, n_hops, S.Cf, nbf, nm, lane, [&](int c, int k, float v) {
+      const int p = p0 + c;
+      const int nsig = (p / 6) < L.n_up ? L.n_up : L.n_dn;
+      dph[p * nm + k] = k < nsig ? v : 0.f;
+    });
+    __syncwarp();
+    return;
+  }
   const int n_out = n_hops * nm, G = split_factor(n_out, nbf);
   const int chunk = (nbf + G - 1) / G, n_task = n_out * G;
   for (int base = 0; base < n_task; base += WARP) {
@@ -674,7 +797,7 @@ __device__ EvalOut eval_full_m(const DevSys& S, const Layout& L, const LayoutM& 
   __threadfence_block();
   __syncwarp();
   // (4) orbital differences of every hop and the determinant ratios
-  orbital_diffs(S, L, AR.dph, dchi, P, 0, P, lane);
+  orbital_diffs(S, L, AR.dph, dchi, P, 0, P, lane, M.tc);
   det_diffs(L, M, sm, AR.dph, 0, P, lane);
   for (int p = lane; p < P; p += WARP) {
     const float D = hdm[p];
@@ -797,7 +920,7 @@ __device__ EvalOut eval_incr_m(const DevSys& S, const Layout& L, const LayoutM& 
     }
   }
   __syncwarp();
-  orbital_diffs(S, L, AR.dph, dc6, 6, 6 * m, 6, lane);
+  orbital_diffs(S, L, AR.dph, dc6, 6, 6 * m, 6, lane, M.tc);
   for (int o = lane; o < 6 * per; o += WARP) {
     const int d = o / per, t = o - d * per, ax = d >> 1;
     const float sa = (d & 1) ? -af : af;

@@ -92,7 +92,13 @@ def test_workspace_sizing_and_validation(lib):
     s, w, p, keep = _structs(W.water_methane(), n_w=4096, precision=1)
     assert lib.lrdmc_workspace_bytes(ctypes.byref(s), ctypes.byref(w), ctypes.byref(p), ctypes.byref(nb)) == 0
     assert nb.value > 2 * 4096 * 8 * (48 + 128 + 640 + 96) + 2 * 4096 * 4 * (96 * 8 + 16 * 96) + 2368 * 4 * 56 * 96
-    for bad in (dict(a=-1.0), dict(node_rule=5), dict(reinv_period=0), dict(precision=2)):
+    # the tensor-core forms (precision 2-4) share the mixed layout
+    for prec in (2, 3, 4):
+        s, w, p, keep = _structs(W.water_methane(), n_w=4096, precision=prec)
+        nt = ctypes.c_size_t()
+        assert lib.lrdmc_workspace_bytes(ctypes.byref(s), ctypes.byref(w), ctypes.byref(p), ctypes.byref(nt)) == 0
+        assert nt.value == nb.value
+    for bad in (dict(a=-1.0), dict(node_rule=5), dict(reinv_period=0), dict(precision=5), dict(precision=-1)):
         s, w, p, keep = _structs(W.h2_sto3g(), **bad)
         assert lib.lrdmc_workspace_bytes(ctypes.byref(s), ctypes.byref(w), ctypes.byref(p),
                                          ctypes.byref(nb)) == 1
