@@ -361,6 +361,7 @@ def run_gpu(args, rank, world):
     e2e_value = world * ws_per_step / (statistics.mean(e2e_ms) / 1e3)
     mixed = run_mixed(args, P, s, x0, lr, flush, rank) if not args.no_mixed else None
     a_scan = run_a_scan(P) if rank == 0 and not args.no_a_scan else None
+    h2 = run_h2(P) if rank == 0 and not args.no_a_scan else None
     adjoint = run_adjoint(P) if rank == 0 and not args.no_adjoint else None
     large = run_large(P, flush) if rank == 0 and not args.no_large else None
     batch = None
@@ -369,7 +370,7 @@ def run_gpu(args, rank, world):
     return dict(value=value, t_total=t_total, step_ms=statistics.mean(step_ms), prop_ms=statistics.mean(prop_ms),
                 launches=launches, achieved=achieved, clocks=clk.summary(), conv_rate=conv_rate,
                 conv_moves=conv_moves, tau=tau, e2e=e2e_value, h2d=h2d, d2h=d2h, slots=slots,
-                energy=lr.energy(), mixed=mixed, imbalance=imbalance, a_scan=a_scan, batch=batch, adjoint=adjoint,
+                energy=lr.energy(), mixed=mixed, imbalance=imbalance, a_scan=a_scan, h2=h2, batch=batch, adjoint=adjoint,
                 large=large)
 
 
@@ -433,6 +434,66 @@ def run_a_scan(P):
     return {"system": "H atom, Slater guide exp(-0.8 r), 2048 walkers, 140 intervals x 15 hops per spacing",
             "a": a_list, "E": E_list, "err": err_list, "E0": float(coef[0]), "E0_err": float(np.sqrt(cov[0, 0])),
             "chi2": chi2, "exact_continuum": -0.5, "wall_s": wall}
+
+
+def run_h2(P):
+    """The H2 run at its stated size: STO-3G H2 (2 electrons, nuclei at
+    z = +-0.7 bohr), a = 0.2, 256 walkers, 100 branching intervals of 20
+    moves (2000 steps), Philox seed 1, node rule 2 (the cap on every electron:
+    the cusp-less Gaussian orbital leaves W unbounded below otherwise), both
+    schedules; the conventional projection time gives the same mean move
+    count (tau = 20 / <b_bar>, b_bar averaged over the walkers at the end of the
+    load-balanced run's first five intervals).  Absolute
+    numbers only: the 256 walkers (3072 hop evaluations per step) leave the
+    GPU mostly idle."""
+    import torch
+    import workloads as W
+    s = W.h2_sto3g()
+    x0 = W.initial_walkers(s, 256, seed=11)
+    out = {"system": "H2 STO-3G, a = 0.2, 256 walkers, 100 intervals x 20 moves, node rule 2"}
+    tau, bbar = None, []
+    for kind, name in ((P.LOAD_BALANCED, "load_balanced"), (P.CONVENTIONAL, "conventional")):
+        lr = P.Lrdmc(s, x0, 0.2, seed=1, p_gbar=10, n_equil=10, node_rule=2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for j in range(100):
+            lr.propagate(kind, n_proj=20, tau=tau or 0.0, max_moves=100000)
+            if kind == P.LOAD_BALANCED and j < 5:      # mean b_bar of the first five intervals' walkers
+                bbar.append(float(np.mean(lr.get_walkers(("ev",))["ev"][:, 0])))
+            lr.branch()
+        if kind == P.LOAD_BALANCED:
+            tau = 20.0 / float(np.mean(bbar))
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        E, err = lr.energy()
+        h = lr.history()
+        moves = float(np.sum(h["moves_mean"])) * 256
+        out[name] = {"E": E, "err": err, "wall_s": wall, "walker_steps_per_s": moves / wall,
+                     "moves_mean": float(np.mean(h["moves_mean"])), "status_or": int(np.bitwise_or.reduce(h["status_or"]))}
+        lr.close()
+    out["tau"] = tau
+    # lattice extrapolation of the same molecule (nodeless guiding function:
+    # fixed node is exact, E(a -> 0) = -1.17447 Ha, the exact H2 energy at
+    # R = 1.4 bohr); spacings below 0.15, where the bias of the cusp-less
+    # Gaussian orbital follows a^2 + a^4
+    spacings, Es, errs = [0.05, 0.07, 0.1, 0.14], [], []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for a in spacings:
+        n_proj = int(round(20 * (0.2 / a) ** 2))
+        lr = P.Lrdmc(s, W.initial_walkers(s, 4096, seed=5), a, seed=7, p_gbar=10, n_equil=75, node_rule=2)
+        for _ in range(300):
+            lr.propagate(P.LOAD_BALANCED, n_proj=n_proj)
+            lr.branch()
+        E, err = lr.energy()
+        Es.append(E)
+        errs.append(err)
+        lr.close()
+    coef, cov, chi2 = P.extrapolate_a(spacings, Es, errs, 2)
+    out["a_scan"] = {"a": spacings, "E": Es, "err": errs, "walkers": 4096, "intervals": 300,
+                     "moves_per_interval": "20 (0.2/a)^2", "E0": float(coef[0]), "E0_err": float(np.sqrt(cov[0, 0])),
+                     "chi2": chi2, "exact": -1.17447, "wall_s": time.perf_counter() - t0}
+    return out
 
 
 def run_adjoint(P):
@@ -691,6 +752,7 @@ def main():
                                       "bias_err_mHa": v["energy_bias_err_mHa"]}
                                   for k, v in mixed["tensor_core"].items()} if mixed else None,
             "a_scan": res["a_scan"],
+            "h2_run": res["h2"],
             "batch": res["batch"],
             "adjoint": res["adjoint"],
             "large_systems": res["large"],

@@ -60,6 +60,7 @@ typedef enum {
 #define LRDMC_WALKER_STEP_CAP  4u
 #define LRDMC_WALKER_STUCK     8u   /* no hop kept by the fixed-node rule (b_bar = 0) */
 #define LRDMC_WALKER_SINGULAR  16u
+#define LRDMC_WALKER_DRIFT     32u  /* re-inverted early: the inverse residual exceeded the drift tolerance */
 
 /* Nuclei and electron counts (Appendix D: V_loc = sum nu_ei + sum nu_ee + V_ii). */
 typedef struct {
@@ -369,6 +370,27 @@ lrdmc_status lrdmc_fp64math(int n, const double* x, double* exp_out, double* rcp
  * stream); LRDMC_ERR_ARG for n < 0, NULL arrays or r_c <= 0. */
 lrdmc_status lrdmc_erf_ratio_table(double* out, int* n_int, int* n_coef);
 lrdmc_status lrdmc_erf_over_r(int n, const double* s, double r_c, double* out, void* stream);
+
+/* Sherman-Morrison drift check (the paper is silent; numerical safeguard).
+ * Between the periodic from-scratch inversions (every reinv_period hops) B is
+ * kept by rank-1 updates, each adding rounding; near a node A is
+ * ill-conditioned and the error grows.  The FP64 propagate kernel, on every
+ * fourth hop since the last inversion, forms one row of A B - I (the row of
+ * the electron after the moved one in its spin block, which the last update
+ * did not touch; A from the cached FP64 orbital values) and re-inverts the
+ * walker's Slater matrices at once when the largest |entry| exceeds tol.
+ * The mixed-precision kernels (whose hop loop runs at its register limit)
+ * check one row per spin block once per interval, before the first hop of a
+ * walker that has hopped since its last inversion; on a hit they re-invert
+ * before the first hop and evaluate that walker in full after it.
+ * Such a walker gets the LRDMC_WALKER_DRIFT status bit.
+ * lrdmc_set_drift_tol: tol >= 0 (0 disables the check; default 1e-11, which
+ * keeps the hop ratios an order of magnitude inside 1e-10 relative);
+ * LRDMC_ERR_ARG for a negative or NaN tol.  Takes effect at the next propagate.
+ * lrdmc_drift_reinversions: drift-triggered re-inversions since the handle
+ * was created, all walkers (synchronises). */
+lrdmc_status lrdmc_set_drift_tol(lrdmc_handle h, double tol);
+lrdmc_status lrdmc_drift_reinversions(lrdmc_handle h, int64_t* n);
 
 /* Load-imbalance measurement (the in-GPU image of the paper's argument that
  * a synchronised interval waits for its slowest walker).  With timing enabled

@@ -85,6 +85,8 @@ def load_library():
         "lrdmc_interval_timing": [P, c_double_p],
         "lrdmc_load": [P, C.c_char_p],
         "lrdmc_stream": [P, C.POINTER(P)],
+        "lrdmc_set_drift_tol": [P, C.c_double],
+        "lrdmc_drift_reinversions": [P, C.POINTER(C.c_int64)],
         "lrdmc_estimate": [C.c_int, c_double_p, c_double_p, C.c_int, C.c_int, c_double_p, c_double_p],
         "lrdmc_extrapolate_a": [C.c_int, c_double_p, c_double_p, c_double_p, C.c_int, c_double_p, c_double_p,
                                 c_double_p],
@@ -357,6 +359,16 @@ class Lrdmc:
 
     def load(self, path):
         self._check(self.lib.lrdmc_load(self._h, os.fsencode(path)))
+
+    def set_drift_tol(self, tol):
+        """Tolerance of the Sherman-Morrison drift check (0 disables it)."""
+        self._check(self.lib.lrdmc_set_drift_tol(self._h, float(tol)))
+
+    def drift_reinversions(self):
+        """Drift-triggered re-inversions since creation (all walkers)."""
+        n = C.c_int64()
+        self._check(self.lib.lrdmc_drift_reinversions(self._h, C.byref(n)))
+        return n.value
 
     def launch_count(self):
         v = C.c_int64()

@@ -16,6 +16,7 @@ constexpr uint32_t ST_NONFINITE = 2u;
 constexpr uint32_t ST_STEP_CAP = 4u;
 constexpr uint32_t ST_STUCK = 8u;
 constexpr uint32_t ST_SINGULAR = 16u;
+constexpr uint32_t ST_DRIFT = 32u;      // a Sherman-Morrison drift check triggered a re-inversion
 
 // Scalars kept at the end of every walker block (doubles; integer-valued
 // fields are exact in double up to 2^53).

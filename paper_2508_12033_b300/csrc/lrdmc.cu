@@ -31,6 +31,13 @@ constexpr int SCRATCH_WARPS_CAP = 148 * 32;
 // Status words (int32) of a handle: [0, 2) reconfiguration status, DSTAT_NEXT
 // the propagate kernels' work counter.
 constexpr int DSTAT_NEXT = 8;
+// status word DSTAT_DRIFT: drift-triggered re-inversions since creation
+constexpr int DSTAT_DRIFT = 9;
+// Default tolerance of the Sherman-Morrison drift check (lrdmc_set_drift_tol):
+// an inverse residual delta perturbs the hop ratios of the spin block by
+// about delta relative, so 1e-11 keeps them an order of magnitude inside the
+// 1e-10 relative agreement the FP64 path is held to.
+constexpr double DRIFT_TOL_DEFAULT = 1e-11;
 // The gradient kernel keeps its working sets in global memory when shared
 // memory would hold fewer than this many of them per SM.
 constexpr int ADJ_MIN_WARPS = 8;
@@ -375,6 +382,7 @@ struct lrdmc_s {
   double E0 = 0.0;
   uint32_t interval = 0;
   int last_kind = 1;
+  double drift_tol = DRIFT_TOL_DEFAULT;
   std::vector<double> wbar, ebar, e0h, mmean;
   std::vector<int> mmax, surv;
   std::vector<uint32_t> stor;
@@ -527,6 +535,8 @@ static StepParams step_params(lrdmc_handle h, const lrdmc_schedule* sch) {
   sp.a = h->prm.a;
   sp.node_rule = h->prm.node_rule;
   sp.reinv_period = h->prm.reinv_period;
+  sp.drift_tol = h->drift_tol;
+  sp.drift_count = h->dstat + DSTAT_DRIFT;
   sp.stamps = h->timing ? h->stamps : nullptr;
   sp.rotate = sch->rotate != 0;
   sp.next = nullptr;
@@ -1693,6 +1703,22 @@ lrdmc_status lrdmc_interval_timing(lrdmc_handle h, double out[6]) {
   out[3] = span > 0 ? sum / (span * resident) : 0.0;
   out[4] = mv / n;
   out[5] = mvmax;
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_set_drift_tol(lrdmc_handle h, double tol) {
+  if (!h || !(tol >= 0.0)) return LRDMC_ERR_ARG;
+  h->drift_tol = tol;
+  return LRDMC_OK;
+}
+
+lrdmc_status lrdmc_drift_reinversions(lrdmc_handle h, int64_t* n) {
+  if (!h || !h->dstat || !n) return LRDMC_ERR_ARG;
+  DeviceGuard g(h->device);
+  int32_t v = 0;
+  CK(h, cudaMemcpyAsync(&v, h->dstat + DSTAT_DRIFT, sizeof v, cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  *n = v;
   return LRDMC_OK;
 }
 

@@ -1118,7 +1118,57 @@ struct StepParams {
   int rotate;                   // randomised lattice: new versors every interval
   unsigned* next;               // optional: zeroed work counter; warps past their first walker take the next
                                 // unclaimed one from it (dynamic assignment), else walkers go round-robin
+  double drift_tol;             // > 0: re-invert when the inverse residual after a hop exceeds it
+  int* drift_count;             // optional: device counter of drift-triggered re-inversions
 };
+
+// Drift of the Sherman-Morrison inverse after electron i hopped: the largest
+// |(A B)_rj - delta_rj| over the columns j of the spin block, for the row r
+// of the next electron of the block (cyclically; the moved electron itself in
+// a one-electron block), with A's rows the FP64 orbital values
+// val[e * vstride + k] and B from B^T in shared memory.  Between from-scratch
+// inversions B accumulates the rounding of every rank-1 update; the product
+// with a row of A that the update did not touch exposes that drift.  Each
+// dot product is split over G lanes (G the largest power of two with n G <=
+// 32, at most 8); the maximum is taken on the integer images of the
+// non-negative residuals (a NaN ranks above every number), so only the dot
+// products use the FP64 pipe.  Result valid in all lanes.  Kept out of line:
+// it runs on one hop in four, and inlined it would add registers to the whole
+// hop loop.
+__device__ __noinline__ double inverse_residual(const Layout& L, const double* val, int vstride,
+                                                   const double* bt, int i, int lane) {
+  const SpinRef sr = spin_ref(L, i);
+  const int n = sr.n, e0 = i - sr.ii, rr = (sr.ii + 1) % n;
+  const double* B = bt + sr.bt_off;   // B[j * n + k] = (A^{-1})_{k j}
+  const double* arow = val + (size_t)(e0 + rr) * vstride;
+  int G = 1;
+  while (G < 8 && n * G * 2 <= WARP) G <<= 1;
+  const int chunk = (n + G - 1) / G;
+  long long worst = 0;
+  for (int base = 0; base < n * G; base += WARP) {
+    const int task = base + lane, j = task / G, part = task - j * G;
+    double acc = 0.0;
+    if (j < n) {
+      const int k1 = min(n, (part + 1) * chunk);
+      for (int k = part * chunk; k < k1; ++k) acc = fma(arow[k], B[j * n + k], acc);
+    }
+    for (int o = 1; o < G; o <<= 1) acc += __shfl_xor_sync(FULL, acc, o);
+    if (j < n) {
+      const long long r = __double_as_longlong(acc - (rr == j ? 1.0 : 0.0)) & 0x7fffffffffffffffll;
+      worst = r > worst ? r : worst;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const long long v = __shfl_xor_sync(FULL, worst, o);
+    worst = v > worst ? v : worst;
+  }
+  return __longlong_as_double(worst);
+}
+
+// The drift check runs on every DRIFT_EVERY-th hop since the last inversion
+// (drift grows gradually; a check per hop would cost a few percent).
+constexpr int DRIFT_EVERY = 4;
 
 // Next walker of a warp after w: from the work counter (first-come order,
 // which evens out walkers of unequal cost) or round-robin.
@@ -1352,11 +1402,20 @@ __device__ void propagate_walker_impl(const DevSys& S, const Layout& L, double* 
         apply_hop<ROT>(S, L, gblk, sm, scr, p, P.a, ia, !cached, T, lane);
         ++moves;
         bool reinv = false;
-        if (++since >= P.reinv_period) {
+        // drift check between the periodic inversions (the moved row of A is
+        // already in the cache)
+        const bool drift = P.drift_tol > 0.0 && since + 1 < P.reinv_period && (since + 1) % DRIFT_EVERY == 0 &&
+                           !(inverse_residual(L, gblk + L.g_cache, 5 * L.n_max, sm + L.s_bt, p / 6, lane) <=
+                             P.drift_tol);
+        if (++since >= P.reinv_period || drift) {
           if (reinvert(L, gblk, sm, scr.gj, lane)) status |= ST_SINGULAR;
           compute_g(S, L, sm, scr.g, 0, L.n_e, lane);
           since = 0;
           reinv = true;
+          if (drift) {
+            status |= ST_DRIFT;
+            if (lane == 0 && P.drift_count) atomicAdd(P.drift_count, 1);
+          }
         }
         EvalOut e;
         if (!cached) {

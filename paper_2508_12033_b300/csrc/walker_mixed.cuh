@@ -1249,6 +1249,31 @@ __device__ void propagate_walker_m(const DevSys& S, const Layout& L, const Layou
     double bbar = sc[SC_BBAR], Wd = sc[SC_WDIAG], eL = sc[SC_EL], kept = sc[SC_KEPT];
     uint32_t status = (uint32_t)sc[SC_STATUS];
     int moves = 0, since = (int)sc[SC_SINCE];
+    if (cached && since > 0 && P.drift_tol > 0.0) {
+      // Sherman-Morrison drift check of the FP64 inverse, once per interval
+      // before the first hop (inside the hop loop it would raise this
+      // kernel's register pressure): one row of A B - I per spin block,
+      // rotating with the interval.  Past the tolerance the walker re-inverts
+      // now and, its hop caches then being stale, evaluates in full after its
+      // first hop (the first step's weight uses the stored evaluation, as it
+      // would without the check)
+      bool drift = false;
+      for (int blk = 0; blk < 2; ++blk) {
+        const int nb = blk ? L.n_dn : L.n_up;
+        if (nb == 0) continue;
+        const int i = (blk ? L.n_up : 0) + (int)(P.interval % (unsigned)nb);
+        drift |= !(inverse_residual(L, cache_val(L, gblk), L.n_max, (const double*)(sm + M.bt), i, lane) <=
+                   P.drift_tol);
+      }
+      if (drift) {
+        if (reinvert_m(L, M, gblk, sm, scr.gj, lane)) status |= ST_SINGULAR;
+        refresh_b32(L, M, sm, 0, L.n_e, lane);
+        since = 0;
+        cached = false;
+        status |= ST_DRIFT;
+        if (lane == 0 && P.drift_count) atomicAdd(P.drift_count, 1);
+      }
+    }
     for (int k = 0;; ++k) {
       if (P.kind == 1 && k >= P.n_proj) break;
       double u_tau, u_move;

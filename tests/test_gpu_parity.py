@@ -82,7 +82,9 @@ def test_load_balanced_interval_matches_oracle(name, sysf, n_w):
     assert_close(g["ev"][:, 3], Wk.ev["eL"], what="eL")
     assert_close(g["ev"][:, 2], Wk.ev["W"], what="W")
     assert_close(g["ratios"], Wk.ev["ratios"], what="ratios")
-    np.testing.assert_array_equal(g["status"], Wk.status)
+    # the drift-check bit (32) marks an early re-inversion, an implementation
+    # event with no counterpart in the oracle (which inverts afresh every step)
+    np.testing.assert_array_equal(g["status"] & ~np.uint32(32), Wk.status)
 
 
 @pytest.mark.parametrize("name,sysf,n_w,tau", [("h2", W.h2_sto3g, 77, 0.06), ("wm", W.water_methane, 33, 0.006)])
@@ -111,7 +113,9 @@ def test_conventional_step_cap_and_zero_projection():
     Wk = OL.init_walkers(s, x0, 0.2)
     OL.propagate_conventional(s, Wk, 0.2, 10.0, seed=1, interval=0, max_moves=3)
     np.testing.assert_array_equal(g["x"], Wk.x)
-    np.testing.assert_array_equal(g["status"], Wk.status)
+    # the drift-check bit (32) marks an early re-inversion, an implementation
+    # event with no counterpart in the oracle (which inverts afresh every step)
+    np.testing.assert_array_equal(g["status"] & ~np.uint32(32), Wk.status)
     lr.clear_status()
     lr.propagate(P.LOAD_BALANCED, n_proj=0)
     g2 = lr.get_walkers()

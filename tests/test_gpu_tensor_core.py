@@ -93,7 +93,7 @@ def test_tensor_core_eval_within_rounding_bounds(precision, name, sysf, n, el_fp
     torch.cuda.synchronize()
     ref = H.evaluate(s, x, a)
     rat_b, el_b = _bounds(s, x, a, precision)
-    r = ratios.cpu().numpy()
+    r = ratios.cpu().numpy().reshape(n, -1)
     rref = ref["ratios"].reshape(n, -1)            # hop p = 6 i + d
     err = np.abs(r - rref)
     allowed = 1.5 * rat_b + 1e-4 * np.maximum(1.0, np.abs(rref))
