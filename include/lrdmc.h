@@ -390,6 +390,27 @@ lrdmc_status lrdmc_erf_over_r(int n, const double* s, double r_c, double* out, v
  * lrdmc_drift_reinversions: drift-triggered re-inversions since the handle
  * was created, all walkers (synchronises). */
 lrdmc_status lrdmc_set_drift_tol(lrdmc_handle h, double tol);
+
+/* Checked build (library facility; the paper has no counterpart).  The build
+ * step also compiles liblrdmc_checked.so with LRDMC_CHECKED defined: there every
+ * data-derived index of the walker and branching kernels (hop, electron and
+ * walker indices, comb and slot indices, shell / primitive / basis / nucleus
+ * indices read from the system image, offsets into the per-hop shared scratch
+ * and into the cache-block arrays) is tested against its extent before use.  A
+ * failed test records the first violation in a device word -- source line of
+ * the check in the high 32 bits, the offending index in the low 32 -- and
+ * redirects the access to index 0 instead of faulting or trapping, so the
+ * context stays usable.  It replaces a memory checker on small cases.
+ *   lrdmc_checked_build: 1 in the checked library, 0 otherwise.
+ *   lrdmc_check_word: synchronises the current device, then reads the word
+ *     (0 = no violation) into *word and, with clear != 0, resets it.
+ *   lrdmc_check_selftest: evaluates the check for index i against extent n on
+ *     the device; *result is i when 0 <= i < n, else 0 with the violation
+ *     recorded (a testing aid for the mechanism itself).
+ * Both return LRDMC_ERR_UNSUPPORTED in the normal library. */
+int lrdmc_checked_build(void);
+lrdmc_status lrdmc_check_word(uint64_t* word, int clear);
+lrdmc_status lrdmc_check_selftest(int i, int n, int* result);
 lrdmc_status lrdmc_drift_reinversions(lrdmc_handle h, int64_t* n);
 
 /* Load-imbalance measurement (the in-GPU image of the paper's argument that

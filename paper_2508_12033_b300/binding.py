@@ -16,7 +16,10 @@ LOAD_BALANCED = 1
 CONVENTIONAL = 0
 
 _LIB = None
-_LIBPATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "liblrdmc.so")
+# LRDMC_CHECKED=1 in the environment selects the checked build (every
+# data-derived kernel index tested; see lrdmc_check_word in lrdmc.h)
+_LIBPATH = os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                        "liblrdmc_checked.so" if os.environ.get("LRDMC_CHECKED") == "1" else "liblrdmc.so")
 
 c_double_p = C.POINTER(C.c_double)
 c_int_p = C.POINTER(C.c_int)
@@ -85,6 +88,9 @@ def load_library():
         "lrdmc_interval_timing": [P, c_double_p],
         "lrdmc_load": [P, C.c_char_p],
         "lrdmc_stream": [P, C.POINTER(P)],
+        "lrdmc_checked_build": [],
+        "lrdmc_check_word": [C.POINTER(C.c_uint64), C.c_int],
+        "lrdmc_check_selftest": [C.c_int, C.c_int, c_int_p],
         "lrdmc_set_drift_tol": [P, C.c_double],
         "lrdmc_drift_reinversions": [P, C.POINTER(C.c_int64)],
         "lrdmc_estimate": [C.c_int, c_double_p, c_double_p, C.c_int, C.c_int, c_double_p, c_double_p],
@@ -595,6 +601,20 @@ def estimate(wbar, ebar, p_gbar=10, n_equil=0):
     if r != 0:
         raise LrdmcError(r, "lrdmc_estimate: invalid history")
     return E.value, err.value
+
+
+def check_word(clear=True):
+    """(violation word, checked) of the checked build: the first out-of-extent
+    index recorded by the kernels (0 = none; source line << 32 | index);
+    checked is False in the normal library, where the word is always 0."""
+    lib = load_library()
+    if not lib.lrdmc_checked_build():
+        return 0, False
+    w = C.c_uint64()
+    r = lib.lrdmc_check_word(C.byref(w), int(bool(clear)))
+    if r != 0:
+        raise LrdmcError(r, "lrdmc_check_word failed")
+    return int(w.value), True
 
 
 def philox4x32(seed, ctr):

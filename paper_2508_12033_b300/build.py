@@ -10,6 +10,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "liblrdmc.so")
+# the checked build: data-derived indices tested in the kernels (LRDMC_CHECKED)
+LIB_CHECKED = os.path.join(PKG, "liblrdmc_checked.so")
 ARCH = "arch=compute_103a,code=sm_103a"
 
 
@@ -34,21 +36,24 @@ def nvcc_command(out: str = LIB, extra=()):
             "-shared", "-I", INCLUDE, *extra, "-o", out, os.path.join(CSRC, "lrdmc.cu")]
 
 
-def is_stale() -> bool:
-    if not os.path.exists(LIB):
+def is_stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(s) > t for s in _sources())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile liblrdmc.so next to this file if it is missing or older than a source."""
-    if force or is_stale():
-        cmd = nvcc_command(LIB + ".tmp")
-        if verbose:
-            print(" ".join(cmd))
-        subprocess.run(cmd, check=True)
-        os.replace(LIB + ".tmp", LIB)
+def build(force: bool = False, verbose: bool = False, checked: bool = True) -> str:
+    """Compile liblrdmc.so (and, with checked, liblrdmc_checked.so) next to
+    this file if missing or older than a source."""
+    targets = [(LIB, ())] + ([(LIB_CHECKED, ("-DLRDMC_CHECKED",))] if checked else [])
+    for lib, extra in targets:
+        if force or is_stale(lib):
+            cmd = nvcc_command(lib + ".tmp", extra)
+            if verbose:
+                print(" ".join(cmd))
+            subprocess.run(cmd, check=True)
+            os.replace(lib + ".tmp", lib)
     return LIB
 
 

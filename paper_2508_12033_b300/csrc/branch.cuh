@@ -229,7 +229,7 @@ __device__ void slot_body(int n, int32_t* __restrict__ src, int32_t* __restrict_
   const int t = threadIdx.x;
   for (int k = t; k < n; k += BR_THREADS) A[k] = 0;
   __syncthreads();
-  for (int al = t; al < n; al += BR_THREADS) A[src[al]] = 1;
+  for (int al = t; al < n; al += BR_THREADS) A[CHK(src[al], n)] = 1;
   __syncthreads();
   // further copies in comb order
   int lo, hi;
@@ -245,7 +245,7 @@ __device__ void slot_body(int n, int32_t* __restrict__ src, int32_t* __restrict_
   __syncthreads();
   for (int k = t; k < n; k += BR_THREADS) A[k] = A[k] ? k : -1;
   __syncthreads();
-  for (int j = t; j < n_free; j += BR_THREADS) A[src[j]] = X[j];
+  for (int j = t; j < n_free; j += BR_THREADS) A[CHK(src[j], n)] = X[j];
   __syncthreads();
   for (int k = t; k < n; k += BR_THREADS) src[k] = A[k];
 }
@@ -458,7 +458,7 @@ __device__ void gather_body(const Layout& L, const double* old_state, double* ne
   for (size_t idx = tid; idx < total; idx += nth) {
     const int a = (int)(idx / per);
     const int o = (int)(idx - (size_t)a * per);
-    const int sa = src[a];
+    const int sa = CHK(src[a], n_w);
     if (inplace && sa == a) continue;
     double2 v = o2[(size_t)sa * per + o];
     if (2 * o == L.g_sc + SC_W) v.x = 1.0;
@@ -474,7 +474,7 @@ __device__ void gather_body(const Layout& L, const double* old_state, double* ne
   const size_t ctotal = (size_t)n_w * cper;
   for (size_t idx = tid; idx < ctotal; idx += nth) {
     const int a = (int)(idx / cper);
-    const int sa = src[a];
+    const int sa = CHK(src[a], n_w);
     if (inplace && sa == a) continue;
     nc[idx] = oc[(size_t)sa * cper + (idx - (size_t)a * cper)];
   }
@@ -487,7 +487,7 @@ __device__ void gather_body(const Layout& L, const double* old_state, double* ne
 __global__ void k_gather_slots(Layout L, double* state, double* cache, const int32_t* __restrict__ src,
                                const int32_t* __restrict__ status) {
   if (status[0] != 0) return;
-  const int a = blockIdx.x, sa = src[a];
+  const int a = blockIdx.x, sa = CHK(src[a], (int)gridDim.x);   // one CTA per walker slot
   if (sa == a) {
     if (threadIdx.x == 0) state[(size_t)a * L.g_stride + L.g_sc + SC_W] = 1.0;
     return;

@@ -3,12 +3,34 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 namespace lrdmc {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int WARP = 32;
+
+// Checked build (compiled with -DLRDMC_CHECKED into a library of its own):
+// CHK(i, n) tests a data-derived index against its extent [0, n).  A failure
+// records the first violation in the device word g_lrdmc_check (source line in
+// the high 32 bits, the offending index in the low 32; later failures keep the
+// first) and returns 0, so the access stays inside the array and nothing
+// traps; the host reads and clears the word with lrdmc_check_word.  In the
+// normal build CHK(i, n) is i.
+#ifdef LRDMC_CHECKED
+__device__ unsigned long long g_lrdmc_check;
+__device__ __forceinline__ long long chk_index(long long i, long long n, int line) {
+  if (i < 0 || i >= n) {
+    atomicCAS(&g_lrdmc_check, 0ull, ((unsigned long long)(unsigned)line << 32) | (unsigned long long)(unsigned)i);
+    return 0;
+  }
+  return i;
+}
+#define CHK(i, n) ((std::decay_t<decltype(i)>)::lrdmc::chk_index((long long)(i), (long long)(n), __LINE__))
+#else
+#define CHK(i, n) (i)
+#endif
 
 // per-walker status bits (mirror LRDMC_WALKER_* in lrdmc.h)
 constexpr uint32_t ST_NEG_DIAG = 1u;

@@ -1706,6 +1706,60 @@ lrdmc_status lrdmc_interval_timing(lrdmc_handle h, double out[6]) {
   return LRDMC_OK;
 }
 
+}  // extern "C"
+
+namespace {
+#ifdef LRDMC_CHECKED
+__device__ int g_chk_selftest_out;
+// Testing aid of the checked build: one thread evaluates CHK(i, n).
+__global__ void k_check_selftest(int i, int n) { g_chk_selftest_out = CHK(i, n); }
+#endif
+}  // namespace
+
+extern "C" {
+
+int lrdmc_checked_build(void) {
+#ifdef LRDMC_CHECKED
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+lrdmc_status lrdmc_check_word(uint64_t* word, int clear) {
+#ifdef LRDMC_CHECKED
+  if (!word) return LRDMC_ERR_ARG;
+  unsigned long long v = 0;
+  if (cudaDeviceSynchronize() != cudaSuccess) return LRDMC_ERR_CUDA;
+  if (cudaMemcpyFromSymbol(&v, g_lrdmc_check, sizeof v) != cudaSuccess) return LRDMC_ERR_CUDA;
+  *word = v;
+  if (clear) {
+    const unsigned long long z = 0;
+    if (cudaMemcpyToSymbol(g_lrdmc_check, &z, sizeof z) != cudaSuccess) return LRDMC_ERR_CUDA;
+  }
+  return LRDMC_OK;
+#else
+  (void)word;
+  (void)clear;
+  return LRDMC_ERR_UNSUPPORTED;
+#endif
+}
+
+lrdmc_status lrdmc_check_selftest(int i, int n, int* result) {
+#ifdef LRDMC_CHECKED
+  if (!result) return LRDMC_ERR_ARG;
+  k_check_selftest<<<1, 1>>>(i, n);
+  if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return LRDMC_ERR_CUDA;
+  if (cudaMemcpyFromSymbol(result, g_chk_selftest_out, sizeof(int)) != cudaSuccess) return LRDMC_ERR_CUDA;
+  return LRDMC_OK;
+#else
+  (void)i;
+  (void)n;
+  (void)result;
+  return LRDMC_ERR_UNSUPPORTED;
+#endif
+}
+
 lrdmc_status lrdmc_set_drift_tol(lrdmc_handle h, double tol) {
   if (!h || !(tol >= 0.0)) return LRDMC_ERR_ARG;
   h->drift_tol = tol;

@@ -38,7 +38,7 @@ __device__ __forceinline__ void shell_derivs(const DevSys& S, int s, const doubl
   const int l = __ldg(S.sh_l + s);
   const int np = __ldg(S.sh_nprim + s);
   const int off = __ldg(S.sh_off + s);
-  const int bf = __ldg(S.sh_bf + s);
+  const int bf = CHK(__ldg(S.sh_bf + s), n_bf);
   // one primitive loop for every shell kind (so that a warp with mixed kinds
   // evaluates the exponentials once): h = c exp(-z r) for the Slater 1s kind,
   // c exp(-a r^2) for Gaussians; s0 = sum h, s1 = sum c1 h, s2 = sum c2 h with
@@ -132,7 +132,7 @@ __device__ __forceinline__ double warp_sum4(const double v[4], int lane) {
 __device__ void orbital_derivs(const DevSys& S, const Layout& L, const double q[3], int n_sig, double* chi5,
                                double* phi5, const double* T, int lane) {
   for (int s = lane; s < S.n_shell; s += WARP) {
-    const int atom = __ldg(S.sh_atom + s);
+    const int atom = CHK(__ldg(S.sh_atom + s), S.n_nuc);
     const double d[3] = {q[0] - __ldg(S.R + 3 * atom), q[1] - __ldg(S.R + 3 * atom + 1),
                          q[2] - __ldg(S.R + 3 * atom + 2)};
     shell_derivs(S, s, d, d[0] * d[0] + d[1] * d[1] + d[2] * d[2], chi5, L.n_bf, T);
@@ -571,7 +571,7 @@ __device__ EvalOut eval_full(const DevSys& S, const Layout& L, const double* __r
             LJ += lap;
             vee += hir;
             if (scr.pt) {
-              double* pt = scr.pt + 4 * (e * ne + j);
+              double* pt = scr.pt + CHK(4 * (e * ne + j), 4 * ne * ne);
               pt[0] = p.u; pt[1] = f; pt[2] = lap; pt[3] = hir;
             }
           } else {
@@ -625,8 +625,8 @@ __device__ EvalOut eval_full(const DevSys& S, const Layout& L, const double* __r
       const double sa = (d & 1) ? -a : a;
       const double v =
           pade_value(fma(sa + sa, proj<ROT>(x + 3 * i, x + 3 * j, V, ax), pr2[i * ne + j]), pair_c(S, L, i, j), S.j2_b);
-      scr.u2[(size_t)j * P + 6 * i + d] = v;
-      scr.u2[(size_t)i * P + 6 * j + (d ^ 1)] = v;
+      scr.u2[CHK((size_t)j * P + 6 * i + d, (size_t)ne * P)] = v;
+      scr.u2[CHK((size_t)i * P + 6 * j + (d ^ 1), (size_t)ne * P)] = v;
     }
     __threadfence_block();
     __syncwarp();
@@ -651,7 +651,7 @@ __device__ EvalOut eval_full(const DevSys& S, const Layout& L, const double* __r
       }
       const double A = __ldg(S.j1A + I);
       if (A != 0.0) J1 += pade_value(s, -A, __ldg(S.j1B + I));
-      for (int sh = __ldg(S.atom_sh + I); sh < __ldg(S.atom_sh + I + 1); ++sh) {
+      for (int sh = CHK(__ldg(S.atom_sh + I), S.n_shell); sh < CHK(__ldg(S.atom_sh + I + 1), S.n_shell + 1); ++sh) {
         const int l = __ldg(S.sh_l + sh), np = __ldg(S.sh_nprim + sh), off = __ldg(S.sh_off + sh),
                   bf = __ldg(S.sh_bf + sh);
         const double arg = l == -1 ? s * rsqrt_nr(s) : s;
@@ -659,14 +659,14 @@ __device__ EvalOut eval_full(const DevSys& S, const Layout& L, const double* __r
         for (int q = 0; q < np; ++q) rad = fma(__ldg(S.coefs + off + q), exp_tab(-__ldg(S.exps + off + q) * arg, T), rad);
         if (l != 1) {
           det = fma(rad, gi[bf], det);
-          if (scr.chi) scr.chi[(size_t)bf * P + p] = rad;
+          if (scr.chi) scr.chi[CHK((size_t)bf * P + p, (size_t)nbf * P)] = rad;
         } else {
           const double c0 = dv[0] * rad, c1 = dv[1] * rad, c2 = dv[2] * rad;
           det = fma(c0, gi[bf], fma(c1, gi[bf + 1], fma(c2, gi[bf + 2], det)));
           if (scr.chi) {
-            scr.chi[(size_t)bf * P + p] = c0;
-            scr.chi[(size_t)(bf + 1) * P + p] = c1;
-            scr.chi[(size_t)(bf + 2) * P + p] = c2;
+            scr.chi[CHK((size_t)bf * P + p, (size_t)nbf * P)] = c0;
+            scr.chi[CHK((size_t)(bf + 1) * P + p, (size_t)nbf * P)] = c1;
+            scr.chi[CHK((size_t)(bf + 2) * P + p, (size_t)nbf * P)] = c2;
           }
         }
       }
@@ -756,8 +756,8 @@ __device__ EvalOut eval_incr(const DevSys& S, const Layout& L, const double* __r
         acc[5] += hir;
         pr2[m * ne + j] = s + a2;
         pr2[j * ne + m] = s + a2;
-        double* pm = scr.pt + 4 * (m * ne + j);
-        double* pj = scr.pt + 4 * (j * ne + m);
+        double* pm = scr.pt + CHK(4 * (m * ne + j), 4 * ne * ne);
+        double* pj = scr.pt + CHK(4 * (j * ne + m), 4 * ne * ne);
         const double ou = pm[0], of = pm[1], ol = pm[2], oh = pm[3];
         const double ox = px - xo0, oy = py - xo1, oz = pz - xo2;
         double* q = ej + 6 * j;
@@ -818,10 +818,10 @@ __device__ EvalOut eval_incr(const DevSys& S, const Layout& L, const double* __r
   {
     double* radp = tmp;   // [n_shell][6]
     for (int sh = lane; sh < S.n_shell; sh += WARP) {
-      const int I = __ldg(S.sh_atom + sh);
+      const int I = CHK(__ldg(S.sh_atom + sh), nn);
       const double* gg = geo + (m * nn + I) * 4;
-      const int l = __ldg(S.sh_l + sh), np = __ldg(S.sh_nprim + sh), off = __ldg(S.sh_off + sh),
-                bf = __ldg(S.sh_bf + sh);
+      const int l = __ldg(S.sh_l + sh), np = __ldg(S.sh_nprim + sh), off = CHK(__ldg(S.sh_off + sh), S.n_prim),
+                bf = CHK(__ldg(S.sh_bf + sh), nbf);
       double rad[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
       if (l == -1) {
         for (int d = 0; d < 6; ++d) {
@@ -858,22 +858,22 @@ __device__ EvalOut eval_incr(const DevSys& S, const Layout& L, const double* __r
         }
       }
       if (l == 1) {
-        for (int d = 0; d < 6; ++d) radp[6 * sh + d] = rad[d];
+        for (int d = 0; d < 6; ++d) radp[CHK(6 * sh + d, L.s_phi5 - L.s_tmp)] = rad[d];
       } else {
-        for (int d = 0; d < 6; ++d) scr.chi[(size_t)bf * P + 6 * m + d] = rad[d];
+        for (int d = 0; d < 6; ++d) scr.chi[CHK((size_t)bf * P + 6 * m + d, (size_t)nbf * P)] = rad[d];
       }
     }
     __syncwarp();
     const int n_pt = 18 * (S.n_shell - S.n_shell_np);
     for (int o = lane; o < n_pt; o += WARP) {
       const int kk = o / 18, r = o - 18 * kk, k = r / 6, d = r - 6 * k, ax = d >> 1;
-      const int sh = __ldg(S.sh_ord + S.n_shell_np + kk);
-      const int I = __ldg(S.sh_atom + sh), bf = __ldg(S.sh_bf + sh);
+      const int sh = CHK(__ldg(S.sh_ord + S.n_shell_np + kk), S.n_shell);
+      const int I = CHK(__ldg(S.sh_atom + sh), nn), bf = CHK(__ldg(S.sh_bf + sh), nbf - 2);
       const double sa = (d & 1) ? -a : a;
       const double* gg = geo + (m * nn + I) * 4;
       const double dk = ROT ? fma(sa, V[3 * ax + k], x[3 * m + k] - __ldg(S.R + 3 * I + k))
                             : gg[1 + k] + (k == ax ? sa : 0.0);
-      scr.chi[(size_t)(bf + k) * P + 6 * m + d] = dk * radp[6 * sh + d];
+      scr.chi[CHK((size_t)(bf + k) * P + 6 * m + d, (size_t)nbf * P)] = dk * radp[CHK(6 * sh + d, L.s_phi5 - L.s_tmp)];
     }
     __syncwarp();
   }
@@ -894,8 +894,8 @@ __device__ EvalOut eval_incr(const DevSys& S, const Layout& L, const double* __r
       s = c != 0.0 ? fma(sa + sa, gg[1 + ax], gg[0]) : 1.0;
     }
     const double v = pade_value(s, c, b);
-    tmp[o] = v;
-    if (pair) scr.u2[(size_t)j * P + 6 * m + d] = v;
+    tmp[CHK(o, L.s_phi5 - L.s_tmp)] = v;
+    if (pair) scr.u2[CHK((size_t)j * P + 6 * m + d, (size_t)ne * P)] = v;
   }
   __threadfence_block();
   __syncwarp();
@@ -928,7 +928,7 @@ __device__ EvalOut eval_incr(const DevSys& S, const Layout& L, const double* __r
       if (task < n_task) {
         const double* gi = g + (p / 6) * nbf;
         const int mu1 = min(nbf, (part + 1) * chunk);
-        for (int mu = part * chunk; mu < mu1; ++mu) det = fma(scr.chi[(size_t)mu * P + p], gi[mu], det);
+        for (int mu = part * chunk; mu < mu1; ++mu) det = fma(scr.chi[CHK((size_t)mu * P + p, (size_t)nbf * P)], gi[mu], det);
       }
       for (int sh = 1; sh < G; sh <<= 1) det += __shfl_xor_sync(FULL, det, sh);
       if (task < n_task && part == 0) hD[p] = det;
@@ -1037,6 +1037,7 @@ __device__ void apply_hop(const DevSys& S, const Layout& L, double* __restrict__
   double* chi5 = sm + L.s_tmp;     // per-hop scratch, refilled by the next evaluation
   double* g = scr.g;
   double* grow = chi5 + 5 * L.n_bf;
+  p = CHK(p, L.n_hop);
   const int i = p / 6, d = p - 6 * i;
   double q[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
   const double sa = (d & 1) ? -a : a;

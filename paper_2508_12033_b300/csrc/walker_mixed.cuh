@@ -899,11 +899,12 @@ __device__ EvalOut eval_incr_m(const DevSys& S, const Layout& L, const LayoutM& 
   for (int o = lane; o < 6 * S.n_shell; o += WARP) {
     const int d = o / S.n_shell, sh = o - d * S.n_shell, ax = d >> 1;
     const float sa = (d & 1) ? -af : af;
-    const int I = __ldg(S.sh_atom + sh);
+    const int I = CHK(__ldg(S.sh_atom + sh), S.n_nuc);
     const float* gg = geo + m * M.geo_st + 4 * I;
     const float del = fmaf(sa + sa, gg[ax], a2f);
     const float r = rt1[m * M.rt1_st + 2 * I];
-    const int l = __ldg(S.sh_l + sh), np = __ldg(S.sh_nprim + sh), off = __ldg(S.sh_off + sh), bf = __ldg(S.sh_bf + sh);
+    const int l = __ldg(S.sh_l + sh), np = __ldg(S.sh_nprim + sh), off = CHK(__ldg(S.sh_off + sh), S.n_prim),
+              bf = CHK(__ldg(S.sh_bf + sh), L.n_bf - (l == 1 ? 2 : 0));
     const float sp = gg[3] + del;
     const float arg = l == -1 ? __fdividef(del, sp * rsqrtf(sp) + r) : del;
     float rd = 0.f, rn = 0.f;
@@ -930,7 +931,7 @@ __device__ EvalOut eval_incr_m(const DevSys& S, const Layout& L, const LayoutM& 
       const float* pp = pair + m * M.pair_st + 2 * j;
       const float del = fmaf(sa + sa, xf[3 * m + ax] - xf[3 * j + ax], a2f);
       v = pade_delta(pp[0], pp[1], del, pair_cf(S, L, m, j), bj);
-      scr.u2[(size_t)j * P + 6 * m + d] = v;
+      scr.u2[CHK((size_t)j * P + 6 * m + d, (size_t)ne * P)] = v;
     } else {
       const int I = t - (ne - 1);
       const float A = __ldg(S.j1Af + I);
@@ -939,7 +940,7 @@ __device__ EvalOut eval_incr_m(const DevSys& S, const Layout& L, const LayoutM& 
         v = pade_delta(rt1[m * M.rt1_st + 2 * I], rt1[m * M.rt1_st + 2 * I + 1], fmaf(sa + sa, gg[ax], a2f), -A,
                        __ldg(S.j1Bf + I));
     }
-    tmp[o] = v;
+    tmp[CHK(o, M.phi5 - M.chi5)] = v;
   }
   __threadfence_block();
   __syncwarp();
@@ -1061,6 +1062,7 @@ __device__ void apply_hop_m(const DevSys& S, const Layout& L, const LayoutM& M, 
   const float* phi5 = sm + M.phi5;
   double* f = (double*)(sm + M.u);
   double* row = (double*)(sm + M.row);
+  p = CHK(p, L.n_hop);
   const int i = p / 6, d = p - 6 * i;
   double q[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
   q[d >> 1] += (d & 1) ? -a : a;
