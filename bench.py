@@ -41,8 +41,8 @@ FP64_UNIT_COUNT_GFLOPS = 148 * 2 * 2 * 2.032
 # FP64 pipe busy fraction, from one ncu capture of the propagate kernel
 # (second launch of `bench.py --steps 2 --warmup 1` with every extra section
 # off); None when the kernel has changed since that capture
-PROPAGATE_TRAFFIC_BYTES = 1.211938048e9 + 0.674147840e9
-PROPAGATE_FP64_PIPE_BUSY = 0.799
+PROPAGATE_TRAFFIC_BYTES = 1.210683904e9 + 0.673413120e9
+PROPAGATE_FP64_PIPE_BUSY = 0.7975
 # walkers per host process in the oracle sample (cpu_baseline and the
 # reference arm): one warm-up interval, then one timed 20-hop interval
 ORACLE_WALKERS_PER_PROC = 8

@@ -90,6 +90,19 @@ __device__ __forceinline__ double rsqrt_nr(double s) {
   return fma(y * e, fma(e, 0.375, 0.5), y);
 }
 
+// Tests on the integer image of a double, so that they issue no FP64-pipe
+// instruction (the order of non-negative doubles is that of their bit
+// patterns read as signed integers; a NaN has an image above +inf's).
+// x > 0 and not NaN (+inf included), as (x > 0.0) evaluates:
+__device__ __forceinline__ bool dpos(double x) {
+  const long long b = __double_as_longlong(x);
+  return b > 0 && b <= 0x7ff0000000000000ll;
+}
+// x != 0.0 (NaN counts as nonzero, as (x != 0.0) evaluates):
+__device__ __forceinline__ bool dnonzero(double x) { return (__double_as_longlong(x) << 1) != 0; }
+// x >= y for x, y >= 0 and not NaN:
+__device__ __forceinline__ bool dge_nonneg(double x, double y) { return __double_as_longlong(x) >= __double_as_longlong(y); }
+
 constexpr int ERF_INT = 73;               // intervals centred at k / 2, k = 0 .. 72
 constexpr int ERF_NC = 11;                // coefficients per interval (degree 10)
 constexpr double ERF_TMAX = 36.25;        // table end; erf(sqrt t) == 1 in double beyond t = 36

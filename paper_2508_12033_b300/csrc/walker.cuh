@@ -206,7 +206,7 @@ __device__ void all_potentials(const DevSys& S, const Layout& L, const double* x
         const double Z = __ldg(S.Z + I);
         if (__ldg(S.kind + I) == 0) {
           nu -= Z * ir;
-          nucap -= s >= a2 ? Z * ir : Z * ia;
+          nucap -= dge_nonneg(s, a2) ? Z * ir : Z * ia;
         } else {
           const double v = -Z * erf_over_r(s, ir, __ldg(S.irc + I), __ldg(S.irc2 + I), S.erftab);
           nu += v;
@@ -746,7 +746,7 @@ __device__ EvalOut eval_incr(const DevSys& S, const Layout& L, const double* __r
       const double ir = rsqrt_nr(s);
       // one Pade evaluation for both kinds; a nucleus without one-body term
       // (c = 0) contributes zeros and is evaluated at a dummy distance
-      const Pair p = pade_ir(pair || c != 0.0 ? ir : 1.0, c, b);
+      const Pair p = pade_ir(pair || dnonzero(c) ? ir : 1.0, c, b);
       const double f = p.up * p.ir, lap = p.upp + 2.0 * f;
       acc[0] += p.u;
       acc[1] = fma(f, dx, acc[1]); acc[2] = fma(f, dy, acc[2]); acc[3] = fma(f, dz, acc[3]);
@@ -782,7 +782,7 @@ __device__ EvalOut eval_incr(const DevSys& S, const Layout& L, const double* __r
         const double Z = __ldg(S.Z + I);
         if (__ldg(S.kind + I) == 0) {
           acc[6] -= Z * ir;
-          acc[7] -= s >= a2 ? Z * ir : Z * ia;
+          acc[7] -= dge_nonneg(s, a2) ? Z * ir : Z * ia;
         } else {
           const double v = -Z * erf_over_r(s, ir, __ldg(S.irc + I), __ldg(S.irc2 + I), S.erftab);
           acc[6] += v;
@@ -891,7 +891,7 @@ __device__ EvalOut eval_incr(const DevSys& S, const Layout& L, const double* __r
       const double* gg = geo + (m * nn + I) * 4;
       c = -__ldg(S.j1A + I);
       b = __ldg(S.j1B + I);
-      s = c != 0.0 ? fma(sa + sa, gg[1 + ax], gg[0]) : 1.0;
+      s = dnonzero(c) ? fma(sa + sa, gg[1 + ax], gg[0]) : 1.0;
     }
     const double v = pade_value(s, c, b);
     tmp[CHK(o, L.s_phi5 - L.s_tmp)] = v;
@@ -990,7 +990,7 @@ __device__ EvalOut init_walker(const DevSys& S, const Layout& L, double* __restr
 __device__ __forceinline__ bool positive(double r) { return __double_as_longlong(r) > 0; }
 
 __device__ int choose_hop(const double* rat, int n_hop, double u, double total, int lane) {
-  if (!(total > 0.0)) return -1;
+  if (!dpos(total)) return -1;
   const long long t = __double_as_longlong(u * total);
   const int per = (n_hop + WARP - 1) / WARP, p0 = lane * per, p1 = min(n_hop, p0 + per);
   double own = 0.0;
@@ -1376,9 +1376,9 @@ __device__ void propagate_walker_impl(const DevSys& S, const Layout& L, double* 
       if (P.kind == 1) {
         // w <- w b_x, b_x = b_bar / (W - E_0)
         const double den = Wd - P.E0;
-        if (den > 0.0) {
+        if (dpos(den)) {
           // refined reciprocal (a few ulp) instead of the FP64 division's longer sequence
-          weight *= den >= 0x1p-1000 ? bbar * rcp_nr(den) : bbar / den;
+          weight *= dge_nonneg(den, 0x1p-1000) ? bbar * rcp_nr(den) : bbar / den;
         } else {
           weight *= 0.0;
           status |= ST_NEG_DIAG;

@@ -1026,7 +1026,7 @@ __device__ EvalOut init_walker_m(const DevSys& S, const Layout& L, const LayoutM
 // if rounding leaves none), with the running sums formed by warp scans over
 // chunks of 32 hops in FP32; total is the evaluation's sum of kept ratios.
 __device__ int choose_hop_m(const float* dl, int n_hop, double u, double total, int lane) {
-  if (!(total > 0.0)) return -1;
+  if (!dpos(total)) return -1;
   const float t = (float)(u * total);
   float base = 0.f;
   int last = -1;
@@ -1282,9 +1282,9 @@ __device__ void propagate_walker_m(const DevSys& S, const Layout& L, const Layou
       step_uniforms(P.seed, (uint32_t)w, (uint32_t)k, P.interval, u_tau, u_move);
       if (P.kind == 1) {
         const double den = Wd - P.E0;
-        if (den > 0.0) {
+        if (dpos(den)) {
           // refined reciprocal (a few ulp) instead of the FP64 division's longer sequence
-          weight *= den >= 0x1p-1000 ? bbar * rcp_nr(den) : bbar / den;
+          weight *= dge_nonneg(den, 0x1p-1000) ? bbar * rcp_nr(den) : bbar / den;
         } else {
           weight *= 0.0;
           status |= ST_NEG_DIAG;

@@ -109,3 +109,28 @@ def test_h2_lattice_extrapolation_reaches_exact_energy():
     sigma = float(np.sqrt(cov[0, 0]))
     assert sigma < 2e-3
     assert abs(coef[0] - (-1.17447)) <= 2.0 * sigma, (coef[0], sigma)
+
+
+def test_h2_schedules_sample_the_same_energy():
+    """The paper's equivalence of the two algorithms (Sec. II.C and its
+    comparison of conventional and load-balanced LRDMC): at the same lattice
+    spacing and the same mean number of moves per branching interval, the
+    conventional and load-balanced runs of H2 at its stated size estimate the
+    same energy, within 2 sigma combined."""
+    from gpu_helpers import lib_or_skip
+    P = lib_or_skip()
+    s = W.h2_sto3g()
+    x0 = W.initial_walkers(s, N_W, seed=11)
+    tau = _tau(s, x0, 2)
+    E, err, moves = {}, {}, {}
+    for schedule in (OL.LOAD_BALANCED, OL.CONVENTIONAL):
+        lr = P.Lrdmc(s, x0, A, seed=SEED, p_gbar=10, n_equil=10, node_rule=2)
+        for _ in range(N_BRANCH):
+            lr.propagate(schedule, n_proj=N_PROJ, tau=tau, max_moves=100000)
+            lr.branch()
+        E[schedule], err[schedule] = lr.energy()
+        moves[schedule] = float(np.mean(lr.history()["moves_mean"]))
+        lr.close()
+    assert abs(moves[OL.CONVENTIONAL] - N_PROJ) < 0.5          # tau gives the same mean move count
+    d = abs(E[OL.LOAD_BALANCED] - E[OL.CONVENTIONAL])
+    assert d <= 2.0 * np.hypot(err[OL.LOAD_BALANCED], err[OL.CONVENTIONAL]), (E, err)
