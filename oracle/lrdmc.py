@@ -253,14 +253,19 @@ def reconfigure_indices(w, xi32: int):
 def branch_stats(W: Walkers, E0, schedule):
     """(wbar, ebar) before reconfiguration: Eq. for the walker-averaged local
     energy (conventional, weights w) or its load-balanced form (weights
-    w / (W(x) - E_0))."""
+    w / (W(x) - E_0)).  The averages run over the walkers of the population:
+    a walker of zero weight (the load-balanced step sets w = 0 where
+    W - E_0 <= 0) carries no weight and contributes nothing, also when its
+    e_L or W is not finite."""
     w = W.w
     wbar = float(np.sum(w)) / len(w)
+    live = w != 0.0
+    wl = w[live]
     if schedule == LOAD_BALANCED:
-        f = w / (W.ev["W"] - E0)
+        f = wl / (W.ev["W"][live] - E0)
     else:
-        f = w
-    ebar = float(np.sum(f * W.ev["eL"]) / np.sum(f))
+        f = wl
+    ebar = float(np.sum(f * W.ev["eL"][live]) / np.sum(f))
     return wbar, ebar
 
 

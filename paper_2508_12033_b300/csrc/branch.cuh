@@ -42,10 +42,15 @@ __device__ void branch_reduce_body(const Layout& L, const double* __restrict__ s
     const double* sc = state + (size_t)a * L.g_stride + L.g_sc;
     const double w = sc[SC_W], e = sc[SC_EL];
     acc[0] += w;
-    acc[1] += w * e;
-    const double f = lb ? w / (sc[SC_WDIAG] - E0) : w;
-    acc[2] += f;
-    acc[3] += f * e;
+    if (w != 0.0) {
+      // a walker of zero weight is no longer part of the population: it adds
+      // nothing to the averages, also when its e_L or W is not finite (the
+      // load-balanced step sets w = 0 where W - E_0 <= 0 or W is NaN)
+      acc[1] += w * e;
+      const double f = lb ? w / (sc[SC_WDIAG] - E0) : w;
+      acc[2] += f;
+      acc[3] += f * e;
+    }
     acc[4] += sc[SC_MOVES];
     acc[5] = fmax(acc[5], sc[SC_MOVES]);
     orv |= (unsigned)sc[SC_STATUS];
@@ -307,10 +312,15 @@ __global__ void __launch_bounds__(BP_THREADS) k_branch_partials(Layout L, const 
     const double* sc = state + (size_t)a * L.g_stride + L.g_sc;
     const double w = sc[SC_W], e = sc[SC_EL];
     acc[0] += w;
-    acc[1] += w * e;
-    const double f = lb ? w / (sc[SC_WDIAG] - E0) : w;
-    acc[2] += f;
-    acc[3] += f * e;
+    if (w != 0.0) {
+      // a walker of zero weight is no longer part of the population: it adds
+      // nothing to the averages, also when its e_L or W is not finite (the
+      // load-balanced step sets w = 0 where W - E_0 <= 0 or W is NaN)
+      acc[1] += w * e;
+      const double f = lb ? w / (sc[SC_WDIAG] - E0) : w;
+      acc[2] += f;
+      acc[3] += f * e;
+    }
     acc[4] += sc[SC_MOVES];
     acc[5] = fmax(acc[5], sc[SC_MOVES]);
     orv |= (unsigned)sc[SC_STATUS];

@@ -328,3 +328,20 @@ def test_fixed_lattice_after_randomised_interval_reevaluates_on_the_axes():
                 s0, l0 = WF.log_psi(s, Wk.x[n])
                 ref = s1 * s0 * np.exp(l1 - l0)
                 assert abs(Wk.ev["ratios"].reshape(6, -1)[n, 6 * i + d] - ref) <= 1e-10 * max(1.0, abs(ref))
+
+
+def test_zero_weight_walkers_carry_no_statistical_weight():
+    """Sec. II.A: the walker-averaged local energy runs over the population
+    with weights w; a walker of zero weight (the load-balanced step zeroes the
+    weight where W - E_0 <= 0) adds nothing, even with a non-finite e_L or W,
+    and the mean weight still counts it in N_w."""
+    import numpy as np
+    from oracle import lrdmc as L
+    ev = {"eL": np.array([-1.0, -2.0, np.nan, -4.0]), "W": np.array([3.0, 4.0, np.nan, 6.0])}
+    Wk = L.Walkers(x=np.zeros((4, 1, 3)), w=np.array([1.0, 2.0, 0.0, 1.0]), ev=ev,
+                   status=np.zeros(4, np.uint32), moves=np.zeros(4, np.int64))
+    wbar, ebar = L.branch_stats(Wk, 1.0, L.CONVENTIONAL)
+    assert wbar == 1.0 and ebar == (-1.0 - 4.0 - 4.0) / 4.0
+    wbar, ebar = L.branch_stats(Wk, 1.0, L.LOAD_BALANCED)
+    f = np.array([1.0 / 2.0, 2.0 / 3.0, 1.0 / 5.0])
+    assert abs(ebar - float(np.sum(f * np.array([-1.0, -2.0, -4.0])) / np.sum(f))) < 1e-15
