@@ -758,7 +758,11 @@ def main():
             "large_systems": res["large"],
             "gpu_launches": res["launches"],
             "clocks": res["clocks"],
-            "energy": {"E": res["energy"][0], "err": res["energy"][1]},
+            "energy_unequilibrated": {"E": res["energy"][0], "err": res["energy"][1],
+                                      "note": "estimator over the bench's ~30 water-methane intervals: not "
+                                              "equilibrated (the synthetic Hamiltonian's ground state lies far "
+                                              "below the random-MO trial function); the H2 sections give "
+                                              "converged energies"},
         }
         print(json.dumps(line))
     if world > 1:
