@@ -1,0 +1,41 @@
+"""Node-crossing hops on the GPU pinned by exact diagonalisation.
+
+The hydrogen atom with the p_z guiding function z exp(-0.1 r^2) (nodal plane
+z = 0, the node of the exact 2p states): every hop across the plane is
+removed by the fixed-node rule and its |ratio| moves into V_sf, and the cap
+nu^a applies to the electron at such sites (Appendix D).  On the lattice
+a (Z^3 + 1/2), a = 0.4, the projection must converge to the lowest eigenvalue
+of that fixed-node lattice Hamiltonian, computed exactly from the paper's
+definitions (tests/lattice_ed.py, box of 96^3 sites: converged to 1e-7).
+Long runs of both schedules, each within 3 sigma (block-jackknife errors;
+the diffuse 2p state decorrelates slowly, so the runs are long) of the exact
+value; both schedules also agree with each other within 3 sigma combined."""
+import numpy as np
+import pytest
+
+import workloads as W
+from lattice_ed import pz_lattice_ground_energy
+
+pytestmark = pytest.mark.gpu
+
+
+def test_node_crossing_runs_reach_the_exact_fixed_node_lattice_energy():
+    from gpu_helpers import lib_or_skip
+    P = lib_or_skip()
+    a, beta = 0.4, 0.1
+    e_exact = pz_lattice_ground_energy(beta, a, 96)
+    s = W.hydrogen_atom_pz(beta)
+    res = {}
+    for kind in (P.LOAD_BALANCED, P.CONVENTIONAL):
+        lr = P.Lrdmc(s, W.lattice_walkers(16384, a, seed=4, spread=12), a, seed=5, p_gbar=20, n_equil=400)
+        for _ in range(1600):
+            lr.propagate(kind, n_proj=15, tau=15 / (6 / (2 * a * a)), max_moves=5000)
+            lr.branch()
+        E, err = lr.energy()
+        assert lr.history()["status_or"].max() == 0
+        assert np.isfinite(err) and err < 3e-3
+        assert abs(E - e_exact) <= 3.0 * err + 1e-4, (kind, E, err, e_exact)
+        res[kind] = (E, err)
+        lr.close()
+    (e1, s1), (e0, s0) = res[P.LOAD_BALANCED], res[P.CONVENTIONAL]
+    assert abs(e1 - e0) <= 3.0 * np.hypot(s1, s0)

@@ -345,3 +345,32 @@ def test_zero_weight_walkers_carry_no_statistical_weight():
     wbar, ebar = L.branch_stats(Wk, 1.0, L.LOAD_BALANCED)
     f = np.array([1.0 / 2.0, 2.0 / 3.0, 1.0 / 5.0])
     assert abs(ebar - float(np.sum(f * np.array([-1.0, -2.0, -4.0])) / np.sum(f))) < 1e-15
+
+
+def test_nodal_lattice_hamiltonian_matches_the_oracle_evaluation():
+    """Node-crossing pieces of Appendix D pinned against the Hamiltonian built
+    from the definitions (tests/lattice_ed.py): for the p_z guiding function
+    of the hydrogen atom, at lattice sites on both sides of the nodal plane,
+    next to it and next to the nucleus, the oracle's sum of kept ratios
+    (2 a^2 b_bar), V_sf and W equal the definitions' values (the cap applied
+    exactly where a hop crosses the node); and the lowest eigenvalue of H^a
+    has converged in the box size used by the GPU pin."""
+    from lattice_ed import pz_lattice_ground_energy, pz_site_terms
+    from oracle import hamiltonian as ham
+    s = W.hydrogen_atom_pz(0.1)
+    a = 0.4
+    rng = np.random.default_rng(3)
+    n = rng.integers(-12, 12, size=(400, 3)).astype(float)
+    n[:20, 2] = rng.choice([-1.0, 0.0], 20)                 # next to the nodal plane
+    n[20:40] = rng.integers(-1, 1, size=(20, 3))              # next to the nucleus
+    x = a * (n + 0.5)
+    kept, vsf, Wd, node = pz_site_terms(0.1, a, x[:, 0], x[:, 1], x[:, 2])
+    ev = ham.evaluate(s, x[:, None, :], a, node_rule=0)
+    assert node.sum() > 30 and (~node).sum() > 300
+    np.testing.assert_allclose(ev["bbar"] * 2 * a * a, kept, rtol=1e-12)
+    np.testing.assert_allclose(ev["vsf"], vsf, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(ev["W"], Wd, rtol=1e-12)
+    assert np.array_equal(ev["n_node"] > 0, node)
+    e80, e96 = pz_lattice_ground_energy(0.1, a, 80), pz_lattice_ground_energy(0.1, a, 96)
+    assert abs(e80 - e96) < 1e-6
+    assert -0.125 < e96 < -0.12       # above the exact 2p energy, by the lattice bias at a = 0.4

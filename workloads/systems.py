@@ -141,6 +141,13 @@ def hydrogen_atom_gauss(beta: float = 8.0 / (9.0 * math.pi)) -> System:
                   [(0, 0, [(beta, 1.0)])], [[1.0]], 0.0, 0.0, 1.0, [0.0], [0.0])
 
 
+def hydrogen_atom_pz(beta: float = 0.1) -> System:
+    """One electron, bare proton, Gaussian p_z trial function z exp(-beta r^2):
+    its nodal plane z = 0 is the node of the exact 2p states."""
+    return _build("H-atom-pz", [[0, 0, 0]], [1.0], [0], [0.0], 1, 0,
+                  [(0, 1, [(beta, 1.0)])], [[0.0, 0.0, 1.0]], 0.0, 0.0, 1.0, [0.0], [0.0])
+
+
 STO3G_H_EXPS = (3.42525, 0.62391, 0.16886)
 STO3G_H_COEFS = (0.15433, 0.53533, 0.44463)
 
