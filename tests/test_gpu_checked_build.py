@@ -2,8 +2,8 @@
 index of the walker and branching kernels is tested against its extent; a
 violation is recorded in a device word and the access redirected, so nothing
 faults or traps.  This file runs the small per-configuration and per-interval
-parity cases and the host-injected failures (NaN and coincident walkers)
-under the checked library in a child process (the library is
+parity cases, the batched kernels and the host-injected failures (NaN and
+coincident walkers) under the checked library in a child process (the library is
 chosen when the binding loads, once per process); the autouse fixture of
 conftest.py then requires the violation word to be zero after every test, and
 the self-test below shows that a violation is recorded and cleared."""
@@ -47,7 +47,7 @@ def test_small_parity_cases_pass_under_the_checked_build():
     build.build()
     env = dict(os.environ, LRDMC_CHECKED="1")
     files = ["tests/test_gpu_checked_build.py", "tests/test_gpu_parity.py", "tests/test_gpu_mixed.py",
-             "tests/test_gpu_drift.py", "tests/test_gpu_failures.py"]
+             "tests/test_gpu_drift.py", "tests/test_gpu_failures.py", "tests/test_gpu_batch.py"]
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-m", "gpu", *files,
                         "-k", "not largest_size and not full_size and not energy_error_bar"],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=1800)
