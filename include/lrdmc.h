@@ -136,7 +136,7 @@ typedef struct {
  *                moved electron's gradient/Laplacian rows and the orbital
  *                differences of its six hops, rows x N_bf x N_orb) on the tensor
  *                cores: warp-level mma.sync with TF32 (2) or BF16 (3) operands
- *                and FP32 accumulation (north star, precision direction); 4 =
+ *                and FP32 accumulation; 4 =
  *                as 2 with each FP32 operand split into two TF32 parts and
  *                three MMAs per product (hi*hi + hi*lo + lo*hi), close to
  *                FP32 accuracy on the tensor cores                            */

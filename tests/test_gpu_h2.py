@@ -12,7 +12,7 @@ every electron) W is bounded below and the run is stable; with the paper's
 per-electron rule (0) the load-balanced estimate is dominated by such
 walkers.  Both are compared: the GPU must reproduce the oracle in either case.
 
-Acceptance (the benchmark spec): run means within 2 sigma of each other, sigma the
+Acceptance: run means within 2 sigma of each other, sigma the
 two runs' block-jackknife errors combined in quadrature.  Both programs draw
 the same Philox streams and take the same hops, so the per-interval histories
 (mean weight and walker-averaged local energy) also agree to floating-point
