@@ -934,15 +934,30 @@ __device__ EvalOut eval_incr(const DevSys& S, const Layout& L, const double* __r
       if (task < n_task && part == 0) hD[p] = det;
     }
   }
-  // (F) pair Jastrow sums of the other electrons' hops: swap the term with m
-  for (int p = lane; p < P; p += WARP) {
-    const int i = p / 6;
-    if (i == m) continue;
-    const int d = p - 6 * i;
-    const double vn = tmp[(d ^ 1) * per + (i < m ? i : i - 1)];
-    double* u = scr.u2 + (size_t)m * P + p;
-    hJ2[p] += vn - *u;
-    *u = vn;
+  // (F) pair Jastrow sums of the other electrons' hops: swap the term with m.
+  // Up to four old terms per lane are loaded before any store, so that their
+  // global-memory latencies overlap (a store through one pointer could alias
+  // the next load, which would otherwise serialise them).
+  {
+    double* um = scr.u2 + (size_t)m * P;
+    for (int base = 0; base < P; base += 4 * WARP) {
+      double vn[4], uo[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int p = base + k * WARP + lane, i = p / 6;
+        const bool ok = p < P && i != m;
+        vn[k] = ok ? tmp[((p - 6 * i) ^ 1) * per + (i < m ? i : i - 1)] : 0.0;
+        uo[k] = ok ? um[p] : 0.0;
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int p = base + k * WARP + lane, i = p / 6;
+        if (p < P && i != m) {
+          hJ2[p] += vn[k] - uo[k];
+          um[p] = vn[k];
+        }
+      }
+    }
   }
   __threadfence_block();
   __syncwarp();
@@ -1079,11 +1094,27 @@ __device__ void apply_hop(const DevSys& S, const Layout& L, double* __restrict__
     const int j = o / n, k = o - j * n;
     B[o] = fma(-row[k], f[j], B[o]);
   }
-  const int e0 = i - sr.ii;
-  for (int o = lane; o < n * L.n_bf; o += WARP) {
-    const int j = o / L.n_bf, mu = o - j * L.n_bf;
-    double* gj = g + (e0 + j) * L.n_bf + mu;
-    *gj = fma(-grow[mu], f[j], *gj);
+  // g_j -= f_j g_i over the spin block's rows (element o = j n_bf + mu), four
+  // loads per lane issued before their stores (overlapped latencies)
+  {
+    double* gb = g + (i - sr.ii) * L.n_bf;
+    const int nt = n * L.n_bf;
+    for (int base = 0; base < nt; base += 4 * WARP) {
+      double gv[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int o = base + k * WARP + lane;
+        gv[k] = o < nt ? gb[o] : 0.0;
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int o = base + k * WARP + lane;
+        if (o < nt) {
+          const int j = o / L.n_bf, mu = o - j * L.n_bf;
+          gb[o] = fma(-grow[mu], f[j], gv[k]);
+        }
+      }
+    }
   }
   for (int o = lane; o < 5 * L.n_max; o += WARP) cache[i * 5 * L.n_max + o] = phi5[o];
   double nu = 0.0, nucap = 0.0;

@@ -966,15 +966,29 @@ __device__ EvalOut eval_incr_m(const DevSys& S, const Layout& L, const LayoutM& 
   // (E) determinant differences of the refreshed block(s) from the cached
   // orbital differences
   det_diffs(L, M, sm, AR.dph, 6 * b0, 6 * b1, lane);
-  // (F) pair Jastrow differences of the other electrons' hops: swap the term with m
-  for (int p = lane; p < P; p += WARP) {
-    const int i = p / 6;
-    if (i == m) continue;
-    const int d = p - 6 * i;
-    const float vn = tmp[(d ^ 1) * per + (i < m ? i : i - 1)];
-    float* u = scr.u2 + (size_t)m * P + p;
-    hj2[p] += vn - *u;
-    *u = vn;
+  // (F) pair Jastrow differences of the other electrons' hops: swap the term
+  // with m; up to four old terms per lane loaded before any store (overlapped
+  // global-memory latencies)
+  {
+    float* um = scr.u2 + (size_t)m * P;
+    for (int base = 0; base < P; base += 4 * WARP) {
+      float vn[4], uo[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int p = base + k * WARP + lane, i = p / 6;
+        const bool ok = p < P && i != m;
+        vn[k] = ok ? tmp[((p - 6 * i) ^ 1) * per + (i < m ? i : i - 1)] : 0.f;
+        uo[k] = ok ? um[p] : 0.f;
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int p = base + k * WARP + lane, i = p / 6;
+        if (p < P && i != m) {
+          hj2[p] += vn[k] - uo[k];
+          um[p] = vn[k];
+        }
+      }
+    }
   }
   __threadfence_block();
   __syncwarp();
