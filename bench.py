@@ -41,8 +41,8 @@ FP64_UNIT_COUNT_GFLOPS = 148 * 2 * 2 * 2.032
 # FP64 pipe busy fraction, from one ncu capture of the propagate kernel
 # (second launch of `bench.py --steps 2 --warmup 1` with every extra section
 # off); None when the kernel has changed since that capture
-PROPAGATE_TRAFFIC_BYTES = 1.210683904e9 + 0.673413120e9
-PROPAGATE_FP64_PIPE_BUSY = 0.7975
+PROPAGATE_TRAFFIC_BYTES = 1.205245696e9 + 0.670677248e9
+PROPAGATE_FP64_PIPE_BUSY = 0.8265
 # walkers per host process in the oracle sample (cpu_baseline and the
 # reference arm): one warm-up interval, then one timed 20-hop interval
 ORACLE_WALKERS_PER_PROC = 8
@@ -53,6 +53,22 @@ ORACLE_WALKERS_PER_PROC = 8
 OP_EXP, OP_RSQ, OP_RCP, OP_ERF = 9.0, 6.0, 4.0, 15.0
 OP_PADE_VALUE = OP_RSQ + 1 + OP_RCP + 1          # u = c / (1/r + b)
 OP_PADE = OP_RSQ + 1 + OP_RCP + 1 + 1 + 2 + 3    # u, u', u'' and 1/r
+
+
+def json_line(obj) -> str:
+    """The result line as strict JSON: a value that is not finite (an error bar
+    over too few intervals) is written as null."""
+    def clean(v):
+        if isinstance(v, dict):
+            return {k: clean(x) for k, x in v.items()}
+        if isinstance(v, (list, tuple)):
+            return [clean(x) for x in v]
+        if isinstance(v, (float, np.floating)):
+            return float(v) if math.isfinite(v) else None
+        if isinstance(v, np.integer):
+            return int(v)
+        return v
+    return json.dumps(clean(obj), allow_nan=False)
 
 
 def algorithmic_ops_per_walker_step(n_e, n_nuc, n_bf, n_prim, n_sig, n_s_shell, n_p_shell):
@@ -696,7 +712,7 @@ def main():
                                  "sample": orc.describe()},
                 "e2e": {"value": v, "unit": "walker-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
                 "wall_s": time.perf_counter() - t0}
-        print(json.dumps(line))
+        print(json_line(line))
         return
     if world > 1:
         import torch
@@ -764,7 +780,7 @@ def main():
                                               "below the random-MO trial function); the H2 sections give "
                                               "converged energies"},
         }
-        print(json.dumps(line))
+        print(json_line(line))
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
