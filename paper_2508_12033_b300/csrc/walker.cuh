@@ -45,31 +45,41 @@ __device__ __forceinline__ void shell_derivs(const DevSys& S, int s, const doubl
   //   Slater: c1 = -z, c2 = z^2 - 2 z / r           (h' and lap h)
   //   s:      c1 = -2a, c2 = 4 a^2 r^2 - 6 a        (grad = c1 h d, lap h)
   //   p:      c1 = -2a, c2 = 4 a^2 r^2 - 10 a       (d_m times the radial part)
-  const bool sl = l == -1;
-  const double ir = sl ? rsqrt_nr(r2) : 0.0;
-  const double arg = sl ? r2 * ir : r2;
-  const double k6 = l == 1 ? 10.0 : 6.0;
   double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-  for (int q = 0; q < np; ++q) {
-    const double z = __ldg(S.exps + off + q);
-    const double h = __ldg(S.coefs + off + q) * exp_tab(-z * arg, T);
-    const double c1 = sl ? -z : -2.0 * z;
-    const double c2 = sl ? z * z - 2.0 * z * ir : (4.0 * z * z * r2 - k6 * z);
-    s0 += h;
-    s1 = fma(c1, h, s1);
-    s2 = fma(c2, h, s2);
+  if (l == -1) {
+    // Slater 1s (a branch of its own: a warp without Slater shells skips it)
+    const double ir = rsqrt_nr(r2);
+    const double r = r2 * ir;
+    for (int q = 0; q < np; ++q) {
+      const double z = __ldg(S.exps + off + q);
+      const double h = __ldg(S.coefs + off + q) * exp_tab(-z * r, T);
+      s0 += h;
+      s1 = fma(-z, h, s1);
+      s2 = fma(z * z - 2.0 * z * ir, h, s2);
+    }
+    s1 *= ir;   // grad = h' d / r
+  } else {
+    const double k6 = l == 1 ? 10.0 : 6.0;
+    for (int q = 0; q < np; ++q) {
+      const double z = __ldg(S.exps + off + q);
+      const double h = __ldg(S.coefs + off + q) * exp_tab(-z * r2, T);
+      s0 += h;
+      s1 = fma(-2.0 * z, h, s1);
+      s2 = fma(4.0 * z * z * r2 - k6 * z, h, s2);
+    }
   }
   if (l != 1) {
-    // Slater: grad = h' d / r; s: grad = c1 h d
-    const double g = sl ? s1 * ir : s1;
+    // s and Slater: grad = s1 d
     out[bf] = s0;
-    for (int m = 0; m < 3; ++m) out[(1 + m) * n_bf + bf] = g * d[m];
+    for (int m = 0; m < 3; ++m) out[(1 + m) * n_bf + bf] = s1 * d[m];
     out[4 * n_bf + bf] = s2;
   } else {
-    // d_m h: grad_n = delta_mn h - 2a d_m d_n h, lap = d_m (4a^2 r^2 - 10 a) h
+    // d_m h: grad_n = delta_mn h - 2a d_m d_n h, lap = d_m (4a^2 r^2 - 10 a) h;
+    // with t_m = d_m s1 the gradient takes one operation per component
     for (int m = 0; m < 3; ++m) {
+      const double t = d[m] * s1;
       out[bf + m] = d[m] * s0;
-      for (int n = 0; n < 3; ++n) out[(1 + n) * n_bf + bf + m] = (m == n ? s0 : 0.0) + d[m] * d[n] * s1;
+      for (int n = 0; n < 3; ++n) out[(1 + n) * n_bf + bf + m] = m == n ? fma(d[n], t, s0) : d[n] * t;
       out[4 * n_bf + bf + m] = d[m] * s2;
     }
   }
@@ -778,16 +788,19 @@ __device__ EvalOut eval_incr(const DevSys& S, const Layout& L, const double* __r
           gg[1] = dx; gg[2] = dy; gg[3] = dz;
         }
         // nu_ei and nu^a_ei (Appendix D): -Z/r and -Z/max(r, a), or the
-        // screened -Z erf(r/r_c)/r for both
+        // screened -Z erf(r/r_c)/r for both, as -Z v and -Z v_cap (only the
+        // screened kind spends FP64 work in its branch)
         const double Z = __ldg(S.Z + I);
+        double v, vcap;
         if (__ldg(S.kind + I) == 0) {
-          acc[6] -= Z * ir;
-          acc[7] -= dge_nonneg(s, a2) ? Z * ir : Z * ia;
+          v = ir;
+          vcap = dge_nonneg(s, a2) ? ir : ia;
         } else {
-          const double v = -Z * erf_over_r(s, ir, __ldg(S.irc + I), __ldg(S.irc2 + I), S.erftab);
-          acc[6] += v;
-          acc[7] += v;
+          v = erf_over_r(s, ir, __ldg(S.irc + I), __ldg(S.irc2 + I), S.erftab);
+          vcap = v;
         }
+        acc[6] = fma(-Z, v, acc[6]);
+        acc[7] = fma(-Z, vcap, acc[7]);
       }
     }
     const double tot = warp_sum8(acc, lane);
