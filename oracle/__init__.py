@@ -20,10 +20,11 @@ product path must never route through it.
 
 Parity status: every function is pinned by a test against something other than
 itself (closed forms, brute force, invariants, exact diagonalisation, an
-independent Philox implementation), except the two readings listed as
-"parity unpinned" in the design notes: the E_0 update rule / estimator
-parameters, and which electrons the nodal cap covers when several electrons
-are present (per electron or per configuration).  The node-crossing pieces
+independent Philox implementation), except two readings of the paper that
+only the agreement of the two implementations fixes ("parity unpinned"): the
+E_0 update rule / estimator parameters, and which electrons the nodal cap
+covers when several electrons are present (per electron or per
+configuration).  The node-crossing pieces
 themselves (removed hops, V_sf, the cap on an electron with such a hop) are
 pinned for one electron, where both rules coincide, by exact
 diagonalisation of the fixed-node lattice Hamiltonian of a nodal guiding
