@@ -843,6 +843,10 @@ __device__ EvalOut eval_incr_m(const DevSys& S, const Layout& L, const LayoutM& 
     for (int t = lane; t < per; t += WARP) {
       if (t < ne - 1) {
         const int j = t < m ? t : t + 1;
+        // the old pair terms first: the stores below could alias them
+        float* pm = scr.pt + 3 * (m * ne + j);
+        float* pj = scr.pt + 3 * (j * ne + m);
+        const float of = pm[0], ol = pm[1], oh = pm[2];
         const float pxj = xf[3 * j], pyj = xf[3 * j + 1], pzj = xf[3 * j + 2];
         const float dx = xm - pxj, dy = ym - pyj, dz = zm - pzj;
         const float s = sqdistf(dx, dy, dz);
@@ -858,9 +862,6 @@ __device__ EvalOut eval_incr_m(const DevSys& S, const Layout& L, const LayoutM& 
         gx = fmaf(f, dx, gx); gy = fmaf(f, dy, gy); gz = fmaf(f, dz, gz);
         LJ += lap;
         vee += hir;
-        float* pm = scr.pt + 3 * (m * ne + j);
-        float* pj = scr.pt + 3 * (j * ne + m);
-        const float of = pm[0], ol = pm[1], oh = pm[2];
         const float ox = pxj - xo0, oy = pyj - xo1, oz = pzj - xo2;
         float* q = ej + 5 * j;
         q[0] += f * -dx - of * ox;
