@@ -39,12 +39,13 @@ __device__ __forceinline__ void shell_derivs(const DevSys& S, int s, const doubl
   const int np = __ldg(S.sh_nprim + s);
   const int off = __ldg(S.sh_off + s);
   const int bf = CHK(__ldg(S.sh_bf + s), n_bf);
-  // one primitive loop for every shell kind (so that a warp with mixed kinds
-  // evaluates the exponentials once): h = c exp(-z r) for the Slater 1s kind,
-  // c exp(-a r^2) for Gaussians; s0 = sum h, s1 = sum c1 h, s2 = sum c2 h with
+  // h = c exp(-z r) for the Slater 1s kind, c exp(-a r^2) for Gaussians;
+  // s0 = sum h, s1 = sum c1 h, s2 = sum c2 h with
   //   Slater: c1 = -z, c2 = z^2 - 2 z / r           (h' and lap h)
   //   s:      c1 = -2a, c2 = 4 a^2 r^2 - 6 a        (grad = c1 h d, lap h)
   //   p:      c1 = -2a, c2 = 4 a^2 r^2 - 10 a       (d_m times the radial part)
+  // The Gaussian kinds share one primitive loop; the Slater kind has a loop of
+  // its own, which a warp without Slater shells (the usual case) skips.
   double s0 = 0.0, s1 = 0.0, s2 = 0.0;
   if (l == -1) {
     // Slater 1s (a branch of its own: a warp without Slater shells skips it)
