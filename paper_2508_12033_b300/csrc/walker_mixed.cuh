@@ -1308,7 +1308,7 @@ __device__ void propagate_walker_m(const DevSys& S, const Layout& L, const Layou
         double t = -log(1.0 - u_tau) / bbar;
         const bool clipped = !(t < tau_left);
         if (clipped) t = tau_left;
-        weight *= exp(-t * eL);
+        weight *= exp_tab(-t * eL, T);
         tau_left -= t;
         if (clipped) break;
       }
