@@ -41,8 +41,8 @@ FP64_UNIT_COUNT_GFLOPS = 148 * 2 * 2 * 2.032
 # FP64 pipe busy fraction, from one ncu capture of the propagate kernel
 # (second launch of `bench.py --steps 2 --warmup 1` with every extra section
 # off); None when the kernel has changed since that capture
-PROPAGATE_TRAFFIC_BYTES = 1.205646848e9 + 0.671259648e9
-PROPAGATE_FP64_PIPE_BUSY = 0.8266
+PROPAGATE_TRAFFIC_BYTES = 1.204502784e9 + 0.671022336e9
+PROPAGATE_FP64_PIPE_BUSY = 0.8270
 # walkers per host process in the oracle sample (cpu_baseline and the
 # reference arm): one warm-up interval, then one timed 20-hop interval
 ORACLE_WALKERS_PER_PROC = 8
