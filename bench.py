@@ -37,12 +37,16 @@ FP64_PEAK_GFLOPS = 1250.0      # nominal B300 FP64 rate (profiling recipe table)
 # FP64 rate from unit counts: 148 SMs x 2 FP64 FMA lanes per clock (the peak
 # ncu reports for the FP64 pipe) x 2 FLOP x 2.032 GHz maximum SM clock
 FP64_UNIT_COUNT_GFLOPS = 148 * 2 * 2 * 2.032
-# DRAM bytes (read + write) of one k_propagate launch of this workload and the
-# FP64 pipe busy fraction, from one ncu capture of the propagate kernel
-# (second launch of `bench.py --steps 2 --warmup 1` with every extra section
-# off); None when the kernel has changed since that capture
+# DRAM bytes (read + write) of one k_propagate launch of this workload, the
+# FP64 pipe busy fraction, and the FP64 warp instructions per walker-step with
+# their mean active lanes (sm__inst_executed_pipe_fp64,
+# sm__thread_inst_executed_pipe_fp64_pred_on), from one ncu capture of the
+# propagate kernel (second launch of `bench.py --steps 2 --warmup 1` with every
+# extra section off); None when the kernel has changed since that capture
 PROPAGATE_TRAFFIC_BYTES = 1.204502784e9 + 0.671022336e9
 PROPAGATE_FP64_PIPE_BUSY = 0.8270
+PROPAGATE_FP64_INST_PER_STEP = 51511632 / 81920
+PROPAGATE_FP64_ACTIVE_LANES = 1384697504 / 51511632
 # walkers per host process in the oracle sample (cpu_baseline and the
 # reference arm): one warm-up interval, then one timed 20-hop interval
 ORACLE_WALKERS_PER_PROC = 8
@@ -746,6 +750,8 @@ def main():
                                         "peaks here; MEASURED_PEAKS has no FP64 entry)",
                          "kernel_ms": res["prop_ms"], "fp64_ops_per_walker_step": res["slots"],
                          "fp64_pipe_busy_ncu": PROPAGATE_FP64_PIPE_BUSY,
+                         "fp64_warp_inst_per_walker_step_ncu": PROPAGATE_FP64_INST_PER_STEP,
+                         "fp64_active_lanes_ncu": PROPAGATE_FP64_ACTIVE_LANES,
                          "peak_unit_count": FP64_UNIT_COUNT_GFLOPS,
                          "frac_vs_unit_count": res["achieved"] / FP64_UNIT_COUNT_GFLOPS,
                          "peak_measured_dfma": measured,
