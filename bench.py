@@ -281,7 +281,11 @@ def run_gpu(args, rank, world):
     import torch
     import workloads as W
     from paper_2508_12033_b300 import build
-    build.build()
+    if rank == 0:
+        build.build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()                   # the other ranks load the library rank 0 made current
     import paper_2508_12033_b300 as P
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))

@@ -49,11 +49,12 @@ def build(force: bool = False, verbose: bool = False, checked: bool = True) -> s
     targets = [(LIB, ())] + ([(LIB_CHECKED, ("-DLRDMC_CHECKED",))] if checked else [])
     for lib, extra in targets:
         if force or is_stale(lib):
-            cmd = nvcc_command(lib + ".tmp", extra)
+            tmp = f"{lib}.{os.getpid()}.tmp"   # per process: concurrent builds never share a file
+            cmd = nvcc_command(tmp, extra)
             if verbose:
                 print(" ".join(cmd))
             subprocess.run(cmd, check=True)
-            os.replace(lib + ".tmp", lib)
+            os.replace(tmp, lib)
     return LIB
 
 
